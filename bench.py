@@ -1,0 +1,305 @@
+"""Benchmark: RSA-2048 CRT decryptions per second on GB300 (plus roofline data).
+
+One step = one rsa_modexp_key call decrypting the whole batch (65536 RSA-2048
+ciphertexts under one seeded key, CRT + constant-time fixed window), inputs
+resident in HBM.  Prints ONE JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload rsa2048|rsa4096] [--window 5] [--no-e2e] [--no-cpu]
+
+Multi-GPU (torchrun, one process per GPU): every rank decrypts its own full
+batch (weak scaling, no data exchange); the timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+WORKLOADS = {
+    "rsa2048": dict(bits=2048, count=65536,
+                    desc="RSA-2048 CRT decryption: 1 seeded key (two 1024-bit primes, Miller-Rabin 40 "
+                         "rounds, e=65537), 65536 ciphertexts uniform in [0,n) as 64 x u32 limbs"),
+    "rsa4096": dict(bits=4096, count=16384,
+                    desc="RSA-4096 CRT decryption: 1 seeded key (two 2048-bit primes, e=65537), 16384 "
+                         "ciphertexts uniform in [0,n) as 128 x u32 limbs"),
+}
+
+SM_COUNT_GB300 = 152
+IMAD_PER_SM_CLK = 64        # 32-bit integer multiply(-add) results per SM per clock
+IMAD_PER_PRODUCT = 2        # a 32x32->64 word product = low half + high half
+
+
+def derived_peak_tprod(sm_count: int, sm_mhz: float) -> float:
+    """Word products per second (x1e12) the IMAD pipe allows at sm_mhz."""
+    return sm_count * IMAD_PER_SM_CLK * sm_mhz * 1e6 / IMAD_PER_PRODUCT / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        loaded = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(key, rows, target_s: float = 12.0) -> dict:
+    """The oracle (CRT reference, as written) on every host core, on a bounded sample."""
+    import oracle
+    threads = oracle.default_threads()
+    probe = min(rows.shape[0], max(threads * 4, 64))
+    t0 = time.perf_counter()
+    oracle.crt_batch(rows[:probe], key.d, key.p, key.q, threads=threads)
+    rate = probe / (time.perf_counter() - t0)
+    n = int(min(rows.shape[0], max(probe, rate * target_s)))
+    t0 = time.perf_counter()
+    oracle.crt_batch(rows[:n], key.d, key.p, key.q, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "decrypts/s", "cores": threads, "kind": "oracle",
+            "sample": "first %d of the %d ciphertexts, oracle CRT routine (schoolbook multiply + "
+                      "Algorithm D + binary square-and-multiply), %d POSIX threads, %.1f s"
+                      % (n, rows.shape[0], threads, dt)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args, spec):
+    """--impl reference: the CPU oracle itself, timed per step on a bounded sample."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    key, rows = workloads.rsa_single(spec["bits"], spec["count"])
+    threads = oracle.default_threads()
+    probe = min(rows.shape[0], max(threads * 4, 64))
+    t0 = time.perf_counter()
+    oracle.crt_batch(rows[:probe], key.d, key.p, key.q, threads=threads)
+    rate = probe / (time.perf_counter() - t0)
+    # size each step so the whole run stays within a couple of minutes
+    per_step = int(max(threads, min(rows.shape[0], rate * 120.0 / max(1, args.steps + args.warmup))))
+    for _ in range(args.warmup):
+        oracle.crt_batch(rows[:per_step], key.d, key.p, key.q, threads=threads)
+    times = []
+    for k in range(args.steps):
+        lo = (k * per_step) % max(1, rows.shape[0] - per_step)
+        t0 = time.perf_counter()
+        oracle.crt_batch(rows[lo:lo + per_step], key.d, key.p, key.q, threads=threads)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = per_step / (ms / 1e3)
+    line = {
+        "impl": "reference", "metric": "RSA-%d CRT decrypts/sec" % spec["bits"], "value": value,
+        "unit": "decrypts/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "gpu_launches": 0,
+        "config": {"workload": spec["desc"], "step": "%d ciphertexts per step (bounded sample)" % per_step},
+        "cpu_baseline": {"value": value, "unit": "decrypts/s", "cores": threads, "kind": "oracle",
+                         "sample": "%d ciphertexts per step, oracle CRT routine, %d POSIX threads"
+                                   % (per_step, threads)},
+        "e2e": {"value": value, "unit": "decrypts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="rsa2048", choices=sorted(WORKLOADS))
+    ap.add_argument("--window", type=int, default=0)
+    ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    spec = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, spec)
+    if args.warmup < 3:
+        args.warmup = 3
+
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1407_1465_gb300 import RSA_EXP_PRIVATE_CRT, RsaContext, build, rsa_modexp_key, rsa_products_per_op
+    build.build()
+
+    key, rows = workloads.rsa_single(spec["bits"], spec["count"])
+    count, L = rows.shape
+    ctx = RsaContext(local, mem_budget_bytes=16 << 30)
+    kid = ctx.keyload(spec["bits"], key.n, key.e, key.d, key.p, key.q)
+    if args.window or args.warps or args.ctas_per_sm:
+        ctx.set_tuning(spec["bits"], RSA_EXP_PRIVATE_CRT, window=args.window, warps_per_cta=args.warps,
+                       ctas_per_sm=args.ctas_per_sm)
+    tune = ctx.get_tuning(spec["bits"], RSA_EXP_PRIVATE_CRT)
+    msgs = torch.from_numpy(rows.view(np.int32)).to(dev)
+    out = torch.empty_like(msgs)
+    status = torch.empty(count, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 126 MB of L2
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+
+    def step():
+        rsa_modexp_key(ctx.handle, kid, RSA_EXP_PRIVATE_CRT, count, msgs, out, status, sptr)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if not bool((status == 0).all()):
+        raise RuntimeError("warm-up produced non-OK statuses")
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    launches0 = ctx.stats()["kernel_launches"]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()                     # L2 flushed between timed steps (not timed)
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = ctx.stats()["kernel_launches"] - launches0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = sum(step_ms) / len(step_ms)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * count / (ms / 1e3)
+
+    # e2e: the host-buffer entry point, pinned host memory, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.from_numpy(rows.view(np.int32)).pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        from paper_1407_1465_gb300 import rsa_modexp_key_host
+        for _ in range(2):
+            rsa_modexp_key_host(ctx.handle, kid, RSA_EXP_PRIVATE_CRT, count, h_in.data_ptr(), h_out.data_ptr(),
+                                None, sptr)
+        ek = max(3, args.steps // 4)
+        if ws > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(ek):
+            rsa_modexp_key_host(ctx.handle, kid, RSA_EXP_PRIVATE_CRT, count, h_in.data_ptr(), h_out.data_ptr(),
+                                None, sptr)
+        e_s = (time.perf_counter() - t0) / ek
+        if ws > 1:
+            t = torch.tensor([e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_s = float(t.item())
+        e2e = {"value": ws * count / e_s, "unit": "decrypts/s", "h2d_bytes_per_step": count * L * 4,
+               "d2h_bytes_per_step": count * L * 4, "steps": ek,
+               "api": "rsa_modexp_key_host (pinned host buffers)"}
+        if not np.array_equal(h_out.numpy().view(np.uint32), out.cpu().numpy().view(np.uint32)):
+            raise RuntimeError("e2e output differs from the device-resident run")
+
+    prods = rsa_products_per_op(spec["bits"], RSA_EXP_PRIVATE_CRT, window=tune["window"])
+    achieved = prods * count / (ms / 1e3) / 1e12
+    peak = derived_peak_tprod(SM_COUNT_GB300, 2070.0)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tprod/s", "frac": achieved / peak,
+                "traffic": None,
+                "peak_note": "derived: 152 SMs x 64 IMAD lanes/clk x 2070 MHz / 2 IMAD per 32x32->64 word product",
+                "products_per_op": prods}
+    if clk.get("sm_mhz"):
+        roofline["frac_at_measured_clock"] = achieved / derived_peak_tprod(SM_COUNT_GB300, clk["sm_mhz"])
+
+    line = {
+        "metric": "RSA-%d CRT decrypts/sec" % spec["bits"], "value": value, "unit": "decrypts/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "gpu_launches": int(launches),
+        "config": {"workload": spec["desc"], "window": tune["window"], "warps_per_cta": tune["warps_per_cta"],
+                   "ctas_per_sm": tune["ctas_per_sm"], "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": "dp%d (independent batches per GPU)" % ws},
+        "wall_s": wall, "clocks": clk, "roofline": roofline, "e2e": e2e,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(key, rows)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

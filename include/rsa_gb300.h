@@ -1,0 +1,190 @@
+/*
+ * rsa_gb300.h -- C ABI of the GB300 (sm_103a) batched RSA modular
+ * exponentiation library (librsagpu.so).
+ *
+ * The operation (paper "Analysis of RSA Algorithm using GPU Programming",
+ * Sec. 2 and Sec. 3.2-3.3, and the decryption note of Sec. 11):
+ *     encryption  C = M^e mod n
+ *     decryption  M = C^d mod n
+ * with 0 <= M < n, n = p*q (key generation, Fig. 1).  Decryption can run
+ * through the Chinese remainder theorem (p and q supplied at key load), which
+ * gives the same value as C^d mod n for any d >= 1.
+ *
+ * Conventions for every entry point:
+ *   - Big numbers are arrays of 32-bit limbs, little-endian by limb (limb 0 is
+ *     the least significant); bytes inside a limb are in the machine's order.
+ *   - A key of nbits bits has L = nbits/32 limbs; its message and result rows
+ *     have exactly L limbs.  p and q have L/2 limbs each.
+ *   - "device pointer" arguments must point to memory of the context's device
+ *     (cudaMalloc'd or a PyTorch CUDA tensor); "host pointer" arguments to
+ *     ordinary host memory.  The caller owns every buffer it passes; the
+ *     library owns its key table and workspace, which count against the
+ *     memory budget given at context creation.
+ *   - Calls taking a stream (a cudaStream_t passed as void*, NULL = legacy
+ *     default stream) only enqueue work and return; nothing is implicitly
+ *     synchronised.  rsa_sync() waits for the stream and reports device-side
+ *     errors recorded since the previous rsa_sync().
+ *   - Return value: RSA_OK (0) or a negative rsa_status.  The message of the
+ *     most recent failure on the calling thread is in rsa_last_error().
+ *   - One context may be used from several host threads; calls are serialised
+ *     internally.
+ */
+#ifndef RSA_GB300_H
+#define RSA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rsa_ctx rsa_ctx; /* opaque, library-owned */
+
+typedef enum rsa_status {
+    RSA_OK = 0,
+    RSA_ERR_ARG = -1,         /* null pointer, bad enum, count out of range */
+    RSA_ERR_KEY = -2,         /* even modulus, p*q != n, zero exponent, unknown/unloaded key id,
+                                 private operation on a key loaded without d (or without p, q) */
+    RSA_ERR_RANGE = -3,       /* per operation: message >= n (its output row is zeroed) */
+    RSA_ERR_NOMEM = -4,       /* memory budget exceeded or device allocation failed */
+    RSA_ERR_CUDA = -5,        /* a CUDA runtime call failed */
+    RSA_ERR_TIMEOUT = -6,     /* a bounded device-side wait gave up */
+    RSA_ERR_UNSUPPORTED = -7  /* key size or operation kind not supported */
+} rsa_status;
+
+/* Which exponent an operation uses. */
+typedef enum rsa_exp_sel {
+    RSA_EXP_PUBLIC = 0,        /* x = e, variable-time binary method (e is public), Fig. 5 */
+    RSA_EXP_PRIVATE_CRT = 1,   /* x = d via p, q: two half-size constant-time fixed-window
+                                  exponentiations (Fig. 6 digits) and Garner recombination */
+    RSA_EXP_PRIVATE_PLAIN = 2  /* x = d directly mod n, constant-time fixed window */
+} rsa_exp_sel;
+
+/* Supported key sizes: nbits in {1024, 2048, 3072, 4096} (multi-limb path), and
+ * nbits = 32 for moduli below 2^32 (single-limb path of the paper's toy example,
+ * n = 17947, e = 131, d = 137, Sec. 2).  PRIVATE_CRT needs p and q; 3072/4096-bit
+ * PUBLIC and PRIVATE_PLAIN run on the wide-operand kernel. */
+
+/* Create a context on CUDA device `device`.  mem_budget_bytes caps the library's
+ * own device memory (key table + workspace); 0 selects 2 GiB.  *out receives the
+ * context.  Errors: RSA_ERR_ARG, RSA_ERR_CUDA. */
+int rsa_ctx_create(rsa_ctx **out, int device, size_t mem_budget_bytes);
+
+/* Release every key and all workspace.  Waits for work the library enqueued. */
+int rsa_ctx_destroy(rsa_ctx *ctx);
+
+/* Load a key (paper Fig. 1: public key (e, n), private key d, primes p, q).
+ * All pointers are host pointers and are copied; the library precomputes the
+ * per-key Montgomery constants (n' = -n^-1 mod 2^32, R mod n, R^2 mod n with
+ * R = 2^(32*L); for p and q also R^2, R^3 mod p|q, dp = d mod (p-1),
+ * dq = d mod (q-1), qinv = q^-1 mod p) and keeps them resident on the device.
+ *   n       L = nbits/32 limbs, odd, top limb nonzero for nbits >= 1024
+ *   e       e_limbs limbs (1 <= e_limbs <= L), e >= 1
+ *   d       L limbs or NULL (then only RSA_EXP_PUBLIC is allowed), d >= 1
+ *   p, q    L/2 limbs each, or both NULL (then RSA_EXP_PRIVATE_CRT is refused);
+ *           must be odd with p*q == n and gcd(p, q) == 1
+ * *key_id_out receives a small non-negative id.
+ * Errors: RSA_ERR_ARG, RSA_ERR_KEY, RSA_ERR_UNSUPPORTED, RSA_ERR_NOMEM, RSA_ERR_CUDA. */
+int rsa_keyload(rsa_ctx *ctx, uint32_t nbits, const uint32_t *n, const uint32_t *e,
+                uint32_t e_limbs, const uint32_t *d, const uint32_t *p, const uint32_t *q,
+                int32_t *key_id_out);
+
+/* Host only, no device needed: compute the key record rsa_keyload() would
+ * upload for the same arguments (header, n, R^2 mod n, R mod n, e, d, and for
+ * CRT keys p, q, R^2 and R^3 mod p|q, R mod p|q, qinv, dp, dq; the word layout
+ * is the one documented in the library's keyrec.h).  With rec == NULL only
+ * *rec_words is set.  Same validation and errors as rsa_keyload(), plus
+ * RSA_ERR_ARG when rec_capacity_words is too small. */
+int rsa_key_record(uint32_t nbits, const uint32_t *n, const uint32_t *e, uint32_t e_limbs,
+                   const uint32_t *d, const uint32_t *p, const uint32_t *q, uint32_t *rec,
+                   size_t rec_capacity_words, size_t *rec_words);
+
+/* Forget a key; its id may be reused.  Waits for work the library enqueued. */
+int rsa_keyunload(rsa_ctx *ctx, int32_t key_id);
+
+/* Query a loaded key: bit size, whether d and whether p, q were supplied. */
+int rsa_key_info(rsa_ctx *ctx, int32_t key_id, uint32_t *nbits, int32_t *has_d, int32_t *has_crt);
+
+/* Uniform batch: `count` operations, all under key `key_id` with exponent `exp_sel`.
+ *   msgs, out   device pointers to count rows of L limbs (row i at msgs + i*L);
+ *               out may equal msgs (in-place) but must not partially overlap it
+ *   op_status   device pointer to count int32 (RSA_OK or RSA_ERR_RANGE), or NULL
+ * Enqueued on `stream`.  Errors (returned before anything is enqueued):
+ * RSA_ERR_ARG, RSA_ERR_KEY, RSA_ERR_UNSUPPORTED, RSA_ERR_NOMEM, RSA_ERR_CUDA. */
+int rsa_modexp_key(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint64_t count,
+                   const uint32_t *msgs, uint32_t *out, int32_t *op_status, void *stream);
+
+/* Ragged batch: operation i uses key key_ids[i] (any loaded key, any size) and
+ * exponent exp_sel[i]; its message is the L_i limbs at msgs + limb_offsets[i]
+ * and its result goes to out + limb_offsets[i].  All five arrays are device
+ * pointers of `count` entries (op_status may be NULL).  The library groups the
+ * operations on the device by (key, exponent kind), forms tiles of 32, orders
+ * the tiles longest-first and runs them in one persistent kernel launch; the
+ * launch sequence is captured once into a CUDA graph and replayed.  Operations
+ * whose key id is invalid or whose exponent kind the key cannot serve get
+ * RSA_ERR_KEY in op_status and a zeroed row; rsa_sync() then also returns
+ * RSA_ERR_KEY.  Enqueued on `stream`. */
+int rsa_modexp_batch(rsa_ctx *ctx, uint64_t count, const int32_t *key_ids,
+                     const uint8_t *exp_sel, const uint64_t *limb_offsets,
+                     const uint32_t *msgs, uint32_t *out, int32_t *op_status, void *stream);
+
+/* Host-buffer forms of the two calls above: every pointer is a host pointer.
+ * The library copies the inputs to its device workspace, runs the batch on
+ * `stream`, copies the results back and waits for completion.  These are the
+ * end-to-end entry points (host->device and device->host copies included). */
+int rsa_modexp_key_host(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint64_t count,
+                        const uint32_t *msgs, uint32_t *out, int32_t *op_status, void *stream);
+int rsa_modexp_batch_host(rsa_ctx *ctx, uint64_t count, const int32_t *key_ids,
+                          const uint8_t *exp_sel, const uint64_t *limb_offsets,
+                          uint64_t total_limbs, const uint32_t *msgs, uint32_t *out,
+                          int32_t *op_status, void *stream);
+
+/* Wait for `stream` and return the first device-side error recorded since the
+ * previous call (RSA_ERR_KEY, RSA_ERR_TIMEOUT), RSA_ERR_CUDA, or RSA_OK. */
+int rsa_sync(rsa_ctx *ctx, void *stream);
+
+/* Message of the most recent failure on the calling thread ("" if none). */
+const char *rsa_last_error(void);
+
+/* Launch parameters of the multi-limb kernels.  Zero fields mean "automatic". */
+typedef struct rsa_tuning {
+    int32_t window;        /* fixed-window width w for private exponents, 1..6 */
+    int32_t warps_per_cta; /* warps per CTA (even for CRT: warp pairs) */
+    int32_t ctas_per_sm;   /* resident CTAs per SM the grid is sized for */
+} rsa_tuning;
+
+/* Set (or, with NULL, reset to automatic) the launch parameters used for keys of
+ * nbits bits and exponent kind exp_sel. */
+int rsa_set_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, const rsa_tuning *t);
+/* Read the parameters currently in force for (nbits, exp_sel). */
+int rsa_get_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, rsa_tuning *t);
+
+/* Counters since context creation. */
+typedef struct rsa_stats {
+    uint64_t kernel_launches;  /* kernels the library launched (graph replays count their kernels) */
+    uint64_t graph_launches;   /* CUDA graph replays */
+    uint64_t ops;              /* operations submitted */
+    uint64_t bytes_resident;   /* device bytes held against the budget */
+} rsa_stats;
+int rsa_get_stats(rsa_ctx *ctx, rsa_stats *s);
+
+/* Word products (32x32->64 multiplies) one operation costs under the counting
+ * rule 2L^2 + L per Montgomery multiplication on L limbs (operand-scanning
+ * CIOS, squarings counted as multiplications), for a key of nbits bits and
+ * exponent kind exp_sel: public exponents of e_bits bits with e_weight set
+ * bits (binary method), private ones at window width `window` (0 = 5).
+ * The figure behind the roofline numbers; it does not depend on the data. */
+double rsa_products_per_op(uint32_t nbits, int32_t exp_sel, uint32_t e_bits, uint32_t e_weight,
+                           int32_t window);
+
+/* Integer-multiply throughput probe on `device`: *imad_lanes_per_s receives
+ * 32-bit multiply-add lane-operations per second from independent mad.lo/
+ * mad.hi chains; *chain_products_per_s the 32x32->64 word products per second
+ * of mad.lo.cc / madc.hi.cc carry chains shaped like the modular multiply. */
+int rsa_imad_probe(int device, double *imad_lanes_per_s, double *chain_products_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RSA_GB300_H */

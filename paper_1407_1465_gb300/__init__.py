@@ -1,0 +1,260 @@
+"""Batched RSA modular exponentiation on GB300 (sm_103a).
+
+Python binding of the C ABI in include/rsa_gb300.h.  The functions below carry
+the C names and only marshal arguments (Python ints -> limb arrays, tensors ->
+device pointers, streams -> cudaStream_t); every step of the computation runs
+in the library's CUDA kernels.  PyTorch is used for device memory and streams.
+
+    ctx = RsaContext()
+    kid = ctx.keyload(2048, n, e, d, p, q)          # Python ints
+    out = ctx.modexp_key(kid, RSA_EXP_PRIVATE_CRT, msgs)  # msgs: CUDA uint32/int32 [count, L]
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (RSA_ERR_ARG, RSA_ERR_CUDA, RSA_ERR_KEY, RSA_ERR_NOMEM, RSA_ERR_RANGE,  # noqa: F401
+                   RSA_ERR_TIMEOUT, RSA_ERR_UNSUPPORTED, RSA_EXP_PRIVATE_CRT, RSA_EXP_PRIVATE_PLAIN,
+                   RSA_EXP_PUBLIC, RSA_OK, RsaError, check, last_error, rsa_stats, rsa_tuning)
+
+__all__ = [
+    "RsaContext", "RsaError", "int_to_limbs", "limbs_to_int",
+    "rsa_ctx_create", "rsa_ctx_destroy", "rsa_keyload", "rsa_key_record", "rsa_keyunload", "rsa_key_info",
+    "rsa_modexp_key", "rsa_modexp_batch", "rsa_modexp_key_host", "rsa_modexp_batch_host",
+    "rsa_sync", "rsa_last_error", "rsa_set_tuning", "rsa_get_tuning", "rsa_get_stats",
+    "rsa_products_per_op", "rsa_imad_probe",
+]
+
+
+def int_to_limbs(x: int, nlimbs: int) -> np.ndarray:
+    if x < 0 or x.bit_length() > 32 * nlimbs:
+        raise ValueError("value does not fit in %d limbs" % nlimbs)
+    return np.frombuffer(x.to_bytes(4 * nlimbs, "little"), dtype="<u4").astype(np.uint32)
+
+
+def limbs_to_int(a) -> int:
+    return int.from_bytes(np.ascontiguousarray(a, dtype=np.uint32).astype("<u4").tobytes(), "little")
+
+
+def _ptr(x):
+    """Device or host address of a tensor / ndarray / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError("cannot take the address of %r" % type(x))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+# ------------------------------------------------------------------ C-named functions
+
+def rsa_ctx_create(device: int = 0, mem_budget_bytes: int = 0) -> int:
+    h = ctypes.c_void_p()
+    check(_lib.lib().rsa_ctx_create(ctypes.byref(h), device, mem_budget_bytes))
+    return h.value
+
+
+def rsa_ctx_destroy(ctx: int) -> None:
+    check(_lib.lib().rsa_ctx_destroy(ctx))
+
+
+def rsa_keyload(ctx: int, nbits: int, n: int, e: int, d: int | None = None,
+                p: int | None = None, q: int | None = None) -> int:
+    L = max(1, nbits // 32)
+    hl = 1 if L == 1 else L // 2
+    na = int_to_limbs(n, L)
+    el = max(1, (e.bit_length() + 31) // 32)
+    ea = int_to_limbs(e, el)
+    da = int_to_limbs(d, L) if d is not None else None
+    pa = int_to_limbs(p, hl) if p is not None else None
+    qa = int_to_limbs(q, hl) if q is not None else None
+    kid = ctypes.c_int32(-1)
+    check(_lib.lib().rsa_keyload(ctx, nbits, _ptr(na), _ptr(ea), el, _ptr(da), _ptr(pa), _ptr(qa),
+                                 ctypes.byref(kid)))
+    return kid.value
+
+
+def rsa_key_record(nbits: int, n: int, e: int, d: int | None = None, p: int | None = None,
+                   q: int | None = None) -> np.ndarray:
+    """Host-only: the device key record rsa_keyload would upload (uint32 words)."""
+    L = max(1, nbits // 32)
+    hl = 1 if L == 1 else L // 2
+    na = int_to_limbs(n, L)
+    el = max(1, (e.bit_length() + 31) // 32)
+    ea = int_to_limbs(e, el)
+    da = int_to_limbs(d, L) if d is not None else None
+    pa = int_to_limbs(p, hl) if p is not None else None
+    qa = int_to_limbs(q, hl) if q is not None else None
+    words = ctypes.c_size_t(0)
+    check(_lib.lib().rsa_key_record(nbits, _ptr(na), _ptr(ea), el, _ptr(da), _ptr(pa), _ptr(qa), None, 0,
+                                    ctypes.byref(words)))
+    rec = np.zeros(words.value, dtype=np.uint32)
+    check(_lib.lib().rsa_key_record(nbits, _ptr(na), _ptr(ea), el, _ptr(da), _ptr(pa), _ptr(qa), _ptr(rec),
+                                    rec.size, ctypes.byref(words)))
+    return rec
+
+
+def rsa_keyunload(ctx: int, key_id: int) -> None:
+    check(_lib.lib().rsa_keyunload(ctx, key_id))
+
+
+def rsa_key_info(ctx: int, key_id: int) -> tuple[int, bool, bool]:
+    nb, hd, hc = ctypes.c_uint32(), ctypes.c_int32(), ctypes.c_int32()
+    check(_lib.lib().rsa_key_info(ctx, key_id, ctypes.byref(nb), ctypes.byref(hd), ctypes.byref(hc)))
+    return nb.value, bool(hd.value), bool(hc.value)
+
+
+def rsa_modexp_key(ctx: int, key_id: int, exp_sel: int, count: int, msgs, out, op_status=None,
+                   stream=None) -> None:
+    check(_lib.lib().rsa_modexp_key(ctx, key_id, exp_sel, count, _ptr(msgs), _ptr(out), _ptr(op_status),
+                                    _stream_ptr(stream)))
+
+
+def rsa_modexp_batch(ctx: int, count: int, key_ids, exp_sel, limb_offsets, msgs, out, op_status=None,
+                     stream=None) -> None:
+    check(_lib.lib().rsa_modexp_batch(ctx, count, _ptr(key_ids), _ptr(exp_sel), _ptr(limb_offsets),
+                                      _ptr(msgs), _ptr(out), _ptr(op_status), _stream_ptr(stream)))
+
+
+def rsa_modexp_key_host(ctx: int, key_id: int, exp_sel: int, count: int, msgs: np.ndarray, out: np.ndarray,
+                        op_status: np.ndarray | None = None, stream=None) -> None:
+    check(_lib.lib().rsa_modexp_key_host(ctx, key_id, exp_sel, count, _ptr(msgs), _ptr(out), _ptr(op_status),
+                                         _stream_ptr(stream)))
+
+
+def rsa_modexp_batch_host(ctx: int, count: int, key_ids, exp_sel, limb_offsets, total_limbs: int, msgs, out,
+                          op_status=None, stream=None) -> None:
+    check(_lib.lib().rsa_modexp_batch_host(ctx, count, _ptr(key_ids), _ptr(exp_sel), _ptr(limb_offsets),
+                                           total_limbs, _ptr(msgs), _ptr(out), _ptr(op_status),
+                                           _stream_ptr(stream)))
+
+
+def rsa_sync(ctx: int, stream=None) -> int:
+    """Waits for the stream; returns the device-side status (raises on CUDA errors)."""
+    rc = _lib.lib().rsa_sync(ctx, _stream_ptr(stream))
+    if rc == RSA_ERR_CUDA:
+        raise RsaError(rc, last_error())
+    return rc
+
+
+def rsa_last_error() -> str:
+    return last_error()
+
+
+def rsa_set_tuning(ctx: int, nbits: int, exp_sel: int, window: int = 0, warps_per_cta: int = 0,
+                   ctas_per_sm: int = 0, reset: bool = False) -> None:
+    if reset:
+        check(_lib.lib().rsa_set_tuning(ctx, nbits, exp_sel, None))
+        return
+    t = rsa_tuning(window, warps_per_cta, ctas_per_sm)
+    check(_lib.lib().rsa_set_tuning(ctx, nbits, exp_sel, ctypes.byref(t)))
+
+
+def rsa_get_tuning(ctx: int, nbits: int, exp_sel: int) -> dict:
+    t = rsa_tuning()
+    check(_lib.lib().rsa_get_tuning(ctx, nbits, exp_sel, ctypes.byref(t)))
+    return {"window": t.window, "warps_per_cta": t.warps_per_cta, "ctas_per_sm": t.ctas_per_sm}
+
+
+def rsa_get_stats(ctx: int) -> dict:
+    s = rsa_stats()
+    check(_lib.lib().rsa_get_stats(ctx, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in rsa_stats._fields_}
+
+
+def rsa_products_per_op(nbits: int, exp_sel: int, e: int = 65537, window: int = 5) -> float:
+    return _lib.lib().rsa_products_per_op(nbits, exp_sel, e.bit_length(), bin(e).count("1"), window)
+
+
+def rsa_imad_probe(device: int = 0) -> tuple[float, float]:
+    a, b = ctypes.c_double(), ctypes.c_double()
+    check(_lib.lib().rsa_imad_probe(device, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+# ------------------------------------------------------------------ convenience wrapper
+
+class RsaContext:
+    """Owns one library context; tensors in, tensors out."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0):
+        self.device = device
+        self.handle = rsa_ctx_create(device, mem_budget_bytes)
+        self._bits = {}
+
+    def close(self):
+        if self.handle:
+            rsa_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def keyload(self, nbits, n, e, d=None, p=None, q=None) -> int:
+        kid = rsa_keyload(self.handle, nbits, n, e, d, p, q)
+        self._bits[kid] = nbits
+        return kid
+
+    def keyunload(self, key_id: int) -> None:
+        rsa_keyunload(self.handle, key_id)
+        self._bits.pop(key_id, None)
+
+    def modexp_key(self, key_id: int, exp_sel: int, msgs, out=None, status=None, stream=None):
+        """msgs: CUDA tensor [count, L] of uint32 (or int32 bit patterns)."""
+        import torch
+        if out is None:
+            out = torch.empty_like(msgs)
+        count = msgs.shape[0] if msgs.dim() > 1 else msgs.numel()
+        rsa_modexp_key(self.handle, key_id, exp_sel, count, msgs, out, status, stream)
+        return out
+
+    def modexp_key_host(self, key_id: int, exp_sel: int, msgs: np.ndarray, out: np.ndarray | None = None,
+                        status: np.ndarray | None = None, stream=None) -> np.ndarray:
+        msgs = np.ascontiguousarray(msgs, dtype=np.uint32)
+        if out is None:
+            out = np.empty_like(msgs)
+        count = msgs.shape[0]
+        rsa_modexp_key_host(self.handle, key_id, exp_sel, count, msgs, out, status, stream)
+        return out
+
+    def modexp_batch(self, key_ids, exp_sel, limb_offsets, msgs, out=None, status=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(msgs)
+        rsa_modexp_batch(self.handle, key_ids.numel(), key_ids, exp_sel, limb_offsets, msgs, out, status, stream)
+        return out
+
+    def sync(self, stream=None) -> int:
+        return rsa_sync(self.handle, stream)
+
+    def set_tuning(self, nbits, exp_sel, **kw):
+        rsa_set_tuning(self.handle, nbits, exp_sel, **kw)
+
+    def get_tuning(self, nbits, exp_sel):
+        return rsa_get_tuning(self.handle, nbits, exp_sel)
+
+    def stats(self) -> dict:
+        return rsa_get_stats(self.handle)

@@ -1,0 +1,112 @@
+"""ctypes binding of librsagpu.so: the C ABI of include/rsa_gb300.h, same names.
+
+Argument marshalling only.  The library must have been built (``build.build()``);
+loading fails loudly otherwise -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librsagpu.so")
+
+RSA_OK = 0
+RSA_ERR_ARG = -1
+RSA_ERR_KEY = -2
+RSA_ERR_RANGE = -3
+RSA_ERR_NOMEM = -4
+RSA_ERR_CUDA = -5
+RSA_ERR_TIMEOUT = -6
+RSA_ERR_UNSUPPORTED = -7
+
+RSA_EXP_PUBLIC = 0
+RSA_EXP_PRIVATE_CRT = 1
+RSA_EXP_PRIVATE_PLAIN = 2
+
+STATUS_NAMES = {
+    0: "RSA_OK", -1: "RSA_ERR_ARG", -2: "RSA_ERR_KEY", -3: "RSA_ERR_RANGE", -4: "RSA_ERR_NOMEM",
+    -5: "RSA_ERR_CUDA", -6: "RSA_ERR_TIMEOUT", -7: "RSA_ERR_UNSUPPORTED",
+}
+
+
+class RsaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (STATUS_NAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class rsa_tuning(ctypes.Structure):
+    _fields_ = [("window", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32)]
+
+
+class rsa_stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_uint64), ("graph_launches", ctypes.c_uint64),
+                ("ops", ctypes.c_uint64), ("bytes_resident", ctypes.c_uint64)]
+
+
+class rsa_server_cfg(ctypes.Structure):
+    _fields_ = [("max_inflight_batches", ctypes.c_int32), ("batch_window_us", ctypes.c_int32),
+                ("max_batch_ops", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_uint64)]
+
+
+# (name, restype, argtypes) for every function declared in include/rsa_gb300.h
+_P = ctypes.c_void_p
+_U32P = ctypes.POINTER(ctypes.c_uint32)
+_I32P = ctypes.POINTER(ctypes.c_int32)
+SIGNATURES = [
+    ("rsa_ctx_create", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_size_t]),
+    ("rsa_ctx_destroy", ctypes.c_int, [_P]),
+    ("rsa_keyload", ctypes.c_int, [_P, ctypes.c_uint32, _P, _P, ctypes.c_uint32, _P, _P, _P, _I32P]),
+    ("rsa_key_record", ctypes.c_int, [ctypes.c_uint32, _P, _P, ctypes.c_uint32, _P, _P, _P, _P,
+                                      ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    ("rsa_keyunload", ctypes.c_int, [_P, ctypes.c_int32]),
+    ("rsa_key_info", ctypes.c_int, [_P, ctypes.c_int32, _U32P, _I32P, _I32P]),
+    ("rsa_modexp_key", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P]),
+    ("rsa_modexp_batch", ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, _P, _P, _P, _P, _P]),
+    ("rsa_modexp_key_host", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P]),
+    ("rsa_modexp_batch_host", ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, _P, ctypes.c_uint64, _P, _P, _P, _P]),
+    ("rsa_sync", ctypes.c_int, [_P, _P]),
+    ("rsa_last_error", ctypes.c_char_p, []),
+    ("rsa_set_tuning", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_int32, ctypes.POINTER(rsa_tuning)]),
+    ("rsa_get_tuning", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_int32, ctypes.POINTER(rsa_tuning)]),
+    ("rsa_get_stats", ctypes.c_int, [_P, ctypes.POINTER(rsa_stats)]),
+    ("rsa_products_per_op", ctypes.c_double, [ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint32,
+                                              ctypes.c_uint32, ctypes.c_int32]),
+    ("rsa_imad_probe", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]),
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib(path: str = LIB_PATH):
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError("librsagpu.so is not built (expected at %s); run "
+                                   "`python -m paper_1407_1465_gb300.build`" % path)
+            handle = ctypes.CDLL(path)
+            for name, res, args in SIGNATURES:
+                fn = getattr(handle, name, None)
+                if fn is None:
+                    continue
+                fn.restype = res
+                fn.argtypes = args
+            _lib = handle
+    return _lib
+
+
+def last_error() -> str:
+    return (lib().rsa_last_error() or b"").decode()
+
+
+def check(rc: int) -> int:
+    if rc != RSA_OK:
+        raise RsaError(rc, last_error())
+    return rc

@@ -1,0 +1,55 @@
+// inst_unit.cuh -- body of one instantiation unit.  Before including, define
+// RSAGPU_UNIT (the CRT half size H of this unit, in limbs).  The unit holds
+//   crt_kernel<H, W>      for W in the instantiated window range
+//   plain_kernel<2H, W>   and pub_kernel<2H>   when 2H <= 64 (register-resident A)
+#include "kernels.cuh"
+#include "launch.h"
+
+#ifndef RSAGPU_UNIT
+#error "define RSAGPU_UNIT"
+#endif
+
+#define RSAGPU_CAT2(a, b) a##b
+#define RSAGPU_CAT(a, b) RSAGPU_CAT2(a, b)
+
+namespace rsagpu {
+
+namespace {
+constexpr int kH = RSAGPU_UNIT;
+constexpr int kL = 2 * kH;
+constexpr int kU = 8;  // outer CIOS block: 8 limbs of B per runtime iteration
+
+template <int W>
+const void *crt_fn() { return reinterpret_cast<const void *>(&crt_kernel<kH, W, kU>); }
+
+template <int W>
+const void *plain_fn() {
+  if constexpr (kL <= 64) return reinterpret_cast<const void *>(&plain_kernel<kL, W, kU>);
+  else return nullptr;
+}
+}  // namespace
+
+const void *RSAGPU_CAT(crt_kernel_fn_, RSAGPU_UNIT)(int W) {
+  switch (W) {
+    case 3: return crt_fn<3>();
+    case 4: return crt_fn<4>();
+    case 5: return crt_fn<5>();
+    case 6: return crt_fn<6>();
+    default: return nullptr;
+  }
+}
+
+const void *RSAGPU_CAT(plain_kernel_fn_, RSAGPU_UNIT)(int W) {
+  switch (W) {
+    case 4: return plain_fn<4>();
+    case 5: return plain_fn<5>();
+    default: return nullptr;
+  }
+}
+
+const void *RSAGPU_CAT(pub_kernel_fn_, RSAGPU_UNIT)() {
+  if constexpr (kL <= 64) return reinterpret_cast<const void *>(&pub_kernel<kL, kU>);
+  else return nullptr;
+}
+
+}  // namespace rsagpu

@@ -1,0 +1,34 @@
+// launch.h -- kernel lookup shared by the runtime and the instantiation units.
+//
+// Each instantiation unit (inst_*.cu) compiles the kernel templates for one
+// limb count; the runtime finds them through these functions and launches
+// them with cudaLaunchKernel.  A null return means "not instantiated".
+#pragma once
+#include <cstdint>
+
+namespace rsagpu {
+
+// CRT decryption, half size H limbs, window W
+const void *crt_kernel_fn(int H, int W);
+// plain private exponent mod n, L limbs, window W
+const void *plain_kernel_fn(int L, int W);
+// public exponent (binary method), L limbs
+const void *pub_kernel_fn(int L);
+// single-limb keys (n < 2^32)
+const void *toy_kernel_fn();
+
+// windows instantiated for the private-exponent kernels
+constexpr int kMinWindow = 3;
+constexpr int kMaxWindow = 6;
+
+#define RSAGPU_DECLARE_UNIT(X)                      \
+  const void *crt_kernel_fn_##X(int W);             \
+  const void *plain_kernel_fn_##X(int W);           \
+  const void *pub_kernel_fn_##X();
+
+RSAGPU_DECLARE_UNIT(16)
+RSAGPU_DECLARE_UNIT(32)
+RSAGPU_DECLARE_UNIT(48)
+RSAGPU_DECLARE_UNIT(64)
+
+}  // namespace rsagpu

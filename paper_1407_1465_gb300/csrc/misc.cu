@@ -1,0 +1,131 @@
+// misc.cu -- single-limb kernel (moduli below 2^32), the integer-multiply
+// throughput probe, and the kernel lookup across instantiation units.
+#include <cstdint>
+
+#include "keyrec.h"
+#include "kernels.cuh"
+#include "launch.h"
+#include "mont.cuh"
+
+namespace rsagpu {
+
+// ------------------------------------------------------------------ single-limb keys
+// The paper's own setting (Sec. 10: 8-bit-class keys, n = 131*137 = 17947):
+// each thread computes one message's x^E mod m with 64-bit products reduced by
+// "%" (Fig. 3), by left-to-right binary square-and-multiply (Fig. 5) over all
+// 32 exponent bit positions with the multiplication always performed and kept
+// by a mask, so the work does not depend on the exponent.
+__device__ __forceinline__ uint32_t pow_mod32(uint32_t x, uint32_t E, uint32_t m) {
+  uint64_t r = 1u % m;
+  const uint64_t xm = x % m;
+#pragma unroll 4
+  for (int b = 31; b >= 0; --b) {
+    r = (r * r) % m;
+    const uint64_t rx = (r * xm) % m;
+    const uint64_t keep = 0ull - (uint64_t)((E >> b) & 1u);
+    r = (rx & keep) | (r & ~keep);
+  }
+  return (uint32_t)r;
+}
+
+__global__ void toy_kernel(ToyArgs a) {
+  const KeyLayout lay(1);
+  const KeyHeader &hd = *reinterpret_cast<const KeyHeader *>(a.keyrec);
+  const uint32_t n = a.keyrec[lay.n];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.count; i += gridDim.x * blockDim.x) {
+    const uint32_t x = a.msgs[i];
+    const bool ok = x < n;
+    uint32_t r;
+    if (a.kind == 0) {
+      r = pow_mod32(x, a.keyrec[lay.e], n);
+    } else if (a.kind == 2) {
+      r = pow_mod32(x, a.keyrec[lay.d], n);
+    } else {
+      // CRT: m_p = x^dp mod p, m_q = x^dq mod q, h = qinv (m_p - m_q) mod p, m = m_q + h q
+      const uint32_t p = hd.reserved[0], q = hd.reserved[1];
+      const uint32_t mp = pow_mod32(x, hd.reserved[2], p);
+      const uint32_t mq = pow_mod32(x, hd.reserved[3], q);
+      const uint64_t diff = ((uint64_t)mp + p - (mq % p)) % p;
+      const uint64_t h = (diff * hd.reserved[4]) % p;
+      r = (uint32_t)(mq + h * q);
+    }
+    a.out[i] = ok ? r : 0u;
+    if (a.status) a.status[i] = ok ? 0 : -3;
+  }
+}
+
+const void *toy_kernel_fn() { return reinterpret_cast<const void *>(&toy_kernel); }
+
+// ------------------------------------------------------------------ lookup
+const void *crt_kernel_fn(int H, int W) {
+  switch (H) {
+    case 16: return crt_kernel_fn_16(W);
+    case 32: return crt_kernel_fn_32(W);
+    case 48: return crt_kernel_fn_48(W);
+    case 64: return crt_kernel_fn_64(W);
+    default: return nullptr;
+  }
+}
+const void *plain_kernel_fn(int L, int W) {
+  switch (L) {
+    case 32: return plain_kernel_fn_16(W);
+    case 64: return plain_kernel_fn_32(W);
+    default: return nullptr;
+  }
+}
+const void *pub_kernel_fn(int L) {
+  switch (L) {
+    case 32: return pub_kernel_fn_16();
+    case 64: return pub_kernel_fn_32();
+    default: return nullptr;
+  }
+}
+
+// ------------------------------------------------------------------ IMAD probe
+// Independent multiply-add chains: 8 accumulators, each step one mad.lo and
+// one mad.hi per accumulator (16 lane-operations per thread per step).
+__global__ void imad_probe_kernel(uint32_t *sink, uint32_t iters, uint32_t seed) {
+  uint32_t a[8], h[8];
+  const uint32_t b = seed * 2654435761u + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    a[k] = seed + 17u * k + blockIdx.x;
+    h[k] = seed ^ (31u * k);
+  }
+  for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a[k]) : "r"(b), "r"(h[k]));
+      asm volatile("mad.hi.u32 %0, %1, %2, %0;" : "+r"(h[k]) : "r"(a[k]), "r"(b));
+    }
+  }
+  uint32_t x = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x ^= a[k] ^ h[k];
+  if (x == 0x9e3779b9u) sink[blockIdx.x * blockDim.x + threadIdx.x] = x;
+}
+
+// Carry chains shaped like the modular multiply: per step, t[0..33] += b * a[0..31]
+// with the even/odd mad.lo.cc / madc.hi.cc chains of mul_acc (32 word products).
+__global__ void chain_probe_kernel(uint32_t *sink, uint32_t iters, uint32_t seed) {
+  uint32_t a[32], t[34];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) a[j] = seed * (j + 1) + threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < 34; ++j) t[j] = 0u;
+  uint32_t b = seed | 1u;
+  for (uint32_t it = 0; it < iters; ++it) {
+    mul_acc<32>(t, a, b);
+    b = t[33] ^ t[0] ^ b;  // keep b data dependent so nothing is hoisted
+    t[33] = 0u;
+  }
+  uint32_t x = 0;
+#pragma unroll
+  for (int j = 0; j < 34; ++j) x ^= t[j];
+  if (x == 0x9e3779b9u) sink[blockIdx.x * blockDim.x + threadIdx.x] = x;
+}
+
+const void *imad_probe_fn() { return reinterpret_cast<const void *>(&imad_probe_kernel); }
+const void *chain_probe_fn() { return reinterpret_cast<const void *>(&chain_probe_kernel); }
+
+}  // namespace rsagpu

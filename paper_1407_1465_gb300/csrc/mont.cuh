@@ -1,0 +1,264 @@
+// mont.cuh -- multi-limb Montgomery arithmetic for one operation per thread.
+//
+// The paper computes g^e mod n with built-in integers (Algorithm 2, Fig. 12)
+// and reduces every product with the identity of Fig. 3,
+// (u*v) mod m = ((u mod m)*(v mod m)) mod m.  For moduli of 1024-4096 bits this
+// library keeps numbers as L little-endian 32-bit limbs and replaces "mod m" by
+// Montgomery multiplication (operand-scanning CIOS form):
+//     mont_mul(A, B) = A * B * R^-1 mod N,   R = 2^(32L), N odd,
+// valid for A < R and B < N; the result is fully reduced (< N).
+//
+// Each CIOS step i adds b_i * A into the accumulator t and then adds q * N with
+// q = t_0 * n' mod 2^32 (n' = -N^-1 mod 2^32), which clears t_0, and shifts t
+// down one limb.  The products are issued as PTX carry chains
+// (mad.lo.cc / madc.hi.cc / madc.lo.cc ... alternating, addc to close a
+// chain), one chain over the even limbs and one over the odd limbs; a chain
+// cannot interleave with another because all share the single carry flag.
+//
+// Operand placement: A (the register operand) lives in registers; B is streamed
+// four limbs at a time from shared memory (a per-lane staging buffer or a
+// warp-uniform constant); N either sits in registers (NREG) or is read from
+// shared memory as warp-uniform 128-bit loads.
+#pragma once
+#include <cstdint>
+
+namespace rsagpu {
+
+// ------------------------------------------------------------------ PTX carry-chain primitives
+__device__ __forceinline__ uint32_t mad_lo_cc(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm volatile("mad.lo.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
+__device__ __forceinline__ uint32_t madc_lo_cc(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm volatile("madc.lo.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
+__device__ __forceinline__ uint32_t mad_hi_cc(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm volatile("mad.hi.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
+__device__ __forceinline__ uint32_t madc_hi_cc(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm volatile("madc.hi.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
+__device__ __forceinline__ uint32_t add_cc(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm volatile("add.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t addc_cc(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm volatile("addc.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t addc(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm volatile("addc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t sub_cc(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm volatile("sub.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t subc_cc(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm volatile("subc.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t subc(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm volatile("subc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+
+// ------------------------------------------------------------------ operand sources
+// B operand: four limbs (b_{4g} .. b_{4g+3}) per get4(g).
+// SmemB{stage + lane, 32}: per-lane staging buffer, layout [L/4][32] of uint4;
+// SmemB{konst, 1}: warp-uniform constant, layout [L/4] of uint4.
+struct SmemB {
+  const uint4 *base;
+  int stride;
+  __device__ __forceinline__ uint4 get4(int g) const { return base[g * stride]; }
+};
+
+// N operand
+template <int L>
+struct NRegs {             // N in registers
+  uint32_t n[L];
+  __device__ __forceinline__ void load(const uint4 *s) {
+#pragma unroll
+    for (int g = 0; g < L / 4; ++g) {
+      uint4 v = s[g];
+      n[4 * g] = v.x; n[4 * g + 1] = v.y; n[4 * g + 2] = v.z; n[4 * g + 3] = v.w;
+    }
+  }
+  __device__ __forceinline__ uint32_t get(int j) const { return n[j]; }
+};
+template <int L>
+struct NSmem {             // N read from shared memory (warp-uniform address)
+  const uint32_t *s;
+  __device__ __forceinline__ uint32_t get(int j) const { return s[j]; }
+};
+
+// ------------------------------------------------------------------ CIOS pieces
+// t[0 .. L+1] += b * a   (t < 2N on entry, so the sum fits in L+2 limbs).
+// Two carry chains: the even limbs of a (products land on limbs 2k, 2k+1) and
+// the odd limbs (limbs 2k+1, 2k+2).  Inside a chain the low and high halves of
+// each product are consumed back to back, so no product stays live.
+template <int L>
+__device__ __forceinline__ void mul_acc(uint32_t (&t)[L + 2], const uint32_t (&a)[L], uint32_t b) {
+  t[0] = mad_lo_cc(a[0], b, t[0]);
+  t[1] = madc_hi_cc(a[0], b, t[1]);
+#pragma unroll
+  for (int k = 1; k < L / 2; ++k) {
+    t[2 * k] = madc_lo_cc(a[2 * k], b, t[2 * k]);
+    t[2 * k + 1] = madc_hi_cc(a[2 * k], b, t[2 * k + 1]);
+  }
+  t[L] = addc_cc(t[L], 0u);
+  t[L + 1] = addc(t[L + 1], 0u);
+  t[1] = mad_lo_cc(a[1], b, t[1]);
+  t[2] = madc_hi_cc(a[1], b, t[2]);
+#pragma unroll
+  for (int k = 1; k < L / 2; ++k) {
+    t[2 * k + 1] = madc_lo_cc(a[2 * k + 1], b, t[2 * k + 1]);
+    t[2 * k + 2] = madc_hi_cc(a[2 * k + 1], b, t[2 * k + 2]);
+  }
+  t[L + 1] = addc(t[L + 1], 0u);
+}
+
+// q = t_0 * n'; t = (t + q*N) / 2^32.  Same even/odd chains as mul_acc; every
+// result is written one limb down (position p goes to t[p-1]), which is the
+// division by 2^32, done in place in increasing position order.
+template <int L, class NS>
+__device__ __forceinline__ void reduce_step(uint32_t (&t)[L + 2], const NS &N, uint32_t np) {
+  const uint32_t q = t[0] * np;
+  // even limbs of N: positions 2k, 2k+1
+  (void)mad_lo_cc(q, N.get(0), t[0]);  // position 0: = 0 mod 2^32, only the carry matters
+  t[0] = madc_hi_cc(q, N.get(0), t[1]);
+#pragma unroll
+  for (int k = 1; k < L / 2; ++k) {
+    t[2 * k - 1] = madc_lo_cc(q, N.get(2 * k), t[2 * k]);
+    t[2 * k] = madc_hi_cc(q, N.get(2 * k), t[2 * k + 1]);
+  }
+  t[L - 1] = addc_cc(t[L], 0u);
+  t[L] = addc(t[L + 1], 0u);
+  // odd limbs of N: positions 2k+1, 2k+2, now held at t[2k], t[2k+1]
+  t[0] = mad_lo_cc(q, N.get(1), t[0]);
+  t[1] = madc_hi_cc(q, N.get(1), t[1]);
+#pragma unroll
+  for (int k = 1; k < L / 2; ++k) {
+    t[2 * k] = madc_lo_cc(q, N.get(2 * k + 1), t[2 * k]);
+    t[2 * k + 1] = madc_hi_cc(q, N.get(2 * k + 1), t[2 * k + 1]);
+  }
+  t[L] = addc(t[L], 0u);
+  t[L + 1] = 0u;
+}
+
+// A = t - N if t >= N else t, without a branch (t < 2N, t[L] in {0,1}).
+template <int L, class NS>
+__device__ __forceinline__ void final_sub(uint32_t (&A)[L], const uint32_t (&t)[L + 2], const NS &N) {
+  uint32_t u[L];
+  u[0] = sub_cc(t[0], N.get(0));
+#pragma unroll
+  for (int j = 1; j < L; ++j) u[j] = subc_cc(t[j], N.get(j));
+  const uint32_t keep_t = subc(t[L], 0u);  // all ones iff t < N
+#pragma unroll
+  for (int j = 0; j < L; ++j) A[j] = (t[j] & keep_t) | (u[j] & ~keep_t);
+}
+
+// A = A * B * R^-1 mod N.  The outer loop runs over B in blocks of U limbs
+// (U a multiple of 4 dividing L): fully unrolled inside a block, a runtime
+// loop across blocks to bound the code size.
+template <int L, int U, class BS, class NS>
+__device__ __forceinline__ void mont_mul(uint32_t (&A)[L], const BS &B, const NS &N, uint32_t np) {
+  static_assert(L % 4 == 0 && U % 4 == 0 && L % U == 0, "limb blocking");
+  uint32_t t[L + 2];
+#pragma unroll
+  for (int j = 0; j < L + 2; ++j) t[j] = 0u;
+#pragma unroll 1
+  for (int i0 = 0; i0 < L; i0 += U) {
+#pragma unroll
+    for (int u = 0; u < U; u += 4) {
+      const uint4 b = B.get4((i0 + u) >> 2);
+      mul_acc<L>(t, A, b.x);
+      reduce_step<L>(t, N, np);
+      mul_acc<L>(t, A, b.y);
+      reduce_step<L>(t, N, np);
+      mul_acc<L>(t, A, b.z);
+      reduce_step<L>(t, N, np);
+      mul_acc<L>(t, A, b.w);
+      reduce_step<L>(t, N, np);
+    }
+  }
+  final_sub<L>(A, t, N);
+}
+
+// ------------------------------------------------------------------ modular add / sub
+// A = (A + B) mod N for A, B < N (B from a per-lane stage).
+template <int L, class NS>
+__device__ __forceinline__ void mod_add(uint32_t (&A)[L], const SmemB &B, const NS &N) {
+  uint32_t s[L];
+#pragma unroll
+  for (int g = 0; g < L / 4; ++g) {
+    const uint4 b = B.get4(g);
+    if (g == 0) s[0] = add_cc(A[0], b.x); else s[4 * g] = addc_cc(A[4 * g], b.x);
+    s[4 * g + 1] = addc_cc(A[4 * g + 1], b.y);
+    s[4 * g + 2] = addc_cc(A[4 * g + 2], b.z);
+    s[4 * g + 3] = addc_cc(A[4 * g + 3], b.w);
+  }
+  uint32_t t[L + 2];
+#pragma unroll
+  for (int j = 0; j < L; ++j) t[j] = s[j];
+  t[L] = addc(0u, 0u);
+  t[L + 1] = 0u;
+  final_sub<L>(A, t, N);
+}
+
+// A = (B - A) mod N for A, B < N (B from a per-lane stage): B - A, plus N on borrow.
+template <int L, class NS>
+__device__ __forceinline__ void mod_rsub(uint32_t (&A)[L], const SmemB &B, const NS &N) {
+  uint32_t s[L];
+#pragma unroll
+  for (int g = 0; g < L / 4; ++g) {
+    const uint4 b = B.get4(g);
+    if (g == 0) s[0] = sub_cc(b.x, A[0]); else s[4 * g] = subc_cc(b.x, A[4 * g]);
+    s[4 * g + 1] = subc_cc(b.y, A[4 * g + 1]);
+    s[4 * g + 2] = subc_cc(b.z, A[4 * g + 2]);
+    s[4 * g + 3] = subc_cc(b.w, A[4 * g + 3]);
+  }
+  const uint32_t neg = subc(0u, 0u);  // all ones iff B < A
+  A[0] = add_cc(s[0], N.get(0) & neg);
+#pragma unroll
+  for (int j = 1; j < L; ++j) A[j] = addc_cc(s[j], N.get(j) & neg);
+}
+
+// ------------------------------------------------------------------ staging helpers
+template <int L>
+__device__ __forceinline__ void to_stage(uint4 *stage_lane, const uint32_t (&A)[L]) {
+#pragma unroll
+  for (int g = 0; g < L / 4; ++g)
+    stage_lane[g * 32] = make_uint4(A[4 * g], A[4 * g + 1], A[4 * g + 2], A[4 * g + 3]);
+}
+template <int L>
+__device__ __forceinline__ void from_stage(uint32_t (&A)[L], const uint4 *stage_lane) {
+#pragma unroll
+  for (int g = 0; g < L / 4; ++g) {
+    const uint4 v = stage_lane[g * 32];
+    A[4 * g] = v.x; A[4 * g + 1] = v.y; A[4 * g + 2] = v.z; A[4 * g + 3] = v.w;
+  }
+}
+template <int L>
+__device__ __forceinline__ void from_uniform(uint32_t (&A)[L], const uint4 *s) {
+#pragma unroll
+  for (int g = 0; g < L / 4; ++g) {
+    const uint4 v = s[g];
+    A[4 * g] = v.x; A[4 * g + 1] = v.y; A[4 * g + 2] = v.z; A[4 * g + 3] = v.w;
+  }
+}
+
+}  // namespace rsagpu

@@ -1,0 +1,527 @@
+// runtime.cu -- the C ABI (include/rsa_gb300.h): contexts, the device-resident
+// key table, per-stream workspace, launch sizing and dispatch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "keyprep.h"
+#include "keyrec.h"
+#include "kernels.cuh"
+#include "launch.h"
+#include "rsa_gb300.h"
+#include "runtime_internal.h"
+
+namespace rsagpu {
+
+thread_local std::string g_last_error;
+
+int set_error(int code, const std::string &msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char *what) {
+  return set_error(RSA_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+const void *imad_probe_fn();
+const void *chain_probe_fn();
+
+// ------------------------------------------------------------------ workspace
+int Ctx::reserve(size_t bytes) {
+  if (used + bytes > budget)
+    return set_error(RSA_ERR_NOMEM, "memory budget exceeded (" + std::to_string(used + bytes) +
+                                        " > " + std::to_string(budget) + " bytes)");
+  used += bytes;
+  return RSA_OK;
+}
+void Ctx::release(size_t bytes) { used -= std::min(used, bytes); }
+
+int Ctx::ensure(DevBuf &b, size_t need) {
+  if (need <= b.bytes) return RSA_OK;
+  size_t want = std::max(need, b.bytes + b.bytes / 2);
+  if (used - b.bytes + want > budget) want = need;
+  if (b.ptr) {
+    cudaFree(b.ptr);
+    release(b.bytes);
+    b.ptr = nullptr;
+    b.bytes = 0;
+  }
+  int rc = reserve(want);
+  if (rc) return rc;
+  cudaError_t e = cudaMalloc(&b.ptr, want);
+  if (e != cudaSuccess) {
+    release(want);
+    cudaGetLastError();
+    return set_error(RSA_ERR_NOMEM, std::string("cudaMalloc workspace: ") + cudaGetErrorString(e));
+  }
+  b.bytes = want;
+  return RSA_OK;
+}
+
+Workspace &Ctx::ws(cudaStream_t s) { return workspaces[s]; }
+
+Ctx::~Ctx() {
+  cudaSetDevice(device);
+  cudaDeviceSynchronize();
+  for (auto &k : keys)
+    if (k.d_rec) cudaFree(k.d_rec);
+  for (auto &kv : workspaces) kv.second.free_all();
+  free_extra();
+}
+
+void Workspace::free_all() {
+  for (DevBuf *b : {&tables, &io_in, &io_out, &io_status, &aux0, &aux1, &aux2, &aux3}) {
+    if (b->ptr) cudaFree(b->ptr);
+    b->ptr = nullptr;
+    b->bytes = 0;
+  }
+}
+
+// ------------------------------------------------------------------ tuning
+static int default_window(uint32_t L, int kind) {
+  (void)L;
+  (void)kind;
+  return 5;
+}
+
+Tune Ctx::tune_for(uint32_t nbits, int kind) const {
+  Tune t{0, 0, 0};
+  auto it = tuning.find({nbits, kind});
+  if (it != tuning.end()) t = it->second;
+  const uint32_t L = nbits / 32;
+  if (!t.window) t.window = default_window(L, kind);
+  if (!t.warps_per_cta) t.warps_per_cta = 4;
+  return t;
+}
+
+// ------------------------------------------------------------------ launch helpers
+static size_t crt_smem_bytes(int H, int P) {
+  const size_t key_words = (KeyLayout(2 * H).total + 3) / 4 * 4;
+  const size_t stage = (size_t)(H / 4) * 32 * 16;
+  return key_words * 4 + (size_t)P * 2 * stage + (size_t)2 * P * stage;
+}
+static size_t exp_smem_bytes(int L, int warps) {
+  const size_t key_words = (KeyLayout(L).total + 3) / 4 * 4;
+  const size_t stage = (size_t)(L / 4) * 32 * 16;
+  return key_words * 4 + (size_t)warps * 2 * stage;
+}
+
+int Ctx::launch_grid(const void *fn, int threads, size_t smem, uint64_t units_per_cta_slot,
+                     uint64_t units, int ctas_per_sm_req, int *grid_out) {
+  cudaError_t e;
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
+  }
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+  if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (per_sm <= 0) return set_error(RSA_ERR_UNSUPPORTED, "kernel does not fit on an SM with this launch shape");
+  if (ctas_per_sm_req > 0) per_sm = std::min(per_sm, ctas_per_sm_req);
+  const uint64_t need = (units + units_per_cta_slot - 1) / units_per_cta_slot;
+  *grid_out = (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)sm_count * per_sm));
+  return RSA_OK;
+}
+
+int Ctx::run_key(const KeySlot &k, int kind, uint64_t count, const uint32_t *msgs, uint32_t *out,
+                 int32_t *status, cudaStream_t s) {
+  if (count == 0) return RSA_OK;
+  Workspace &w = ws(s);
+  const uint32_t L = k.L;
+  cudaError_t e;
+  if (L == 1) {
+    ToyArgs a{k.d_rec, msgs, out, status, (uint32_t)count, kind};
+    const void *fn = toy_kernel_fn();
+    int grid = (int)std::min<uint64_t>((count + 255) / 256, (uint64_t)sm_count * 8);
+    void *args[] = {&a};
+    e = cudaLaunchKernel(fn, dim3(grid), dim3(256), args, 0, s);
+    if (e != cudaSuccess) return cuda_error(e, "launch toy_kernel");
+    stats.kernel_launches++;
+    return RSA_OK;
+  }
+  const Tune t = tune_for(k.nbits, kind);
+  if (kind == RSA_EXP_PRIVATE_CRT) {
+    const int H = (int)L / 2;
+    const void *fn = crt_kernel_fn(H, t.window);
+    if (!fn) return set_error(RSA_ERR_UNSUPPORTED, "no CRT kernel for this key size / window");
+    const int P = std::max(1, t.warps_per_cta / 2);
+    const int threads = 64 * P;
+    const size_t smem = crt_smem_bytes(H, P);
+    const uint64_t ntiles = (count + 31) / 32;
+    int grid = 0;
+    int rc = launch_grid(fn, threads, smem, (uint64_t)P, ntiles, t.ctas_per_sm, &grid);
+    if (rc) return rc;
+    const size_t tbytes = (size_t)grid * 2 * P * ((size_t)1 << t.window) * H * 128;
+    rc = ensure(w.tables, tbytes);
+    if (rc) return rc;
+    CrtArgs a{k.d_rec, msgs, out, status, (uint32_t)count, static_cast<uint4 *>(w.tables.ptr)};
+    void *args[] = {&a};
+    e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, s);
+    if (e != cudaSuccess) return cuda_error(e, "launch crt_kernel");
+    stats.kernel_launches++;
+    last_grid = grid;
+    last_threads = threads;
+    return RSA_OK;
+  }
+  const bool pub = (kind == RSA_EXP_PUBLIC);
+  const void *fn = pub ? pub_kernel_fn((int)L) : plain_kernel_fn((int)L, t.window);
+  if (!fn) return set_error(RSA_ERR_UNSUPPORTED, "no kernel for this key size / exponent kind");
+  const int warps = std::max(1, t.warps_per_cta);
+  const int threads = 32 * warps;
+  const size_t smem = exp_smem_bytes((int)L, warps);
+  const uint64_t ntiles = (count + 31) / 32;
+  int grid = 0;
+  int rc = launch_grid(fn, threads, smem, (uint64_t)warps, ntiles, t.ctas_per_sm, &grid);
+  if (rc) return rc;
+  uint4 *tables = nullptr;
+  if (!pub) {
+    const size_t tbytes = (size_t)grid * warps * ((size_t)1 << t.window) * L * 128;
+    rc = ensure(w.tables, tbytes);
+    if (rc) return rc;
+    tables = static_cast<uint4 *>(w.tables.ptr);
+  }
+  ExpArgs a{k.d_rec, msgs, out, status, (uint32_t)count, tables};
+  void *args[] = {&a};
+  e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, s);
+  if (e != cudaSuccess) return cuda_error(e, pub ? "launch pub_kernel" : "launch plain_kernel");
+  stats.kernel_launches++;
+  last_grid = grid;
+  last_threads = threads;
+  return RSA_OK;
+}
+
+int Ctx::check_key(int32_t key_id, int kind, const KeySlot **out) {
+  if (key_id < 0 || (size_t)key_id >= keys.size() || !keys[key_id].used)
+    return set_error(RSA_ERR_KEY, "unknown key id " + std::to_string(key_id));
+  const KeySlot &k = keys[key_id];
+  if (kind != RSA_EXP_PUBLIC && kind != RSA_EXP_PRIVATE_CRT && kind != RSA_EXP_PRIVATE_PLAIN)
+    return set_error(RSA_ERR_ARG, "bad exp_sel " + std::to_string(kind));
+  if (kind != RSA_EXP_PUBLIC && !(k.flags & KEY_HAS_D))
+    return set_error(RSA_ERR_KEY, "private operation on a key loaded without d");
+  if (kind == RSA_EXP_PRIVATE_CRT && !(k.flags & KEY_HAS_CRT))
+    return set_error(RSA_ERR_KEY, "CRT operation on a key loaded without p, q");
+  *out = &k;
+  return RSA_OK;
+}
+
+}  // namespace rsagpu
+
+using namespace rsagpu;
+
+// ====================================================================== C ABI
+extern "C" {
+
+int rsa_ctx_create(rsa_ctx **out, int device, size_t mem_budget_bytes) {
+  if (!out) return set_error(RSA_ERR_ARG, "out is null");
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev) return set_error(RSA_ERR_ARG, "no such CUDA device");
+  e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
+  Ctx *c = new Ctx();
+  c->device = device;
+  c->budget = mem_budget_bytes ? mem_budget_bytes : ((size_t)2 << 30);
+  e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_error(e, "cudaDeviceGetAttribute");
+  }
+  *out = reinterpret_cast<rsa_ctx *>(c);
+  return RSA_OK;
+}
+
+int rsa_ctx_destroy(rsa_ctx *ctx) {
+  if (!ctx) return set_error(RSA_ERR_ARG, "ctx is null");
+  delete reinterpret_cast<Ctx *>(ctx);
+  return RSA_OK;
+}
+
+static int make_record(uint32_t nbits, const uint32_t *n, const uint32_t *e, uint32_t e_limbs,
+                       const uint32_t *d, const uint32_t *p, const uint32_t *q, std::vector<uint32_t> &rec,
+                       uint32_t &flags) {
+  if (!n || !e) return set_error(RSA_ERR_ARG, "null argument");
+  if ((p == nullptr) != (q == nullptr)) return set_error(RSA_ERR_ARG, "p and q must both be given or both be null");
+  if (nbits % 32 != 0 || nbits == 0 || nbits > 4096) return set_error(RSA_ERR_UNSUPPORTED, "unsupported key size");
+  const uint32_t L = nbits / 32;
+  if (e_limbs == 0 || e_limbs > L) return set_error(RSA_ERR_ARG, "e_limbs must be in 1..L");
+  KeyInput in;
+  in.nbits = nbits;
+  in.n.assign(n, n + L);
+  in.e.assign(e, e + e_limbs);
+  if (d) in.d.assign(d, d + L);
+  const uint32_t hl = (L == 1) ? 1u : L / 2;
+  if (p) {
+    in.p.assign(p, p + hl);
+    in.q.assign(q, q + hl);
+  }
+  char cls = 0;
+  std::string msg = build_key_record(in, rec, flags, &cls);
+  if (!msg.empty())
+    return set_error(cls == 'U' ? RSA_ERR_UNSUPPORTED : cls == 'A' ? RSA_ERR_ARG : RSA_ERR_KEY, msg);
+  return RSA_OK;
+}
+
+int rsa_key_record(uint32_t nbits, const uint32_t *n, const uint32_t *e, uint32_t e_limbs, const uint32_t *d,
+                   const uint32_t *p, const uint32_t *q, uint32_t *rec, size_t rec_capacity_words,
+                   size_t *rec_words) {
+  std::vector<uint32_t> r;
+  uint32_t flags = 0;
+  int rc = make_record(nbits, n, e, e_limbs, d, p, q, r, flags);
+  if (rc) return rc;
+  if (rec_words) *rec_words = r.size();
+  if (!rec) return RSA_OK;
+  if (rec_capacity_words < r.size()) return set_error(RSA_ERR_ARG, "record buffer too small");
+  std::copy(r.begin(), r.end(), rec);
+  return RSA_OK;
+}
+
+int rsa_keyload(rsa_ctx *ctx, uint32_t nbits, const uint32_t *n, const uint32_t *e, uint32_t e_limbs,
+                const uint32_t *d, const uint32_t *p, const uint32_t *q, int32_t *key_id_out) {
+  if (!ctx || !key_id_out) return set_error(RSA_ERR_ARG, "null argument");
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  std::lock_guard<std::mutex> lock(c->mu);
+  std::vector<uint32_t> rec;
+  uint32_t flags = 0;
+  int rc0 = make_record(nbits, n, e, e_limbs, d, p, q, rec, flags);
+  if (rc0) return rc0;
+  const uint32_t L = nbits / 32;
+  const size_t bytes = rec.size() * 4;
+  int rc = c->reserve(bytes);
+  if (rc) return rc;
+  cudaSetDevice(c->device);
+  uint32_t *dptr = nullptr;
+  cudaError_t ce = cudaMalloc(&dptr, bytes);
+  if (ce != cudaSuccess) {
+    c->release(bytes);
+    cudaGetLastError();
+    return set_error(RSA_ERR_NOMEM, std::string("cudaMalloc key record: ") + cudaGetErrorString(ce));
+  }
+  ce = cudaMemcpy(dptr, rec.data(), bytes, cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) {
+    cudaFree(dptr);
+    c->release(bytes);
+    return cuda_error(ce, "cudaMemcpy key record");
+  }
+  int32_t id = -1;
+  for (size_t i = 0; i < c->keys.size(); ++i)
+    if (!c->keys[i].used) {
+      id = (int32_t)i;
+      break;
+    }
+  if (id < 0) {
+    id = (int32_t)c->keys.size();
+    c->keys.emplace_back();
+  }
+  KeySlot &k = c->keys[id];
+  k.used = true;
+  k.nbits = nbits;
+  k.L = L;
+  k.flags = flags;
+  k.d_rec = dptr;
+  k.bytes = bytes;
+  k.host_rec = rec;
+  c->key_epoch++;
+  *key_id_out = id;
+  return RSA_OK;
+}
+
+int rsa_keyunload(rsa_ctx *ctx, int32_t key_id) {
+  if (!ctx) return set_error(RSA_ERR_ARG, "ctx is null");
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  std::lock_guard<std::mutex> lock(c->mu);
+  if (key_id < 0 || (size_t)key_id >= c->keys.size() || !c->keys[key_id].used)
+    return set_error(RSA_ERR_KEY, "unknown key id");
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  KeySlot &k = c->keys[key_id];
+  cudaFree(k.d_rec);
+  c->release(k.bytes);
+  k = KeySlot();
+  c->key_epoch++;
+  return RSA_OK;
+}
+
+int rsa_key_info(rsa_ctx *ctx, int32_t key_id, uint32_t *nbits, int32_t *has_d, int32_t *has_crt) {
+  if (!ctx) return set_error(RSA_ERR_ARG, "ctx is null");
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  std::lock_guard<std::mutex> lock(c->mu);
+  if (key_id < 0 || (size_t)key_id >= c->keys.size() || !c->keys[key_id].used)
+    return set_error(RSA_ERR_KEY, "unknown key id");
+  const KeySlot &k = c->keys[key_id];
+  if (nbits) *nbits = k.nbits;
+  if (has_d) *has_d = (k.flags & KEY_HAS_D) ? 1 : 0;
+  if (has_crt) *has_crt = (k.flags & KEY_HAS_CRT) ? 1 : 0;
+  return RSA_OK;
+}
+
+int rsa_modexp_key(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint64_t count, const uint32_t *msgs,
+                   uint32_t *out, int32_t *op_status, void *stream) {
+  if (!ctx) return set_error(RSA_ERR_ARG, "ctx is null");
+  if (count > 0 && (!msgs || !out)) return set_error(RSA_ERR_ARG, "null message or output pointer");
+  if (count > 0x7fffffffull) return set_error(RSA_ERR_ARG, "count exceeds 2^31 - 1");
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  std::lock_guard<std::mutex> lock(c->mu);
+  const KeySlot *k = nullptr;
+  int rc = c->check_key(key_id, exp_sel, &k);
+  if (rc) return rc;
+  if (k->L > 1 && ((reinterpret_cast<uintptr_t>(msgs) | reinterpret_cast<uintptr_t>(out)) & 15u))
+    return set_error(RSA_ERR_ARG, "message and output rows must be 16-byte aligned");
+  cudaSetDevice(c->device);
+  c->stats.ops += count;
+  return c->run_key(*k, exp_sel, count, msgs, out, op_status, static_cast<cudaStream_t>(stream));
+}
+
+int rsa_modexp_key_host(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint64_t count, const uint32_t *msgs,
+                        uint32_t *out, int32_t *op_status, void *stream) {
+  if (!ctx) return set_error(RSA_ERR_ARG, "ctx is null");
+  if (count > 0 && (!msgs || !out)) return set_error(RSA_ERR_ARG, "null message or output pointer");
+  if (count > 0x7fffffffull) return set_error(RSA_ERR_ARG, "count exceeds 2^31 - 1");
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  std::lock_guard<std::mutex> lock(c->mu);
+  const KeySlot *k = nullptr;
+  int rc = c->check_key(key_id, exp_sel, &k);
+  if (rc) return rc;
+  if (count == 0) return RSA_OK;
+  cudaSetDevice(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Workspace &w = c->ws(s);
+  const size_t bytes = (size_t)count * k->L * 4;
+  if ((rc = c->ensure(w.io_in, bytes)) || (rc = c->ensure(w.io_out, bytes))) return rc;
+  if (op_status && (rc = c->ensure(w.io_status, (size_t)count * 4))) return rc;
+  cudaError_t e = cudaMemcpyAsync(w.io_in.ptr, msgs, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync H2D");
+  c->stats.ops += count;
+  rc = c->run_key(*k, exp_sel, count, static_cast<uint32_t *>(w.io_in.ptr), static_cast<uint32_t *>(w.io_out.ptr),
+                  op_status ? static_cast<int32_t *>(w.io_status.ptr) : nullptr, s);
+  if (rc) return rc;
+  e = cudaMemcpyAsync(out, w.io_out.ptr, bytes, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync D2H");
+  if (op_status) {
+    e = cudaMemcpyAsync(op_status, w.io_status.ptr, (size_t)count * 4, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync D2H status");
+  }
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
+  return RSA_OK;
+}
+
+int rsa_sync(rsa_ctx *ctx, void *stream) {
+  if (!ctx) return set_error(RSA_ERR_ARG, "ctx is null");
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  cudaSetDevice(c->device);
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
+  std::lock_guard<std::mutex> lock(c->mu);
+  return c->collect_device_errors(static_cast<cudaStream_t>(stream));
+}
+
+const char *rsa_last_error(void) { return g_last_error.c_str(); }
+
+int rsa_set_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, const rsa_tuning *t) {
+  if (!ctx) return set_error(RSA_ERR_ARG, "ctx is null");
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  std::lock_guard<std::mutex> lock(c->mu);
+  if (!t) {
+    c->tuning.erase({nbits, exp_sel});
+    return RSA_OK;
+  }
+  if (t->window && (t->window < kMinWindow || t->window > kMaxWindow))
+    return set_error(RSA_ERR_ARG, "window out of range");
+  if (t->warps_per_cta < 0 || t->warps_per_cta > 8 || t->ctas_per_sm < 0)
+    return set_error(RSA_ERR_ARG, "bad launch shape");
+  if (exp_sel == RSA_EXP_PRIVATE_CRT && (t->warps_per_cta & 1))
+    return set_error(RSA_ERR_ARG, "CRT kernels run warp pairs: warps_per_cta must be even");
+  c->tuning[{nbits, exp_sel}] = Tune{t->window, t->warps_per_cta, t->ctas_per_sm};
+  return RSA_OK;
+}
+
+int rsa_get_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, rsa_tuning *t) {
+  if (!ctx || !t) return set_error(RSA_ERR_ARG, "null argument");
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  std::lock_guard<std::mutex> lock(c->mu);
+  Tune x = c->tune_for(nbits, exp_sel);
+  t->window = x.window;
+  t->warps_per_cta = x.warps_per_cta;
+  t->ctas_per_sm = x.ctas_per_sm;
+  return RSA_OK;
+}
+
+int rsa_get_stats(rsa_ctx *ctx, rsa_stats *s) {
+  if (!ctx || !s) return set_error(RSA_ERR_ARG, "null argument");
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  std::lock_guard<std::mutex> lock(c->mu);
+  *s = c->stats;
+  s->bytes_resident = c->used;
+  return RSA_OK;
+}
+
+double rsa_products_per_op(uint32_t nbits, int32_t exp_sel, uint32_t e_bits, uint32_t e_weight, int32_t window) {
+  const double L = nbits / 32.0;
+  auto mm = [](double l) { return 2.0 * l * l + l; };
+  const int W = window > 0 ? window : 5;
+  if (exp_sel == RSA_EXP_PUBLIC) {
+    if (e_bits == 0) return 0.0;
+    const double mults = 2.0 + (e_bits - 1) + (e_weight > 0 ? e_weight - 1 : 0);
+    return mults * mm(L);
+  }
+  if (exp_sel == RSA_EXP_PRIVATE_PLAIN) {
+    const double nwin = std::ceil(32.0 * L / W);
+    const double mults = 2.0 + ((1 << W) - 2) + (nwin - 1) * (W + 1);
+    return mults * mm(L);
+  }
+  const double H = L / 2.0;
+  const double nwin = std::ceil(32.0 * H / W);
+  const double per_half = 2.0 + ((1 << W) - 2) + (nwin - 1) * (W + 1);
+  return (2.0 * per_half + 3.0) * mm(H) + H * H;
+}
+
+int rsa_imad_probe(int device, double *imad_lanes_per_s, double *chain_products_per_s) {
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  uint32_t *sink = nullptr;
+  const int threads = 256, blocks = sms * 8;
+  e = cudaMalloc(&sink, (size_t)threads * blocks * 4);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMalloc probe");
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  auto run = [&](const void *fn, uint32_t iters, float *ms) -> cudaError_t {
+    uint32_t seed = 12345u;
+    void *args[] = {&sink, &iters, &seed};
+    cudaError_t r = cudaLaunchKernel(fn, dim3(blocks), dim3(threads), args, 0, nullptr);  // warm-up
+    if (r != cudaSuccess) return r;
+    cudaEventRecord(a);
+    r = cudaLaunchKernel(fn, dim3(blocks), dim3(threads), args, 0, nullptr);
+    if (r != cudaSuccess) return r;
+    cudaEventRecord(b);
+    r = cudaEventSynchronize(b);
+    cudaEventElapsedTime(ms, a, b);
+    return r;
+  };
+  float ms1 = 0, ms2 = 0;
+  const uint32_t it1 = 20000, it2 = 4000;
+  e = run(imad_probe_fn(), it1, &ms1);
+  if (e == cudaSuccess) e = run(chain_probe_fn(), it2, &ms2);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(sink);
+  if (e != cudaSuccess) return cuda_error(e, "probe kernel");
+  const double thr = (double)threads * blocks;
+  if (imad_lanes_per_s) *imad_lanes_per_s = thr * it1 * 16.0 / (ms1 * 1e-3);
+  if (chain_products_per_s) *chain_products_per_s = thr * it2 * 32.0 / (ms2 * 1e-3);
+  return RSA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+// runtime_internal.h -- library-private state behind the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "rsa_gb300.h"
+
+namespace rsagpu {
+
+int set_error(int code, const std::string &msg);
+int cuda_error(cudaError_t e, const char *what);
+
+struct DevBuf {
+  void *ptr = nullptr;
+  size_t bytes = 0;
+};
+
+// Scratch owned per stream, so work enqueued on different streams never shares it.
+struct Workspace {
+  DevBuf tables;                  // window tables of the private-exponent kernels
+  DevBuf io_in, io_out, io_status;  // host-buffer entry points
+  DevBuf aux0, aux1, aux2, aux3;  // ragged-batch planning buffers
+  void free_all();
+};
+
+struct KeySlot {
+  bool used = false;
+  uint32_t nbits = 0, L = 0, flags = 0;
+  uint32_t *d_rec = nullptr;      // device key record (keyrec.h)
+  size_t bytes = 0;
+  std::vector<uint32_t> host_rec; // host copy of the record
+};
+
+struct Tune {
+  int window, warps_per_cta, ctas_per_sm;
+};
+
+struct Ctx {
+  int device = 0;
+  int sm_count = 0;
+  size_t budget = 0, used = 0;
+  std::mutex mu;
+  std::vector<KeySlot> keys;
+  uint64_t key_epoch = 0;         // bumped on every key load/unload
+  std::map<cudaStream_t, Workspace> workspaces;
+  std::map<std::pair<uint32_t, int>, Tune> tuning;
+  rsa_stats stats{};
+  int last_grid = 0, last_threads = 0;
+  // ragged-batch state (batch.cu)
+  void *batch_state = nullptr;
+
+  ~Ctx();
+  int reserve(size_t bytes);
+  void release(size_t bytes);
+  int ensure(DevBuf &b, size_t need);
+  Workspace &ws(cudaStream_t s);
+  Tune tune_for(uint32_t nbits, int kind) const;
+  int check_key(int32_t key_id, int kind, const KeySlot **out);
+  int launch_grid(const void *fn, int threads, size_t smem, uint64_t units_per_cta_slot, uint64_t units,
+                  int ctas_per_sm_req, int *grid_out);
+  int run_key(const KeySlot &k, int kind, uint64_t count, const uint32_t *msgs, uint32_t *out,
+              int32_t *status, cudaStream_t s);
+  int collect_device_errors(cudaStream_t s);
+  void free_extra();
+};
+
+}  // namespace rsagpu
