@@ -140,6 +140,27 @@ int rsa_modexp_batch_host(rsa_ctx *ctx, uint64_t count, const int32_t *key_ids,
                           uint64_t total_limbs, const uint32_t *msgs, uint32_t *out,
                           int32_t *op_status, void *stream);
 
+/* CRT decryption that allocates no memory (no context, no cudaMalloc).
+ * The paper has no counterpart; this exists for callers that cannot allocate
+ * device memory at call time -- code inside a CUDA graph capture, plug-ins whose
+ * host process owns all device memory through its own pool, or services that
+ * forbid allocation after start-up so a request can never fail on it.
+ *   key_record  device pointer to the words rsa_key_record() returns for a key
+ *               given with d, p and q (copied by the caller into memory it owns)
+ *   nbits       1024, 2048, 3072 or 4096 (other sizes: RSA_ERR_UNSUPPORTED)
+ *   msgs, out   device pointers to count rows of nbits/32 limbs (16-byte aligned)
+ *   op_status   device pointer to count int32 (RSA_OK / RSA_ERR_RANGE) or NULL
+ * Results are identical to rsa_modexp_key(..., RSA_EXP_PRIVATE_CRT, ...).
+ * The window-table scratch is a fixed 32 MiB array inside the library, held on
+ * every GPU that loads it until the process exits; the launch is sized to fit
+ * it (window width 4), so throughput is below rsa_modexp_key's.  All calls
+ * share that array: calls that overlap on the GPU race and must be ordered on
+ * one stream.  The first call on a device looks up the array's address with
+ * that device current; make it before any stream capture.  Enqueued on
+ * `stream`; errors are returned before anything is enqueued. */
+int rsa_crt_decrypt_noalloc(const uint32_t *key_record, uint32_t nbits, uint64_t count,
+                            const uint32_t *msgs, uint32_t *out, int32_t *op_status, void *stream);
+
 /* Wait for `stream` and return the first device-side error recorded since the
  * previous call (RSA_ERR_KEY, RSA_ERR_TIMEOUT), RSA_ERR_CUDA, or RSA_OK. */
 int rsa_sync(rsa_ctx *ctx, void *stream);

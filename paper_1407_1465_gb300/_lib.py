@@ -68,6 +68,7 @@ SIGNATURES = [
     ("rsa_modexp_batch", ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, _P, _P, _P, _P, _P]),
     ("rsa_modexp_key_host", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P]),
     ("rsa_modexp_batch_host", ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, _P, ctypes.c_uint64, _P, _P, _P, _P]),
+    ("rsa_crt_decrypt_noalloc", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, _P, _P, _P]),
     ("rsa_sync", ctypes.c_int, [_P, _P]),
     ("rsa_last_error", ctypes.c_char_p, []),
     ("rsa_set_tuning", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_int32, ctypes.POINTER(rsa_tuning)]),
