@@ -113,6 +113,90 @@ def cpu_baseline(key, rows, target_s: float = 12.0) -> dict:
                       % (n, rows.shape[0], threads, dt)}
 
 
+def run_ragged(args):
+    """Ragged batch: 256 keys, 200000 operations, one rsa_modexp_batch (one graph
+    launch) per step, against a loop of one rsa_modexp_key launch per
+    (key, kind) group over the same operations."""
+    import torch
+    from paper_1407_1465_gb300 import RsaContext, build, rsa_modexp_batch, rsa_modexp_key, rsa_products_per_op
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rb = workloads.ragged()
+    ctx = RsaContext(0, mem_budget_bytes=16 << 30)
+    kids = [ctx.keyload(k.bits, k.n, k.e, k.d, k.p, k.q) for k in rb.keys]
+    key_ids = torch.from_numpy(np.array([kids[k] for k in rb.key_ids], dtype=np.int32)).to(dev)
+    sels = torch.from_numpy(rb.exp_sel).to(dev)
+    offs = torch.from_numpy(rb.offsets.view(np.int64)).to(dev)
+    msgs = torch.from_numpy(rb.packed.view(np.int32)).to(dev)
+    out = torch.empty_like(msgs)
+    status = torch.empty(len(rb.msgs), dtype=torch.int32, device=dev)
+    count = len(rb.msgs)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    # groups for the one-key-per-launch loop, gathered contiguously (untimed)
+    groups = {}
+    for i, (k, s) in enumerate(zip(rb.key_ids, rb.exp_sel)):
+        groups.setdefault((int(k), int(s)), []).append(i)
+    gbufs = []
+    for (k, s), idx in sorted(groups.items()):
+        rows = np.stack([rb.msgs[i] for i in idx])
+        t = torch.from_numpy(rows.view(np.int32)).to(dev)
+        gbufs.append((kids[k], s, len(idx), t, torch.empty_like(t), idx))
+    prods = 0.0
+    for i in range(count):
+        key = rb.keys[rb.key_ids[i]]
+        prods += rsa_products_per_op(key.bits, int(rb.exp_sel[i]), key.e, 5)
+
+    def step_ragged():
+        rsa_modexp_batch(ctx.handle, count, key_ids, sels, offs, msgs, out, status, sptr)
+
+    def step_loop():
+        for kid, s, n, t, o, _ in gbufs:
+            rsa_modexp_key(ctx.handle, kid, s, n, t, o, None, sptr)
+
+    res = {}
+    for name, fn in (("ragged", step_ragged), ("loop", step_loop)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for a, b in ev:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+        res[name] = ms
+    if ctx.sync() != 0 or not bool((status == 0).all()):
+        raise RuntimeError("ragged batch reported errors")
+    # the loop's results must equal the ragged batch's
+    got = out.cpu().numpy().view(np.uint32)
+    for kid, s, n, t, o, idx in gbufs[:40]:
+        oo = o.cpu().numpy().view(np.uint32)
+        for j, i in enumerate(idx[:4]):
+            off = int(rb.offsets[i])
+            if not np.array_equal(got[off:off + oo.shape[1]], oo[j]):
+                raise RuntimeError("ragged and per-key results differ")
+    line = {
+        "metric": "ragged-batch ops/sec (256 keys, 200000 ops, one graph launch)",
+        "value": count / (res["ragged"] / 1e3), "unit": "ops/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ragged"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "ragged: 256 seeded keys (1024/2048/3072/4096 bits at 0.1/0.5/0.2/0.2), "
+                               "Zipf(1.1) counts summing to 200000, 70% CRT decrypt / 30% public",
+                   "groups": len(gbufs)},
+        "one_key_per_launch": {"ms_per_step": res["loop"], "value": count / (res["loop"] / 1e3),
+                               "launches": len(gbufs)},
+        "speedup_vs_loop": res["loop"] / res["ragged"],
+        "roofline": {"bound": "alu", "achieved": prods / (res["ragged"] / 1e3) / 1e12, "unit": "Tprod/s",
+                     "products_per_step": prods},
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -165,14 +249,21 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="rsa2048", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rsa2048", choices=sorted(WORKLOADS) + ["ragged"])
     ap.add_argument("--window", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--variant", type=int, default=0, help="squaring variant: 1 CIOS, 2 separated, 0 auto")
+    ap.add_argument("--count", type=int, default=0, help="override the message count (small profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
-    spec = WORKLOADS[args.workload]
+    if args.workload == "ragged":
+        return run_ragged(args)
+    spec = dict(WORKLOADS[args.workload])
+    if args.count:
+        spec["count"] = args.count
+        spec["desc"] += " [count overridden: %d ciphertexts]" % args.count
     if args.impl == "reference":
         return run_reference(args, spec)
     if args.warmup < 3:
@@ -190,13 +281,15 @@ def main():
     from paper_1407_1465_gb300 import RSA_EXP_PRIVATE_CRT, RsaContext, build, rsa_modexp_key, rsa_products_per_op
     build.build()
 
-    key, rows = workloads.rsa_single(spec["bits"], spec["count"])
+    key, rows = workloads.rsa_single(spec["bits"], WORKLOADS[args.workload]["count"])
+    rows = rows[:spec["count"]] if spec["count"] <= rows.shape[0] else \
+        workloads.messages_below(key.n, spec["count"], workloads.DEFAULT_SEED, ("single", spec["bits"]))
     count, L = rows.shape
     ctx = RsaContext(local, mem_budget_bytes=16 << 30)
     kid = ctx.keyload(spec["bits"], key.n, key.e, key.d, key.p, key.q)
-    if args.window or args.warps or args.ctas_per_sm:
+    if args.window or args.warps or args.ctas_per_sm or args.variant:
         ctx.set_tuning(spec["bits"], RSA_EXP_PRIVATE_CRT, window=args.window, warps_per_cta=args.warps,
-                       ctas_per_sm=args.ctas_per_sm)
+                       ctas_per_sm=args.ctas_per_sm, variant=args.variant)
     tune = ctx.get_tuning(spec["bits"], RSA_EXP_PRIVATE_CRT)
     msgs = torch.from_numpy(rows.view(np.int32)).to(dev)
     out = torch.empty_like(msgs)
@@ -287,7 +380,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic", "gpu_launches": int(launches),
         "config": {"workload": spec["desc"], "window": tune["window"], "warps_per_cta": tune["warps_per_cta"],
-                   "ctas_per_sm": tune["ctas_per_sm"], "l2": "flushed between timed steps (256 MiB write)",
+                   "ctas_per_sm": tune["ctas_per_sm"], "variant": tune["variant"], "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "dp%d (independent batches per GPU)" % ws},
         "wall_s": wall, "clocks": clk, "roofline": roofline, "e2e": e2e,
     }

@@ -161,6 +161,56 @@ int rsa_modexp_batch_host(rsa_ctx *ctx, uint64_t count, const int32_t *key_ids,
 int rsa_crt_decrypt_noalloc(const uint32_t *key_record, uint32_t nbits, uint64_t count,
                             const uint32_t *msgs, uint32_t *out, int32_t *op_status, void *stream);
 
+/* ---------------------------------------------------------------- serving
+ * A request loop on top of rsa_modexp_batch.  A scheduler thread admits
+ * requests when they have arrived and their device footprint fits the budget,
+ * packs every admitted request (any keys, sizes, kinds) into one ragged batch
+ * per free slot, and runs up to max_inflight_batches batches at once on
+ * separate streams, so requests arriving while others are on the GPU start
+ * without waiting for them (continuous batching).  Key state stays resident
+ * in the context.  Results are copied into each request's host buffer. */
+typedef struct rsa_server_cfg {
+    int32_t max_inflight_batches; /* concurrent batches (streams); 0 -> 4 */
+    int32_t batch_window_us;      /* wait this long after the first arrival for more; 0 -> 200 */
+    int32_t max_batch_ops;        /* operations per batch; 0 -> 65536 */
+    int32_t reserved;
+    uint64_t mem_budget_bytes;    /* device bytes for in-flight requests; 0 -> 2 GiB */
+} rsa_server_cfg;
+
+typedef struct rsa_request {
+    int32_t key_id;
+    int32_t exp_sel;
+    uint32_t count;               /* messages in this request */
+    uint32_t reserved;
+    const uint32_t *msgs;         /* host: count rows of the key's L limbs */
+    uint32_t *out;                /* host: count rows, written when done */
+    int32_t *status;              /* host: count statuses, or NULL */
+    uint64_t arrive_ns;           /* arrival time, ns after rsa_server_start; 0 = at submit */
+} rsa_request;
+
+typedef struct rsa_server_stats {
+    uint64_t submitted, completed, rejected, ops_completed, batches;
+    uint64_t peak_bytes;          /* largest device footprint of in-flight requests */
+    double p50_us, p99_us, mean_us, max_us;   /* request latency: arrival -> result in host buffer */
+    double span_s;                /* first arrival -> last completion */
+} rsa_server_stats;
+
+/* Start the request loop of `ctx` (one per context).  The buffers a request
+ * points to must stay valid until it completes. */
+int rsa_server_start(rsa_ctx *ctx, const rsa_server_cfg *cfg);
+/* Queue a request; *ticket identifies it.  RSA_ERR_NOMEM when the request alone
+ * exceeds the budget, RSA_ERR_KEY / RSA_ERR_ARG for a bad key or kind. */
+int rsa_server_submit(rsa_ctx *ctx, const rsa_request *req, uint64_t *ticket);
+/* *done = 1 when the request completed, 0 while pending, a negative status on failure. */
+int rsa_server_poll(rsa_ctx *ctx, uint64_t ticket, int32_t *done);
+/* Wait until every submitted request completed (timeout_ms <= 0: no limit).
+ * RSA_ERR_TIMEOUT when the limit passes first. */
+int rsa_server_drain(rsa_ctx *ctx, int32_t timeout_ms);
+/* Latency and throughput counters since start (or the last reset). */
+int rsa_server_get_stats(rsa_ctx *ctx, rsa_server_stats *s, int32_t reset);
+/* Drain and stop the loop; releases its buffers. */
+int rsa_server_stop(rsa_ctx *ctx);
+
 /* Wait for `stream` and return the first device-side error recorded since the
  * previous call (RSA_ERR_KEY, RSA_ERR_TIMEOUT), RSA_ERR_CUDA, or RSA_OK. */
 int rsa_sync(rsa_ctx *ctx, void *stream);
@@ -170,13 +220,18 @@ const char *rsa_last_error(void);
 
 /* Launch parameters of the multi-limb kernels.  Zero fields mean "automatic". */
 typedef struct rsa_tuning {
-    int32_t window;        /* fixed-window width w for private exponents, 1..6 */
-    int32_t warps_per_cta; /* warps per CTA (even for CRT: warp pairs) */
+    int32_t window;        /* fixed-window width w for private exponents, 3..6 */
+    int32_t warps_per_cta; /* warps per CTA (even for CRT: warp pairs), 1..8 */
     int32_t ctas_per_sm;   /* resident CTAs per SM the grid is sized for */
+    int32_t variant;       /* squarings of private exponents: 1 = through the general
+                              CIOS multiply, 2 = separated square + reduction (fewer
+                              word products, more registers); 0 = automatic */
 } rsa_tuning;
 
 /* Set (or, with NULL, reset to automatic) the launch parameters used for keys of
- * nbits bits and exponent kind exp_sel. */
+ * nbits bits and exponent kind exp_sel.  exp_sel = RSA_TUNE_RAGGED (with nbits 0)
+ * addresses the persistent kernel of rsa_modexp_batch (only ctas_per_sm applies). */
+#define RSA_TUNE_RAGGED 3
 int rsa_set_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, const rsa_tuning *t);
 /* Read the parameters currently in force for (nbits, exp_sel). */
 int rsa_get_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, rsa_tuning *t);

@@ -25,7 +25,9 @@ __all__ = [
     "rsa_ctx_create", "rsa_ctx_destroy", "rsa_keyload", "rsa_key_record", "rsa_keyunload", "rsa_key_info",
     "rsa_modexp_key", "rsa_modexp_batch", "rsa_modexp_key_host", "rsa_modexp_batch_host",
     "rsa_sync", "rsa_last_error", "rsa_set_tuning", "rsa_get_tuning", "rsa_get_stats",
-    "rsa_products_per_op", "rsa_imad_probe",
+    "rsa_products_per_op", "rsa_imad_probe", "rsa_crt_decrypt_noalloc",
+    "rsa_server_start", "rsa_server_submit", "rsa_server_poll", "rsa_server_drain", "rsa_server_get_stats",
+    "rsa_server_stop",
 ]
 
 
@@ -157,23 +159,29 @@ def rsa_sync(ctx: int, stream=None) -> int:
     return rc
 
 
+def rsa_crt_decrypt_noalloc(key_record, nbits: int, count: int, msgs, out, op_status=None, stream=None) -> None:
+    check(_lib.lib().rsa_crt_decrypt_noalloc(_ptr(key_record), nbits, count, _ptr(msgs), _ptr(out), _ptr(op_status),
+                                             _stream_ptr(stream)))
+
+
 def rsa_last_error() -> str:
     return last_error()
 
 
 def rsa_set_tuning(ctx: int, nbits: int, exp_sel: int, window: int = 0, warps_per_cta: int = 0,
-                   ctas_per_sm: int = 0, reset: bool = False) -> None:
+                   ctas_per_sm: int = 0, variant: int = 0, reset: bool = False) -> None:
     if reset:
         check(_lib.lib().rsa_set_tuning(ctx, nbits, exp_sel, None))
         return
-    t = rsa_tuning(window, warps_per_cta, ctas_per_sm)
+    t = rsa_tuning(window, warps_per_cta, ctas_per_sm, variant)
     check(_lib.lib().rsa_set_tuning(ctx, nbits, exp_sel, ctypes.byref(t)))
 
 
 def rsa_get_tuning(ctx: int, nbits: int, exp_sel: int) -> dict:
     t = rsa_tuning()
     check(_lib.lib().rsa_get_tuning(ctx, nbits, exp_sel, ctypes.byref(t)))
-    return {"window": t.window, "warps_per_cta": t.warps_per_cta, "ctas_per_sm": t.ctas_per_sm}
+    return {"window": t.window, "warps_per_cta": t.warps_per_cta, "ctas_per_sm": t.ctas_per_sm,
+            "variant": t.variant}
 
 
 def rsa_get_stats(ctx: int) -> dict:
@@ -190,6 +198,44 @@ def rsa_imad_probe(device: int = 0) -> tuple[float, float]:
     a, b = ctypes.c_double(), ctypes.c_double()
     check(_lib.lib().rsa_imad_probe(device, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+# ------------------------------------------------------------------ serving
+
+def rsa_server_start(ctx: int, max_inflight_batches: int = 0, batch_window_us: int = 0, max_batch_ops: int = 0,
+                     mem_budget_bytes: int = 0) -> None:
+    cfg = _lib.rsa_server_cfg(max_inflight_batches, batch_window_us, max_batch_ops, 0, mem_budget_bytes)
+    check(_lib.lib().rsa_server_start(ctx, ctypes.byref(cfg)))
+
+
+def rsa_server_submit(ctx: int, key_id: int, exp_sel: int, msgs: np.ndarray, out: np.ndarray,
+                      status: np.ndarray | None = None, arrive_ns: int = 0) -> int:
+    """Queue one request (host buffers, which must stay alive until it completes)."""
+    count = msgs.shape[0] if msgs.ndim > 1 else msgs.size
+    req = _lib.rsa_request(key_id, exp_sel, count, 0, _ptr(msgs), _ptr(out), _ptr(status), arrive_ns)
+    t = ctypes.c_uint64()
+    check(_lib.lib().rsa_server_submit(ctx, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def rsa_server_poll(ctx: int, ticket: int) -> int:
+    d = ctypes.c_int32()
+    check(_lib.lib().rsa_server_poll(ctx, ticket, ctypes.byref(d)))
+    return d.value
+
+
+def rsa_server_drain(ctx: int, timeout_ms: int = 0) -> None:
+    check(_lib.lib().rsa_server_drain(ctx, timeout_ms))
+
+
+def rsa_server_get_stats(ctx: int, reset: bool = False) -> dict:
+    s = _lib.rsa_server_stats()
+    check(_lib.lib().rsa_server_get_stats(ctx, ctypes.byref(s), 1 if reset else 0))
+    return {k: getattr(s, k) for k, _ in _lib.rsa_server_stats._fields_}
+
+
+def rsa_server_stop(ctx: int) -> None:
+    check(_lib.lib().rsa_server_stop(ctx))
 
 
 # ------------------------------------------------------------------ convenience wrapper

@@ -39,7 +39,7 @@ class RsaError(RuntimeError):
 
 class rsa_tuning(ctypes.Structure):
     _fields_ = [("window", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("variant", ctypes.c_int32)]
 
 
 class rsa_stats(ctypes.Structure):
@@ -49,7 +49,21 @@ class rsa_stats(ctypes.Structure):
 
 class rsa_server_cfg(ctypes.Structure):
     _fields_ = [("max_inflight_batches", ctypes.c_int32), ("batch_window_us", ctypes.c_int32),
-                ("max_batch_ops", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_uint64)]
+                ("max_batch_ops", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("mem_budget_bytes", ctypes.c_uint64)]
+
+
+class rsa_request(ctypes.Structure):
+    _fields_ = [("key_id", ctypes.c_int32), ("exp_sel", ctypes.c_int32), ("count", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("msgs", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("status", ctypes.c_void_p), ("arrive_ns", ctypes.c_uint64)]
+
+
+class rsa_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("ops_completed", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
+                ("max_us", ctypes.c_double), ("span_s", ctypes.c_double)]
 
 
 # (name, restype, argtypes) for every function declared in include/rsa_gb300.h
@@ -69,6 +83,12 @@ SIGNATURES = [
     ("rsa_modexp_key_host", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P]),
     ("rsa_modexp_batch_host", ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, _P, ctypes.c_uint64, _P, _P, _P, _P]),
     ("rsa_crt_decrypt_noalloc", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, _P, _P, _P]),
+    ("rsa_server_start", ctypes.c_int, [_P, ctypes.POINTER(rsa_server_cfg)]),
+    ("rsa_server_submit", ctypes.c_int, [_P, ctypes.POINTER(rsa_request), ctypes.POINTER(ctypes.c_uint64)]),
+    ("rsa_server_poll", ctypes.c_int, [_P, ctypes.c_uint64, _I32P]),
+    ("rsa_server_drain", ctypes.c_int, [_P, ctypes.c_int32]),
+    ("rsa_server_get_stats", ctypes.c_int, [_P, ctypes.POINTER(rsa_server_stats), ctypes.c_int32]),
+    ("rsa_server_stop", ctypes.c_int, [_P]),
     ("rsa_sync", ctypes.c_int, [_P, _P]),
     ("rsa_last_error", ctypes.c_char_p, []),
     ("rsa_set_tuning", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_int32, ctypes.POINTER(rsa_tuning)]),

@@ -1,14 +1,368 @@
-// batch.cu -- ragged multi-key batches (rsa_modexp_batch).
+// batch.cu -- ragged multi-key batches (rsa_modexp_batch): the device-side
+// planning kernels, the per-stream CUDA graph that runs plan + execute, and
+// the device error collection used by rsa_sync().
+//
+// Graph (built once per context and stream, kernel parameters updated every
+// call): reset -> count -> tiles -> scatter -> persistent execute.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "batch.h"
+#include "kernels.cuh"
+#include "launch.h"
 #include "runtime_internal.h"
 
 namespace rsagpu {
+namespace {
+
+// error bits in ctl[2]: bit k set <=> some operation failed with status -k
+__device__ __forceinline__ void flag_error(uint32_t *ctl, int32_t code) { atomicOr(&ctl[2], 1u << (-code)); }
+
+__global__ void plan_reset(BatchDesc d) {
+  const uint32_t nb = d.nkeys * 3;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
+    d.bcount[i] = 0u;
+    d.bfill[i] = 0u;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 16 && threadIdx.x != 2) d.ctl[threadIdx.x] = 0u;
+}
+
+// classify each operation into a bucket (key id * 3 + kind); invalid ones get a status
+__global__ void plan_count(BatchDesc d) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.count; i += gridDim.x * blockDim.x) {
+    const int32_t kid = d.key_ids[i];
+    const int32_t kind = d.exp_sel[i];
+    int32_t err = 0, b = -1;
+    if (kid < 0 || (uint32_t)kid >= d.nkeys || d.dir[kid].rec == nullptr) {
+      err = -2;
+    } else if (kind > 2) {
+      err = -1;
+    } else {
+      const KeyDirEntry e = d.dir[kid];
+      if (kind != 0 && !(e.flags & KEY_HAS_D)) err = -2;
+      else if (kind == 1 && !(e.flags & KEY_HAS_CRT)) err = -2;
+      else if (batch_class(e.L, kind) < 0) err = -7;
+      else if (e.L > 1 && (d.offsets[i] & 3u)) err = -1;   // rows must be 16-byte aligned
+      else b = kid * 3 + kind;
+    }
+    d.op_bucket[i] = b;
+    if (b >= 0) {
+      atomicAdd(&d.bcount[b], 1u);
+    } else {
+      if (d.status) d.status[i] = err;
+      flag_error(d.ctl, err);
+    }
+  }
+}
+
+// Block-wide exclusive scan of one value per thread (blockDim.x == 1024).
+__device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total, uint32_t *sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = sh[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    sh[lane] = w;
+  }
+  __syncthreads();
+  const uint32_t before = (warp > 0 ? sh[warp - 1] : 0u) + x - v;
+  *total = sh[31];
+  __syncthreads();
+  return before;
+}
+
+// one block of 1024 threads: bucket offsets and tile descriptors, longest class first
+__global__ void __launch_bounds__(1024) plan_tiles(BatchDesc d) {
+  __shared__ uint32_t sh[32];
+  const uint32_t nb = d.nkeys * 3;
+  const uint32_t per = (nb + blockDim.x - 1) / blockDim.x;
+  const uint32_t b0 = threadIdx.x * per, b1 = min(nb, b0 + per);
+  uint32_t op_base = 0, tile_base = 0;
+  int32_t group = -1;
+  for (int rank = 0; rank < CLS_COUNT; ++rank) {
+    // ranks are grouped: record where each execution group's tiles start and end
+    int32_t g = -1;
+    for (int c = 0; c < CLS_COUNT; ++c)
+      if (d.class_rank[c] == rank) g = batch_group(c);
+    if (g != group) {
+      if (threadIdx.x == 0) {
+        if (group >= 0) d.ctl[8 + group] = min(tile_base, d.max_tiles);
+        d.ctl[4 + g] = min(tile_base, d.max_tiles);
+      }
+      group = g;
+    }
+    uint32_t my_ops = 0, my_tiles = 0;
+    for (uint32_t b = b0; b < b1; ++b) {
+      const uint32_t c = d.bcount[b];
+      if (!c) continue;
+      const int32_t cls = batch_class(d.dir[b / 3].L, (int)(b % 3));
+      if (d.class_rank[cls] != rank) continue;
+      const uint32_t to = (uint32_t)batch_tile_ops(cls);
+      my_ops += c;
+      my_tiles += (c + to - 1) / to;
+    }
+    uint32_t tot_ops, tot_tiles;
+    uint32_t op_off = op_base + block_exclusive_scan(my_ops, &tot_ops, sh);
+    uint32_t tile_off = tile_base + block_exclusive_scan(my_tiles, &tot_tiles, sh);
+    for (uint32_t b = b0; b < b1; ++b) {
+      const uint32_t c = d.bcount[b];
+      if (!c) continue;
+      const int32_t cls = batch_class(d.dir[b / 3].L, (int)(b % 3));
+      if (d.class_rank[cls] != rank) continue;
+      const uint32_t to = (uint32_t)batch_tile_ops(cls);
+      d.boff[b] = op_off;
+      const uint32_t nt = (c + to - 1) / to;
+      for (uint32_t j = 0; j < nt && tile_off + j < d.max_tiles; ++j)
+        d.tiles[tile_off + j] = TileDesc{(int32_t)b, (int32_t)(op_off + j * to), (int32_t)min(to, c - j * to), cls};
+      op_off += c;
+      tile_off += nt;
+    }
+    op_base += tot_ops;
+    tile_base += tot_tiles;
+  }
+  if (threadIdx.x == 0) {
+    d.ctl[1] = min(tile_base, d.max_tiles);
+    if (group >= 0) d.ctl[8 + group] = min(tile_base, d.max_tiles);
+  }
+}
+
+__global__ void plan_scatter(BatchDesc d) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.count; i += gridDim.x * blockDim.x) {
+    const int32_t b = d.op_bucket[i];
+    if (b < 0) continue;
+    const uint32_t pos = d.boff[b] + atomicAdd(&d.bfill[b], 1u);
+    d.sorted[pos] = (int32_t)i;
+  }
+}
+
+// approximate word products per operation of a class, for the longest-first order
+double class_cost(int32_t cls) {
+  auto mm = [](double l) { return 2.0 * l * l + l; };
+  switch (cls) {
+    case CLS_TOY: return 1.0;
+    case CLS_CRT16: return 2.0 * 660 * mm(16);
+    case CLS_CRT32: return 2.0 * 1300 * mm(32);
+    case CLS_CRT48: return 2.0 * 1880 * mm(48);
+    case CLS_CRT64: return 2.0 * 2500 * mm(64);
+    case CLS_PUB32: return 19 * mm(32);
+    case CLS_PUB64: return 19 * mm(64);
+    case CLS_PUB96: return 19 * mm(96) * 2.0;   // shared-memory operands run slower
+    case CLS_PUB128: return 19 * mm(128) * 2.0;
+    case CLS_PLAIN32: return 1300 * mm(32);
+    case CLS_PLAIN64: return 2600 * mm(64);
+    default: return 0.0;
+  }
+}
+
+}  // namespace
+
+struct BatchState {
+  cudaStream_t stream = nullptr;
+  bool built = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t nodes[7] = {};
+  int exec_grid = 0;
+  DevBuf keydir;
+  uint64_t keydir_epoch = ~0ull;
+};
+
+static std::vector<BatchState *> &batch_states(Ctx *c) {
+  if (!c->batch_state) c->batch_state = new std::vector<BatchState *>();
+  return *static_cast<std::vector<BatchState *> *>(c->batch_state);
+}
+
+void Ctx::free_extra() {
+  if (!batch_state) return;
+  for (BatchState *b : batch_states(this)) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->keydir.ptr) cudaFree(b->keydir.ptr);
+    delete b;
+  }
+  delete static_cast<std::vector<BatchState *> *>(batch_state);
+  batch_state = nullptr;
+}
 
 int Ctx::collect_device_errors(cudaStream_t s) {
-  (void)s;
+  auto it = workspaces.find(s);
+  if (it == workspaces.end() || !it->second.aux3.ptr) return RSA_OK;
+  uint32_t bits = 0;
+  uint32_t *ctl = static_cast<uint32_t *>(it->second.aux3.ptr);
+  cudaError_t e = cudaMemcpy(&bits, ctl + 2, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_error(e, "read device error word");
+  if (!bits) return RSA_OK;
+  const uint32_t zero = 0;
+  cudaMemcpy(ctl + 2, &zero, 4, cudaMemcpyHostToDevice);
+  for (int code : {2, 1, 7, 6, 4}) {
+    if (bits & (1u << code)) {
+      const char *what = code == 2 ? "operation with an unknown key or a kind its key cannot serve"
+                         : code == 1 ? "operation with a bad exponent kind or a misaligned row"
+                         : code == 7 ? "operation kind not supported for its key size"
+                         : code == 6 ? "device-side wait timed out" : "out of memory";
+      return set_error(-code, std::string("ragged batch: ") + what);
+    }
+  }
   return RSA_OK;
 }
 
-void Ctx::free_extra() {}
+static BatchState *state_for(Ctx *c, cudaStream_t s) {
+  for (BatchState *b : batch_states(c))
+    if (b->stream == s) return b;
+  BatchState *b = new BatchState();
+  b->stream = s;
+  batch_states(c).push_back(b);
+  return b;
+}
+
+int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_sel, const uint64_t *offsets,
+                   const uint32_t *msgs, uint32_t *out, int32_t *status, cudaStream_t s) {
+  if (count == 0) return RSA_OK;
+  BatchState *st = state_for(this, s);
+  Workspace &w = ws(s);
+  const uint32_t nkeys = (uint32_t)keys.size();
+  // key directory (rebuilt when keys change)
+  if (st->keydir_epoch != key_epoch || !st->keydir.ptr) {
+    std::vector<KeyDirEntry> dir(std::max<uint32_t>(nkeys, 1));
+    for (uint32_t i = 0; i < nkeys; ++i) {
+      const KeySlot &k = keys[i];
+      if (!k.used) continue;
+      const KeyHeader *hd = reinterpret_cast<const KeyHeader *>(k.host_rec.data());
+      dir[i] = KeyDirEntry{k.d_rec, k.L, k.flags, k.nbits, hd->e_bits};
+    }
+    int rc = ensure(st->keydir, dir.size() * sizeof(KeyDirEntry));
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpy(st->keydir.ptr, dir.data(), dir.size() * sizeof(KeyDirEntry), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_error(e, "upload key directory");
+    st->keydir_epoch = key_epoch;
+  }
+  const uint32_t nb = std::max<uint32_t>(nkeys, 1) * 3;
+  const uint32_t max_tiles = (uint32_t)(count / 32 + nb + 1);
+  int rc;
+  if ((rc = ensure(w.aux0, (size_t)count * 8)) ||                  // op_bucket + sorted
+      (rc = ensure(w.aux1, (size_t)nb * 12)) ||                    // bcount, bfill, boff
+      (rc = ensure(w.aux2, (size_t)max_tiles * sizeof(TileDesc))) ||
+      (rc = ensure(w.aux3, 64)))
+    return rc;
+  int grids_exec[GRP_COUNT];
+  int max_grid = 0;
+  for (int g = 0; g < GRP_COUNT; ++g) {
+    const void *fn = batch_exec_fn(g);
+    const size_t sm = batch_exec_smem_bytes(g);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(batch_exec)");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 64, sm);
+    if (e != cudaSuccess) return cuda_error(e, "occupancy(batch_exec)");
+    const Tune t = tune_for(0, RSA_TUNE_RAGGED);
+    if (t.ctas_per_sm > 0) per_sm = std::min(per_sm, t.ctas_per_sm);
+    grids_exec[g] = std::max(1, per_sm) * sm_count;
+    max_grid = std::max(max_grid, grids_exec[g]);
+  }
+  st->exec_grid = max_grid;
+  // window tables: one slot per resident warp of each group (groups run concurrently)
+  const size_t slot_u4 = (size_t)2 * kBatchTableU4PerWarp;
+  if ((rc = ensure(w.tables, (size_t)(grids_exec[0] + grids_exec[1] + grids_exec[2]) * slot_u4 * 16))) return rc;
+
+  BatchDesc d{};
+  d.count = (uint32_t)count;
+  d.nkeys = std::max<uint32_t>(nkeys, 1);
+  d.key_ids = key_ids;
+  d.exp_sel = exp_sel;
+  d.offsets = offsets;
+  d.msgs = msgs;
+  d.out = out;
+  d.status = status;
+  d.dir = static_cast<const KeyDirEntry *>(st->keydir.ptr);
+  d.op_bucket = static_cast<int32_t *>(w.aux0.ptr);
+  d.sorted = d.op_bucket + count;
+  d.bcount = static_cast<uint32_t *>(w.aux1.ptr);
+  d.bfill = d.bcount + nb;
+  d.boff = d.bfill + nb;
+  d.tiles = static_cast<TileDesc *>(w.aux2.ptr);
+  d.ctl = static_cast<uint32_t *>(w.aux3.ptr);
+  d.tables = static_cast<uint4 *>(w.tables.ptr);
+  d.max_tiles = max_tiles;
+  {
+    std::vector<int32_t> order(CLS_COUNT);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [](int32_t a, int32_t b) {
+      if (batch_group(a) != batch_group(b)) return batch_group(a) < batch_group(b);
+      return class_cost(a) > class_cost(b);
+    });
+    for (int r = 0; r < CLS_COUNT; ++r) d.class_rank[order[r]] = r;
+  }
+  const int g_ops = (int)std::min<uint64_t>((count + 255) / 256, (uint64_t)sm_count * 8);
+  const int g_nb = (int)std::min<uint32_t>((nb + 255) / 256, (uint32_t)sm_count * 8);
+  // nodes: reset -> count -> tiles -> scatter -> {big, mid, wide} (the three run concurrently)
+  constexpr int kNodes = 7;
+  const void *fns[kNodes] = {reinterpret_cast<const void *>(&plan_reset), reinterpret_cast<const void *>(&plan_count),
+                             reinterpret_cast<const void *>(&plan_tiles), reinterpret_cast<const void *>(&plan_scatter),
+                             batch_exec_fn(GRP_BIG), batch_exec_fn(GRP_MID), batch_exec_fn(GRP_WIDE)};
+  const dim3 grids[kNodes] = {dim3(std::max(1, g_nb)), dim3(g_ops), dim3(1), dim3(g_ops),
+                              dim3(grids_exec[0]), dim3(grids_exec[1]), dim3(grids_exec[2])};
+  const dim3 blocks[kNodes] = {dim3(256), dim3(256), dim3(1024), dim3(256), dim3(64), dim3(64), dim3(64)};
+  const size_t smems[kNodes] = {0, 0, 0, 0, batch_exec_smem_bytes(0), batch_exec_smem_bytes(1),
+                                batch_exec_smem_bytes(2)};
+  BatchDesc dg[kNodes];
+  void *args[kNodes][1];
+  for (int i = 0; i < kNodes; ++i) {
+    dg[i] = d;
+    args[i][0] = &dg[i];
+  }
+  // each group's warps index their own slice of the table scratch
+  dg[5].tables = d.tables + (size_t)grids_exec[0] * slot_u4;
+  dg[6].tables = dg[5].tables + (size_t)grids_exec[1] * slot_u4;
+  cudaError_t e;
+  auto params = [&](int i) {
+    cudaKernelNodeParams p{};
+    p.func = const_cast<void *>(fns[i]);
+    p.gridDim = grids[i];
+    p.blockDim = blocks[i];
+    p.sharedMemBytes = (unsigned)smems[i];
+    p.kernelParams = args[i];
+    return p;
+  };
+  if (!st->built) {
+    if ((e = cudaGraphCreate(&st->graph, 0)) != cudaSuccess) return cuda_error(e, "cudaGraphCreate");
+    for (int i = 0; i < kNodes; ++i) {
+      cudaKernelNodeParams p = params(i);
+      const int dep = i < 4 ? i - 1 : 3;
+      e = cudaGraphAddKernelNode(&st->nodes[i], st->graph, dep >= 0 ? &st->nodes[dep] : nullptr, dep >= 0 ? 1 : 0, &p);
+      if (e != cudaSuccess) return cuda_error(e, "cudaGraphAddKernelNode");
+    }
+    if ((e = cudaGraphInstantiate(&st->exec, st->graph, 0)) != cudaSuccess)
+      return cuda_error(e, "cudaGraphInstantiate");
+    st->built = true;
+  } else {
+    for (int i = 0; i < kNodes; ++i) {
+      cudaKernelNodeParams p = params(i);
+      e = cudaGraphExecKernelNodeSetParams(st->exec, st->nodes[i], &p);
+      if (e != cudaSuccess) return cuda_error(e, "cudaGraphExecKernelNodeSetParams");
+    }
+  }
+  if ((e = cudaGraphLaunch(st->exec, s)) != cudaSuccess) return cuda_error(e, "cudaGraphLaunch");
+  stats.graph_launches++;
+  stats.kernel_launches += 7;
+  return RSA_OK;
+}
 
 }  // namespace rsagpu
 
@@ -19,17 +373,59 @@ extern "C" {
 int rsa_modexp_batch(rsa_ctx *ctx, uint64_t count, const int32_t *key_ids, const uint8_t *exp_sel,
                      const uint64_t *limb_offsets, const uint32_t *msgs, uint32_t *out, int32_t *op_status,
                      void *stream) {
-  (void)ctx; (void)count; (void)key_ids; (void)exp_sel; (void)limb_offsets; (void)msgs; (void)out;
-  (void)op_status; (void)stream;
-  return set_error(RSA_ERR_UNSUPPORTED, "ragged batches are not available yet");
+  if (!ctx) return set_error(RSA_ERR_ARG, "ctx is null");
+  if (count > 0x7fffffffull) return set_error(RSA_ERR_ARG, "count exceeds 2^31 - 1");
+  if (count > 0 && (!key_ids || !exp_sel || !limb_offsets || !msgs || !out))
+    return set_error(RSA_ERR_ARG, "null pointer");
+  if ((reinterpret_cast<uintptr_t>(msgs) | reinterpret_cast<uintptr_t>(out)) & 15u)
+    return set_error(RSA_ERR_ARG, "message and output buffers must be 16-byte aligned");
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  std::lock_guard<std::mutex> lock(c->mu);
+  cudaSetDevice(c->device);
+  c->stats.ops += count;
+  return c->run_batch(count, key_ids, exp_sel, limb_offsets, msgs, out, op_status, static_cast<cudaStream_t>(stream));
 }
 
 int rsa_modexp_batch_host(rsa_ctx *ctx, uint64_t count, const int32_t *key_ids, const uint8_t *exp_sel,
-                          const uint64_t *limb_offsets, uint64_t total_limbs, const uint32_t *msgs,
-                          uint32_t *out, int32_t *op_status, void *stream) {
-  (void)ctx; (void)count; (void)key_ids; (void)exp_sel; (void)limb_offsets; (void)total_limbs; (void)msgs;
-  (void)out; (void)op_status; (void)stream;
-  return set_error(RSA_ERR_UNSUPPORTED, "ragged batches are not available yet");
+                          const uint64_t *limb_offsets, uint64_t total_limbs, const uint32_t *msgs, uint32_t *out,
+                          int32_t *op_status, void *stream) {
+  if (!ctx) return set_error(RSA_ERR_ARG, "ctx is null");
+  if (count > 0x7fffffffull) return set_error(RSA_ERR_ARG, "count exceeds 2^31 - 1");
+  if (count == 0) return RSA_OK;
+  if (!key_ids || !exp_sel || !limb_offsets || !msgs || !out) return set_error(RSA_ERR_ARG, "null pointer");
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  std::lock_guard<std::mutex> lock(c->mu);
+  cudaSetDevice(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Workspace &w = c->ws(s);
+  // layout of io_in: [key_ids | exp_sel (padded to 8) | offsets | msgs], io_out: out, io_status: status
+  const size_t kb = (size_t)count * 4, eb = ((size_t)count + 7) / 8 * 8, ob = (size_t)count * 8;
+  const size_t mb = (size_t)total_limbs * 4;
+  const size_t head = (kb + eb + ob + 255) / 256 * 256;
+  int rc;
+  if ((rc = c->ensure(w.io_in, head + mb)) || (rc = c->ensure(w.io_out, mb)) ||
+      (op_status && (rc = c->ensure(w.io_status, (size_t)count * 4))))
+    return rc;
+  char *base = static_cast<char *>(w.io_in.ptr);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(base, key_ids, kb, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(base + kb, exp_sel, (size_t)count, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(base + kb + eb, limb_offsets, ob, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(base + head, msgs, mb, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_error(e, "cudaMemcpyAsync H2D");
+  c->stats.ops += count;
+  rc = c->run_batch(count, reinterpret_cast<const int32_t *>(base), reinterpret_cast<const uint8_t *>(base + kb),
+                    reinterpret_cast<const uint64_t *>(base + kb + eb), reinterpret_cast<const uint32_t *>(base + head),
+                    static_cast<uint32_t *>(w.io_out.ptr),
+                    op_status ? static_cast<int32_t *>(w.io_status.ptr) : nullptr, s);
+  if (rc) return rc;
+  if ((e = cudaMemcpyAsync(out, w.io_out.ptr, mb, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_error(e, "cudaMemcpyAsync D2H");
+  if (op_status &&
+      (e = cudaMemcpyAsync(op_status, w.io_status.ptr, (size_t)count * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_error(e, "cudaMemcpyAsync D2H status");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
+  return c->collect_device_errors(s);
 }
 
 }  // extern "C"

@@ -1,0 +1,92 @@
+// batch.h -- ragged multi-key batches: shared definitions of the planning
+// kernels (batch.cu) and the persistent execution kernel (batch_exec.cu).
+//
+// A ragged batch mixes keys of every supported size and all exponent kinds.
+// Operations are grouped on the device into buckets (key id x exponent kind),
+// each bucket is cut into tiles (32 operations for a CRT warp pair, 64 for the
+// other kinds: one warp per 32), tiles are laid out longest-first by class
+// (the cost of one operation of that size and kind) and one persistent kernel
+// pulls tiles from an atomic counter until none are left.
+#pragma once
+#include <cstdint>
+
+#include "keyrec.h"
+
+namespace rsagpu {
+
+struct KeyDirEntry {          // one per key id; rec == null for a free slot
+  const uint32_t *rec;
+  uint32_t L, flags, nbits, e_bits;
+};
+
+struct TileDesc {
+  int32_t bucket;             // key id * 3 + exponent kind
+  int32_t op_start;           // first slot in the sorted operation list
+  int32_t nops;               // live operations in the tile
+  int32_t cls;                // work class (below)
+};
+
+// Work classes: what the execution kernel runs for a (key size, kind) pair.
+enum : int32_t {
+  CLS_TOY = 0,                                   // single-limb keys, any kind
+  CLS_CRT16 = 1, CLS_CRT32 = 2, CLS_CRT48 = 3, CLS_CRT64 = 4,   // CRT, half size H
+  CLS_PUB32 = 5, CLS_PUB64 = 6, CLS_PUB96 = 7, CLS_PUB128 = 8,  // public exponent, L limbs
+  CLS_PLAIN32 = 9, CLS_PLAIN64 = 10,             // plain private exponent, L limbs
+  CLS_COUNT = 11
+};
+
+// Window widths the execution kernel is compiled with, per class.
+constexpr int kBatchWindowCrt16 = 4, kBatchWindowCrt32 = 4, kBatchWindowCrt48 = 5, kBatchWindowCrt64 = 5;
+constexpr int kBatchWindowPlain = 4;
+// Largest per-warp window table (CRT H=64 at w=5, plain L=64 at w=4): uint4 count.
+constexpr size_t kBatchTableU4PerWarp = (size_t)32 * 64 * 8;
+
+__host__ __device__ inline int32_t batch_class(uint32_t L, int kind) {
+  if (L == 1) return CLS_TOY;
+  if (kind == 1) return L == 32 ? CLS_CRT16 : L == 64 ? CLS_CRT32 : L == 96 ? CLS_CRT48 : L == 128 ? CLS_CRT64 : -1;
+  if (kind == 0) return L == 32 ? CLS_PUB32 : L == 64 ? CLS_PUB64 : L == 96 ? CLS_PUB96 : L == 128 ? CLS_PUB128 : -1;
+  if (kind == 2) return L == 32 ? CLS_PLAIN32 : L == 64 ? CLS_PLAIN64 : -1;
+  return -1;
+}
+
+// Execution groups: one persistent kernel each, so every group gets the
+// register allocation its own largest class needs.  Group order is the order
+// of tile ranges: the large CRT classes first, then the rest, then the wide
+// public-exponent classes.
+enum : int32_t { GRP_BIG = 0, GRP_MID = 1, GRP_WIDE = 2, GRP_COUNT = 3 };
+__host__ __device__ inline int32_t batch_group(int32_t cls) {
+  if (cls == CLS_CRT48 || cls == CLS_CRT64) return GRP_BIG;
+  if (cls == CLS_PUB96 || cls == CLS_PUB128) return GRP_WIDE;
+  return GRP_MID;
+}
+
+// operations per tile of a class
+__host__ __device__ inline int32_t batch_tile_ops(int32_t cls) {
+  return (cls >= CLS_CRT16 && cls <= CLS_CRT64) || cls == CLS_PUB96 || cls == CLS_PUB128 ? 32 : 64;
+}
+
+struct BatchDesc {
+  uint32_t count, nkeys;
+  const int32_t *key_ids;
+  const uint8_t *exp_sel;
+  const uint64_t *offsets;
+  const uint32_t *msgs;
+  uint32_t *out;
+  int32_t *status;
+  const KeyDirEntry *dir;
+  // workspace
+  int32_t *op_bucket;         // [count]
+  int32_t *sorted;            // [count]
+  uint32_t *bcount, *bfill, *boff;  // [nkeys * 3]
+  TileDesc *tiles;            // [max_tiles]
+  uint32_t *ctl;              // [0] unused, [1] tile count, [2] error bits,
+                              // [4+g] first tile of group g, [8+g] end, [12+g] counter
+  uint4 *tables;              // per resident warp: kBatchTableU4PerWarp
+  uint32_t max_tiles;
+  int32_t class_rank[CLS_COUNT];  // position of each class in the longest-first order
+};
+
+const void *batch_exec_fn(int group);
+size_t batch_exec_smem_bytes(int group);
+
+}  // namespace rsagpu

@@ -1,0 +1,132 @@
+// batch_exec.cu -- the persistent execution kernel of ragged batches.
+//
+// One CTA is a warp pair (64 threads).  It repeatedly takes the next tile from
+// the planned list (an atomic counter; tiles are ordered longest-first, so the
+// short ones fill the tail), copies the tile's key record into shared memory
+// and runs the tile function of its class:
+//   CRT       both warps, q half and p half (crt_tile)
+//   public    L <= 64: one warp per 32 operations (pub_tile);
+//             L = 96, 128: warp 0 only, operands in shared memory (pub_wide_tile)
+//   plain     one warp per 32 operations (plain_tile)
+//   toy       one thread per operation (toy_op)
+#include "batch.h"
+#include "kernels.cuh"
+
+namespace rsagpu {
+namespace {
+
+constexpr int kU = 8;
+constexpr int kKeyWordsMax = (KeyLayout(128).total + 3) / 4 * 4;
+// work area after the key record: the largest of
+//   CRT H=64: exchange + 2 stages = 3 * 64 * 128 B; public L=64: 2 warps x 2 stages = 4 * 64 * 128 B;
+//   public wide L=128: 1 warp x 2 stages = 2 * 128 * 128 B
+constexpr size_t kWorkBytes = (size_t)4 * 64 * 128;
+constexpr size_t kSmemBytes = (size_t)kKeyWordsMax * 4 + kWorkBytes;
+
+template <int H, int W>
+__device__ __forceinline__ void run_crt(const uint32_t *ks, uint4 *work, uint4 *table_warp, int warp, int lane,
+                                        const TileIO &io) {
+  constexpr int kStage = (H / 4) * 32;
+  uint4 *xb = work + lane;
+  uint4 *stage_lane = work + kStage + warp * kStage + lane;
+  crt_tile<H, W, kU, (H <= 32)>(ks, warp == 1, lane, stage_lane, xb, table_warp + lane, 1, io);
+}
+
+template <int L>
+__device__ __forceinline__ void run_pub(const uint32_t *ks, uint4 *work, int warp, int lane, const TileIO &io) {
+  constexpr int kStage = (L / 4) * 32;
+  uint4 *sq = work + warp * 2 * kStage + lane;
+  pub_tile<L, kU>(ks, lane, sq, sq + kStage, io);
+}
+
+template <int L>
+__device__ __forceinline__ void run_pub_wide(const uint32_t *ks, uint4 *work, int lane, const TileIO &io) {
+  constexpr int kStage = (L / 4) * 32;
+  pub_wide_tile<L, 4>(ks, lane, work + lane, work + kStage + lane, io);
+}
+
+template <int L>
+__device__ __forceinline__ void run_plain(const uint32_t *ks, uint4 *work, uint4 *table_warp, int warp, int lane,
+                                          const TileIO &io) {
+  constexpr int kStage = (L / 4) * 32;
+  plain_tile<L, kBatchWindowPlain, kU, (L <= 32)>(ks, lane, work + warp * kStage + lane, table_warp + lane, io);
+}
+
+template <int G>
+__global__ void __launch_bounds__(64, 1) batch_exec_kernel(BatchDesc d) {
+  extern __shared__ uint4 smem4[];
+  __shared__ int32_t s_tile;
+  uint32_t *ks = reinterpret_cast<uint32_t *>(smem4);
+  uint4 *work = smem4 + kKeyWordsMax / 4;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint4 *table_warp = d.tables + ((size_t)blockIdx.x * 2 + warp) * kBatchTableU4PerWarp;
+  const uint32_t first = d.ctl[4 + G], end = d.ctl[8 + G];
+#pragma unroll 1
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = (int32_t)(first + atomicAdd(&d.ctl[12 + G], 1u));
+    __syncthreads();
+    const uint32_t t = (uint32_t)s_tile;
+    if (t >= end) break;
+    const TileDesc td = d.tiles[t];
+    const int32_t kid = td.bucket / 3, kind = td.bucket % 3;
+    const KeyDirEntry e = d.dir[kid];
+    const uint32_t words = (KeyLayout(e.L).total + 3) / 4 * 4;
+    const uint4 *src = reinterpret_cast<const uint4 *>(e.rec);
+    for (uint32_t i = threadIdx.x; i < words / 4; i += blockDim.x)
+      smem4[i] = (i * 4 < KeyLayout(e.L).total) ? src[i] : make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    // per-warp slice of a 64-operation tile
+    const int32_t wn = min(32, max(0, td.nops - 32 * warp));
+    const TileIO io_pair{d.msgs, d.out, d.status, d.sorted, d.offsets, (uint32_t)td.op_start, (uint32_t)td.nops};
+    const TileIO io_warp{d.msgs, d.out, d.status, d.sorted, d.offsets, (uint32_t)(td.op_start + 32 * warp),
+                         (uint32_t)wn};
+    if constexpr (G == GRP_BIG) {
+      if (td.cls == CLS_CRT48) run_crt<48, kBatchWindowCrt48>(ks, work, table_warp, warp, lane, io_pair);
+      else if (td.cls == CLS_CRT64) run_crt<64, kBatchWindowCrt64>(ks, work, table_warp, warp, lane, io_pair);
+    } else if constexpr (G == GRP_WIDE) {
+      if (warp == 0) {
+        if (td.cls == CLS_PUB96) run_pub_wide<96>(ks, work, lane, io_pair);
+        else if (td.cls == CLS_PUB128) run_pub_wide<128>(ks, work, lane, io_pair);
+      }
+    } else {
+      const KeyHeader &hd = *reinterpret_cast<const KeyHeader *>(ks);
+      switch (td.cls) {
+        case CLS_CRT16: run_crt<16, kBatchWindowCrt16>(ks, work, table_warp, warp, lane, io_pair); break;
+        case CLS_CRT32: run_crt<32, kBatchWindowCrt32>(ks, work, table_warp, warp, lane, io_pair); break;
+        case CLS_PUB32: if (wn > 0) run_pub<32>(ks, work, warp, lane, io_warp); break;
+        case CLS_PUB64: if (wn > 0) run_pub<64>(ks, work, warp, lane, io_warp); break;
+        case CLS_PLAIN32: if (wn > 0) run_plain<32>(ks, work, table_warp, warp, lane, io_warp); break;
+        case CLS_PLAIN64: if (wn > 0) run_plain<64>(ks, work, table_warp, warp, lane, io_warp); break;
+        case CLS_TOY: {
+          const int slot = (int)threadIdx.x;
+          if (slot < td.nops) {
+            const uint32_t op = (uint32_t)d.sorted[td.op_start + slot];
+            const size_t off = (size_t)d.offsets[op];
+            const uint32_t x = d.msgs[off];
+            const bool ok = x < ks[KeyLayout(1).n];
+            const uint32_t r = toy_op(ks, hd, kind, x);
+            d.out[off] = ok ? r : 0u;
+            if (d.status) d.status[op] = ok ? 0 : -3;
+          }
+          break;
+        }
+        default: break;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+const void *batch_exec_fn(int group) {
+  switch (group) {
+    case GRP_BIG: return reinterpret_cast<const void *>(&batch_exec_kernel<GRP_BIG>);
+    case GRP_MID: return reinterpret_cast<const void *>(&batch_exec_kernel<GRP_MID>);
+    case GRP_WIDE: return reinterpret_cast<const void *>(&batch_exec_kernel<GRP_WIDE>);
+    default: return nullptr;
+  }
+}
+size_t batch_exec_smem_bytes(int group) { (void)group; return kSmemBytes; }
+
+}  // namespace rsagpu

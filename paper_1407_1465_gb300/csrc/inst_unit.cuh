@@ -19,37 +19,53 @@ constexpr int kH = RSAGPU_UNIT;
 constexpr int kL = 2 * kH;
 constexpr int kU = 8;  // outer CIOS block: 8 limbs of B per runtime iteration
 
-template <int W>
-const void *crt_fn() { return reinterpret_cast<const void *>(&crt_kernel<kH, W, kU>); }
+// separated squaring where its 2L-limb product fits in registers
+constexpr bool kSqrOk = (kH <= 32);
+constexpr bool kSqrOkFull = (kL <= 32);
 
 template <int W>
-const void *plain_fn() {
-  if constexpr (kL <= 64) return reinterpret_cast<const void *>(&plain_kernel<kL, W, kU>);
-  else return nullptr;
+const void *crt_fn(int variant) {
+  if (variant == 2 || (variant == 0 && kSqrOk)) {
+    if constexpr (kSqrOk) return reinterpret_cast<const void *>(&crt_kernel<kH, W, kU, true>);
+    else return nullptr;
+  }
+  return reinterpret_cast<const void *>(&crt_kernel<kH, W, kU, false>);
+}
+
+template <int W>
+const void *plain_fn(int variant) {
+  if constexpr (kL <= 64) {
+    if (variant == 2 || (variant == 0 && kSqrOkFull)) {
+      if constexpr (kSqrOkFull) return reinterpret_cast<const void *>(&plain_kernel<kL, W, kU, true>);
+      else return nullptr;
+    }
+    return reinterpret_cast<const void *>(&plain_kernel<kL, W, kU, false>);
+  }
+  return nullptr;
 }
 }  // namespace
 
-const void *RSAGPU_CAT(crt_kernel_fn_, RSAGPU_UNIT)(int W) {
+const void *RSAGPU_CAT(crt_kernel_fn_, RSAGPU_UNIT)(int W, int variant) {
   switch (W) {
-    case 3: return crt_fn<3>();
-    case 4: return crt_fn<4>();
-    case 5: return crt_fn<5>();
-    case 6: return crt_fn<6>();
+    case 3: return crt_fn<3>(variant);
+    case 4: return crt_fn<4>(variant);
+    case 5: return crt_fn<5>(variant);
+    case 6: return crt_fn<6>(variant);
     default: return nullptr;
   }
 }
 
-const void *RSAGPU_CAT(plain_kernel_fn_, RSAGPU_UNIT)(int W) {
+const void *RSAGPU_CAT(plain_kernel_fn_, RSAGPU_UNIT)(int W, int variant) {
   switch (W) {
-    case 4: return plain_fn<4>();
-    case 5: return plain_fn<5>();
+    case 4: return plain_fn<4>(variant);
+    case 5: return plain_fn<5>(variant);
     default: return nullptr;
   }
 }
 
 const void *RSAGPU_CAT(pub_kernel_fn_, RSAGPU_UNIT)() {
   if constexpr (kL <= 64) return reinterpret_cast<const void *>(&pub_kernel<kL, kU>);
-  else return nullptr;
+  else return reinterpret_cast<const void *>(&pub_wide_kernel<kL, 4>);
 }
 
 }  // namespace rsagpu

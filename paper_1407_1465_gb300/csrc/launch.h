@@ -8,10 +8,12 @@
 
 namespace rsagpu {
 
+// Squaring variant of the private-exponent kernels: 0 = automatic (separated
+// squaring where it fits in registers), 1 = CIOS squaring, 2 = separated.
 // CRT decryption, half size H limbs, window W
-const void *crt_kernel_fn(int H, int W);
+const void *crt_kernel_fn(int H, int W, int variant = 0);
 // plain private exponent mod n, L limbs, window W
-const void *plain_kernel_fn(int L, int W);
+const void *plain_kernel_fn(int L, int W, int variant = 0);
 // public exponent (binary method), L limbs
 const void *pub_kernel_fn(int L);
 // single-limb keys (n < 2^32)
@@ -22,8 +24,8 @@ constexpr int kMinWindow = 3;
 constexpr int kMaxWindow = 6;
 
 #define RSAGPU_DECLARE_UNIT(X)                      \
-  const void *crt_kernel_fn_##X(int W);             \
-  const void *plain_kernel_fn_##X(int W);           \
+  const void *crt_kernel_fn_##X(int W, int variant);   \
+  const void *plain_kernel_fn_##X(int W, int variant); \
   const void *pub_kernel_fn_##X();
 
 RSAGPU_DECLARE_UNIT(16)

@@ -10,24 +10,6 @@
 namespace rsagpu {
 
 // ------------------------------------------------------------------ single-limb keys
-// The paper's own setting (Sec. 10: 8-bit-class keys, n = 131*137 = 17947):
-// each thread computes one message's x^E mod m with 64-bit products reduced by
-// "%" (Fig. 3), by left-to-right binary square-and-multiply (Fig. 5) over all
-// 32 exponent bit positions with the multiplication always performed and kept
-// by a mask, so the work does not depend on the exponent.
-__device__ __forceinline__ uint32_t pow_mod32(uint32_t x, uint32_t E, uint32_t m) {
-  uint64_t r = 1u % m;
-  const uint64_t xm = x % m;
-#pragma unroll 4
-  for (int b = 31; b >= 0; --b) {
-    r = (r * r) % m;
-    const uint64_t rx = (r * xm) % m;
-    const uint64_t keep = 0ull - (uint64_t)((E >> b) & 1u);
-    r = (rx & keep) | (r & ~keep);
-  }
-  return (uint32_t)r;
-}
-
 __global__ void toy_kernel(ToyArgs a) {
   const KeyLayout lay(1);
   const KeyHeader &hd = *reinterpret_cast<const KeyHeader *>(a.keyrec);
@@ -35,20 +17,7 @@ __global__ void toy_kernel(ToyArgs a) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.count; i += gridDim.x * blockDim.x) {
     const uint32_t x = a.msgs[i];
     const bool ok = x < n;
-    uint32_t r;
-    if (a.kind == 0) {
-      r = pow_mod32(x, a.keyrec[lay.e], n);
-    } else if (a.kind == 2) {
-      r = pow_mod32(x, a.keyrec[lay.d], n);
-    } else {
-      // CRT: m_p = x^dp mod p, m_q = x^dq mod q, h = qinv (m_p - m_q) mod p, m = m_q + h q
-      const uint32_t p = hd.reserved[0], q = hd.reserved[1];
-      const uint32_t mp = pow_mod32(x, hd.reserved[2], p);
-      const uint32_t mq = pow_mod32(x, hd.reserved[3], q);
-      const uint64_t diff = ((uint64_t)mp + p - (mq % p)) % p;
-      const uint64_t h = (diff * hd.reserved[4]) % p;
-      r = (uint32_t)(mq + h * q);
-    }
+    const uint32_t r = toy_op(a.keyrec, hd, a.kind, x);
     a.out[i] = ok ? r : 0u;
     if (a.status) a.status[i] = ok ? 0 : -3;
   }
@@ -57,19 +26,19 @@ __global__ void toy_kernel(ToyArgs a) {
 const void *toy_kernel_fn() { return reinterpret_cast<const void *>(&toy_kernel); }
 
 // ------------------------------------------------------------------ lookup
-const void *crt_kernel_fn(int H, int W) {
+const void *crt_kernel_fn(int H, int W, int variant) {
   switch (H) {
-    case 16: return crt_kernel_fn_16(W);
-    case 32: return crt_kernel_fn_32(W);
-    case 48: return crt_kernel_fn_48(W);
-    case 64: return crt_kernel_fn_64(W);
+    case 16: return crt_kernel_fn_16(W, variant);
+    case 32: return crt_kernel_fn_32(W, variant);
+    case 48: return crt_kernel_fn_48(W, variant);
+    case 64: return crt_kernel_fn_64(W, variant);
     default: return nullptr;
   }
 }
-const void *plain_kernel_fn(int L, int W) {
+const void *plain_kernel_fn(int L, int W, int variant) {
   switch (L) {
-    case 32: return plain_kernel_fn_16(W);
-    case 64: return plain_kernel_fn_32(W);
+    case 32: return plain_kernel_fn_16(W, variant);
+    case 64: return plain_kernel_fn_32(W, variant);
     default: return nullptr;
   }
 }
@@ -77,6 +46,8 @@ const void *pub_kernel_fn(int L) {
   switch (L) {
     case 32: return pub_kernel_fn_16();
     case 64: return pub_kernel_fn_32();
+    case 96: return pub_kernel_fn_48();
+    case 128: return pub_kernel_fn_64();
     default: return nullptr;
   }
 }

@@ -198,6 +198,230 @@ __device__ __forceinline__ void mont_mul(uint32_t (&A)[L], const BS &B, const NS
   final_sub<L>(A, t, N);
 }
 
+// A = A^2 * R^-1 mod N (A < N), separated form: the square A^2 first, then a
+// Montgomery reduction of the 2L-limb product.  The square needs each cross
+// product a_i a_j (i < j) once, doubled, plus the diagonal a_i^2:
+// L(L+1)/2 word products instead of L^2; the reduction costs L^2 + L like the
+// second half of CIOS.  Every index is a compile-time constant (fully
+// unrolled), so the 2L-limb product lives in registers.
+template <int L, class NS>
+__device__ __forceinline__ void mont_sqr(uint32_t (&A)[L], const NS &N, uint32_t np) {
+  uint32_t t[2 * L];
+#pragma unroll
+  for (int k = 0; k < 2 * L; ++k) t[k] = 0u;
+  // cross products, row i: t[i+j .. i+j+1] += a_i * a_j for j > i, two chains
+  // (j - i odd, j - i even), each closed by propagating its carry two limbs up
+#pragma unroll
+  for (int i = 0; i < L - 1; ++i) {
+#pragma unroll
+    for (int par = 0; par < 2; ++par) {
+      const int j0 = i + 1 + par;
+      if (j0 <= L - 1) {
+        t[i + j0] = mad_lo_cc(A[i], A[j0], t[i + j0]);
+        t[i + j0 + 1] = madc_hi_cc(A[i], A[j0], t[i + j0 + 1]);
+        int last = i + j0 + 1;
+#pragma unroll
+        for (int j = j0 + 2; j < L; j += 2) {
+          t[i + j] = madc_lo_cc(A[i], A[j], t[i + j]);
+          t[i + j + 1] = madc_hi_cc(A[i], A[j], t[i + j + 1]);
+          last = i + j + 1;
+        }
+        if (last + 2 < 2 * L) {
+          t[last + 1] = addc_cc(t[last + 1], 0u);
+          t[last + 2] = addc(t[last + 2], 0u);
+        } else if (last + 1 < 2 * L) {
+          t[last + 1] = addc(t[last + 1], 0u);
+        }
+      }
+    }
+  }
+  // double (the cross sum is below 2^(64L-1), so nothing leaves the top limb)
+#pragma unroll
+  for (int k = 2 * L - 1; k > 0; --k) t[k] = __funnelshift_l(t[k - 1], t[k], 1);
+  t[0] <<= 1;
+  // diagonal squares a_i^2 at limbs 2i, 2i+1
+  t[0] = mad_lo_cc(A[0], A[0], t[0]);
+  t[1] = madc_hi_cc(A[0], A[0], t[1]);
+#pragma unroll
+  for (int i = 1; i < L; ++i) {
+    t[2 * i] = madc_lo_cc(A[i], A[i], t[2 * i]);
+    t[2 * i + 1] = madc_hi_cc(A[i], A[i], t[2 * i + 1]);
+  }
+  // Montgomery reduction: step i clears limb i by adding q*N*2^(32i); the
+  // carry leaving limb i+L waits in c and enters at the next step's top limb.
+  uint32_t c = 0u;
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    const uint32_t q = t[i] * np;
+    (void)mad_lo_cc(q, N.get(0), t[i]);
+    t[i + 1] = madc_hi_cc(q, N.get(0), t[i + 1]);
+#pragma unroll
+    for (int k = 1; k < L / 2; ++k) {
+      t[i + 2 * k] = madc_lo_cc(q, N.get(2 * k), t[i + 2 * k]);
+      t[i + 2 * k + 1] = madc_hi_cc(q, N.get(2 * k), t[i + 2 * k + 1]);
+    }
+    t[i + L] = addc_cc(t[i + L], c);
+    const uint32_t c1 = addc(0u, 0u);
+    t[i + 1] = mad_lo_cc(q, N.get(1), t[i + 1]);
+    t[i + 2] = madc_hi_cc(q, N.get(1), t[i + 2]);
+#pragma unroll
+    for (int k = 1; k < L / 2; ++k) {
+      t[i + 2 * k + 1] = madc_lo_cc(q, N.get(2 * k + 1), t[i + 2 * k + 1]);
+      t[i + 2 * k + 2] = madc_hi_cc(q, N.get(2 * k + 1), t[i + 2 * k + 2]);
+    }
+    c = addc(c1, 0u);
+  }
+  uint32_t r[L + 2];
+#pragma unroll
+  for (int j = 0; j < L; ++j) r[j] = t[L + j];
+  r[L] = c;
+  r[L + 1] = 0u;
+  final_sub<L>(A, r, N);
+}
+
+// ------------------------------------------------------------------ wide operands (L = 96, 128)
+// 128-bit shared-memory load issued exactly where written (volatile asm is not
+// reordered against the carry-chain asm), so operands are not hoisted into
+// registers ahead of their use.
+__device__ __forceinline__ uint4 lds128(const uint4 *p) {
+  uint4 v;
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+  return v;
+}
+
+// For moduli too wide to keep A in registers next to the accumulator, A lives
+// in a per-lane staging buffer (layout [L/4][32] of uint4) and is streamed
+// like B; only t stays in registers.  Same CIOS steps and chains as mul_acc.
+
+// t += b * A with A read from shared memory (even limbs, then odd limbs)
+template <int L>
+__device__ __forceinline__ void mul_acc_smem(uint32_t (&t)[L + 2], const uint4 *A_lane, uint32_t b) {
+  {
+    const uint4 a = lds128(A_lane);
+    t[0] = mad_lo_cc(a.x, b, t[0]);
+    t[1] = madc_hi_cc(a.x, b, t[1]);
+    t[2] = madc_lo_cc(a.z, b, t[2]);
+    t[3] = madc_hi_cc(a.z, b, t[3]);
+  }
+#pragma unroll
+  for (int g = 1; g < L / 4; ++g) {
+    const uint4 a = lds128(A_lane + g * 32);
+    t[4 * g] = madc_lo_cc(a.x, b, t[4 * g]);
+    t[4 * g + 1] = madc_hi_cc(a.x, b, t[4 * g + 1]);
+    t[4 * g + 2] = madc_lo_cc(a.z, b, t[4 * g + 2]);
+    t[4 * g + 3] = madc_hi_cc(a.z, b, t[4 * g + 3]);
+  }
+  t[L] = addc_cc(t[L], 0u);
+  t[L + 1] = addc(t[L + 1], 0u);
+  {
+    const uint4 a = lds128(A_lane);
+    t[1] = mad_lo_cc(a.y, b, t[1]);
+    t[2] = madc_hi_cc(a.y, b, t[2]);
+    t[3] = madc_lo_cc(a.w, b, t[3]);
+    t[4] = madc_hi_cc(a.w, b, t[4]);
+  }
+#pragma unroll
+  for (int g = 1; g < L / 4; ++g) {
+    const uint4 a = lds128(A_lane + g * 32);
+    t[4 * g + 1] = madc_lo_cc(a.y, b, t[4 * g + 1]);
+    t[4 * g + 2] = madc_hi_cc(a.y, b, t[4 * g + 2]);
+    t[4 * g + 3] = madc_lo_cc(a.w, b, t[4 * g + 3]);
+    t[4 * g + 4] = madc_hi_cc(a.w, b, t[4 * g + 4]);
+  }
+  t[L + 1] = addc(t[L + 1], 0u);
+}
+
+// reduce_step with N read from shared memory four limbs at a time next to its
+// use (the even chain takes .x/.z, the odd chain .y/.w of each group).
+template <int L>
+__device__ __forceinline__ void reduce_step_smem(uint32_t (&t)[L + 2], const uint4 *N4, uint32_t np) {
+  const uint32_t q = t[0] * np;
+  {
+    const uint4 n = lds128(N4);
+    (void)mad_lo_cc(q, n.x, t[0]);
+    t[0] = madc_hi_cc(q, n.x, t[1]);
+    t[1] = madc_lo_cc(q, n.z, t[2]);
+    t[2] = madc_hi_cc(q, n.z, t[3]);
+  }
+#pragma unroll
+  for (int g = 1; g < L / 4; ++g) {
+    const uint4 n = lds128(N4 + g);
+    t[4 * g - 1] = madc_lo_cc(q, n.x, t[4 * g]);
+    t[4 * g] = madc_hi_cc(q, n.x, t[4 * g + 1]);
+    t[4 * g + 1] = madc_lo_cc(q, n.z, t[4 * g + 2]);
+    t[4 * g + 2] = madc_hi_cc(q, n.z, t[4 * g + 3]);
+  }
+  t[L - 1] = addc_cc(t[L], 0u);
+  t[L] = addc(t[L + 1], 0u);
+  {
+    const uint4 n = lds128(N4);
+    t[0] = mad_lo_cc(q, n.y, t[0]);
+    t[1] = madc_hi_cc(q, n.y, t[1]);
+    t[2] = madc_lo_cc(q, n.w, t[2]);
+    t[3] = madc_hi_cc(q, n.w, t[3]);
+  }
+#pragma unroll
+  for (int g = 1; g < L / 4; ++g) {
+    const uint4 n = lds128(N4 + g);
+    t[4 * g] = madc_lo_cc(q, n.y, t[4 * g]);
+    t[4 * g + 1] = madc_hi_cc(q, n.y, t[4 * g + 1]);
+    t[4 * g + 2] = madc_lo_cc(q, n.w, t[4 * g + 2]);
+    t[4 * g + 3] = madc_hi_cc(q, n.w, t[4 * g + 3]);
+  }
+  t[L] = addc(t[L], 0u);
+  t[L + 1] = 0u;
+}
+
+// A_lane = t - N if t >= N else t (t < 2N), written back in groups of four.
+// First pass finds the borrow of t - N, second pass recomputes the difference
+// limb by limb and selects, so no L-limb temporary is needed.
+template <int L, class NS>
+__device__ __forceinline__ void final_sub_smem(uint4 *A_lane, const uint32_t (&t)[L + 2], const NS &N) {
+  uint32_t d = sub_cc(t[0], N.get(0));
+#pragma unroll
+  for (int j = 1; j < L; ++j) d = subc_cc(t[j], N.get(j));
+  const uint32_t keep_t = subc(t[L], 0u);  // all ones iff t < N
+  (void)d;
+  uint32_t u0 = sub_cc(t[0], N.get(0));
+#pragma unroll
+  for (int g = 0; g < L / 4; ++g) {
+    uint32_t u1, u2, u3;
+    if (g > 0) u0 = subc_cc(t[4 * g], N.get(4 * g));
+    u1 = subc_cc(t[4 * g + 1], N.get(4 * g + 1));
+    u2 = subc_cc(t[4 * g + 2], N.get(4 * g + 2));
+    u3 = subc_cc(t[4 * g + 3], N.get(4 * g + 3));
+    A_lane[g * 32] = make_uint4((t[4 * g] & keep_t) | (u0 & ~keep_t), (t[4 * g + 1] & keep_t) | (u1 & ~keep_t),
+                                (t[4 * g + 2] & keep_t) | (u2 & ~keep_t), (t[4 * g + 3] & keep_t) | (u3 & ~keep_t));
+  }
+}
+
+// A_lane = A * B * R^-1 mod N with A in shared memory (B may alias A).
+template <int L, int U, class NS>
+__device__ __forceinline__ void mont_mul_smemA(uint4 *A_lane, const SmemB &B, const NS &N, uint32_t np) {
+  static_assert(L % 4 == 0 && U % 4 == 0 && L % U == 0, "limb blocking");
+  const uint4 *N4 = reinterpret_cast<const uint4 *>(N.s);
+  uint32_t t[L + 2];
+#pragma unroll
+  for (int j = 0; j < L + 2; ++j) t[j] = 0u;
+#pragma unroll 1
+  for (int i0 = 0; i0 < L; i0 += U) {
+#pragma unroll
+    for (int u = 0; u < U; u += 4) {
+      const uint4 b = B.get4((i0 + u) >> 2);
+      mul_acc_smem<L>(t, A_lane, b.x);
+      reduce_step_smem<L>(t, N4, np);
+      mul_acc_smem<L>(t, A_lane, b.y);
+      reduce_step_smem<L>(t, N4, np);
+      mul_acc_smem<L>(t, A_lane, b.z);
+      reduce_step_smem<L>(t, N4, np);
+      mul_acc_smem<L>(t, A_lane, b.w);
+      reduce_step_smem<L>(t, N4, np);
+    }
+  }
+  final_sub_smem<L>(A_lane, t, N);
+}
+
 // ------------------------------------------------------------------ modular add / sub
 // A = (A + B) mod N for A, B < N (B from a per-lane stage).
 template <int L, class NS>

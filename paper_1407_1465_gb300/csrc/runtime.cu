@@ -93,7 +93,7 @@ static int default_window(uint32_t L, int kind) {
 }
 
 Tune Ctx::tune_for(uint32_t nbits, int kind) const {
-  Tune t{0, 0, 0};
+  Tune t{0, 0, 0, 0};
   auto it = tuning.find({nbits, kind});
   if (it != tuning.end()) t = it->second;
   const uint32_t L = nbits / 32;
@@ -150,7 +150,7 @@ int Ctx::run_key(const KeySlot &k, int kind, uint64_t count, const uint32_t *msg
   const Tune t = tune_for(k.nbits, kind);
   if (kind == RSA_EXP_PRIVATE_CRT) {
     const int H = (int)L / 2;
-    const void *fn = crt_kernel_fn(H, t.window);
+    const void *fn = crt_kernel_fn(H, t.window, t.variant);
     if (!fn) return set_error(RSA_ERR_UNSUPPORTED, "no CRT kernel for this key size / window");
     const int P = std::max(1, t.warps_per_cta / 2);
     const int threads = 64 * P;
@@ -172,7 +172,7 @@ int Ctx::run_key(const KeySlot &k, int kind, uint64_t count, const uint32_t *msg
     return RSA_OK;
   }
   const bool pub = (kind == RSA_EXP_PUBLIC);
-  const void *fn = pub ? pub_kernel_fn((int)L) : plain_kernel_fn((int)L, t.window);
+  const void *fn = pub ? pub_kernel_fn((int)L) : plain_kernel_fn((int)L, t.window, t.variant);
   if (!fn) return set_error(RSA_ERR_UNSUPPORTED, "no kernel for this key size / exponent kind");
   const int warps = std::max(1, t.warps_per_cta);
   const int threads = 32 * warps;
@@ -242,6 +242,7 @@ int rsa_ctx_create(rsa_ctx **out, int device, size_t mem_budget_bytes) {
 
 int rsa_ctx_destroy(rsa_ctx *ctx) {
   if (!ctx) return set_error(RSA_ERR_ARG, "ctx is null");
+  if (reinterpret_cast<Ctx *>(ctx)->server) rsa_server_stop(ctx);
   delete reinterpret_cast<Ctx *>(ctx);
   return RSA_OK;
 }
@@ -439,9 +440,10 @@ int rsa_set_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, const rsa_tuni
     return set_error(RSA_ERR_ARG, "window out of range");
   if (t->warps_per_cta < 0 || t->warps_per_cta > 8 || t->ctas_per_sm < 0)
     return set_error(RSA_ERR_ARG, "bad launch shape");
+  if (t->variant < 0 || t->variant > 2) return set_error(RSA_ERR_ARG, "variant must be 0, 1 or 2");
   if (exp_sel == RSA_EXP_PRIVATE_CRT && (t->warps_per_cta & 1))
     return set_error(RSA_ERR_ARG, "CRT kernels run warp pairs: warps_per_cta must be even");
-  c->tuning[{nbits, exp_sel}] = Tune{t->window, t->warps_per_cta, t->ctas_per_sm};
+  c->tuning[{nbits, exp_sel}] = Tune{t->window, t->warps_per_cta, t->ctas_per_sm, t->variant};
   return RSA_OK;
 }
 
@@ -453,6 +455,7 @@ int rsa_get_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, rsa_tuning *t)
   t->window = x.window;
   t->warps_per_cta = x.warps_per_cta;
   t->ctas_per_sm = x.ctas_per_sm;
+  t->variant = x.variant;
   return RSA_OK;
 }
 

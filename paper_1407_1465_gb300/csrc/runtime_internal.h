@@ -38,7 +38,7 @@ struct KeySlot {
 };
 
 struct Tune {
-  int window, warps_per_cta, ctas_per_sm;
+  int window, warps_per_cta, ctas_per_sm, variant;
 };
 
 struct Ctx {
@@ -52,8 +52,9 @@ struct Ctx {
   std::map<std::pair<uint32_t, int>, Tune> tuning;
   rsa_stats stats{};
   int last_grid = 0, last_threads = 0;
-  // ragged-batch state (batch.cu)
+  // ragged-batch state (batch.cu) and the request loop (server.cu)
   void *batch_state = nullptr;
+  void *server = nullptr;
 
   ~Ctx();
   int reserve(size_t bytes);
@@ -66,6 +67,8 @@ struct Ctx {
                   int ctas_per_sm_req, int *grid_out);
   int run_key(const KeySlot &k, int kind, uint64_t count, const uint32_t *msgs, uint32_t *out,
               int32_t *status, cudaStream_t s);
+  int run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_sel, const uint64_t *offsets,
+                const uint32_t *msgs, uint32_t *out, int32_t *status, cudaStream_t s);
   int collect_device_errors(cudaStream_t s);
   void free_extra();
 };

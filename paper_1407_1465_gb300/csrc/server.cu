@@ -1,0 +1,481 @@
+// server.cu -- the request loop (rsa_server_*): arrival replay, admission by
+// device-memory budget, continuous batching over several streams, latency
+// accounting.  Host code; the GPU work of each batch is rsa_modexp_batch's
+// graph (batch.cu) on the slot's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "keyrec.h"
+#include "runtime_internal.h"
+
+namespace rsagpu {
+namespace {
+
+uint64_t now_ns() {
+  return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+struct Req {
+  uint64_t ticket = 0;
+  int32_t key_id = 0, exp_sel = 0;
+  uint32_t count = 0, L = 0;
+  const uint32_t *msgs = nullptr;
+  uint32_t *out = nullptr;
+  int32_t *status = nullptr;
+  uint64_t arrive = 0;   // steady-clock ns
+  uint64_t bytes = 0;    // device footprint
+  int32_t state = 0;     // 0 queued, 1 in flight, 2 done, < 0 failed
+  uint64_t done = 0;
+};
+
+// one in-flight batch: a stream, its staging buffers and the requests it carries
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool busy = false;
+  size_t cap_bytes = 0;                 // device bytes for messages + results + metadata
+  uint32_t cap_ops = 0, cap_limbs = 0;
+  // pinned host staging
+  int32_t *h_keys = nullptr;
+  uint8_t *h_sel = nullptr;
+  uint64_t *h_off = nullptr;
+  uint32_t *h_msgs = nullptr, *h_out = nullptr;
+  int32_t *h_status = nullptr;
+  // device buffers
+  void *d_buf = nullptr;
+  int32_t *d_keys = nullptr;
+  uint8_t *d_sel = nullptr;
+  uint64_t *d_off = nullptr;
+  uint32_t *d_msgs = nullptr, *d_out = nullptr;
+  int32_t *d_status = nullptr;
+  std::vector<Req *> reqs;
+  std::vector<uint64_t> req_off;        // first limb of each request in the staging buffers
+  uint64_t bytes = 0;
+};
+
+}  // namespace
+
+struct Server {
+  Ctx *ctx = nullptr;
+  rsa_server_cfg cfg{};
+  std::thread thr;
+  std::mutex mu;
+  std::condition_variable cv, done_cv;
+  bool stop = false;
+  uint64_t epoch = 0;
+  uint64_t next_ticket = 1;
+  std::deque<Req *> queue;                      // not yet admitted, in submission order
+  std::unordered_map<uint64_t, Req *> all;      // every request not yet retired
+  std::vector<Slot> slots;
+  uint64_t inflight_bytes = 0, peak_bytes = 0;
+  uint64_t pending = 0;                         // submitted and not finished
+  // statistics
+  std::vector<double> lat_us;
+  uint64_t submitted = 0, completed = 0, rejected = 0, ops_completed = 0, batches = 0;
+  uint64_t first_arrive = 0, last_done = 0;
+  int fatal = 0;
+
+  int init();
+  void release();
+  void loop();
+  bool launch(Slot &s, std::vector<Req *> &batch);
+  void finish(Slot &s);
+};
+
+namespace {
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+}
+
+int Server::init() {
+  const int n = cfg.max_inflight_batches;
+  const size_t per_slot = cfg.mem_budget_bytes / (size_t)n;
+  slots.resize(n);
+  for (Slot &s : slots) {
+    s.cap_bytes = per_slot;
+    // per operation: key id 4 + kind 1 + offset 8 + status 4 (+ padding) ~ 24 bytes of metadata
+    s.cap_ops = (uint32_t)std::min<size_t>((size_t)cfg.max_batch_ops, per_slot / 64);
+    const size_t meta = align256((size_t)s.cap_ops * 4) + align256(s.cap_ops) + align256((size_t)s.cap_ops * 8) +
+                        align256((size_t)s.cap_ops * 4);
+    if (per_slot <= meta + 4096) return set_error(RSA_ERR_ARG, "memory budget too small for the slot count");
+    s.cap_limbs = (uint32_t)std::min<size_t>((per_slot - meta) / 8, 0xffffffffu);  // messages + results
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_error(e, "server stream/event");
+    if ((e = cudaMallocHost(&s.h_keys, (size_t)s.cap_ops * 4)) != cudaSuccess ||
+        (e = cudaMallocHost(&s.h_sel, s.cap_ops)) != cudaSuccess ||
+        (e = cudaMallocHost(&s.h_off, (size_t)s.cap_ops * 8)) != cudaSuccess ||
+        (e = cudaMallocHost(&s.h_status, (size_t)s.cap_ops * 4)) != cudaSuccess ||
+        (e = cudaMallocHost(&s.h_msgs, (size_t)s.cap_limbs * 4)) != cudaSuccess ||
+        (e = cudaMallocHost(&s.h_out, (size_t)s.cap_limbs * 4)) != cudaSuccess)
+      return cuda_error(e, "server pinned staging");
+    const size_t dev = meta + (size_t)s.cap_limbs * 8;
+    int rc = ctx->reserve(dev);
+    if (rc) return rc;
+    if ((e = cudaMalloc(&s.d_buf, dev)) != cudaSuccess) {
+      ctx->release(dev);
+      return set_error(RSA_ERR_NOMEM, std::string("server device buffers: ") + cudaGetErrorString(e));
+    }
+    char *p = static_cast<char *>(s.d_buf);
+    s.d_keys = reinterpret_cast<int32_t *>(p);
+    p += align256((size_t)s.cap_ops * 4);
+    s.d_sel = reinterpret_cast<uint8_t *>(p);
+    p += align256(s.cap_ops);
+    s.d_off = reinterpret_cast<uint64_t *>(p);
+    p += align256((size_t)s.cap_ops * 8);
+    s.d_status = reinterpret_cast<int32_t *>(p);
+    p += align256((size_t)s.cap_ops * 4);
+    s.d_msgs = reinterpret_cast<uint32_t *>(p);
+    s.d_out = s.d_msgs + s.cap_limbs;
+  }
+  return RSA_OK;
+}
+
+void Server::release() {
+  for (Slot &s : slots) {
+    if (s.stream) cudaStreamSynchronize(s.stream);
+    if (s.d_buf) {
+      cudaFree(s.d_buf);
+      ctx->release(align256((size_t)s.cap_ops * 4) + align256(s.cap_ops) + align256((size_t)s.cap_ops * 8) +
+                   align256((size_t)s.cap_ops * 4) + (size_t)s.cap_limbs * 8);
+    }
+    for (void *h : {(void *)s.h_keys, (void *)s.h_sel, (void *)s.h_off, (void *)s.h_status, (void *)s.h_msgs,
+                    (void *)s.h_out})
+      if (h) cudaFreeHost(h);
+    if (s.ev) cudaEventDestroy(s.ev);
+    if (s.stream) cudaStreamDestroy(s.stream);
+  }
+  slots.clear();
+  for (auto &kv : all) delete kv.second;
+  all.clear();
+  queue.clear();
+}
+
+// Pack `batch` into the slot's staging buffers and enqueue copies + the ragged batch.
+bool Server::launch(Slot &s, std::vector<Req *> &batch) {
+  uint32_t op = 0;
+  uint64_t limb = 0;
+  s.reqs = batch;
+  s.req_off.clear();
+  s.bytes = 0;
+  for (Req *r : s.reqs) {
+    const uint32_t step = r->L == 1 ? 1u : r->L;
+    limb = r->L == 1 ? limb : (limb + 3) / 4 * 4;
+    s.req_off.push_back(limb);
+    std::memcpy(s.h_msgs + limb, r->msgs, (size_t)r->count * r->L * 4);
+    for (uint32_t i = 0; i < r->count; ++i) {
+      s.h_keys[op] = r->key_id;
+      s.h_sel[op] = (uint8_t)r->exp_sel;
+      s.h_off[op] = limb + (uint64_t)i * step;
+      ++op;
+    }
+    limb += (uint64_t)r->count * r->L;
+    s.bytes += r->bytes;
+    r->state = 1;
+  }
+  cudaStream_t st = s.stream;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(s.d_keys, s.h_keys, (size_t)op * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(s.d_sel, s.h_sel, op, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(s.d_off, s.h_off, (size_t)op * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(s.d_msgs, s.h_msgs, limb * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+    fatal = cuda_error(e, "server H2D");
+    return false;
+  }
+  int rc;
+  {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    rc = ctx->run_batch(op, s.d_keys, s.d_sel, s.d_off, s.d_msgs, s.d_out, s.d_status, st);
+  }
+  if (rc) {
+    fatal = rc;
+    return false;
+  }
+  if ((e = cudaMemcpyAsync(s.h_out, s.d_out, limb * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(s.h_status, s.d_status, (size_t)op * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaEventRecord(s.ev, st)) != cudaSuccess) {
+    fatal = cuda_error(e, "server D2H");
+    return false;
+  }
+  s.busy = true;
+  batches++;
+  return true;
+}
+
+// Copy results of a completed slot back to the requests' buffers.
+void Server::finish(Slot &s) {
+  uint32_t op = 0;
+  const uint64_t t = now_ns();
+  for (size_t k = 0; k < s.reqs.size(); ++k) {
+    Req *r = s.reqs[k];
+    std::memcpy(r->out, s.h_out + s.req_off[k], (size_t)r->count * r->L * 4);
+    int32_t worst = 0;
+    for (uint32_t i = 0; i < r->count; ++i) {
+      const int32_t v = s.h_status[op + i];
+      if (r->status) r->status[i] = v;
+      if (v != 0 && worst == 0) worst = v;
+    }
+    op += r->count;
+    r->done = t;
+    r->state = 2;
+    lat_us.push_back((double)(t - r->arrive) / 1e3);
+    completed++;
+    ops_completed += r->count;
+    last_done = t;
+    pending--;
+  }
+  inflight_bytes -= s.bytes;
+  s.reqs.clear();
+  s.busy = false;
+}
+
+void Server::loop() {
+  cudaSetDevice(ctx->device);
+  std::unique_lock<std::mutex> lock(mu);
+  std::vector<Req *> batch;
+  while (true) {
+    // 1. retire finished batches
+    for (Slot &s : slots) {
+      if (s.busy && cudaEventQuery(s.ev) == cudaSuccess) finish(s);
+    }
+    if (pending == 0) done_cv.notify_all();
+    if (stop && queue.empty() && std::none_of(slots.begin(), slots.end(), [](const Slot &s) { return s.busy; }))
+      break;
+    // 2. form a batch for a free slot from requests that have arrived and fit
+    Slot *free_slot = nullptr;
+    for (Slot &s : slots)
+      if (!s.busy) {
+        free_slot = &s;
+        break;
+      }
+    const uint64_t t = now_ns();
+    bool launched = false;
+    if (free_slot && !queue.empty() && queue.front()->arrive <= t && !fatal) {
+      // wait (briefly) after the first arrival for more, unless the batch is already full
+      const uint64_t window = (uint64_t)cfg.batch_window_us * 1000ull;
+      const uint64_t first = queue.front()->arrive;
+      uint32_t ops = 0;
+      uint64_t limbs = 0;
+      bool full = false;
+      for (Req *r : queue) {
+        if (r->arrive > t) break;
+        const uint64_t l = (limbs + 3) / 4 * 4 + (uint64_t)r->count * r->L;
+        if (ops + r->count > free_slot->cap_ops || l > free_slot->cap_limbs) {
+          full = true;
+          break;
+        }
+        ops += r->count;
+        limbs = l;
+      }
+      if (full || t >= first + window || stop) {
+        batch.clear();
+        ops = 0;
+        limbs = 0;
+        while (!queue.empty()) {
+          Req *r = queue.front();
+          if (r->arrive > t) break;
+          const uint64_t l = (limbs + 3) / 4 * 4 + (uint64_t)r->count * r->L;
+          if (ops + r->count > free_slot->cap_ops || l > free_slot->cap_limbs) break;
+          ops += r->count;
+          limbs = l;
+          batch.push_back(r);
+          queue.pop_front();
+        }
+        if (!batch.empty()) {
+          uint64_t bytes = 0;
+          for (Req *r : batch) bytes += r->bytes;
+          inflight_bytes += bytes;
+          peak_bytes = std::max(peak_bytes, inflight_bytes);
+          lock.unlock();
+          const bool ok = launch(*free_slot, batch);
+          lock.lock();
+          if (!ok) {
+            for (Req *r : batch) {
+              r->state = fatal ? fatal : RSA_ERR_CUDA;
+              pending--;
+            }
+            inflight_bytes -= bytes;
+          }
+          launched = true;
+        }
+      }
+    }
+    if (!launched) {
+      // sleep until the next arrival, the end of the batching window, or a completion check
+      uint64_t wait_ns = 20000;  // poll in-flight events every 20 us
+      if (!queue.empty() && queue.front()->arrive > t) wait_ns = std::min<uint64_t>(wait_ns, queue.front()->arrive - t);
+      cv.wait_for(lock, std::chrono::nanoseconds(wait_ns));
+    }
+  }
+}
+
+}  // namespace rsagpu
+
+using namespace rsagpu;
+
+static Server *server_of(rsa_ctx *ctx) {
+  return ctx ? static_cast<Server *>(reinterpret_cast<Ctx *>(ctx)->server) : nullptr;
+}
+
+extern "C" {
+
+int rsa_server_start(rsa_ctx *ctx, const rsa_server_cfg *cfg) {
+  if (!ctx) return set_error(RSA_ERR_ARG, "ctx is null");
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (c->server) return set_error(RSA_ERR_ARG, "a server is already running on this context");
+  Server *s = new Server();
+  s->ctx = c;
+  if (cfg) s->cfg = *cfg;
+  if (s->cfg.max_inflight_batches <= 0) s->cfg.max_inflight_batches = 4;
+  if (s->cfg.batch_window_us <= 0) s->cfg.batch_window_us = 200;
+  if (s->cfg.max_batch_ops <= 0) s->cfg.max_batch_ops = 65536;
+  if (s->cfg.mem_budget_bytes == 0) s->cfg.mem_budget_bytes = (uint64_t)2 << 30;
+  cudaSetDevice(c->device);
+  int rc = s->init();
+  if (rc) {
+    s->release();
+    delete s;
+    return rc;
+  }
+  s->epoch = now_ns();
+  c->server = s;
+  s->thr = std::thread([s] { s->loop(); });
+  return RSA_OK;
+}
+
+int rsa_server_submit(rsa_ctx *ctx, const rsa_request *req, uint64_t *ticket) {
+  Server *s = server_of(ctx);
+  if (!s) return set_error(RSA_ERR_ARG, "no server running on this context");
+  if (!req || !ticket || (req->count > 0 && (!req->msgs || !req->out)))
+    return set_error(RSA_ERR_ARG, "null request field");
+  Ctx *c = s->ctx;
+  uint32_t L = 0;
+  {
+    std::lock_guard<std::mutex> lock(c->mu);
+    const KeySlot *k = nullptr;
+    int rc = c->check_key(req->key_id, req->exp_sel, &k);
+    if (rc) return rc;
+    L = k->L;
+  }
+  Req *r = new Req();
+  r->key_id = req->key_id;
+  r->exp_sel = req->exp_sel;
+  r->count = req->count;
+  r->L = L;
+  r->msgs = req->msgs;
+  r->out = req->out;
+  r->status = req->status;
+  r->bytes = (uint64_t)req->count * (8ull * L + 24ull);
+  std::lock_guard<std::mutex> lock(s->mu);
+  const Slot &s0 = s->slots[0];
+  if ((uint64_t)req->count * L + 4 > s0.cap_limbs || req->count > s0.cap_ops) {
+    delete r;
+    s->rejected++;
+    return set_error(RSA_ERR_NOMEM, "request exceeds the per-batch share of the memory budget");
+  }
+  r->arrive = req->arrive_ns ? s->epoch + req->arrive_ns : now_ns();
+  r->ticket = s->next_ticket++;
+  if (!s->first_arrive || r->arrive < s->first_arrive) s->first_arrive = r->arrive;
+  if (req->count == 0) {
+    r->state = 2;
+    r->done = r->arrive;
+  } else {
+    s->queue.push_back(r);
+    s->pending++;
+  }
+  s->all[r->ticket] = r;
+  s->submitted++;
+  *ticket = r->ticket;
+  s->cv.notify_one();
+  return RSA_OK;
+}
+
+int rsa_server_poll(rsa_ctx *ctx, uint64_t ticket, int32_t *done) {
+  Server *s = server_of(ctx);
+  if (!s || !done) return set_error(RSA_ERR_ARG, "no server or null argument");
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return set_error(RSA_ERR_ARG, "unknown ticket");
+  const int32_t st = it->second->state;
+  *done = st == 2 ? 1 : st < 0 ? st : 0;
+  if (st == 2 || st < 0) {
+    delete it->second;
+    s->all.erase(it);
+  }
+  return RSA_OK;
+}
+
+int rsa_server_drain(rsa_ctx *ctx, int32_t timeout_ms) {
+  Server *s = server_of(ctx);
+  if (!s) return set_error(RSA_ERR_ARG, "no server running on this context");
+  std::unique_lock<std::mutex> lock(s->mu);
+  s->cv.notify_one();
+  auto pred = [s] { return s->pending == 0; };
+  if (timeout_ms <= 0) {
+    s->done_cv.wait(lock, pred);
+  } else if (!s->done_cv.wait_for(lock, std::chrono::milliseconds(timeout_ms), pred)) {
+    return set_error(RSA_ERR_TIMEOUT, "requests still pending after the timeout");
+  }
+  return s->fatal ? s->fatal : RSA_OK;
+}
+
+int rsa_server_get_stats(rsa_ctx *ctx, rsa_server_stats *st, int32_t reset) {
+  Server *s = server_of(ctx);
+  if (!s || !st) return set_error(RSA_ERR_ARG, "no server or null argument");
+  std::lock_guard<std::mutex> lock(s->mu);
+  std::memset(st, 0, sizeof(*st));
+  st->submitted = s->submitted;
+  st->completed = s->completed;
+  st->rejected = s->rejected;
+  st->ops_completed = s->ops_completed;
+  st->batches = s->batches;
+  st->peak_bytes = s->peak_bytes;
+  if (!s->lat_us.empty()) {
+    std::vector<double> v = s->lat_us;
+    std::sort(v.begin(), v.end());
+    auto pct = [&](double p) { return v[std::min(v.size() - 1, (size_t)(p * (v.size() - 1) + 0.5))]; };
+    st->p50_us = pct(0.50);
+    st->p99_us = pct(0.99);
+    st->max_us = v.back();
+    double sum = 0;
+    for (double x : v) sum += x;
+    st->mean_us = sum / v.size();
+  }
+  if (s->last_done > s->first_arrive) st->span_s = (double)(s->last_done - s->first_arrive) / 1e9;
+  if (reset) {
+    s->lat_us.clear();
+    s->submitted = s->completed = s->rejected = s->ops_completed = s->batches = 0;
+    s->peak_bytes = s->inflight_bytes;
+    s->first_arrive = s->last_done = 0;
+  }
+  return RSA_OK;
+}
+
+int rsa_server_stop(rsa_ctx *ctx) {
+  Server *s = server_of(ctx);
+  if (!s) return set_error(RSA_ERR_ARG, "no server running on this context");
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_one();
+  if (s->thr.joinable()) s->thr.join();
+  s->release();
+  reinterpret_cast<Ctx *>(ctx)->server = nullptr;
+  delete s;
+  return RSA_OK;
+}
+
+}  // extern "C"

@@ -103,9 +103,11 @@ def test_crt_parity(torch_cuda, ctx, keys, kids, bits, count):
         assert np.array_equal(got[:16], plain)
 
 
-@pytest.mark.parametrize("bits", [1024, 2048])
+@pytest.mark.parametrize("bits", [1024, 2048, 3072, 4096])
 @pytest.mark.parametrize("kind", [PUB, PLAIN])
 def test_full_modulus_parity(torch_cuda, ctx, keys, kids, bits, kind):
+    if kind == PLAIN and bits > 2048:
+        pytest.skip("plain private exponent is offered up to 2048 bits")
     key = keys[bits]
     rows = workloads.messages_below(key.n, 45, 6, ("full", bits, kind))
     got, st = run(torch_cuda, ctx, kids[bits], kind, rows)
@@ -126,7 +128,7 @@ def test_edge_messages(torch_cuda, ctx, keys, kids, bits):
     key = keys[bits]
     good, bad = _edge_rows(key)
     rows = np.concatenate([good, bad])
-    kinds = [CRT] + ([PUB, PLAIN] if bits <= 2048 else [])
+    kinds = [CRT, PUB] + ([PLAIN] if bits <= 2048 else [])
     for kind in kinds:
         got, st = run(torch_cuda, ctx, kids[bits], kind, rows)
         ng = good.shape[0]
