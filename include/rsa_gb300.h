@@ -201,6 +201,13 @@ int rsa_server_start(rsa_ctx *ctx, const rsa_server_cfg *cfg);
 /* Queue a request; *ticket identifies it.  RSA_ERR_NOMEM when the request alone
  * exceeds the budget, RSA_ERR_KEY / RSA_ERR_ARG for a bad key or kind. */
 int rsa_server_submit(rsa_ctx *ctx, const rsa_request *req, uint64_t *ticket);
+/* Queue n requests at once (in arrival order); tickets (n entries) may be NULL.
+ * Stops at the first refused request and returns its error; *accepted (may be
+ * NULL) receives how many were queued. */
+int rsa_server_submit_many(rsa_ctx *ctx, const rsa_request *reqs, uint32_t n, uint64_t *tickets,
+                           uint32_t *accepted);
+/* The loop's arrival clock: nanoseconds since rsa_server_start. */
+int rsa_server_clock(rsa_ctx *ctx, uint64_t *ns_since_start);
 /* *done = 1 when the request completed, 0 while pending, a negative status on failure. */
 int rsa_server_poll(rsa_ctx *ctx, uint64_t ticket, int32_t *done);
 /* Wait until every submitted request completed (timeout_ms <= 0: no limit).
@@ -225,7 +232,8 @@ typedef struct rsa_tuning {
     int32_t ctas_per_sm;   /* resident CTAs per SM the grid is sized for */
     int32_t variant;       /* squarings of private exponents: 1 = through the general
                               CIOS multiply, 2 = separated square + reduction (fewer
-                              word products, more registers); 0 = automatic */
+                              word products, but a larger instruction footprint; slower
+                              on GB300); 0 = automatic (currently 1) */
 } rsa_tuning;
 
 /* Set (or, with NULL, reset to automatic) the launch parameters used for keys of
@@ -235,6 +243,18 @@ typedef struct rsa_tuning {
 int rsa_set_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, const rsa_tuning *t);
 /* Read the parameters currently in force for (nbits, exp_sel). */
 int rsa_get_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, rsa_tuning *t);
+
+/* Autotuner: time every launch shape (window 3..6 for private kinds, warps
+ * per CTA 2/4/8, CTAs per SM 1/2/max, both squaring variants) for key_id's
+ * size and kind exp_sel on a synthetic batch of `count` operations (the work
+ * of these kernels does not depend on the message values), install the
+ * fastest with rsa_set_tuning() and append it to the cache file `cache_path`
+ * (NULL: $RSA_TUNE_CACHE, else no file).  A cached entry for the same GPU name,
+ * SM count, size, kind and batch-size bucket is used without timing.
+ * *best receives the chosen parameters, *best_ms its time per batch.
+ * Synchronous; allocates scratch from the context's budget. */
+int rsa_autotune(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint64_t count, const char *cache_path,
+                 rsa_tuning *best, double *best_ms);
 
 /* Counters since context creation. */
 typedef struct rsa_stats {

@@ -25,8 +25,8 @@ __all__ = [
     "rsa_ctx_create", "rsa_ctx_destroy", "rsa_keyload", "rsa_key_record", "rsa_keyunload", "rsa_key_info",
     "rsa_modexp_key", "rsa_modexp_batch", "rsa_modexp_key_host", "rsa_modexp_batch_host",
     "rsa_sync", "rsa_last_error", "rsa_set_tuning", "rsa_get_tuning", "rsa_get_stats",
-    "rsa_products_per_op", "rsa_imad_probe", "rsa_crt_decrypt_noalloc",
-    "rsa_server_start", "rsa_server_submit", "rsa_server_poll", "rsa_server_drain", "rsa_server_get_stats",
+    "rsa_products_per_op", "rsa_imad_probe", "rsa_crt_decrypt_noalloc", "rsa_autotune",
+    "rsa_server_start", "rsa_server_submit", "rsa_server_submit_many", "rsa_server_clock", "rsa_server_poll", "rsa_server_drain", "rsa_server_get_stats",
     "rsa_server_stop",
 ]
 
@@ -184,6 +184,16 @@ def rsa_get_tuning(ctx: int, nbits: int, exp_sel: int) -> dict:
             "variant": t.variant}
 
 
+def rsa_autotune(ctx: int, key_id: int, exp_sel: int, count: int, cache_path: str | None = None) -> dict:
+    """Time the launch shapes for this key's size and kind; installs and returns the fastest."""
+    t = rsa_tuning()
+    ms = ctypes.c_double()
+    check(_lib.lib().rsa_autotune(ctx, key_id, exp_sel, count, cache_path.encode() if cache_path else None,
+                                  ctypes.byref(t), ctypes.byref(ms)))
+    return {"window": t.window, "warps_per_cta": t.warps_per_cta, "ctas_per_sm": t.ctas_per_sm,
+            "variant": t.variant, "ms": ms.value}
+
+
 def rsa_get_stats(ctx: int) -> dict:
     s = rsa_stats()
     check(_lib.lib().rsa_get_stats(ctx, ctypes.byref(s)))
@@ -215,6 +225,24 @@ def rsa_server_submit(ctx: int, key_id: int, exp_sel: int, msgs: np.ndarray, out
     req = _lib.rsa_request(key_id, exp_sel, count, 0, _ptr(msgs), _ptr(out), _ptr(status), arrive_ns)
     t = ctypes.c_uint64()
     check(_lib.lib().rsa_server_submit(ctx, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+REQUEST_DTYPE = np.dtype([("key_id", "<i4"), ("exp_sel", "<i4"), ("count", "<u4"), ("reserved", "<u4"),
+                          ("msgs", "<u8"), ("out", "<u8"), ("status", "<u8"), ("arrive_ns", "<u8")])
+
+
+def rsa_server_submit_many(ctx: int, reqs: np.ndarray) -> int:
+    """Queue a structured array of REQUEST_DTYPE records; returns how many were accepted."""
+    reqs = np.ascontiguousarray(reqs, dtype=REQUEST_DTYPE)
+    acc = ctypes.c_uint32()
+    check(_lib.lib().rsa_server_submit_many(ctx, reqs.ctypes.data, reqs.size, None, ctypes.byref(acc)))
+    return acc.value
+
+
+def rsa_server_clock(ctx: int) -> int:
+    t = ctypes.c_uint64()
+    check(_lib.lib().rsa_server_clock(ctx, ctypes.byref(t)))
     return t.value
 
 

@@ -85,6 +85,8 @@ SIGNATURES = [
     ("rsa_crt_decrypt_noalloc", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, _P, _P, _P]),
     ("rsa_server_start", ctypes.c_int, [_P, ctypes.POINTER(rsa_server_cfg)]),
     ("rsa_server_submit", ctypes.c_int, [_P, ctypes.POINTER(rsa_request), ctypes.POINTER(ctypes.c_uint64)]),
+    ("rsa_server_submit_many", ctypes.c_int, [_P, _P, ctypes.c_uint32, _P, ctypes.POINTER(ctypes.c_uint32)]),
+    ("rsa_server_clock", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
     ("rsa_server_poll", ctypes.c_int, [_P, ctypes.c_uint64, _I32P]),
     ("rsa_server_drain", ctypes.c_int, [_P, ctypes.c_int32]),
     ("rsa_server_get_stats", ctypes.c_int, [_P, ctypes.POINTER(rsa_server_stats), ctypes.c_int32]),
@@ -94,6 +96,8 @@ SIGNATURES = [
     ("rsa_set_tuning", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_int32, ctypes.POINTER(rsa_tuning)]),
     ("rsa_get_tuning", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_int32, ctypes.POINTER(rsa_tuning)]),
     ("rsa_get_stats", ctypes.c_int, [_P, ctypes.POINTER(rsa_stats)]),
+    ("rsa_autotune", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_char_p,
+                                    ctypes.POINTER(rsa_tuning), ctypes.POINTER(ctypes.c_double)]),
     ("rsa_products_per_op", ctypes.c_double, [ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint32,
                                               ctypes.c_uint32, ctypes.c_int32]),
     ("rsa_imad_probe", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),

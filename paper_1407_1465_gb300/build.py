@@ -51,7 +51,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int = 0) -> str:
     cu, cpp = _sources()
     headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
         glob.glob(os.path.join(INCLUDE, "*.h"))
-    stamp = _stamp(cu + cpp + headers + [os.path.abspath(__file__)])
+    stamp = _stamp(cu + cpp + headers + [os.path.abspath(__file__)]) + os.environ.get("RSAGPU_DEFINES", "")
     stamp_path = os.path.join(OUT_DIR, "stamp.txt")
     if not force and os.path.exists(LIB_PATH) and os.path.exists(stamp_path):
         with open(stamp_path) as f:
@@ -60,6 +60,9 @@ def build(force: bool = False, verbose: bool = False, jobs: int = 0) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = _nvcc()
     common = ["-std=c++17", "-O3", "-I", INCLUDE, "-I", CSRC]
+    # optional extra definitions for tuning builds, e.g. RSAGPU_DEFINES="RSAGPU_CIOS_BLOCK=4"
+    for d in os.environ.get("RSAGPU_DEFINES", "").split():
+        common += ["-D" + d]
     cmds = []
     objs = []
     for src in cu:

@@ -29,7 +29,7 @@ __device__ __forceinline__ void run_crt(const uint32_t *ks, uint4 *work, uint4 *
   constexpr int kStage = (H / 4) * 32;
   uint4 *xb = work + lane;
   uint4 *stage_lane = work + kStage + warp * kStage + lane;
-  crt_tile<H, W, kU, (H <= 32)>(ks, warp == 1, lane, stage_lane, xb, table_warp + lane, 1, io);
+  crt_tile<H, W, kU, false>(ks, warp == 1, lane, stage_lane, xb, table_warp + lane, 1, io);
 }
 
 template <int L>
@@ -49,7 +49,7 @@ template <int L>
 __device__ __forceinline__ void run_plain(const uint32_t *ks, uint4 *work, uint4 *table_warp, int warp, int lane,
                                           const TileIO &io) {
   constexpr int kStage = (L / 4) * 32;
-  plain_tile<L, kBatchWindowPlain, kU, (L <= 32)>(ks, lane, work + warp * kStage + lane, table_warp + lane, io);
+  plain_tile<L, kBatchWindowPlain, kU, false>(ks, lane, work + warp * kStage + lane, table_warp + lane, io);
 }
 
 template <int G>

@@ -17,15 +17,25 @@ namespace rsagpu {
 namespace {
 constexpr int kH = RSAGPU_UNIT;
 constexpr int kL = 2 * kH;
-constexpr int kU = 8;  // outer CIOS block: 8 limbs of B per runtime iteration
+// outer CIOS block: limbs of B per runtime iteration (fully unrolled inside).
+// Measured on GB300: 8 is best up to 32-limb halves, 4 for 48/64 limbs (smaller
+// loop body, fewer registers).
+#ifdef RSAGPU_CIOS_BLOCK
+constexpr int kU = RSAGPU_CIOS_BLOCK;
+#else
+constexpr int kU = (RSAGPU_UNIT <= 32) ? 8 : 4;
+#endif
 
 // separated squaring where its 2L-limb product fits in registers
 constexpr bool kSqrOk = (kH <= 32);
 constexpr bool kSqrOkFull = (kL <= 32);
 
+// variant 0 (automatic) is the CIOS squaring: the separated squaring issues fewer
+// products but its unrolled body overflows the instruction cache (ncu: stalls on
+// "no instruction" dominate), so it is slower on GB300.
 template <int W>
 const void *crt_fn(int variant) {
-  if (variant == 2 || (variant == 0 && kSqrOk)) {
+  if (variant == 2) {
     if constexpr (kSqrOk) return reinterpret_cast<const void *>(&crt_kernel<kH, W, kU, true>);
     else return nullptr;
   }
@@ -35,7 +45,7 @@ const void *crt_fn(int variant) {
 template <int W>
 const void *plain_fn(int variant) {
   if constexpr (kL <= 64) {
-    if (variant == 2 || (variant == 0 && kSqrOkFull)) {
+    if (variant == 2) {
       if constexpr (kSqrOkFull) return reinterpret_cast<const void *>(&plain_kernel<kL, W, kU, true>);
       else return nullptr;
     }

@@ -121,19 +121,30 @@ __device__ __forceinline__ void fixed_window_exp(uint32_t (&A)[L], const uint32_
   table_select<L, W>(stage_lane, table_lane, exp_digit<W>(E, (uint32_t)(nwin - 1)));
   from_stage<L>(A, stage_lane);
   // remaining windows: W squarings, then one multiplication by T[digit]
+  if constexpr (SQR) {
 #pragma unroll 1
-  for (int k = nwin - 2; k >= 0; --k) {
+    for (int k = nwin - 2; k >= 0; --k) {
 #pragma unroll 1
-    for (int s = 0; s < W; ++s) {
-      if constexpr (SQR) {
-        mont_sqr<L>(A, N, np);
-      } else {
-        to_stage<L>(stage_lane, A);
-        mont_mul<L, U>(A, st, N, np);
-      }
+      for (int s = 0; s < W; ++s) mont_sqr<L>(A, N, np);
+      table_select<L, W>(stage_lane, table_lane, exp_digit<W>(E, (uint32_t)k));
+      mont_mul<L, U>(A, st, N, np);
     }
-    table_select<L, W>(stage_lane, table_lane, exp_digit<W>(E, (uint32_t)k));
-    mont_mul<L, U>(A, st, N, np);
+  } else {
+    // one call site of mont_mul for every step keeps the hot code small
+    const int nsteps = (nwin - 1) * (W + 1);
+    int k = nwin - 2, s = 0;
+#pragma unroll 1
+    for (int step = 0; step < nsteps; ++step) {
+      if (s < W) {
+        to_stage<L>(stage_lane, A);
+        ++s;
+      } else {
+        table_select<L, W>(stage_lane, table_lane, exp_digit<W>(E, (uint32_t)k));
+        s = 0;
+        --k;
+      }
+      mont_mul<L, U>(A, st, N, np);
+    }
   }
 }
 

@@ -171,6 +171,20 @@ __device__ __forceinline__ void final_sub(uint32_t (&A)[L], const uint32_t (&t)[
   for (int j = 0; j < L; ++j) A[j] = (t[j] & keep_t) | (u[j] & ~keep_t);
 }
 
+template <int L>
+__device__ __forceinline__ void reduce_step_smem(uint32_t (&t)[L + 2], const uint4 *N4, uint32_t np);
+
+template <class NS> struct IsNSmem { static constexpr bool value = false; };
+template <int L> struct IsNSmem<NSmem<L>> { static constexpr bool value = true; };
+
+// One reduction step with the modulus from registers, or from shared memory
+// with 128-bit loads issued next to their use.
+template <int L, class NS>
+__device__ __forceinline__ void reduce_any(uint32_t (&t)[L + 2], const NS &N, uint32_t np) {
+  if constexpr (IsNSmem<NS>::value) reduce_step_smem<L>(t, reinterpret_cast<const uint4 *>(N.s), np);
+  else reduce_step<L>(t, N, np);
+}
+
 // A = A * B * R^-1 mod N.  The outer loop runs over B in blocks of U limbs
 // (U a multiple of 4 dividing L): fully unrolled inside a block, a runtime
 // loop across blocks to bound the code size.
@@ -186,13 +200,13 @@ __device__ __forceinline__ void mont_mul(uint32_t (&A)[L], const BS &B, const NS
     for (int u = 0; u < U; u += 4) {
       const uint4 b = B.get4((i0 + u) >> 2);
       mul_acc<L>(t, A, b.x);
-      reduce_step<L>(t, N, np);
+      reduce_any<L>(t, N, np);
       mul_acc<L>(t, A, b.y);
-      reduce_step<L>(t, N, np);
+      reduce_any<L>(t, N, np);
       mul_acc<L>(t, A, b.z);
-      reduce_step<L>(t, N, np);
+      reduce_any<L>(t, N, np);
       mul_acc<L>(t, A, b.w);
-      reduce_step<L>(t, N, np);
+      reduce_any<L>(t, N, np);
     }
   }
   final_sub<L>(A, t, N);

@@ -109,7 +109,8 @@ int Server::init() {
     const size_t meta = align256((size_t)s.cap_ops * 4) + align256(s.cap_ops) + align256((size_t)s.cap_ops * 8) +
                         align256((size_t)s.cap_ops * 4);
     if (per_slot <= meta + 4096) return set_error(RSA_ERR_ARG, "memory budget too small for the slot count");
-    s.cap_limbs = (uint32_t)std::min<size_t>((per_slot - meta) / 8, 0xffffffffu);  // messages + results
+    // messages + results; a multiple of 4 limbs keeps the result area 16-byte aligned
+    s.cap_limbs = (uint32_t)std::min<size_t>((per_slot - meta) / 8, 0xfffffff0u) & ~3u;
     cudaError_t e;
     if ((e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming)) != cudaSuccess)
@@ -399,6 +400,27 @@ int rsa_server_submit(rsa_ctx *ctx, const rsa_request *req, uint64_t *ticket) {
   s->submitted++;
   *ticket = r->ticket;
   s->cv.notify_one();
+  return RSA_OK;
+}
+
+int rsa_server_submit_many(rsa_ctx *ctx, const rsa_request *reqs, uint32_t n, uint64_t *tickets,
+                           uint32_t *accepted) {
+  if (accepted) *accepted = 0;
+  if (!reqs && n) return set_error(RSA_ERR_ARG, "null request array");
+  for (uint32_t i = 0; i < n; ++i) {
+    uint64_t t = 0;
+    const int rc = rsa_server_submit(ctx, &reqs[i], &t);
+    if (rc) return rc;
+    if (tickets) tickets[i] = t;
+    if (accepted) *accepted = i + 1;
+  }
+  return RSA_OK;
+}
+
+int rsa_server_clock(rsa_ctx *ctx, uint64_t *ns) {
+  Server *s = server_of(ctx);
+  if (!s || !ns) return set_error(RSA_ERR_ARG, "no server or null argument");
+  *ns = now_ns() - s->epoch;
   return RSA_OK;
 }
 

@@ -1,0 +1,171 @@
+// tune.cu -- rsa_autotune: times launch shapes of the uniform kernels and
+// keeps the fastest, with a small text cache keyed by GPU and problem class.
+//
+// Cache lines: "<gpu name>|<sm count>|<nbits>|<kind>|<log2 count bucket> window warps ctas variant ms"
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "runtime_internal.h"
+
+namespace rsagpu {
+namespace {
+
+std::string cache_key(int device, int sms, uint32_t nbits, int kind, uint64_t count) {
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, device);
+  std::string name(prop.name);
+  for (char &c : name)
+    if (c == '|' || c == ' ') c = '_';
+  const int bucket = count ? (int)std::floor(std::log2((double)count)) : 0;
+  std::ostringstream os;
+  os << name << "|" << sms << "|" << nbits << "|" << kind << "|" << bucket;
+  return os.str();
+}
+
+bool cache_lookup(const std::string &path, const std::string &key, Tune *t, double *ms) {
+  std::ifstream f(path);
+  if (!f) return false;
+  std::string line;
+  bool found = false;
+  while (std::getline(f, line)) {
+    std::istringstream is(line);
+    std::string k;
+    Tune x{};
+    double m = 0;
+    if (!(is >> k >> x.window >> x.warps_per_cta >> x.ctas_per_sm >> x.variant >> m)) continue;
+    if (k == key) {
+      *t = x;
+      *ms = m;
+      found = true;  // last entry wins
+    }
+  }
+  return found;
+}
+
+}  // namespace
+}  // namespace rsagpu
+
+using namespace rsagpu;
+
+extern "C" int rsa_autotune(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint64_t count, const char *cache_path,
+                            rsa_tuning *best, double *best_ms) {
+  if (!ctx) return set_error(RSA_ERR_ARG, "ctx is null");
+  if (count == 0 || count > (1u << 24)) return set_error(RSA_ERR_ARG, "count must be in 1..2^24");
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  std::unique_lock<std::mutex> lock(c->mu);
+  const KeySlot *k = nullptr;
+  int rc = c->check_key(key_id, exp_sel, &k);
+  if (rc) return rc;
+  if (k->L == 1) return set_error(RSA_ERR_UNSUPPORTED, "single-limb keys have no launch parameters to tune");
+  const uint32_t nbits = k->nbits, L = k->L;
+  const std::string path = cache_path ? cache_path : (std::getenv("RSA_TUNE_CACHE") ? std::getenv("RSA_TUNE_CACHE") : "");
+  const std::string key = cache_key(c->device, c->sm_count, nbits, exp_sel, count);
+  Tune chosen{};
+  double chosen_ms = 0;
+  if (!path.empty() && cache_lookup(path, key, &chosen, &chosen_ms)) {
+    c->tuning[{nbits, exp_sel}] = chosen;
+  } else {
+    cudaSetDevice(c->device);
+    const size_t bytes = (size_t)count * L * 4;
+    DevBuf in, out;
+    if ((rc = c->ensure(in, bytes)) || (rc = c->ensure(out, bytes))) {
+      if (in.ptr) { cudaFree(in.ptr); c->release(in.bytes); }
+      return rc;
+    }
+    // messages 0x01010101...: below any modulus of full bit length
+    cudaMemset(in.ptr, 0x01, bytes);
+    cudaStream_t s = nullptr;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const Tune saved = c->tune_for(nbits, exp_sel);
+    const bool priv = exp_sel != RSA_EXP_PUBLIC;
+    std::vector<int> windows = priv ? std::vector<int>{3, 4, 5, 6} : std::vector<int>{0};
+    std::vector<int> warps = exp_sel == RSA_EXP_PRIVATE_CRT ? std::vector<int>{2, 4, 8} : std::vector<int>{1, 2, 4, 8};
+    std::vector<int> variants = priv ? std::vector<int>{1, 2} : std::vector<int>{0};
+    double best_t = 1e30;
+    int err = RSA_OK;
+    for (int v : variants)
+      for (int w : windows)
+        for (int wp : warps)
+          for (int cps : {0, 1, 2}) {
+            c->tuning[{nbits, exp_sel}] = Tune{w, wp, cps, v};
+            // warm-up, then the median of three timed runs
+            if (c->run_key(*k, exp_sel, count, static_cast<uint32_t *>(in.ptr), static_cast<uint32_t *>(out.ptr),
+                           nullptr, s) != RSA_OK)
+              continue;  // shape not available (kernel not instantiated or does not fit)
+            float t3[3];
+            for (int r = 0; r < 3; ++r) {
+              cudaEventRecord(a, s);
+              c->run_key(*k, exp_sel, count, static_cast<uint32_t *>(in.ptr), static_cast<uint32_t *>(out.ptr),
+                         nullptr, s);
+              cudaEventRecord(b, s);
+              cudaError_t e = cudaEventSynchronize(b);
+              if (e != cudaSuccess) {
+                err = cuda_error(e, "autotune run");
+                break;
+              }
+              cudaEventElapsedTime(&t3[r], a, b);
+            }
+            if (err) break;
+            std::sort(t3, t3 + 3);
+            if (t3[1] < best_t) {
+              best_t = t3[1];
+              chosen = Tune{w, wp, cps, v};
+            }
+          }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaStreamSynchronize(s);
+    {
+      auto it = c->workspaces.find(s);
+      if (it != c->workspaces.end()) {
+        Workspace &w = it->second;
+        for (DevBuf *d : {&w.tables, &w.io_in, &w.io_out, &w.io_status, &w.aux0, &w.aux1, &w.aux2, &w.aux3})
+          if (d->ptr) {
+            cudaFree(d->ptr);
+            c->release(d->bytes);
+          }
+        c->workspaces.erase(it);
+      }
+    }
+    cudaStreamDestroy(s);
+    cudaFree(in.ptr);
+    c->release(in.bytes);
+    cudaFree(out.ptr);
+    c->release(out.bytes);
+    if (err) {
+      c->tuning[{nbits, exp_sel}] = saved;
+      return err;
+    }
+    if (best_t >= 1e29) {
+      c->tuning[{nbits, exp_sel}] = saved;
+      return set_error(RSA_ERR_UNSUPPORTED, "no launch shape ran for this key size and kind");
+    }
+    chosen_ms = best_t;
+    c->tuning[{nbits, exp_sel}] = chosen;
+    if (!path.empty()) {
+      std::ofstream f(path, std::ios::app);
+      f << key << " " << chosen.window << " " << chosen.warps_per_cta << " " << chosen.ctas_per_sm << " "
+        << chosen.variant << " " << chosen_ms << "\n";
+    }
+  }
+  if (best) {
+    best->window = chosen.window;
+    best->warps_per_cta = chosen.warps_per_cta;
+    best->ctas_per_sm = chosen.ctas_per_sm;
+    best->variant = chosen.variant;
+  }
+  if (best_ms) *best_ms = chosen_ms;
+  return RSA_OK;
+}

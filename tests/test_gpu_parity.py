@@ -209,3 +209,18 @@ def test_full_rsa4096_workload(torch_cuda, ctx, keys, kids):
     assert np.array_equal(dec[idx], expect(key, CRT, rows[idx]))
     back = oracle.modexp_batch(dec, key.e, key.n)            # every row, through the oracle
     assert np.array_equal(back, rows)
+
+
+def test_autotune_installs_a_working_shape(torch_cuda, ctx, keys, kids, tmp_path):
+    from paper_1407_1465_gb300 import rsa_autotune
+    key = keys[2048]
+    cache = str(tmp_path / "tune.txt")
+    best = rsa_autotune(ctx.handle, kids[2048], CRT, 4096, cache)
+    assert best["ms"] > 0 and 3 <= best["window"] <= 6 and best["warps_per_cta"] in (2, 4, 8)
+    assert ctx.get_tuning(2048, CRT)["window"] == best["window"]
+    again = rsa_autotune(ctx.handle, kids[2048], CRT, 4096, cache)     # served from the cache file
+    assert again == best
+    rows = workloads.messages_below(key.n, 100, 12, "tuned")
+    got, st = run(torch_cuda, ctx, kids[2048], CRT, rows)
+    assert (st == 0).all() and np.array_equal(got, expect(key, CRT, rows))
+    ctx.set_tuning(2048, CRT, reset=True)
