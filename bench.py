@@ -251,6 +251,17 @@ def run_serving(args):
     return 0
 
 
+def aggregate_ranks(ms_per_step: float, units_per_rank: int, world_size: int, dist=None, device=None):
+    """Max-over-ranks step time and the whole-job rate (weak scaling: every rank
+    processes its own batch, no data exchange).  Returns (ms, units per second)."""
+    if world_size > 1:
+        import torch
+        t = torch.tensor([ms_per_step], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_per_step = float(t.item())
+    return ms_per_step, world_size * units_per_rank / (ms_per_step / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -389,12 +400,7 @@ def main():
     clk = clocks.stop()
     launches = ctx.stats()["kernel_launches"] - launches0
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = sum(step_ms) / len(step_ms)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * count / (ms / 1e3)
+    ms, value = aggregate_ranks(sum(step_ms) / len(step_ms), count, ws, dist, dev)
 
     # e2e: the host-buffer entry point, pinned host memory, copies inside the timed region
     e2e = None

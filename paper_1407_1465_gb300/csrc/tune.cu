@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <fstream>
+#include <iomanip>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -156,6 +157,7 @@ extern "C" int rsa_autotune(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint6
     c->tuning[{nbits, exp_sel}] = chosen;
     if (!path.empty()) {
       std::ofstream f(path, std::ios::app);
+      f.precision(17);
       f << key << " " << chosen.window << " " << chosen.warps_per_cta << " " << chosen.ctas_per_sm << " "
         << chosen.variant << " " << chosen_ms << "\n";
     }

@@ -219,7 +219,8 @@ def test_autotune_installs_a_working_shape(torch_cuda, ctx, keys, kids, tmp_path
     assert best["ms"] > 0 and 3 <= best["window"] <= 6 and best["warps_per_cta"] in (2, 4, 8)
     assert ctx.get_tuning(2048, CRT)["window"] == best["window"]
     again = rsa_autotune(ctx.handle, kids[2048], CRT, 4096, cache)     # served from the cache file
-    assert again == best
+    assert again["ms"] == pytest.approx(best["ms"], rel=1e-9)
+    assert {k: again[k] for k in again if k != "ms"} == {k: best[k] for k in best if k != "ms"}
     rows = workloads.messages_below(key.n, 100, 12, "tuned")
     got, st = run(torch_cuda, ctx, kids[2048], CRT, rows)
     assert (st == 0).all() and np.array_equal(got, expect(key, CRT, rows))
