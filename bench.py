@@ -342,6 +342,7 @@ def main():
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--variant", type=int, default=0, help="squaring variant: 1 CIOS, 2 separated, 0 auto")
+    ap.add_argument("--tpo", type=int, default=0, help="lanes per operation: 1, 2, 4 (0 auto)")
     ap.add_argument("--count", type=int, default=0, help="override the message count (small profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -377,9 +378,9 @@ def main():
     count, L = rows.shape
     ctx = RsaContext(local, mem_budget_bytes=16 << 30)
     kid = ctx.keyload(spec["bits"], key.n, key.e, key.d, key.p, key.q)
-    if args.window or args.warps or args.ctas_per_sm or args.variant:
+    if args.window or args.warps or args.ctas_per_sm or args.variant or args.tpo:
         ctx.set_tuning(spec["bits"], RSA_EXP_PRIVATE_CRT, window=args.window, warps_per_cta=args.warps,
-                       ctas_per_sm=args.ctas_per_sm, variant=args.variant)
+                       ctas_per_sm=args.ctas_per_sm, variant=args.variant, threads_per_op=args.tpo)
     tune = ctx.get_tuning(spec["bits"], RSA_EXP_PRIVATE_CRT)
     msgs = torch.from_numpy(rows.view(np.int32)).to(dev)
     out = torch.empty_like(msgs)
@@ -454,7 +455,8 @@ def main():
     peak = derived_peak_tprod(SM_COUNT_GB300, 2070.0)
     prof = PROFILED_TRAFFIC.get(args.workload)
     traffic = None
-    if prof and prof["window"] == tune["window"] and tune["variant"] in (0, 1) and prof["stamp"] == kernel_stamp():
+    if (prof and prof["window"] == tune["window"] and tune["variant"] in (0, 1) and tune["threads_per_op"] == 1
+            and prof["stamp"] == kernel_stamp()):
         traffic = prof["dram_bytes_per_op"] * count
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tprod/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_unit": "DRAM bytes per launch",
@@ -474,7 +476,8 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic", "gpu_launches": int(launches),
         "config": {"workload": spec["desc"], "window": tune["window"], "warps_per_cta": tune["warps_per_cta"],
-                   "ctas_per_sm": tune["ctas_per_sm"], "variant": tune["variant"], "l2": "flushed between timed steps (256 MiB write)",
+                   "ctas_per_sm": tune["ctas_per_sm"], "variant": tune["variant"],
+                   "threads_per_op": tune["threads_per_op"], "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "dp%d (independent batches per GPU)" % ws},
         "wall_s": wall, "clocks": clk, "roofline": roofline, "e2e": e2e,
     }

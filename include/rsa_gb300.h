@@ -234,6 +234,8 @@ typedef struct rsa_tuning {
                               CIOS multiply, 2 = separated square + reduction (fewer
                               word products, but a larger instruction footprint; slower
                               on GB300); 0 = automatic (currently 1) */
+    int32_t threads_per_op; /* lanes cooperating on one operation: 1, 2 or 4 (numbers
+                              sliced over the lanes, warp-shuffle carries); 0 = automatic */
 } rsa_tuning;
 
 /* Set (or, with NULL, reset to automatic) the launch parameters used for keys of

@@ -169,11 +169,11 @@ def rsa_last_error() -> str:
 
 
 def rsa_set_tuning(ctx: int, nbits: int, exp_sel: int, window: int = 0, warps_per_cta: int = 0,
-                   ctas_per_sm: int = 0, variant: int = 0, reset: bool = False) -> None:
+                   ctas_per_sm: int = 0, variant: int = 0, threads_per_op: int = 0, reset: bool = False) -> None:
     if reset:
         check(_lib.lib().rsa_set_tuning(ctx, nbits, exp_sel, None))
         return
-    t = rsa_tuning(window, warps_per_cta, ctas_per_sm, variant)
+    t = rsa_tuning(window, warps_per_cta, ctas_per_sm, variant, threads_per_op)
     check(_lib.lib().rsa_set_tuning(ctx, nbits, exp_sel, ctypes.byref(t)))
 
 
@@ -191,7 +191,7 @@ def rsa_autotune(ctx: int, key_id: int, exp_sel: int, count: int, cache_path: st
     check(_lib.lib().rsa_autotune(ctx, key_id, exp_sel, count, cache_path.encode() if cache_path else None,
                                   ctypes.byref(t), ctypes.byref(ms)))
     return {"window": t.window, "warps_per_cta": t.warps_per_cta, "ctas_per_sm": t.ctas_per_sm,
-            "variant": t.variant, "ms": ms.value}
+            "variant": t.variant, "threads_per_op": t.threads_per_op, "ms": ms.value}
 
 
 def rsa_get_stats(ctx: int) -> dict:

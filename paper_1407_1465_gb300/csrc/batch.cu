@@ -163,8 +163,8 @@ double class_cost(int32_t cls) {
     case CLS_CRT64: return 2.0 * 2500 * mm(64);
     case CLS_PUB32: return 19 * mm(32);
     case CLS_PUB64: return 19 * mm(64);
-    case CLS_PUB96: return 19 * mm(96) * 2.0;   // shared-memory operands run slower
-    case CLS_PUB128: return 19 * mm(128) * 2.0;
+    case CLS_PUB96: return 19 * mm(96);
+    case CLS_PUB128: return 19 * mm(128);
     case CLS_PLAIN32: return 1300 * mm(32);
     case CLS_PLAIN64: return 2600 * mm(64);
     default: return 0.0;
@@ -254,7 +254,7 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
     st->keydir_epoch = key_epoch;
   }
   const uint32_t nb = std::max<uint32_t>(nkeys, 1) * 3;
-  const uint32_t max_tiles = (uint32_t)(count / 32 + nb + 1);
+  const uint32_t max_tiles = (uint32_t)(count / 16 + nb + 1);   // smallest tile: 16 operations
   int rc;
   if ((rc = ensure(w.aux0, (size_t)count * 8)) ||                  // op_bucket + sorted
       (rc = ensure(w.aux1, (size_t)nb * 12)) ||                    // bcount, bfill, boff

@@ -31,6 +31,7 @@ enum : int32_t {
   CLS_TOY = 0,                                   // single-limb keys, any kind
   CLS_CRT16 = 1, CLS_CRT32 = 2, CLS_CRT48 = 3, CLS_CRT64 = 4,   // CRT, half size H
   CLS_PUB32 = 5, CLS_PUB64 = 6, CLS_PUB96 = 7, CLS_PUB128 = 8,  // public exponent, L limbs
+                                                                // (96, 128: four lanes per operation)
   CLS_PLAIN32 = 9, CLS_PLAIN64 = 10,             // plain private exponent, L limbs
   CLS_COUNT = 11
 };
@@ -60,9 +61,11 @@ __host__ __device__ inline int32_t batch_group(int32_t cls) {
   return GRP_MID;
 }
 
-// operations per tile of a class
+// operations per tile of a class: CRT 32 (warp pair on the same 32), wide
+// public 16 (4 lanes per operation, 8 per warp), others 64 (32 per warp)
 __host__ __device__ inline int32_t batch_tile_ops(int32_t cls) {
-  return (cls >= CLS_CRT16 && cls <= CLS_CRT64) || cls == CLS_PUB96 || cls == CLS_PUB128 ? 32 : 64;
+  if (cls == CLS_PUB96 || cls == CLS_PUB128) return 16;
+  return (cls >= CLS_CRT16 && cls <= CLS_CRT64) ? 32 : 64;
 }
 
 struct BatchDesc {

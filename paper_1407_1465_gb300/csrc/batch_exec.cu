@@ -6,11 +6,12 @@
 // and runs the tile function of its class:
 //   CRT       both warps, q half and p half (crt_tile)
 //   public    L <= 64: one warp per 32 operations (pub_tile);
-//             L = 96, 128: warp 0 only, operands in shared memory (pub_wide_tile)
+//             L = 96, 128: four lanes per operation, 8 operations per warp (pub_tile_t)
 //   plain     one warp per 32 operations (plain_tile)
 //   toy       one thread per operation (toy_op)
 #include "batch.h"
 #include "kernels.cuh"
+#include "kernels_t.cuh"
 
 namespace rsagpu {
 namespace {
@@ -39,10 +40,13 @@ __device__ __forceinline__ void run_pub(const uint32_t *ks, uint4 *work, int war
   pub_tile<L, kU>(ks, lane, sq, sq + kStage, io);
 }
 
+// wide public exponents: 4 lanes per operation, 8 operations per warp
 template <int L>
-__device__ __forceinline__ void run_pub_wide(const uint32_t *ks, uint4 *work, int lane, const TileIO &io) {
-  constexpr int kStage = (L / 4) * 32;
-  pub_wide_tile<L, 4>(ks, lane, work + lane, work + kStage + lane, io);
+__device__ __forceinline__ void run_pub_wide(const uint32_t *ks, uint4 *work, int warp, int lane, const TileIO &io) {
+  constexpr int kStage = (L / 4) * 8;
+  const Group<4> g(lane);
+  uint4 *sq = work + warp * 2 * kStage;
+  pub_tile_t<L, 4, 8>(ks, g, sq + g.opi, sq + kStage + g.opi, io);
 }
 
 template <int L>
@@ -84,10 +88,12 @@ __global__ void __launch_bounds__(64, 1) batch_exec_kernel(BatchDesc d) {
       if (td.cls == CLS_CRT48) run_crt<48, kBatchWindowCrt48>(ks, work, table_warp, warp, lane, io_pair);
       else if (td.cls == CLS_CRT64) run_crt<64, kBatchWindowCrt64>(ks, work, table_warp, warp, lane, io_pair);
     } else if constexpr (G == GRP_WIDE) {
-      if (warp == 0) {
-        if (td.cls == CLS_PUB96) run_pub_wide<96>(ks, work, lane, io_pair);
-        else if (td.cls == CLS_PUB128) run_pub_wide<128>(ks, work, lane, io_pair);
-      }
+      // 16-operation tiles: 8 per warp
+      const int32_t wn8 = min(8, max(0, td.nops - 8 * warp));
+      const TileIO io8{d.msgs, d.out, d.status, d.sorted, d.offsets, (uint32_t)(td.op_start + 8 * warp),
+                       (uint32_t)wn8};
+      if (td.cls == CLS_PUB96) run_pub_wide<96>(ks, work, warp, lane, io8);
+      else if (td.cls == CLS_PUB128) run_pub_wide<128>(ks, work, warp, lane, io8);
     } else {
       const KeyHeader &hd = *reinterpret_cast<const KeyHeader *>(ks);
       switch (td.cls) {

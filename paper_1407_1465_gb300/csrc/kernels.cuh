@@ -30,6 +30,13 @@
 
 namespace rsagpu {
 
+// Named barrier of a warp pair (64 threads).  The warp is reconverged first and
+// the non-aligned form is used, so the barrier never meets a diverged warp.
+__device__ __forceinline__ void pair_barrier(int bar_id) {
+  __syncwarp();
+  asm volatile("barrier.sync %0, 64;" ::"r"(bar_id) : "memory");
+}
+
 // Message/result row loads and stores (rows are 16-byte aligned: L % 4 == 0).
 template <int L>
 __device__ __forceinline__ void load_row(uint32_t (&A)[L], const uint32_t *row, bool valid) {
@@ -233,10 +240,10 @@ __device__ __forceinline__ void crt_tile(const uint32_t *ks, bool isP, int lane,
     // m_q = from-Montgomery; hand it to the p warp
     mont_mul<H, U>(A, SmemB{reinterpret_cast<const uint4 *>(ks + lay.unitH), 1}, N, np);
     to_stage<H>(xb, A);
-    asm volatile("bar.sync %0, 64;" ::"r"(bar_id) : "memory");
+    pair_barrier(bar_id);
     return;
   }
-  asm volatile("bar.sync %0, 64;" ::"r"(bar_id) : "memory");
+  pair_barrier(bar_id);
   to_stage<H>(stage_lane, A);                      // A_p = m_p * R mod p
   from_stage<H>(A, xb);                            // m_q
   mont_mul<H, U>(A, SmemB{r2, 1}, N, np);          // m_q * R mod p

@@ -97,12 +97,15 @@ static int default_window(uint32_t L, int kind) {
 }
 
 Tune Ctx::tune_for(uint32_t nbits, int kind) const {
-  Tune t{0, 0, 0, 0};
+  Tune t{0, 0, 0, 0, 0};
   auto it = tuning.find({nbits, kind});
   if (it != tuning.end()) t = it->second;
   const uint32_t L = nbits / 32;
   if (!t.window) t.window = default_window(L, kind);
   if (!t.warps_per_cta) t.warps_per_cta = 4;
+  // lanes per operation: one, except public exponents of 3072/4096-bit moduli,
+  // whose one-lane form keeps its operands in shared memory and spills
+  if (!t.tpo) t.tpo = (kind == RSA_EXP_PUBLIC && L > 64) ? 4 : 1;
   return t;
 }
 
@@ -111,6 +114,15 @@ static size_t crt_smem_bytes(int H, int P) {
   const size_t key_words = (KeyLayout(2 * H).total + 3) / 4 * 4;
   const size_t stage = (size_t)(H / 4) * 32 * 16;
   return key_words * 4 + (size_t)P * 2 * stage + (size_t)2 * P * stage;
+}
+static size_t crt_t_smem_bytes(int H, int T, int P) {
+  const size_t key_words = (KeyLayout(2 * H).total + 3) / 4 * 4;
+  const size_t stage = (size_t)(H / 4) * (32 / T) * 16;
+  return key_words * 4 + (size_t)P * 2 * stage + (size_t)2 * P * stage;
+}
+static size_t pub_t_smem_bytes(int L, int T, int warps) {
+  const size_t key_words = (KeyLayout(L).total + 3) / 4 * 4;
+  return key_words * 4 + (size_t)warps * 2 * (L / 4) * (32 / T) * 16;
 }
 static size_t exp_smem_bytes(int L, int warps) {
   const size_t key_words = (KeyLayout(L).total + 3) / 4 * 4;
@@ -152,6 +164,49 @@ int Ctx::run_key(const KeySlot &k, int kind, uint64_t count, const uint32_t *msg
     return RSA_OK;
   }
   const Tune t = tune_for(k.nbits, kind);
+  if (t.tpo > 1 && kind == RSA_EXP_PRIVATE_CRT) {
+    const int H = (int)L / 2, T = t.tpo;
+    const void *fn = crt_kernel_t_fn(H, T, t.window);
+    if (!fn) return set_error(RSA_ERR_UNSUPPORTED, "no CRT kernel for this size / window / lanes per operation");
+    const int P = std::max(1, t.warps_per_cta / 2);
+    const int threads = 64 * P;
+    const size_t smem = crt_t_smem_bytes(H, T, P);
+    const uint64_t ntiles = (count + 32 / T - 1) / (32 / T);
+    int grid = 0;
+    int rc = launch_grid(fn, threads, smem, (uint64_t)P, ntiles, t.ctas_per_sm, &grid);
+    if (rc) return rc;
+    const size_t tbytes = (size_t)grid * 2 * P * ((size_t)1 << t.window) * (H / T) * 128;
+    rc = ensure(w.tables, tbytes);
+    if (rc) return rc;
+    CrtArgs a{k.d_rec, msgs, out, status, (uint32_t)count, static_cast<uint4 *>(w.tables.ptr)};
+    void *args[] = {&a};
+    e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, s);
+    if (e != cudaSuccess) return cuda_error(e, "launch crt_kernel_t");
+    stats.kernel_launches++;
+    last_grid = grid;
+    last_threads = threads;
+    return RSA_OK;
+  }
+  if (t.tpo > 1 && kind == RSA_EXP_PUBLIC) {
+    const int T = t.tpo;
+    const void *fn = pub_kernel_t_fn((int)L, T);
+    if (!fn) return set_error(RSA_ERR_UNSUPPORTED, "no public kernel for this size / lanes per operation");
+    const int warps = std::max(1, t.warps_per_cta);
+    const int threads = 32 * warps;
+    const size_t smem = pub_t_smem_bytes((int)L, T, warps);
+    const uint64_t ntiles = (count + 32 / T - 1) / (32 / T);
+    int grid = 0;
+    int rc = launch_grid(fn, threads, smem, (uint64_t)warps, ntiles, t.ctas_per_sm, &grid);
+    if (rc) return rc;
+    ExpArgs a{k.d_rec, msgs, out, status, (uint32_t)count, nullptr};
+    void *args[] = {&a};
+    e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, s);
+    if (e != cudaSuccess) return cuda_error(e, "launch pub_kernel_t");
+    stats.kernel_launches++;
+    last_grid = grid;
+    last_threads = threads;
+    return RSA_OK;
+  }
   if (kind == RSA_EXP_PRIVATE_CRT) {
     const int H = (int)L / 2;
     const void *fn = crt_kernel_fn(H, t.window, t.variant);
@@ -445,9 +500,11 @@ int rsa_set_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, const rsa_tuni
   if (t->warps_per_cta < 0 || t->warps_per_cta > 8 || t->ctas_per_sm < 0)
     return set_error(RSA_ERR_ARG, "bad launch shape");
   if (t->variant < 0 || t->variant > 2) return set_error(RSA_ERR_ARG, "variant must be 0, 1 or 2");
+  if (!(t->threads_per_op == 0 || t->threads_per_op == 1 || t->threads_per_op == 2 || t->threads_per_op == 4))
+    return set_error(RSA_ERR_ARG, "threads_per_op must be 0, 1, 2 or 4");
   if (exp_sel == RSA_EXP_PRIVATE_CRT && (t->warps_per_cta & 1))
     return set_error(RSA_ERR_ARG, "CRT kernels run warp pairs: warps_per_cta must be even");
-  c->tuning[{nbits, exp_sel}] = Tune{t->window, t->warps_per_cta, t->ctas_per_sm, t->variant};
+  c->tuning[{nbits, exp_sel}] = Tune{t->window, t->warps_per_cta, t->ctas_per_sm, t->variant, t->threads_per_op};
   return RSA_OK;
 }
 
@@ -460,6 +517,7 @@ int rsa_get_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, rsa_tuning *t)
   t->warps_per_cta = x.warps_per_cta;
   t->ctas_per_sm = x.ctas_per_sm;
   t->variant = x.variant;
+  t->threads_per_op = x.tpo;
   return RSA_OK;
 }
 

@@ -38,7 +38,7 @@ struct KeySlot {
 };
 
 struct Tune {
-  int window, warps_per_cta, ctas_per_sm, variant;
+  int window, warps_per_cta, ctas_per_sm, variant, tpo;
 };
 
 struct Ctx {

@@ -1,7 +1,7 @@
 // tune.cu -- rsa_autotune: times launch shapes of the uniform kernels and
 // keeps the fastest, with a small text cache keyed by GPU and problem class.
 //
-// Cache lines: "<gpu name>|<sm count>|<nbits>|<kind>|<log2 count bucket> window warps ctas variant ms"
+// Cache lines: "<gpu name>|<sm count>|<nbits>|<kind>|<log2 count bucket> window warps ctas variant tpo ms"
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -42,7 +42,7 @@ bool cache_lookup(const std::string &path, const std::string &key, Tune *t, doub
     std::string k;
     Tune x{};
     double m = 0;
-    if (!(is >> k >> x.window >> x.warps_per_cta >> x.ctas_per_sm >> x.variant >> m)) continue;
+    if (!(is >> k >> x.window >> x.warps_per_cta >> x.ctas_per_sm >> x.variant >> x.tpo >> m)) continue;
     if (k == key) {
       *t = x;
       *ms = m;
@@ -96,11 +96,13 @@ extern "C" int rsa_autotune(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint6
     std::vector<int> variants = priv ? std::vector<int>{1, 2} : std::vector<int>{0};
     double best_t = 1e30;
     int err = RSA_OK;
+    for (int tpo : {1, 2, 4})
     for (int v : variants)
       for (int w : windows)
         for (int wp : warps)
           for (int cps : {0, 1, 2}) {
-            c->tuning[{nbits, exp_sel}] = Tune{w, wp, cps, v};
+            if (tpo > 1 && (v == 2 || exp_sel == RSA_EXP_PRIVATE_PLAIN)) continue;  // not offered
+            c->tuning[{nbits, exp_sel}] = Tune{w, wp, cps, v, tpo};
             // warm-up, then the median of three timed runs
             if (c->run_key(*k, exp_sel, count, static_cast<uint32_t *>(in.ptr), static_cast<uint32_t *>(out.ptr),
                            nullptr, s) != RSA_OK)
@@ -122,7 +124,7 @@ extern "C" int rsa_autotune(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint6
             std::sort(t3, t3 + 3);
             if (t3[1] < best_t) {
               best_t = t3[1];
-              chosen = Tune{w, wp, cps, v};
+              chosen = Tune{w, wp, cps, v, tpo};
             }
           }
     cudaEventDestroy(a);
@@ -159,7 +161,7 @@ extern "C" int rsa_autotune(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint6
       std::ofstream f(path, std::ios::app);
       f.precision(17);
       f << key << " " << chosen.window << " " << chosen.warps_per_cta << " " << chosen.ctas_per_sm << " "
-        << chosen.variant << " " << chosen_ms << "\n";
+        << chosen.variant << " " << chosen.tpo << " " << chosen_ms << "\n";
     }
   }
   if (best) {
@@ -167,6 +169,7 @@ extern "C" int rsa_autotune(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint6
     best->warps_per_cta = chosen.warps_per_cta;
     best->ctas_per_sm = chosen.ctas_per_sm;
     best->variant = chosen.variant;
+    best->threads_per_op = chosen.tpo;
   }
   if (best_ms) *best_ms = chosen_ms;
   return RSA_OK;

@@ -225,3 +225,43 @@ def test_autotune_installs_a_working_shape(torch_cuda, ctx, keys, kids, tmp_path
     got, st = run(torch_cuda, ctx, kids[2048], CRT, rows)
     assert (st == 0).all() and np.array_equal(got, expect(key, CRT, rows))
     ctx.set_tuning(2048, CRT, reset=True)
+
+
+@pytest.mark.parametrize("tpo", [2, 4])
+@pytest.mark.parametrize("bits", [2048, 3072, 4096])
+def test_lanes_per_operation_crt(torch_cuda, ctx, keys, kids, bits, tpo):
+    """One operation spread over 2 or 4 lanes (warp-shuffle carries) gives the
+    same results; counts leave a ragged last tile."""
+    key = keys[bits]
+    good, bad = _edge_rows(key)
+    rows = np.concatenate([workloads.messages_below(key.n, 45, 21, ("tpo", bits, tpo)), good, bad])
+    ng = rows.shape[0] - bad.shape[0]
+    want = expect(key, CRT, rows[:ng])
+    try:
+        for w in (4, 5):
+            ctx.set_tuning(bits, CRT, window=w, threads_per_op=tpo)
+            got, st = run(torch_cuda, ctx, kids[bits], CRT, rows)
+            assert (st[:ng] == 0).all() and (st[ng:] == -3).all()
+            assert np.array_equal(got[:ng], want), (bits, tpo, w)
+            assert not got[ng:].any()
+    finally:
+        ctx.set_tuning(bits, CRT, reset=True)
+
+
+@pytest.mark.parametrize("tpo", [2, 4])
+@pytest.mark.parametrize("bits", [2048, 3072, 4096])
+def test_lanes_per_operation_public(torch_cuda, ctx, keys, kids, bits, tpo):
+    if bits == 2048 and tpo == 4:
+        pytest.skip("not instantiated")
+    key = keys[bits]
+    good, bad = _edge_rows(key)
+    rows = np.concatenate([workloads.messages_below(key.n, 37, 22, ("tpo-pub", bits, tpo)), good, bad])
+    ng = rows.shape[0] - bad.shape[0]
+    try:
+        ctx.set_tuning(bits, PUB, threads_per_op=tpo)
+        got, st = run(torch_cuda, ctx, kids[bits], PUB, rows)
+        assert (st[:ng] == 0).all() and (st[ng:] == -3).all()
+        assert np.array_equal(got[:ng], expect(key, PUB, rows[:ng]))
+        assert not got[ng:].any()
+    finally:
+        ctx.set_tuning(bits, PUB, reset=True)
