@@ -181,7 +181,7 @@ def rsa_get_tuning(ctx: int, nbits: int, exp_sel: int) -> dict:
     t = rsa_tuning()
     check(_lib.lib().rsa_get_tuning(ctx, nbits, exp_sel, ctypes.byref(t)))
     return {"window": t.window, "warps_per_cta": t.warps_per_cta, "ctas_per_sm": t.ctas_per_sm,
-            "variant": t.variant}
+            "variant": t.variant, "threads_per_op": t.threads_per_op}
 
 
 def rsa_autotune(ctx: int, key_id: int, exp_sel: int, count: int, cache_path: str | None = None) -> dict:

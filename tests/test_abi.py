@@ -146,3 +146,12 @@ def test_ctx_without_gpu_reports_error(lib):
     with pytest.raises(RsaError) as ei:
         rsa_ctx_create(0)
     assert ei.value.code in (-1, -5)
+
+
+def test_tuning_dict_has_every_field():
+    from paper_1407_1465_gb300 import _lib
+    import inspect
+    import paper_1407_1465_gb300 as pkg
+    src = inspect.getsource(pkg.rsa_get_tuning) + inspect.getsource(pkg.rsa_autotune)
+    for name, _ in _lib.rsa_tuning._fields_:
+        assert src.count('"%s"' % name) >= 2, name
