@@ -30,7 +30,7 @@ __global__ void plan_reset(BatchDesc d) {
     d.bcount[i] = 0u;
     d.bfill[i] = 0u;
   }
-  if (blockIdx.x == 0 && threadIdx.x < 16 && threadIdx.x != 2) d.ctl[threadIdx.x] = 0u;
+  if (blockIdx.x == 0 && threadIdx.x < 16 && threadIdx.x != 2) d.ctl[threadIdx.x] = 0u;  // ranges, counters
 }
 
 // classify each operation into a bucket (key id * 3 + kind); invalid ones get a status
@@ -178,7 +178,7 @@ struct BatchState {
   bool built = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaGraphNode_t nodes[7] = {};
+  cudaGraphNode_t nodes[4 + GRP_COUNT] = {};
   int exec_grid = 0;
   DevBuf keydir;
   uint64_t keydir_epoch = ~0ull;
@@ -254,7 +254,7 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
     st->keydir_epoch = key_epoch;
   }
   const uint32_t nb = std::max<uint32_t>(nkeys, 1) * 3;
-  const uint32_t max_tiles = (uint32_t)(count / 16 + nb + 1);   // smallest tile: 16 operations
+  const uint32_t max_tiles = (uint32_t)(count / 8 + nb + 1);   // smallest tile: 8 operations
   int rc;
   if ((rc = ensure(w.aux0, (size_t)count * 8)) ||                  // op_bucket + sorted
       (rc = ensure(w.aux1, (size_t)nb * 12)) ||                    // bcount, bfill, boff
@@ -279,7 +279,9 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
   st->exec_grid = max_grid;
   // window tables: one slot per resident warp of each group (groups run concurrently)
   const size_t slot_u4 = (size_t)2 * kBatchTableU4PerWarp;
-  if ((rc = ensure(w.tables, (size_t)(grids_exec[0] + grids_exec[1] + grids_exec[2]) * slot_u4 * 16))) return rc;
+  size_t all_slots = 0;
+  for (int gi = 0; gi < GRP_COUNT; ++gi) all_slots += (size_t)grids_exec[gi];
+  if ((rc = ensure(w.tables, all_slots * slot_u4 * 16))) return rc;
 
   BatchDesc d{};
   d.count = (uint32_t)count;
@@ -311,16 +313,14 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
   }
   const int g_ops = (int)std::min<uint64_t>((count + 255) / 256, (uint64_t)sm_count * 8);
   const int g_nb = (int)std::min<uint32_t>((nb + 255) / 256, (uint32_t)sm_count * 8);
-  // nodes: reset -> count -> tiles -> scatter -> {big, mid, wide} (the three run concurrently)
-  constexpr int kNodes = 7;
+  // nodes: reset -> count -> tiles -> scatter -> {one persistent kernel per group} (run concurrently)
+  constexpr int kNodes = 4 + GRP_COUNT;
   const void *fns[kNodes] = {reinterpret_cast<const void *>(&plan_reset), reinterpret_cast<const void *>(&plan_count),
                              reinterpret_cast<const void *>(&plan_tiles), reinterpret_cast<const void *>(&plan_scatter),
-                             batch_exec_fn(GRP_BIG), batch_exec_fn(GRP_MID), batch_exec_fn(GRP_WIDE)};
-  const dim3 grids[kNodes] = {dim3(std::max(1, g_nb)), dim3(g_ops), dim3(1), dim3(g_ops),
-                              dim3(grids_exec[0]), dim3(grids_exec[1]), dim3(grids_exec[2])};
-  const dim3 blocks[kNodes] = {dim3(256), dim3(256), dim3(1024), dim3(256), dim3(64), dim3(64), dim3(64)};
-  const size_t smems[kNodes] = {0, 0, 0, 0, batch_exec_smem_bytes(0), batch_exec_smem_bytes(1),
-                                batch_exec_smem_bytes(2)};
+                             batch_exec_fn(0), batch_exec_fn(1), batch_exec_fn(2), batch_exec_fn(3)};
+  dim3 grids[kNodes] = {dim3(std::max(1, g_nb)), dim3(g_ops), dim3(1), dim3(g_ops)};
+  dim3 blocks[kNodes] = {dim3(256), dim3(256), dim3(1024), dim3(256)};
+  size_t smems[kNodes] = {0, 0, 0, 0};
   BatchDesc dg[kNodes];
   void *args[kNodes][1];
   for (int i = 0; i < kNodes; ++i) {
@@ -328,8 +328,14 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
     args[i][0] = &dg[i];
   }
   // each group's warps index their own slice of the table scratch
-  dg[5].tables = d.tables + (size_t)grids_exec[0] * slot_u4;
-  dg[6].tables = dg[5].tables + (size_t)grids_exec[1] * slot_u4;
+  size_t slot_off = 0;
+  for (int gi = 0; gi < GRP_COUNT; ++gi) {
+    grids[4 + gi] = dim3(grids_exec[gi]);
+    blocks[4 + gi] = dim3(64);
+    smems[4 + gi] = batch_exec_smem_bytes(gi);
+    dg[4 + gi].tables = d.tables + slot_off;
+    slot_off += (size_t)grids_exec[gi] * slot_u4;
+  }
   cudaError_t e;
   auto params = [&](int i) {
     cudaKernelNodeParams p{};
@@ -344,7 +350,7 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
     if ((e = cudaGraphCreate(&st->graph, 0)) != cudaSuccess) return cuda_error(e, "cudaGraphCreate");
     for (int i = 0; i < kNodes; ++i) {
       cudaKernelNodeParams p = params(i);
-      const int dep = i < 4 ? i - 1 : 3;
+      const int dep = i < 4 ? i - 1 : 3;   // the group kernels all follow the scatter
       e = cudaGraphAddKernelNode(&st->nodes[i], st->graph, dep >= 0 ? &st->nodes[dep] : nullptr, dep >= 0 ? 1 : 0, &p);
       if (e != cudaSuccess) return cuda_error(e, "cudaGraphAddKernelNode");
     }
@@ -360,7 +366,7 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
   }
   if ((e = cudaGraphLaunch(st->exec, s)) != cudaSuccess) return cuda_error(e, "cudaGraphLaunch");
   stats.graph_launches++;
-  stats.kernel_launches += 7;
+  stats.kernel_launches += 4 + GRP_COUNT;
   return RSA_OK;
 }
 

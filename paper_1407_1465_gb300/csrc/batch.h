@@ -52,20 +52,26 @@ __host__ __device__ inline int32_t batch_class(uint32_t L, int kind) {
 
 // Execution groups: one persistent kernel each, so every group gets the
 // register allocation its own largest class needs.  Group order is the order
-// of tile ranges: the large CRT classes first, then the rest, then the wide
-// public-exponent classes.
-enum : int32_t { GRP_BIG = 0, GRP_MID = 1, GRP_WIDE = 2, GRP_COUNT = 3 };
+// of tile ranges (longest operations first).
+//   BIG   CRT of 3072/4096-bit keys, four lanes per operation (128 registers)
+//   CRT   CRT of 1024/2048-bit keys, public/plain of 1024-bit keys, toy keys
+//   L64   public/plain exponents of 2048-bit moduli (one lane, 232 registers)
+//   WIDE  public exponents of 3072/4096-bit moduli, four lanes per operation
+enum : int32_t { GRP_BIG = 0, GRP_CRT = 1, GRP_L64 = 2, GRP_WIDE = 3, GRP_COUNT = 4 };
 __host__ __device__ inline int32_t batch_group(int32_t cls) {
   if (cls == CLS_CRT48 || cls == CLS_CRT64) return GRP_BIG;
   if (cls == CLS_PUB96 || cls == CLS_PUB128) return GRP_WIDE;
-  return GRP_MID;
+  if (cls == CLS_PUB64 || cls == CLS_PLAIN64) return GRP_L64;
+  return GRP_CRT;
 }
 
-// operations per tile of a class: CRT 32 (warp pair on the same 32), wide
-// public 16 (4 lanes per operation, 8 per warp), others 64 (32 per warp)
+// operations per tile of a class: CRT 32 (warp pair on the same 32), wide CRT 8
+// (4 lanes per operation, the pair on the same 8), wide public 16 (4 lanes per
+// operation, 8 per warp), others 64 (32 per warp)
 __host__ __device__ inline int32_t batch_tile_ops(int32_t cls) {
+  if (cls == CLS_CRT48 || cls == CLS_CRT64) return 8;
   if (cls == CLS_PUB96 || cls == CLS_PUB128) return 16;
-  return (cls >= CLS_CRT16 && cls <= CLS_CRT64) ? 32 : 64;
+  return (cls == CLS_CRT16 || cls == CLS_CRT32) ? 32 : 64;
 }
 
 struct BatchDesc {
@@ -83,7 +89,7 @@ struct BatchDesc {
   uint32_t *bcount, *bfill, *boff;  // [nkeys * 3]
   TileDesc *tiles;            // [max_tiles]
   uint32_t *ctl;              // [0] unused, [1] tile count, [2] error bits,
-                              // [4+g] first tile of group g, [8+g] end, [12+g] counter
+                              // [4+g] first tile of group g, [8+g] end, [12+g] counter (g < 4)
   uint4 *tables;              // per resident warp: kBatchTableU4PerWarp
   uint32_t max_tiles;
   int32_t class_rank[CLS_COUNT];  // position of each class in the longest-first order

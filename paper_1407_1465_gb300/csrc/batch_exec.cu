@@ -33,6 +33,17 @@ __device__ __forceinline__ void run_crt(const uint32_t *ks, uint4 *work, uint4 *
   crt_tile<H, W, kU, false>(ks, warp == 1, lane, stage_lane, xb, table_warp + lane, 1, io);
 }
 
+// CRT of 3072/4096-bit keys: four lanes per operation, the pair on the same 8 operations
+template <int H, int W>
+__device__ __forceinline__ void run_crt4(const uint32_t *ks, uint4 *work, uint4 *table_warp, int warp, int lane,
+                                         const TileIO &io) {
+  constexpr int kStage = (H / 4) * 8;
+  const Group<4> g(lane);
+  uint4 *xb = work + g.opi;
+  uint4 *stage_op = work + kStage + warp * kStage + g.opi;
+  crt_tile_t<H, 4, W, 8>(ks, warp == 1, g, stage_op, xb, table_warp + lane, 1, io);
+}
+
 template <int L>
 __device__ __forceinline__ void run_pub(const uint32_t *ks, uint4 *work, int warp, int lane, const TileIO &io) {
   constexpr int kStage = (L / 4) * 32;
@@ -85,8 +96,13 @@ __global__ void __launch_bounds__(64, 1) batch_exec_kernel(BatchDesc d) {
     const TileIO io_warp{d.msgs, d.out, d.status, d.sorted, d.offsets, (uint32_t)(td.op_start + 32 * warp),
                          (uint32_t)wn};
     if constexpr (G == GRP_BIG) {
-      if (td.cls == CLS_CRT48) run_crt<48, kBatchWindowCrt48>(ks, work, table_warp, warp, lane, io_pair);
-      else if (td.cls == CLS_CRT64) run_crt<64, kBatchWindowCrt64>(ks, work, table_warp, warp, lane, io_pair);
+      if (td.cls == CLS_CRT48) run_crt4<48, kBatchWindowCrt48>(ks, work, table_warp, warp, lane, io_pair);
+      else if (td.cls == CLS_CRT64) run_crt4<64, kBatchWindowCrt64>(ks, work, table_warp, warp, lane, io_pair);
+    } else if constexpr (G == GRP_L64) {
+      if (wn > 0) {
+        if (td.cls == CLS_PUB64) run_pub<64>(ks, work, warp, lane, io_warp);
+        else if (td.cls == CLS_PLAIN64) run_plain<64>(ks, work, table_warp, warp, lane, io_warp);
+      }
     } else if constexpr (G == GRP_WIDE) {
       // 16-operation tiles: 8 per warp
       const int32_t wn8 = min(8, max(0, td.nops - 8 * warp));
@@ -100,9 +116,7 @@ __global__ void __launch_bounds__(64, 1) batch_exec_kernel(BatchDesc d) {
         case CLS_CRT16: run_crt<16, kBatchWindowCrt16>(ks, work, table_warp, warp, lane, io_pair); break;
         case CLS_CRT32: run_crt<32, kBatchWindowCrt32>(ks, work, table_warp, warp, lane, io_pair); break;
         case CLS_PUB32: if (wn > 0) run_pub<32>(ks, work, warp, lane, io_warp); break;
-        case CLS_PUB64: if (wn > 0) run_pub<64>(ks, work, warp, lane, io_warp); break;
         case CLS_PLAIN32: if (wn > 0) run_plain<32>(ks, work, table_warp, warp, lane, io_warp); break;
-        case CLS_PLAIN64: if (wn > 0) run_plain<64>(ks, work, table_warp, warp, lane, io_warp); break;
         case CLS_TOY: {
           const int slot = (int)threadIdx.x;
           if (slot < td.nops) {
@@ -128,7 +142,8 @@ __global__ void __launch_bounds__(64, 1) batch_exec_kernel(BatchDesc d) {
 const void *batch_exec_fn(int group) {
   switch (group) {
     case GRP_BIG: return reinterpret_cast<const void *>(&batch_exec_kernel<GRP_BIG>);
-    case GRP_MID: return reinterpret_cast<const void *>(&batch_exec_kernel<GRP_MID>);
+    case GRP_CRT: return reinterpret_cast<const void *>(&batch_exec_kernel<GRP_CRT>);
+    case GRP_L64: return reinterpret_cast<const void *>(&batch_exec_kernel<GRP_L64>);
     case GRP_WIDE: return reinterpret_cast<const void *>(&batch_exec_kernel<GRP_WIDE>);
     default: return nullptr;
   }
