@@ -132,7 +132,7 @@ __device__ __forceinline__ void fixed_window_exp(uint32_t (&A)[L], const uint32_
 #pragma unroll 1
     for (int k = nwin - 2; k >= 0; --k) {
 #pragma unroll 1
-      for (int s = 0; s < W; ++s) mont_sqr<L>(A, N, np);
+      for (int s = 0; s < W; ++s) mont_sqr_h<L, U>(A, N, np, stage_lane);
       table_select<L, W>(stage_lane, table_lane, exp_digit<W>(E, (uint32_t)k));
       mont_mul<L, U>(A, st, N, np);
     }

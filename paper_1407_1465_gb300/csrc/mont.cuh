@@ -293,6 +293,82 @@ __device__ __forceinline__ void mont_sqr(uint32_t (&A)[L], const NS &N, uint32_t
   final_sub<L>(A, r, N);
 }
 
+// A = A^2 * R^-1 mod N (A < N), separated form with a compact reduction: the
+// square's cross products (each a_i a_j, i < j, once), doubled, plus the
+// diagonal, fully unrolled (L(L+1)/2 word products); its upper L limbs go to
+// the per-lane stage and the Montgomery reduction runs as the same U-blocked
+// loop as mont_mul, taking one upper limb per step:
+//   t = low L limbs; for each i: t[L] += upper_i, then reduce_step (q, + q*N, / 2^32).
+template <int L, int U, class NS>
+__device__ __forceinline__ void mont_sqr_h(uint32_t (&A)[L], const NS &N, uint32_t np, uint4 *stage_lane) {
+  static_assert(L % 4 == 0 && U % 4 == 0 && L % U == 0, "limb blocking");
+  uint32_t t2[2 * L];
+#pragma unroll
+  for (int k = 0; k < 2 * L; ++k) t2[k] = 0u;
+#pragma unroll
+  for (int i = 0; i < L - 1; ++i) {
+#pragma unroll
+    for (int par = 0; par < 2; ++par) {
+      const int j0 = i + 1 + par;
+      if (j0 <= L - 1) {
+        t2[i + j0] = mad_lo_cc(A[i], A[j0], t2[i + j0]);
+        t2[i + j0 + 1] = madc_hi_cc(A[i], A[j0], t2[i + j0 + 1]);
+        int last = i + j0 + 1;
+#pragma unroll
+        for (int j = j0 + 2; j < L; j += 2) {
+          t2[i + j] = madc_lo_cc(A[i], A[j], t2[i + j]);
+          t2[i + j + 1] = madc_hi_cc(A[i], A[j], t2[i + j + 1]);
+          last = i + j + 1;
+        }
+        if (last + 2 < 2 * L) {
+          t2[last + 1] = addc_cc(t2[last + 1], 0u);
+          t2[last + 2] = addc(t2[last + 2], 0u);
+        } else if (last + 1 < 2 * L) {
+          t2[last + 1] = addc(t2[last + 1], 0u);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 2 * L - 1; k > 0; --k) t2[k] = __funnelshift_l(t2[k - 1], t2[k], 1);
+  t2[0] <<= 1;
+  t2[0] = mad_lo_cc(A[0], A[0], t2[0]);
+  t2[1] = madc_hi_cc(A[0], A[0], t2[1]);
+#pragma unroll
+  for (int i = 1; i < L; ++i) {
+    t2[2 * i] = madc_lo_cc(A[i], A[i], t2[2 * i]);
+    t2[2 * i + 1] = madc_hi_cc(A[i], A[i], t2[2 * i + 1]);
+  }
+#pragma unroll
+  for (int g = 0; g < L / 4; ++g)
+    stage_lane[g * 32] = make_uint4(t2[L + 4 * g], t2[L + 4 * g + 1], t2[L + 4 * g + 2], t2[L + 4 * g + 3]);
+  uint32_t t[L + 2];
+#pragma unroll
+  for (int j = 0; j < L; ++j) t[j] = t2[j];
+  t[L] = 0u;
+  t[L + 1] = 0u;
+#pragma unroll 1
+  for (int i0 = 0; i0 < L; i0 += U) {
+#pragma unroll
+    for (int u = 0; u < U; u += 4) {
+      const uint4 up = stage_lane[((i0 + u) >> 2) * 32];
+      t[L] = add_cc(t[L], up.x);
+      t[L + 1] = addc(t[L + 1], 0u);
+      reduce_any<L>(t, N, np);
+      t[L] = add_cc(t[L], up.y);
+      t[L + 1] = addc(t[L + 1], 0u);
+      reduce_any<L>(t, N, np);
+      t[L] = add_cc(t[L], up.z);
+      t[L + 1] = addc(t[L + 1], 0u);
+      reduce_any<L>(t, N, np);
+      t[L] = add_cc(t[L], up.w);
+      t[L + 1] = addc(t[L + 1], 0u);
+      reduce_any<L>(t, N, np);
+    }
+  }
+  final_sub<L>(A, t, N);
+}
+
 // ------------------------------------------------------------------ wide operands (L = 96, 128)
 // 128-bit shared-memory load issued exactly where written (volatile asm is not
 // reordered against the carry-chain asm), so operands are not hoisted into

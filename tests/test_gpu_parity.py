@@ -142,11 +142,20 @@ def test_window_and_launch_shapes(torch_cuda, ctx, keys, kids):
     rows = workloads.messages_below(key.n, 200, 8, "shapes")
     want = expect(key, CRT, rows)
     try:
-        for w in (3, 4, 5, 6):
-            for warps, cps in ((2, 0), (4, 1), (8, 0)):
-                ctx.set_tuning(2048, CRT, window=w, warps_per_cta=warps, ctas_per_sm=cps)
-                got, _ = run(torch_cuda, ctx, kids[2048], CRT, rows)
-                assert np.array_equal(got, want), (w, warps, cps)
+        for variant in (1, 2):
+            for w in (3, 4, 5, 6):
+                for warps, cps in ((2, 0), (4, 1), (8, 0)):
+                    ctx.set_tuning(2048, CRT, window=w, warps_per_cta=warps, ctas_per_sm=cps, variant=variant)
+                    got, _ = run(torch_cuda, ctx, kids[2048], CRT, rows)
+                    assert np.array_equal(got, want), (variant, w, warps, cps)
+        # the separated squaring on 1024-bit keys too (16-limb halves), and for the plain exponent
+        key1 = keys[1024]
+        rows1 = workloads.messages_below(key1.n, 70, 8, "shapes1024")
+        for kind in (CRT, PLAIN):
+            ctx.set_tuning(1024, kind, variant=2)
+            got, _ = run(torch_cuda, ctx, kids[1024], kind, rows1)
+            assert np.array_equal(got, expect(key1, kind, rows1)), kind
+            ctx.set_tuning(1024, kind, reset=True)
     finally:
         ctx.set_tuning(2048, CRT, reset=True)
 
