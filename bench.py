@@ -30,13 +30,18 @@ if ROOT not in sys.path:
 import workloads  # noqa: E402
 
 WORKLOADS = {
-    "rsa2048": dict(bits=2048, count=65536,
-                    desc="RSA-2048 CRT decryption: 1 seeded key (two 1024-bit primes, Miller-Rabin 40 "
-                         "rounds, e=65537), 65536 ciphertexts uniform in [0,n) as 64 x u32 limbs"),
-    "rsa4096": dict(bits=4096, count=16384,
-                    desc="RSA-4096 CRT decryption: 1 seeded key (two 2048-bit primes, e=65537), 16384 "
-                         "ciphertexts uniform in [0,n) as 128 x u32 limbs"),
+    "rsa2048": dict(bits=2048, count=65536),
+    "rsa4096": dict(bits=4096, count=16384),
 }
+
+
+def workload_desc(bits, count, kind="crt"):
+    """Names the single-key workload: key size, message count, limb layout and the
+    operation (CRT decryption with d, or encryption with e = 65537)."""
+    what = "CRT decryption" if kind == "crt" else "public-exponent encryption (e=65537)"
+    items = "ciphertexts" if kind == "crt" else "messages"
+    return ("RSA-%d %s: 1 seeded key (two %d-bit primes, Miller-Rabin 40 rounds, e=65537), %d %s uniform "
+            "in [0,n) as %d x u32 limbs" % (bits, what, bits // 2, count, items, bits // 32))
 
 # DRAM traffic of the benchmark's kernel from one ncu capture (profiles/
 # crt_kernel_rsa2048_w4_cios_ncu_full.md), valid only while the kernel sources
@@ -115,22 +120,77 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(key, rows, target_s: float = 12.0) -> dict:
-    """The oracle (CRT reference, as written) on every host core, on a bounded sample."""
+def cpu_baseline(key, rows, target_s: float = 12.0, public: bool = False) -> dict:
+    """The oracle (as written) on every host core, on a bounded sample: its CRT
+    routine for decryptions, its left-to-right binary method with e for encryptions."""
     import oracle
     threads = oracle.default_threads()
+
+    def run(r):
+        if public:
+            oracle.modexp_batch(r, key.e, key.n, threads=threads)
+        else:
+            oracle.crt_batch(r, key.d, key.p, key.q, threads=threads)
+
     probe = min(rows.shape[0], max(threads * 4, 64))
     t0 = time.perf_counter()
-    oracle.crt_batch(rows[:probe], key.d, key.p, key.q, threads=threads)
+    run(rows[:probe])
     rate = probe / (time.perf_counter() - t0)
     n = int(min(rows.shape[0], max(probe, rate * target_s)))
     t0 = time.perf_counter()
-    oracle.crt_batch(rows[:n], key.d, key.p, key.q, threads=threads)
+    run(rows[:n])
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "decrypts/s", "cores": threads, "kind": "oracle",
-            "sample": "first %d of the %d ciphertexts, oracle CRT routine (schoolbook multiply + "
-                      "Algorithm D + binary square-and-multiply), %d POSIX threads, %.1f s"
-                      % (n, rows.shape[0], threads, dt)}
+    what = ("left-to-right binary modexp with e" if public else "CRT routine") + \
+        " (schoolbook multiply + Algorithm D + binary square-and-multiply)"
+    return {"value": n / dt, "unit": "encryptions/s" if public else "decrypts/s", "cores": threads,
+            "kind": "oracle", "sample": "first %d of the %d messages, oracle %s, %d POSIX threads, %.1f s"
+                                        % (n, rows.shape[0], what, threads, dt)}
+
+
+def run_toy(args):
+    """The paper's own example (Sec. 2): n = 17947 = 131*137, e = 131, d = 137; 4096
+    single-limb packets uniform in [0, 2525], encrypted then decrypted (plain d, as
+    printed), one launch each per step.  Launch-latency bound: reported as ops/s
+    and microseconds per launch, no roofline claim."""
+    import torch
+    from paper_1407_1465_gb300 import (RSA_EXP_PRIVATE_PLAIN, RSA_EXP_PUBLIC, RsaContext, build,
+                                       rsa_modexp_key)
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ctx = RsaContext(0)
+    t = workloads
+    kid = ctx.keyload(32, t.TOY_N, t.TOY_E, t.TOY_D, t.TOY_P, t.TOY_Q)
+    pk = torch.from_numpy(t.toy_packets(4096).view(np.int32)).to(dev)
+    enc, dec = torch.empty_like(pk), torch.empty_like(pk)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+
+    def step():
+        rsa_modexp_key(ctx.handle, kid, RSA_EXP_PUBLIC, 4096, pk, enc, None, sptr)
+        rsa_modexp_key(ctx.handle, kid, RSA_EXP_PRIVATE_PLAIN, 4096, enc, dec, None, sptr)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    import oracle
+    want = [oracle.modexp(int(m), t.TOY_D, t.TOY_N) for m in enc.cpu().numpy().view(np.uint32)[:64]]
+    if list(dec.cpu().numpy().view(np.uint32)[:64]) != want:
+        raise RuntimeError("toy results differ from the oracle")
+    line = {"metric": "toy key (n=17947, e=131, d=137): modexps/sec", "value": 8192 / (ms / 1e3),
+            "unit": "ops/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "us_per_launch": ms * 1e3 / 2, "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "4096 packets uniform in [0,2525], encrypt (e=131) + decrypt (d=137) per step"}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
 
 
 def run_ragged(args):
@@ -295,34 +355,46 @@ def run_reference(args, spec):
     if rank != 0:
         return 0
     import oracle
-    key, rows = workloads.rsa_single(spec["bits"], spec["count"])
+    key, rows = workloads.rsa_single(spec["bits"], WORKLOADS[args.workload]["count"])
     threads = oracle.default_threads()
+    public = args.kind == "public"
+
+    def run(sub):
+        if public:
+            return oracle.modexp_batch(sub, key.e, key.n, threads=threads)
+        return oracle.crt_batch(sub, key.d, key.p, key.q, threads=threads)
+
     probe = min(rows.shape[0], max(threads * 4, 64))
     t0 = time.perf_counter()
-    oracle.crt_batch(rows[:probe], key.d, key.p, key.q, threads=threads)
+    run(rows[:probe])
     rate = probe / (time.perf_counter() - t0)
     # size each step so the whole run stays within a couple of minutes
     per_step = int(max(threads, min(rows.shape[0], rate * 120.0 / max(1, args.steps + args.warmup))))
     for _ in range(args.warmup):
-        oracle.crt_batch(rows[:per_step], key.d, key.p, key.q, threads=threads)
+        run(rows[:per_step])
     times = []
     for k in range(args.steps):
         lo = (k * per_step) % max(1, rows.shape[0] - per_step)
         t0 = time.perf_counter()
-        oracle.crt_batch(rows[lo:lo + per_step], key.d, key.p, key.q, threads=threads)
+        run(rows[lo:lo + per_step])
         times.append(time.perf_counter() - t0)
     ms = 1e3 * sum(times) / len(times)
     value = per_step / (ms / 1e3)
+    unit = "encryptions/s" if public else "decrypts/s"
+    metric = ("RSA-%d encryptions/sec (e=65537)" if public else "RSA-%d CRT decrypts/sec") % spec["bits"]
+    items = "messages" if public else "ciphertexts"
+    routine = "left-to-right binary modexp with e" if public else "CRT routine"
     line = {
-        "impl": "reference", "metric": "RSA-%d CRT decrypts/sec" % spec["bits"], "value": value,
-        "unit": "decrypts/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "impl": "reference", "metric": metric, "value": value,
+        "unit": unit, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic", "gpu_launches": 0,
-        "config": {"workload": spec["desc"], "step": "%d ciphertexts per step (bounded sample)" % per_step},
-        "cpu_baseline": {"value": value, "unit": "decrypts/s", "cores": threads, "kind": "oracle",
-                         "sample": "%d ciphertexts per step, oracle CRT routine, %d POSIX threads"
-                                   % (per_step, threads)},
-        "e2e": {"value": value, "unit": "decrypts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config": {"workload": workload_desc(spec["bits"], spec["count"], args.kind),
+                   "step": "%d %s per step (bounded sample)" % (per_step, items)},
+        "cpu_baseline": {"value": value, "unit": unit, "cores": threads, "kind": "oracle",
+                         "sample": "%d %s per step, oracle %s, %d POSIX threads"
+                                   % (per_step, items, routine, threads)},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -334,7 +406,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="rsa2048", choices=sorted(WORKLOADS) + ["ragged", "serving"])
+    ap.add_argument("--workload", default="rsa2048", choices=sorted(WORKLOADS) + ["ragged", "serving", "toy"])
+    ap.add_argument("--kind", default="crt", choices=["crt", "public"],
+                    help="rsa2048/rsa4096: CRT decryption (default) or public-exponent encryption")
     ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000,100000,200000")
     ap.add_argument("--duration", type=float, default=1.0, help="seconds of arrivals per rate (serving)")
     ap.add_argument("--window-us", type=int, default=200, help="batching window of the serving loop")
@@ -351,10 +425,11 @@ def main():
         return run_ragged(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "toy":
+        return run_toy(args)
     spec = dict(WORKLOADS[args.workload])
     if args.count:
         spec["count"] = args.count
-        spec["desc"] += " [count overridden: %d ciphertexts]" % args.count
     if args.impl == "reference":
         return run_reference(args, spec)
     if args.warmup < 3:
@@ -369,8 +444,12 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    from paper_1407_1465_gb300 import RSA_EXP_PRIVATE_CRT, RsaContext, build, rsa_modexp_key, rsa_products_per_op
+    from paper_1407_1465_gb300 import (RSA_EXP_PRIVATE_CRT, RSA_EXP_PUBLIC, RsaContext, build, rsa_modexp_key,
+                                       rsa_products_per_op)
     build.build()
+    kind = RSA_EXP_PRIVATE_CRT if args.kind == "crt" else RSA_EXP_PUBLIC
+    metric = ("RSA-%d CRT decrypts/sec" if args.kind == "crt" else "RSA-%d encryptions/sec (e=65537)") % spec["bits"]
+    unit = "decrypts/s" if args.kind == "crt" else "encryptions/s"
 
     key, rows = workloads.rsa_single(spec["bits"], WORKLOADS[args.workload]["count"])
     rows = rows[:spec["count"]] if spec["count"] <= rows.shape[0] else \
@@ -379,9 +458,9 @@ def main():
     ctx = RsaContext(local, mem_budget_bytes=16 << 30)
     kid = ctx.keyload(spec["bits"], key.n, key.e, key.d, key.p, key.q)
     if args.window or args.warps or args.ctas_per_sm or args.variant or args.tpo:
-        ctx.set_tuning(spec["bits"], RSA_EXP_PRIVATE_CRT, window=args.window, warps_per_cta=args.warps,
+        ctx.set_tuning(spec["bits"], kind, window=args.window, warps_per_cta=args.warps,
                        ctas_per_sm=args.ctas_per_sm, variant=args.variant, threads_per_op=args.tpo)
-    tune = ctx.get_tuning(spec["bits"], RSA_EXP_PRIVATE_CRT)
+    tune = ctx.get_tuning(spec["bits"], kind)
     msgs = torch.from_numpy(rows.view(np.int32)).to(dev)
     out = torch.empty_like(msgs)
     status = torch.empty(count, dtype=torch.int32, device=dev)
@@ -390,7 +469,7 @@ def main():
     sptr = stream.cuda_stream
 
     def step():
-        rsa_modexp_key(ctx.handle, kid, RSA_EXP_PRIVATE_CRT, count, msgs, out, status, sptr)
+        rsa_modexp_key(ctx.handle, kid, kind, count, msgs, out, status, sptr)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -430,30 +509,30 @@ def main():
         h_out = torch.empty_like(h_in).pin_memory()
         from paper_1407_1465_gb300 import rsa_modexp_key_host
         for _ in range(2):
-            rsa_modexp_key_host(ctx.handle, kid, RSA_EXP_PRIVATE_CRT, count, h_in.data_ptr(), h_out.data_ptr(),
+            rsa_modexp_key_host(ctx.handle, kid, kind, count, h_in.data_ptr(), h_out.data_ptr(),
                                 None, sptr)
         ek = max(3, args.steps // 4)
         if ws > 1:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(ek):
-            rsa_modexp_key_host(ctx.handle, kid, RSA_EXP_PRIVATE_CRT, count, h_in.data_ptr(), h_out.data_ptr(),
+            rsa_modexp_key_host(ctx.handle, kid, kind, count, h_in.data_ptr(), h_out.data_ptr(),
                                 None, sptr)
         e_s = (time.perf_counter() - t0) / ek
         if ws > 1:
             t = torch.tensor([e_s], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e_s = float(t.item())
-        e2e = {"value": ws * count / e_s, "unit": "decrypts/s", "h2d_bytes_per_step": count * L * 4,
+        e2e = {"value": ws * count / e_s, "unit": unit, "h2d_bytes_per_step": count * L * 4,
                "d2h_bytes_per_step": count * L * 4, "steps": ek,
                "api": "rsa_modexp_key_host (pinned host buffers)"}
         if not np.array_equal(h_out.numpy().view(np.uint32), out.cpu().numpy().view(np.uint32)):
             raise RuntimeError("e2e output differs from the device-resident run")
 
-    prods = rsa_products_per_op(spec["bits"], RSA_EXP_PRIVATE_CRT, window=tune["window"])
+    prods = rsa_products_per_op(spec["bits"], kind, e=key.e, window=tune["window"])
     achieved = prods * count / (ms / 1e3) / 1e12
     peak = derived_peak_tprod(SM_COUNT_GB300, 2070.0)
-    prof = PROFILED_TRAFFIC.get(args.workload)
+    prof = PROFILED_TRAFFIC.get(args.workload) if args.kind == "crt" else None
     traffic = None
     if (prof and prof["window"] == tune["window"] and tune["variant"] in (0, 1) and tune["threads_per_op"] == 1
             and prof["stamp"] == kernel_stamp()):
@@ -471,18 +550,18 @@ def main():
         roofline["frac_at_measured_clock"] = achieved / derived_peak_tprod(SM_COUNT_GB300, clk["sm_mhz"])
 
     line = {
-        "metric": "RSA-%d CRT decrypts/sec" % spec["bits"], "value": value, "unit": "decrypts/s",
+        "metric": metric, "value": value, "unit": unit,
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic", "gpu_launches": int(launches),
-        "config": {"workload": spec["desc"], "window": tune["window"], "warps_per_cta": tune["warps_per_cta"],
+        "config": {"workload": workload_desc(spec["bits"], count, args.kind), "window": tune["window"], "warps_per_cta": tune["warps_per_cta"],
                    "ctas_per_sm": tune["ctas_per_sm"], "variant": tune["variant"],
                    "threads_per_op": tune["threads_per_op"], "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "dp%d (independent batches per GPU)" % ws},
         "wall_s": wall, "clocks": clk, "roofline": roofline, "e2e": e2e,
     }
     if rank == 0 and ws == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(key, rows)
+        line["cpu_baseline"] = cpu_baseline(key, rows, public=(kind == RSA_EXP_PUBLIC))
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
