@@ -233,7 +233,11 @@ typedef struct rsa_tuning {
     int32_t variant;       /* squarings of private exponents: 1 = through the general
                               CIOS multiply, 2 = separated square + reduction (fewer
                               word products, but a larger instruction footprint; slower
-                              on GB300); 0 = automatic (currently 1) */
+                              on GB300); 3 = RSA-2048 CRT only: the Montgomery reduction
+                              on the tensor cores (tcgen05 MMAs of byte digits against
+                              Toeplitz matrices of p, q and -p^-1, -q^-1 mod 2^1024;
+                              the per-message product stays on the CUDA cores);
+                              0 = automatic (currently 1) */
     int32_t threads_per_op; /* lanes cooperating on one operation: 1, 2 or 4 (numbers
                               sliced over the lanes, warp-shuffle carries); 0 = automatic */
 } rsa_tuning;
@@ -257,6 +261,18 @@ int rsa_get_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, rsa_tuning *t)
  * Synchronous; allocates scratch from the context's budget. */
 int rsa_autotune(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint64_t count, const char *cache_path,
                  rsa_tuning *best, double *best_ms);
+
+/* Tensor-core operands of one 1024-bit prime m (variant 3), exactly as built at
+ * key load: two K-major fp16 matrices in the no-swizzle core-matrix layout
+ * ([k/8][row/8][row%8][k%8]), K = 144 (128 byte digits + a 16-column bias block
+ * of the value 2048):
+ *   bytes [0, 36864):     128 rows, row n, column k < 128: byte n-k of -m^-1 mod 2^1024
+ *   bytes [36864, 78336): 144 rows, row j, column k < 128: byte 112+j-k of m
+ * (0 where the byte index is outside 0..127).  m: 32 limbs, little-endian, odd.
+ * out: host buffer of at least RSA_TC_IMAGE_BYTES bytes.  No GPU is used.
+ * Errors: RSA_ERR_ARG (null pointer, short buffer, even m). */
+#define RSA_TC_IMAGE_BYTES 78336
+int rsa_tc_operand_image(const uint32_t *m, void *out, size_t out_bytes);
 
 /* Counters since context creation. */
 typedef struct rsa_stats {

@@ -22,7 +22,8 @@ from ._lib import (RSA_ERR_ARG, RSA_ERR_CUDA, RSA_ERR_KEY, RSA_ERR_NOMEM, RSA_ER
 
 __all__ = [
     "RsaContext", "RsaError", "int_to_limbs", "limbs_to_int",
-    "rsa_ctx_create", "rsa_ctx_destroy", "rsa_keyload", "rsa_key_record", "rsa_keyunload", "rsa_key_info",
+    "rsa_ctx_create", "rsa_ctx_destroy", "rsa_keyload", "rsa_key_record", "rsa_tc_operand_image",
+    "rsa_keyunload", "rsa_key_info",
     "rsa_modexp_key", "rsa_modexp_batch", "rsa_modexp_key_host", "rsa_modexp_batch_host",
     "rsa_sync", "rsa_last_error", "rsa_set_tuning", "rsa_get_tuning", "rsa_get_stats",
     "rsa_products_per_op", "rsa_imad_probe", "rsa_crt_decrypt_noalloc", "rsa_autotune",
@@ -114,6 +115,18 @@ def rsa_key_record(nbits: int, n: int, e: int, d: int | None = None, p: int | No
     check(_lib.lib().rsa_key_record(nbits, _ptr(na), _ptr(ea), el, _ptr(da), _ptr(pa), _ptr(qa), _ptr(rec),
                                     rec.size, ctypes.byref(words)))
     return rec
+
+
+RSA_TC_IMAGE_BYTES = 78336
+
+
+def rsa_tc_operand_image(m: int) -> np.ndarray:
+    """Host-only: the tensor-core operand images (uint8, RSA_TC_IMAGE_BYTES) of a
+    1024-bit odd prime m, as built at key load for the variant-3 CRT path."""
+    ma = int_to_limbs(m, 32)
+    out = np.zeros(RSA_TC_IMAGE_BYTES, dtype=np.uint8)
+    check(_lib.lib().rsa_tc_operand_image(_ptr(ma), _ptr(out), out.size))
+    return out
 
 
 def rsa_keyunload(ctx: int, key_id: int) -> None:

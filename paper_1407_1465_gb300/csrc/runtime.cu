@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "crt_tc.h"
 #include "keyprep.h"
 #include "keyrec.h"
 #include "kernels.cuh"
@@ -71,14 +72,16 @@ Workspace &Ctx::ws(cudaStream_t s) { return workspaces[s]; }
 Ctx::~Ctx() {
   cudaSetDevice(device);
   cudaDeviceSynchronize();
-  for (auto &k : keys)
+  for (auto &k : keys) {
     if (k.d_rec) cudaFree(k.d_rec);
+    if (k.d_tc) cudaFree(k.d_tc);
+  }
   for (auto &kv : workspaces) kv.second.free_all();
   free_extra();
 }
 
 void Workspace::free_all() {
-  for (DevBuf *b : {&tables, &io_in, &io_out, &io_status, &aux0, &aux1, &aux2, &aux3}) {
+  for (DevBuf *b : {&tables, &io_in, &io_out, &io_status, &aux0, &aux1, &aux2, &aux3, &halves}) {
     if (b->ptr) cudaFree(b->ptr);
     b->ptr = nullptr;
     b->bytes = 0;
@@ -166,6 +169,23 @@ int Ctx::run_key(const KeySlot &k, int kind, uint64_t count, const uint32_t *msg
     return RSA_OK;
   }
   const Tune t = tune_for(k.nbits, kind);
+  if (kind == RSA_EXP_PRIVATE_CRT && t.variant == 3) {
+    // Montgomery reduction on the tensor cores (crt_tc.cu): 2048-bit keys only
+    if (L != 2 * (uint32_t)tcr::kH || !k.d_tc)
+      return set_error(RSA_ERR_UNSUPPORTED, "the tensor-core CRT path needs a 2048-bit key with p and q");
+    if (count > 0xFFFFFFFFull) return set_error(RSA_ERR_ARG, "count out of range");
+    const int grid = tcr::tc_grid((uint32_t)count, sm_count);
+    int rc = ensure(w.tables, tcr::tc_tables_bytes(grid));
+    if (rc) return rc;
+    rc = ensure(w.halves, tcr::tc_halves_bytes((uint32_t)count));
+    if (rc) return rc;
+    e = tcr::launch_crt_tc(k.d_rec, k.d_tc, msgs, out, status, (uint32_t)count, grid, w.tables.ptr, w.halves.ptr, s);
+    if (e != cudaSuccess) return cuda_error(e, "launch crt_tc kernels");
+    stats.kernel_launches += 2;
+    last_grid = grid;
+    last_threads = tcr::kThreads;
+    return RSA_OK;
+  }
   if (t.tpo > 1 && kind == RSA_EXP_PRIVATE_CRT) {
     const int H = (int)L / 2, T = t.tpo;
     const void *fn = crt_kernel_t_fn(H, T, t.window);
@@ -333,6 +353,13 @@ static int make_record(uint32_t nbits, const uint32_t *n, const uint32_t *e, uin
   return RSA_OK;
 }
 
+int rsa_tc_operand_image(const uint32_t *m, void *out, size_t out_bytes) {
+  if (!m || !out) return set_error(RSA_ERR_ARG, "null argument");
+  if (out_bytes < tcr::kImgPrime) return set_error(RSA_ERR_ARG, "output buffer too small");
+  if (!tcr::build_tc_image(m, static_cast<uint8_t *>(out))) return set_error(RSA_ERR_ARG, "modulus must be odd");
+  return RSA_OK;
+}
+
 int rsa_key_record(uint32_t nbits, const uint32_t *n, const uint32_t *e, uint32_t e_limbs, const uint32_t *d,
                    const uint32_t *p, const uint32_t *q, uint32_t *rec, size_t rec_capacity_words,
                    size_t *rec_words) {
@@ -374,6 +401,26 @@ int rsa_keyload(rsa_ctx *ctx, uint32_t nbits, const uint32_t *n, const uint32_t 
     c->release(bytes);
     return cuda_error(ce, "cudaMemcpy key record");
   }
+  // tensor-core operand images of q and p for the RSA-2048 CRT path
+  void *dtc = nullptr;
+  size_t tc_bytes = 0;
+  if (L == 2 * (uint32_t)tcr::kH && (flags & KEY_HAS_CRT)) {
+    constexpr KeyLayout lay(2 * tcr::kH);
+    std::vector<uint8_t> img(tcr::kImgKey);
+    const bool ok = tcr::build_tc_image(rec.data() + lay.q, img.data()) &&
+                    tcr::build_tc_image(rec.data() + lay.p, img.data() + tcr::kImgPrime);
+    if (ok && c->reserve(img.size()) == RSA_OK) {
+      if (cudaMalloc(&dtc, img.size()) == cudaSuccess &&
+          cudaMemcpy(dtc, img.data(), img.size(), cudaMemcpyHostToDevice) == cudaSuccess) {
+        tc_bytes = img.size();
+      } else {
+        if (dtc) cudaFree(dtc);
+        dtc = nullptr;
+        cudaGetLastError();
+        c->release(img.size());
+      }
+    }
+  }
   int32_t id = -1;
   for (size_t i = 0; i < c->keys.size(); ++i)
     if (!c->keys[i].used) {
@@ -392,6 +439,8 @@ int rsa_keyload(rsa_ctx *ctx, uint32_t nbits, const uint32_t *n, const uint32_t 
   k.d_rec = dptr;
   k.bytes = bytes;
   k.host_rec = rec;
+  k.d_tc = dtc;
+  k.tc_bytes = tc_bytes;
   c->key_epoch++;
   *key_id_out = id;
   return RSA_OK;
@@ -408,6 +457,10 @@ int rsa_keyunload(rsa_ctx *ctx, int32_t key_id) {
   KeySlot &k = c->keys[key_id];
   cudaFree(k.d_rec);
   c->release(k.bytes);
+  if (k.d_tc) {
+    cudaFree(k.d_tc);
+    c->release(k.tc_bytes);
+  }
   k = KeySlot();
   c->key_epoch++;
   return RSA_OK;
@@ -501,7 +554,7 @@ int rsa_set_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, const rsa_tuni
     return set_error(RSA_ERR_ARG, "window out of range");
   if (t->warps_per_cta < 0 || t->warps_per_cta > 8 || t->ctas_per_sm < 0)
     return set_error(RSA_ERR_ARG, "bad launch shape");
-  if (t->variant < 0 || t->variant > 2) return set_error(RSA_ERR_ARG, "variant must be 0, 1 or 2");
+  if (t->variant < 0 || t->variant > 3) return set_error(RSA_ERR_ARG, "variant must be 0 .. 3");
   if (!(t->threads_per_op == 0 || t->threads_per_op == 1 || t->threads_per_op == 2 || t->threads_per_op == 4))
     return set_error(RSA_ERR_ARG, "threads_per_op must be 0, 1, 2 or 4");
   if (exp_sel == RSA_EXP_PRIVATE_CRT && (t->warps_per_cta & 1))

@@ -26,6 +26,7 @@ struct Workspace {
   DevBuf tables;                  // window tables of the private-exponent kernels
   DevBuf io_in, io_out, io_status;  // host-buffer entry points
   DevBuf aux0, aux1, aux2, aux3;  // ragged-batch planning buffers
+  DevBuf halves;                  // tensor-core CRT path: per-prime results between its two kernels
   void free_all();
 };
 
@@ -35,6 +36,8 @@ struct KeySlot {
   uint32_t *d_rec = nullptr;      // device key record (keyrec.h)
   size_t bytes = 0;
   std::vector<uint32_t> host_rec; // host copy of the record
+  void *d_tc = nullptr;           // tensor-core operand images (2048-bit keys with p, q)
+  size_t tc_bytes = 0;
 };
 
 struct Tune {
