@@ -267,11 +267,11 @@ int rsa_autotune(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint64_t count, 
  * ([k/8][row/8][row%8][k%8]), K = 144 (128 byte digits + a 16-column bias block
  * of the value 2048):
  *   bytes [0, 36864):     128 rows, row n, column k < 128: byte n-k of -m^-1 mod 2^1024
- *   bytes [36864, 78336): 144 rows, row j, column k < 128: byte 112+j-k of m
+ *   bytes [36864, 73728): 128 rows, row j, column k < 128: byte 124+j-k of m
  * (0 where the byte index is outside 0..127).  m: 32 limbs, little-endian, odd.
  * out: host buffer of at least RSA_TC_IMAGE_BYTES bytes.  No GPU is used.
  * Errors: RSA_ERR_ARG (null pointer, short buffer, even m). */
-#define RSA_TC_IMAGE_BYTES 78336
+#define RSA_TC_IMAGE_BYTES 73728
 int rsa_tc_operand_image(const uint32_t *m, void *out, size_t out_bytes);
 
 /* Counters since context creation. */

@@ -117,7 +117,7 @@ def rsa_key_record(nbits: int, n: int, e: int, d: int | None = None, p: int | No
     return rec
 
 
-RSA_TC_IMAGE_BYTES = 78336
+RSA_TC_IMAGE_BYTES = 73728
 
 
 def rsa_tc_operand_image(m: int) -> np.ndarray:

@@ -4,21 +4,23 @@
 // Decryption follows the CRT route of the library's other kernels:
 // M = C^d mod n computed as m_p = C^dp mod p and m_q = C^dq mod q, then
 // recombined (Garner).  Each half is a constant-time fixed-window
-// exponentiation (Fig. 6 of the paper with k = 4) whose every modular
+// exponentiation (Fig. 6 of the paper with k = W) whose every modular
 // multiplication is a Montgomery product A*B*R^-1 mod m, R = 2^1024.
 //
 // The Montgomery product is split between the two kinds of units:
 //   1. CUDA cores: T = A * B, 32 x 32 limbs, product scanning with PTX carry
 //      chains (one thread per operation).  The low half of T leaves the
 //      registers as byte digits (fp16) in shared memory.
-//   2. Tensor core, MMA 1: mu_cols = T_lo * Toep(m'), the column sums of the
-//      byte convolution of T mod R with m' = -m^-1 mod R (only columns < 128).
+//   2. Tensor core, MMA 1: the column sums of the byte convolution of
+//      T mod R with m' = -m^-1 mod R (columns 0..127).
 //   3. CUDA cores: carry-propagate the columns into the bytes of
 //      mu = T*m' mod R, written back as fp16 digits.
-//   4. Tensor core, MMA 2: the column sums of mu * m for positions 112..255.
-//   5. CUDA cores: the carry out of the low half (ceil of the top four low
-//      columns; the lower ones add less than 2^-8 of a unit), the high half
-//      carry-propagated and added to T_hi, one conditional subtraction of m.
+//   4. Tensor core, MMA 2: the column sums of mu * m for positions 124..251;
+//      positions 252..254 (six byte products) on the CUDA cores.
+//   5. CUDA cores: the carry out of the low half (ceil of positions 124..127
+//      with T's top bytes, over 2^32: the lower positions add less than 2^-8
+//      of a unit), the high half carry-propagated and added to T_hi, one
+//      conditional subtraction of m.
 // m' and m are the same for every message of the batch, which is what makes
 // steps 2 and 4 matrix products (messages x digits) x (digits x digits); the
 // per-message product A*B (step 1) stays on the CUDA cores.  Exactness: the
@@ -26,11 +28,14 @@
 // every column sum is an integer below 2^23 and the fp32 accumulation is exact
 // (tcprep.cpp describes the bias that makes the sums readable as integers).
 //
-// Work layout: one CTA per SM (384 threads), all of one prime; three tiles of
-// 128 operations, each with its own A buffer, 160 TMEM columns, mbarrier and
-// named barrier, run independently, so one tile's MMAs overlap the other
-// tiles' CUDA-core work.  A tile's thread r owns operation r of the tile and
-// TMEM lane r.  The Garner recombination runs afterwards in its own kernel.
+// Work layout: one CTA per SM (512 threads), all of one prime; four tiles of
+// 128 operations, each with its own A buffer, 128 TMEM columns, mbarrier and
+// named barrier, run independently, so one tile's MMAs and carry passes
+// overlap the other tiles' multiplications.  A tile's thread r owns operation
+// r of the tile and TMEM lane r.  The B operand of step 1 is staged in the
+// upper half (k-blocks 8..15) of the thread's own row of the A buffer: the
+// product scan reads limb group g before it overwrites k-block 8 + g.  The
+// Garner recombination runs afterwards in its own kernel.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,32 +51,36 @@ namespace rsagpu {
 namespace tcr {
 
 // ---------------------------------------------------------------- shared memory map (bytes)
-constexpr int kKbA = (kRows / 8) * 128;            // k-block stride of an A buffer (2048)
-constexpr int kKbM = (kN1 / 8) * 128;              // k-block stride of BM (2048)
-constexpr int kKbP = (kN2 / 8) * 128;              // k-block stride of BP (2304)
+constexpr int kKb = (kRows / 8) * 128;              // k-block stride of A buffers, BM and BP (2048)
+static_assert(kN1 == kRows && kN2 == kRows, "all operands have 128 rows");
 constexpr int kOffBm = 0;
 constexpr int kOffBp = kOffBm + (int)kImgBm;
 constexpr int kOffAbias = kOffBp + (int)kImgBp;     // 128 x 16 bias A operand
 constexpr int kOffA = kOffAbias + kRows * 16 * 2;   // kTiles A buffers of 128 x 128 digits
 constexpr int kABytes = kRows * kDig * 2;
-constexpr int kOffStage = kOffA + kTiles * kABytes; // [kH/4][kThreads] uint4
-constexpr int kOffKey = kOffStage + kThreads * kH * 4;
+constexpr int kOffKey = kOffA + kTiles * kABytes;
 // key constants (words): m, R^2, R^3, R mod m, unit, exponent (kH + 4 limbs)
 constexpr int kKm = 0, kKr2 = kH, kKr3 = 2 * kH, kKone = 3 * kH, kKunit = 4 * kH, kKexp = 5 * kH;
 constexpr int kKeyWords = 6 * kH + 4;
-constexpr int kOffCtrl = kOffKey + kKeyWords * 4;   // 3 mbarriers (8 B each), TMEM base at +32
+constexpr int kOffCtrl = kOffKey + kKeyWords * 4;   // kTiles mbarriers (8 B each), TMEM base at +48
 constexpr int kSmem = kOffCtrl + 64;
-static_assert(kOffA % 128 == 0 && kOffStage % 16 == 0 && kOffCtrl % 8 == 0, "alignment");
+static_assert(kOffA % 128 == 0 && kOffKey % 16 == 0 && kOffCtrl % 8 == 0 && kTiles * 8 <= 48, "layout");
 static_assert(kSmem <= 227 * 1024, "shared memory");
 
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kTileCols = 160;                 // >= kN2, per tile
-constexpr uint32_t kIdesc1 = tc::idesc_f16_f32(128, kN1);
-constexpr uint32_t kIdesc2 = tc::idesc_f16_f32(128, kN2);
-constexpr int kNwin = 32 * kH / kWin;               // windows of the 1024-bit exponent
-constexpr int kTblU4 = (1 << kWin) * (kH / 4) * kRows;   // uint4 per tile slot: [entry][g][row]
+constexpr uint32_t kTileCols = 128;
+static_assert(kTiles * kTileCols <= kTmemCols, "TMEM");
+constexpr uint32_t kIdesc = tc::idesc_f16_f32(128, 128);
 constexpr uint32_t kBias = 0x3F000000u;             // fp32 bits of the column bias 1/2
 constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr int kStageKb = 8;                          // the stage: k-blocks 8..15 of the thread's row
+
+template <int W>
+struct Win {
+  static constexpr int kEntries = 1 << W;
+  static constexpr int kNwin = (32 * kH + W - 1) / W;            // windows of the 1024-bit exponent
+  static constexpr int kTblU4 = kEntries * (kH / 4) * kRows;     // uint4 per tile slot: [entry][g][row]
+};
 
 struct HalfArgs {
   const uint32_t *keyrec;
@@ -120,7 +129,10 @@ __device__ __forceinline__ uint32_t mul_emit(uint32_t (&t)[L], const uint32_t (&
 
 __device__ __forceinline__ uint4 lds128a(uint32_t saddr) {
   uint4 v;
-  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(saddr) : "memory");
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(saddr)
+               : "memory");
   return v;
 }
 
@@ -131,7 +143,8 @@ __device__ __forceinline__ uint32_t ccarry(uint32_t x) { return tc::prmt(x, 0u, 
 // column state x) + cin; the carry out returns in cin.  Each group of four
 // columns becomes one limb of byte digits.
 template <int NL>
-__device__ __forceinline__ void add_columns(uint32_t (&t)[kH], int j0, const uint32_t *v, uint32_t &x, uint32_t &cin) {
+__device__ __forceinline__ void add_columns(uint32_t (&t)[kH], int j0, const uint32_t *v, uint32_t &x,
+                                            uint32_t &cin) {
   uint32_t X[NL];
 #pragma unroll
   for (int i = 0; i < NL; ++i) {
@@ -161,11 +174,36 @@ struct Tile {
   bool dead;   // the tile voted to stop: uniform across its 128 threads
 };
 
+// Issue the nine MMAs of one product (bias block, then 8 K-steps of 16 digits)
+// and the commit; leader thread only.
+__device__ __forceinline__ void issue_mmas(const Tile &ts, uint32_t b_off) {
+  tc::fence_after_sync();
+  tc::mma_f16(ts.tmem, tc::sdesc(ts.sb + kOffAbias, kKb, 128), tc::sdesc(ts.sb + b_off + 16 * kKb, kKb, 128),
+              kIdesc, 0u);
+#pragma unroll 1
+  for (int s = 0; s < kDig / 16; ++s)
+    tc::mma_f16(ts.tmem, tc::sdesc(ts.abuf + s * 2 * kKb, kKb, 128),
+                tc::sdesc(ts.sb + b_off + s * 2 * kKb, kKb, 128), kIdesc, 1u);
+  tc::commit(ts.mbar);
+}
+
+__device__ __forceinline__ void wait_mmas(Tile &ts) {
+  if (!tc::mbar_wait(ts.mbar, ts.phase, kWaitLimit)) {
+    ts.err = true;
+    ts.pending = ts.phase;
+  }
+  ts.phase ^= 1u;
+  tc::fence_after_sync();
+}
+
 // A = A * B * R^-1 mod m (A < R, B < m; result < m).  B: kH limbs in shared
-// memory at bsa, four limbs per 16 bytes, consecutive groups `bstr` bytes apart.
+// memory at bsa, four limbs per 16 bytes, consecutive groups `bstr` bytes
+// apart (the thread's stage, or a key constant).
 __device__ __forceinline__ void mont_step(uint32_t (&A)[kH], uint32_t bsa, uint32_t bstr, Tile &ts,
                                           const uint32_t *Ms) {
-  // 1. T = A * B: the low 32 limbs leave as digits, t ends as T_hi
+  // 1. T = A * B: the low 32 limbs leave as digits, t ends as T_hi.  Block i0
+  //    reads B groups i0/4, i0/4+1 (stage k-blocks 8 + i0/4 ..) before it
+  //    writes k-blocks i0/2 .. i0/2+3, so the stage is never overwritten early.
   uint32_t t[kH];
 #pragma unroll
   for (int j = 0; j < kH; ++j) t[j] = 0u;
@@ -184,10 +222,10 @@ __device__ __forceinline__ void mont_step(uint32_t (&A)[kH], uint32_t bsa, uint3
     e[6] = mul_emit<kH>(t, A, b1.z);
     e[7] = mul_emit<kH>(t, A, b1.w);
     // limbs i0..i0+7 are digits 4*i0 .. 4*i0+31: k-blocks i0/2 .. i0/2+3
-    const uint32_t ad = ts.arow + (uint32_t)(i0 >> 1) * kKbA;
+    const uint32_t ad = ts.arow + (uint32_t)(i0 >> 1) * kKb;
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-      tc::sts128(ad + q * kKbA, tc::prmt(e[2 * q], 0u, 0x4140u), tc::prmt(e[2 * q], 0u, 0x4342u),
+      tc::sts128(ad + q * kKb, tc::prmt(e[2 * q], 0u, 0x4140u), tc::prmt(e[2 * q], 0u, 0x4342u),
                  tc::prmt(e[2 * q + 1], 0u, 0x4140u), tc::prmt(e[2 * q + 1], 0u, 0x4342u));
     top = e[7];
   }
@@ -196,95 +234,76 @@ __device__ __forceinline__ void mont_step(uint32_t (&A)[kH], uint32_t bsa, uint3
   tc::fence_before_sync();
   ts.dead = tc::bar_red_or(ts.bar_id, kRows, ts.err);
   if (ts.dead) return;
-  if (ts.leader) {
-    tc::fence_after_sync();
-    tc::mma_f16(ts.tmem, tc::sdesc(ts.sb + kOffAbias, kKbA, 128), tc::sdesc(ts.sb + kOffBm + 16 * kKbM, kKbM, 128),
-                kIdesc1, 0u);
-#pragma unroll 1
-    for (int s = 0; s < kDig / 16; ++s)
-      tc::mma_f16(ts.tmem, tc::sdesc(ts.abuf + s * 2 * kKbA, kKbA, 128),
-                  tc::sdesc(ts.sb + kOffBm + s * 2 * kKbM, kKbM, 128), kIdesc1, 1u);
-    tc::commit(ts.mbar);
-  }
-  if (!tc::mbar_wait(ts.mbar, ts.phase, kWaitLimit)) {
-    ts.err = true;
-    ts.pending = ts.phase;
-  }
-  ts.phase ^= 1u;
-  tc::fence_after_sync();
-  // 3. mu = carry-propagated columns mod R, back to shared memory as digits
+  if (ts.leader) issue_mmas(ts, kOffBm);
+  wait_mmas(ts);
+  // 3. mu = carry-propagated columns mod R, back to shared memory as digits;
+  //    its top digits are kept for positions 252..254 of mu * m
+  uint32_t mu_top = 0u;   // [mu_124, mu_125, mu_126, mu_127]
   {
     uint32_t x = kBias;
 #pragma unroll 1
-    for (int c0 = 0; c0 < kDig; c0 += 32) {
-      uint32_t v[32];
-      tc::ld32(ts.taddr + (uint32_t)c0, v);
+    for (int c0 = 0; c0 < kDig; c0 += 16) {
+      uint32_t v[16];
+      tc::ld16(ts.taddr + (uint32_t)c0, v);
       tc::wait_ld();
-      uint32_t w[16];
+      uint32_t w[8];
 #pragma unroll
-      for (int j = 0; j < 32; j += 2) {
+      for (int j = 0; j < 16; j += 2) {
         const uint32_t x0 = v[j] + ccarry(x);
         const uint32_t x1 = v[j + 1] + ccarry(x0);
         w[j >> 1] = tc::prmt(x0, x1, 0xB4B0u);   // [x0.b0, 0, x1.b0, 0]: two fp16 digits
         x = x1;
       }
-      const uint32_t ad = ts.arow + (uint32_t)(c0 >> 3) * kKbA;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) tc::sts128(ad + q * kKbA, w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+      const uint32_t ad = ts.arow + (uint32_t)(c0 >> 3) * kKb;
+      tc::sts128(ad, w[0], w[1], w[2], w[3]);
+      tc::sts128(ad + kKb, w[4], w[5], w[6], w[7]);
+      mu_top = tc::prmt(w[6], w[7], 0x6420u);   // in the last chunk: digits 124..127
     }
   }
-  // 4. MMA 2: columns 112..255 of mu * m
+  // 4. MMA 2: positions 124..251 of mu * m
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
   ts.dead = tc::bar_red_or(ts.bar_id, kRows, ts.err);
   if (ts.dead) return;
-  if (ts.leader) {
-    tc::fence_after_sync();
-    tc::mma_f16(ts.tmem, tc::sdesc(ts.sb + kOffAbias, kKbA, 128), tc::sdesc(ts.sb + kOffBp + 16 * kKbP, kKbP, 128),
-                kIdesc2, 0u);
-#pragma unroll 1
-    for (int s = 0; s < kDig / 16; ++s)
-      tc::mma_f16(ts.tmem, tc::sdesc(ts.abuf + s * 2 * kKbA, kKbA, 128),
-                  tc::sdesc(ts.sb + kOffBp + s * 2 * kKbP, kKbP, 128), kIdesc2, 1u);
-    tc::commit(ts.mbar);
+  if (ts.leader) issue_mmas(ts, kOffBp);
+  // positions 252..255 while the tensor core works: sum of mu_i * m_j, i + j = position
+  uint32_t top_cols[4];
+  {
+    const uint32_t mt = Ms[kH - 1];
+    const uint32_t a5 = (mu_top >> 8) & 0xFFu, a6 = (mu_top >> 16) & 0xFFu, a7 = mu_top >> 24;
+    const uint32_t b5 = (mt >> 8) & 0xFFu, b6 = (mt >> 16) & 0xFFu, b7 = mt >> 24;
+    top_cols[0] = kBias + a5 * b7 + a6 * b6 + a7 * b5;
+    top_cols[1] = kBias + a6 * b7 + a7 * b6;
+    top_cols[2] = kBias + a7 * b7;
+    top_cols[3] = kBias;
   }
-  if (!tc::mbar_wait(ts.mbar, ts.phase, kWaitLimit)) {
-    ts.err = true;
-    ts.pending = ts.phase;
-  }
-  ts.phase ^= 1u;
-  tc::fence_after_sync();
+  wait_mmas(ts);
   // 5. U = T_hi + (T_lo + mu*m) / R, then one conditional subtraction.  The
   // columns are carry-propagated 4 at a time into limbs that are added to T_hi
   // right away (the carry between chunks is kept in a register: cin).
   uint32_t x, cin = 0u;
   {
-    uint32_t v[32];
-    tc::ld32(ts.taddr + 0u, v);   // positions 112..143
+    uint32_t v[16];
+    tc::ld16(ts.taddr + 0u, v);   // positions 124..139
     tc::wait_ld();
     // carry out of the low half: ceil of positions 124..127 (with T's top limb) / 2^32
-    const uint32_t y0 = v[12] + (top & 0xFFu);
-    const uint32_t y1 = v[13] + ((top >> 8) & 0xFFu) + ccarry(y0);
-    const uint32_t y2 = v[14] + ((top >> 16) & 0xFFu) + ccarry(y1);
-    const uint32_t y3 = v[15] + (top >> 24) + ccarry(y2);
+    const uint32_t y0 = v[0] + (top & 0xFFu);
+    const uint32_t y1 = v[1] + ((top >> 8) & 0xFFu) + ccarry(y0);
+    const uint32_t y2 = v[2] + ((top >> 16) & 0xFFu) + ccarry(y1);
+    const uint32_t y3 = v[3] + (top >> 24) + ccarry(y2);
     const uint32_t low = (y0 | y1 | y2 | y3) & 0xFFu;
     x = (ccarry(y3) + (low != 0u ? 1u : 0u)) << 8;   // so that ccarry(x) is that carry
-    add_columns<4>(t, 0, v + 16, x, cin);
+    add_columns<3>(t, 0, v + 4, x, cin);              // positions 128..139: limbs 0..2
   }
 #pragma unroll
-  for (int c = 1; c < 4; ++c) {
-    uint32_t v[32];
-    tc::ld32(ts.taddr + (uint32_t)(32 * c), v);
-    tc::wait_ld();
-    add_columns<8>(t, 4 + 8 * (c - 1), v, x, cin);
-  }
-  {
+  for (int c = 1; c < 8; ++c) {
     uint32_t v[16];
-    tc::ld16(ts.taddr + 128u, v);   // positions 240..255
+    tc::ld16(ts.taddr + (uint32_t)(16 * c), v);       // positions 124 + 16c .. +15
     tc::wait_ld();
-    add_columns<4>(t, 28, v, x, cin);
+    add_columns<4>(t, 3 + 4 * (c - 1), v, x, cin);    // limbs 3 + 4(c-1) .. +3
   }
   tc::fence_before_sync();   // this tile's TMEM reads precede the next MMA (ordered by the next barrier)
+  add_columns<1>(t, kH - 1, top_cols, x, cin);        // positions 252..255: limb 31
   uint32_t u[kH + 2];
 #pragma unroll
   for (int j = 0; j < kH; ++j) u[j] = t[j];
@@ -293,19 +312,22 @@ __device__ __forceinline__ void mont_step(uint32_t (&A)[kH], uint32_t bsa, uint3
   final_sub<kH>(A, u, NSmem<kH>{Ms});
 }
 
-// ---------------------------------------------------------------- table helpers (global, per tile slot)
+// ---------------------------------------------------------------- table and stage helpers
+// Table of one tile slot in global memory: [entry][g][row] of uint4 (g = limb / 4).
+template <int W>
 __device__ __forceinline__ void tbl_store(uint4 *tbl, int e, const uint32_t (&A)[kH]) {
 #pragma unroll
   for (int g = 0; g < kH / 4; ++g)
     tbl[(e * (kH / 4) + g) * kRows] = make_uint4(A[4 * g], A[4 * g + 1], A[4 * g + 2], A[4 * g + 3]);
 }
 // stage <- T[d], reading every entry (constant time)
-__device__ __forceinline__ void tbl_select(uint4 *stage, const uint4 *tbl, uint32_t d) {
+template <int W>
+__device__ __forceinline__ void tbl_select(uint8_t *stage, const uint4 *tbl, uint32_t d) {
 #pragma unroll 1
   for (int g = 0; g < kH / 4; ++g) {
     uint4 acc = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-    for (int e = 0; e < (1 << kWin); ++e) {
+    for (int e = 0; e < (1 << W); ++e) {
       const uint4 v = tbl[(e * (kH / 4) + g) * kRows];
       const uint32_t msk = 0u - (uint32_t)((uint32_t)e == d);
       acc.x |= v.x & msk;
@@ -313,23 +335,30 @@ __device__ __forceinline__ void tbl_select(uint4 *stage, const uint4 *tbl, uint3
       acc.z |= v.z & msk;
       acc.w |= v.w & msk;
     }
-    stage[g * kThreads] = acc;
+    *reinterpret_cast<uint4 *>(stage + g * kKb) = acc;
   }
 }
-__device__ __forceinline__ void stage_put(uint4 *stage, const uint32_t (&A)[kH]) {
+__device__ __forceinline__ void stage_from(uint8_t *stage, const uint4 *src, int src_stride) {
 #pragma unroll
-  for (int g = 0; g < kH / 4; ++g) stage[g * kThreads] = make_uint4(A[4 * g], A[4 * g + 1], A[4 * g + 2], A[4 * g + 3]);
+  for (int g = 0; g < kH / 4; ++g) *reinterpret_cast<uint4 *>(stage + g * kKb) = src[g * src_stride];
 }
-__device__ __forceinline__ void stage_get(uint32_t (&A)[kH], const uint4 *stage) {
+__device__ __forceinline__ void stage_put(uint8_t *stage, const uint32_t (&A)[kH]) {
+#pragma unroll
+  for (int g = 0; g < kH / 4; ++g)
+    *reinterpret_cast<uint4 *>(stage + g * kKb) = make_uint4(A[4 * g], A[4 * g + 1], A[4 * g + 2], A[4 * g + 3]);
+}
+__device__ __forceinline__ void stage_get(uint32_t (&A)[kH], const uint8_t *stage) {
 #pragma unroll
   for (int g = 0; g < kH / 4; ++g) {
-    const uint4 v = stage[g * kThreads];
+    const uint4 v = *reinterpret_cast<const uint4 *>(stage + g * kKb);
     A[4 * g] = v.x; A[4 * g + 1] = v.y; A[4 * g + 2] = v.z; A[4 * g + 3] = v.w;
   }
 }
 
 // ---------------------------------------------------------------- exponentiation kernel (both primes)
+template <int W>
 __global__ void __launch_bounds__(kThreads, 1) crt_tc_half_kernel(HalfArgs a) {
+  using Wn = Win<W>;
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int slot = warp >> 2;                   // tile slot 0 .. kTiles-1
@@ -339,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, 1) crt_tc_half_kernel(HalfArgs a) {
   const uint32_t sb = tc::smem_addr(smem);
   uint32_t *ctrl = reinterpret_cast<uint32_t *>(smem + kOffCtrl);
 
-  if (warp == 0) tc::tmem_alloc(sb + kOffCtrl + 32, kTmemCols);
+  if (warp == 0) tc::tmem_alloc(sb + kOffCtrl + 48, kTmemCols);
   if (tid == 0) {
     for (int t = 0; t < kTiles; ++t) tc::mbar_init(sb + kOffCtrl + 8 * t, 1u);
     tc::mbar_init_fence();
@@ -367,7 +396,8 @@ __global__ void __launch_bounds__(kThreads, 1) crt_tc_half_kernel(HalfArgs a) {
     uint4 *s4 = reinterpret_cast<uint4 *>(smem + kOffBm);
     for (int i = tid; i < (int)(kImgPrime / 16); i += kThreads) s4[i] = img[i];
     uint4 *ab = reinterpret_cast<uint4 *>(smem + kOffAbias);
-    for (int i = tid; i < kRows * 16 * 2 / 16; i += kThreads) ab[i] = make_uint4(0x01000100u, 0x01000100u, 0x01000100u, 0x01000100u);
+    for (int i = tid; i < kRows * 16 * 2 / 16; i += kThreads)
+      ab[i] = make_uint4(0x01000100u, 0x01000100u, 0x01000100u, 0x01000100u);
   }
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
@@ -378,7 +408,7 @@ __global__ void __launch_bounds__(kThreads, 1) crt_tc_half_kernel(HalfArgs a) {
   ts.sb = sb;
   ts.abuf = sb + kOffA + slot * kABytes;
   ts.arow = ts.abuf + (uint32_t)(r >> 3) * 128 + (uint32_t)(r & 7) * 16;
-  ts.tmem = ctrl[8] + (uint32_t)slot * kTileCols;
+  ts.tmem = ctrl[12] + (uint32_t)slot * kTileCols;
   ts.taddr = ts.tmem + ((uint32_t)((warp & 3) * 32) << 16);
   ts.mbar = sb + kOffCtrl + 8 * slot;
   ts.phase = 0u;
@@ -390,10 +420,9 @@ __global__ void __launch_bounds__(kThreads, 1) crt_tc_half_kernel(HalfArgs a) {
 
   const uint32_t *Ms = kc + kKm;
   const NSmem<kH> N{Ms};
-  uint4 *stage = reinterpret_cast<uint4 *>(smem + kOffStage) + tid;
-  const uint32_t stage_sa = sb + kOffStage + (uint32_t)tid * 16;
-  const uint32_t stage_str = kThreads * 16;
-  uint4 *tbl = a.tables + (size_t)(blockIdx.x * kTiles + slot) * kTblU4 + r;
+  uint8_t *stage = smem + (ts.arow - sb) + kStageKb * kKb;   // this thread's stage (generic pointer)
+  const uint32_t stage_sa = ts.arow + kStageKb * kKb;
+  uint4 *tbl = a.tables + (size_t)(blockIdx.x * kTiles + slot) * Wn::kTblU4 + r;
 
   for (uint32_t tile = cta + a.ctas_per_prime * (uint32_t)slot; tile < a.ntiles;
        tile += a.ctas_per_prime * kTiles) {
@@ -402,45 +431,45 @@ __global__ void __launch_bounds__(kThreads, 1) crt_tc_half_kernel(HalfArgs a) {
     const uint32_t *msg = a.msgs + (size_t)(valid ? row : a.count - 1) * (2 * kH);
     uint32_t A[kH];
     if (!ts.dead) {
-      const int nexp = (kNwin - 1) * (kWin + 1);
-      const int nst = 16 + nexp + (pi == 0 ? 1 : 0);
-      int k = kNwin - 2, s = 0;
+      constexpr int ntab = Wn::kEntries;                  // steps 2 .. ntab-1 build T[2 .. ntab-1]
+      constexpr int nexp = (Wn::kNwin - 1) * (W + 1);
+      const int nst = ntab + nexp + (pi == 0 ? 1 : 0);
+      int k = Wn::kNwin - 2, s = 0;
 #pragma unroll 1
       for (int st = 0; st < nst; ++st) {
-        uint32_t bsa = stage_sa, bstr = stage_str;
+        uint32_t bsa = stage_sa, bstr = kKb;
         if (st == 0) {                      // c_lo * R mod m
           load_row<kH>(A, msg, true);
           bsa = sb + kOffKey + 4 * kKr2;
           bstr = 16;
         } else if (st == 1) {               // c_hi * R^2 mod m
-          tbl_store(tbl, 1, A);
+          tbl_store<W>(tbl, 1, A);
           load_row<kH>(A, msg + kH, true);
           bsa = sb + kOffKey + 4 * kKr3;
           bstr = 16;
-        } else if (st < 16) {               // table T[i] = x^i * R, i = 2 .. 15
+        } else if (st < ntab) {             // table T[i] = x^i * R, i = 2 .. ntab-1
           if (st == 2) {
-#pragma unroll
-            for (int g = 0; g < kH / 4; ++g) stage[g * kThreads] = tbl[(1 * (kH / 4) + g) * kRows];   // c_lo * R
-            mod_add<kH>(A, SmemB{stage, kThreads}, N);   // x * R = c * R mod m
-            tbl_store(tbl, 1, A);
+            stage_from(stage, tbl + 1 * (kH / 4) * kRows, kRows);   // c_lo * R
+            mod_add<kH>(A, SmemB{reinterpret_cast<const uint4 *>(stage), kKb / 16}, N);   // x R = c R mod m
+            tbl_store<W>(tbl, 1, A);
             uint32_t one[kH];
             from_uniform<kH>(one, reinterpret_cast<const uint4 *>(kc + kKone));
-            tbl_store(tbl, 0, one);
-            stage_put(stage, A);
+            tbl_store<W>(tbl, 0, one);
           } else {
-            tbl_store(tbl, st - 1, A);
+            tbl_store<W>(tbl, st - 1, A);
           }
-        } else if (st < 16 + nexp) {        // windows: kWin squarings, then T[digit]
-          if (st == 16) {
-            tbl_store(tbl, 15, A);
-            tbl_select(stage, tbl, exp_digit<kWin>(kc + kKexp, (uint32_t)(kNwin - 1)));
+          stage_from(stage, tbl + 1 * (kH / 4) * kRows, kRows);     // B = x R
+        } else if (st < ntab + nexp) {      // windows: W squarings, then T[digit]
+          if (st == ntab) {
+            tbl_store<W>(tbl, ntab - 1, A);
+            tbl_select<W>(stage, tbl, exp_digit<W>(kc + kKexp, (uint32_t)(Wn::kNwin - 1)));
             stage_get(A, stage);
           }
-          if (s < kWin) {
+          if (s < W) {
             stage_put(stage, A);
             ++s;
           } else {
-            tbl_select(stage, tbl, exp_digit<kWin>(kc + kKexp, (uint32_t)k));
+            tbl_select<W>(stage, tbl, exp_digit<W>(kc + kKexp, (uint32_t)k));
             s = 0;
             --k;
           }
@@ -466,7 +495,7 @@ __global__ void __launch_bounds__(kThreads, 1) crt_tc_half_kernel(HalfArgs a) {
   __syncthreads();
   if (warp == 0) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(ctrl[8], kTmemCols);
+    tc::tmem_dealloc(ctrl[12], kTmemCols);
   }
 }
 
@@ -514,7 +543,9 @@ __global__ void __launch_bounds__(kGThreads) crt_tc_garner_kernel(GarnerArgs a) 
   t[kH + 1] = 0u;
   const uint32_t *qs = ks + lay.q;
   const uint32_t *mrow = a.msgs + (size_t)rr * L;
-  const bool ok = valid && row_below(mrow, ks + lay.n, L) && a.herr[rr] == 0u && a.herr[a.count + rr] == 0u;
+  const bool below = row_below(mrow, ks + lay.n, L);
+  const bool timed_out = a.herr[rr] != 0u || a.herr[a.count + rr] != 0u;
+  const bool ok = valid && below && !timed_out;
   uint4 *orow = reinterpret_cast<uint4 *>(a.out + (size_t)rr * L);
 #pragma unroll 1
   for (int i0 = 0; i0 < kH; i0 += 4) {
@@ -531,13 +562,10 @@ __global__ void __launch_bounds__(kGThreads) crt_tc_garner_kernel(GarnerArgs a) 
   }
 #pragma unroll
   for (int g = 0; g < kH / 4; ++g)
-    if (valid) orow[kH / 4 + g] = ok ? make_uint4(t[4 * g], t[4 * g + 1], t[4 * g + 2], t[4 * g + 3]) : make_uint4(0u, 0u, 0u, 0u);
-  if (valid && a.status) {
-    int32_t st = 0;
-    if (a.herr[rr] != 0u || a.herr[a.count + rr] != 0u) st = -6;        // RSA_ERR_TIMEOUT
-    else if (!row_below(mrow, ks + lay.n, L)) st = -3;                  // RSA_ERR_RANGE
-    a.status[rr] = st;
-  }
+    if (valid)
+      orow[kH / 4 + g] = ok ? make_uint4(t[4 * g], t[4 * g + 1], t[4 * g + 2], t[4 * g + 3])
+                            : make_uint4(0u, 0u, 0u, 0u);
+  if (valid && a.status) a.status[rr] = timed_out ? -6 /* RSA_ERR_TIMEOUT */ : (below ? 0 : -3 /* RSA_ERR_RANGE */);
 }
 
 // ---------------------------------------------------------------- host side
@@ -545,12 +573,16 @@ size_t tc_smem_bytes() { return (size_t)kSmem; }
 
 int tc_grid(uint32_t count, int sm_count) {
   const uint32_t ntiles = (count + kRows - 1) / kRows;
-  const uint32_t want = (ntiles + kTiles - 1) / kTiles;            // CTAs per prime to give every slot a tile
-  const uint32_t per_prime = std::max<uint32_t>(1u, std::min<uint32_t>(want, (uint32_t)std::max(1, sm_count / 2)));
+  const uint32_t want = (ntiles + kTiles - 1) / kTiles;   // CTAs per prime so every slot has a tile
+  const uint32_t per_prime =
+      std::max<uint32_t>(1u, std::min<uint32_t>(want, (uint32_t)std::max(1, sm_count / 2)));
   return (int)(2 * per_prime);
 }
 
-size_t tc_tables_bytes(int grid) { return (size_t)grid * kTiles * kTblU4 * 16; }
+size_t tc_tables_bytes(int grid, int window) {
+  const size_t per_slot = (window == 3) ? (size_t)Win<3>::kTblU4 : (size_t)Win<4>::kTblU4;
+  return (size_t)grid * kTiles * per_slot * 16;
+}
 
 static uint32_t pad_count(uint32_t count) { return (count + 31u) & ~31u; }
 
@@ -558,15 +590,21 @@ size_t tc_halves_bytes(uint32_t count) {
   return (size_t)2 * (kH / 4) * pad_count(count) * 16 + (size_t)2 * count * 4;
 }
 
-cudaError_t launch_crt_tc(const uint32_t *keyrec, const void *image, const uint32_t *msgs, uint32_t *out,
-                          int32_t *status, uint32_t count, int grid, void *tables, void *halves,
-                          cudaStream_t s) {
+template <int W>
+static cudaError_t launch_half(const HalfArgs &h, int grid, cudaStream_t s) {
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(crt_tc_half_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    cudaError_t e = cudaFuncSetAttribute(crt_tc_half_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
+  crt_tc_half_kernel<W><<<grid, kThreads, kSmem, s>>>(h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_crt_tc(const uint32_t *keyrec, const void *image, const uint32_t *msgs, uint32_t *out,
+                          int32_t *status, uint32_t count, int grid, int window, void *tables, void *halves,
+                          cudaStream_t s) {
   const uint32_t cp = pad_count(count);
   HalfArgs h;
   h.keyrec = keyrec;
@@ -579,8 +617,7 @@ cudaError_t launch_crt_tc(const uint32_t *keyrec, const void *image, const uint3
   h.count_pad = cp;
   h.ntiles = (count + kRows - 1) / kRows;
   h.ctas_per_prime = (uint32_t)grid / 2;
-  crt_tc_half_kernel<<<grid, kThreads, kSmem, s>>>(h);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = (window == 3) ? launch_half<3>(h, grid, s) : launch_half<4>(h, grid, s);
   if (e != cudaSuccess) return e;
   GarnerArgs g;
   g.keyrec = keyrec;

@@ -175,11 +175,13 @@ int Ctx::run_key(const KeySlot &k, int kind, uint64_t count, const uint32_t *msg
       return set_error(RSA_ERR_UNSUPPORTED, "the tensor-core CRT path needs a 2048-bit key with p and q");
     if (count > 0xFFFFFFFFull) return set_error(RSA_ERR_ARG, "count out of range");
     const int grid = tcr::tc_grid((uint32_t)count, sm_count);
-    int rc = ensure(w.tables, tcr::tc_tables_bytes(grid));
+    const int win = (t.window == 3) ? 3 : 4;   // windows instantiated for this path
+    int rc = ensure(w.tables, tcr::tc_tables_bytes(grid, win));
     if (rc) return rc;
     rc = ensure(w.halves, tcr::tc_halves_bytes((uint32_t)count));
     if (rc) return rc;
-    e = tcr::launch_crt_tc(k.d_rec, k.d_tc, msgs, out, status, (uint32_t)count, grid, w.tables.ptr, w.halves.ptr, s);
+    e = tcr::launch_crt_tc(k.d_rec, k.d_tc, msgs, out, status, (uint32_t)count, grid, win, w.tables.ptr,
+                           w.halves.ptr, s);
     if (e != cudaSuccess) return cuda_error(e, "launch crt_tc kernels");
     stats.kernel_launches += 2;
     last_grid = grid;

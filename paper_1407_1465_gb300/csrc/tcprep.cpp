@@ -12,7 +12,7 @@
 //
 //   BM (128 x 144): row n (output digit n of mu), column k < 128: m'_{n-k}
 //       (0 outside 0 <= n-k < 128);  columns 128..143: 2048 (bias block)
-//   BP (144 x 144): row j = output position n = 112 + j of mu * m,
+//   BP (128 x 144): row j = output position n = 124 + j of mu * m,
 //       column k < 128: m_{n-k} (0 outside 0 <= n-k < 128);  columns 128..143: 2048
 //
 // The bias block meets a constant A block of 2^-16 (an fp16 subnormal) in the
@@ -46,7 +46,6 @@ size_t core_off(int row, int k, int rows) {
 
 // out = a * b mod 2^(32 n)
 void mul_lo(const uint32_t *a, const uint32_t *b, uint32_t *out, int n) {
-  std::vector<uint64_t> acc(n, 0);
   std::vector<uint32_t> r(n, 0);
   for (int i = 0; i < n; ++i) {
     uint64_t carry = 0;
@@ -108,7 +107,7 @@ bool build_tc_image(const uint32_t *m, uint8_t *out) {
     for (int k = 0; k < kKt; ++k) {
       uint16_t h;
       if (k < kDig) {
-        const int i = (kDig - 16) + j - k;
+        const int i = kN2First + j - k;
         h = (i >= 0 && i < kDig) ? f16_of_int(byte_of(m, i)) : 0;
       } else {
         h = bias;

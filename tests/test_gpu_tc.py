@@ -41,8 +41,8 @@ def keys():
     return ks
 
 
-def run(torch, ctx, kid, kind, rows, variant):
-    ctx.set_tuning(2048, kind, variant=variant)
+def run(torch, ctx, kid, kind, rows, variant, window=0):
+    ctx.set_tuning(2048, kind, variant=variant, window=window)
     try:
         rows = np.ascontiguousarray(rows, dtype=np.uint32)
         t = torch.from_numpy(rows.view(np.int32)).cuda()
@@ -55,12 +55,13 @@ def run(torch, ctx, kid, kind, rows, variant):
         ctx.set_tuning(2048, kind, reset=True)
 
 
-@pytest.mark.parametrize("count", [1, 77, 128, 129, 385, 1000])
-def test_tc_crt_parity(torch_cuda, ctx, keys, count):
+@pytest.mark.parametrize("window", [3, 4])
+@pytest.mark.parametrize("count", [1, 77, 128, 129, 513, 1000])
+def test_tc_crt_parity(torch_cuda, ctx, keys, count, window):
     key = keys[0]
     kid = ctx.keyload(2048, key.n, key.e, key.d, key.p, key.q)
     rows = workloads.messages_below(key.n, count, 31, ("tc", count))
-    got, st = run(torch_cuda, ctx, kid, CRT, rows, TC)
+    got, st = run(torch_cuda, ctx, kid, CRT, rows, TC, window)
     assert (st == 0).all()
     assert np.array_equal(got, oracle.crt_batch(rows, key.d, key.p, key.q))
     ctx.keyunload(kid)
@@ -74,7 +75,7 @@ def test_tc_edge_messages(torch_cuda, ctx, keys):
                 (1 << 2047), (1 << 2047) - 1, n // 2, (1 << 1024) - 1, 1 << 1024, (1 << 32) - 1]
         bad = [n, n + 1, (1 << 2048) - 1]
         rows = np.concatenate([workloads.ints_to_rows(vals, L), workloads.ints_to_rows(bad, L)])
-        got, st = run(torch_cuda, ctx, kid, CRT, rows, TC)
+        got, st = run(torch_cuda, ctx, kid, CRT, rows, TC, 3 if key is keys[1] else 4)
         ng = len(vals)
         assert (st[:ng] == 0).all() and (st[ng:] == -3).all()
         assert np.array_equal(got[:ng], oracle.crt_batch(rows[:ng], key.d, key.p, key.q))

@@ -4,6 +4,8 @@ The variant-3 kernel (crt_tc.cu) reduces T = A*B modulo a 1024-bit prime p
 with Montgomery's method, R = 2^1024, as two matrix products of byte digits:
   mu = (T mod R) * p' mod R,  p' = -p^-1 mod R      (MMA 1 + a carry pass)
   U  = (T + mu * p) / R                              (MMA 2 + a carry pass)
+MMA 2 produces positions 124..251 of mu * p; positions 252..254 (six byte
+products) are added on the CUDA cores.
 The B operands are Toeplitz matrices of p' and p that the host builds at key
 load (rsa_tc_operand_image returns the same bytes).  These tests
   - decode the image (fp16, K-major core-matrix layout) and compare every
@@ -20,7 +22,7 @@ import pytest
 import workloads
 
 R = 1 << 1024
-ROWS_BM, ROWS_BP, KT = 128, 144, 144
+ROWS_BM, ROWS_BP, KT = 128, 128, 144
 
 
 @pytest.fixture(scope="module")
@@ -67,7 +69,7 @@ def test_image_is_the_toeplitz_of_p_and_p_prime(lib, key):
         assert (m * mp) % R == R - 1
         bm, bp = decode(img, 0, ROWS_BM), decode(img, ROWS_BM * KT * 2, ROWS_BP)
         assert np.array_equal(bm, toeplitz(digits(mp), ROWS_BM, 0))
-        assert np.array_equal(bp, toeplitz(digits(m), ROWS_BP, 112))
+        assert np.array_equal(bp, toeplitz(digits(m), ROWS_BP, 124))
 
 
 def test_image_rejects_even_modulus(lib):
@@ -98,13 +100,17 @@ def replay_reduction(T, m, bm, bp):
     mu_d, _ = carry_pass(v.astype(np.int64))
     mu = int.from_bytes(bytes(mu_d.astype(np.uint8)), "little")
     a2 = np.concatenate([mu_d * 2.0 ** -24, bias_a])
-    w = ((a2 @ bp.T) - 0.5) * 2.0 ** 24                     # positions 112..255 of mu * m
+    w = ((a2 @ bp.T) - 0.5) * 2.0 ** 24                     # positions 124..251 of mu * m
     assert np.all(w == np.round(w)) and w.max() < 2 ** 23
     w = w.astype(np.int64)
+    md = digits(m)                                          # positions 252..255: direct products
+    top = [mu_d[125] * md[127] + mu_d[126] * md[126] + mu_d[127] * md[125],
+           mu_d[126] * md[127] + mu_d[127] * md[126], mu_d[127] * md[127], 0]
+    w = np.concatenate([w, np.array(top, dtype=np.int64)])  # positions 124..255
     # carry out of the low half: ceil((positions 124..127 with T's bytes) / 2^32)
-    y, c = carry_pass([w[12 + i] + t_lo[124 + i] for i in range(4)])
+    y, c = carry_pass([w[i] + t_lo[124 + i] for i in range(4)])
     carry = c + (1 if y.any() else 0)
-    hi_d, cout = carry_pass(w[16:], carry)
+    hi_d, cout = carry_pass(w[4:], carry)
     U = (T >> 1024) + int.from_bytes(bytes(hi_d.astype(np.uint8)), "little") + (cout << 1024)
     return mu, carry, U
 
