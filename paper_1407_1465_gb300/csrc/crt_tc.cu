@@ -74,6 +74,12 @@ constexpr uint32_t kIdesc = tc::idesc_f16_f32(128, 128);
 constexpr uint32_t kBias = 0x3F000000u;             // fp32 bits of the column bias 1/2
 constexpr uint32_t kWaitLimit = 1u << 22;
 constexpr int kStageKb = 8;                          // the stage: k-blocks 8..15 of the thread's row
+// Steps ahead of a window's multiplication at which the tile's table is
+// prefetched into L2 (0: no prefetch).  The tables of all tiles in flight
+// exceed L2; each one is needed only at its multiplications.
+#ifndef RSAGPU_TC_PREFETCH
+#define RSAGPU_TC_PREFETCH 0
+#endif
 
 template <int W>
 struct Win {
@@ -196,20 +202,95 @@ __device__ __forceinline__ void wait_mmas(Tile &ts) {
   tc::fence_after_sync();
 }
 
+// Cross products of one row of the square, a_i * a_j for j = j0, j0+2, ... < kH
+// (one parity of j), added at positions i+j (low) and i+j+1 (high) as one
+// carry chain; the chain's carry lands on the position after its last high word.
+template <int I, int J0>
+__device__ __forceinline__ void sq_chain(uint32_t (&c)[2 * kH], const uint32_t (&a)[kH]) {
+  if constexpr (J0 < kH) {
+    c[I + J0] = mad_lo_cc(a[I], a[J0], c[I + J0]);
+    c[I + J0 + 1] = madc_hi_cc(a[I], a[J0], c[I + J0 + 1]);
+#pragma unroll
+    for (int j = J0 + 2; j < kH; j += 2) {
+      c[I + j] = madc_lo_cc(a[I], a[j], c[I + j]);
+      c[I + j + 1] = madc_hi_cc(a[I], a[j], c[I + j + 1]);
+    }
+    constexpr int last = J0 + ((kH - 1 - J0) / 2) * 2;
+    c[I + last + 2] = addc(c[I + last + 2], 0u);
+  }
+}
+
+// T limbs p0, p0+1 of T = A^2 = 2C + D (C: cross products, D: the squares
+// a_k^2 at positions 2k, 2k+1); the doubling shifts in the top bit of the limb
+// below, the carry of the T chain is kept in `tc_carry` between rows.
+__device__ __forceinline__ void sq_emit2(uint32_t c_lo, uint32_t c0, uint32_t c1, uint32_t d0, uint32_t d1,
+                                         uint32_t &tc_carry, uint32_t &t0, uint32_t &t1) {
+  const uint32_t x0 = __funnelshift_l(c_lo, c0, 1), x1 = __funnelshift_l(c0, c1, 1);
+  (void)add_cc(tc_carry, 0xFFFFFFFFu);   // carry flag <- tc_carry
+  t0 = addc_cc(x0, d0);
+  t1 = addc_cc(x1, d1);
+  tc_carry = addc(0u, 0u);
+}
+
+__device__ __forceinline__ void emit_digits(uint32_t arow, int p, uint32_t v) {
+  // limb p of T_lo: digits 4p..4p+3 = k-block p/2, bytes (p%2)*8 .. +7
+  asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(arow + (uint32_t)(p >> 1) * kKb + (uint32_t)(p & 1) * 8),
+               "r"(tc::prmt(v, 0u, 0x4140u)), "r"(tc::prmt(v, 0u, 0x4342u))
+               : "memory");
+}
+
+// T = A^2 for step 1 of the Montgomery product: each cross product once
+// (kH(kH-1)/2 words), doubled, plus the kH squares.  Row i adds a_i * a_j,
+// j > i, in two chains (odd and even j - i); after row i the positions up to
+// 2i+2 are final, so T limbs 2i+1 and 2i+2 are formed and leave: limbs below
+// kH as digits (the thread's A row), the rest into t (= T_hi).  Returns T
+// limb kH-1.
+template <int I>
+__device__ __forceinline__ void sq_rows(uint32_t (&c)[2 * kH], const uint32_t (&a)[kH], uint32_t (&t)[kH],
+                                        uint32_t arow, uint32_t &tc_carry, uint32_t &top) {
+  if constexpr (I < kH - 1) {
+    sq_chain<I, I + 1>(c, a);
+    sq_chain<I, I + 2>(c, a);
+    uint32_t t0, t1;
+    const uint32_t dh = __umulhi(a[I], a[I]), dl = a[I + 1] * a[I + 1];
+    sq_emit2(c[2 * I], c[2 * I + 1], c[2 * I + 2], dh, dl, tc_carry, t0, t1);
+    constexpr int p0 = 2 * I + 1, p1 = 2 * I + 2;
+    if constexpr (p0 < kH) emit_digits(arow, p0, t0); else t[p0 - kH] = t0;
+    if constexpr (p1 < kH) emit_digits(arow, p1, t1); else t[p1 - kH] = t1;
+    if constexpr (p0 == kH - 1) top = t0;
+    if constexpr (p1 == kH - 1) top = t1;
+    sq_rows<I + 1>(c, a, t, arow, tc_carry, top);
+  }
+}
+
+__device__ __forceinline__ uint32_t square_p(uint32_t (&t)[kH], const uint32_t (&a)[kH], uint32_t arow) {
+  uint32_t c[2 * kH];
+#pragma unroll
+  for (int j = 0; j < 2 * kH; ++j) c[j] = 0u;
+  uint32_t tc_carry = 0u, top = 0u;
+  emit_digits(arow, 0, a[0] * a[0]);                       // T_0 = lo(a_0^2)
+  sq_rows<0>(c, a, t, arow, tc_carry, top);
+  // T_63 = 2C_63 (+ the bit from C_62) + hi(a_31^2) + carry
+  t[kH - 1] = __funnelshift_l(c[2 * kH - 2], c[2 * kH - 1], 1) + __umulhi(a[kH - 1], a[kH - 1]) + tc_carry;
+  return top;
+}
+
 // A = A * B * R^-1 mod m (A < R, B < m; result < m).  B: kH limbs in shared
 // memory at bsa, four limbs per 16 bytes, consecutive groups `bstr` bytes
 // apart (the thread's stage, or a key constant).
-__device__ __forceinline__ void mont_step(uint32_t (&A)[kH], uint32_t bsa, uint32_t bstr, Tile &ts,
+__device__ __forceinline__ void mont_step(uint32_t (&A)[kH], bool sq, uint32_t bsa, uint32_t bstr, Tile &ts,
                                           const uint32_t *Ms) {
-  // 1. T = A * B: the low 32 limbs leave as digits, t ends as T_hi.  Block i0
-  //    reads B groups i0/4, i0/4+1 (stage k-blocks 8 + i0/4 ..) before it
-  //    writes k-blocks i0/2 .. i0/2+3, so the stage is never overwritten early.
+  // 1. T = A * B (or A^2 when sq): the low 32 limbs leave as digits, t ends
+  //    as T_hi.  Block i0 of the general product reads B groups i0/4, i0/4+1
+  //    (stage k-blocks 8 + i0/4 ..) before it writes k-blocks i0/2 .. i0/2+3,
+  //    so the stage is never overwritten early.
   uint32_t t[kH];
 #pragma unroll
   for (int j = 0; j < kH; ++j) t[j] = 0u;
   uint32_t top = 0u;
+  if (sq) top = square_p(t, A, ts.arow);
 #pragma unroll 1
-  for (int i0 = 0; i0 < kH; i0 += 8) {
+  for (int i0 = 0; i0 < (sq ? 0 : kH); i0 += 8) {
     const uint4 b0 = lds128a(bsa + (uint32_t)(i0 >> 2) * bstr);
     const uint4 b1 = lds128a(bsa + (uint32_t)((i0 >> 2) + 1) * bstr);
     uint32_t e[8];
@@ -438,6 +519,7 @@ __global__ void __launch_bounds__(kThreads, 1) crt_tc_half_kernel(HalfArgs a) {
 #pragma unroll 1
       for (int st = 0; st < nst; ++st) {
         uint32_t bsa = stage_sa, bstr = kKb;
+        bool sq = false;
         if (st == 0) {                      // c_lo * R mod m
           load_row<kH>(A, msg, true);
           bsa = sb + kOffKey + 4 * kKr2;
@@ -455,6 +537,7 @@ __global__ void __launch_bounds__(kThreads, 1) crt_tc_half_kernel(HalfArgs a) {
             uint32_t one[kH];
             from_uniform<kH>(one, reinterpret_cast<const uint4 *>(kc + kKone));
             tbl_store<W>(tbl, 0, one);
+            sq = true;                        // T[2] = x^2
           } else {
             tbl_store<W>(tbl, st - 1, A);
           }
@@ -466,8 +549,14 @@ __global__ void __launch_bounds__(kThreads, 1) crt_tc_half_kernel(HalfArgs a) {
             stage_get(A, stage);
           }
           if (s < W) {
-            stage_put(stage, A);
+            sq = true;
             ++s;
+            if (RSAGPU_TC_PREFETCH > 0 && s == W + 1 - RSAGPU_TC_PREFETCH && ts.leader) {
+              const uint4 *tb = tbl - r;   // the slot's table: one contiguous block
+#pragma unroll 1
+              for (int e = 0; e < Wn::kEntries; ++e)
+                tc::prefetch_l2(tb + (size_t)e * (kH / 4) * kRows, (kH / 4) * kRows * 16);
+            }
           } else {
             tbl_select<W>(stage, tbl, exp_digit<W>(kc + kKexp, (uint32_t)k));
             s = 0;
@@ -477,7 +566,7 @@ __global__ void __launch_bounds__(kThreads, 1) crt_tc_half_kernel(HalfArgs a) {
           bsa = sb + kOffKey + 4 * kKunit;
           bstr = 16;
         }
-        mont_step(A, bsa, bstr, ts, Ms);
+        mont_step(A, sq, bsa, bstr, ts, Ms);
         if (ts.dead) break;
       }
     }

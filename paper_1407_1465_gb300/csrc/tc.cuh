@@ -116,6 +116,13 @@ __device__ __forceinline__ void ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 __device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// ---------------------------------------------------------------- L2 prefetch (bulk, asynchronous hint)
+// Asks the copy engine to bring [p, p + bytes) into L2; 16-byte aligned, bytes
+// a multiple of 16.  No completion to wait for.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // ---------------------------------------------------------------- misc
 // Named barrier over `nthreads` threads that also ORs a predicate across them.
 __device__ __forceinline__ bool bar_red_or(int id, int nthreads, bool pred) {
