@@ -47,17 +47,21 @@ def workload_desc(bits, count, kind="crt"):
 # crt_kernel_rsa2048_w4_cios_ncu_full.md), valid only while the kernel sources
 # hash to the recorded stamp and the window matches; otherwise reported as null.
 PROFILED_TRAFFIC = {
-    "rsa2048": {"window": 4, "stamp": "2c547aada0325644", "dram_bytes_per_op": 257607.0,
-                "source": "profiles/crt_kernel_rsa2048_w4_cios_ncu_full.md"},
+    # (workload, variant): one ncu capture of that kernel, valid while its sources hash to the stamp
+    ("rsa2048", 3): {"window": 3, "stamp": "9071ad691c33a427", "dram_bytes_per_op": 1282.3,
+                     "files": ["crt_tc.cu", "crt_tc.h", "tc.cuh", "mont.cuh", "kernels.cuh", "keyrec.h"],
+                     "source": "profiles/crt_tc_half_kernel_rsa2048_w3_ncu_full.md"},
+    ("rsa2048", 1): {"window": 4, "stamp": "2c547aada0325644", "dram_bytes_per_op": 257607.0,
+                     "files": ["kernels.cuh", "mont.cuh", "inst_unit.cuh", "inst_h32.cu", "keyrec.h"],
+                     "source": "profiles/crt_kernel_rsa2048_w4_cios_ncu_full.md"},
 }
-KERNEL_FILES = ["kernels.cuh", "mont.cuh", "inst_unit.cuh", "inst_h32.cu", "keyrec.h"]
 
 
-def kernel_stamp() -> str:
+def kernel_stamp(files) -> str:
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1407_1465_gb300", "csrc")
-    for fn in KERNEL_FILES:
+    for fn in files:
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -71,6 +75,34 @@ IMAD_PER_PRODUCT = 2        # a 32x32->64 word product = low half + high half
 def derived_peak_tprod(sm_count: int, sm_mhz: float) -> float:
     """Word products per second (x1e12) the IMAD pipe allows at sm_mhz."""
     return sm_count * IMAD_PER_SM_CLK * sm_mhz * 1e6 / IMAD_PER_PRODUCT / 1e12
+
+
+def tc_work_per_op(bits: int, window: int):
+    """CUDA-core word products and tensor-core FLOPs of one CRT decryption on the
+    tensor-core path (variant 3): per half, 2 input products + 2^w - 2 table
+    products + (windows - 1) * (w + 1) window steps (+1 for q leaving Montgomery
+    form); squarings issue H(H+1)/2 word products, other products H^2; every step
+    runs two fp16 MMAs of 9 K-steps (M = 128 rows: 2 * 128 * 16 FLOPs per row
+    each); Garner adds two CIOS products and one H x H product."""
+    H = bits // 64
+    nwin = -(-32 * H // window)
+    steps_half = (1 << window) + (nwin - 1) * (window + 1)
+    squares_half = 1 + (nwin - 1) * window
+    steps = 2 * steps_half + 1
+    mults = steps - 2 * squares_half
+    issued = 2 * squares_half * (H * (H + 1) // 2) + mults * H * H + 2 * (2 * H * H + H) + H * H
+    tensor_flops = steps * 2 * 9 * 2 * 128 * 16
+    return issued, tensor_flops
+
+
+def measured_bf16_tflops():
+    """Burst dense bf16 TFLOP/s from MEASURED_PEAKS.json (fp16 runs at the same
+    rate), else the fallback figure for GB300."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
 
 
 class ClockSampler:
@@ -532,10 +564,10 @@ def main():
     prods = rsa_products_per_op(spec["bits"], kind, e=key.e, window=tune["window"])
     achieved = prods * count / (ms / 1e3) / 1e12
     peak = derived_peak_tprod(SM_COUNT_GB300, 2070.0)
-    prof = PROFILED_TRAFFIC.get(args.workload) if args.kind == "crt" else None
+    prof = PROFILED_TRAFFIC.get((args.workload, tune["variant"])) if args.kind == "crt" else None
     traffic = None
-    if (prof and prof["window"] == tune["window"] and tune["variant"] in (0, 1) and tune["threads_per_op"] == 1
-            and prof["stamp"] == kernel_stamp()):
+    if (prof and prof["window"] == tune["window"] and tune["threads_per_op"] == 1
+            and prof["stamp"] == kernel_stamp(prof["files"])):
         traffic = prof["dram_bytes_per_op"] * count
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tprod/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_unit": "DRAM bytes per launch",
@@ -544,10 +576,21 @@ def main():
                 "peak_note": "derived from unit counts and clock: 152 SMs x 64 IMAD lanes/clk x 2070 MHz / 2 IMAD "
                              "(low + high half) per 32x32->64 word product; measured on GB300 the high-half "
                              "multiply issues at about half rate, so carry-chain code tops out near "
-                             "6.6-6.7 T products/s (DESIGN.md section 5)",
+                             "6.6-6.7 T products/s",
                 "products_per_op": prods}
     if clk.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = achieved / derived_peak_tprod(SM_COUNT_GB300, clk["sm_mhz"])
+    if tune["variant"] == 3 and args.kind == "crt":
+        issued, tflops_op = tc_work_per_op(spec["bits"], tune["window"])
+        tpk, tsrc = measured_bf16_tflops()
+        t_ach = tflops_op * count / (ms / 1e3) / 1e12
+        roofline["issued_products_per_op"] = issued
+        roofline["issued_achieved"] = issued * count / (ms / 1e3) / 1e12
+        roofline["issued_frac"] = roofline["issued_achieved"] / peak
+        roofline["tensor"] = {"achieved": t_ach, "peak": tpk, "unit": "TFLOP/s", "frac": t_ach / tpk,
+                              "flops_per_op": tflops_op, "peak_source": tsrc + " dense bf16 (fp16 same rate)"}
+        roofline["note"] = ("tensor-core path: the Montgomery reductions run as fp16 MMAs, so the algorithmic "
+                            "CIOS count can exceed the IMAD peak; issued_* is the CUDA-core work actually run")
 
     line = {
         "metric": metric, "value": value, "unit": unit,

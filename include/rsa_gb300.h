@@ -236,8 +236,9 @@ typedef struct rsa_tuning {
                               on GB300); 3 = RSA-2048 CRT only: the Montgomery reduction
                               on the tensor cores (tcgen05 MMAs of byte digits against
                               Toeplitz matrices of p, q and -p^-1, -q^-1 mod 2^1024;
-                              the per-message product stays on the CUDA cores);
-                              0 = automatic (currently 1) */
+                              the per-message product stays on the CUDA cores; windows
+                              3 and 4); 0 = automatic: 3 for RSA-2048 CRT (window 3),
+                              1 otherwise */
     int32_t threads_per_op; /* lanes cooperating on one operation: 1, 2 or 4 (numbers
                               sliced over the lanes, warp-shuffle carries); 0 = automatic */
 } rsa_tuning;
@@ -251,7 +252,8 @@ int rsa_set_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, const rsa_tuni
 int rsa_get_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, rsa_tuning *t);
 
 /* Autotuner: time every launch shape (window 3..6 for private kinds, warps
- * per CTA 2/4/8, CTAs per SM 1/2/max, both squaring variants) for key_id's
+ * per CTA 2/4/8, CTAs per SM 1/2/max, both squaring variants, lanes per operation,
+ * and for RSA-2048 CRT the tensor-core path at windows 3 and 4) for key_id's
  * size and kind exp_sel on a synthetic batch of `count` operations (the work
  * of these kernels does not depend on the message values), install the
  * fastest with rsa_set_tuning() and append it to the cache file `cache_path`

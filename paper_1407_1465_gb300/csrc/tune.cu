@@ -94,6 +94,7 @@ extern "C" int rsa_autotune(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint6
     std::vector<int> windows = priv ? std::vector<int>{3, 4, 5, 6} : std::vector<int>{0};
     std::vector<int> warps = exp_sel == RSA_EXP_PRIVATE_CRT ? std::vector<int>{2, 4, 8} : std::vector<int>{1, 2, 4, 8};
     std::vector<int> variants = priv ? std::vector<int>{1, 2} : std::vector<int>{0};
+    if (exp_sel == RSA_EXP_PRIVATE_CRT && k->d_tc) variants.push_back(3);
     double best_t = 1e30;
     int err = RSA_OK;
     for (int tpo : {1, 2, 4})
@@ -102,6 +103,8 @@ extern "C" int rsa_autotune(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint6
         for (int wp : warps)
           for (int cps : {0, 1, 2}) {
             if (tpo > 1 && (v == 2 || exp_sel == RSA_EXP_PRIVATE_PLAIN)) continue;  // not offered
+            // the tensor-core path has its own fixed launch shape and windows 3, 4
+            if (v == 3 && (tpo != 1 || wp != warps[0] || cps != 0 || (w != 3 && w != 4))) continue;
             c->tuning[{nbits, exp_sel}] = Tune{w, wp, cps, v, tpo};
             // warm-up, then the median of three timed runs
             if (c->run_key(*k, exp_sel, count, static_cast<uint32_t *>(in.ptr), static_cast<uint32_t *>(out.ptr),
@@ -134,7 +137,8 @@ extern "C" int rsa_autotune(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint6
       auto it = c->workspaces.find(s);
       if (it != c->workspaces.end()) {
         Workspace &w = it->second;
-        for (DevBuf *d : {&w.tables, &w.io_in, &w.io_out, &w.io_status, &w.aux0, &w.aux1, &w.aux2, &w.aux3})
+        for (DevBuf *d : {&w.tables, &w.io_in, &w.io_out, &w.io_status, &w.aux0, &w.aux1, &w.aux2, &w.aux3,
+                          &w.halves})
           if (d->ptr) {
             cudaFree(d->ptr);
             c->release(d->bytes);

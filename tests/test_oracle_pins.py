@@ -42,7 +42,7 @@ def test_toy_key_as_printed_and_corrected(oracle_lib):
     n, e, d = t["n"], t["e"], t["d"]
     phi = (t["p"] - 1) * (t["q"] - 1)
     assert t["p"] * t["q"] == n
-    # the printed pair is not an RSA inverse (paper error, recorded in DESIGN)
+    # the printed pair is not an RSA inverse: e*d mod phi(n) = 267, not 1 (Sec. 2 example)
     assert (e * d) % phi == 267
     d_fix = workloads.TOY_D_CORRECTED
     assert (e * d_fix) % phi == 1
