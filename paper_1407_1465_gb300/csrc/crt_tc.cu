@@ -13,8 +13,8 @@
 //      registers as byte digits (fp16) in shared memory.
 //   2. Tensor core, MMA 1: the column sums of the byte convolution of
 //      T mod R with m' = -m^-1 mod R (columns 0..127).
-//   3. CUDA cores: carry-propagate the columns into the bytes of
-//      mu = T*m' mod R, written back as fp16 digits.
+//   3. CUDA cores: carry-propagate the columns (two at a time, as base-2^16
+//      digits) into the bytes of mu = T*m' mod R, written back as fp16 digits.
 //   4. Tensor core, MMA 2: the column sums of mu * m for positions 124..251;
 //      positions 252..254 (six byte products) on the CUDA cores.
 //   5. CUDA cores: the carry out of the low half (ceil of positions 124..127
@@ -142,24 +142,28 @@ __device__ __forceinline__ uint4 lds128a(uint32_t saddr) {
   return v;
 }
 
-// carry of a column word x = 0x3F000000 + x' (x' < 2^24): x' >> 8
-__device__ __forceinline__ uint32_t ccarry(uint32_t x) { return tc::prmt(x, 0u, 0x4421u); }
+// Two adjacent column words (bias 0x3F000000 each, sums w < 2^23) as one
+// base-2^16 column: w_even + 256 w_odd < 2^31.01.  Shifting the odd word up a
+// byte drops its bias (0x3F000000 << 8 = 0 mod 2^32); the even word's bias is
+// its byte 3, cleared by the permute.  Neither depends on the running carry.
+__device__ __forceinline__ uint32_t pair_cols(uint32_t w_even, uint32_t w_odd) {
+  return tc::prmt(w_even, 0u, 0x4210u) + tc::prmt(w_odd, 0u, 0x2104u);
+}
 
-// t[j0 .. j0+NL) += (4*NL column words v, carry-propagated from the running
-// column state x) + cin; the carry out returns in cin.  Each group of four
-// columns becomes one limb of byte digits.
+// t[j0 .. j0+NL) += (4*NL column words v, carry-propagated from the carry c
+// in base 2^16: two columns per step) + cin; the column carry returns in c and
+// the limb carry in cin.  Two base-2^16 digits make one limb.
 template <int NL>
-__device__ __forceinline__ void add_columns(uint32_t (&t)[kH], int j0, const uint32_t *v, uint32_t &x,
+__device__ __forceinline__ void add_columns(uint32_t (&t)[kH], int j0, const uint32_t *v, uint32_t &c,
                                             uint32_t &cin) {
   uint32_t X[NL];
 #pragma unroll
   for (int i = 0; i < NL; ++i) {
-    const uint32_t x0 = v[4 * i] + ccarry(x);
-    const uint32_t x1 = v[4 * i + 1] + ccarry(x0);
-    const uint32_t x2 = v[4 * i + 2] + ccarry(x1);
-    const uint32_t x3 = v[4 * i + 3] + ccarry(x2);
-    X[i] = tc::prmt(tc::prmt(x0, x1, 0x0040u), tc::prmt(x2, x3, 0x4000u), 0x7610u);
-    x = x3;
+    const uint32_t y0 = pair_cols(v[4 * i], v[4 * i + 1]) + c;
+    c = y0 >> 16;
+    const uint32_t y1 = pair_cols(v[4 * i + 2], v[4 * i + 3]) + c;
+    c = y1 >> 16;
+    X[i] = tc::prmt(y0, y1, 0x5410u);   // [y0.b0, y0.b1, y1.b0, y1.b1]
   }
   (void)add_cc(cin, 0xFFFFFFFFu);   // carry flag <- cin (0 or 1)
 #pragma unroll
@@ -321,24 +325,25 @@ __device__ __forceinline__ void mont_step(uint32_t (&A)[kH], bool sq, uint32_t b
   //    its top digits are kept for positions 252..254 of mu * m
   uint32_t mu_top = 0u;   // [mu_124, mu_125, mu_126, mu_127]
   {
-    uint32_t x = kBias;
+    uint32_t c = 0u;        // carry between base-2^16 columns
 #pragma unroll 1
     for (int c0 = 0; c0 < kDig; c0 += 16) {
       uint32_t v[16];
       tc::ld16(ts.taddr + (uint32_t)c0, v);
       tc::wait_ld();
-      uint32_t w[8];
+      uint32_t y[8];
 #pragma unroll
-      for (int j = 0; j < 16; j += 2) {
-        const uint32_t x0 = v[j] + ccarry(x);
-        const uint32_t x1 = v[j + 1] + ccarry(x0);
-        w[j >> 1] = tc::prmt(x0, x1, 0xB4B0u);   // [x0.b0, 0, x1.b0, 0]: two fp16 digits
-        x = x1;
+      for (int j = 0; j < 8; ++j) {
+        y[j] = pair_cols(v[2 * j], v[2 * j + 1]) + c;
+        c = y[j] >> 16;
       }
       const uint32_t ad = ts.arow + (uint32_t)(c0 >> 3) * kKb;
-      tc::sts128(ad, w[0], w[1], w[2], w[3]);
-      tc::sts128(ad + kKb, w[4], w[5], w[6], w[7]);
-      mu_top = tc::prmt(w[6], w[7], 0x6420u);   // in the last chunk: digits 124..127
+      // [y.b0, 0, y.b1, 0]: the two bytes of a base-2^16 digit as fp16 digits
+      tc::sts128(ad, tc::prmt(y[0], 0u, 0x4140u), tc::prmt(y[1], 0u, 0x4140u), tc::prmt(y[2], 0u, 0x4140u),
+                 tc::prmt(y[3], 0u, 0x4140u));
+      tc::sts128(ad + kKb, tc::prmt(y[4], 0u, 0x4140u), tc::prmt(y[5], 0u, 0x4140u), tc::prmt(y[6], 0u, 0x4140u),
+                 tc::prmt(y[7], 0u, 0x4140u));
+      mu_top = tc::prmt(y[6], y[7], 0x5410u);   // in the last chunk: digits 124..127
     }
   }
   // 4. MMA 2: positions 124..251 of mu * m
@@ -362,33 +367,30 @@ __device__ __forceinline__ void mont_step(uint32_t (&A)[kH], bool sq, uint32_t b
   // 5. U = T_hi + (T_lo + mu*m) / R, then one conditional subtraction.  The
   // columns are carry-propagated 4 at a time into limbs that are added to T_hi
   // right away (the carry between chunks is kept in a register: cin).
-  uint32_t x, cin = 0u;
+  uint32_t c, cin = 0u;
   {
     uint32_t v[16];
     tc::ld16(ts.taddr + 0u, v);   // positions 124..139
     tc::wait_ld();
     // carry out of the low half: ceil of positions 124..127 (with T's top limb) / 2^32
-    const uint32_t y0 = v[0] + (top & 0xFFu);
-    const uint32_t y1 = v[1] + ((top >> 8) & 0xFFu) + ccarry(y0);
-    const uint32_t y2 = v[2] + ((top >> 16) & 0xFFu) + ccarry(y1);
-    const uint32_t y3 = v[3] + (top >> 24) + ccarry(y2);
-    const uint32_t low = (y0 | y1 | y2 | y3) & 0xFFu;
-    x = (ccarry(y3) + (low != 0u ? 1u : 0u)) << 8;   // so that ccarry(x) is that carry
-    add_columns<3>(t, 0, v + 4, x, cin);              // positions 128..139: limbs 0..2
+    const uint32_t y0 = pair_cols(v[0], v[1]) + (top & 0xFFFFu);
+    const uint32_t y1 = pair_cols(v[2], v[3]) + (top >> 16) + (y0 >> 16);
+    c = (y1 >> 16) + (((y0 | y1) & 0xFFFFu) != 0u ? 1u : 0u);
+    add_columns<3>(t, 0, v + 4, c, cin);              // positions 128..139: limbs 0..2
   }
 #pragma unroll
-  for (int c = 1; c < 8; ++c) {
+  for (int k = 1; k < 8; ++k) {
     uint32_t v[16];
-    tc::ld16(ts.taddr + (uint32_t)(16 * c), v);       // positions 124 + 16c .. +15
+    tc::ld16(ts.taddr + (uint32_t)(16 * k), v);       // positions 124 + 16k .. +15
     tc::wait_ld();
-    add_columns<4>(t, 3 + 4 * (c - 1), v, x, cin);    // limbs 3 + 4(c-1) .. +3
+    add_columns<4>(t, 3 + 4 * (k - 1), v, c, cin);    // limbs 3 + 4(k-1) .. +3
   }
   tc::fence_before_sync();   // this tile's TMEM reads precede the next MMA (ordered by the next barrier)
-  add_columns<1>(t, kH - 1, top_cols, x, cin);        // positions 252..255: limb 31
+  add_columns<1>(t, kH - 1, top_cols, c, cin);        // positions 252..255: limb 31
   uint32_t u[kH + 2];
 #pragma unroll
   for (int j = 0; j < kH; ++j) u[j] = t[j];
-  u[kH] = ccarry(x) + cin;
+  u[kH] = c + cin;
   u[kH + 1] = 0u;
   final_sub<kH>(A, u, NSmem<kH>{Ms});
 }
@@ -404,19 +406,26 @@ __device__ __forceinline__ void tbl_store(uint4 *tbl, int e, const uint32_t (&A)
 // stage <- T[d], reading every entry (constant time)
 template <int W>
 __device__ __forceinline__ void tbl_select(uint8_t *stage, const uint4 *tbl, uint32_t d) {
+  constexpr int G = (W <= 3) ? 2 : 1;   // limb groups whose loads are in flight together
 #pragma unroll 1
-  for (int g = 0; g < kH / 4; ++g) {
-    uint4 acc = make_uint4(0u, 0u, 0u, 0u);
+  for (int g0 = 0; g0 < kH / 4; g0 += G) {
+    uint4 acc[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) acc[u] = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
     for (int e = 0; e < (1 << W); ++e) {
-      const uint4 v = tbl[(e * (kH / 4) + g) * kRows];
       const uint32_t msk = 0u - (uint32_t)((uint32_t)e == d);
-      acc.x |= v.x & msk;
-      acc.y |= v.y & msk;
-      acc.z |= v.z & msk;
-      acc.w |= v.w & msk;
+#pragma unroll
+      for (int u = 0; u < G; ++u) {
+        const uint4 v = tbl[(e * (kH / 4) + g0 + u) * kRows];
+        acc[u].x |= v.x & msk;
+        acc[u].y |= v.y & msk;
+        acc[u].z |= v.z & msk;
+        acc[u].w |= v.w & msk;
+      }
     }
-    *reinterpret_cast<uint4 *>(stage + g * kKb) = acc;
+#pragma unroll
+    for (int u = 0; u < G; ++u) *reinterpret_cast<uint4 *>(stage + (g0 + u) * kKb) = acc[u];
   }
 }
 __device__ __forceinline__ void stage_from(uint8_t *stage, const uint4 *src, int src_stride) {
