@@ -96,6 +96,7 @@ struct HalfArgs {
   uint32_t *herr;           // [prime][count]: 1 if a bounded wait gave up
   uint4 *tables;            // [grid * kTiles][kTblU4]
   uint32_t count, count_pad, ntiles, ctas_per_prime;
+  uint32_t wait_polls;      // polls of an MMA mbarrier before a tile gives up
 };
 
 struct GarnerArgs {
@@ -197,8 +198,8 @@ __device__ __forceinline__ void issue_mmas(const Tile &ts, uint32_t b_off) {
   tc::commit(ts.mbar);
 }
 
-__device__ __forceinline__ void wait_mmas(Tile &ts) {
-  if (!tc::mbar_wait(ts.mbar, ts.phase, kWaitLimit)) {
+__device__ __forceinline__ void wait_mmas(Tile &ts, uint32_t polls) {
+  if (!tc::mbar_wait(ts.mbar, ts.phase, polls)) {
     ts.err = true;
     ts.pending = ts.phase;
   }
@@ -283,7 +284,7 @@ __device__ __forceinline__ uint32_t square_p(uint32_t (&t)[kH], const uint32_t (
 // memory at bsa, four limbs per 16 bytes, consecutive groups `bstr` bytes
 // apart (the thread's stage, or a key constant).
 __device__ __forceinline__ void mont_step(uint32_t (&A)[kH], bool sq, uint32_t bsa, uint32_t bstr, Tile &ts,
-                                          const uint32_t *Ms) {
+                                          const uint32_t *Ms, uint32_t polls) {
   // 1. T = A * B (or A^2 when sq): the low 32 limbs leave as digits, t ends
   //    as T_hi.  Block i0 of the general product reads B groups i0/4, i0/4+1
   //    (stage k-blocks 8 + i0/4 ..) before it writes k-blocks i0/2 .. i0/2+3,
@@ -320,7 +321,7 @@ __device__ __forceinline__ void mont_step(uint32_t (&A)[kH], bool sq, uint32_t b
   ts.dead = tc::bar_red_or(ts.bar_id, kRows, ts.err);
   if (ts.dead) return;
   if (ts.leader) issue_mmas(ts, kOffBm);
-  wait_mmas(ts);
+  wait_mmas(ts, polls);
   // 3. mu = carry-propagated columns mod R, back to shared memory as digits;
   //    its top digits are kept for positions 252..254 of mu * m
   uint32_t mu_top = 0u;   // [mu_124, mu_125, mu_126, mu_127]
@@ -363,7 +364,7 @@ __device__ __forceinline__ void mont_step(uint32_t (&A)[kH], bool sq, uint32_t b
     top_cols[2] = kBias + a7 * b7;
     top_cols[3] = kBias;
   }
-  wait_mmas(ts);
+  wait_mmas(ts, polls);
   // 5. U = T_hi + (T_lo + mu*m) / R, then one conditional subtraction.  The
   // columns are carry-propagated 4 at a time into limbs that are added to T_hi
   // right away (the carry between chunks is kept in a register: cin).
@@ -575,7 +576,7 @@ __global__ void __launch_bounds__(kThreads, 1) crt_tc_half_kernel(HalfArgs a) {
           bsa = sb + kOffKey + 4 * kKunit;
           bstr = 16;
         }
-        mont_step(A, sq, bsa, bstr, ts, Ms);
+        mont_step(A, sq, bsa, bstr, ts, Ms, a.wait_polls);
         if (ts.dead) break;
       }
     }
@@ -587,7 +588,8 @@ __global__ void __launch_bounds__(kThreads, 1) crt_tc_half_kernel(HalfArgs a) {
       a.herr[(size_t)pi * a.count + row] = (ts.err || ts.dead) ? 1u : 0u;
     }
   }
-  // a tile that gave up may still have an MMA in flight: wait for it (bounded) before freeing TMEM
+  // a tile that gave up may still have an MMA in flight: wait for it (bounded,
+  // with the full poll budget whatever the steps used) before freeing TMEM
   if (ts.leader && ts.pending < 2u) (void)tc::mbar_wait(ts.mbar, ts.pending, kWaitLimit);
   tc::fence_before_sync();
   __syncthreads();
@@ -702,7 +704,7 @@ static cudaError_t launch_half(const HalfArgs &h, int grid, cudaStream_t s) {
 
 cudaError_t launch_crt_tc(const uint32_t *keyrec, const void *image, const uint32_t *msgs, uint32_t *out,
                           int32_t *status, uint32_t count, int grid, int window, void *tables, void *halves,
-                          cudaStream_t s) {
+                          uint32_t wait_polls, cudaStream_t s) {
   const uint32_t cp = pad_count(count);
   HalfArgs h;
   h.keyrec = keyrec;
@@ -715,6 +717,7 @@ cudaError_t launch_crt_tc(const uint32_t *keyrec, const void *image, const uint3
   h.count_pad = cp;
   h.ntiles = (count + kRows - 1) / kRows;
   h.ctas_per_prime = (uint32_t)grid / 2;
+  h.wait_polls = wait_polls;
   cudaError_t e = (window == 3) ? launch_half<3>(h, grid, s) : launch_half<4>(h, grid, s);
   if (e != cudaSuccess) return e;
   GarnerArgs g;

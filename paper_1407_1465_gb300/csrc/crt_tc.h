@@ -33,9 +33,13 @@ size_t tc_smem_bytes();
 
 #if defined(__CUDACC__)
 // Enqueues the two-prime exponentiation kernel and the recombination kernel.
+// wait_polls bounds every wait on an MMA's completion (kDefaultWaitPolls in
+// normal use); a tile whose wait gives up reports RSA_ERR_TIMEOUT for its
+// operations.
+constexpr uint32_t kDefaultWaitPolls = 1u << 22;
 cudaError_t launch_crt_tc(const uint32_t *keyrec, const void *image, const uint32_t *msgs, uint32_t *out,
                           int32_t *status, uint32_t count, int grid, int window, void *tables, void *halves,
-                          cudaStream_t s);
+                          uint32_t wait_polls, cudaStream_t s);
 #endif
 
 }  // namespace tcr

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -188,8 +189,12 @@ int Ctx::run_key(const KeySlot &k, int kind, uint64_t count, const uint32_t *msg
     if (rc) return rc;
     rc = ensure(w.halves, tcr::tc_halves_bytes((uint32_t)count));
     if (rc) return rc;
+    // RSAGPU_TC_WAIT_POLLS overrides the poll budget of the kernel's bounded
+    // waits (0: every wait gives up at once), to exercise the timeout path
+    uint32_t polls = tcr::kDefaultWaitPolls;
+    if (const char *ev = std::getenv("RSAGPU_TC_WAIT_POLLS")) polls = (uint32_t)std::strtoul(ev, nullptr, 10);
     e = tcr::launch_crt_tc(k.d_rec, k.d_tc, msgs, out, status, (uint32_t)count, grid, win, w.tables.ptr,
-                           w.halves.ptr, s);
+                           w.halves.ptr, polls, s);
     if (e != cudaSuccess) return cuda_error(e, "launch crt_tc kernels");
     stats.kernel_launches += 2;
     last_grid = grid;

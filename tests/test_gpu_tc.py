@@ -115,3 +115,21 @@ def test_tc_rejects_other_sizes(torch_cuda, ctx, keys):
     finally:
         ctx.set_tuning(4096, CRT, reset=True)
         ctx.keyunload(kid)
+
+
+def test_tc_wait_timeout_reports_status(torch_cuda, ctx, keys, monkeypatch):
+    """The kernel's waits on MMA completion are bounded.  With a poll budget of
+    0 every wait gives up at once: each operation must come back as
+    RSA_ERR_TIMEOUT (-6) with a zeroed row, the launch must end by itself, and
+    the context must work normally afterwards."""
+    key = keys[0]
+    kid = ctx.keyload(2048, key.n, key.e, key.d, key.p, key.q)
+    rows = workloads.messages_below(key.n, 300, 41, ("tc_timeout",))
+    monkeypatch.setenv("RSAGPU_TC_WAIT_POLLS", "0")
+    got, st = run(torch_cuda, ctx, kid, CRT, rows, TC)
+    assert (st == -6).all() and not got.any()
+    monkeypatch.delenv("RSAGPU_TC_WAIT_POLLS")
+    got, st = run(torch_cuda, ctx, kid, CRT, rows, TC)
+    assert (st == 0).all()
+    assert np.array_equal(got, oracle.crt_batch(rows, key.d, key.p, key.q))
+    ctx.keyunload(kid)
