@@ -152,7 +152,7 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(key, rows, target_s: float = 12.0, public: bool = False) -> dict:
+def cpu_baseline(key, rows, target_s: float = 12.0, public: bool = False, e: int = 0) -> dict:
     """The oracle (as written) on every host core, on a bounded sample: its CRT
     routine for decryptions, its left-to-right binary method with e for encryptions."""
     import oracle
@@ -160,7 +160,7 @@ def cpu_baseline(key, rows, target_s: float = 12.0, public: bool = False) -> dic
 
     def run(r):
         if public:
-            oracle.modexp_batch(r, key.e, key.n, threads=threads)
+            oracle.modexp_batch(r, e or key.e, key.n, threads=threads)
         else:
             oracle.crt_batch(r, key.d, key.p, key.q, threads=threads)
 
@@ -439,6 +439,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="rsa2048", choices=sorted(WORKLOADS) + ["ragged", "serving", "toy"])
+    ap.add_argument("--e-bits", type=int, default=0,
+                    help="--kind public: a seeded random public exponent of this many bits instead of 65537")
     ap.add_argument("--kind", default="crt", choices=["crt", "public"],
                     help="rsa2048/rsa4096: CRT decryption (default) or public-exponent encryption")
     ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000,100000,200000")
@@ -482,13 +484,24 @@ def main():
     kind = RSA_EXP_PRIVATE_CRT if args.kind == "crt" else RSA_EXP_PUBLIC
     metric = ("RSA-%d CRT decrypts/sec" if args.kind == "crt" else "RSA-%d encryptions/sec (e=65537)") % spec["bits"]
     unit = "decrypts/s" if args.kind == "crt" else "encryptions/s"
+    if args.kind == "public" and args.e_bits:
+        metric = "RSA-%d public-exponent operations/sec (e of %d bits)" % (spec["bits"], args.e_bits)
+        unit = "ops/s"
 
     key, rows = workloads.rsa_single(spec["bits"], WORKLOADS[args.workload]["count"])
     rows = rows[:spec["count"]] if spec["count"] <= rows.shape[0] else \
         workloads.messages_below(key.n, spec["count"], workloads.DEFAULT_SEED, ("single", spec["bits"]))
     count, L = rows.shape
     ctx = RsaContext(local, mem_budget_bytes=16 << 30)
-    kid = ctx.keyload(spec["bits"], key.n, key.e, key.d, key.p, key.q)
+    e_pub = key.e
+    if args.kind == "public" and args.e_bits:
+        # a long public (non-secret) exponent: the case the sliding-window method serves
+        rng = np.random.default_rng(workloads.DEFAULT_SEED + args.e_bits)
+        e_pub = (1 << (args.e_bits - 1)) | (int.from_bytes(rng.bytes((args.e_bits + 7) // 8), "little")
+                                            % (1 << (args.e_bits - 1))) | 1
+        kid = ctx.keyload(spec["bits"], key.n, e_pub)
+    else:
+        kid = ctx.keyload(spec["bits"], key.n, key.e, key.d, key.p, key.q)
     if args.window or args.warps or args.ctas_per_sm or args.variant or args.tpo:
         ctx.set_tuning(spec["bits"], kind, window=args.window, warps_per_cta=args.warps,
                        ctas_per_sm=args.ctas_per_sm, variant=args.variant, threads_per_op=args.tpo)
@@ -561,7 +574,7 @@ def main():
         if not np.array_equal(h_out.numpy().view(np.uint32), out.cpu().numpy().view(np.uint32)):
             raise RuntimeError("e2e output differs from the device-resident run")
 
-    prods = rsa_products_per_op(spec["bits"], kind, e=key.e, window=tune["window"])
+    prods = rsa_products_per_op(spec["bits"], kind, e=e_pub, window=tune["window"])
     achieved = prods * count / (ms / 1e3) / 1e12
     peak = derived_peak_tprod(SM_COUNT_GB300, 2070.0)
     prof = PROFILED_TRAFFIC.get((args.workload, tune["variant"])) if args.kind == "crt" else None
@@ -603,8 +616,11 @@ def main():
                    "parallelism": "dp%d (independent batches per GPU)" % ws},
         "wall_s": wall, "clocks": clk, "roofline": roofline, "e2e": e2e,
     }
+    if args.kind == "public" and args.e_bits:
+        line["config"]["workload"] = line["config"]["workload"].replace(
+            "(e=65537)", "(seeded odd e of %d bits)" % args.e_bits)
     if rank == 0 and ws == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(key, rows, public=(kind == RSA_EXP_PUBLIC))
+        line["cpu_baseline"] = cpu_baseline(key, rows, public=(kind == RSA_EXP_PUBLIC), e=e_pub)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

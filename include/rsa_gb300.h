@@ -50,7 +50,9 @@ typedef enum rsa_status {
     RSA_ERR_NOMEM = -4,       /* memory budget exceeded or device allocation failed */
     RSA_ERR_CUDA = -5,        /* a CUDA runtime call failed */
     RSA_ERR_TIMEOUT = -6,     /* a bounded device-side wait gave up */
-    RSA_ERR_UNSUPPORTED = -7  /* key size or operation kind not supported */
+    RSA_ERR_UNSUPPORTED = -7, /* key size or operation kind not supported */
+    RSA_ERR_VERIFY = -8       /* per operation of rsa_verify_key: s^e mod n differs from the
+                                 expected representative */
 } rsa_status;
 
 /* Which exponent an operation uses. */
@@ -114,6 +116,29 @@ int rsa_key_info(rsa_ctx *ctx, int32_t key_id, uint32_t *nbits, int32_t *has_d, 
  * RSA_ERR_ARG, RSA_ERR_KEY, RSA_ERR_UNSUPPORTED, RSA_ERR_NOMEM, RSA_ERR_CUDA. */
 int rsa_modexp_key(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint64_t count,
                    const uint32_t *msgs, uint32_t *out, int32_t *op_status, void *stream);
+
+/* Signatures on the same kernels (Sec. 3.2-3.3: signing applies the private
+ * exponent, verifying the public one).  A "representative" is the integer to be
+ * signed, already hashed and padded by the caller (no hashing or padding here),
+ * as L limbs below n.
+ *
+ * rsa_sign_key: sigs[i] = reps[i]^d mod n, through p, q (CRT) when the key has
+ *   them, else with d directly.  reps, sigs: device pointers to count rows of L
+ *   limbs (16-byte aligned; sigs may equal reps).  op_status: device pointer to
+ *   count int32 (RSA_OK, or RSA_ERR_RANGE for a representative >= n, whose
+ *   signature row is zeroed), or NULL.
+ * rsa_verify_key: op_status[i] = RSA_OK when sigs[i]^e mod n == reps[i],
+ *   RSA_ERR_VERIFY when it differs, RSA_ERR_RANGE when sigs[i] >= n.  sigs,
+ *   reps: device pointers to count rows of L limbs; op_status is required (the
+ *   verdicts).  Scratch for the recovered representatives comes from the
+ *   context's budget.
+ * Both are enqueued on `stream`.  Errors (before anything is enqueued):
+ * RSA_ERR_ARG, RSA_ERR_KEY (rsa_sign_key on a key loaded without d),
+ * RSA_ERR_UNSUPPORTED, RSA_ERR_NOMEM, RSA_ERR_CUDA. */
+int rsa_sign_key(rsa_ctx *ctx, int32_t key_id, uint64_t count, const uint32_t *reps, uint32_t *sigs,
+                 int32_t *op_status, void *stream);
+int rsa_verify_key(rsa_ctx *ctx, int32_t key_id, uint64_t count, const uint32_t *sigs, const uint32_t *reps,
+                   int32_t *op_status, void *stream);
 
 /* Ragged batch: operation i uses key key_ids[i] (any loaded key, any size) and
  * exponent exp_sel[i]; its message is the L_i limbs at msgs + limb_offsets[i]
@@ -227,7 +252,8 @@ const char *rsa_last_error(void);
 
 /* Launch parameters of the multi-limb kernels.  Zero fields mean "automatic". */
 typedef struct rsa_tuning {
-    int32_t window;        /* fixed-window width w for private exponents, 3..6 */
+    int32_t window;        /* fixed-window width w for private exponents, 3..6; for
+                              sliding-window public exponents the maximum window */
     int32_t warps_per_cta; /* warps per CTA (even for CRT: warp pairs), 1..8 */
     int32_t ctas_per_sm;   /* resident CTAs per SM the grid is sized for */
     int32_t variant;       /* squarings of private exponents: 1 = through the general
@@ -238,7 +264,10 @@ typedef struct rsa_tuning {
                               Toeplitz matrices of p, q and -p^-1, -q^-1 mod 2^1024;
                               the per-message product stays on the CUDA cores; windows
                               3 and 4); 0 = automatic: 3 for RSA-2048 CRT (window 3),
-                              1 otherwise */
+                              1 otherwise.  For RSA_EXP_PUBLIC (moduli up to 2048
+                              bits): 1 = binary method (Fig. 5), 2 = sliding windows
+                              of up to `window` bits (Fig. 7; window 4..6, default 5),
+                              0 = sliding for exponents longer than 64 bits */
     int32_t threads_per_op; /* lanes cooperating on one operation: 1, 2 or 4 (numbers
                               sliced over the lanes, warp-shuffle carries); 0 = automatic */
 } rsa_tuning;

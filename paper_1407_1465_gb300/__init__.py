@@ -17,7 +17,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (RSA_ERR_ARG, RSA_ERR_CUDA, RSA_ERR_KEY, RSA_ERR_NOMEM, RSA_ERR_RANGE,  # noqa: F401
-                   RSA_ERR_TIMEOUT, RSA_ERR_UNSUPPORTED, RSA_EXP_PRIVATE_CRT, RSA_EXP_PRIVATE_PLAIN,
+                   RSA_ERR_TIMEOUT, RSA_ERR_UNSUPPORTED, RSA_ERR_VERIFY, RSA_EXP_PRIVATE_CRT, RSA_EXP_PRIVATE_PLAIN,
                    RSA_EXP_PUBLIC, RSA_OK, RsaError, check, last_error, rsa_stats, rsa_tuning)
 
 __all__ = [
@@ -25,6 +25,7 @@ __all__ = [
     "rsa_ctx_create", "rsa_ctx_destroy", "rsa_keyload", "rsa_key_record", "rsa_tc_operand_image",
     "rsa_keyunload", "rsa_key_info",
     "rsa_modexp_key", "rsa_modexp_batch", "rsa_modexp_key_host", "rsa_modexp_batch_host",
+    "rsa_sign_key", "rsa_verify_key",
     "rsa_sync", "rsa_last_error", "rsa_set_tuning", "rsa_get_tuning", "rsa_get_stats",
     "rsa_products_per_op", "rsa_imad_probe", "rsa_crt_decrypt_noalloc", "rsa_autotune",
     "rsa_server_start", "rsa_server_submit", "rsa_server_submit_many", "rsa_server_clock", "rsa_server_poll", "rsa_server_drain", "rsa_server_get_stats",
@@ -142,6 +143,16 @@ def rsa_key_info(ctx: int, key_id: int) -> tuple[int, bool, bool]:
 def rsa_modexp_key(ctx: int, key_id: int, exp_sel: int, count: int, msgs, out, op_status=None,
                    stream=None) -> None:
     check(_lib.lib().rsa_modexp_key(ctx, key_id, exp_sel, count, _ptr(msgs), _ptr(out), _ptr(op_status),
+                                    _stream_ptr(stream)))
+
+
+def rsa_sign_key(ctx: int, key_id: int, count: int, reps, sigs, op_status=None, stream=None) -> None:
+    check(_lib.lib().rsa_sign_key(ctx, key_id, count, _ptr(reps), _ptr(sigs), _ptr(op_status),
+                                  _stream_ptr(stream)))
+
+
+def rsa_verify_key(ctx: int, key_id: int, count: int, sigs, reps, op_status, stream=None) -> None:
+    check(_lib.lib().rsa_verify_key(ctx, key_id, count, _ptr(sigs), _ptr(reps), _ptr(op_status),
                                     _stream_ptr(stream)))
 
 
@@ -317,6 +328,24 @@ class RsaContext:
         count = msgs.shape[0] if msgs.dim() > 1 else msgs.numel()
         rsa_modexp_key(self.handle, key_id, exp_sel, count, msgs, out, status, stream)
         return out
+
+    def sign(self, key_id: int, reps, sigs=None, status=None, stream=None):
+        """reps: CUDA tensor [count, L]; returns the signatures reps^d mod n."""
+        import torch
+        if sigs is None:
+            sigs = torch.empty_like(reps)
+        count = reps.shape[0] if reps.dim() > 1 else reps.numel()
+        rsa_sign_key(self.handle, key_id, count, reps, sigs, status, stream)
+        return sigs
+
+    def verify(self, key_id: int, sigs, reps, status=None, stream=None):
+        """Returns an int32 CUDA tensor of verdicts: 0 valid, RSA_ERR_VERIFY, RSA_ERR_RANGE."""
+        import torch
+        count = sigs.shape[0] if sigs.dim() > 1 else sigs.numel()
+        if status is None:
+            status = torch.empty(count, dtype=torch.int32, device=sigs.device)
+        rsa_verify_key(self.handle, key_id, count, sigs, reps, status, stream)
+        return status
 
     def modexp_key_host(self, key_id: int, exp_sel: int, msgs: np.ndarray, out: np.ndarray | None = None,
                         status: np.ndarray | None = None, stream=None) -> np.ndarray:

@@ -20,6 +20,7 @@ RSA_ERR_NOMEM = -4
 RSA_ERR_CUDA = -5
 RSA_ERR_TIMEOUT = -6
 RSA_ERR_UNSUPPORTED = -7
+RSA_ERR_VERIFY = -8
 
 RSA_EXP_PUBLIC = 0
 RSA_EXP_PRIVATE_CRT = 1
@@ -27,7 +28,7 @@ RSA_EXP_PRIVATE_PLAIN = 2
 
 STATUS_NAMES = {
     0: "RSA_OK", -1: "RSA_ERR_ARG", -2: "RSA_ERR_KEY", -3: "RSA_ERR_RANGE", -4: "RSA_ERR_NOMEM",
-    -5: "RSA_ERR_CUDA", -6: "RSA_ERR_TIMEOUT", -7: "RSA_ERR_UNSUPPORTED",
+    -5: "RSA_ERR_CUDA", -6: "RSA_ERR_TIMEOUT", -7: "RSA_ERR_UNSUPPORTED", -8: "RSA_ERR_VERIFY",
 }
 
 
@@ -81,6 +82,8 @@ SIGNATURES = [
     ("rsa_key_info", ctypes.c_int, [_P, ctypes.c_int32, _U32P, _I32P, _I32P]),
     ("rsa_modexp_key", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P]),
     ("rsa_modexp_batch", ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, _P, _P, _P, _P, _P]),
+    ("rsa_sign_key", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P]),
+    ("rsa_verify_key", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P]),
     ("rsa_modexp_key_host", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P]),
     ("rsa_modexp_batch_host", ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, _P, ctypes.c_uint64, _P, _P, _P, _P]),
     ("rsa_crt_decrypt_noalloc", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, _P, _P, _P]),

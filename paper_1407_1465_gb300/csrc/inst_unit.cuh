@@ -73,6 +73,18 @@ const void *RSAGPU_CAT(plain_kernel_fn_, RSAGPU_UNIT)(int W, int variant) {
   }
 }
 
+const void *RSAGPU_CAT(pub_slide_kernel_fn_, RSAGPU_UNIT)(int W) {
+  if constexpr (kL <= 64) {
+    switch (W) {
+      case 4: return reinterpret_cast<const void *>(&pub_slide_kernel<kL, kU, 4>);
+      case 5: return reinterpret_cast<const void *>(&pub_slide_kernel<kL, kU, 5>);
+      case 6: return reinterpret_cast<const void *>(&pub_slide_kernel<kL, kU, 6>);
+      default: return nullptr;
+    }
+  }
+  return nullptr;
+}
+
 const void *RSAGPU_CAT(pub_kernel_fn_, RSAGPU_UNIT)() {
   if constexpr (kL <= 64) return reinterpret_cast<const void *>(&pub_kernel<kL, kU>);
   else return reinterpret_cast<const void *>(&pub_wide_kernel<kL, 4>);

@@ -490,6 +490,137 @@ __global__ void __launch_bounds__(256) pub_kernel(ExpArgs a) {
   }
 }
 
+// ------------------------------------------------------------------ public exponent, sliding windows
+// Fig. 7 (sliding window method) for long public, i.e. non-secret, exponents.
+// The exponent is scanned from its top bit: a 0 bit costs one squaring; a 1
+// bit opens the longest window of at most W bits that ends in a 1 bit (an odd
+// value v), which costs its squarings and one multiplication by x^v from a
+// table of the odd powers x, x^3, ..., x^(2^W - 1).  The leading window is a
+// table read.  The exponent is the key's (the same for every lane and not
+// secret), so the control flow and the table index may depend on it; every
+// product goes through one mont_mul call site.
+template <int L>
+__device__ __forceinline__ void table_load(uint32_t (&A)[L], const uint4 *table_lane, int e) {
+#pragma unroll
+  for (int g = 0; g < L / 4; ++g) {
+    const uint4 v = table_lane[(e * (L / 4) + g) * 32];
+    A[4 * g] = v.x; A[4 * g + 1] = v.y; A[4 * g + 2] = v.z; A[4 * g + 3] = v.w;
+  }
+}
+
+// Bits i down to the lowest 1 bit at or above max(i - W + 1, 0), as a value; *j gets that bit's index.
+template <int W>
+__device__ __forceinline__ uint32_t slide_window(const uint32_t *E, int i, int *j) {
+  int lo = i - W + 1 > 0 ? i - W + 1 : 0;
+  while (!((E[lo >> 5] >> (lo & 31)) & 1u)) ++lo;
+  uint32_t v = 0;
+  for (int b = i; b >= lo; --b) v = (v << 1) | ((E[b >> 5] >> (b & 31)) & 1u);
+  *j = lo;
+  return v;
+}
+
+template <int L, int U, int W>
+__device__ __forceinline__ void pub_slide_tile(const uint32_t *ks, int lane, uint4 *sq_lane, uint4 *x2_lane,
+                                               uint4 *table_lane, const TileIO &io) {
+  constexpr KeyLayout lay(L);
+  constexpr int NT = 1 << (W - 1);   // table entries: x^(2t+1), t < NT
+  const KeyHeader &hd = *reinterpret_cast<const KeyHeader *>(ks);
+  using NS = typename std::conditional<NPick<L, false>::reg, NRegs<L>, NSmem<L>>::type;
+  NS N;
+  if constexpr (NPick<L, false>::reg) N.load(reinterpret_cast<const uint4 *>(ks + lay.n)); else N.s = ks + lay.n;
+  const uint32_t *E = ks + lay.e;
+  const LaneOp lo = lane_op(io, lane, L);
+  uint32_t A[L];
+  load_row<L>(A, lo.row, lo.valid);
+  int i = (int)hd.e_bits - 1;   // highest exponent bit not yet consumed
+  int nsq = 0, tidx = 0, step = 0;
+  bool mul_pending = false, started = false, finished = false;
+#pragma unroll 1
+  while (true) {
+    SmemB B{sq_lane, 32};
+    if (step == 0) {
+      B = SmemB{reinterpret_cast<const uint4 *>(ks + lay.r2n), 1};   // x R
+    } else if (step == 1) {
+      to_stage<L>(sq_lane, A);                                       // x^2 R
+    } else if (step <= NT) {
+      B = SmemB{x2_lane, 32};                                        // x^(2(step-1)+1) R
+    } else {
+      if (!started) {                                                // leading window
+        int j;
+        const uint32_t v = slide_window<W>(E, i, &j);
+        table_load<L>(A, table_lane, (int)(v >> 1));
+        i = j - 1;
+        started = true;
+      }
+      if (nsq == 0 && !mul_pending) {
+        if (i < 0) {
+          if (finished) break;
+          B = SmemB{reinterpret_cast<const uint4 *>(ks + lay.unitL), 1};   // leave Montgomery form
+          finished = true;
+        } else if (!((E[i >> 5] >> (i & 31)) & 1u)) {
+          nsq = 1;
+          --i;
+        } else {
+          int j;
+          const uint32_t v = slide_window<W>(E, i, &j);
+          nsq = i - j + 1;
+          tidx = (int)(v >> 1);
+          mul_pending = true;
+          i = j - 1;
+        }
+      }
+      if (!finished) {
+        if (nsq > 0) {
+          to_stage<L>(sq_lane, A);
+          --nsq;
+        } else {
+#pragma unroll
+          for (int g = 0; g < L / 4; ++g) sq_lane[g * 32] = table_lane[(tidx * (L / 4) + g) * 32];
+          mul_pending = false;
+        }
+      }
+    }
+    mont_mul<L, U>(A, B, N, hd.np_n);
+    if (step == 0) {
+      table_store<L>(table_lane, 0, A);
+    } else if (step == 1) {
+      to_stage<L>(x2_lane, A);
+      table_load<L>(A, table_lane, 0);
+    } else if (step <= NT) {
+      table_store<L>(table_lane, step - 1, A);
+    }
+    ++step;
+  }
+  const bool ok = lo.valid && row_below(lo.row, ks + lay.n, L);
+  if (lo.valid) {
+    uint4 *orow = reinterpret_cast<uint4 *>(lo.orow);
+#pragma unroll
+    for (int g = 0; g < L / 4; ++g)
+      orow[g] = ok ? make_uint4(A[4 * g], A[4 * g + 1], A[4 * g + 2], A[4 * g + 3]) : make_uint4(0u, 0u, 0u, 0u);
+    if (io.status) io.status[lo.op] = ok ? 0 : -3;
+  }
+}
+
+// tables: per warp 2^(W-1) * L/4 * 32 uint4
+template <int L, int U, int W>
+__global__ void __launch_bounds__(256) pub_slide_kernel(ExpArgs a) {
+  using Sm = ExpSmem<L>;
+  extern __shared__ uint4 smem4[];
+  load_key_smem<L>(smem4, a.keyrec);
+  const uint32_t *ks = reinterpret_cast<const uint32_t *>(smem4);
+  const int nw = blockDim.x / 32, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint4 *sq_lane = smem4 + Sm::kKeyWords / 4 + (size_t)warp * 2 * Sm::kStageU4 + lane;
+  uint4 *x2_lane = sq_lane + Sm::kStageU4;
+  uint4 *table_lane = a.tables + (size_t)(blockIdx.x * nw + warp) * (1 << (W - 1)) * (L / 4) * 32 + lane;
+  const uint32_t ntiles = (a.count + 31) / 32;
+#pragma unroll 1
+  for (uint32_t tile = blockIdx.x * nw + warp; tile < ntiles; tile += gridDim.x * nw) {
+    const uint32_t base = tile * 32;
+    const TileIO io{a.msgs, a.out, a.status, nullptr, nullptr, base, min(32u, a.count - base)};
+    pub_slide_tile<L, U, W>(ks, lane, sq_lane, x2_lane, table_lane, io);
+  }
+}
+
 // ------------------------------------------------------------------ public exponent, wide moduli
 // L = 96 or 128 limbs: A, the base x and the key constants stay in shared
 // memory (mont_mul_smemA); same binary method as pub_tile.

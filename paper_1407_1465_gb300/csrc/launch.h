@@ -16,6 +16,8 @@ const void *crt_kernel_fn(int H, int W, int variant = 0);
 const void *plain_kernel_fn(int L, int W, int variant = 0);
 // public exponent (binary method), L limbs
 const void *pub_kernel_fn(int L);
+// public exponent, sliding windows of up to W bits (Fig. 7), L <= 64 limbs
+const void *pub_slide_kernel_fn(int L, int W);
 // single-limb keys (n < 2^32)
 const void *toy_kernel_fn();
 // T lanes per operation (T = 2, 4): CRT with half size H, public exponent with L limbs
@@ -29,7 +31,8 @@ constexpr int kMaxWindow = 6;
 #define RSAGPU_DECLARE_UNIT(X)                      \
   const void *crt_kernel_fn_##X(int W, int variant);   \
   const void *plain_kernel_fn_##X(int W, int variant); \
-  const void *pub_kernel_fn_##X();
+  const void *pub_kernel_fn_##X();                     \
+  const void *pub_slide_kernel_fn_##X(int W);
 
 RSAGPU_DECLARE_UNIT(16)
 RSAGPU_DECLARE_UNIT(32)

@@ -42,6 +42,14 @@ const void *plain_kernel_fn(int L, int W, int variant) {
     default: return nullptr;
   }
 }
+const void *pub_slide_kernel_fn(int L, int W) {
+  switch (L) {
+    case 32: return pub_slide_kernel_fn_16(W);
+    case 64: return pub_slide_kernel_fn_32(W);
+    default: return nullptr;
+  }
+}
+
 const void *pub_kernel_fn(int L) {
   switch (L) {
     case 32: return pub_kernel_fn_16();

@@ -82,7 +82,7 @@ Ctx::~Ctx() {
 }
 
 void Workspace::free_all() {
-  for (DevBuf *b : {&tables, &io_in, &io_out, &io_status, &aux0, &aux1, &aux2, &aux3, &halves}) {
+  for (DevBuf *b : {&tables, &io_in, &io_out, &io_status, &aux0, &aux1, &aux2, &aux3, &halves, &verify}) {
     if (b->ptr) cudaFree(b->ptr);
     b->ptr = nullptr;
     b->bytes = 0;
@@ -94,6 +94,9 @@ void Workspace::free_all() {
 // entries per window, so the smaller table wins although it needs a few more
 // multiplications (RSA-2048 CRT: w = 4 1.25 M/s, w = 5 1.18 M/s, w = 6 0.97 M/s;
 // RSA-4096 CRT: 128 K/s, 127 K/s, 118 K/s).
+// Public exponents longer than this use sliding windows (variant 0).
+constexpr uint32_t kSlideMinBits = 64;
+
 static int default_window(uint32_t L, int kind) {
   (void)L;
   (void)kind;
@@ -111,7 +114,7 @@ Tune Ctx::tune_for(uint32_t nbits, int kind) const {
   if (!t.variant && kind == RSA_EXP_PRIVATE_CRT && L == 2 * (uint32_t)tcr::kH && t.tpo <= 1 &&
       (t.window == 0 || t.window == 3 || t.window == 4))
     t.variant = 3;
-  if (!t.window) t.window = (t.variant == 3) ? 3 : default_window(L, kind);
+  if (!t.window) t.window = (t.variant == 3) ? 3 : (kind == RSA_EXP_PUBLIC ? 5 : default_window(L, kind));
   if (!t.warps_per_cta) t.warps_per_cta = 4;
   // lanes per operation (GB300 sweeps): four for 3072/4096-bit keys -- CRT halves of
   // 48/64 limbs need 255 registers on one lane and 128 on four (RSA-4096 CRT:
@@ -268,8 +271,14 @@ int Ctx::run_key(const KeySlot &k, int kind, uint64_t count, const uint32_t *msg
     return RSA_OK;
   }
   const bool pub = (kind == RSA_EXP_PUBLIC);
-  const void *fn = pub ? pub_kernel_fn((int)L) : plain_kernel_fn((int)L, t.window, t.variant);
-  if (!fn) return set_error(RSA_ERR_UNSUPPORTED, "no kernel for this key size / exponent kind");
+  // public exponents: sliding windows (Fig. 7) for long exponents, where they
+  // save multiplications; the binary method (Fig. 5) for short ones such as
+  // 65537, where the window table would cost more than it saves
+  const uint32_t e_bits = k.host_rec.size() > 7 ? k.host_rec[7] : 0u;
+  const bool slide = pub && L <= 64 && (t.variant == 2 || (t.variant == 0 && e_bits > kSlideMinBits));
+  const void *fn = pub ? (slide ? pub_slide_kernel_fn((int)L, t.window) : pub_kernel_fn((int)L))
+                       : plain_kernel_fn((int)L, t.window, t.variant);
+  if (!fn) return set_error(RSA_ERR_UNSUPPORTED, "no kernel for this key size / exponent kind / window");
   const int warps = std::max(1, t.warps_per_cta);
   const int threads = 32 * warps;
   const size_t smem = exp_smem_bytes((int)L, warps);
@@ -278,8 +287,9 @@ int Ctx::run_key(const KeySlot &k, int kind, uint64_t count, const uint32_t *msg
   int rc = launch_grid(fn, threads, smem, (uint64_t)warps, ntiles, t.ctas_per_sm, &grid);
   if (rc) return rc;
   uint4 *tables = nullptr;
-  if (!pub) {
-    const size_t tbytes = (size_t)grid * warps * ((size_t)1 << t.window) * L * 128;
+  if (!pub || slide) {
+    const size_t entries = slide ? ((size_t)1 << (t.window - 1)) : ((size_t)1 << t.window);
+    const size_t tbytes = (size_t)grid * warps * entries * L * 128;
     rc = ensure(w.tables, tbytes);
     if (rc) return rc;
     tables = static_cast<uint4 *>(w.tables.ptr);
@@ -287,7 +297,7 @@ int Ctx::run_key(const KeySlot &k, int kind, uint64_t count, const uint32_t *msg
   ExpArgs a{k.d_rec, msgs, out, status, (uint32_t)count, tables};
   void *args[] = {&a};
   e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, s);
-  if (e != cudaSuccess) return cuda_error(e, pub ? "launch pub_kernel" : "launch plain_kernel");
+  if (e != cudaSuccess) return cuda_error(e, pub ? "launch public-exponent kernel" : "launch plain_kernel");
   stats.kernel_launches++;
   last_grid = grid;
   last_threads = threads;

@@ -27,6 +27,7 @@ struct Workspace {
   DevBuf io_in, io_out, io_status;  // host-buffer entry points
   DevBuf aux0, aux1, aux2, aux3;  // ragged-batch planning buffers
   DevBuf halves;                  // tensor-core CRT path: per-prime results between its two kernels
+  DevBuf verify;                  // rsa_verify_key: recovered representatives
   void free_all();
 };
 

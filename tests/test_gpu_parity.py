@@ -274,3 +274,27 @@ def test_lanes_per_operation_public(torch_cuda, ctx, keys, kids, bits, tpo):
         assert not got[ng:].any()
     finally:
         ctx.set_tuning(bits, PUB, reset=True)
+
+
+@pytest.mark.parametrize("bits", [1024, 2048])
+def test_public_sliding_window_long_exponents(torch_cuda, ctx, keys, bits):
+    """Long public exponents: the sliding-window method (Fig. 7, windows 4..6)
+    and the binary method (Fig. 5) both equal the oracle; short windows and an
+    exponent whose top window is shorter than w are covered by the exponent set."""
+    key = keys[bits]
+    rng = np.random.default_rng(bits + 17)
+    exps = [(1 << (bits - 1)) | int.from_bytes(rng.bytes(bits // 8), "little") % (1 << (bits - 1)) | 1,
+            (1 << 200) + 1, 3, 0b1000000000000000000000000000000000000000000000000000000000000000000000101]
+    rows = workloads.messages_below(key.n, 45, 61, ("slide", bits))
+    for e in exps:
+        kid = ctx.keyload(bits, key.n, e)
+        want = oracle.modexp_batch(rows, e, key.n)
+        try:
+            for variant, window in ((1, 0), (2, 4), (2, 5), (2, 6), (0, 0)):
+                ctx.set_tuning(bits, PUB, variant=variant, window=window)
+                got, st = run(torch_cuda, ctx, kid, PUB, rows)
+                assert (st == 0).all()
+                assert np.array_equal(got, want), (e.bit_length(), variant, window)
+        finally:
+            ctx.set_tuning(bits, PUB, reset=True)
+            ctx.keyunload(kid)
