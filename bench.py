@@ -225,6 +225,56 @@ def run_toy(args):
     return 0
 
 
+def run_mr(args):
+    """Key generation's primality step: one Miller-Rabin round per seeded odd
+    1024-bit candidate (top bit set, bases in [2, n/2)), 65536 candidates per
+    step, all device-resident; a sample of verdicts is checked against the
+    oracle.  Reported as rounds/s."""
+    import torch
+    from paper_1407_1465_gb300 import RsaContext, build
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    count = args.count or 65536
+    rng = np.random.default_rng(workloads.DEFAULT_SEED + 1024)
+    cands = rng.integers(0, 1 << 32, size=(count, 32), dtype=np.uint64).astype(np.uint32)
+    cands[:, 0] |= 1
+    cands[:, 31] |= 0x80000000
+    bases = rng.integers(0, 1 << 32, size=(count, 1, 32), dtype=np.uint64).astype(np.uint32)
+    bases[:, 0, 31] &= 0x3FFFFFFF
+    bases[:, 0, 0] |= 2
+    ctx = RsaContext(0, mem_budget_bytes=4 << 30)
+    c = torch.from_numpy(cands.view(np.int32)).to(dev)
+    b = torch.from_numpy(bases.view(np.int32)).to(dev)
+    v = torch.empty(count, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 1)):
+        ctx.miller_rabin(1024, c, b, v, stream.cuda_stream)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        ctx.miller_rabin(1024, c, b, v, stream.cuda_stream)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    import oracle
+    got = v.cpu().numpy()
+    idx = np.arange(0, count, max(1, count // 24))
+    want = [oracle.miller_rabin(workloads.rows_to_ints(cands[i:i + 1])[0],
+                                workloads.rows_to_ints(bases[i, :, :])) for i in idx]
+    if list(got[idx]) != want:
+        raise RuntimeError("Miller-Rabin verdicts differ from the oracle")
+    line = {"metric": "Miller-Rabin rounds/sec (1024-bit candidates)", "value": count / (ms / 1e3),
+            "unit": "rounds/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "probable_primes_in_batch": int((got == 1).sum()),
+            "config": {"workload": "%d seeded odd 1024-bit candidates, one base each, one launch per step" % count}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_ragged(args):
     """Ragged batch: 256 keys, 200000 operations, one rsa_modexp_batch (one graph
     launch) per step, against a loop of one rsa_modexp_key launch per
@@ -438,7 +488,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="rsa2048", choices=sorted(WORKLOADS) + ["ragged", "serving", "toy"])
+    ap.add_argument("--workload", default="rsa2048", choices=sorted(WORKLOADS) + ["ragged", "serving", "toy", "mr"])
     ap.add_argument("--e-bits", type=int, default=0,
                     help="--kind public: a seeded random public exponent of this many bits instead of 65537")
     ap.add_argument("--kind", default="crt", choices=["crt", "public"],
@@ -461,6 +511,8 @@ def main():
         return run_serving(args)
     if args.workload == "toy":
         return run_toy(args)
+    if args.workload == "mr":
+        return run_mr(args)
     spec = dict(WORKLOADS[args.workload])
     if args.count:
         spec["count"] = args.count

@@ -140,6 +140,21 @@ int rsa_sign_key(rsa_ctx *ctx, int32_t key_id, uint64_t count, const uint32_t *r
 int rsa_verify_key(rsa_ctx *ctx, int32_t key_id, uint64_t count, const uint32_t *sigs, const uint32_t *reps,
                    int32_t *op_status, void *stream);
 
+/* Batch Miller-Rabin probable-prime tests, the step before key generation
+ * (Fig. 1 asks for two large primes; the paper names no test).  Candidate i is
+ * the odd integer n_i of nbits/32 limbs at cands + i*L (nbits 512 or 1024; the
+ * top bit need not be set); its `rounds` bases are the rows
+ * bases + (i*rounds + r)*L, each in [2, n_i - 2] (drawn by the caller).
+ * Writing n_i - 1 = d 2^s with d odd, base a passes when a^d = 1 or
+ * a^(d 2^r) = n_i - 1 (mod n_i) for some r < s.  verdicts[i] = 1 when every
+ * base passes (probable prime), 0 when some base proves n_i composite, -1 for
+ * an even candidate or one below 5.  All pointers are device pointers (rows
+ * 16-byte aligned); the powers are constant-time in the candidate.  Enqueued
+ * on `stream`.  Errors: RSA_ERR_ARG, RSA_ERR_UNSUPPORTED, RSA_ERR_NOMEM,
+ * RSA_ERR_CUDA. */
+int rsa_mr_batch(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *cands, uint32_t rounds,
+                 const uint32_t *bases, int32_t *verdicts, void *stream);
+
 /* Ragged batch: operation i uses key key_ids[i] (any loaded key, any size) and
  * exponent exp_sel[i]; its message is the L_i limbs at msgs + limb_offsets[i]
  * and its result goes to out + limb_offsets[i].  All five arrays are device

@@ -71,6 +71,8 @@ def _bind(lib):
     lib.oracle_default_threads.restype = ctypes.c_int
     lib.oracle_modexp_batch.argtypes = [ctypes.POINTER(_BatchArgs), sz, ctypes.c_int]
     lib.oracle_modexp_batch.restype = ctypes.c_int
+    lib.oracle_miller_rabin.argtypes = [_u32p, sz, _u32p, sz]
+    lib.oracle_miller_rabin.restype = ctypes.c_int
     return lib
 
 
@@ -209,3 +211,32 @@ def crt_batch(msgs: np.ndarray, d: int, p: int, q: int, threads: int = 0, lib=No
 
 def default_threads(lib=None) -> int:
     return (lib or load()).oracle_default_threads()
+
+
+# ---------------------------------------------------------------- primality (key generation)
+
+def miller_rabin(n: int, bases, lib=None) -> int:
+    """Miller-Rabin with the given bases: 1 probable prime, 0 composite, -1 invalid n."""
+    lib = lib or load()
+    nm = limbs_for(n)
+    na = to_limbs(n, nm)
+    ba = np.concatenate([to_limbs(b, nm) for b in bases]) if len(bases) else np.zeros(nm, dtype=np.uint32)
+    return int(lib.oracle_miller_rabin(_ptr(na), nm, _ptr(np.ascontiguousarray(ba)), len(bases)))
+
+
+def miller_rabin_batch(cands: np.ndarray, bases: np.ndarray, threads: int = 0, lib=None) -> np.ndarray:
+    """cands: (count, L) uint32 rows; bases: (count, rounds, L).  Verdicts as int32."""
+    from concurrent.futures import ThreadPoolExecutor
+    lib = lib or load()
+    cands = np.ascontiguousarray(cands, dtype=np.uint32)
+    bases = np.ascontiguousarray(bases, dtype=np.uint32)
+    count, L = cands.shape
+    rounds = bases.shape[1]
+    out = np.zeros(count, dtype=np.int32)
+
+    def one(i):
+        out[i] = lib.oracle_miller_rabin(_ptr(cands[i]), L, _ptr(bases[i]), rounds)
+
+    with ThreadPoolExecutor(max_workers=threads or default_threads(lib)) as ex:
+        list(ex.map(one, range(count)))
+    return out

@@ -451,6 +451,47 @@ typedef struct {
     const oracle_batch_args *a;
 } batch_slice;
 
+/* ------------------------------------------------------------------ */
+/* Miller-Rabin probable-prime test (key generation, Fig. 1: "choose two   */
+/* large primes"; the paper names no test, this is the standard one)       */
+/* ------------------------------------------------------------------ */
+
+/* n odd, n >= 5, nm limbs; bases: nbases numbers of nm limbs, each in [2, n-2].
+ * Write n - 1 = d * 2^s with d odd.  Base a passes when a^d = 1 (mod n) or
+ * a^(d * 2^r) = n - 1 (mod n) for some 0 <= r < s.  Returns 1 when every base
+ * passes (n is a probable prime), 0 when some base witnesses that n is
+ * composite, -1 for an even n or n < 5.  Powers by the left-to-right binary
+ * method (Fig. 5), squarings by the schoolbook product and Algorithm D. */
+int oracle_miller_rabin(const uint32_t *n, size_t nm, const uint32_t *bases, size_t nbases) {
+    const uint32_t five = 5;
+    if ((n[0] & 1u) == 0 || nat_cmp(n, nm, &five, 1) < 0) return -1;
+    uint32_t *nm1 = calloc(nm, 4), *d = calloc(nm, 4), *x = calloc(nm, 4), *t = calloc(nm, 4);
+    uint32_t *one = calloc(nm, 4), *w = calloc(2 * nm, 4);
+    memcpy(nm1, n, nm * 4);
+    nm1[0] -= 1u;                               /* n odd: no borrow */
+    one[0] = 1u;
+    size_t s = 0;                               /* trailing zero bits of n - 1 */
+    while (!exp_bit(nm1, s)) s++;
+    for (size_t i = 0; i < nm; i++) {           /* d = (n - 1) >> s */
+        const size_t src = i + s / 32, sh = s % 32;
+        uint32_t lo = src < nm ? nm1[src] : 0u, hi = src + 1 < nm ? nm1[src + 1] : 0u;
+        d[i] = sh ? (lo >> sh) | (hi << (32 - sh)) : lo;
+    }
+    int result = 1;
+    for (size_t b = 0; b < nbases && result == 1; b++) {
+        oracle_modexp_l2r(bases + b * nm, nm, d, nm, n, nm, x);
+        int pass = nat_cmp(x, nm, one, nm) == 0 || nat_cmp(x, nm, nm1, nm) == 0;
+        for (size_t r = 1; r < s && !pass; r++) {
+            nat_mulmod(x, x, n, nm, t, w);
+            memcpy(x, t, nm * 4);
+            if (nat_cmp(x, nm, nm1, nm) == 0) pass = 1;
+        }
+        if (!pass) result = 0;
+    }
+    free(nm1); free(d); free(x); free(t); free(one); free(w);
+    return result;
+}
+
 static void run_one(const oracle_batch_args *a, size_t i) {
     const uint32_t *msg = a->msgs + i * a->msg_stride;
     uint32_t *out = a->out + i * a->out_stride;

@@ -55,6 +55,9 @@ typedef struct {
     size_t nh;
 } oracle_batch_args;
 
+/* Miller-Rabin: 1 probable prime, 0 composite, -1 invalid n (even or < 5). */
+int oracle_miller_rabin(const uint32_t *n, size_t nm, const uint32_t *bases, size_t nbases);
+
 int oracle_default_threads(void);
 int oracle_modexp_batch(const oracle_batch_args *a, size_t count, int nthreads);
 

@@ -25,7 +25,7 @@ __all__ = [
     "rsa_ctx_create", "rsa_ctx_destroy", "rsa_keyload", "rsa_key_record", "rsa_tc_operand_image",
     "rsa_keyunload", "rsa_key_info",
     "rsa_modexp_key", "rsa_modexp_batch", "rsa_modexp_key_host", "rsa_modexp_batch_host",
-    "rsa_sign_key", "rsa_verify_key",
+    "rsa_sign_key", "rsa_verify_key", "rsa_mr_batch",
     "rsa_sync", "rsa_last_error", "rsa_set_tuning", "rsa_get_tuning", "rsa_get_stats",
     "rsa_products_per_op", "rsa_imad_probe", "rsa_crt_decrypt_noalloc", "rsa_autotune",
     "rsa_server_start", "rsa_server_submit", "rsa_server_submit_many", "rsa_server_clock", "rsa_server_poll", "rsa_server_drain", "rsa_server_get_stats",
@@ -154,6 +154,11 @@ def rsa_sign_key(ctx: int, key_id: int, count: int, reps, sigs, op_status=None, 
 def rsa_verify_key(ctx: int, key_id: int, count: int, sigs, reps, op_status, stream=None) -> None:
     check(_lib.lib().rsa_verify_key(ctx, key_id, count, _ptr(sigs), _ptr(reps), _ptr(op_status),
                                     _stream_ptr(stream)))
+
+
+def rsa_mr_batch(ctx: int, nbits: int, count: int, cands, rounds: int, bases, verdicts, stream=None) -> None:
+    check(_lib.lib().rsa_mr_batch(ctx, nbits, count, _ptr(cands), rounds, _ptr(bases), _ptr(verdicts),
+                                  _stream_ptr(stream)))
 
 
 def rsa_modexp_batch(ctx: int, count: int, key_ids, exp_sel, limb_offsets, msgs, out, op_status=None,
@@ -346,6 +351,17 @@ class RsaContext:
             status = torch.empty(count, dtype=torch.int32, device=sigs.device)
         rsa_verify_key(self.handle, key_id, count, sigs, reps, status, stream)
         return status
+
+    def miller_rabin(self, nbits: int, cands, bases, verdicts=None, stream=None):
+        """cands: CUDA tensor [count, nbits/32]; bases: [count, rounds, nbits/32].
+        Returns int32 verdicts: 1 probable prime, 0 composite, -1 invalid."""
+        import torch
+        count = cands.shape[0]
+        rounds = bases.shape[1] if bases.dim() == 3 else 0
+        if verdicts is None:
+            verdicts = torch.empty(count, dtype=torch.int32, device=cands.device)
+        rsa_mr_batch(self.handle, nbits, count, cands, rounds, bases, verdicts, stream)
+        return verdicts
 
     def modexp_key_host(self, key_id: int, exp_sel: int, msgs: np.ndarray, out: np.ndarray | None = None,
                         status: np.ndarray | None = None, stream=None) -> np.ndarray:

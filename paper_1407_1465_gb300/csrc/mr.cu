@@ -1,0 +1,262 @@
+// mr.cu -- batch Miller-Rabin probable-prime tests (key generation, Fig. 1:
+// "choose two large primes"; the paper names no test, this is the standard one).
+//
+// One candidate per thread, 32 per warp.  Every candidate is its own modulus, so
+// its Montgomery constants are derived in the kernel:
+//   n' = -n^-1 mod 2^32   Newton's iteration on one word,
+//   R mod n               32L modular doublings of 1 (R = 2^(32L)),
+//   R^2 mod n             64 more doublings give 2^64 R mod n, then log2(L/2)
+//                         Montgomery squarings, each (2^k R)^2 / R = 2^(2k) R.
+// A round with base a: n - 1 = d 2^s with d odd; x = a^d mod n by the
+// constant-time fixed-window method with this lane's own exponent d (the
+// candidates are future secret primes), then up to s - 1 squarings looking for
+// n - 1.  In Montgomery form 1 is R mod n and n - 1 is n - (R mod n).  Loop
+// counts are the same for the whole warp (windows over 32L bits, squarings up
+// to the warp's largest s), so nothing diverges.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "kernels.cuh"
+#include "mont.cuh"
+#include "rsa_gb300.h"
+#include "runtime_internal.h"
+
+namespace rsagpu {
+
+namespace {
+
+constexpr int kMrWindow = 4;
+constexpr int kMrThreads = 128;
+
+struct MrArgs {
+  const uint32_t *cands;    // count rows of L limbs
+  const uint32_t *bases;    // count * rounds rows of L limbs, row i * rounds + r
+  int32_t *verdict;         // count: 1 probable prime, 0 composite, -1 invalid candidate
+  uint4 *tables;            // per warp 2^W * L/4 * 32 uint4
+  uint32_t count, rounds;
+};
+
+template <int L>
+struct MrSmem {
+  static constexpr int kStageU4 = (L / 4) * 32;   // one [L/4][32] uint4 buffer per warp
+  static constexpr int kBuffers = 5;              // B operand, R^2, one, minus one, exponent d
+  static constexpr size_t bytes(int warps) { return (size_t)warps * kBuffers * kStageU4 * 16; }
+};
+
+// x = 2x mod n for x < n: the doubled value has L limbs plus a top bit; one
+// conditional subtraction (2x < 2n), selected without a branch.
+template <int L>
+__device__ __forceinline__ void dbl_mod(uint32_t (&x)[L], const NRegs<L> &N) {
+  uint32_t y[L], t[L];
+  const uint32_t top = x[L - 1] >> 31;
+  y[0] = x[0] << 1;
+#pragma unroll
+  for (int j = 1; j < L; ++j) y[j] = __funnelshift_l(x[j - 1], x[j], 1);
+  t[0] = sub_cc(y[0], N.n[0]);
+#pragma unroll
+  for (int j = 1; j < L; ++j) t[j] = subc_cc(y[j], N.n[j]);
+  const uint32_t keep = subc(top, 0u);   // all ones iff 2x < n
+#pragma unroll
+  for (int j = 0; j < L; ++j) x[j] = (y[j] & keep) | (t[j] & ~keep);
+}
+
+// word j of a lane's number in a [L/4][32] stage (0 beyond the top)
+template <int L>
+__device__ __forceinline__ uint32_t stage_word(const uint4 *lane, int j) {
+  if (j >= L) return 0u;
+  const uint4 v = lane[(j >> 2) * 32];
+  const int c = j & 3;
+  return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w;
+}
+
+template <int L>
+__device__ __forceinline__ bool stage_equal(const uint32_t (&A)[L], const uint4 *lane) {
+  uint32_t diff = 0;
+#pragma unroll
+  for (int g = 0; g < L / 4; ++g) {
+    const uint4 v = lane[g * 32];
+    diff |= (A[4 * g] ^ v.x) | (A[4 * g + 1] ^ v.y) | (A[4 * g + 2] ^ v.z) | (A[4 * g + 3] ^ v.w);
+  }
+  return diff == 0;
+}
+
+template <int L, int W>
+__device__ __forceinline__ uint32_t lane_digit(const uint4 *d_lane, int k) {
+  const int bit = k * W;
+  const uint32_t lo = stage_word<L>(d_lane, bit >> 5), hi = stage_word<L>(d_lane, (bit >> 5) + 1);
+  return __funnelshift_r(lo, hi, bit & 31) & ((1u << W) - 1u);
+}
+
+template <int L, int W, int U>
+__global__ void __launch_bounds__(kMrThreads) mr_kernel(MrArgs a) {
+  using Sm = MrSmem<L>;
+  extern __shared__ uint4 smem4[];
+  const int nw = blockDim.x / 32, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint4 *base_w = smem4 + (size_t)warp * Sm::kBuffers * Sm::kStageU4 + lane;
+  uint4 *b_lane = base_w, *r2_lane = base_w + Sm::kStageU4, *one_lane = base_w + 2 * Sm::kStageU4;
+  uint4 *m1_lane = base_w + 3 * Sm::kStageU4, *d_lane = base_w + 4 * Sm::kStageU4;
+  uint4 *table_lane = a.tables + (size_t)(blockIdx.x * nw + warp) * (1 << W) * (L / 4) * 32 + lane;
+  const uint32_t ntiles = (a.count + 31) / 32;
+  constexpr int kSqToR2 = (L == 16) ? 3 : 4;    // log2(L / 2)
+  constexpr int kNwin = (32 * L + W - 1) / W;
+#pragma unroll 1
+  for (uint32_t tile = blockIdx.x * nw + warp; tile < ntiles; tile += gridDim.x * nw) {
+    const uint32_t i = tile * 32 + (uint32_t)lane;
+    const bool live = i < a.count;
+    const uint32_t row = live ? i : a.count - 1;
+    NRegs<L> N;
+    {
+      const uint4 *r4 = reinterpret_cast<const uint4 *>(a.cands + (size_t)row * L);
+#pragma unroll
+      for (int g = 0; g < L / 4; ++g) {
+        const uint4 v = r4[g];
+        N.n[4 * g] = v.x; N.n[4 * g + 1] = v.y; N.n[4 * g + 2] = v.z; N.n[4 * g + 3] = v.w;
+      }
+    }
+    uint32_t hi_or = 0;
+#pragma unroll
+    for (int j = 1; j < L; ++j) hi_or |= N.n[j];
+    const bool valid = (N.n[0] & 1u) && (hi_or != 0u || N.n[0] >= 5u);
+    if (!valid) N.n[0] |= 1u;                // keep the arithmetic defined; the verdict is -1 anyway
+    // n' = -n^-1 mod 2^32: x = n is right to 3 bits, each step doubles them
+    uint32_t inv = N.n[0];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) inv *= 2u - N.n[0] * inv;
+    const uint32_t np = 0u - inv;
+    uint32_t x[L];
+    // R mod n, and n - R mod n (the Montgomery forms of 1 and n - 1)
+#pragma unroll
+    for (int j = 0; j < L; ++j) x[j] = 0u;
+    x[0] = 1u;
+#pragma unroll 1
+    for (int k = 0; k < 32 * L; ++k) dbl_mod<L>(x, N);
+    to_stage<L>(one_lane, x);
+    {
+      uint32_t m1[L];
+      m1[0] = sub_cc(N.n[0], x[0]);
+#pragma unroll
+      for (int j = 1; j < L; ++j) m1[j] = subc_cc(N.n[j], x[j]);
+      to_stage<L>(m1_lane, m1);
+    }
+    // R^2 mod n
+#pragma unroll 1
+    for (int k = 0; k < 64; ++k) dbl_mod<L>(x, N);
+#pragma unroll 1
+    for (int k = 0; k < kSqToR2; ++k) {
+      to_stage<L>(b_lane, x);
+      mont_mul<L, U>(x, SmemB{b_lane, 32}, N, np);
+    }
+    to_stage<L>(r2_lane, x);
+    // n - 1 = d 2^s, d odd (n - 1 is n with bit 0 cleared)
+    int s = 0;
+    {
+      N.n[0] &= ~1u;
+      to_stage<L>(d_lane, N.n);
+      int j = 0;
+      while (j < L - 1 && stage_word<L>(d_lane, j) == 0u) ++j;
+      const uint32_t w = stage_word<L>(d_lane, j);
+      s = 32 * j + (w ? __ffs(w) - 1 : 0);
+      uint32_t d[L];
+      const int q = s >> 5, r = s & 31;
+#pragma unroll
+      for (int k = 0; k < L; ++k)
+        d[k] = __funnelshift_r(stage_word<L>(d_lane, k + q), stage_word<L>(d_lane, k + q + 1), r);
+      to_stage<L>(d_lane, d);
+      N.n[0] |= 1u;
+    }
+    const int s_max = __reduce_max_sync(0xffffffffu, s);
+    int verdict = 1;
+#pragma unroll 1
+    for (uint32_t rd = 0; rd < a.rounds; ++rd) {
+      uint32_t A[L];
+      load_row<L>(A, a.bases + ((size_t)row * a.rounds + rd) * L, true);
+      mont_mul<L, U>(A, SmemB{r2_lane, 32}, N, np);            // a R
+      // table T[e] = a^e R, e < 2^W (T[0] = R mod n), then the fixed windows
+#pragma unroll
+      for (int g = 0; g < L / 4; ++g) table_lane[g * 32] = one_lane[g * 32];   // T[0] = R mod n
+      table_store<L>(table_lane, 1, A);
+      to_stage<L>(b_lane, A);
+#pragma unroll 1
+      for (int e = 2; e < (1 << W); ++e) {
+        mont_mul<L, U>(A, SmemB{b_lane, 32}, N, np);
+        table_store<L>(table_lane, e, A);
+      }
+      table_select<L, W>(b_lane, table_lane, lane_digit<L, W>(d_lane, kNwin - 1));
+      from_stage<L>(A, b_lane);
+      int k = kNwin - 2, sq = 0;
+      const int nsteps = (kNwin - 1) * (W + 1);
+#pragma unroll 1
+      for (int st = 0; st < nsteps; ++st) {
+        if (sq < W) {
+          to_stage<L>(b_lane, A);
+          ++sq;
+        } else {
+          table_select<L, W>(b_lane, table_lane, lane_digit<L, W>(d_lane, k));
+          sq = 0;
+          --k;
+        }
+        mont_mul<L, U>(A, SmemB{b_lane, 32}, N, np);
+      }
+      bool pass = stage_equal<L>(A, one_lane) || stage_equal<L>(A, m1_lane);
+#pragma unroll 1
+      for (int j = 1; j < s_max; ++j) {
+        to_stage<L>(b_lane, A);
+        mont_mul<L, U>(A, SmemB{b_lane, 32}, N, np);
+        if (j < s && stage_equal<L>(A, m1_lane)) pass = true;
+      }
+      if (!pass) verdict = 0;
+    }
+    if (live) a.verdict[i] = valid ? verdict : -1;
+  }
+}
+
+template <int L>
+cudaError_t launch_mr(const MrArgs &h, int grid, cudaStream_t s) {
+  const size_t smem = MrSmem<L>::bytes(kMrThreads / 32);
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(mr_kernel<L, kMrWindow, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  mr_kernel<L, kMrWindow, 8><<<grid, kMrThreads, smem, s>>>(h);
+  return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace rsagpu
+
+using namespace rsagpu;
+
+extern "C" int rsa_mr_batch(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *cands, uint32_t rounds,
+                            const uint32_t *bases, int32_t *verdicts, void *stream) {
+  if (!ctx) return set_error(RSA_ERR_ARG, "ctx is null");
+  if (nbits != 512 && nbits != 1024) return set_error(RSA_ERR_UNSUPPORTED, "candidates of 512 or 1024 bits");
+  if (count == 0) return RSA_OK;
+  if (!cands || !verdicts || (rounds > 0 && !bases)) return set_error(RSA_ERR_ARG, "null pointer");
+  if (count > 0x7fffffffull || rounds > 256) return set_error(RSA_ERR_ARG, "count or rounds out of range");
+  if ((reinterpret_cast<uintptr_t>(cands) | reinterpret_cast<uintptr_t>(bases)) & 15u)
+    return set_error(RSA_ERR_ARG, "candidate and base rows must be 16-byte aligned");
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  std::lock_guard<std::mutex> lock(c->mu);
+  cudaSetDevice(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Workspace &w = c->ws(s);
+  const int L = (int)nbits / 32;
+  const uint64_t warps_needed = (count + 31) / 32;
+  const int per_cta = kMrThreads / 32;
+  const int grid = (int)std::max<uint64_t>(
+      1, std::min<uint64_t>((warps_needed + per_cta - 1) / per_cta, (uint64_t)c->sm_count * 4));
+  const size_t tbytes = (size_t)grid * per_cta * ((size_t)1 << kMrWindow) * (size_t)(L / 4) * 32 * 16;
+  int rc = c->ensure(w.tables, tbytes);
+  if (rc) return rc;
+  MrArgs h{cands, bases, verdicts, static_cast<uint4 *>(w.tables.ptr), (uint32_t)count, rounds};
+  cudaError_t e = (L == 16) ? launch_mr<16>(h, grid, s) : launch_mr<32>(h, grid, s);
+  if (e != cudaSuccess) return cuda_error(e, "launch mr_kernel");
+  c->stats.kernel_launches++;
+  c->stats.ops += count;
+  return RSA_OK;
+}

@@ -56,6 +56,13 @@ MUTANTS = [
      "uint64_t t = (uint64_t)hq[i] + carry;"),
     ("naive one multiplication short", "for (uint64_t k = 2; k <= e; k++) {",
      "for (uint64_t k = 3; k <= e; k++) {"),
+    ("mr skips the a^d = n-1 check", "int pass = nat_cmp(x, nm, one, nm) == 0 || nat_cmp(x, nm, nm1, nm) == 0;",
+     "int pass = nat_cmp(x, nm, one, nm) == 0;"),
+    ("mr one squaring short", "for (size_t r = 1; r < s && !pass; r++) {",
+     "for (size_t r = 2; r < s && !pass; r++) {"),
+    ("mr accepts a square root of 1", "            if (nat_cmp(x, nm, nm1, nm) == 0) pass = 1;",
+     "            if (nat_cmp(x, nm, nm1, nm) == 0 || nat_cmp(x, nm, one, nm) == 0) pass = 1;"),
+    ("mr exponent not halved enough", "while (!exp_bit(nm1, s)) s++;", "while (!exp_bit(nm1, s + 1)) s++;"),
 ]
 
 
@@ -114,6 +121,23 @@ def battery(lib) -> list:
                 fails.append("kary")
             if e and oracle.modexp(gg, e, m, "sliding", k=k, lib=lib) != ref:
                 fails.append("sliding")
+    # Miller-Rabin: trial division below 3000 (bases 2, 3, 5, 7 are exact there),
+    # the strong pseudoprime 2047 (passes base 2 only), Carmichael numbers
+    try:
+        for n in range(5, 3000, 2):
+            bases = [b for b in (2, 3, 5, 7) if b <= n - 2]
+            isp = all(n % f for f in range(3, int(n ** 0.5) + 1, 2))
+            if oracle.miller_rabin(n, bases, lib=lib) != int(isp):
+                fails.append("mr trial division")
+                break
+        if oracle.miller_rabin(2047, [2], lib=lib) != 1 or oracle.miller_rabin(2047, [3], lib=lib) != 0:
+            fails.append("mr 2047")
+        if any(oracle.miller_rabin(n, [2], lib=lib) != 0 for n in (561, 1105, 1729, 8911)):
+            fails.append("mr carmichael")
+        if oracle.miller_rabin((1 << 127) - 1, [3, 5, 7], lib=lib) != 1:
+            fails.append("mr mersenne")
+    except Exception as exc:
+        fails.append("mr raised %r" % exc)
     key = workloads.gen_key(256, seed=5, index=1, mr_rounds=10)
     for mm in workloads.rows_to_ints(workloads.messages_below(key.n, 8, 5, "mut")):
         c = pow(mm, key.e, key.n)

@@ -10,6 +10,7 @@ Sources of truth used here:
 """
 import random
 
+import numpy as np
 import pytest
 
 import oracle
@@ -194,3 +195,52 @@ def test_batch_driver_matches_scalar(oracle_lib):
     want = [pow(m, key.d, key.n) for m in ints]
     assert workloads.rows_to_ints(out_plain) == want
     assert workloads.rows_to_ints(out_crt) == want
+
+
+# ------------------------------------------------------------------ Miller-Rabin (key generation, Fig. 1)
+
+def _trial_division_prime(n):
+    if n < 2:
+        return False
+    f = 2
+    while f * f <= n:
+        if n % f == 0:
+            return False
+        f += 1
+    return True
+
+
+def test_miller_rabin_matches_trial_division_small(oracle_lib):
+    """Bases 2, 3, 5, 7 decide primality exactly below 3 215 031 751."""
+    for n in range(5, 6000, 2):
+        bases = [b for b in (2, 3, 5, 7) if b <= n - 2]
+        assert oracle.miller_rabin(n, bases) == int(_trial_division_prime(n)), n
+
+
+def test_miller_rabin_strong_pseudoprimes_and_carmichael(oracle_lib):
+    # 2047 = 23 * 89 is the smallest strong pseudoprime to base 2: base 2 passes, base 3 does not
+    assert oracle.miller_rabin(2047, [2]) == 1
+    assert oracle.miller_rabin(2047, [3]) == 0
+    # Carmichael numbers fool the Fermat test for every coprime base but not Miller-Rabin base 2
+    for n in (561, 1105, 1729, 2465, 2821, 6601, 8911):
+        assert oracle.miller_rabin(n, [2]) == 0, n
+    # F5 = 2^32 + 1 = 641 * 6700417 and 2^67 - 1 = 193707721 * 761838257287 are composite
+    assert oracle.miller_rabin((1 << 32) + 1, [3]) == 0
+    assert 193707721 * 761838257287 == (1 << 67) - 1
+    assert oracle.miller_rabin((1 << 67) - 1, [3, 5]) == 0
+    # but 2^p - 1 (p prime) always passes base 2: 2^p = 1 (mod n); a strong-pseudoprime pin
+    assert oracle.miller_rabin((1 << 67) - 1, [2]) == 1
+    # even and tiny inputs are rejected
+    assert oracle.miller_rabin(10, [3]) == -1 and oracle.miller_rabin(3, [2]) == -1
+
+
+def test_miller_rabin_mersenne_primes(oracle_lib):
+    """2^127 - 1, 2^521 - 1 and 2^607 - 1 are prime: every base passes."""
+    rng = np.random.default_rng(11)
+    for p in (127, 521, 607):
+        n = (1 << p) - 1
+        bases = [2 + int.from_bytes(rng.bytes(p // 8 + 1), "little") % (n - 3) for _ in range(6)]
+        assert oracle.miller_rabin(n, bases) == 1, p
+    # and a product of two of them is not
+    n = ((1 << 127) - 1) * ((1 << 521) - 1)
+    assert oracle.miller_rabin(n, [2, 3]) == 0
