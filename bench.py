@@ -378,7 +378,7 @@ def run_serving(args):
     scratch = [np.zeros_like(p) for p in pools]
     rates = [float(r) for r in args.rates.split(",")]
     results = []
-    rsa_server_start(ctx.handle, max_inflight_batches=4, batch_window_us=args.window_us, mem_budget_bytes=2 << 30)
+    rsa_server_start(ctx.handle, max_inflight_batches=args.slots, batch_window_us=args.window_us, mem_budget_bytes=2 << 30)
     for i in range(64):   # warm-up: graphs and workspaces of every slot
         k = i % len(kids)
         rsa_server_submit(ctx.handle, kids[k], 1, pools[k][:8], scratch[k][:8])
@@ -406,7 +406,8 @@ def run_serving(args):
             "dtype": "u32", "data": "synthetic",
             "config": {"workload": "256 ragged keys, 1-64 msgs/request, 70%% CRT / 30%% public, 2 GiB budget, "
                                    "%.1f s of arrivals per rate" % args.duration, "rates": rates,
-                       "batch_window_us": args.window_us},
+                       "batch_window_us": args.window_us, "slots": args.slots,
+                       "batching": "one modulus size per batch (the oldest waiting request picks it)"},
             "sweep": results}
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -489,6 +490,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="rsa2048", choices=sorted(WORKLOADS) + ["ragged", "serving", "toy", "mr"])
+    ap.add_argument("--slots", type=int, default=8, help="serving: batches in flight at once")
     ap.add_argument("--e-bits", type=int, default=0,
                     help="--kind public: a seeded random public exponent of this many bits instead of 65537")
     ap.add_argument("--kind", default="crt", choices=["crt", "public"],

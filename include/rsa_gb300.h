@@ -204,13 +204,15 @@ int rsa_crt_decrypt_noalloc(const uint32_t *key_record, uint32_t nbits, uint64_t
 /* ---------------------------------------------------------------- serving
  * A request loop on top of rsa_modexp_batch.  A scheduler thread admits
  * requests when they have arrived and their device footprint fits the budget,
- * packs every admitted request (any keys, sizes, kinds) into one ragged batch
- * per free slot, and runs up to max_inflight_batches batches at once on
- * separate streams, so requests arriving while others are on the GPU start
- * without waiting for them (continuous batching).  Key state stays resident
- * in the context.  Results are copied into each request's host buffer. */
+ * packs admitted requests of one modulus size (any keys and kinds of that size;
+ * the oldest waiting request picks the size) into one ragged batch per free
+ * slot, and runs up to max_inflight_batches batches at once on separate
+ * streams, so requests arriving while others are on the GPU start without
+ * waiting for them (continuous batching) and a batch finishes at its own size's
+ * latency.  Key state stays resident in the context.  Results are copied into
+ * each request's host buffer. */
 typedef struct rsa_server_cfg {
-    int32_t max_inflight_batches; /* concurrent batches (streams); 0 -> 4 */
+    int32_t max_inflight_batches; /* concurrent batches (streams); 0 -> 8 */
     int32_t batch_window_us;      /* wait this long after the first arrival for more; 0 -> 200 */
     int32_t max_batch_ops;        /* operations per batch; 0 -> 65536 */
     int32_t reserved;

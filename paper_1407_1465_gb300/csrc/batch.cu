@@ -180,6 +180,7 @@ struct BatchState {
   cudaGraphExec_t exec = nullptr;
   cudaGraphNode_t nodes[4 + GRP_COUNT] = {};
   int exec_grid = 0;
+  int grids_exec[GRP_COUNT] = {};
   DevBuf keydir;
   uint64_t keydir_epoch = ~0ull;
 };
@@ -232,9 +233,11 @@ static BatchState *state_for(Ctx *c, cudaStream_t s) {
   return b;
 }
 
-int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_sel, const uint64_t *offsets,
-                   const uint32_t *msgs, uint32_t *out, int32_t *status, cudaStream_t s) {
-  if (count == 0) return RSA_OK;
+// Key directory and scratch of the ragged path on stream s, sized for batches
+// of up to max_count operations.  Growing a buffer frees the old one, which
+// waits for the whole device, so callers that keep batches in flight on
+// several streams (the request loop) size them once up front.
+int Ctx::prepare_batch(cudaStream_t s, uint64_t max_count) {
   BatchState *st = state_for(this, s);
   Workspace &w = ws(s);
   const uint32_t nkeys = (uint32_t)keys.size();
@@ -254,14 +257,13 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
     st->keydir_epoch = key_epoch;
   }
   const uint32_t nb = std::max<uint32_t>(nkeys, 1) * 3;
-  const uint32_t max_tiles = (uint32_t)(count / 8 + nb + 1);   // smallest tile: 8 operations
+  const uint64_t max_tiles = max_count / 8 + nb + 1;   // smallest tile: 8 operations
   int rc;
-  if ((rc = ensure(w.aux0, (size_t)count * 8)) ||                  // op_bucket + sorted
-      (rc = ensure(w.aux1, (size_t)nb * 12)) ||                    // bcount, bfill, boff
+  if ((rc = ensure(w.aux0, (size_t)max_count * 8)) ||                  // op_bucket + sorted
+      (rc = ensure(w.aux1, (size_t)nb * 12)) ||                        // bcount, bfill, boff
       (rc = ensure(w.aux2, (size_t)max_tiles * sizeof(TileDesc))) ||
       (rc = ensure(w.aux3, 64)))
     return rc;
-  int grids_exec[GRP_COUNT];
   int max_grid = 0;
   for (int g = 0; g < GRP_COUNT; ++g) {
     const void *fn = batch_exec_fn(g);
@@ -273,15 +275,30 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
     if (e != cudaSuccess) return cuda_error(e, "occupancy(batch_exec)");
     const Tune t = tune_for(0, RSA_TUNE_RAGGED);
     if (t.ctas_per_sm > 0) per_sm = std::min(per_sm, t.ctas_per_sm);
-    grids_exec[g] = std::max(1, per_sm) * sm_count;
-    max_grid = std::max(max_grid, grids_exec[g]);
+    st->grids_exec[g] = std::max(1, per_sm) * sm_count;
+    max_grid = std::max(max_grid, st->grids_exec[g]);
   }
   st->exec_grid = max_grid;
   // window tables: one slot per resident warp of each group (groups run concurrently)
   const size_t slot_u4 = (size_t)2 * kBatchTableU4PerWarp;
   size_t all_slots = 0;
-  for (int gi = 0; gi < GRP_COUNT; ++gi) all_slots += (size_t)grids_exec[gi];
-  if ((rc = ensure(w.tables, all_slots * slot_u4 * 16))) return rc;
+  for (int gi = 0; gi < GRP_COUNT; ++gi) all_slots += (size_t)st->grids_exec[gi];
+  return ensure(w.tables, all_slots * slot_u4 * 16);
+}
+
+int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_sel, const uint64_t *offsets,
+                   const uint32_t *msgs, uint32_t *out, int32_t *status, cudaStream_t s) {
+  if (count == 0) return RSA_OK;
+  int rc = prepare_batch(s, count);
+  if (rc) return rc;
+  BatchState *st = state_for(this, s);
+  Workspace &w = ws(s);
+  const uint32_t nkeys = (uint32_t)keys.size();
+  const uint32_t nb = std::max<uint32_t>(nkeys, 1) * 3;
+  const uint32_t max_tiles = (uint32_t)(count / 8 + nb + 1);
+  int grids_exec[GRP_COUNT];
+  for (int g = 0; g < GRP_COUNT; ++g) grids_exec[g] = st->grids_exec[g];
+  const size_t slot_u4 = (size_t)2 * kBatchTableU4PerWarp;
 
   BatchDesc d{};
   d.count = (uint32_t)count;

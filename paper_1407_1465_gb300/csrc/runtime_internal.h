@@ -71,6 +71,7 @@ struct Ctx {
                   int ctas_per_sm_req, int *grid_out);
   int run_key(const KeySlot &k, int kind, uint64_t count, const uint32_t *msgs, uint32_t *out,
               int32_t *status, cudaStream_t s);
+  int prepare_batch(cudaStream_t s, uint64_t max_count);
   int run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_sel, const uint64_t *offsets,
                 const uint32_t *msgs, uint32_t *out, int32_t *status, cudaStream_t s);
   int collect_device_errors(cudaStream_t s);

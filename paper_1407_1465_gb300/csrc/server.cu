@@ -140,6 +140,11 @@ int Server::init() {
     p += align256((size_t)s.cap_ops * 4);
     s.d_msgs = reinterpret_cast<uint32_t *>(p);
     s.d_out = s.d_msgs + s.cap_limbs;
+    // the ragged path's scratch on this slot's stream, sized for the slot's
+    // largest batch now, so no buffer grows (and waits for the device) later
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    rc = ctx->prepare_batch(s.stream, s.cap_ops);
+    if (rc) return rc;
   }
   return RSA_OK;
 }
@@ -264,14 +269,19 @@ void Server::loop() {
     const uint64_t t = now_ns();
     bool launched = false;
     if (free_slot && !queue.empty() && queue.front()->arrive <= t && !fatal) {
-      // wait (briefly) after the first arrival for more, unless the batch is already full
+      // A batch carries one modulus size: the oldest waiting request fixes it
+      // and requests of other sizes wait for another slot, so a batch finishes
+      // at its own size's latency instead of the slowest size's.  Wait
+      // (briefly) after that request's arrival for more, unless the batch is full.
       const uint64_t window = (uint64_t)cfg.batch_window_us * 1000ull;
       const uint64_t first = queue.front()->arrive;
+      const uint32_t cls = queue.front()->L;
       uint32_t ops = 0;
       uint64_t limbs = 0;
       bool full = false;
       for (Req *r : queue) {
         if (r->arrive > t) break;
+        if (r->L != cls) continue;
         const uint64_t l = (limbs + 3) / 4 * 4 + (uint64_t)r->count * r->L;
         if (ops + r->count > free_slot->cap_ops || l > free_slot->cap_limbs) {
           full = true;
@@ -284,15 +294,19 @@ void Server::loop() {
         batch.clear();
         ops = 0;
         limbs = 0;
-        while (!queue.empty()) {
-          Req *r = queue.front();
+        for (size_t qi = 0; qi < queue.size();) {
+          Req *r = queue[qi];
           if (r->arrive > t) break;
+          if (r->L != cls) {
+            ++qi;
+            continue;
+          }
           const uint64_t l = (limbs + 3) / 4 * 4 + (uint64_t)r->count * r->L;
           if (ops + r->count > free_slot->cap_ops || l > free_slot->cap_limbs) break;
           ops += r->count;
           limbs = l;
           batch.push_back(r);
-          queue.pop_front();
+          queue.erase(queue.begin() + (long)qi);
         }
         if (!batch.empty()) {
           uint64_t bytes = 0;
@@ -339,7 +353,7 @@ int rsa_server_start(rsa_ctx *ctx, const rsa_server_cfg *cfg) {
   Server *s = new Server();
   s->ctx = c;
   if (cfg) s->cfg = *cfg;
-  if (s->cfg.max_inflight_batches <= 0) s->cfg.max_inflight_batches = 4;
+  if (s->cfg.max_inflight_batches <= 0) s->cfg.max_inflight_batches = 8;
   if (s->cfg.batch_window_us <= 0) s->cfg.batch_window_us = 200;
   if (s->cfg.max_batch_ops <= 0) s->cfg.max_batch_ops = 65536;
   if (s->cfg.mem_budget_bytes == 0) s->cfg.mem_budget_bytes = (uint64_t)2 << 30;
