@@ -73,6 +73,8 @@ def _bind(lib):
     lib.oracle_modexp_batch.restype = ctypes.c_int
     lib.oracle_miller_rabin.argtypes = [_u32p, sz, _u32p, sz]
     lib.oracle_miller_rabin.restype = ctypes.c_int
+    lib.oracle_batch_gcd_row.argtypes = [_u32p, sz, sz, sz, _u32p]
+    lib.oracle_batch_gcd_row.restype = ctypes.c_int
     return lib
 
 
@@ -240,3 +242,26 @@ def miller_rabin_batch(cands: np.ndarray, bases: np.ndarray, threads: int = 0, l
     with ThreadPoolExecutor(max_workers=threads or default_threads(lib)) as ex:
         list(ex.map(one, range(count)))
     return out
+
+
+# ---------------------------------------------------------------- batch GCD (weak-key detection)
+
+def batch_gcd(moduli: np.ndarray, rows=None, threads: int = 0, lib=None) -> tuple[np.ndarray, np.ndarray]:
+    """moduli: (count, L) uint32 rows.  For each selected row i (all by default)
+    g_i = gcd(n_i, product of the other valid moduli) and its flag (-1 invalid
+    n_i, 0 g = 1, 1 proper factor, 2 g = n_i).  Returns (gcds, flags) in the
+    order of ``rows``."""
+    from concurrent.futures import ThreadPoolExecutor
+    lib = lib or load()
+    mods = np.ascontiguousarray(moduli, dtype=np.uint32)
+    count, L = mods.shape
+    rows = list(range(count)) if rows is None else [int(r) for r in rows]
+    gcds = np.zeros((len(rows), L), dtype=np.uint32)
+    flags = np.zeros(len(rows), dtype=np.int32)
+
+    def one(k):
+        flags[k] = lib.oracle_batch_gcd_row(_ptr(mods), count, L, rows[k], _ptr(gcds[k]))
+
+    with ThreadPoolExecutor(max_workers=threads or default_threads(lib)) as ex:
+        list(ex.map(one, range(len(rows))))
+    return gcds, flags

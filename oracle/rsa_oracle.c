@@ -492,6 +492,49 @@ int oracle_miller_rabin(const uint32_t *n, size_t nm, const uint32_t *bases, siz
     return result;
 }
 
+/* ------------------------------------------------------------------ */
+/* Batch GCD (weak-key detection, the introduction's motivation)       */
+/* ------------------------------------------------------------------ */
+
+/* a modulus takes part when it is odd and at least 3 */
+static int valid_modulus(const uint32_t *n, size_t L) {
+    const uint32_t three = 3;
+    return (n[0] & 1u) && nat_cmp(n, L, &three, 1) >= 0;
+}
+
+/* g (L limbs) = gcd(n_i, product of the other valid moduli), by the
+ * definition taken modulo n_i: r = 1, r = r * (n_j mod n_i) mod n_i for every
+ * valid j != i (Fig. 3's identity), then Euclid's algorithm,
+ * gcd(a, b) = gcd(b, a mod b) until b = 0, with Algorithm D remainders.
+ * Returns -1 for an invalid n_i (g = 0), 0 when g = 1, 2 when g = n_i and 1
+ * otherwise. */
+int oracle_batch_gcd_row(const uint32_t *mods, size_t count, size_t L, size_t i, uint32_t *g) {
+    const uint32_t *ni = mods + i * L;
+    memset(g, 0, L * 4);
+    if (!valid_modulus(ni, L)) return -1;
+    uint32_t *r = calloc(L, 4), *x = calloc(L, 4), *t = calloc(L, 4), *w = calloc(2 * L, 4);
+    uint32_t *a = calloc(L, 4);
+    r[0] = 1u;
+    for (size_t j = 0; j < count; j++) {
+        const uint32_t *nj = mods + j * L;
+        if (j == i || !valid_modulus(nj, L)) continue;
+        reduce(nj, L, ni, L, x);
+        nat_mulmod(r, x, ni, L, t, w);
+        memcpy(r, t, L * 4);
+    }
+    memcpy(a, ni, L * 4);
+    while (nat_len(r, L) != 0) {
+        nat_divmod(a, L, r, L, NULL, t);
+        memcpy(a, r, L * 4);
+        memcpy(r, t, L * 4);
+    }
+    memcpy(g, a, L * 4);
+    const uint32_t one = 1;
+    const int flag = nat_cmp(g, L, &one, 1) == 0 ? 0 : nat_cmp(g, L, ni, L) == 0 ? 2 : 1;
+    free(r); free(x); free(t); free(w); free(a);
+    return flag;
+}
+
 static void run_one(const oracle_batch_args *a, size_t i) {
     const uint32_t *msg = a->msgs + i * a->msg_stride;
     uint32_t *out = a->out + i * a->out_stride;

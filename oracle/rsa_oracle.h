@@ -58,6 +58,11 @@ typedef struct {
 /* Miller-Rabin: 1 probable prime, 0 composite, -1 invalid n (even or < 5). */
 int oracle_miller_rabin(const uint32_t *n, size_t nm, const uint32_t *bases, size_t nbases);
 
+/* Batch GCD, one row: g (L limbs) = gcd(n_i, prod of the other valid moduli);
+ * mods holds count rows of L limbs; a modulus is valid when odd and >= 3.
+ * Returns -1 invalid n_i (g = 0), 0 g = 1, 1 proper factor, 2 g = n_i. */
+int oracle_batch_gcd_row(const uint32_t *mods, size_t count, size_t L, size_t i, uint32_t *g);
+
 int oracle_default_threads(void);
 int oracle_modexp_batch(const oracle_batch_args *a, size_t count, int nthreads);
 

@@ -63,6 +63,17 @@ MUTANTS = [
     ("mr accepts a square root of 1", "            if (nat_cmp(x, nm, nm1, nm) == 0) pass = 1;",
      "            if (nat_cmp(x, nm, nm1, nm) == 0 || nat_cmp(x, nm, one, nm) == 0) pass = 1;"),
     ("mr exponent not halved enough", "while (!exp_bit(nm1, s)) s++;", "while (!exp_bit(nm1, s + 1)) s++;"),
+    ("bgcd multiplies n_i into its own product", "if (j == i || !valid_modulus(nj, L)) continue;",
+     "if (!valid_modulus(nj, L)) continue;"),
+    ("bgcd keeps invalid moduli", "if (j == i || !valid_modulus(nj, L)) continue;", "if (j == i) continue;"),
+    ("bgcd rejects the modulus 3", "return (n[0] & 1u) && nat_cmp(n, L, &three, 1) >= 0;",
+     "return (n[0] & 1u) && nat_cmp(n, L, &three, 1) > 0;"),
+    ("bgcd returns the last remainder", "    memcpy(g, a, L * 4);\n    const uint32_t one", "    memcpy(g, r, L * 4);\n    const uint32_t one"),
+    ("bgcd euclid updates in the wrong order", "        memcpy(a, r, L * 4);\n        memcpy(r, t, L * 4);\n",
+     "        memcpy(r, t, L * 4);\n        memcpy(a, r, L * 4);\n"),
+    ("bgcd product forgets earlier factors", "        nat_mulmod(r, x, ni, L, t, w);\n        memcpy(r, t, L * 4);\n",
+     "        memcpy(r, x, L * 4);\n"),
+    ("bgcd flags swapped", "nat_cmp(g, L, ni, L) == 0 ? 2 : 1;", "nat_cmp(g, L, ni, L) == 0 ? 1 : 2;"),
 ]
 
 
@@ -138,6 +149,27 @@ def battery(lib) -> list:
             fails.append("mr mersenne")
     except Exception as exc:
         fails.append("mr raised %r" % exc)
+    # batch GCD: constructed sharing and brute force on tiny moduli.  Euclid's
+    # loop ends only with a correct remainder, so these run only when division
+    # passed (a broken division is already caught above)
+    try:
+        if any(f.startswith("divmod") for f in fails):
+            raise StopIteration
+        import bgcd_cases
+        values, _, want, flags = bgcd_cases.constructed_case()
+        g, f = oracle.batch_gcd(workloads.ints_to_rows(values, 8), threads=2, lib=lib)
+        if workloads.rows_to_ints(g) != want or f.tolist() != flags:
+            fails.append("bgcd constructed")
+        for mods in bgcd_cases.brute_cases(trials=15):
+            want, flags = bgcd_cases.brute_case(mods)
+            g, f = oracle.batch_gcd(workloads.ints_to_rows(mods, 1), threads=1, lib=lib)
+            if workloads.rows_to_ints(g) != want or f.tolist() != flags:
+                fails.append("bgcd brute force")
+                break
+    except StopIteration:
+        pass
+    except Exception as exc:
+        fails.append("bgcd raised %r" % exc)
     key = workloads.gen_key(256, seed=5, index=1, mr_rounds=10)
     for mm in workloads.rows_to_ints(workloads.messages_below(key.n, 8, 5, "mut")):
         c = pow(mm, key.e, key.n)

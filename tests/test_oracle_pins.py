@@ -244,3 +244,47 @@ def test_miller_rabin_mersenne_primes(oracle_lib):
     # and a product of two of them is not
     n = ((1 << 127) - 1) * ((1 << 521) - 1)
     assert oracle.miller_rabin(n, [2, 3]) == 0
+
+
+# ------------------------------------------------------------------ batch GCD (weak-key detection)
+
+def _ints_rows(vals, L):
+    return workloads.ints_to_rows(vals, L)
+
+
+def test_batch_gcd_constructed_sharing(oracle_lib):
+    """Planted shared primes (21-bit primes and Mersenne primes, a duplicate, a
+    prime square, invalid entries holding primes of valid moduli): every g_i
+    equals the value read off the known factorisations."""
+    import bgcd_cases
+    values, _, want, flags = bgcd_cases.constructed_case()
+    L = 8                                                  # 2^127-1 squared-scale moduli fit 256 bits
+    assert max(values).bit_length() <= 32 * L
+    g, f = oracle.batch_gcd(_ints_rows(values, L), threads=3)
+    assert workloads.rows_to_ints(g) == want
+    assert f.tolist() == flags
+    assert sorted(set(flags)) == [-1, 0, 1, 2]
+
+
+def test_batch_gcd_brute_force_tiny(oracle_lib):
+    """Tiny moduli: the largest common divisor of n_i and the exact product of
+    the others, found by scanning every candidate divisor."""
+    import bgcd_cases
+    for mods in bgcd_cases.brute_cases():
+        want, flags = bgcd_cases.brute_case(mods)
+        g, f = oracle.batch_gcd(_ints_rows(mods, 1), threads=2)
+        assert workloads.rows_to_ints(g) == want, mods
+        assert f.tolist() == flags, mods
+
+
+def test_batch_gcd_special_cases(oracle_lib):
+    # one modulus: the product of the others is empty (1), so g = 1
+    g, f = oracle.batch_gcd(_ints_rows([MERSENNE_127 := (1 << 127) - 1], 4))
+    assert workloads.rows_to_ints(g) == [1] and f.tolist() == [0]
+    # every other modulus invalid: still g = 1
+    g, f = oracle.batch_gcd(_ints_rows([MERSENNE_127, 0, 2, 1, 1 << 100], 4))
+    assert workloads.rows_to_ints(g) == [1, 0, 0, 0, 0] and f.tolist() == [0, -1, -1, -1, -1]
+    # selected rows come back in the order asked for
+    vals = [15, 21, 35, 143]
+    g, f = oracle.batch_gcd(_ints_rows(vals, 1), rows=[3, 0])
+    assert workloads.rows_to_ints(g) == [1, 15] and f.tolist() == [0, 2]

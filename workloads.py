@@ -21,6 +21,9 @@ Workloads (sizes as in the benchmark configurations):
   ragged   256 keys with sizes {1024, 2048, 3072, 4096} (p = .1/.5/.2/.2),
            Zipf(1.1) per-key counts summing to 200000, 70% CRT / 30% public
   serving  Poisson arrivals, 1..64 messages per request, keys of the ragged set
+  bgcd     weak-key scan: 16384 RSA-2048-shaped moduli n = a b (a, b random odd
+           1024-bit numbers with the top two bits set), 16 planted pairs that
+           reuse a factor
 """
 from __future__ import annotations
 
@@ -429,3 +432,41 @@ def poisson_requests(rate: float, duration: float, num_keys: int, seed: int,
         out.append(Request(t_arrive=t, key_id=st.below(num_keys),
                            exp_sel=EXP_PRIVATE_CRT if st.uniform01() < crt_frac else EXP_PUBLIC,
                            count=min_msgs + st.below(max_msgs - min_msgs + 1)))
+
+
+# ------------------------------------------------------------------ batch GCD (weak-key scan)
+
+def random_odd_halves(count: int, bits: int, seed: int, tag) -> list[int]:
+    """``count`` random odd ``bits``-bit integers with the top two bits set."""
+    words64 = (bits + 63) // 64
+    w = draws(stream_key(seed, "half", bits, tag), 0, count * words64).reshape(count, words64)
+    vals = rows_to_ints(w.view(np.uint32).reshape(count, 2 * words64))
+    top = 3 << (bits - 2)
+    mask = (1 << bits) - 1
+    return [(v & mask) | top | 1 for v in vals]
+
+
+def weak_key_moduli(count: int = 16384, bits: int = 2048, seed: int = DEFAULT_SEED, shared: int = 16):
+    """RSA-shaped moduli n_i = a_i b_i (a_i, b_i random odd bits/2-bit numbers,
+    top two bits set, so n_i has bits or bits - 1 bits) with ``shared`` planted
+    pairs (i, j): n_j = a_i b_j reuses n_i's factor a_i.  The halves are not
+    forced to be prime (the scan's arithmetic is the same), so unplanted pairs
+    may also share small factors.  Returns (rows (count, bits/32) uint32, pairs)."""
+    a = random_odd_halves(count, bits // 2, seed, ("a", count))
+    b = random_odd_halves(count, bits // 2, seed, ("b", count))
+    pairs = []
+    if count >= 2 and shared:
+        key = stream_key(seed, "pairs", count, bits)
+        pos = (draws(key, 0, 4 * shared) % np.uint64(count)).astype(np.int64).tolist()
+        used = set()
+        for k in range(0, len(pos), 2):
+            i, j = pos[k], pos[k + 1]
+            if i == j or i in used or j in used:
+                continue
+            used.update((i, j))
+            pairs.append((i, j))
+            if len(pairs) == shared:
+                break
+    for i, j in pairs:
+        a[j] = a[i]
+    return ints_to_rows([x * y for x, y in zip(a, b)], bits // 32), pairs
