@@ -275,6 +275,110 @@ def run_mr(args):
     return 0
 
 
+def bgcd_issued_products(count: int, L: int, blk: int, parts: int) -> float:
+    """Word products the batch-GCD kernels issue (block products, per-modulus
+    word reductions L per word, Montgomery multiplications 2L^2 + L each)."""
+    nblk = -(-count // blk)
+    mm = 2 * L * L + L
+    own = min(32, count)
+    pre = nblk * L * L * blk * (blk - 1) / 2
+    per_lane = (count - own) * L * L + max(0, nblk - -(-own // blk)) * mm + (own - 1) * mm + (parts - 1) * mm
+    return pre + count * per_lane
+
+
+def run_bgcd(args):
+    """Weak-key scan: g_i = gcd(n_i, product of the other moduli) over 16384
+    RSA-2048-shaped moduli (16 planted shared factors), one rsa_batch_gcd per
+    step, moduli device-resident; reported as modulus pairs/s.  e2e adds the
+    host-to-device copy of the moduli and the read-back of the flags."""
+    import torch
+    import oracle
+    from paper_1407_1465_gb300 import RsaContext, build, rsa_batch_gcd, rsa_batch_gcd_plan
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    count = args.count or 16384
+    bits = 2048
+    L = bits // 32
+    rows, pairs = workloads.weak_key_moduli(count, bits)
+    ctx = RsaContext(0, mem_budget_bytes=8 << 30)
+    m = torch.from_numpy(rows.view(np.int32)).to(dev)
+    g = torch.empty_like(m)
+    fl = torch.empty(count, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    for _ in range(max(args.warmup, 3)):
+        rsa_batch_gcd(ctx.handle, bits, count, m, g, fl, sptr)
+    torch.cuda.synchronize()
+    clk = ClockSampler(0)
+    clk.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        rsa_batch_gcd(ctx.handle, bits, count, m, g, fl, sptr)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    pairs_per_s = count * (count - 1) / (ms / 1e3)
+    flags = fl.cpu().numpy()
+    idx = sorted({0, count - 1, pairs[0][0], pairs[0][1]} | set(range(1, count, max(1, count // 6))))
+    og, of = oracle.batch_gcd(rows, rows=idx)
+    if not (np.array_equal(g.cpu().numpy().view(np.uint32)[idx], og) and np.array_equal(flags[idx], of)):
+        raise RuntimeError("batch gcd differs from the oracle")
+    blk, parts = rsa_batch_gcd_plan(ctx.handle, bits, count)
+    issued = bgcd_issued_products(count, L, blk, parts)
+    achieved = issued / (ms / 1e3) / 1e12
+    peak = derived_peak_tprod(SM_COUNT_GB300, 2070.0)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tprod/s", "frac": achieved / peak,
+                "traffic": None, "issued_products_per_step": issued,
+                "definitional_products_per_step": count * (count - 1) * (2 * L * L + L),
+                "note": "issued word products of the three kernels (word reductions cost L per word, half of a "
+                        "Montgomery multiplication) against the derived IMAD peak (152 SMs x 64 lanes x 2070 MHz / 2)"}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_measured_clock"] = achieved / derived_peak_tprod(SM_COUNT_GB300, clocks["sm_mhz"])
+    e2e = None
+    if not args.no_e2e:
+        host = torch.from_numpy(rows.view(np.int32)).pin_memory()
+        fh = torch.empty(count, dtype=torch.int32).pin_memory()
+        md = torch.empty_like(m)
+        torch.cuda.synchronize()
+        ev2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev2[0].record(stream)
+        for _ in range(args.steps):
+            md.copy_(host, non_blocking=True)
+            rsa_batch_gcd(ctx.handle, bits, count, md, None, fl, sptr)
+            fh.copy_(fl, non_blocking=True)
+        ev2[1].record(stream)
+        torch.cuda.synchronize()
+        ms2 = ev2[0].elapsed_time(ev2[1]) / args.steps
+        e2e = {"value": count * (count - 1) / (ms2 / 1e3), "unit": "pairs/s",
+               "h2d_bytes_per_step": int(rows.nbytes), "d2h_bytes_per_step": int(count * 4)}
+    cpu = None
+    if not args.no_cpu:
+        threads = oracle.default_threads()
+        sample = list(range(0, count, max(1, count // (4 * threads))))[: 4 * threads]
+        t0 = time.perf_counter()
+        oracle.batch_gcd(rows, rows=sample, threads=threads)
+        dt = time.perf_counter() - t0
+        cpu = {"value": len(sample) * (count - 1) / dt, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+               "sample": "%d of the %d moduli (each against all %d others), oracle product mod n_i and Euclid, "
+                         "%d POSIX threads" % (len(sample), count, count - 1, threads)}
+    line = {"metric": "batch GCD modulus pairs/sec (RSA-2048 weak-key scan)", "value": pairs_per_s,
+            "unit": "pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "gpu_launches": 3 * args.steps,
+            "config": {"workload": "%d RSA-2048-shaped moduli (products of random odd 1024-bit halves), %d planted "
+                                   "shared factors, one rsa_batch_gcd per step" % (count, len(pairs)),
+                       "block": blk, "parts": parts, "l2": "moduli and block products stay L2-resident (4 MiB each)"},
+            "flags": {"coprime": int((flags == 0).sum()), "factor_found": int((flags == 1).sum()),
+                      "whole_modulus": int((flags == 2).sum())},
+            "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_ragged(args):
     """Ragged batch: 256 keys, 200000 operations, one rsa_modexp_batch (one graph
     launch) per step, against a loop of one rsa_modexp_key launch per
@@ -489,7 +593,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="rsa2048", choices=sorted(WORKLOADS) + ["ragged", "serving", "toy", "mr"])
+    ap.add_argument("--workload", default="rsa2048", choices=sorted(WORKLOADS) + ["ragged", "serving", "toy", "mr", "bgcd"])
     ap.add_argument("--slots", type=int, default=8, help="serving: batches in flight at once")
     ap.add_argument("--e-bits", type=int, default=0,
                     help="--kind public: a seeded random public exponent of this many bits instead of 65537")
@@ -515,6 +619,8 @@ def main():
         return run_toy(args)
     if args.workload == "mr":
         return run_mr(args)
+    if args.workload == "bgcd":
+        return run_bgcd(args)
     spec = dict(WORKLOADS[args.workload])
     if args.count:
         spec["count"] = args.count

@@ -155,6 +155,31 @@ int rsa_verify_key(rsa_ctx *ctx, int32_t key_id, uint64_t count, const uint32_t 
 int rsa_mr_batch(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *cands, uint32_t rounds,
                  const uint32_t *bases, int32_t *verdicts, void *stream);
 
+/* Batch GCD (weak-key detection; the introduction rests RSA's security on the
+ * difficulty of factoring n, and two moduli sharing a prime are both factored
+ * by one gcd).  For the `count` moduli n_i of nbits/32 limbs at
+ * moduli + i*L (nbits 512, 1024 or 2048; a modulus may have leading zero
+ * limbs), g_i = gcd(n_i, prod_{j != i, n_j valid} n_j).  A modulus is valid
+ * when it is odd and at least 3; invalid ones are left out of every product.
+ * gcds (count rows of L limbs, or NULL) receives g_i (zeros for an invalid
+ * n_i); flags (count int32, or NULL) receives 0 when g_i = 1 (n_i shares no
+ * factor with the others), 1 when 1 < g_i < n_i (g_i is a proper factor),
+ * 2 when g_i = n_i (a duplicate modulus, or each prime of n_i is shared:
+ * separate it with pairwise gcds), -1 for an invalid n_i.  At least one of
+ * gcds and flags must be given.  All pointers are device pointers (rows
+ * 16-byte aligned); the work is count^2 / 2 Montgomery-word operations of the
+ * modulus size, in three kernels enqueued on `stream`.  Errors: RSA_ERR_ARG
+ * (null or misaligned pointers, count above 2^26), RSA_ERR_UNSUPPORTED,
+ * RSA_ERR_NOMEM, RSA_ERR_CUDA. */
+int rsa_batch_gcd(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *moduli, uint32_t *gcds,
+                  int32_t *flags, void *stream);
+/* The work split rsa_batch_gcd would use for `count` moduli: the block size
+ * of its block products (moduli multiplied together before the per-modulus
+ * reduction) and the number of parts the moduli range is cut into for load
+ * balance (each part's partial products are multiplied in a last kernel).
+ * For work accounting; no GPU work.  Errors as rsa_batch_gcd. */
+int rsa_batch_gcd_plan(rsa_ctx *ctx, uint32_t nbits, uint64_t count, uint32_t *block, uint64_t *parts);
+
 /* Ragged batch: operation i uses key key_ids[i] (any loaded key, any size) and
  * exponent exp_sel[i]; its message is the L_i limbs at msgs + limb_offsets[i]
  * and its result goes to out + limb_offsets[i].  All five arrays are device

@@ -25,7 +25,7 @@ __all__ = [
     "rsa_ctx_create", "rsa_ctx_destroy", "rsa_keyload", "rsa_key_record", "rsa_tc_operand_image",
     "rsa_keyunload", "rsa_key_info",
     "rsa_modexp_key", "rsa_modexp_batch", "rsa_modexp_key_host", "rsa_modexp_batch_host",
-    "rsa_sign_key", "rsa_verify_key", "rsa_mr_batch",
+    "rsa_sign_key", "rsa_verify_key", "rsa_mr_batch", "rsa_batch_gcd", "rsa_batch_gcd_plan",
     "rsa_sync", "rsa_last_error", "rsa_set_tuning", "rsa_get_tuning", "rsa_get_stats",
     "rsa_products_per_op", "rsa_imad_probe", "rsa_crt_decrypt_noalloc", "rsa_autotune",
     "rsa_server_start", "rsa_server_submit", "rsa_server_submit_many", "rsa_server_clock", "rsa_server_poll", "rsa_server_drain", "rsa_server_get_stats",
@@ -159,6 +159,18 @@ def rsa_verify_key(ctx: int, key_id: int, count: int, sigs, reps, op_status, str
 def rsa_mr_batch(ctx: int, nbits: int, count: int, cands, rounds: int, bases, verdicts, stream=None) -> None:
     check(_lib.lib().rsa_mr_batch(ctx, nbits, count, _ptr(cands), rounds, _ptr(bases), _ptr(verdicts),
                                   _stream_ptr(stream)))
+
+
+def rsa_batch_gcd(ctx: int, nbits: int, count: int, moduli, gcds, flags, stream=None) -> None:
+    check(_lib.lib().rsa_batch_gcd(ctx, nbits, count, _ptr(moduli), _ptr(gcds), _ptr(flags), _stream_ptr(stream)))
+
+
+def rsa_batch_gcd_plan(ctx: int, nbits: int, count: int) -> tuple[int, int]:
+    """(block size, parts) of the work split rsa_batch_gcd uses for count moduli."""
+    blk = ctypes.c_uint32(0)
+    parts = ctypes.c_uint64(0)
+    check(_lib.lib().rsa_batch_gcd_plan(ctx, nbits, count, ctypes.byref(blk), ctypes.byref(parts)))
+    return blk.value, parts.value
 
 
 def rsa_modexp_batch(ctx: int, count: int, key_ids, exp_sel, limb_offsets, msgs, out, op_status=None,
@@ -362,6 +374,19 @@ class RsaContext:
             verdicts = torch.empty(count, dtype=torch.int32, device=cands.device)
         rsa_mr_batch(self.handle, nbits, count, cands, rounds, bases, verdicts, stream)
         return verdicts
+
+    def batch_gcd(self, nbits: int, moduli, gcds=None, flags=None, stream=None):
+        """moduli: CUDA tensor [count, nbits/32] (int32 view of the limbs).
+        Returns (gcds, flags): g_i = gcd(n_i, product of the other valid
+        moduli) and int32 flags 0 coprime, 1 proper factor, 2 g = n, -1 invalid."""
+        import torch
+        count = moduli.shape[0]
+        if gcds is None:
+            gcds = torch.empty_like(moduli)
+        if flags is None:
+            flags = torch.empty(count, dtype=torch.int32, device=moduli.device)
+        rsa_batch_gcd(self.handle, nbits, count, moduli, gcds, flags, stream)
+        return gcds, flags
 
     def modexp_key_host(self, key_id: int, exp_sel: int, msgs: np.ndarray, out: np.ndarray | None = None,
                         status: np.ndarray | None = None, stream=None) -> np.ndarray:

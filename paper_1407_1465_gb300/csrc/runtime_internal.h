@@ -28,6 +28,7 @@ struct Workspace {
   DevBuf aux0, aux1, aux2, aux3;  // ragged-batch planning buffers
   DevBuf halves;                  // tensor-core CRT path: per-prime results between its two kernels
   DevBuf verify;                  // rsa_verify_key: recovered representatives
+  DevBuf gcd0, gcd1;              // rsa_batch_gcd: validity + block products, partial products
   void free_all();
 };
 

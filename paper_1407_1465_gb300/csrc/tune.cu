@@ -138,7 +138,7 @@ extern "C" int rsa_autotune(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint6
       if (it != c->workspaces.end()) {
         Workspace &w = it->second;
         for (DevBuf *d : {&w.tables, &w.io_in, &w.io_out, &w.io_status, &w.aux0, &w.aux1, &w.aux2, &w.aux3,
-                          &w.halves, &w.verify})
+                          &w.halves, &w.verify, &w.gcd0, &w.gcd1})
           if (d->ptr) {
             cudaFree(d->ptr);
             c->release(d->bytes);
