@@ -277,7 +277,9 @@ def run_mr(args):
 
 def bgcd_issued_products(count: int, L: int, blk: int, parts: int) -> float:
     """Word products the batch-GCD kernels issue (block products, per-modulus
-    word reductions L per word, Montgomery multiplications 2L^2 + L each)."""
+    word reductions L per word, Montgomery multiplications 2L^2 + L each; the
+    parts' partial products are multiplied pairwise, parts - 1 products per
+    modulus in all)."""
     nblk = -(-count // blk)
     mm = 2 * L * L + L
     own = min(32, count)
@@ -312,6 +314,7 @@ def run_bgcd(args):
     torch.cuda.synchronize()
     clk = ClockSampler(0)
     clk.start()
+    launches0 = ctx.stats()["kernel_launches"]
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     ev[0].record(stream)
     for _ in range(args.steps):
@@ -319,6 +322,7 @@ def run_bgcd(args):
     ev[1].record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
+    launches = ctx.stats()["kernel_launches"] - launches0
     ms = ev[0].elapsed_time(ev[1]) / args.steps
     pairs_per_s = count * (count - 1) / (ms / 1e3)
     flags = fl.cpu().numpy()
@@ -367,7 +371,7 @@ def run_bgcd(args):
     line = {"metric": "batch GCD modulus pairs/sec (RSA-2048 weak-key scan)", "value": pairs_per_s,
             "unit": "pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": int(launches),
             "config": {"workload": "%d RSA-2048-shaped moduli (products of random odd 1024-bit halves), %d planted "
                                    "shared factors, one rsa_batch_gcd per step" % (count, len(pairs)),
                        "block": blk, "parts": parts, "l2": "moduli and block products stay L2-resident (4 MiB each)"},

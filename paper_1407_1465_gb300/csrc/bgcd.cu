@@ -21,8 +21,9 @@
 //     multiplication into the running product;
 //   * the 32 moduli of the thread's own warp (the own block) go through CIOS
 //     Montgomery multiplications one by one, skipping j = i;
-//   * a finishing kernel multiplies the partial products of the parts the
-//     j range was split into (for load balance) and runs a binary gcd.
+//   * the j range is split into parts for load balance; a tree of launches
+//     multiplies the parts' partial products pairwise, and a last kernel runs
+//     a binary gcd.
 // Moduli that are even or below 3 are invalid: they are left out of every
 // product, and their own result is flagged.
 #include <cuda_runtime.h>
@@ -449,6 +450,43 @@ __device__ __forceinline__ void binary_gcd(uint32_t (&u)[L], uint32_t (&v)[L]) {
   }
 }
 
+// One level of the tree that multiplies the parts' partial products together:
+// part[p] = part[p] * part[p + half] for p < cur - half (Montgomery products,
+// so each level adds a power of R^-1, a unit modulo n_i).
+template <int L, int U>
+__global__ void __launch_bounds__(kGcdThreads) bgcd_combine_kernel(GcdArgs a, uint32_t cur, uint32_t half) {
+  using Sm = GcdSmem<L>;
+  extern __shared__ uint4 smem4[];
+  const int nw = blockDim.x / 32, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint4 *acc_lane = smem4 + (size_t)warp * Sm::kBuffers * Sm::kStageU4 + lane;
+  uint4 *r_lane = acc_lane + Sm::kStageU4;
+  const uint32_t nsb = (a.count + kOwn - 1) / kOwn, pairs = cur - half;
+  const uint64_t ntasks = (uint64_t)nsb * pairs;
+#pragma unroll 1
+  for (uint64_t task = (uint64_t)blockIdx.x * nw + warp; task < ntasks; task += (uint64_t)gridDim.x * nw) {
+    const uint32_t w = (uint32_t)(task / pairs), p = (uint32_t)(task % pairs);
+    const uint32_t i = w * kOwn + (uint32_t)lane;
+    const bool live = i < a.count;
+    const uint32_t row = live ? i : a.count - 1;
+    NRegs<L> N;
+    load_n<L>(N, a.mods + (size_t)row * L);
+    N.n[0] |= 1u;
+    const uint32_t np = neg_inv32(N.n[0]);
+    uint4 *dst = reinterpret_cast<uint4 *>(a.part + ((size_t)p * a.count + row) * L);
+    const uint4 *src = reinterpret_cast<const uint4 *>(a.part + ((size_t)(p + half) * a.count + row) * L);
+#pragma unroll
+    for (int g = 0; g < L / 4; ++g) {
+      acc_lane[g * 32] = dst[g];
+      r_lane[g * 32] = src[g];
+    }
+    mont_mul_lanes<L, U>(acc_lane, r_lane, N, np);
+    if (live) {
+#pragma unroll
+      for (int g = 0; g < L / 4; ++g) dst[g] = acc_lane[g * 32];
+    }
+  }
+}
+
 // Combine the parts' partial products, then g_i = gcd(n_i, product).
 template <int L, int U>
 __global__ void __launch_bounds__(kGcdThreads) bgcd_finish_kernel(GcdArgs a) {
@@ -535,6 +573,8 @@ struct GcdLaunch {
       e = cudaFuncSetAttribute(main_fn(m), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(bgcd_finish_kernel<L, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(bgcd_combine_kernel<L, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(bgcd)");
     done = true;
     return 0;
@@ -544,20 +584,42 @@ struct GcdLaunch {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, main_fn(minb), kGcdThreads, smem);
     return e == cudaSuccess ? std::max(1, n) : 1;
   }
-  static cudaError_t run(const GcdArgs &h, int grid_blk, int grid_main, int grid_fin, size_t smem, int minb,
-                         cudaStream_t s) {
+  // Returns the number of kernels launched through *launches.
+  static cudaError_t run(const GcdArgs &h, int grid_blk, int grid_main, int grid_fin, uint64_t cap, size_t smem,
+                         int minb, cudaStream_t s, int *launches) {
     bgcd_block_kernel<L><<<grid_blk, 64, 0, s>>>(h);
     if (minb == 2) bgcd_kernel<L, U, 2><<<grid_main, kGcdThreads, smem, s>>>(h);
     else bgcd_kernel<L, U, 3><<<grid_main, kGcdThreads, smem, s>>>(h);
-    bgcd_finish_kernel<L, U><<<grid_fin, kGcdThreads, smem, s>>>(h);
+    int n = 3;
+    const uint64_t nsb = (h.count + kOwn - 1) / kOwn;
+    for (uint32_t cur = h.nparts; cur > 1;) {
+      const uint32_t half = (cur + 1) / 2;
+      const uint64_t tasks = nsb * (cur - half);
+      const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((tasks + 3) / 4, cap));
+      bgcd_combine_kernel<L, U><<<grid, kGcdThreads, smem, s>>>(h, cur, half);
+      ++n;
+      cur = half;
+    }
+    GcdArgs f = h;
+    f.nparts = 1;
+    bgcd_finish_kernel<L, U><<<grid_fin, kGcdThreads, smem, s>>>(f);
+    *launches = n;
     return cudaGetLastError();
   }
 };
 
-int gcd_block_size() {
+// Moduli per block product.  Larger blocks need fewer Montgomery
+// multiplications into the running product (one per block) but the block
+// products themselves take longer (one thread multiplies B moduli in
+// sequence: 0.46 / 1.9 / 8.5 ms for B = 8 / 16 / 32 at 2048 bits on GB300).
+// Measured for 2048-bit moduli: 32 wins from about 12288 moduli up (16384:
+// 188 ms against 193 ms with 16), 8 below about 4096 (2048: 4.4 ms of block
+// products and reductions against 5.5 ms with 16).
+int gcd_block_size(uint64_t count) {
   const char *v = std::getenv("RSAGPU_GCD_BLOCK");
-  const int b = v ? std::atoi(v) : 16;
-  return (b == 8 || b == 16 || b == 32) ? b : 16;
+  const int def = count >= 12288 ? 32 : count >= 4096 ? 16 : 8;
+  const int b = v ? std::atoi(v) : def;
+  return (b == 8 || b == 16 || b == 32) ? b : def;
 }
 
 }  // namespace
@@ -577,7 +639,7 @@ struct GcdPlan {
 
 int gcd_plan(const Ctx *c, uint32_t nbits, uint64_t count, GcdPlan *pl) {
   pl->L = nbits / 32;
-  pl->blk = (uint32_t)gcd_block_size();
+  pl->blk = (uint32_t)gcd_block_size(count);
   pl->nblk = (count + pl->blk - 1) / pl->blk;
   pl->nsb = (count + kOwn - 1) / kOwn;
   const uint32_t L = pl->L;
@@ -641,11 +703,12 @@ extern "C" int rsa_batch_gcd(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const
   const int grid_blk = (int)std::max<uint64_t>(1, std::min<uint64_t>((pl.nblk + 63) / 64, (uint64_t)c->sm_count * 8));
   const int grid_main = (int)std::max<uint64_t>(1, std::min<uint64_t>((pl.nsb * pl.nparts + 3) / 4, cap));
   const int grid_fin = (int)std::max<uint64_t>(1, std::min<uint64_t>((pl.nsb + 3) / 4, cap));
-  cudaError_t e = (L == 16)   ? GcdLaunch<16>::run(h, grid_blk, grid_main, grid_fin, pl.smem, pl.minb, s)
-                  : (L == 32) ? GcdLaunch<32>::run(h, grid_blk, grid_main, grid_fin, pl.smem, pl.minb, s)
-                              : GcdLaunch<64>::run(h, grid_blk, grid_main, grid_fin, pl.smem, pl.minb, s);
+  int launches = 0;
+  cudaError_t e = (L == 16)   ? GcdLaunch<16>::run(h, grid_blk, grid_main, grid_fin, cap, pl.smem, pl.minb, s, &launches)
+                  : (L == 32) ? GcdLaunch<32>::run(h, grid_blk, grid_main, grid_fin, cap, pl.smem, pl.minb, s, &launches)
+                              : GcdLaunch<64>::run(h, grid_blk, grid_main, grid_fin, cap, pl.smem, pl.minb, s, &launches);
   if (e != cudaSuccess) return cuda_error(e, "launch bgcd kernels");
-  c->stats.kernel_launches += 3;
+  c->stats.kernel_launches += (uint64_t)launches;
   c->stats.ops += count;
   return RSA_OK;
 }

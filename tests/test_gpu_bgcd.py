@@ -91,7 +91,9 @@ def test_bgcd_invalid_and_short_moduli(torch_cuda, ctx):
     vals = workloads.rows_to_ints(rows)
     vals[3] = 0
     vals[10] = 1
-    vals[11] = vals[12] * 2                      # even, holds modulus 12's factors
+    p12 = vals[12] >> 600 | 1                    # modulus 12 = p12 * r; an even entry holds p12
+    vals[12] = p12 * (vals[13] >> 600 | 1)
+    vals[11] = 2 * p12 * (vals[14] >> 600 | 1)
     vals[20] = 3
     vals[21] = 9
     vals[30] = vals[31] >> 500 | 1               # short modulus, leading zero limbs
@@ -104,8 +106,9 @@ def test_bgcd_invalid_and_short_moduli(torch_cuda, ctx):
     assert f[40] == 2 and f[41] == 2 and f[20] != 0
 
 
-@pytest.mark.parametrize("block,minb", [("8", "3"), ("32", "3"), ("16", "2"), ("32", "2")])
+@pytest.mark.parametrize("block,minb", [("8", "3"), ("32", "3"), ("16", "2"), ("32", "2"), ("8", "2")])
 def test_bgcd_block_sizes_agree(torch_cuda, ctx, monkeypatch, block, minb):
+    """Every block size and both register variants."""
     monkeypatch.setenv("RSAGPU_GCD_BLOCK", block)
     monkeypatch.setenv("RSAGPU_GCD_MINB", minb)
     rows = _random_odd(450, 2048, 13)
