@@ -491,12 +491,14 @@ def run_serving(args):
         k = i % len(kids)
         rsa_server_submit(ctx.handle, kids[k], 1, pools[k][:8], scratch[k][:8])
     rsa_server_drain(ctx.handle, 600000)
+    # --key-bits: requests only under the keys of that size (latency of one size class)
+    subset = [i for i, k in enumerate(rb_keys) if not args.key_bits or k.bits == args.key_bits]
     for rate in rates:
         reqs = workloads.poisson_requests(rate, args.duration, len(kids), workloads.DEFAULT_SEED)
         arr = np.zeros(len(reqs), dtype=REQUEST_DTYPE)
         lead = rsa_server_clock(ctx.handle) + 200_000_000      # arrivals start 200 ms from now
         for j, rq in enumerate(reqs):
-            k = rq.key_id
+            k = subset[rq.key_id % len(subset)]
             arr[j] = (kids[k], rq.exp_sel, rq.count, 0, pools[k].ctypes.data, scratch[k].ctypes.data, 0,
                       lead + int(rq.t_arrive * 1e9))
         rsa_server_get_stats(ctx.handle, reset=True)
@@ -515,6 +517,7 @@ def run_serving(args):
             "config": {"workload": "256 ragged keys, 1-64 msgs/request, 70%% CRT / 30%% public, 2 GiB budget, "
                                    "%.1f s of arrivals per rate" % args.duration, "rates": rates,
                        "batch_window_us": args.window_us, "slots": args.slots,
+                       "key_bits": args.key_bits or "all",
                        "batching": "one modulus size per batch (the oldest waiting request picks it)"},
             "sweep": results}
     print(json.dumps(line), flush=True)
@@ -598,7 +601,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="rsa2048", choices=sorted(WORKLOADS) + ["ragged", "serving", "toy", "mr", "bgcd"])
-    ap.add_argument("--slots", type=int, default=8, help="serving: batches in flight at once")
+    ap.add_argument("--slots", type=int, default=16, help="serving: batches in flight at once")
+    ap.add_argument("--key-bits", type=int, default=0, help="serving: only requests under keys of this size")
     ap.add_argument("--e-bits", type=int, default=0,
                     help="--kind public: a seeded random public exponent of this many bits instead of 65537")
     ap.add_argument("--kind", default="crt", choices=["crt", "public"],

@@ -237,7 +237,7 @@ int rsa_crt_decrypt_noalloc(const uint32_t *key_record, uint32_t nbits, uint64_t
  * latency.  Key state stays resident in the context.  Results are copied into
  * each request's host buffer. */
 typedef struct rsa_server_cfg {
-    int32_t max_inflight_batches; /* concurrent batches (streams); 0 -> 8 */
+    int32_t max_inflight_batches; /* concurrent batches (streams); 0 -> 16 */
     int32_t batch_window_us;      /* wait this long after the first arrival for more; 0 -> 200 */
     int32_t max_batch_ops;        /* operations per batch; 0 -> 65536 */
     int32_t reserved;

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -47,7 +48,7 @@ __global__ void plan_count(BatchDesc d) {
       const KeyDirEntry e = d.dir[kid];
       if (kind != 0 && !(e.flags & KEY_HAS_D)) err = -2;
       else if (kind == 1 && !(e.flags & KEY_HAS_CRT)) err = -2;
-      else if (batch_class(e.L, kind) < 0) err = -7;
+      else if (batch_class(e.L, kind, d.wide_crt32) < 0) err = -7;
       else if (e.L > 1 && (d.offsets[i] & 3u)) err = -1;   // rows must be 16-byte aligned
       else b = kid * 3 + kind;
     }
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(1024) plan_tiles(BatchDesc d) {
     for (uint32_t b = b0; b < b1; ++b) {
       const uint32_t c = d.bcount[b];
       if (!c) continue;
-      const int32_t cls = batch_class(d.dir[b / 3].L, (int)(b % 3));
+      const int32_t cls = batch_class(d.dir[b / 3].L, (int)(b % 3), d.wide_crt32);
       if (d.class_rank[cls] != rank) continue;
       const uint32_t to = (uint32_t)batch_tile_ops(cls);
       my_ops += c;
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(1024) plan_tiles(BatchDesc d) {
     for (uint32_t b = b0; b < b1; ++b) {
       const uint32_t c = d.bcount[b];
       if (!c) continue;
-      const int32_t cls = batch_class(d.dir[b / 3].L, (int)(b % 3));
+      const int32_t cls = batch_class(d.dir[b / 3].L, (int)(b % 3), d.wide_crt32);
       if (d.class_rank[cls] != rank) continue;
       const uint32_t to = (uint32_t)batch_tile_ops(cls);
       d.boff[b] = op_off;
@@ -152,6 +153,14 @@ __global__ void plan_scatter(BatchDesc d) {
   }
 }
 
+// Share (percent) of one wave of the four-lane group up to which a ragged
+// batch runs 2048-bit CRT four lanes per operation; 0 disables it.
+uint64_t ragged_wide_fraction() {
+  const char *v = std::getenv("RSAGPU_RAGGED_WIDE_PCT");
+  const long p = v ? std::atol(v) : 100;
+  return p < 0 ? 0 : (uint64_t)p;
+}
+
 // approximate word products per operation of a class, for the longest-first order
 double class_cost(int32_t cls) {
   auto mm = [](double l) { return 2.0 * l * l + l; };
@@ -161,6 +170,8 @@ double class_cost(int32_t cls) {
     case CLS_CRT32: return 2.0 * 1300 * mm(32);
     case CLS_CRT48: return 2.0 * 1880 * mm(48);
     case CLS_CRT64: return 2.0 * 2500 * mm(64);
+    case CLS_CRT32W: return 2.0 * 1300 * mm(32) / 4;   // per lane
+    case CLS_CRT64W: return 2.0 * 2500 * mm(64) / 8;
     case CLS_PUB32: return 19 * mm(32);
     case CLS_PUB64: return 19 * mm(64);
     case CLS_PUB96: return 19 * mm(96);
@@ -319,6 +330,12 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
   d.ctl = static_cast<uint32_t *>(w.aux3.ptr);
   d.tables = static_cast<uint4 *>(w.tables.ptr);
   d.max_tiles = max_tiles;
+  // Small batches run 2048-bit CRT with four lanes per operation and 4096-bit
+  // CRT with eight: each operation finishes sooner (about 2.2x at 2048 bits),
+  // and while the batch fits in one wave of the multi-lane group (8 operations
+  // per resident warp pair) the GPU has idle SMs anyway.  Larger batches keep
+  // one (four) lanes per operation, which has the higher throughput.
+  d.wide_crt32 = count <= (uint64_t)8 * (uint64_t)grids_exec[GRP_BIG] * ragged_wide_fraction() / 100 ? 1u : 0u;
   {
     std::vector<int32_t> order(CLS_COUNT);
     std::iota(order.begin(), order.end(), 0);

@@ -33,7 +33,10 @@ enum : int32_t {
   CLS_PUB32 = 5, CLS_PUB64 = 6, CLS_PUB96 = 7, CLS_PUB128 = 8,  // public exponent, L limbs
                                                                 // (96, 128: four lanes per operation)
   CLS_PLAIN32 = 9, CLS_PLAIN64 = 10,             // plain private exponent, L limbs
-  CLS_COUNT = 11
+  CLS_CRT32W = 11,                               // CRT of 2048-bit keys, four lanes per operation
+  CLS_CRT64W = 12,                               // CRT of 4096-bit keys, eight lanes per operation
+                                                 // (the W classes: small batches, latency over throughput)
+  CLS_COUNT = 13
 };
 
 // Window widths the execution kernel is compiled with, per class.
@@ -42,9 +45,13 @@ constexpr int kBatchWindowPlain = 4;
 // Largest per-warp window table (CRT H=64 at w=5, plain L=64 at w=4): uint4 count.
 constexpr size_t kBatchTableU4PerWarp = (size_t)32 * 64 * 8;
 
-__host__ __device__ inline int32_t batch_class(uint32_t L, int kind) {
+// wide: run 2048-bit CRT with four lanes per operation (CLS_CRT32W) and
+// 4096-bit CRT with eight (CLS_CRT64W)
+__host__ __device__ inline int32_t batch_class(uint32_t L, int kind, bool wide = false) {
   if (L == 1) return CLS_TOY;
-  if (kind == 1) return L == 32 ? CLS_CRT16 : L == 64 ? CLS_CRT32 : L == 96 ? CLS_CRT48 : L == 128 ? CLS_CRT64 : -1;
+  if (kind == 1)
+    return L == 32 ? CLS_CRT16 : L == 64 ? (wide ? CLS_CRT32W : CLS_CRT32) : L == 96 ? CLS_CRT48
+           : L == 128 ? (wide ? CLS_CRT64W : CLS_CRT64) : -1;
   if (kind == 0) return L == 32 ? CLS_PUB32 : L == 64 ? CLS_PUB64 : L == 96 ? CLS_PUB96 : L == 128 ? CLS_PUB128 : -1;
   if (kind == 2) return L == 32 ? CLS_PLAIN32 : L == 64 ? CLS_PLAIN64 : -1;
   return -1;
@@ -53,23 +60,25 @@ __host__ __device__ inline int32_t batch_class(uint32_t L, int kind) {
 // Execution groups: one persistent kernel each, so every group gets the
 // register allocation its own largest class needs.  Group order is the order
 // of tile ranges (longest operations first).
-//   BIG   CRT of 3072/4096-bit keys, four lanes per operation (128 registers)
+//   BIG   CRT of 3072/4096-bit keys (and of 2048-bit keys in small batches),
+//         four lanes per operation (eight for 4096-bit keys in small batches)
 //   CRT   CRT of 1024/2048-bit keys, public/plain of 1024-bit keys, toy keys
 //   L64   public/plain exponents of 2048-bit moduli (one lane, 232 registers)
 //   WIDE  public exponents of 3072/4096-bit moduli, four lanes per operation
 enum : int32_t { GRP_BIG = 0, GRP_CRT = 1, GRP_L64 = 2, GRP_WIDE = 3, GRP_COUNT = 4 };
 __host__ __device__ inline int32_t batch_group(int32_t cls) {
-  if (cls == CLS_CRT48 || cls == CLS_CRT64) return GRP_BIG;
+  if (cls == CLS_CRT48 || cls == CLS_CRT64 || cls == CLS_CRT32W || cls == CLS_CRT64W) return GRP_BIG;
   if (cls == CLS_PUB96 || cls == CLS_PUB128) return GRP_WIDE;
   if (cls == CLS_PUB64 || cls == CLS_PLAIN64) return GRP_L64;
   return GRP_CRT;
 }
 
 // operations per tile of a class: CRT 32 (warp pair on the same 32), wide CRT 8
-// (4 lanes per operation, the pair on the same 8), wide public 16 (4 lanes per
+// (4 lanes per operation, the pair on the same 8; 4 with 8 lanes), wide public 16 (4 lanes per
 // operation, 8 per warp), others 64 (32 per warp)
 __host__ __device__ inline int32_t batch_tile_ops(int32_t cls) {
-  if (cls == CLS_CRT48 || cls == CLS_CRT64) return 8;
+  if (cls == CLS_CRT64W) return 4;
+  if (cls == CLS_CRT48 || cls == CLS_CRT64 || cls == CLS_CRT32W) return 8;
   if (cls == CLS_PUB96 || cls == CLS_PUB128) return 16;
   return (cls == CLS_CRT16 || cls == CLS_CRT32) ? 32 : 64;
 }
@@ -93,6 +102,7 @@ struct BatchDesc {
   uint4 *tables;              // per resident warp: kBatchTableU4PerWarp
   uint32_t max_tiles;
   int32_t class_rank[CLS_COUNT];  // position of each class in the longest-first order
+  uint32_t wide_crt32;        // small batch: 2048/4096-bit CRT as CLS_CRT32W / CLS_CRT64W
 };
 
 const void *batch_exec_fn(int group);

@@ -44,6 +44,17 @@ __device__ __forceinline__ void run_crt4(const uint32_t *ks, uint4 *work, uint4 
   crt_tile_t<H, 4, W, 8>(ks, warp == 1, g, stage_op, xb, table_warp + lane, 1, io);
 }
 
+// CRT of 4096-bit keys in small batches: eight lanes per operation, the pair on the same 4
+template <int H, int W>
+__device__ __forceinline__ void run_crt8(const uint32_t *ks, uint4 *work, uint4 *table_warp, int warp, int lane,
+                                         const TileIO &io) {
+  constexpr int kStage = (H / 4) * 4;
+  const Group<8> g(lane);
+  uint4 *xb = work + g.opi;
+  uint4 *stage_op = work + kStage + warp * kStage + g.opi;
+  crt_tile_t<H, 8, W, 8>(ks, warp == 1, g, stage_op, xb, table_warp + lane, 1, io);
+}
+
 template <int L>
 __device__ __forceinline__ void run_pub(const uint32_t *ks, uint4 *work, int warp, int lane, const TileIO &io) {
   constexpr int kStage = (L / 4) * 32;
@@ -98,6 +109,8 @@ __global__ void __launch_bounds__(64, 1) batch_exec_kernel(BatchDesc d) {
     if constexpr (G == GRP_BIG) {
       if (td.cls == CLS_CRT48) run_crt4<48, kBatchWindowCrt48>(ks, work, table_warp, warp, lane, io_pair);
       else if (td.cls == CLS_CRT64) run_crt4<64, kBatchWindowCrt64>(ks, work, table_warp, warp, lane, io_pair);
+      else if (td.cls == CLS_CRT32W) run_crt4<32, kBatchWindowCrt32>(ks, work, table_warp, warp, lane, io_pair);
+      else if (td.cls == CLS_CRT64W) run_crt8<64, kBatchWindowCrt64>(ks, work, table_warp, warp, lane, io_pair);
     } else if constexpr (G == GRP_L64) {
       if (wn > 0) {
         if (td.cls == CLS_PUB64) run_pub<64>(ks, work, warp, lane, io_warp);

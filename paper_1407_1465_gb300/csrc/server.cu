@@ -353,7 +353,7 @@ int rsa_server_start(rsa_ctx *ctx, const rsa_server_cfg *cfg) {
   Server *s = new Server();
   s->ctx = c;
   if (cfg) s->cfg = *cfg;
-  if (s->cfg.max_inflight_batches <= 0) s->cfg.max_inflight_batches = 8;
+  if (s->cfg.max_inflight_batches <= 0) s->cfg.max_inflight_batches = 16;
   if (s->cfg.batch_window_us <= 0) s->cfg.batch_window_us = 200;
   if (s->cfg.max_batch_ops <= 0) s->cfg.max_batch_ops = 65536;
   if (s->cfg.mem_budget_bytes == 0) s->cfg.mem_budget_bytes = (uint64_t)2 << 30;

@@ -100,8 +100,12 @@ def mixed_keys(ctx):
     return keys, kids
 
 
+@pytest.mark.parametrize("wide", ["100", "0"])
 @pytest.mark.parametrize("count", [1, 63, 700])
-def test_ragged_mix_matches_oracle(torch_cuda, ctx, mixed_keys, count):
+def test_ragged_mix_matches_oracle(torch_cuda, ctx, mixed_keys, monkeypatch, count, wide):
+    """Small batches run 2048/4096-bit CRT with 4/8 lanes per operation
+    (RSAGPU_RAGGED_WIDE_PCT=100, the default); 0 forces one/four lanes."""
+    monkeypatch.setenv("RSAGPU_RAGGED_WIDE_PCT", wide)
     keys, kids = mixed_keys
     ops, key_ids, sels, offsets, packed = build_mix(keys, kids, count, 100 + count)
     out, st, rc = run_batch(torch_cuda, ctx, key_ids, sels, offsets, packed)
