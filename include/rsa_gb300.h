@@ -282,7 +282,10 @@ int rsa_server_poll(rsa_ctx *ctx, uint64_t ticket, int32_t *done);
 int rsa_server_drain(rsa_ctx *ctx, int32_t timeout_ms);
 /* Latency and throughput counters since start (or the last reset). */
 int rsa_server_get_stats(rsa_ctx *ctx, rsa_server_stats *s, int32_t reset);
-/* Drain and stop the loop; releases its buffers. */
+/* Stop the loop: requests that have arrived are run to completion; requests
+ * whose arrival time is still in the future are cancelled (never run,
+ * RSA_ERR_TIMEOUT written to each of their status entries when a status array
+ * was given).  Releases the loop's buffers; tickets are invalid afterwards. */
 int rsa_server_stop(rsa_ctx *ctx);
 
 /* Wait for `stream` and return the first device-side error recorded since the

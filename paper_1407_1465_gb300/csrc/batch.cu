@@ -290,16 +290,22 @@ int Ctx::prepare_batch(cudaStream_t s, uint64_t max_count) {
     max_grid = std::max(max_grid, st->grids_exec[g]);
   }
   st->exec_grid = max_grid;
-  // window tables: one slot per resident warp of each group (groups run concurrently)
-  const size_t slot_u4 = (size_t)2 * kBatchTableU4PerWarp;
-  size_t all_slots = 0;
-  for (int gi = 0; gi < GRP_COUNT; ++gi) all_slots += (size_t)st->grids_exec[gi];
-  return ensure(w.tables, all_slots * slot_u4 * 16);
+  // window tables: one per resident warp of each group (groups run concurrently),
+  // each the size its group's largest class needs
+  size_t table_u4 = 0;
+  for (int gi = 0; gi < GRP_COUNT; ++gi) table_u4 += (size_t)st->grids_exec[gi] * 2 * batch_table_u4(gi);
+  return ensure(w.tables, std::max<size_t>(table_u4, 1) * 16);
+}
+
+uint64_t Ctx::batch_wave_ops(cudaStream_t s) {
+  const BatchState *st = state_for(this, s);
+  return (uint64_t)8 * (uint64_t)st->grids_exec[GRP_BIG] * ragged_wide_fraction() / 100;
 }
 
 int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_sel, const uint64_t *offsets,
-                   const uint32_t *msgs, uint32_t *out, int32_t *status, cudaStream_t s) {
+                   const uint32_t *msgs, uint32_t *out, int32_t *status, cudaStream_t s, int wide) {
   if (count == 0) return RSA_OK;
+  NvtxRange range("rsa_modexp_batch");
   int rc = prepare_batch(s, count);
   if (rc) return rc;
   BatchState *st = state_for(this, s);
@@ -309,7 +315,6 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
   const uint32_t max_tiles = (uint32_t)(count / 8 + nb + 1);
   int grids_exec[GRP_COUNT];
   for (int g = 0; g < GRP_COUNT; ++g) grids_exec[g] = st->grids_exec[g];
-  const size_t slot_u4 = (size_t)2 * kBatchTableU4PerWarp;
 
   BatchDesc d{};
   d.count = (uint32_t)count;
@@ -335,7 +340,7 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
   // and while the batch fits in one wave of the multi-lane group (8 operations
   // per resident warp pair) the GPU has idle SMs anyway.  Larger batches keep
   // one (four) lanes per operation, which has the higher throughput.
-  d.wide_crt32 = count <= (uint64_t)8 * (uint64_t)grids_exec[GRP_BIG] * ragged_wide_fraction() / 100 ? 1u : 0u;
+  d.wide_crt32 = (wide < 0 ? count <= batch_wave_ops(s) : wide != 0) ? 1u : 0u;
   {
     std::vector<int32_t> order(CLS_COUNT);
     std::iota(order.begin(), order.end(), 0);
@@ -363,12 +368,18 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
   }
   // each group's warps index their own slice of the table scratch
   size_t slot_off = 0;
+  // a batch with few tiles launches only the CTAs it can use (at most one
+  // per tile: count / smallest tile + one partial tile per bucket), so that
+  // its tiles start on separate SMs instead of wherever the first CTAs landed
+  const uint64_t tile_min[GRP_COUNT] = {d.wide_crt32 ? 4u : 8u, 32u, 32u, 16u};
+  static_assert(GRP_BIG == 0 && GRP_CRT == 1 && GRP_L64 == 2 && GRP_WIDE == 3, "tile_min order");
   for (int gi = 0; gi < GRP_COUNT; ++gi) {
-    grids[4 + gi] = dim3(grids_exec[gi]);
+    const uint64_t useful = count / tile_min[gi] + std::min<uint64_t>(nb, count) + 1;
+    grids[4 + gi] = dim3((unsigned)std::min<uint64_t>((uint64_t)grids_exec[gi], useful));
     blocks[4 + gi] = dim3(64);
     smems[4 + gi] = batch_exec_smem_bytes(gi);
     dg[4 + gi].tables = d.tables + slot_off;
-    slot_off += (size_t)grids_exec[gi] * slot_u4;
+    slot_off += (size_t)grids_exec[gi] * 2 * batch_table_u4(gi);
   }
   cudaError_t e;
   auto params = [&](int i) {

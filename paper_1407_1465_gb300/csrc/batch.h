@@ -42,8 +42,6 @@ enum : int32_t {
 // Window widths the execution kernel is compiled with, per class.
 constexpr int kBatchWindowCrt16 = 4, kBatchWindowCrt32 = 4, kBatchWindowCrt48 = 5, kBatchWindowCrt64 = 5;
 constexpr int kBatchWindowPlain = 4;
-// Largest per-warp window table (CRT H=64 at w=5, plain L=64 at w=4): uint4 count.
-constexpr size_t kBatchTableU4PerWarp = (size_t)32 * 64 * 8;
 
 // wide: run 2048-bit CRT with four lanes per operation (CLS_CRT32W) and
 // 4096-bit CRT with eight (CLS_CRT64W)
@@ -73,6 +71,19 @@ __host__ __device__ inline int32_t batch_group(int32_t cls) {
   return GRP_CRT;
 }
 
+// Window-table scratch per warp (uint4) of an execution group: 2^w entries of
+// (limbs per lane)/4 uint4 for each of the 32 lanes, for the largest class the
+// group runs (each call site checks its own need against this at compile time).
+__host__ __device__ constexpr size_t batch_table_need(int w, int limbs_per_lane) {
+  return ((size_t)1 << w) * (size_t)(limbs_per_lane / 4) * 32;
+}
+__host__ __device__ constexpr size_t batch_table_u4(int group) {
+  return group == GRP_BIG   ? batch_table_need(5, 16)   // CRT H=64, w=5, four lanes: 16 limbs per lane
+         : group == GRP_CRT ? batch_table_need(4, 32)   // CRT H=32, w=4; plain L=32, w=4
+         : group == GRP_L64 ? batch_table_need(4, 64)   // plain L=64, w=4
+                            : 0;                        // public exponents only: no table
+}
+
 // operations per tile of a class: CRT 32 (warp pair on the same 32), wide CRT 8
 // (4 lanes per operation, the pair on the same 8; 4 with 8 lanes), wide public 16 (4 lanes per
 // operation, 8 per warp), others 64 (32 per warp)
@@ -99,7 +110,7 @@ struct BatchDesc {
   TileDesc *tiles;            // [max_tiles]
   uint32_t *ctl;              // [0] unused, [1] tile count, [2] error bits,
                               // [4+g] first tile of group g, [8+g] end, [12+g] counter (g < 4)
-  uint4 *tables;              // per resident warp: kBatchTableU4PerWarp
+  uint4 *tables;              // per resident warp of the group: batch_table_u4(group)
   uint32_t max_tiles;
   int32_t class_rank[CLS_COUNT];  // position of each class in the longest-first order
   uint32_t wide_crt32;        // small batch: 2048/4096-bit CRT as CLS_CRT32W / CLS_CRT64W

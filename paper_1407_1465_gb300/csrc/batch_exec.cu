@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(64, 1) batch_exec_kernel(BatchDesc d) {
   uint32_t *ks = reinterpret_cast<uint32_t *>(smem4);
   uint4 *work = smem4 + kKeyWordsMax / 4;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint4 *table_warp = d.tables + ((size_t)blockIdx.x * 2 + warp) * kBatchTableU4PerWarp;
+  uint4 *table_warp = d.tables + ((size_t)blockIdx.x * 2 + warp) * batch_table_u4(G);
   const uint32_t first = d.ctl[4 + G], end = d.ctl[8 + G];
 #pragma unroll 1
   for (;;) {
@@ -107,11 +107,17 @@ __global__ void __launch_bounds__(64, 1) batch_exec_kernel(BatchDesc d) {
     const TileIO io_warp{d.msgs, d.out, d.status, d.sorted, d.offsets, (uint32_t)(td.op_start + 32 * warp),
                          (uint32_t)wn};
     if constexpr (G == GRP_BIG) {
+      static_assert(batch_table_need(kBatchWindowCrt48, 48 / 4) <= batch_table_u4(GRP_BIG) &&
+                        batch_table_need(kBatchWindowCrt64, 64 / 4) <= batch_table_u4(GRP_BIG) &&
+                        batch_table_need(kBatchWindowCrt32, 32 / 4) <= batch_table_u4(GRP_BIG) &&
+                        batch_table_need(kBatchWindowCrt64, 64 / 8) <= batch_table_u4(GRP_BIG),
+                    "window table of a four/eight-lane CRT class");
       if (td.cls == CLS_CRT48) run_crt4<48, kBatchWindowCrt48>(ks, work, table_warp, warp, lane, io_pair);
       else if (td.cls == CLS_CRT64) run_crt4<64, kBatchWindowCrt64>(ks, work, table_warp, warp, lane, io_pair);
       else if (td.cls == CLS_CRT32W) run_crt4<32, kBatchWindowCrt32>(ks, work, table_warp, warp, lane, io_pair);
       else if (td.cls == CLS_CRT64W) run_crt8<64, kBatchWindowCrt64>(ks, work, table_warp, warp, lane, io_pair);
     } else if constexpr (G == GRP_L64) {
+      static_assert(batch_table_need(kBatchWindowPlain, 64) <= batch_table_u4(GRP_L64), "plain L=64 table");
       if (wn > 0) {
         if (td.cls == CLS_PUB64) run_pub<64>(ks, work, warp, lane, io_warp);
         else if (td.cls == CLS_PLAIN64) run_plain<64>(ks, work, table_warp, warp, lane, io_warp);
@@ -124,6 +130,10 @@ __global__ void __launch_bounds__(64, 1) batch_exec_kernel(BatchDesc d) {
       if (td.cls == CLS_PUB96) run_pub_wide<96>(ks, work, warp, lane, io8);
       else if (td.cls == CLS_PUB128) run_pub_wide<128>(ks, work, warp, lane, io8);
     } else {
+      static_assert(batch_table_need(kBatchWindowCrt16, 16) <= batch_table_u4(GRP_CRT) &&
+                        batch_table_need(kBatchWindowCrt32, 32) <= batch_table_u4(GRP_CRT) &&
+                        batch_table_need(kBatchWindowPlain, 32) <= batch_table_u4(GRP_CRT),
+                    "window table of a one-lane class");
       const KeyHeader &hd = *reinterpret_cast<const KeyHeader *>(ks);
       switch (td.cls) {
         case CLS_CRT16: run_crt<16, kBatchWindowCrt16>(ks, work, table_warp, warp, lane, io_pair); break;

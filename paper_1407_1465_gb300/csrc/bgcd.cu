@@ -688,6 +688,7 @@ extern "C" int rsa_batch_gcd(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const
   cudaSetDevice(c->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Workspace &w = c->ws(s);
+  NvtxRange range("rsa_batch_gcd");
   GcdPlan pl;
   if ((rc = gcd_plan(c, nbits, count, &pl))) return rc;
   const uint32_t L = pl.L;

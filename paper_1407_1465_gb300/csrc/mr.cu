@@ -244,6 +244,7 @@ extern "C" int rsa_mr_batch(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const 
   std::lock_guard<std::mutex> lock(c->mu);
   cudaSetDevice(c->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  NvtxRange range("rsa_mr_batch");
   Workspace &w = c->ws(s);
   const int L = (int)nbits / 32;
   const uint64_t warps_needed = (count + 31) / 32;

@@ -525,6 +525,7 @@ int rsa_modexp_key(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint64_t count
     return set_error(RSA_ERR_ARG, "message and output rows must be 16-byte aligned");
   cudaSetDevice(c->device);
   c->stats.ops += count;
+  NvtxRange range("rsa_modexp_key");
   return c->run_key(*k, exp_sel, count, msgs, out, op_status, static_cast<cudaStream_t>(stream));
 }
 

@@ -9,9 +9,20 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "rsa_gb300.h"
 
 namespace rsagpu {
+
+// NVTX range over a host call (named in Nsight timelines; costs nothing
+// measurable without a tool attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 int set_error(int code, const std::string &msg);
 int cuda_error(cudaError_t e, const char *what);
@@ -73,8 +84,12 @@ struct Ctx {
   int run_key(const KeySlot &k, int kind, uint64_t count, const uint32_t *msgs, uint32_t *out,
               int32_t *status, cudaStream_t s);
   int prepare_batch(cudaStream_t s, uint64_t max_count);
+  // wide: 1 runs 2048/4096-bit CRT on 4/8 lanes per operation, 0 on 1/4,
+  // -1 decides by the batch's own size (at most batch_wave_ops operations)
   int run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_sel, const uint64_t *offsets,
-                const uint32_t *msgs, uint32_t *out, int32_t *status, cudaStream_t s);
+                const uint32_t *msgs, uint32_t *out, int32_t *status, cudaStream_t s, int wide = -1);
+  // operations one wave of the multi-lane group holds (after prepare_batch on s)
+  uint64_t batch_wave_ops(cudaStream_t s);
   int collect_device_errors(cudaStream_t s);
   void free_extra();
 };

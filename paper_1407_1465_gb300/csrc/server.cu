@@ -63,6 +63,7 @@ struct Slot {
   std::vector<Req *> reqs;
   std::vector<uint64_t> req_off;        // first limb of each request in the staging buffers
   uint64_t bytes = 0;
+  uint32_t ops = 0;
 };
 
 }  // namespace
@@ -80,6 +81,7 @@ struct Server {
   std::unordered_map<uint64_t, Req *> all;      // every request not yet retired
   std::vector<Slot> slots;
   uint64_t inflight_bytes = 0, peak_bytes = 0;
+  uint64_t inflight_ops = 0, wave_ops = 0;       // operations on the GPU; one multi-lane wave
   uint64_t pending = 0;                         // submitted and not finished
   // statistics
   std::vector<double> lat_us;
@@ -145,6 +147,7 @@ int Server::init() {
     std::lock_guard<std::mutex> lock(ctx->mu);
     rc = ctx->prepare_batch(s.stream, s.cap_ops);
     if (rc) return rc;
+    wave_ops = ctx->batch_wave_ops(s.stream);
   }
   return RSA_OK;
 }
@@ -171,6 +174,7 @@ void Server::release() {
 
 // Pack `batch` into the slot's staging buffers and enqueue copies + the ragged batch.
 bool Server::launch(Slot &s, std::vector<Req *> &batch) {
+  NvtxRange range("server batch");
   uint32_t op = 0;
   uint64_t limb = 0;
   s.reqs = batch;
@@ -203,7 +207,10 @@ bool Server::launch(Slot &s, std::vector<Req *> &batch) {
   int rc;
   {
     std::lock_guard<std::mutex> lock(ctx->mu);
-    rc = ctx->run_batch(op, s.d_keys, s.d_sel, s.d_off, s.d_msgs, s.d_out, s.d_status, st);
+    // the multi-lane (lower latency) shapes while everything in flight fits in
+    // one wave of the GPU; past that, the higher-throughput shapes
+    const int wide = inflight_ops + op <= wave_ops ? 1 : 0;
+    rc = ctx->run_batch(op, s.d_keys, s.d_sel, s.d_off, s.d_msgs, s.d_out, s.d_status, st, wide);
   }
   if (rc) {
     fatal = rc;
@@ -216,6 +223,8 @@ bool Server::launch(Slot &s, std::vector<Req *> &batch) {
     return false;
   }
   s.busy = true;
+  s.ops = op;
+  inflight_ops += op;
   batches++;
   return true;
 }
@@ -243,6 +252,8 @@ void Server::finish(Slot &s) {
     pending--;
   }
   inflight_bytes -= s.bytes;
+  inflight_ops -= s.ops;
+  s.ops = 0;
   s.reqs.clear();
   s.busy = false;
 }
@@ -255,6 +266,23 @@ void Server::loop() {
     // 1. retire finished batches
     for (Slot &s : slots) {
       if (s.busy && cudaEventQuery(s.ev) == cudaSuccess) finish(s);
+    }
+    // on stop, requests whose arrival time has not come are cancelled: never
+    // launched, RSA_ERR_TIMEOUT in each of their status entries
+    if (stop) {
+      const uint64_t now = now_ns();
+      for (auto it = queue.begin(); it != queue.end();) {
+        Req *r = *it;
+        if (r->arrive <= now) {
+          ++it;
+          continue;
+        }
+        r->state = RSA_ERR_TIMEOUT;
+        if (r->status)
+          for (uint32_t i = 0; i < r->count; ++i) r->status[i] = RSA_ERR_TIMEOUT;
+        pending--;
+        it = queue.erase(it);
+      }
     }
     if (pending == 0) done_cv.notify_all();
     if (stop && queue.empty() && std::none_of(slots.begin(), slots.end(), [](const Slot &s) { return s.busy; }))

@@ -6,6 +6,9 @@ GPU.  Every request's result must equal the oracle's and the result of the
 same messages run alone through rsa_modexp_key; a request larger than the
 memory budget allows is refused at submit.
 """
+import threading
+import time
+
 import numpy as np
 import pytest
 
@@ -70,5 +73,61 @@ def test_serving_mixed_arrivals(torch_cuda):
             rsa_server_submit(ctx.handle, kids[3], CRT, big, np.zeros_like(big))
         assert ei.value.code == -4
         rsa_server_stop(ctx.handle)
+    finally:
+        ctx.close()
+
+
+
+def test_serving_failure_paths(torch_cuda):
+    """A request whose arrival time never comes (a dropped doorbell) keeps the
+    drain from finishing: rsa_server_drain returns RSA_ERR_TIMEOUT, and
+    rsa_server_stop cancels it promptly with RSA_ERR_TIMEOUT in its status.
+    A submitting thread that dies half way leaves what it queued to be served
+    correctly; a request under an unknown key is refused at submit."""
+    from paper_1407_1465_gb300 import (RsaContext, RsaError, build, rsa_server_clock, rsa_server_drain,
+                                       rsa_server_poll, rsa_server_start, rsa_server_stop, rsa_server_submit)
+    build.build()
+    key = workloads.gen_keys([(2048, 0)], workloads.DEFAULT_SEED)[0]
+    ctx = RsaContext(0, mem_budget_bytes=4 << 30)
+    try:
+        kid = ctx.keyload(key.bits, key.n, key.e, key.d, key.p, key.q)
+        rsa_server_start(ctx.handle, max_inflight_batches=4, batch_window_us=100, mem_budget_bytes=64 << 20)
+        done = []
+        died = []
+
+        def producer():
+            try:
+                for r in range(10):
+                    if r == 5:
+                        raise RuntimeError("producer died")
+                    msgs = workloads.messages_below(key.n, 7 + r, 5, ("fail", r))
+                    out = np.zeros_like(msgs)
+                    t = rsa_server_submit(ctx.handle, kid, CRT, msgs, out)
+                    done.append((t, msgs, out))
+            except RuntimeError as exc:
+                died.append(exc)
+
+        th = threading.Thread(target=producer)
+        th.start()
+        th.join()
+        assert died and len(done) == 5
+        far_msgs = workloads.messages_below(key.n, 3, 6, "far")
+        far_out = np.zeros_like(far_msgs)
+        far_status = np.full(3, 99, dtype=np.int32)
+        rsa_server_submit(ctx.handle, kid, CRT, far_msgs, far_out, far_status,
+                          arrive_ns=rsa_server_clock(ctx.handle) + 3600 * 10**9)
+        with pytest.raises(RsaError) as ei:
+            rsa_server_drain(ctx.handle, timeout_ms=2000)
+        assert ei.value.code == -6
+        for t, msgs, out in done:
+            assert rsa_server_poll(ctx.handle, t) == 1
+            assert np.array_equal(out, oracle.crt_batch(msgs, key.d, key.p, key.q))
+        with pytest.raises(RsaError) as ei:
+            rsa_server_submit(ctx.handle, 999, CRT, far_msgs, np.zeros_like(far_msgs))
+        assert ei.value.code == -2
+        t0 = time.monotonic()
+        rsa_server_stop(ctx.handle)
+        assert time.monotonic() - t0 < 5.0
+        assert (far_status == -6).all() and not far_out.any()
     finally:
         ctx.close()
