@@ -43,10 +43,17 @@ namespace {
 constexpr int kGcdThreads = 128;
 constexpr int kOwn = 32;            // moduli per warp: the own block
 
+// Scratch words per block of the product tree for blocks of B moduli: one
+// level buffer of B L words and B/2 partial products of up to (B/2 + 1) L words.
+__host__ __device__ constexpr size_t gcd_scratch_words(uint32_t L, uint32_t B) {
+  return ((size_t)B + (size_t)(B / 2) * (B / 2 + 1)) * L;
+}
+
 struct GcdArgs {
   const uint32_t *mods;   // count rows of L words
   uint8_t *valid;         // count: 1 odd and > 1
   uint32_t *bprod;        // block c at c * blk * L words, blk * L words each
+  uint32_t *bscratch;     // block c at c * gcd_scratch_words(L, blk): the product tree's buffers
   uint32_t *part;         // nparts * count rows of L words
   uint32_t *gcds;         // count rows of L words, or null
   int32_t *flags;         // count, or null
@@ -300,51 +307,94 @@ __device__ __forceinline__ bool valid_mod(const uint32_t *row, int L) {
   return (row[0] & 1u) && (hi != 0u || row[0] >= 3u);
 }
 
-// Block products, one thread per block: P_c = prod of the block's valid
-// moduli (an invalid one counts as 1), B*L words, built in place: multiplying
-// the m*L-word prefix by n_j scans it from the bottom, word a of the result is
-// final once row a is added, so it overwrites the row's own multiplier.
+// Block products, one warp per block: P_c = prod of the block's valid moduli
+// (an invalid one, and a slot past the last modulus, counts as 1), B*L words,
+// by a product tree.  Level l multiplies pairs of 2^(l-1) L-word numbers;
+// each product A*B is split over the L-word chunks B_k of B, one lane each:
+// lane (p, k) scans A's words against B_k held in registers (word a of
+// A*B_k is final once row a is added), and when a product has several chunks
+// one lane adds the partial products A*B_k * 2^(32 k L) with a running carry.
+// The levels alternate between a scratch buffer and the block's slot of
+// bprod so that the last one lands in bprod.
 template <int L>
 __global__ void __launch_bounds__(64) bgcd_block_kernel(GcdArgs a) {
   const uint32_t nblk = (a.count + a.blk - 1) / a.blk;
-  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nblk; c += gridDim.x * blockDim.x) {
-    const uint32_t j0 = c * a.blk, j1 = min(a.count, j0 + a.blk);
-    uint32_t *z = a.bprod + (size_t)c * a.blk * L;
-    uint4 *z4 = reinterpret_cast<uint4 *>(z);
-    for (uint32_t j = j0; j < j1; ++j) {
-      const uint32_t *row = a.mods + (size_t)j * L;
-      const bool ok = valid_mod(row, L);
+  const int lane = threadIdx.x & 31;
+  const uint32_t c = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (c >= nblk) return;                               // whole warp
+  const uint32_t blk = a.blk, half = blk / 2;
+  const uint32_t j0 = c * blk;
+  int levels = 0;
+  for (uint32_t v = blk; v > 1; v >>= 1) ++levels;
+  uint32_t *slot = a.bprod + (size_t)c * blk * L;
+  uint32_t *scr = a.bscratch + (size_t)c * gcd_scratch_words(L, blk);
+  uint32_t *part = scr + (size_t)blk * L;             // after the level buffer
+  // level 0 into the buffer the parity of `levels` picks (odd: scratch)
+  uint32_t *cur = (levels & 1) ? scr : slot;
+  uint32_t *nxt = (levels & 1) ? slot : scr;
+  for (uint32_t e = (uint32_t)lane; e < blk; e += 32) {
+    const uint32_t j = j0 + e;
+    bool ok = false;
+    if (j < a.count) {
+      ok = valid_mod(a.mods + (size_t)j * L, L);
       a.valid[j] = ok ? 1 : 0;
-      const uint32_t m = j - j0;                       // words in the prefix: m * L
-      uint4 *top = z4 + (size_t)m * (L / 4);
-      if (m == 0) {
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(cur + (size_t)e * L);
+    const uint4 *src = reinterpret_cast<const uint4 *>(a.mods + (size_t)j * L);
 #pragma unroll 1
-        for (int g = 0; g < L / 4; ++g)
-          top[g] = ok ? __ldg(reinterpret_cast<const uint4 *>(row) + g) : make_uint4(g == 0 ? 1u : 0u, 0u, 0u, 0u);
-        continue;
-      }
-      if (!ok) {                                       // times 1: L more zero words
-#pragma unroll 1
-        for (int g = 0; g < L / 4; ++g) top[g] = make_uint4(0u, 0u, 0u, 0u);
-        continue;
-      }
+    for (int g = 0; g < L / 4; ++g) dst[g] = ok ? __ldg(src + g) : make_uint4(g == 0 ? 1u : 0u, 0u, 0u, 0u);
+  }
+  __syncwarp();
+  for (int l = 1; l <= levels; ++l) {
+    const uint32_t s_words = (uint32_t)L << (l - 1);   // each factor
+    const uint32_t cp = 1u << (l - 1);                 // chunks of B per product
+    const uint32_t np = blk >> l;                      // products at this level
+    if ((uint32_t)lane < half) {
+      const uint32_t p = (uint32_t)lane / cp, k = (uint32_t)lane % cp;
+      const uint32_t *A = cur + (size_t)(2 * p) * s_words;
+      const uint32_t *B = cur + (size_t)(2 * p + 1) * s_words + (size_t)k * L;
+      uint32_t *P = cp == 1 ? nxt + (size_t)p * 2 * s_words : part + (size_t)lane * (s_words + L);
       NRegs<L> X;
-      load_n<L>(X, row);
+      load_n<L>(X, B);
       uint32_t t[L + 2];
 #pragma unroll
-      for (int k = 0; k < L + 2; ++k) t[k] = 0u;
+      for (int q = 0; q < L + 2; ++q) t[q] = 0u;
+      const uint4 *A4 = reinterpret_cast<const uint4 *>(A);
+      uint4 *P4 = reinterpret_cast<uint4 *>(P);
 #pragma unroll 1
-      for (uint32_t g = 0; g < m * (L / 4); ++g) {
-        uint4 v = z4[g];
+      for (uint32_t g = 0; g < s_words / 4; ++g) {
+        uint4 v = A4[g];
         v.x = mul_shift<L>(t, X, v.x);
         v.y = mul_shift<L>(t, X, v.y);
         v.z = mul_shift<L>(t, X, v.z);
         v.w = mul_shift<L>(t, X, v.w);
-        z4[g] = v;
+        P4[g] = v;
       }
 #pragma unroll
-      for (int g = 0; g < L / 4; ++g) top[g] = make_uint4(t[4 * g], t[4 * g + 1], t[4 * g + 2], t[4 * g + 3]);
+      for (int g = 0; g < L / 4; ++g)
+        P4[s_words / 4 + g] = make_uint4(t[4 * g], t[4 * g + 1], t[4 * g + 2], t[4 * g + 3]);
     }
+    __syncwarp();
+    if (cp > 1 && (uint32_t)lane < np) {
+      // out = sum_k part_k * 2^(32 k L), part_k of s_words + L words
+      const uint32_t p = (uint32_t)lane, pw = s_words + L;
+      const uint32_t *base = part + (size_t)p * cp * pw;
+      uint32_t *out = nxt + (size_t)p * 2 * s_words;
+      uint64_t carry = 0;
+#pragma unroll 1
+      for (uint32_t w = 0; w < 2 * s_words; ++w) {
+        uint64_t acc = carry;
+        const uint32_t khi = min(cp - 1, w / L);
+        const uint32_t klo = w >= pw ? (w - pw) / L + 1 : 0u;
+        for (uint32_t k = klo; k <= khi; ++k) acc += base[(size_t)k * pw + (w - k * L)];
+        out[w] = (uint32_t)acc;
+        carry = acc >> 32;
+      }
+    }
+    __syncwarp();
+    uint32_t *tmp = cur;
+    cur = nxt;
+    nxt = tmp;
   }
 }
 
@@ -609,15 +659,14 @@ struct GcdLaunch {
 };
 
 // Moduli per block product.  Larger blocks need fewer Montgomery
-// multiplications into the running product (one per block) but the block
-// products themselves take longer (one thread multiplies B moduli in
-// sequence: 0.46 / 1.9 / 8.5 ms for B = 8 / 16 / 32 at 2048 bits on GB300).
-// Measured for 2048-bit moduli: 32 wins from about 12288 moduli up (16384:
-// 188 ms against 193 ms with 16), 8 below about 4096 (2048: 4.4 ms of block
-// products and reductions against 5.5 ms with 16).
+// multiplications into the running product (one per block) and longer
+// product trees (block kernel 1.4 ms at B = 32 for 16384 2048-bit moduli on
+// GB300).  Measured for 2048-bit moduli: 32 wins from about 8192 moduli up
+// (16384: 181.0 ms against 192.0 with 16 and 218.7 with 8); at 2048 moduli 8
+// and 16 tie (5.4 ms) and 32 is slower (6.0 ms).
 int gcd_block_size(uint64_t count) {
   const char *v = std::getenv("RSAGPU_GCD_BLOCK");
-  const int def = count >= 12288 ? 32 : count >= 4096 ? 16 : 8;
+  const int def = count >= 8192 ? 32 : count >= 4096 ? 16 : 8;
   const int b = v ? std::atoi(v) : def;
   return (b == 8 || b == 16 || b == 32) ? b : def;
 }
@@ -694,14 +743,16 @@ extern "C" int rsa_batch_gcd(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const
   const uint32_t L = pl.L;
   const size_t valid_bytes = ((size_t)count + 15) / 16 * 16;
   const size_t bprod_bytes = (size_t)pl.nblk * pl.blk * L * 4;
-  if ((rc = c->ensure(w.gcd0, valid_bytes + bprod_bytes)) ||
+  const size_t scratch_bytes = (size_t)pl.nblk * gcd_scratch_words(L, pl.blk) * 4;
+  if ((rc = c->ensure(w.gcd0, valid_bytes + bprod_bytes + scratch_bytes)) ||
       (rc = c->ensure(w.gcd1, (size_t)pl.nparts * count * L * 4)))
     return rc;
   uint8_t *base = static_cast<uint8_t *>(w.gcd0.ptr);
-  GcdArgs h{moduli, base, reinterpret_cast<uint32_t *>(base + valid_bytes), static_cast<uint32_t *>(w.gcd1.ptr),
+  GcdArgs h{moduli, base, reinterpret_cast<uint32_t *>(base + valid_bytes),
+            reinterpret_cast<uint32_t *>(base + valid_bytes + bprod_bytes), static_cast<uint32_t *>(w.gcd1.ptr),
             gcds, flags, (uint32_t)count, pl.blk, (uint32_t)pl.nparts};
   const uint64_t cap = (uint64_t)pl.per_sm * c->sm_count;
-  const int grid_blk = (int)std::max<uint64_t>(1, std::min<uint64_t>((pl.nblk + 63) / 64, (uint64_t)c->sm_count * 8));
+  const int grid_blk = (int)((pl.nblk + 1) / 2);      // one warp per block, two per CTA
   const int grid_main = (int)std::max<uint64_t>(1, std::min<uint64_t>((pl.nsb * pl.nparts + 3) / 4, cap));
   const int grid_fin = (int)std::max<uint64_t>(1, std::min<uint64_t>((pl.nsb + 3) / 4, cap));
   int launches = 0;
