@@ -22,7 +22,24 @@ constexpr int kKeyWordsMax = (KeyLayout(128).total + 3) / 4 * 4;
 //   CRT H=64: exchange + 2 stages = 3 * 64 * 128 B; public L=64: 2 warps x 2 stages = 4 * 64 * 128 B;
 //   public wide L=128: 1 warp x 2 stages = 2 * 128 * 128 B
 constexpr size_t kWorkBytes = (size_t)4 * 64 * 128;
-constexpr size_t kSmemBytes = (size_t)kKeyWordsMax * 4 + kWorkBytes;
+// work area each group's tile functions use (the largest of its classes):
+//   BIG  four-lane CRT H=64: exchange + 2 stages of (H/4) x 8 uint4
+//   CRT  public L=32: 2 warps x 2 stages of (L/4) x 32 uint4 (CRT H=32 needs 3 such stages)
+//   L64  public L=64: 2 warps x 2 stages of (L/4) x 32 uint4
+//   WIDE public L=128, four lanes: 2 warps x 2 stages of (L/4) x 8 uint4
+__host__ __device__ constexpr size_t work_bytes(int g) {
+  return g == GRP_BIG   ? (size_t)3 * (64 / 4) * 8 * 16
+         : g == GRP_CRT ? (size_t)4 * (32 / 4) * 32 * 16
+         : g == GRP_L64 ? (size_t)4 * (64 / 4) * 32 * 16
+                        : (size_t)4 * (128 / 4) * 8 * 16;
+}
+static_assert(work_bytes(GRP_BIG) <= kWorkBytes && work_bytes(GRP_CRT) <= kWorkBytes &&
+                  work_bytes(GRP_L64) <= kWorkBytes && work_bytes(GRP_WIDE) <= kWorkBytes,
+              "work areas");
+// uint4 count of the stages a tile function indexes: n_stages * kStage
+__host__ __device__ constexpr size_t stage_u4(int n_stages, int limbs, int ops_per_warp) {
+  return (size_t)n_stages * (limbs / 4) * ops_per_warp;
+}
 
 template <int H, int W>
 __device__ __forceinline__ void run_crt(const uint32_t *ks, uint4 *work, uint4 *table_warp, int warp, int lane,
@@ -78,8 +95,10 @@ __device__ __forceinline__ void run_plain(const uint32_t *ks, uint4 *work, uint4
   plain_tile<L, kBatchWindowPlain, kU, false>(ks, lane, work + warp * kStage + lane, table_warp + lane, io);
 }
 
+// The multi-lane CRT group needs about 12 KB of shared memory per CTA, so
+// registers decide its occupancy: capped at 128 a thread, 8 CTAs per SM.
 template <int G>
-__global__ void __launch_bounds__(64, 1) batch_exec_kernel(BatchDesc d) {
+__global__ void __launch_bounds__(64, G == GRP_BIG ? 8 : 1) batch_exec_kernel(BatchDesc d) {
   extern __shared__ uint4 smem4[];
   __shared__ int32_t s_tile;
   uint32_t *ks = reinterpret_cast<uint32_t *>(smem4);
@@ -107,6 +126,9 @@ __global__ void __launch_bounds__(64, 1) batch_exec_kernel(BatchDesc d) {
     const TileIO io_warp{d.msgs, d.out, d.status, d.sorted, d.offsets, (uint32_t)(td.op_start + 32 * warp),
                          (uint32_t)wn};
     if constexpr (G == GRP_BIG) {
+      static_assert(stage_u4(3, 48, 8) * 16 <= work_bytes(GRP_BIG) && stage_u4(3, 64, 8) * 16 <= work_bytes(GRP_BIG) &&
+                        stage_u4(3, 32, 8) * 16 <= work_bytes(GRP_BIG) && stage_u4(3, 64, 4) * 16 <= work_bytes(GRP_BIG),
+                    "work area of a four/eight-lane CRT class");
       static_assert(batch_table_need(kBatchWindowCrt48, 48 / 4) <= batch_table_u4(GRP_BIG) &&
                         batch_table_need(kBatchWindowCrt64, 64 / 4) <= batch_table_u4(GRP_BIG) &&
                         batch_table_need(kBatchWindowCrt32, 32 / 4) <= batch_table_u4(GRP_BIG) &&
@@ -118,6 +140,8 @@ __global__ void __launch_bounds__(64, 1) batch_exec_kernel(BatchDesc d) {
       else if (td.cls == CLS_CRT64W) run_crt8<64, kBatchWindowCrt64>(ks, work, table_warp, warp, lane, io_pair);
     } else if constexpr (G == GRP_L64) {
       static_assert(batch_table_need(kBatchWindowPlain, 64) <= batch_table_u4(GRP_L64), "plain L=64 table");
+      static_assert(stage_u4(4, 64, 32) * 16 <= work_bytes(GRP_L64) && stage_u4(2, 64, 32) * 16 <= work_bytes(GRP_L64),
+                    "work area of the L=64 classes");
       if (wn > 0) {
         if (td.cls == CLS_PUB64) run_pub<64>(ks, work, warp, lane, io_warp);
         else if (td.cls == CLS_PLAIN64) run_plain<64>(ks, work, table_warp, warp, lane, io_warp);
@@ -125,11 +149,16 @@ __global__ void __launch_bounds__(64, 1) batch_exec_kernel(BatchDesc d) {
     } else if constexpr (G == GRP_WIDE) {
       // 16-operation tiles: 8 per warp
       const int32_t wn8 = min(8, max(0, td.nops - 8 * warp));
+      static_assert(stage_u4(4, 128, 8) * 16 <= work_bytes(GRP_WIDE) && stage_u4(4, 96, 8) * 16 <= work_bytes(GRP_WIDE),
+                    "work area of the wide public classes");
       const TileIO io8{d.msgs, d.out, d.status, d.sorted, d.offsets, (uint32_t)(td.op_start + 8 * warp),
                        (uint32_t)wn8};
       if (td.cls == CLS_PUB96) run_pub_wide<96>(ks, work, warp, lane, io8);
       else if (td.cls == CLS_PUB128) run_pub_wide<128>(ks, work, warp, lane, io8);
     } else {
+      static_assert(stage_u4(3, 32, 32) * 16 <= work_bytes(GRP_CRT) && stage_u4(4, 32, 32) * 16 <= work_bytes(GRP_CRT) &&
+                        stage_u4(2, 32, 32) * 16 <= work_bytes(GRP_CRT),
+                    "work area of the one-lane classes");
       static_assert(batch_table_need(kBatchWindowCrt16, 16) <= batch_table_u4(GRP_CRT) &&
                         batch_table_need(kBatchWindowCrt32, 32) <= batch_table_u4(GRP_CRT) &&
                         batch_table_need(kBatchWindowPlain, 32) <= batch_table_u4(GRP_CRT),
@@ -171,6 +200,6 @@ const void *batch_exec_fn(int group) {
     default: return nullptr;
   }
 }
-size_t batch_exec_smem_bytes(int group) { (void)group; return kSmemBytes; }
+size_t batch_exec_smem_bytes(int group) { return (size_t)kKeyWordsMax * 4 + work_bytes(group); }
 
 }  // namespace rsagpu
