@@ -96,7 +96,9 @@ __device__ __forceinline__ void run_plain(const uint32_t *ks, uint4 *work, uint4
 }
 
 // The multi-lane CRT group needs about 12 KB of shared memory per CTA, so
-// registers decide its occupancy: capped at 128 a thread, 8 CTAs per SM.
+// registers decide its occupancy: capped at 128 a thread (20 bytes of
+// spills), 8 CTAs per SM instead of 5.  The same cap on the one-lane group
+// spills in its 32-limb CRT and was not faster (728 K against 732 K ops/s).
 template <int G>
 __global__ void __launch_bounds__(64, G == GRP_BIG ? 8 : 1) batch_exec_kernel(BatchDesc d) {
   extern __shared__ uint4 smem4[];
