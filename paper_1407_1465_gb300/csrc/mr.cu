@@ -34,15 +34,23 @@ struct MrArgs {
   const uint32_t *cands;    // count rows of L limbs
   const uint32_t *bases;    // count * rounds rows of L limbs, row i * rounds + r
   int32_t *verdict;         // count: 1 probable prime, 0 composite, -1 invalid candidate
-  uint4 *tables;            // per warp 2^W * L/4 * 32 uint4
+  uint4 *tables;            // per warp 2^W * L/4 * 32 uint4, then kLaneBufs stages
   uint32_t count, rounds;
 };
 
+// Per-warp [L/4][32] uint4 buffers.  The B operand of every multiplication
+// sits in shared memory; R^2, the Montgomery forms of 1 and n - 1 and the
+// exponent d are read once per round or per window and live in global memory
+// next to the window table (coalesced, L2-resident), which keeps shared memory
+// from limiting the resident warps.
 template <int L>
 struct MrSmem {
   static constexpr int kStageU4 = (L / 4) * 32;   // one [L/4][32] uint4 buffer per warp
-  static constexpr int kBuffers = 5;              // B operand, R^2, one, minus one, exponent d
+  static constexpr int kBuffers = 1;              // B operand
+  static constexpr int kLaneBufs = 4;             // global: R^2, one, minus one, exponent d
   static constexpr size_t bytes(int warps) { return (size_t)warps * kBuffers * kStageU4 * 16; }
+  template <int W>
+  __host__ __device__ static constexpr size_t global_u4_per_warp() { return ((size_t)1 << W) * (L / 4) * 32 + (size_t)kLaneBufs * kStageU4; }
 };
 
 // x = 2x mod n for x < n: the doubled value has L limbs plus a top bit; one
@@ -94,10 +102,10 @@ __global__ void __launch_bounds__(kMrThreads) mr_kernel(MrArgs a) {
   using Sm = MrSmem<L>;
   extern __shared__ uint4 smem4[];
   const int nw = blockDim.x / 32, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint4 *base_w = smem4 + (size_t)warp * Sm::kBuffers * Sm::kStageU4 + lane;
-  uint4 *b_lane = base_w, *r2_lane = base_w + Sm::kStageU4, *one_lane = base_w + 2 * Sm::kStageU4;
-  uint4 *m1_lane = base_w + 3 * Sm::kStageU4, *d_lane = base_w + 4 * Sm::kStageU4;
-  uint4 *table_lane = a.tables + (size_t)(blockIdx.x * nw + warp) * (1 << W) * (L / 4) * 32 + lane;
+  uint4 *b_lane = smem4 + (size_t)warp * Sm::kBuffers * Sm::kStageU4 + lane;
+  uint4 *table_lane = a.tables + (size_t)(blockIdx.x * nw + warp) * Sm::template global_u4_per_warp<W>() + lane;
+  uint4 *r2_lane = table_lane + ((size_t)1 << W) * (L / 4) * 32;
+  uint4 *one_lane = r2_lane + Sm::kStageU4, *m1_lane = r2_lane + 2 * Sm::kStageU4, *d_lane = r2_lane + 3 * Sm::kStageU4;
   const uint32_t ntiles = (a.count + 31) / 32;
   constexpr int kSqToR2 = (L == 16) ? 3 : 4;    // log2(L / 2)
   constexpr int kNwin = (32 * L + W - 1) / W;
@@ -251,7 +259,9 @@ extern "C" int rsa_mr_batch(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const 
   const int per_cta = kMrThreads / 32;
   const int grid = (int)std::max<uint64_t>(
       1, std::min<uint64_t>((warps_needed + per_cta - 1) / per_cta, (uint64_t)c->sm_count * 4));
-  const size_t tbytes = (size_t)grid * per_cta * ((size_t)1 << kMrWindow) * (size_t)(L / 4) * 32 * 16;
+  const size_t per_warp_u4 = (L == 16) ? MrSmem<16>::global_u4_per_warp<kMrWindow>()
+                                       : MrSmem<32>::global_u4_per_warp<kMrWindow>();
+  const size_t tbytes = (size_t)grid * per_cta * per_warp_u4 * 16;
   int rc = c->ensure(w.tables, tbytes);
   if (rc) return rc;
   MrArgs h{cands, bases, verdicts, static_cast<uint4 *>(w.tables.ptr), (uint32_t)count, rounds};
