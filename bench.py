@@ -48,7 +48,7 @@ def workload_desc(bits, count, kind="crt"):
 # hash to the recorded stamp and the window matches; otherwise reported as null.
 PROFILED_TRAFFIC = {
     # (workload, variant): one ncu capture of that kernel, valid while its sources hash to the stamp
-    ("rsa2048", 3): {"window": 3, "stamp": "58ece2abe3de3d97", "dram_bytes_per_op": 1167.4,
+    ("rsa2048", 3): {"window": 3, "stamp": "4ac01f94619e9b34", "dram_bytes_per_op": 1167.4,
                      "files": ["crt_tc.cu", "crt_tc.h", "tc.cuh", "mont.cuh", "kernels.cuh", "keyrec.h"],
                      "source": "profiles/crt_tc_half_kernel_rsa2048_w3_ncu_full.md"},
     ("rsa2048", 1): {"window": 4, "stamp": "2c547aada0325644", "dram_bytes_per_op": 257607.0,

@@ -615,9 +615,9 @@ struct GcdLaunch {
   static const void *main_fn(int minb) {
     return minb == 2 ? (const void *)bgcd_kernel<L, U, 2> : (const void *)bgcd_kernel<L, U, 3>;
   }
+  // Shared-memory opt-in of the kernels above 48 KiB, set on every call: the
+  // attribute belongs to the current device's context, and setting it is cheap.
   static int prepare(size_t smem) {
-    static bool done = false;
-    if (done) return 0;
     cudaError_t e = cudaSuccess;
     for (int m = 2; m <= 3 && e == cudaSuccess; ++m)
       e = cudaFuncSetAttribute(main_fn(m), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -626,7 +626,6 @@ struct GcdLaunch {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(bgcd_combine_kernel<L, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(bgcd)");
-    done = true;
     return 0;
   }
   static int per_sm(size_t smem, int minb) {

@@ -692,12 +692,9 @@ size_t tc_halves_bytes(uint32_t count) {
 
 template <int W>
 static cudaError_t launch_half(const HalfArgs &h, int grid, cudaStream_t s) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(crt_tc_half_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  // set on every call: the attribute belongs to the current device's context
+  cudaError_t e = cudaFuncSetAttribute(crt_tc_half_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+  if (e != cudaSuccess) return e;
   crt_tc_half_kernel<W><<<grid, kThreads, kSmem, s>>>(h);
   return cudaGetLastError();
 }

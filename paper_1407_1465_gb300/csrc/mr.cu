@@ -223,13 +223,10 @@ __global__ void __launch_bounds__(kMrThreads) mr_kernel(MrArgs a) {
 template <int L>
 cudaError_t launch_mr(const MrArgs &h, int grid, cudaStream_t s) {
   const size_t smem = MrSmem<L>::bytes(kMrThreads / 32);
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(mr_kernel<L, kMrWindow, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  // set on every call: the attribute belongs to the current device's context
+  cudaError_t e = cudaFuncSetAttribute(mr_kernel<L, kMrWindow, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
   mr_kernel<L, kMrWindow, 8><<<grid, kMrThreads, smem, s>>>(h);
   return cudaGetLastError();
 }
