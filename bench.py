@@ -446,6 +446,12 @@ def run_ragged(args):
         key = rb.keys[rb.key_ids[i]]
         prods += rsa_products_per_op(key.bits, int(rb.exp_sel[i]), key.e, 5)
 
+    tuning = None
+    if args.autotune:
+        # the ragged autotuner on this very batch (untimed): lanes per operation and CTA cap
+        from paper_1407_1465_gb300 import rsa_autotune_batch
+        tuning = rsa_autotune_batch(ctx.handle, count, key_ids, sels, offs, msgs, out)
+
     def step_ragged():
         rsa_modexp_batch(ctx.handle, count, key_ids, sels, offs, msgs, out, status, sptr)
 
@@ -486,7 +492,7 @@ def run_ragged(args):
                    "groups": len(gbufs)},
         "one_key_per_launch": {"ms_per_step": res["loop"], "value": count / (res["loop"] / 1e3),
                                "launches": len(gbufs)},
-        "speedup_vs_loop": res["loop"] / res["ragged"],
+        "speedup_vs_loop": res["loop"] / res["ragged"], "tuning": tuning or "automatic",
         "roofline": {"bound": "alu", "achieved": prods / (res["ragged"] / 1e3) / 1e12, "unit": "Tprod/s",
                      "products_per_step": prods},
     }
@@ -655,6 +661,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-latency", action="store_true", help="skip the serving-latency sweep of the default run")
+    ap.add_argument("--autotune", action="store_true", help="ragged: run the ragged autotuner on the batch first")
     args = ap.parse_args()
     if args.workload == "ragged":
         return run_ragged(args)

@@ -319,7 +319,11 @@ typedef struct rsa_tuning {
 
 /* Set (or, with NULL, reset to automatic) the launch parameters used for keys of
  * nbits bits and exponent kind exp_sel.  exp_sel = RSA_TUNE_RAGGED (with nbits 0)
- * addresses the persistent kernel of rsa_modexp_batch (only ctas_per_sm applies). */
+ * addresses rsa_modexp_batch and the request loop: ctas_per_sm caps the resident
+ * CTAs per SM of its persistent kernels, threads_per_op picks the lanes per
+ * operation of 2048/4096-bit CRT (1: one/four lanes, the throughput shapes; 4:
+ * four/eight lanes, the latency shapes; 0: automatic, the latency shapes while
+ * the work fits one wave of the GPU); the other fields do not apply. */
 #define RSA_TUNE_RAGGED 3
 int rsa_set_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, const rsa_tuning *t);
 /* Read the parameters currently in force for (nbits, exp_sel). */
@@ -337,6 +341,18 @@ int rsa_get_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, rsa_tuning *t)
  * Synchronous; allocates scratch from the context's budget. */
 int rsa_autotune(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint64_t count, const char *cache_path,
                  rsa_tuning *best, double *best_ms);
+
+/* Autotuner for ragged batches: times the given batch (the arguments of
+ * rsa_modexp_batch, device pointers; out receives its results) under each
+ * lanes-per-operation policy (threads_per_op 1 and 4) and resident-CTA cap
+ * (ctas_per_sm 0 = occupancy maximum, 2, 4), installs the fastest as the
+ * RSA_TUNE_RAGGED tuning and returns it in *best (*best_ms: time per batch,
+ * median of three).  Window widths and tiles are fixed per work class.
+ * Synchronous, on a private stream.  Errors: RSA_ERR_ARG, RSA_ERR_KEY (the
+ * batch holds operations its keys cannot serve), RSA_ERR_NOMEM, RSA_ERR_CUDA. */
+int rsa_autotune_batch(rsa_ctx *ctx, uint64_t count, const int32_t *key_ids, const uint8_t *exp_sel,
+                       const uint64_t *limb_offsets, const uint32_t *msgs, uint32_t *out, rsa_tuning *best,
+                       double *best_ms);
 
 /* Tensor-core operands of one 1024-bit prime m (variant 3), exactly as built at
  * key load: two K-major fp16 matrices in the no-swizzle core-matrix layout

@@ -18,7 +18,7 @@ import numpy as np
 from . import _lib
 from ._lib import (RSA_ERR_ARG, RSA_ERR_CUDA, RSA_ERR_KEY, RSA_ERR_NOMEM, RSA_ERR_RANGE,  # noqa: F401
                    RSA_ERR_TIMEOUT, RSA_ERR_UNSUPPORTED, RSA_ERR_VERIFY, RSA_EXP_PRIVATE_CRT, RSA_EXP_PRIVATE_PLAIN,
-                   RSA_EXP_PUBLIC, RSA_OK, RsaError, check, last_error, rsa_stats, rsa_tuning)
+                   RSA_EXP_PUBLIC, RSA_OK, RSA_TUNE_RAGGED, RsaError, check, last_error, rsa_stats, rsa_tuning)
 
 __all__ = [
     "RsaContext", "RsaError", "int_to_limbs", "limbs_to_int",
@@ -27,7 +27,7 @@ __all__ = [
     "rsa_modexp_key", "rsa_modexp_batch", "rsa_modexp_key_host", "rsa_modexp_batch_host",
     "rsa_sign_key", "rsa_verify_key", "rsa_mr_batch", "rsa_batch_gcd", "rsa_batch_gcd_plan",
     "rsa_sync", "rsa_last_error", "rsa_set_tuning", "rsa_get_tuning", "rsa_get_stats",
-    "rsa_products_per_op", "rsa_imad_probe", "rsa_crt_decrypt_noalloc", "rsa_autotune",
+    "rsa_products_per_op", "rsa_imad_probe", "rsa_crt_decrypt_noalloc", "rsa_autotune", "rsa_autotune_batch",
     "rsa_server_start", "rsa_server_submit", "rsa_server_submit_many", "rsa_server_clock", "rsa_server_poll", "rsa_server_drain", "rsa_server_get_stats",
     "rsa_server_stop",
 ]
@@ -235,6 +235,16 @@ def rsa_autotune(ctx: int, key_id: int, exp_sel: int, count: int, cache_path: st
             "variant": t.variant, "threads_per_op": t.threads_per_op, "ms": ms.value}
 
 
+def rsa_autotune_batch(ctx: int, count: int, key_ids, exp_sel, limb_offsets, msgs, out) -> dict:
+    """Time the ragged batch under each lanes-per-operation policy and resident-CTA
+    cap; installs the fastest as the RSA_TUNE_RAGGED tuning and returns it."""
+    t = rsa_tuning()
+    ms = ctypes.c_double()
+    check(_lib.lib().rsa_autotune_batch(ctx, count, _ptr(key_ids), _ptr(exp_sel), _ptr(limb_offsets), _ptr(msgs),
+                                        _ptr(out), ctypes.byref(t), ctypes.byref(ms)))
+    return {"ctas_per_sm": t.ctas_per_sm, "threads_per_op": t.threads_per_op, "ms": ms.value}
+
+
 def rsa_get_stats(ctx: int) -> dict:
     s = rsa_stats()
     check(_lib.lib().rsa_get_stats(ctx, ctypes.byref(s)))
@@ -403,6 +413,13 @@ class RsaContext:
             out = torch.empty_like(msgs)
         rsa_modexp_batch(self.handle, key_ids.numel(), key_ids, exp_sel, limb_offsets, msgs, out, status, stream)
         return out
+
+    def autotune_batch(self, key_ids, exp_sel, limb_offsets, msgs, out=None) -> dict:
+        """Tune rsa_modexp_batch on this batch (installs the fastest shapes)."""
+        import torch
+        if out is None:
+            out = torch.empty_like(msgs)
+        return rsa_autotune_batch(self.handle, key_ids.numel(), key_ids, exp_sel, limb_offsets, msgs, out)
 
     def sync(self, stream=None) -> int:
         return rsa_sync(self.handle, stream)

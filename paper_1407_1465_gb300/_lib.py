@@ -25,6 +25,7 @@ RSA_ERR_VERIFY = -8
 RSA_EXP_PUBLIC = 0
 RSA_EXP_PRIVATE_CRT = 1
 RSA_EXP_PRIVATE_PLAIN = 2
+RSA_TUNE_RAGGED = 3          # rsa_set_tuning / rsa_get_tuning: the ragged-batch kernels
 
 STATUS_NAMES = {
     0: "RSA_OK", -1: "RSA_ERR_ARG", -2: "RSA_ERR_KEY", -3: "RSA_ERR_RANGE", -4: "RSA_ERR_NOMEM",
@@ -105,6 +106,8 @@ SIGNATURES = [
     ("rsa_get_stats", ctypes.c_int, [_P, ctypes.POINTER(rsa_stats)]),
     ("rsa_autotune", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_char_p,
                                     ctypes.POINTER(rsa_tuning), ctypes.POINTER(ctypes.c_double)]),
+    ("rsa_autotune_batch", ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, _P, _P, _P,
+                                          ctypes.POINTER(rsa_tuning), ctypes.POINTER(ctypes.c_double)]),
     ("rsa_products_per_op", ctypes.c_double, [ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint32,
                                               ctypes.c_uint32, ctypes.c_int32]),
     ("rsa_imad_probe", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),

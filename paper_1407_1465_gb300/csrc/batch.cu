@@ -235,6 +235,39 @@ int Ctx::collect_device_errors(cudaStream_t s) {
   return RSA_OK;
 }
 
+void Ctx::release_stream(cudaStream_t s) {
+  cudaStreamSynchronize(s);
+  if (batch_state) {
+    std::vector<BatchState *> &v = batch_states(this);
+    for (auto it = v.begin(); it != v.end(); ++it) {
+      BatchState *b = *it;
+      if (b->stream != s) continue;
+      if (b->exec) cudaGraphExecDestroy(b->exec);
+      if (b->graph) cudaGraphDestroy(b->graph);
+      if (b->keydir.ptr) {
+        cudaFree(b->keydir.ptr);
+        release(b->keydir.bytes);
+      }
+      delete b;
+      v.erase(it);
+      break;
+    }
+  }
+  auto it = workspaces.find(s);
+  if (it != workspaces.end()) {
+    Workspace &w = it->second;
+    for (DevBuf *d : {&w.tables, &w.io_in, &w.io_out, &w.io_status, &w.aux0, &w.aux1, &w.aux2, &w.aux3, &w.halves,
+                      &w.verify, &w.gcd0, &w.gcd1})
+      if (d->ptr) {
+        cudaFree(d->ptr);
+        release(d->bytes);
+        d->ptr = nullptr;
+        d->bytes = 0;
+      }
+    workspaces.erase(it);
+  }
+}
+
 static BatchState *state_for(Ctx *c, cudaStream_t s) {
   for (BatchState *b : batch_states(c))
     if (b->stream == s) return b;
@@ -340,7 +373,13 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
   // and while the batch fits in one wave of the multi-lane group (8 operations
   // per resident warp pair) the GPU has idle SMs anyway.  Larger batches keep
   // one (four) lanes per operation, which has the higher throughput.
-  d.wide_crt32 = (wide < 0 ? count <= batch_wave_ops(s) : wide != 0) ? 1u : 0u;
+  // lanes per operation of the long CRT sizes: the caller's choice, else the
+  // tuned one (threads_per_op 1: one/four lanes, 4: four/eight), else by size
+  if (wide < 0) {
+    const int tpo = tune_for(0, RSA_TUNE_RAGGED).tpo;
+    wide = tpo == 4 ? 1 : tpo == 1 ? 0 : (count <= batch_wave_ops(s) ? 1 : 0);
+  }
+  d.wide_crt32 = wide != 0 ? 1u : 0u;
   {
     std::vector<int32_t> order(CLS_COUNT);
     std::iota(order.begin(), order.end(), 0);

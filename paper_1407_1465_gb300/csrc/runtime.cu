@@ -120,6 +120,7 @@ Tune Ctx::tune_for(uint32_t nbits, int kind) const {
   // 48/64 limbs need 255 registers on one lane and 128 on four (RSA-4096 CRT:
   // 127 K/s -> 145 K/s), and the one-lane public exponent of those sizes spills --
   // one lane otherwise (RSA-2048 CRT: 1.24 M/s on one lane, 1.10 M on two).
+  if (kind == RSA_TUNE_RAGGED) return t;   // ragged batches: 0 fields stay automatic
   if (!t.tpo) t.tpo = (L > 64 && kind != RSA_EXP_PRIVATE_PLAIN) ? 4 : 1;
   return t;
 }
@@ -590,6 +591,8 @@ int rsa_set_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, const rsa_tuni
   if (t->variant < 0 || t->variant > 3) return set_error(RSA_ERR_ARG, "variant must be 0 .. 3");
   if (!(t->threads_per_op == 0 || t->threads_per_op == 1 || t->threads_per_op == 2 || t->threads_per_op == 4))
     return set_error(RSA_ERR_ARG, "threads_per_op must be 0, 1, 2 or 4");
+  if (exp_sel == RSA_TUNE_RAGGED && t->threads_per_op == 2)
+    return set_error(RSA_ERR_ARG, "ragged batches: threads_per_op must be 0 (automatic), 1 or 4");
   if (exp_sel == RSA_EXP_PRIVATE_CRT && (t->warps_per_cta & 1))
     return set_error(RSA_ERR_ARG, "CRT kernels run warp pairs: warps_per_cta must be even");
   c->tuning[{nbits, exp_sel}] = Tune{t->window, t->warps_per_cta, t->ctas_per_sm, t->variant, t->threads_per_op};

@@ -91,6 +91,10 @@ struct Ctx {
   // operations one wave of the multi-lane group holds (after prepare_batch on s)
   uint64_t batch_wave_ops(cudaStream_t s);
   int collect_device_errors(cudaStream_t s);
+  // Free everything the library keeps for stream s (its ragged-batch graph and
+  // key directory, its workspace buffers) before the caller destroys s.
+  // Synchronises s first.
+  void release_stream(cudaStream_t s);
   void free_extra();
 };
 

@@ -164,7 +164,13 @@ void Server::release() {
                     (void *)s.h_out})
       if (h) cudaFreeHost(h);
     if (s.ev) cudaEventDestroy(s.ev);
-    if (s.stream) cudaStreamDestroy(s.stream);
+    if (s.stream) {
+      {
+        std::lock_guard<std::mutex> lock(ctx->mu);
+        ctx->release_stream(s.stream);   // the slot's ragged scratch leaves the budget
+      }
+      cudaStreamDestroy(s.stream);
+    }
   }
   slots.clear();
   for (auto &kv : all) delete kv.second;
@@ -209,7 +215,8 @@ bool Server::launch(Slot &s, std::vector<Req *> &batch) {
     std::lock_guard<std::mutex> lock(ctx->mu);
     // the multi-lane (lower latency) shapes while everything in flight fits in
     // one wave of the GPU; past that, the higher-throughput shapes
-    const int wide = inflight_ops + op <= wave_ops ? 1 : 0;
+    const int tuned = ctx->tune_for(0, RSA_TUNE_RAGGED).tpo;
+    const int wide = tuned == 4 ? 1 : tuned == 1 ? 0 : (inflight_ops + op <= wave_ops ? 1 : 0);
     rc = ctx->run_batch(op, s.d_keys, s.d_sel, s.d_off, s.d_msgs, s.d_out, s.d_status, st, wide);
   }
   if (rc) {

@@ -132,20 +132,7 @@ extern "C" int rsa_autotune(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint6
           }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    cudaStreamSynchronize(s);
-    {
-      auto it = c->workspaces.find(s);
-      if (it != c->workspaces.end()) {
-        Workspace &w = it->second;
-        for (DevBuf *d : {&w.tables, &w.io_in, &w.io_out, &w.io_status, &w.aux0, &w.aux1, &w.aux2, &w.aux3,
-                          &w.halves, &w.verify, &w.gcd0, &w.gcd1})
-          if (d->ptr) {
-            cudaFree(d->ptr);
-            c->release(d->bytes);
-          }
-        c->workspaces.erase(it);
-      }
-    }
+    c->release_stream(s);
     cudaStreamDestroy(s);
     cudaFree(in.ptr);
     c->release(in.bytes);
@@ -176,5 +163,81 @@ extern "C" int rsa_autotune(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint6
     best->threads_per_op = chosen.tpo;
   }
   if (best_ms) *best_ms = chosen_ms;
+  return RSA_OK;
+}
+
+// Ragged batches: time the caller's batch under each lanes-per-operation
+// policy of the long CRT sizes (one/four lanes, four/eight lanes) and each cap
+// on resident CTAs per SM of the persistent groups (occupancy maximum, 2, 4),
+// keep the fastest as the RSA_TUNE_RAGGED tuning.  Window widths and tiles are
+// fixed per work class (batch.h).
+extern "C" int rsa_autotune_batch(rsa_ctx *ctx, uint64_t count, const int32_t *key_ids, const uint8_t *exp_sel,
+                                  const uint64_t *limb_offsets, const uint32_t *msgs, uint32_t *out,
+                                  rsa_tuning *best, double *best_ms) {
+  if (!ctx) return set_error(RSA_ERR_ARG, "ctx is null");
+  if (count == 0 || count > 0x7fffffffull) return set_error(RSA_ERR_ARG, "count must be in 1..2^31-1");
+  if (!key_ids || !exp_sel || !limb_offsets || !msgs || !out) return set_error(RSA_ERR_ARG, "null pointer");
+  if ((reinterpret_cast<uintptr_t>(msgs) | reinterpret_cast<uintptr_t>(out)) & 15u)
+    return set_error(RSA_ERR_ARG, "message and output buffers must be 16-byte aligned");
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  std::lock_guard<std::mutex> lock(c->mu);
+  cudaSetDevice(c->device);
+  const std::pair<uint32_t, int> tk{0u, RSA_TUNE_RAGGED};
+  const bool had = c->tuning.count(tk) != 0;
+  const Tune saved = had ? c->tuning[tk] : Tune{0, 0, 0, 0, 0};
+  cudaStream_t s = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_error(e, "autotune stream");
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  double best_t = 1e30;
+  Tune chosen{0, 0, 0, 0, 0};
+  int err = RSA_OK;
+  for (int tpo : {1, 4}) {
+    for (int cps : {0, 2, 4}) {
+      c->tuning[tk] = Tune{0, 0, cps, 0, tpo};
+      if (c->run_batch(count, key_ids, exp_sel, limb_offsets, msgs, out, nullptr, s) != RSA_OK) continue;
+      float t3[3];
+      for (int r = 0; r < 3 && !err; ++r) {
+        cudaEventRecord(a, s);
+        if ((err = c->run_batch(count, key_ids, exp_sel, limb_offsets, msgs, out, nullptr, s))) break;
+        cudaEventRecord(b, s);
+        if ((e = cudaEventSynchronize(b)) != cudaSuccess) {
+          err = cuda_error(e, "autotune batch run");
+          break;
+        }
+        cudaEventElapsedTime(&t3[r], a, b);
+      }
+      if (err) break;
+      std::sort(t3, t3 + 3);
+      if (t3[1] < best_t) {
+        best_t = t3[1];
+        chosen = Tune{0, 0, cps, 0, tpo};
+      }
+    }
+    if (err) break;
+  }
+  // operations the batch itself rejects leave error bits on the stream: read
+  // and clear them so they do not surface at the caller's next rsa_sync
+  if (!err) err = c->collect_device_errors(s);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  c->release_stream(s);
+  cudaStreamDestroy(s);
+  if (err || best_t >= 1e29) {
+    if (had) c->tuning[tk] = saved;
+    else c->tuning.erase(tk);
+    return err ? err : set_error(RSA_ERR_UNSUPPORTED, "no launch shape ran for this batch");
+  }
+  c->tuning[tk] = chosen;
+  if (best) {
+    best->window = 0;
+    best->warps_per_cta = 0;
+    best->ctas_per_sm = chosen.ctas_per_sm;
+    best->variant = 0;
+    best->threads_per_op = chosen.tpo;
+  }
+  if (best_ms) *best_ms = best_t;
   return RSA_OK;
 }

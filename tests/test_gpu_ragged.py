@@ -188,3 +188,29 @@ def test_ragged_full_workload_sampled(torch_cuda, ctx):
         assert np.array_equal(out[off:off + row.size], expect_one(key, int(rb.exp_sel[i]), row))
     for k in kids:
         ctx.keyunload(k)
+
+
+def test_ragged_autotune_batch(torch_cuda, ctx, mixed_keys):
+    """The ragged autotuner times the batch under each lanes-per-operation policy
+    and CTA cap, installs the fastest, and results stay exact under it."""
+    from paper_1407_1465_gb300 import RSA_TUNE_RAGGED, RsaError
+    keys, kids = mixed_keys
+    ops, key_ids, sels, offsets, packed = build_mix(keys, kids, 300, 77)
+    dev = torch_cuda.device("cuda")
+    k = torch_cuda.from_numpy(key_ids).to(dev)
+    s = torch_cuda.from_numpy(sels).to(dev)
+    o = torch_cuda.from_numpy(offsets.view(np.int64)).to(dev)
+    m = torch_cuda.from_numpy(packed.view(np.int32)).to(dev)
+    try:
+        best = ctx.autotune_batch(k, s, o, m)
+        assert best["threads_per_op"] in (1, 4) and best["ctas_per_sm"] in (0, 2, 4) and best["ms"] > 0
+        t = ctx.get_tuning(0, RSA_TUNE_RAGGED)
+        assert t["threads_per_op"] == best["threads_per_op"] and t["ctas_per_sm"] == best["ctas_per_sm"]
+        out, st, rc = run_batch(torch_cuda, ctx, key_ids, sels, offsets, packed)
+        assert rc == 0 and (st == 0).all()
+        for (kk, kind, row), off in zip(ops, offsets):
+            assert np.array_equal(out[int(off):int(off) + row.size], expect_one(keys[kk], kind, row))
+        with pytest.raises(RsaError):
+            ctx.set_tuning(0, RSA_TUNE_RAGGED, threads_per_op=2)
+    finally:
+        ctx.set_tuning(0, RSA_TUNE_RAGGED, reset=True)

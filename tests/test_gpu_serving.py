@@ -131,3 +131,20 @@ def test_serving_failure_paths(torch_cuda):
         assert (far_status == -6).all() and not far_out.any()
     finally:
         ctx.close()
+
+
+def test_serving_restart_returns_memory(torch_cuda):
+    """Stopping the loop gives its slots' buffers back to the context's budget,
+    so the loop can be started again in the same context."""
+    from paper_1407_1465_gb300 import RsaContext, build, rsa_server_start, rsa_server_stop
+    build.build()
+    ctx = RsaContext(0, mem_budget_bytes=3 << 30)
+    try:
+        base = ctx.stats()["bytes_resident"]
+        for _ in range(3):
+            rsa_server_start(ctx.handle, max_inflight_batches=4, batch_window_us=100, mem_budget_bytes=64 << 20)
+            assert ctx.stats()["bytes_resident"] > base
+            rsa_server_stop(ctx.handle)
+            assert ctx.stats()["bytes_resident"] == base
+    finally:
+        ctx.close()
