@@ -501,7 +501,7 @@ def run_ragged(args):
     return 0
 
 
-def serving_sweep(rates, duration, slots, window_us, key_bits=0):
+def serving_sweep(rates, duration, slots, window_us, key_bits=0, mix_sizes=False):
     """The request loop under Poisson arrivals over the 256 ragged keys (1-64
     messages per request, 70% CRT / 30% public, 2 GiB budget for in-flight
     requests), one pass per rate; returns a result dict per rate."""
@@ -518,7 +518,8 @@ def serving_sweep(rates, duration, slots, window_us, key_bits=0):
     pools = [workloads.messages_below(k.n, 64, 9, ("pool", i)) for i, k in enumerate(rb_keys)]
     scratch = [np.zeros_like(p) for p in pools]
     results = []
-    rsa_server_start(ctx.handle, max_inflight_batches=slots, batch_window_us=window_us, mem_budget_bytes=2 << 30)
+    rsa_server_start(ctx.handle, max_inflight_batches=slots, batch_window_us=window_us, mem_budget_bytes=2 << 30,
+                     mix_sizes=mix_sizes)
     for i in range(64):   # warm-up: graphs and workspaces of every slot
         k = i % len(kids)
         rsa_server_submit(ctx.handle, kids[k], 1, pools[k][:8], scratch[k][:8])
@@ -552,7 +553,7 @@ def run_serving(args):
     in-flight requests; p50/p99 request latency (arrival -> result in the host
     buffer) against sustained operations per second."""
     rates = [float(r) for r in args.rates.split(",")]
-    results = serving_sweep(rates, args.duration, args.slots, args.window_us, args.key_bits)
+    results = serving_sweep(rates, args.duration, args.slots, args.window_us, args.key_bits, args.mix_sizes)
     best = max(results, key=lambda r: r["sustained_ops_per_s"] or 0)
     line = {"metric": "serving: sustained ops/sec and p50/p99 request latency (Poisson arrivals)",
             "value": best["sustained_ops_per_s"], "unit": "ops/s", "n_gpus": 1, "higher_is_better": True,
@@ -561,7 +562,8 @@ def run_serving(args):
                                    "%.1f s of arrivals per rate" % args.duration, "rates": rates,
                        "batch_window_us": args.window_us, "slots": args.slots,
                        "key_bits": args.key_bits or "all",
-                       "batching": "one modulus size per batch (the oldest waiting request picks it)"},
+                       "batching": ("every modulus size in one batch" if args.mix_sizes else
+                                    "one modulus size per batch (the oldest waiting request picks it)")},
             "sweep": results}
     print(json.dumps(line), flush=True)
     return 0
@@ -645,6 +647,7 @@ def main():
     ap.add_argument("--workload", default="rsa2048", choices=sorted(WORKLOADS) + ["ragged", "serving", "toy", "mr", "bgcd"])
     ap.add_argument("--slots", type=int, default=16, help="serving: batches in flight at once")
     ap.add_argument("--key-bits", type=int, default=0, help="serving: only requests under keys of this size")
+    ap.add_argument("--mix-sizes", action="store_true", help="serving: batches take every modulus size")
     ap.add_argument("--e-bits", type=int, default=0,
                     help="--kind public: a seeded random public exponent of this many bits instead of 65537")
     ap.add_argument("--kind", default="crt", choices=["crt", "public"],

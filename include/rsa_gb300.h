@@ -240,9 +240,11 @@ typedef struct rsa_server_cfg {
     int32_t max_inflight_batches; /* concurrent batches (streams); 0 -> 16 */
     int32_t batch_window_us;      /* wait this long after the first arrival for more; 0 -> 200 */
     int32_t max_batch_ops;        /* operations per batch; 0 -> 65536 */
-    int32_t reserved;
+    int32_t flags;                /* RSA_SERVER_MIX_SIZES: a batch takes requests of every
+                                     modulus size (default: one size per batch, see above) */
     uint64_t mem_budget_bytes;    /* device bytes for in-flight requests; 0 -> 2 GiB */
 } rsa_server_cfg;
+#define RSA_SERVER_MIX_SIZES 1
 
 typedef struct rsa_request {
     int32_t key_id;

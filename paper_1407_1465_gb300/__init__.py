@@ -264,8 +264,9 @@ def rsa_imad_probe(device: int = 0) -> tuple[float, float]:
 # ------------------------------------------------------------------ serving
 
 def rsa_server_start(ctx: int, max_inflight_batches: int = 0, batch_window_us: int = 0, max_batch_ops: int = 0,
-                     mem_budget_bytes: int = 0) -> None:
-    cfg = _lib.rsa_server_cfg(max_inflight_batches, batch_window_us, max_batch_ops, 0, mem_budget_bytes)
+                     mem_budget_bytes: int = 0, mix_sizes: bool = False) -> None:
+    flags = _lib.RSA_SERVER_MIX_SIZES if mix_sizes else 0
+    cfg = _lib.rsa_server_cfg(max_inflight_batches, batch_window_us, max_batch_ops, flags, mem_budget_bytes)
     check(_lib.lib().rsa_server_start(ctx, ctypes.byref(cfg)))
 
 

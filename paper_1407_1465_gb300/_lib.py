@@ -51,8 +51,11 @@ class rsa_stats(ctypes.Structure):
 
 class rsa_server_cfg(ctypes.Structure):
     _fields_ = [("max_inflight_batches", ctypes.c_int32), ("batch_window_us", ctypes.c_int32),
-                ("max_batch_ops", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("max_batch_ops", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("mem_budget_bytes", ctypes.c_uint64)]
+
+
+RSA_SERVER_MIX_SIZES = 1
 
 
 class rsa_request(ctypes.Structure):

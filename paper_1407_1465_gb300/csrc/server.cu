@@ -311,12 +311,13 @@ void Server::loop() {
       const uint64_t window = (uint64_t)cfg.batch_window_us * 1000ull;
       const uint64_t first = queue.front()->arrive;
       const uint32_t cls = queue.front()->L;
+      const bool mixed = (cfg.flags & RSA_SERVER_MIX_SIZES) != 0;
       uint32_t ops = 0;
       uint64_t limbs = 0;
       bool full = false;
       for (Req *r : queue) {
         if (r->arrive > t) break;
-        if (r->L != cls) continue;
+        if (!mixed && r->L != cls) continue;
         const uint64_t l = (limbs + 3) / 4 * 4 + (uint64_t)r->count * r->L;
         if (ops + r->count > free_slot->cap_ops || l > free_slot->cap_limbs) {
           full = true;
@@ -332,7 +333,7 @@ void Server::loop() {
         for (size_t qi = 0; qi < queue.size();) {
           Req *r = queue[qi];
           if (r->arrive > t) break;
-          if (r->L != cls) {
+          if (!mixed && r->L != cls) {
             ++qi;
             continue;
           }

@@ -28,7 +28,10 @@ def torch_cuda():
     return torch
 
 
-def test_serving_mixed_arrivals(torch_cuda):
+@pytest.mark.parametrize("mix_sizes", [False, True])
+def test_serving_mixed_arrivals(torch_cuda, mix_sizes):
+    """One modulus size per batch (the default) and batches that take every size
+    (RSA_SERVER_MIX_SIZES) give the same, exact results."""
     from paper_1407_1465_gb300 import (RsaContext, RsaError, build, rsa_server_drain, rsa_server_get_stats,
                                        rsa_server_poll, rsa_server_start, rsa_server_stop, rsa_server_submit)
     build.build()
@@ -36,7 +39,8 @@ def test_serving_mixed_arrivals(torch_cuda):
     ctx = RsaContext(0, mem_budget_bytes=8 << 30)
     try:
         kids = [ctx.keyload(k.bits, k.n, k.e, k.d, k.p, k.q) for k in keys]
-        rsa_server_start(ctx.handle, max_inflight_batches=3, batch_window_us=300, mem_budget_bytes=64 << 20)
+        rsa_server_start(ctx.handle, max_inflight_batches=3, batch_window_us=300, mem_budget_bytes=64 << 20,
+                         mix_sizes=mix_sizes)
         st = workloads.Stream(workloads.stream_key(3, "serve"))
         reqs = []
         for r in range(90):
