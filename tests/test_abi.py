@@ -155,3 +155,25 @@ def test_tuning_dict_has_every_field():
     src = inspect.getsource(pkg.rsa_get_tuning) + inspect.getsource(pkg.rsa_autotune)
     for name, _ in _lib.rsa_tuning._fields_:
         assert src.count('"%s"' % name) >= 2, name
+
+
+def test_null_context_is_an_argument_error(lib):
+    """Every entry point that takes a context refuses a null one with
+    RSA_ERR_ARG before touching a device (host-side validation)."""
+    import ctypes
+    u64 = ctypes.c_uint64(0)
+    calls = {
+        "rsa_batch_gcd": lambda: lib.rsa_batch_gcd(None, 2048, 4, None, None, None, None),
+        "rsa_batch_gcd_plan": lambda: lib.rsa_batch_gcd_plan(None, 2048, 4, None, None),
+        "rsa_mr_batch": lambda: lib.rsa_mr_batch(None, 1024, 4, None, 1, None, None, None),
+        "rsa_autotune_batch": lambda: lib.rsa_autotune_batch(None, 4, None, None, None, None, None, None, None),
+        "rsa_modexp_batch": lambda: lib.rsa_modexp_batch(None, 4, None, None, None, None, None, None, None),
+        "rsa_sign_key": lambda: lib.rsa_sign_key(None, 0, 4, None, None, None, None),
+        "rsa_verify_key": lambda: lib.rsa_verify_key(None, 0, 4, None, None, None, None),
+        "rsa_server_clock": lambda: lib.rsa_server_clock(None, ctypes.byref(u64)),
+        "rsa_server_drain": lambda: lib.rsa_server_drain(None, 10),
+        "rsa_server_stop": lambda: lib.rsa_server_stop(None),
+    }
+    for name, call in calls.items():
+        assert call() == -1, name
+
