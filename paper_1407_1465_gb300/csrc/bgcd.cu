@@ -7,11 +7,13 @@
 // modulo an odd n, it is enough to know prod_{j != i} n_j * R^(-e) mod n_i for
 // some e, which Montgomery arithmetic gives without corrections.
 //
-// With schoolbook word arithmetic a product / remainder tree does no fewer word
-// products than working modulus by modulus, so each thread owns one modulus n_i
-// and runs over all the others:
+// With schoolbook word arithmetic a product / remainder tree does more word
+// products (its divisions alone about 4 L^2 k^2 for k moduli of L words) than
+// working modulus by modulus (about L^2 k^2 here), so each thread owns one
+// modulus n_i and runs over all the others:
 //   * block products: a first kernel multiplies the moduli together in blocks
-//     of B (8, 16 or 32) as plain integers of B*L words;
+//     of B (8, 16 or 32) as plain integers of B*L words, one warp per block
+//     (a product tree whose levels split each product over lanes);
 //   * for a block that does not hold n_i the thread reduces the block product
 //     word by word: q = t_0 n' mod 2^32, t = (t + q n_i) / 2^32, then the next
 //     word of the block product enters at the top.  After all M words the
