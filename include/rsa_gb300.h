@@ -173,6 +173,12 @@ int rsa_mr_batch(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *c
  * RSA_ERR_NOMEM, RSA_ERR_CUDA. */
 int rsa_batch_gcd(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *moduli, uint32_t *gcds,
                   int32_t *flags, void *stream);
+/* rsa_batch_gcd with host buffers: moduli, gcds (or NULL) and flags (or NULL)
+ * are host pointers (pinned memory copies fastest); the copies in and out run
+ * on `stream`, and the call returns when the results are in host memory.
+ * Device buffers come from the context's workspace.  Errors as rsa_batch_gcd. */
+int rsa_batch_gcd_host(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *moduli, uint32_t *gcds,
+                       int32_t *flags, void *stream);
 /* The work split rsa_batch_gcd would use for `count` moduli: the block size
  * of its block products (moduli multiplied together before the per-modulus
  * reduction) and the number of parts the moduli range is cut into for load

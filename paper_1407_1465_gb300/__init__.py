@@ -25,7 +25,7 @@ __all__ = [
     "rsa_ctx_create", "rsa_ctx_destroy", "rsa_keyload", "rsa_key_record", "rsa_tc_operand_image",
     "rsa_keyunload", "rsa_key_info",
     "rsa_modexp_key", "rsa_modexp_batch", "rsa_modexp_key_host", "rsa_modexp_batch_host",
-    "rsa_sign_key", "rsa_verify_key", "rsa_mr_batch", "rsa_batch_gcd", "rsa_batch_gcd_plan",
+    "rsa_sign_key", "rsa_verify_key", "rsa_mr_batch", "rsa_batch_gcd", "rsa_batch_gcd_host", "rsa_batch_gcd_plan",
     "rsa_sync", "rsa_last_error", "rsa_set_tuning", "rsa_get_tuning", "rsa_get_stats",
     "rsa_products_per_op", "rsa_imad_probe", "rsa_crt_decrypt_noalloc", "rsa_autotune", "rsa_autotune_batch",
     "rsa_server_start", "rsa_server_submit", "rsa_server_submit_many", "rsa_server_clock", "rsa_server_poll", "rsa_server_drain", "rsa_server_get_stats",
@@ -163,6 +163,11 @@ def rsa_mr_batch(ctx: int, nbits: int, count: int, cands, rounds: int, bases, ve
 
 def rsa_batch_gcd(ctx: int, nbits: int, count: int, moduli, gcds, flags, stream=None) -> None:
     check(_lib.lib().rsa_batch_gcd(ctx, nbits, count, _ptr(moduli), _ptr(gcds), _ptr(flags), _stream_ptr(stream)))
+
+
+def rsa_batch_gcd_host(ctx: int, nbits: int, count: int, moduli: np.ndarray, gcds, flags, stream=None) -> None:
+    check(_lib.lib().rsa_batch_gcd_host(ctx, nbits, count, _ptr(moduli), _ptr(gcds), _ptr(flags),
+                                        _stream_ptr(stream)))
 
 
 def rsa_batch_gcd_plan(ctx: int, nbits: int, count: int) -> tuple[int, int]:

@@ -89,6 +89,7 @@ SIGNATURES = [
     ("rsa_sign_key", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P]),
     ("rsa_mr_batch", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, ctypes.c_uint32, _P, _P, _P]),
     ("rsa_batch_gcd", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, _P, _P, _P]),
+    ("rsa_batch_gcd_host", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, _P, _P, _P]),
     ("rsa_batch_gcd_plan", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, _P]),
     ("rsa_verify_key", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P]),
     ("rsa_modexp_key_host", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P]),

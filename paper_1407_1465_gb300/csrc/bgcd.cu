@@ -725,18 +725,15 @@ int gcd_check(rsa_ctx *ctx, uint32_t nbits, uint64_t count) {
 }  // namespace
 }  // namespace rsagpu
 
-extern "C" int rsa_batch_gcd(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *moduli, uint32_t *gcds,
-                             int32_t *flags, void *stream) {
-  int rc = gcd_check(ctx, nbits, count);
-  if (rc) return rc;
-  if (count == 0) return RSA_OK;
-  if (!moduli || (!gcds && !flags)) return set_error(RSA_ERR_ARG, "null pointer");
-  if ((reinterpret_cast<uintptr_t>(moduli) | reinterpret_cast<uintptr_t>(gcds)) & 15u)
-    return set_error(RSA_ERR_ARG, "modulus and gcd rows must be 16-byte aligned");
-  Ctx *c = reinterpret_cast<Ctx *>(ctx);
-  std::lock_guard<std::mutex> lock(c->mu);
+namespace rsagpu {
+namespace {
+
+// The launches of one scan on stream s: block products, reductions, the
+// combine tree (one launch per level), gcd.  Context lock held.
+int batch_gcd_run(Ctx *c, uint32_t nbits, uint64_t count, const uint32_t *moduli, uint32_t *gcds, int32_t *flags,
+                  cudaStream_t s) {
+  int rc;
   cudaSetDevice(c->device);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   Workspace &w = c->ws(s);
   NvtxRange range("rsa_batch_gcd");
   GcdPlan pl;
@@ -763,6 +760,51 @@ extern "C" int rsa_batch_gcd(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const
   if (e != cudaSuccess) return cuda_error(e, "launch bgcd kernels");
   c->stats.kernel_launches += (uint64_t)launches;
   c->stats.ops += count;
+  return RSA_OK;
+}
+
+}  // namespace
+}  // namespace rsagpu
+
+extern "C" int rsa_batch_gcd(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *moduli, uint32_t *gcds,
+                             int32_t *flags, void *stream) {
+  int rc = gcd_check(ctx, nbits, count);
+  if (rc) return rc;
+  if (count == 0) return RSA_OK;
+  if (!moduli || (!gcds && !flags)) return set_error(RSA_ERR_ARG, "null pointer");
+  if ((reinterpret_cast<uintptr_t>(moduli) | reinterpret_cast<uintptr_t>(gcds)) & 15u)
+    return set_error(RSA_ERR_ARG, "modulus and gcd rows must be 16-byte aligned");
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  std::lock_guard<std::mutex> lock(c->mu);
+  return batch_gcd_run(c, nbits, count, moduli, gcds, flags, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int rsa_batch_gcd_host(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *moduli,
+                                  uint32_t *gcds, int32_t *flags, void *stream) {
+  int rc = gcd_check(ctx, nbits, count);
+  if (rc) return rc;
+  if (count == 0) return RSA_OK;
+  if (!moduli || (!gcds && !flags)) return set_error(RSA_ERR_ARG, "null pointer");
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  std::lock_guard<std::mutex> lock(c->mu);
+  cudaSetDevice(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Workspace &w = c->ws(s);
+  const size_t bytes = (size_t)count * (nbits / 32) * 4;
+  if ((rc = c->ensure(w.io_in, bytes)) || (gcds && (rc = c->ensure(w.io_out, bytes))) ||
+      (flags && (rc = c->ensure(w.io_status, (size_t)count * 4))))
+    return rc;
+  cudaError_t e = cudaMemcpyAsync(w.io_in.ptr, moduli, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync H2D");
+  uint32_t *dg = gcds ? static_cast<uint32_t *>(w.io_out.ptr) : nullptr;
+  int32_t *df = flags ? static_cast<int32_t *>(w.io_status.ptr) : nullptr;
+  if ((rc = batch_gcd_run(c, nbits, count, static_cast<const uint32_t *>(w.io_in.ptr), dg, df, s))) return rc;
+  if (gcds && (e = cudaMemcpyAsync(gcds, dg, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_error(e, "cudaMemcpyAsync D2H gcds");
+  if (flags && (e = cudaMemcpyAsync(flags, df, (size_t)count * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_error(e, "cudaMemcpyAsync D2H flags");
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
   return RSA_OK;
 }
 

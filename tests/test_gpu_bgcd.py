@@ -152,3 +152,20 @@ def test_bgcd_full_weak_key_workload(torch_cuda, ctx):
                  | {pairs[0][0], pairs[0][1]})
     og, of = oracle.batch_gcd(rows, rows=idx)
     assert np.array_equal(g[idx], og) and np.array_equal(f[idx], of)
+
+
+def test_bgcd_host_buffers(torch_cuda, ctx):
+    """rsa_batch_gcd_host: host moduli in, host gcds and flags out, equal to the
+    device form and to the oracle; either output may be left out."""
+    from paper_1407_1465_gb300 import rsa_batch_gcd_host
+    rows = _random_odd(333, 1024, 21)
+    g = np.zeros_like(rows)
+    f = np.zeros(rows.shape[0], dtype=np.int32)
+    rsa_batch_gcd_host(ctx.handle, 1024, rows.shape[0], rows, g, f)
+    og, of = oracle.batch_gcd(rows)
+    assert np.array_equal(g, og) and np.array_equal(f, of)
+    f2 = np.full(rows.shape[0], 99, dtype=np.int32)
+    rsa_batch_gcd_host(ctx.handle, 1024, rows.shape[0], rows, None, f2)
+    assert np.array_equal(f2, of)
+    dg, df = gpu_gcd(torch_cuda, ctx, 1024, rows)
+    assert np.array_equal(dg, g) and np.array_equal(df, f)
