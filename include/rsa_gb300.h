@@ -142,7 +142,7 @@ int rsa_verify_key(rsa_ctx *ctx, int32_t key_id, uint64_t count, const uint32_t 
 
 /* Batch Miller-Rabin probable-prime tests, the step before key generation
  * (Fig. 1 asks for two large primes; the paper names no test).  Candidate i is
- * the odd integer n_i of nbits/32 limbs at cands + i*L (nbits 512 or 1024; the
+ * the odd integer n_i of nbits/32 limbs at cands + i*L (nbits 512, 1024 or 2048; the
  * top bit need not be set); its `rounds` bases are the rows
  * bases + (i*rounds + r)*L, each in [2, n_i - 2] (drawn by the caller).
  * Writing n_i - 1 = d 2^s with d odd, base a passes when a^d = 1 or

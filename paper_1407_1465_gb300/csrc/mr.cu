@@ -107,7 +107,8 @@ __global__ void __launch_bounds__(kMrThreads) mr_kernel(MrArgs a) {
   uint4 *r2_lane = table_lane + ((size_t)1 << W) * (L / 4) * 32;
   uint4 *one_lane = r2_lane + Sm::kStageU4, *m1_lane = r2_lane + 2 * Sm::kStageU4, *d_lane = r2_lane + 3 * Sm::kStageU4;
   const uint32_t ntiles = (a.count + 31) / 32;
-  constexpr int kSqToR2 = (L == 16) ? 3 : 4;    // log2(L / 2)
+  constexpr int kSqToR2 = (L == 16) ? 3 : (L == 32) ? 4 : 5;    // log2(L / 2)
+  static_assert(L == 16 || L == 32 || L == 64, "candidate sizes");
   constexpr int kNwin = (32 * L + W - 1) / W;
 #pragma unroll 1
   for (uint32_t tile = blockIdx.x * nw + warp; tile < ntiles; tile += gridDim.x * nw) {
@@ -239,7 +240,8 @@ using namespace rsagpu;
 extern "C" int rsa_mr_batch(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *cands, uint32_t rounds,
                             const uint32_t *bases, int32_t *verdicts, void *stream) {
   if (!ctx) return set_error(RSA_ERR_ARG, "ctx is null");
-  if (nbits != 512 && nbits != 1024) return set_error(RSA_ERR_UNSUPPORTED, "candidates of 512 or 1024 bits");
+  if (nbits != 512 && nbits != 1024 && nbits != 2048)
+    return set_error(RSA_ERR_UNSUPPORTED, "candidates of 512, 1024 or 2048 bits");
   if (count == 0) return RSA_OK;
   if (!cands || !verdicts || (rounds > 0 && !bases)) return set_error(RSA_ERR_ARG, "null pointer");
   if (count > 0x7fffffffull || rounds > 256) return set_error(RSA_ERR_ARG, "count or rounds out of range");
@@ -255,14 +257,15 @@ extern "C" int rsa_mr_batch(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const 
   const uint64_t warps_needed = (count + 31) / 32;
   const int per_cta = kMrThreads / 32;
   const int grid = (int)std::max<uint64_t>(
-      1, std::min<uint64_t>((warps_needed + per_cta - 1) / per_cta, (uint64_t)c->sm_count * 4));
-  const size_t per_warp_u4 = (L == 16) ? MrSmem<16>::global_u4_per_warp<kMrWindow>()
-                                       : MrSmem<32>::global_u4_per_warp<kMrWindow>();
+      1, std::min<uint64_t>((warps_needed + per_cta - 1) / per_cta, (uint64_t)c->sm_count * (L == 64 ? 2 : 4)));
+  const size_t per_warp_u4 = (L == 16)   ? MrSmem<16>::global_u4_per_warp<kMrWindow>()
+                             : (L == 32) ? MrSmem<32>::global_u4_per_warp<kMrWindow>()
+                                         : MrSmem<64>::global_u4_per_warp<kMrWindow>();
   const size_t tbytes = (size_t)grid * per_cta * per_warp_u4 * 16;
   int rc = c->ensure(w.tables, tbytes);
   if (rc) return rc;
   MrArgs h{cands, bases, verdicts, static_cast<uint4 *>(w.tables.ptr), (uint32_t)count, rounds};
-  cudaError_t e = (L == 16) ? launch_mr<16>(h, grid, s) : launch_mr<32>(h, grid, s);
+  cudaError_t e = (L == 16) ? launch_mr<16>(h, grid, s) : (L == 32) ? launch_mr<32>(h, grid, s) : launch_mr<64>(h, grid, s);
   if (e != cudaSuccess) return cuda_error(e, "launch mr_kernel");
   c->stats.kernel_launches++;
   c->stats.ops += count;

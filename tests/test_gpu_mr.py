@@ -1,6 +1,6 @@
 """GPU: batch Miller-Rabin (key generation) against the oracle's Miller-Rabin.
 
-Candidates at 512 and 1024 bits: primes from seeded key generation, products of
+Candidates at 512, 1024 and 2048 bits (the last: RSA-4096 key generation): primes from seeded key generation, products of
 two primes (RSA moduli of the half size), squares of primes, seeded random odd
 numbers (almost all composite), Mersenne numbers below the size (2^127 - 1 and
 2^521 - 1 prime, 2^67 - 1 composite but a strong probable prime to base 2),
@@ -46,11 +46,13 @@ def _candidates(bits):
     cands += [(1 << 127) - 1, (1 << 67) - 1, 2047, 561, 1729, 8911]
     if bits >= 1024:
         cands.append((1 << 521) - 1)
+    if bits >= 2048:
+        cands.append((1 << 1279) - 1)               # a Mersenne prime
     cands += [10, 3, 1 << 40]                        # invalid: even or below 5
     return cands
 
 
-@pytest.mark.parametrize("bits", [512, 1024])
+@pytest.mark.parametrize("bits", [512, 1024, 2048])
 def test_mr_batch_matches_oracle(torch_cuda, ctx, bits):
     L = bits // 32
     cands = _candidates(bits)
