@@ -152,3 +152,52 @@ def test_serving_restart_returns_memory(torch_cuda):
             assert ctx.stats()["bytes_resident"] == base
     finally:
         ctx.close()
+
+
+def test_serving_concurrent_submitters(torch_cuda):
+    """Four host threads submit at once (the binding releases the GIL, so the
+    submits overlap); every request completes with the oracle's result."""
+    from paper_1407_1465_gb300 import (RsaContext, build, rsa_server_drain, rsa_server_poll, rsa_server_start,
+                                       rsa_server_stop, rsa_server_submit)
+    build.build()
+    keys = workloads.gen_keys([(1024, 0), (2048, 0)], workloads.DEFAULT_SEED)
+    ctx = RsaContext(0, mem_budget_bytes=4 << 30)
+    try:
+        kids = [ctx.keyload(k.bits, k.n, k.e, k.d, k.p, k.q) for k in keys]
+        rsa_server_start(ctx.handle, max_inflight_batches=4, batch_window_us=100, mem_budget_bytes=64 << 20)
+        done = [[] for _ in range(4)]
+        errors = []
+
+        def submitter(tid):
+            try:
+                for r in range(25):
+                    k = (tid + r) % 2
+                    kind = CRT if r % 3 else PUB
+                    msgs = workloads.messages_below(keys[k].n, 1 + (r * 7 + tid) % 20, tid, ("conc", r))
+                    out = np.zeros_like(msgs)
+                    t = rsa_server_submit(ctx.handle, kids[k], kind, msgs, out)
+                    done[tid].append((t, k, kind, msgs, out))
+            except Exception as exc:   # reported below, not swallowed
+                errors.append(exc)
+
+        threads = [threading.Thread(target=submitter, args=(i,)) for i in range(4)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        assert not errors
+        rsa_server_drain(ctx.handle, timeout_ms=120000)
+        tickets = set()
+        for lst in done:
+            for t, k, kind, msgs, out in lst:
+                assert t not in tickets
+                tickets.add(t)
+                assert rsa_server_poll(ctx.handle, t) == 1
+                key = keys[k]
+                want = (oracle.crt_batch(msgs, key.d, key.p, key.q) if kind == CRT
+                        else oracle.modexp_batch(msgs, key.e, key.n))
+                assert np.array_equal(out, want)
+        assert len(tickets) == 100
+        rsa_server_stop(ctx.handle)
+    finally:
+        ctx.close()
