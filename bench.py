@@ -226,8 +226,8 @@ def run_toy(args):
 
 
 def mr_issued_products(cands: np.ndarray, rounds: int, L: int = 32, W: int = 4) -> float:
-    """Word products of one rsa_mr_batch launch over 1024-bit candidates (one
-    thread per candidate, 32 per warp): per candidate 4 squarings for R^2 mod n,
+    """Word products of one rsa_mr_batch launch (one thread per candidate, 32
+    per warp): per candidate log2(L/2) squarings for R^2 mod n,
     then per round 1 (into Montgomery form) + 2^W - 2 table entries +
     (32L/W - 1)(W + 1) window steps + the warp's largest s - 1 squarings."""
     mm = 2 * L * L + L
@@ -242,26 +242,30 @@ def mr_issued_products(cands: np.ndarray, rounds: int, L: int = 32, W: int = 4) 
     s_pad = np.concatenate([s, np.full(warps * 32 - count, s[-1] if count else 0)]).reshape(warps, 32)
     sq_tail = np.maximum(s_pad.max(axis=1) - 1, 0).sum() * 32
     per_round = 1 + (2 ** W - 2) + (32 * L // W - 1) * (W + 1)
-    return float(mm) * (4 * warps * 32 + rounds * (per_round * warps * 32 + sq_tail))
+    sq_to_r2 = {16: 3, 32: 4, 64: 5}[L]
+    return float(mm) * (sq_to_r2 * warps * 32 + rounds * (per_round * warps * 32 + sq_tail))
 
 
 def run_mr(args):
     """Key generation's primality step: one Miller-Rabin round per seeded odd
-    1024-bit candidate (top bit set, bases in [2, n/2)), 65536 candidates per
-    step, all device-resident; a sample of verdicts is checked against the
-    oracle.  Reported as rounds/s."""
+    candidate of --mr-bits bits (1024 default, the primes of RSA-2048; 2048 for
+    RSA-4096; top bit set, bases in [2, n/2)), 65536 candidates per step, all
+    device-resident; a sample of verdicts is checked against the oracle.
+    Reported as rounds/s."""
     import torch
     from paper_1407_1465_gb300 import RsaContext, build
     build.build()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     count = args.count or 65536
-    rng = np.random.default_rng(workloads.DEFAULT_SEED + 1024)
-    cands = rng.integers(0, 1 << 32, size=(count, 32), dtype=np.uint64).astype(np.uint32)
+    bits = args.mr_bits
+    L = bits // 32
+    rng = np.random.default_rng(workloads.DEFAULT_SEED + bits)
+    cands = rng.integers(0, 1 << 32, size=(count, L), dtype=np.uint64).astype(np.uint32)
     cands[:, 0] |= 1
-    cands[:, 31] |= 0x80000000
-    bases = rng.integers(0, 1 << 32, size=(count, 1, 32), dtype=np.uint64).astype(np.uint32)
-    bases[:, 0, 31] &= 0x3FFFFFFF
+    cands[:, L - 1] |= 0x80000000
+    bases = rng.integers(0, 1 << 32, size=(count, 1, L), dtype=np.uint64).astype(np.uint32)
+    bases[:, 0, L - 1] &= 0x3FFFFFFF
     bases[:, 0, 0] |= 2
     ctx = RsaContext(0, mem_budget_bytes=4 << 30)
     c = torch.from_numpy(cands.view(np.int32)).to(dev)
@@ -269,12 +273,12 @@ def run_mr(args):
     v = torch.empty(count, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
     for _ in range(max(args.warmup, 1)):
-        ctx.miller_rabin(1024, c, b, v, stream.cuda_stream)
+        ctx.miller_rabin(bits, c, b, v, stream.cuda_stream)
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     ev[0].record(stream)
     for _ in range(args.steps):
-        ctx.miller_rabin(1024, c, b, v, stream.cuda_stream)
+        ctx.miller_rabin(bits, c, b, v, stream.cuda_stream)
     ev[1].record(stream)
     torch.cuda.synchronize()
     ms = ev[0].elapsed_time(ev[1]) / args.steps
@@ -285,19 +289,19 @@ def run_mr(args):
                                 workloads.rows_to_ints(bases[i, :, :])) for i in idx]
     if list(got[idx]) != want:
         raise RuntimeError("Miller-Rabin verdicts differ from the oracle")
-    issued = mr_issued_products(cands, rounds=1)
+    issued = mr_issued_products(cands, rounds=1, L=L)
     achieved = issued / (ms / 1e3) / 1e12
     peak = derived_peak_tprod(SM_COUNT_GB300, 2070.0)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tprod/s", "frac": achieved / peak,
                 "traffic": None, "issued_products_per_step": issued,
-                "note": "CIOS Montgomery products (2L^2 + L word products each) the kernel runs: R^2 by 4 squarings, "
-                        "to Montgomery form, 14 table entries, 255 windows x 5 steps, and each warp's largest s - 1 "
-                        "squarings; against the derived IMAD peak"}
-    line = {"metric": "Miller-Rabin rounds/sec (1024-bit candidates)", "value": count / (ms / 1e3),
+                "note": "CIOS Montgomery products (2L^2 + L word products each) the kernel runs: R^2 by log2(L/2) "
+                        "squarings, to Montgomery form, 14 table entries, 8L - 1 windows x 5 steps, and each warp's "
+                        "largest s - 1 squarings; against the derived IMAD peak"}
+    line = {"metric": "Miller-Rabin rounds/sec (%d-bit candidates)" % bits, "value": count / (ms / 1e3),
             "unit": "rounds/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "probable_primes_in_batch": int((got == 1).sum()), "roofline": roofline,
-            "config": {"workload": "%d seeded odd 1024-bit candidates, one base each, one launch per step" % count}}
+            "config": {"workload": "%d seeded odd %d-bit candidates, one base each, one launch per step" % (count, bits)}}
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0
@@ -648,6 +652,7 @@ def main():
     ap.add_argument("--slots", type=int, default=16, help="serving: batches in flight at once")
     ap.add_argument("--key-bits", type=int, default=0, help="serving: only requests under keys of this size")
     ap.add_argument("--mix-sizes", action="store_true", help="serving: batches take every modulus size")
+    ap.add_argument("--mr-bits", type=int, default=1024, choices=[512, 1024, 2048], help="mr: candidate size")
     ap.add_argument("--e-bits", type=int, default=0,
                     help="--kind public: a seeded random public exponent of this many bits instead of 65537")
     ap.add_argument("--kind", default="crt", choices=["crt", "public"],
