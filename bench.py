@@ -231,12 +231,17 @@ def mr_issued_products(cands: np.ndarray, rounds: int, L: int = 32, W: int = 4) 
     then per round 1 (into Montgomery form) + 2^W - 2 table entries +
     (32L/W - 1)(W + 1) window steps + the warp's largest s - 1 squarings."""
     mm = 2 * L * L + L
-    n1 = cands.astype(np.uint64)
-    # s = trailing zero bits of n - 1 (n odd): of the low limb (n - 1 has them there for these candidates)
-    low = (n1[:, 0] - 1) & np.uint64(0xFFFFFFFF)
-    s = np.zeros(len(cands), dtype=np.int64)
+    # s = trailing zero bits of n - 1 (n odd: n - 1 is n with bit 0 cleared), as
+    # the kernel finds it: the first nonzero limb, then its trailing zeros
+    m = cands.astype(np.uint64)
+    m[:, 0] &= np.uint64(0xFFFFFFFE)
+    nz = m != 0
+    first = np.where(nz.any(axis=1), nz.argmax(axis=1), L - 1)
+    word = m[np.arange(len(m)), first]
+    tz = np.zeros(len(m), dtype=np.int64)
     for b in range(32):
-        s += ((low & np.uint64((1 << (b + 1)) - 1)) == 0)
+        tz += ((word & np.uint64((1 << (b + 1)) - 1)) == 0) & (word != 0)
+    s = 32 * first.astype(np.int64) + tz
     count = len(cands)
     warps = -(-count // 32)
     s_pad = np.concatenate([s, np.full(warps * 32 - count, s[-1] if count else 0)]).reshape(warps, 32)

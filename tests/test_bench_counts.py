@@ -1,0 +1,81 @@
+"""The benchmark's roofline numerators, counted step by step.
+
+bench.py reports achieved word products per second from closed forms; here the
+same counts are re-derived by walking the kernels' loops (blocks, super-blocks,
+lanes, tree levels, window steps), so a slip in a closed form shows up.
+"""
+import numpy as np
+import pytest
+
+import bench
+
+
+def _bgcd_walk(count, L, blk, parts):
+    """Word products of one batch-GCD scan, loop by loop (count a multiple of 32)."""
+    mm = 2 * L * L + L
+    nblk = -(-count // blk)
+    total = 0
+    # block products: a product tree per block; level l multiplies blk / 2^l pairs of
+    # 2^(l-1) L-word numbers, each split over 2^(l-1) chunks of L words (s words x L words)
+    for _c in range(nblk):
+        lev, s = 1, L
+        while (1 << lev) <= blk:
+            lanes = blk // 2
+            total += lanes * s * L
+            lev += 1
+            s *= 2
+    nsb = -(-count // 32)
+    for i in range(count):
+        w = i // 32
+        for sb in range(nsb):
+            if sb == w:
+                members = min(count, 32 * sb + 32) - 32 * sb
+                total += (members - 1) * mm                       # CIOS per own modulus, j != i
+            else:
+                for c in range(sb * (32 // blk), min(nblk, (sb + 1) * (32 // blk))):
+                    members = min(count, (c + 1) * blk) - c * blk
+                    total += members * L * L                      # word reductions: L per word
+                    total += mm                                   # into the running product
+        total += (parts - 1) * mm                                 # the combine tree, per lane
+    return total
+
+
+@pytest.mark.parametrize("count,L,blk,parts", [(32, 16, 8, 1), (96, 16, 16, 3), (256, 32, 32, 5),
+                                               (640, 64, 16, 10)])
+def test_bgcd_issued_products_matches_loop_count(count, L, blk, parts):
+    assert bench.bgcd_issued_products(count, L, blk, parts) == _bgcd_walk(count, L, blk, parts)
+
+
+def _mr_walk(cands, rounds, L, W=4):
+    """Word products of one Miller-Rabin launch, per lane, from the kernel's loops."""
+    mm = 2 * L * L + L
+    count = cands.shape[0]
+    warps = -(-count // 32)
+    nwin = -(-(32 * L) // W)
+    total = 0
+    for wi in range(warps):
+        rows = [min(wi * 32 + ln, count - 1) for ln in range(32)]   # dead lanes repeat the last row
+        ss = []
+        for r in rows:
+            n = int.from_bytes(cands[r].astype("<u4").tobytes(), "little")
+            m = n - 1
+            ss.append((m & -m).bit_length() - 1)
+        s_max = max(ss)
+        for _ in range(32):
+            total += {16: 3, 32: 4, 64: 5}[L] * mm              # R^2 by squarings
+            for _r in range(rounds):
+                total += mm                                      # into Montgomery form
+                total += (2 ** W - 2) * mm                       # table entries 2 .. 2^W - 1
+                total += (nwin - 1) * (W + 1) * mm               # W squarings + 1 product per window
+                total += max(s_max - 1, 0) * mm                  # the n - 1 search
+    return total
+
+
+@pytest.mark.parametrize("L", [16, 32])
+def test_mr_issued_products_matches_loop_count(L):
+    rng = np.random.default_rng(L)
+    cands = rng.integers(0, 1 << 32, size=(77, L), dtype=np.uint64).astype(np.uint32)
+    cands[:, 0] |= 1
+    cands[5, 0] = 0x00000001                                     # n - 1 with many trailing zeros
+    cands[5, 1] = 0x80000000
+    assert bench.mr_issued_products(cands, 1, L=L) == _mr_walk(cands, 1, L)
