@@ -79,3 +79,37 @@ def test_mr_issued_products_matches_loop_count(L):
     cands[5, 0] = 0x00000001                                     # n - 1 with many trailing zeros
     cands[5, 1] = 0x80000000
     assert bench.mr_issued_products(cands, 1, L=L) == _mr_walk(cands, 1, L)
+
+
+def _tc_walk(bits, W):
+    """CUDA-core word products and tensor FLOPs of one RSA-2048 CRT decryption on
+    the tensor-core path, replaying the kernel's step loop: per half, steps 0-1
+    bring c_lo, c_hi into Montgomery form, steps 2 .. 2^W - 1 build the table
+    (step 2 squares), then each window is W squarings and one product by the
+    selected entry; the q half adds one product leaving Montgomery form; then
+    Garner (two CIOS products and one H x H product)."""
+    H = bits // 64
+    nwin = -(-(32 * H) // W)
+    ntab = 1 << W
+    nexp = (nwin - 1) * (W + 1)
+    prods = flops = 0
+    for pi in (0, 1):
+        s = 0
+        for st in range(ntab + nexp + (1 if pi == 0 else 0)):
+            sq = False
+            if 2 <= st < ntab:
+                sq = st == 2
+            elif ntab <= st < ntab + nexp:
+                if s < W:
+                    sq, s = True, s + 1
+                else:
+                    s = 0
+            prods += H * (H + 1) // 2 if sq else H * H
+            flops += 2 * (2 * 128 * (9 * 16))                # two MMAs, N = 128, K = 144, per row
+    prods += 2 * (2 * H * H + H) + H * H
+    return prods, flops
+
+
+@pytest.mark.parametrize("W", [3, 4])
+def test_tc_work_per_op_matches_the_step_loop(W):
+    assert bench.tc_work_per_op(2048, W) == _tc_walk(2048, W)
