@@ -420,6 +420,21 @@ class RsaContext:
         rsa_modexp_batch(self.handle, key_ids.numel(), key_ids, exp_sel, limb_offsets, msgs, out, status, stream)
         return out
 
+    def autotune(self, key_id: int, exp_sel: int, count: int, cache_path: str | None = None) -> dict:
+        """Tune rsa_modexp_key for this key's size and kind (installs the fastest shape)."""
+        return rsa_autotune(self.handle, key_id, exp_sel, count, cache_path)
+
+    def batch_gcd_host(self, nbits: int, moduli: np.ndarray, gcds: np.ndarray | None = None,
+                       flags: np.ndarray | None = None, stream=None):
+        """Host-buffer batch GCD: numpy rows in, (gcds, flags) numpy arrays out."""
+        moduli = np.ascontiguousarray(moduli, dtype=np.uint32)
+        if gcds is None:
+            gcds = np.empty_like(moduli)
+        if flags is None:
+            flags = np.empty(moduli.shape[0], dtype=np.int32)
+        rsa_batch_gcd_host(self.handle, nbits, moduli.shape[0], moduli, gcds, flags, stream)
+        return gcds, flags
+
     def autotune_batch(self, key_ids, exp_sel, limb_offsets, msgs, out=None) -> dict:
         """Tune rsa_modexp_batch on this batch (installs the fastest shapes)."""
         import torch
