@@ -169,3 +169,5 @@ def test_bgcd_host_buffers(torch_cuda, ctx):
     assert np.array_equal(f2, of)
     dg, df = gpu_gcd(torch_cuda, ctx, 1024, rows)
     assert np.array_equal(dg, g) and np.array_equal(df, f)
+    hg, hf = ctx.batch_gcd_host(1024, rows)                  # the context method
+    assert np.array_equal(hg, g) and np.array_equal(hf, f)
