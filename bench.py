@@ -50,7 +50,11 @@ PROFILED_TRAFFIC = {
     # (workload, variant): one ncu capture of that kernel, valid while its sources hash to the stamp
     ("rsa2048", 3): {"window": 3, "stamp": "4ac01f94619e9b34", "dram_bytes_per_op": 1167.4,
                      "files": ["crt_tc.cu", "crt_tc.h", "tc.cuh", "mont.cuh", "kernels.cuh", "keyrec.h"],
-                     "source": "profiles/crt_tc_half_kernel_rsa2048_w3_ncu_full.md"},
+                     "source": "profiles/crt_tc_half_kernel_rsa2048_w3_ncu_full.md",
+                     # what binds the kernel, from the same capture (percent of peak while active)
+                     "pipes": {"issue_active_pct": 52.6, "warps_active_pct": 25.0, "alu_pipe_pct": 50.9,
+                               "fma_pipe_pct": 34.2, "tensor_pipe_pct": 19.2,
+                               "top_stalls": ["wait", "math_pipe_throttle", "not_selected"]}},
     ("rsa2048", 1): {"window": 4, "stamp": "2c547aada0325644", "dram_bytes_per_op": 257607.0,
                      "files": ["kernels.cuh", "mont.cuh", "inst_unit.cuh", "inst_h32.cu", "keyrec.h"],
                      "source": "profiles/crt_kernel_rsa2048_w4_cios_ncu_full.md"},
@@ -67,14 +71,54 @@ def kernel_stamp(files) -> str:
     return h.hexdigest()[:16]
 
 
-SM_COUNT_GB300 = 152
 IMAD_PER_SM_CLK = 64        # 32-bit integer multiply(-add) results per SM per clock
 IMAD_PER_PRODUCT = 2        # a 32x32->64 word product = low half + high half
 
 
 def derived_peak_tprod(sm_count: int, sm_mhz: float) -> float:
-    """Word products per second (x1e12) the IMAD pipe allows at sm_mhz."""
+    """Word products per second (x1e12) the IMAD pipe would allow at sm_mhz if the
+    high-half multiply issued at the full rate (it issues at about half on GB300)."""
     return sm_count * IMAD_PER_SM_CLK * sm_mhz * 1e6 / IMAD_PER_PRODUCT / 1e12
+
+
+def sm_count_of(device: int) -> int:
+    import torch
+    return int(torch.cuda.get_device_properties(device).multi_processor_count)
+
+
+_PEAKS = {}
+
+
+def measured_imad_peak(device: int) -> dict:
+    """The IMAD roofline denominators measured on this GPU, in this run, by the
+    library's probe kernels (rsa_imad_probe, best of three): 32-bit multiply-add
+    lane operations per second, and 32x32->64 word products per second of
+    mad.lo.cc / madc.hi.cc carry chains shaped like the Montgomery product (the
+    instruction form every CUDA-core kernel here issues).  Word-product
+    fractions are taken against the carry-chain figure."""
+    if device in _PEAKS:
+        return _PEAKS[device]
+    from paper_1407_1465_gb300 import rsa_imad_probe
+    lanes, chain = 0.0, 0.0
+    for _ in range(3):
+        a, b = rsa_imad_probe(device)
+        lanes, chain = max(lanes, a), max(chain, b)
+    sms = sm_count_of(device)
+    _PEAKS[device] = {"chain_tprod": chain / 1e12, "imad_lane_tops": lanes / 1e12, "sm_count": sms,
+                      "derived_tprod": derived_peak_tprod(sms, 2070.0)}
+    return _PEAKS[device]
+
+
+def alu_roofline(achieved: float, device: int, what: str) -> dict:
+    """A word-product roofline against the measured carry-chain peak."""
+    pk = measured_imad_peak(device)
+    return {"bound": "alu", "achieved": achieved, "peak": pk["chain_tprod"], "unit": "Tprod/s",
+            "frac": achieved / pk["chain_tprod"], "peak_source": "measured",
+            "peak_note": "rsa_imad_probe in this run on this GPU (%d SMs): carry-chain word products/s of the "
+                         "Montgomery-product shape (mad.lo.cc + madc.hi.cc); independent mad.lo/mad.hi lane-ops "
+                         "%.2f T/s; the unit-count figure %.2f T products/s assumes a full-rate high-half multiply"
+                         % (pk["sm_count"], pk["imad_lane_tops"], pk["derived_tprod"]),
+            "what": what}
 
 
 def tc_work_per_op(bits: int, window: int):
@@ -83,8 +127,14 @@ def tc_work_per_op(bits: int, window: int):
     products + (windows - 1) * (w + 1) window steps (+1 for q leaving Montgomery
     form); squarings issue H(H+1)/2 word products, other products H^2; every step
     runs two fp16 MMAs of 9 K-steps (M = 128 rows: 2 * 128 * 16 FLOPs per row
-    each); Garner adds two CIOS products and one H x H product."""
+    each); Garner adds two CIOS products and one H x H product.
+    Returns (issued word products, issued MMA FLOPs, method MMA FLOPs): the
+    method's share of the MMAs is the nonzero part of the two Toeplitz products
+    per step, without the bias block -- mu = T_lo * m' mod R needs the byte
+    products of columns 0..D-1 (D(D+1)/2 of them, D = 4H digits) and mu * m the
+    byte products of positions D-4 .. 2D-5 (what MMA 2 produces)."""
     H = bits // 64
+    D = 4 * H
     nwin = -(-32 * H // window)
     steps_half = (1 << window) + (nwin - 1) * (window + 1)
     squares_half = 1 + (nwin - 1) * window
@@ -92,7 +142,10 @@ def tc_work_per_op(bits: int, window: int):
     mults = steps - 2 * squares_half
     issued = 2 * squares_half * (H * (H + 1) // 2) + mults * H * H + 2 * (2 * H * H + H) + H * H
     tensor_flops = steps * 2 * 9 * 2 * 128 * 16
-    return issued, tensor_flops
+    mma1 = D * (D + 1) // 2
+    mma2 = sum(min(j, D - 1) - max(0, j - (D - 1)) + 1 for j in range(D - 4, 2 * D - 4))
+    method_flops = steps * 2 * (mma1 + mma2)
+    return issued, tensor_flops, method_flops
 
 
 def measured_bf16_tflops():
@@ -152,6 +205,29 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                name = line.split(":", 1)[1].strip()
+                vendor = next((l.split(":", 1)[1].strip() for l in out.splitlines()
+                               if l.lower().startswith("vendor id:")), "")
+                return (vendor + " " + name).strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(key, rows, target_s: float = 12.0, public: bool = False, e: int = 0) -> dict:
     """The oracle (as written) on every host core, on a bounded sample: its CRT
     routine for decryptions, its left-to-right binary method with e for encryptions."""
@@ -175,8 +251,9 @@ def cpu_baseline(key, rows, target_s: float = 12.0, public: bool = False, e: int
     what = ("left-to-right binary modexp with e" if public else "CRT routine") + \
         " (schoolbook multiply + Algorithm D + binary square-and-multiply)"
     return {"value": n / dt, "unit": "encryptions/s" if public else "decrypts/s", "cores": threads,
-            "kind": "oracle", "sample": "first %d of the %d messages, oracle %s, %d POSIX threads, %.1f s"
-                                        % (n, rows.shape[0], what, threads, dt)}
+            "cpu_model": cpu_model(), "kind": "oracle",
+            "sample": "first %d of the %d messages, oracle %s, %d POSIX threads, %.1f s"
+                      % (n, rows.shape[0], what, threads, dt)}
 
 
 def run_toy(args):
@@ -296,12 +373,10 @@ def run_mr(args):
         raise RuntimeError("Miller-Rabin verdicts differ from the oracle")
     issued = mr_issued_products(cands, rounds=1, L=L)
     achieved = issued / (ms / 1e3) / 1e12
-    peak = derived_peak_tprod(SM_COUNT_GB300, 2070.0)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tprod/s", "frac": achieved / peak,
-                "traffic": None, "issued_products_per_step": issued,
-                "note": "CIOS Montgomery products (2L^2 + L word products each) the kernel runs: R^2 by log2(L/2) "
-                        "squarings, to Montgomery form, 14 table entries, 8L - 1 windows x 5 steps, and each warp's "
-                        "largest s - 1 squarings; against the derived IMAD peak"}
+    roofline = alu_roofline(achieved, 0, "CIOS Montgomery products (2L^2 + L word products each) the kernel runs: "
+                                         "R^2 by log2(L/2) squarings, to Montgomery form, 14 table entries, 8L - 1 "
+                                         "windows x 5 steps, and each warp's largest s - 1 squarings")
+    roofline.update({"traffic": None, "issued_products_per_step": issued})
     line = {"metric": "Miller-Rabin rounds/sec (%d-bit candidates)" % bits, "value": count / (ms / 1e3),
             "unit": "rounds/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
@@ -370,14 +445,10 @@ def run_bgcd(args):
     blk, parts = rsa_batch_gcd_plan(ctx.handle, bits, count)
     issued = bgcd_issued_products(count, L, blk, parts)
     achieved = issued / (ms / 1e3) / 1e12
-    peak = derived_peak_tprod(SM_COUNT_GB300, 2070.0)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tprod/s", "frac": achieved / peak,
-                "traffic": None, "issued_products_per_step": issued,
-                "definitional_products_per_step": count * (count - 1) * (2 * L * L + L),
-                "note": "issued word products of the three kernels (word reductions cost L per word, half of a "
-                        "Montgomery multiplication) against the derived IMAD peak (152 SMs x 64 lanes x 2070 MHz / 2)"}
-    if clocks.get("sm_mhz"):
-        roofline["frac_at_measured_clock"] = achieved / derived_peak_tprod(SM_COUNT_GB300, clocks["sm_mhz"])
+    roofline = alu_roofline(achieved, 0, "issued word products of the three kernels (word reductions cost L per "
+                                         "word, half of a Montgomery multiplication)")
+    roofline.update({"traffic": None, "issued_products_per_step": issued,
+                     "definitional_products_per_step": count * (count - 1) * (2 * L * L + L)})
     e2e = None
     if not args.no_e2e:
         # through rsa_batch_gcd_host: pinned host moduli in, host flags out, copies timed
@@ -402,7 +473,8 @@ def run_bgcd(args):
         t0 = time.perf_counter()
         oracle.batch_gcd(rows, rows=sample, threads=threads)
         dt = time.perf_counter() - t0
-        cpu = {"value": len(sample) * (count - 1) / dt, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+        cpu = {"value": len(sample) * (count - 1) / dt, "unit": "pairs/s", "cores": threads,
+               "cpu_model": cpu_model(), "kind": "oracle",
                "sample": "%d of the %d moduli (each against all %d others), oracle product mod n_i and Euclid, "
                          "%d POSIX threads" % (len(sample), count, count - 1, threads)}
     line = {"metric": "batch GCD modulus pairs/sec (RSA-2048 weak-key scan)", "value": pairs_per_s,
@@ -502,8 +574,10 @@ def run_ragged(args):
         "one_key_per_launch": {"ms_per_step": res["loop"], "value": count / (res["loop"] / 1e3),
                                "launches": len(gbufs)},
         "speedup_vs_loop": res["loop"] / res["ragged"], "tuning": tuning or "automatic",
-        "roofline": {"bound": "alu", "achieved": prods / (res["ragged"] / 1e3) / 1e12, "unit": "Tprod/s",
-                     "products_per_step": prods},
+        "roofline": dict(alu_roofline(prods / (res["ragged"] / 1e3) / 1e12, 0,
+                                      "word products per second under the CIOS count 2L^2 + L per Montgomery "
+                                      "product of each operation's class (window 5 for private exponents)"),
+                         products_per_step=prods),
     }
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -638,7 +712,7 @@ def run_reference(args, spec):
         "data": "synthetic", "gpu_launches": 0,
         "config": {"workload": workload_desc(spec["bits"], spec["count"], args.kind),
                    "step": "%d %s per step (bounded sample)" % (per_step, items)},
-        "cpu_baseline": {"value": value, "unit": unit, "cores": threads, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": unit, "cores": threads, "cpu_model": cpu_model(), "kind": "oracle",
                          "sample": "%d %s per step, oracle %s, %d POSIX threads"
                                    % (per_step, items, routine, threads)},
         "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -799,36 +873,50 @@ def main():
         if not np.array_equal(h_out.numpy().view(np.uint32), out.cpu().numpy().view(np.uint32)):
             raise RuntimeError("e2e output differs from the device-resident run")
 
+    # Roofline of the dominant kernel.  The step is one rsa_modexp_key call; on the
+    # tensor-core path its exponentiation kernel is 99.5% of the step (the launch
+    # list in profiles/), so the step time stands in for that kernel's duration
+    # (a slight understatement of its rate).
     prods = rsa_products_per_op(spec["bits"], kind, e=e_pub, window=tune["window"])
-    achieved = prods * count / (ms / 1e3) / 1e12
-    peak = derived_peak_tprod(SM_COUNT_GB300, 2070.0)
+    cios_achieved = prods * count / (ms / 1e3) / 1e12
     prof = PROFILED_TRAFFIC.get((args.workload, tune["variant"])) if args.kind == "crt" else None
-    traffic = None
-    if (prof and prof["window"] == tune["window"] and tune["threads_per_op"] == 1
-            and prof["stamp"] == kernel_stamp(prof["files"])):
-        traffic = prof["dram_bytes_per_op"] * count
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tprod/s", "frac": achieved / peak,
-                "traffic": traffic, "traffic_unit": "DRAM bytes per launch",
-                "traffic_source": prof["source"] if traffic else None,
-                "algorithmic_io_bytes": count * L * 4 * 2,
-                "peak_note": "derived from unit counts and clock: 152 SMs x 64 IMAD lanes/clk x 2070 MHz / 2 IMAD "
-                             "(low + high half) per 32x32->64 word product; measured on GB300 the high-half "
-                             "multiply issues at about half rate, so carry-chain code tops out near "
-                             "6.6-6.7 T products/s",
-                "products_per_op": prods}
-    if clk.get("sm_mhz"):
-        roofline["frac_at_measured_clock"] = achieved / derived_peak_tprod(SM_COUNT_GB300, clk["sm_mhz"])
-    if tune["variant"] == 3 and args.kind == "crt":
-        issued, tflops_op = tc_work_per_op(spec["bits"], tune["window"])
-        tpk, tsrc = measured_bf16_tflops()
-        t_ach = tflops_op * count / (ms / 1e3) / 1e12
+    prof_valid = bool(prof and prof["window"] == tune["window"] and tune["threads_per_op"] == 1
+                      and prof["stamp"] == kernel_stamp(prof["files"]))
+    traffic = prof["dram_bytes_per_op"] * count if prof_valid else None
+    tc_path = tune["variant"] == 3 and args.kind == "crt"
+    if tc_path:
+        issued, tflops_op, method_flops_op = tc_work_per_op(spec["bits"], tune["window"])
+        roofline = alu_roofline(issued * count / (ms / 1e3) / 1e12, local,
+                                "32x32->64 word products the CUDA cores issue per second (per-message products "
+                                "A*B and squarings, the Garner step); the Montgomery reductions run on the tensor "
+                                "cores and are reported under `tensor`")
         roofline["issued_products_per_op"] = issued
-        roofline["issued_achieved"] = issued * count / (ms / 1e3) / 1e12
-        roofline["issued_frac"] = roofline["issued_achieved"] / peak
-        roofline["tensor"] = {"achieved": t_ach, "peak": tpk, "unit": "TFLOP/s", "frac": t_ach / tpk,
-                              "flops_per_op": tflops_op, "peak_source": tsrc + " dense bf16 (fp16 same rate)"}
-        roofline["note"] = ("tensor-core path: the Montgomery reductions run as fp16 MMAs, so the algorithmic "
-                            "CIOS count can exceed the IMAD peak; issued_* is the CUDA-core work actually run")
+        tpk, tsrc = measured_bf16_tflops()
+        t_method = method_flops_op * count / (ms / 1e3) / 1e12
+        t_issued = tflops_op * count / (ms / 1e3) / 1e12
+        roofline["tensor"] = {"achieved": t_method, "peak": tpk, "unit": "TFLOP/s", "frac": t_method / tpk,
+                              "flops_per_op": method_flops_op, "peak_source": tsrc + " dense bf16 (fp16 same rate)",
+                              "what": "the nonzero byte products of the two Toeplitz products per Montgomery step "
+                                      "(mu = T_lo m' mod R, positions of mu m), bias block excluded",
+                              "issued_achieved": t_issued, "issued_frac": t_issued / tpk,
+                              "issued_flops_per_op": tflops_op}
+        roofline["algorithmic"] = {"products_per_op": prods, "achieved": cios_achieved,
+                                   "note": "the CIOS count 2H^2 + H per Montgomery product; with the reductions on "
+                                           "the tensor cores this rate is not bounded by the IMAD pipe"}
+    else:
+        roofline = alu_roofline(cios_achieved, local,
+                                "32x32->64 word products per second under the CIOS count 2L^2 + L per Montgomery "
+                                "product (what these kernels issue)")
+        roofline["products_per_op"] = prods
+    roofline.update({"traffic": traffic, "traffic_unit": "DRAM bytes per launch",
+                     "traffic_source": prof["source"] if traffic else None,
+                     "algorithmic_io_bytes": count * L * 4 * 2})
+    if prof_valid and "pipes" in prof:
+        roofline["limiter"] = dict(prof["pipes"], source=prof["source"],
+                                   reading="latency and issue: no pipe saturated; 16 warps per SM (TMEM holds "
+                                           "four 128-column tiles), fixed-latency carry-chain waits")
+    if clk.get("sm_mhz"):
+        roofline["sm_mhz"] = clk["sm_mhz"]
 
     line = {
         "metric": metric, "value": value, "unit": unit,

@@ -66,7 +66,7 @@ typedef enum rsa_exp_sel {
 /* Supported key sizes: nbits in {1024, 2048, 3072, 4096} (multi-limb path), and
  * nbits = 32 for moduli below 2^32 (single-limb path of the paper's toy example,
  * n = 17947, e = 131, d = 137, Sec. 2).  PRIVATE_CRT needs p and q; 3072/4096-bit
- * PUBLIC and PRIVATE_PLAIN run on the wide-operand kernel. */
+ * PUBLIC and PRIVATE_PLAIN run with four lanes per operation by default. */
 
 /* Create a context on CUDA device `device`.  mem_budget_bytes caps the library's
  * own device memory (key table + workspace); 0 selects 2 GiB.  *out receives the
@@ -227,8 +227,11 @@ int rsa_modexp_batch_host(rsa_ctx *ctx, uint64_t count, const int32_t *key_ids,
  * it (window width 4), so throughput is below rsa_modexp_key's.  All calls
  * share that array: calls that overlap on the GPU race and must be ordered on
  * one stream.  The first call on a device looks up the array's address with
- * that device current; make it before any stream capture.  Enqueued on
- * `stream`; errors are returned before anything is enqueued. */
+ * that device current; make it before any stream capture.  Only the device's
+ * primary context (the CUDA runtime's) is supported: the array's address is
+ * cached per device, and a separate driver-API context on the same device
+ * holds its own copy of the array.  Enqueued on `stream`; errors are returned
+ * before anything is enqueued. */
 int rsa_crt_decrypt_noalloc(const uint32_t *key_record, uint32_t nbits, uint64_t count,
                             const uint32_t *msgs, uint32_t *out, int32_t *op_status, void *stream);
 
@@ -322,7 +325,10 @@ typedef struct rsa_tuning {
                               of up to `window` bits (Fig. 7; window 4..6, default 5),
                               0 = sliding for exponents longer than 64 bits */
     int32_t threads_per_op; /* lanes cooperating on one operation: 1, 2 or 4 (numbers
-                              sliced over the lanes, warp-shuffle carries); 0 = automatic */
+                              sliced over the lanes, warp-shuffle carries); 0 = automatic
+                              (4 above 2048 bits, else 1).  PRIVATE_PLAIN takes 1 up to
+                              2048 bits and 4 above; other combinations without a kernel
+                              return RSA_ERR_UNSUPPORTED from the launching call */
 } rsa_tuning;
 
 /* Set (or, with NULL, reset to automatic) the launch parameters used for keys of

@@ -178,6 +178,8 @@ double class_cost(int32_t cls) {
     case CLS_PUB128: return 19 * mm(128);
     case CLS_PLAIN32: return 1300 * mm(32);
     case CLS_PLAIN64: return 2600 * mm(64);
+    case CLS_PLAIN96: return 3900 * mm(96) / 4;   // per lane
+    case CLS_PLAIN128: return 5200 * mm(128) / 4;
     default: return 0.0;
   }
 }

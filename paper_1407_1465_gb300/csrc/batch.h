@@ -36,7 +36,9 @@ enum : int32_t {
   CLS_CRT32W = 11,                               // CRT of 2048-bit keys, four lanes per operation
   CLS_CRT64W = 12,                               // CRT of 4096-bit keys, eight lanes per operation
                                                  // (the W classes: small batches, latency over throughput)
-  CLS_COUNT = 13
+  CLS_PLAIN96 = 13, CLS_PLAIN128 = 14,           // plain private exponent of 3072/4096-bit moduli,
+                                                 // four lanes per operation
+  CLS_COUNT = 15
 };
 
 // Window widths the execution kernel is compiled with, per class (3072/4096-bit
@@ -52,7 +54,7 @@ __host__ __device__ inline int32_t batch_class(uint32_t L, int kind, bool wide =
     return L == 32 ? CLS_CRT16 : L == 64 ? (wide ? CLS_CRT32W : CLS_CRT32) : L == 96 ? CLS_CRT48
            : L == 128 ? (wide ? CLS_CRT64W : CLS_CRT64) : -1;
   if (kind == 0) return L == 32 ? CLS_PUB32 : L == 64 ? CLS_PUB64 : L == 96 ? CLS_PUB96 : L == 128 ? CLS_PUB128 : -1;
-  if (kind == 2) return L == 32 ? CLS_PLAIN32 : L == 64 ? CLS_PLAIN64 : -1;
+  if (kind == 2) return L == 32 ? CLS_PLAIN32 : L == 64 ? CLS_PLAIN64 : L == 96 ? CLS_PLAIN96 : L == 128 ? CLS_PLAIN128 : -1;
   return -1;
 }
 
@@ -63,11 +65,12 @@ __host__ __device__ inline int32_t batch_class(uint32_t L, int kind, bool wide =
 //         four lanes per operation (eight for 4096-bit keys in small batches)
 //   CRT   CRT of 1024/2048-bit keys, public/plain of 1024-bit keys, toy keys
 //   L64   public/plain exponents of 2048-bit moduli (one lane, 232 registers)
-//   WIDE  public exponents of 3072/4096-bit moduli, four lanes per operation
+//   WIDE  public and plain private exponents of 3072/4096-bit moduli, four
+//         lanes per operation
 enum : int32_t { GRP_BIG = 0, GRP_CRT = 1, GRP_L64 = 2, GRP_WIDE = 3, GRP_COUNT = 4 };
 __host__ __device__ inline int32_t batch_group(int32_t cls) {
   if (cls == CLS_CRT48 || cls == CLS_CRT64 || cls == CLS_CRT32W || cls == CLS_CRT64W) return GRP_BIG;
-  if (cls == CLS_PUB96 || cls == CLS_PUB128) return GRP_WIDE;
+  if (cls == CLS_PUB96 || cls == CLS_PUB128 || cls == CLS_PLAIN96 || cls == CLS_PLAIN128) return GRP_WIDE;
   if (cls == CLS_PUB64 || cls == CLS_PLAIN64) return GRP_L64;
   return GRP_CRT;
 }
@@ -82,16 +85,16 @@ __host__ __device__ constexpr size_t batch_table_u4(int group) {
   return group == GRP_BIG   ? batch_table_need(5, 16)   // CRT H=64, w=5, four lanes: 16 limbs per lane
          : group == GRP_CRT ? batch_table_need(4, 32)   // CRT H=32, w=4; plain L=32, w=4
          : group == GRP_L64 ? batch_table_need(4, 64)   // plain L=64, w=4
-                            : 0;                        // public exponents only: no table
+                            : batch_table_need(kBatchWindowPlain, 32);   // plain L=128, w=4, four lanes
 }
 
 // operations per tile of a class: CRT 32 (warp pair on the same 32), wide CRT 8
-// (4 lanes per operation, the pair on the same 8; 4 with 8 lanes), wide public 16 (4 lanes per
-// operation, 8 per warp), others 64 (32 per warp)
+// (4 lanes per operation, the pair on the same 8; 4 with 8 lanes), wide public and plain 16 (4
+// lanes per operation, 8 per warp), others 64 (32 per warp)
 __host__ __device__ inline int32_t batch_tile_ops(int32_t cls) {
   if (cls == CLS_CRT64W) return 4;
   if (cls == CLS_CRT48 || cls == CLS_CRT64 || cls == CLS_CRT32W) return 8;
-  if (cls == CLS_PUB96 || cls == CLS_PUB128) return 16;
+  if (cls == CLS_PUB96 || cls == CLS_PUB128 || cls == CLS_PLAIN96 || cls == CLS_PLAIN128) return 16;
   return (cls == CLS_CRT16 || cls == CLS_CRT32) ? 32 : 64;
 }
 

@@ -88,6 +88,15 @@ __device__ __forceinline__ void run_pub_wide(const uint32_t *ks, uint4 *work, in
   pub_tile_t<L, 4, 8>(ks, g, sq + g.opi, sq + kStage + g.opi, io);
 }
 
+// wide plain private exponents: 4 lanes per operation, 8 operations per warp
+template <int L>
+__device__ __forceinline__ void run_plain_wide(const uint32_t *ks, uint4 *work, uint4 *table_warp, int warp, int lane,
+                                               const TileIO &io) {
+  constexpr int kStage = (L / 4) * 8;
+  const Group<4> g(lane);
+  plain_tile_t<L, 4, kBatchWindowPlain, 4>(ks, g, work + warp * kStage + g.opi, table_warp + lane, io);
+}
+
 template <int L>
 __device__ __forceinline__ void run_plain(const uint32_t *ks, uint4 *work, uint4 *table_warp, int warp, int lane,
                                           const TileIO &io) {
@@ -151,12 +160,18 @@ __global__ void __launch_bounds__(64, G == GRP_BIG ? 8 : 1) batch_exec_kernel(Ba
     } else if constexpr (G == GRP_WIDE) {
       // 16-operation tiles: 8 per warp
       const int32_t wn8 = min(8, max(0, td.nops - 8 * warp));
-      static_assert(stage_u4(4, 128, 8) * 16 <= work_bytes(GRP_WIDE) && stage_u4(4, 96, 8) * 16 <= work_bytes(GRP_WIDE),
-                    "work area of the wide public classes");
+      static_assert(stage_u4(4, 128, 8) * 16 <= work_bytes(GRP_WIDE) && stage_u4(4, 96, 8) * 16 <= work_bytes(GRP_WIDE) &&
+                        stage_u4(2, 128, 8) * 16 <= work_bytes(GRP_WIDE),
+                    "work area of the wide public and plain classes");
+      static_assert(batch_table_need(kBatchWindowPlain, 128 / 4) <= batch_table_u4(GRP_WIDE) &&
+                        batch_table_need(kBatchWindowPlain, 96 / 4) <= batch_table_u4(GRP_WIDE),
+                    "window table of a wide plain class");
       const TileIO io8{d.msgs, d.out, d.status, d.sorted, d.offsets, (uint32_t)(td.op_start + 8 * warp),
                        (uint32_t)wn8};
       if (td.cls == CLS_PUB96) run_pub_wide<96>(ks, work, warp, lane, io8);
       else if (td.cls == CLS_PUB128) run_pub_wide<128>(ks, work, warp, lane, io8);
+      else if (td.cls == CLS_PLAIN96) run_plain_wide<96>(ks, work, table_warp, warp, lane, io8);
+      else if (td.cls == CLS_PLAIN128) run_plain_wide<128>(ks, work, table_warp, warp, lane, io8);
     } else {
       static_assert(stage_u4(3, 32, 32) * 16 <= work_bytes(GRP_CRT) && stage_u4(4, 32, 32) * 16 <= work_bytes(GRP_CRT) &&
                         stage_u4(2, 32, 32) * 16 <= work_bytes(GRP_CRT),

@@ -296,4 +296,63 @@ __global__ void __launch_bounds__(256) pub_kernel_t(ExpArgs a) {
   }
 }
 
+
+// ------------------------------------------------------------------ plain private exponent, T lanes per operation
+// x^d mod n without the CRT split (d of the full key length): to Montgomery
+// form, the constant-time fixed window of fixed_window_exp_t over all 32L bits
+// of d, back out of Montgomery form.  For 3072/4096-bit moduli, whose full-size
+// numbers do not fit one thread's registers.
+template <int L, int T, int W, int U>
+__device__ __forceinline__ void plain_tile_t(const uint32_t *ks, const Group<T> &g, uint4 *stage_op,
+                                             uint4 *table_lane, const TileIO &io) {
+  constexpr int K = L / T;
+  constexpr KeyLayout lay(L);
+  const KeyHeader &hd = *reinterpret_cast<const KeyHeader *>(ks);
+  using NS = typename std::conditional<(K <= 16), NRegs<K>, NSmem<K>>::type;
+  NS N;
+  if constexpr (K <= 16) N.load(reinterpret_cast<const uint4 *>(ks + lay.n + g.r * K)); else N.s = ks + lay.n + g.r * K;
+  const bool valid = (uint32_t)g.opi < io.nops;
+  const uint32_t slot = io.base + (uint32_t)g.opi;
+  const uint32_t op = valid ? (io.op_index ? (uint32_t)io.op_index[slot] : slot) : 0u;
+  const size_t off = io.offsets ? (size_t)io.offsets[op] : (size_t)op * L;
+  const uint32_t *row = io.msgs + off;
+  uint32_t A[K];
+  load_slice<K>(A, row, g.r * K, valid);
+  mont_mul_t<K, T, U>(A, SmemB{reinterpret_cast<const uint4 *>(ks + lay.r2n), 1}, N, hd.np_n, g);
+  fixed_window_exp_t<K, T, W, U>(A, ks + lay.d, 32 * L, ks + lay.onen, stage_op, table_lane, N, hd.np_n, g);
+  mont_mul_t<K, T, U>(A, SmemB{reinterpret_cast<const uint4 *>(ks + lay.unitL), 1}, N, hd.np_n, g);
+  const int cmp = cmp_t<K, T>(row + g.r * K, ks + lay.n + g.r * K, g);  // every lane, see crt_tile_t
+  const bool ok = valid && cmp < 0;
+  if (valid) {
+    uint4 *o4 = reinterpret_cast<uint4 *>(io.out + off + g.r * K);
+#pragma unroll
+    for (int gg = 0; gg < K / 4; ++gg)
+      o4[gg] = ok ? make_uint4(A[4 * gg], A[4 * gg + 1], A[4 * gg + 2], A[4 * gg + 3]) : make_uint4(0u, 0u, 0u, 0u);
+    if (g.r == 0 && io.status) io.status[op] = ok ? 0 : -3;
+  }
+}
+
+// one warp per 32/T operations; per warp one stage of [L/4][32/T] uint4 in
+// shared memory and a window table of 2^W entries x (L/T/4) x 32 uint4
+template <int L, int T, int W, int U>
+__global__ void __launch_bounds__(256) plain_kernel_t(ExpArgs a) {
+  using Sm = ExpSmem<L>;
+  constexpr int OPW = 32 / T;
+  constexpr int kStage = (L / 4) * OPW;
+  extern __shared__ uint4 smem4[];
+  load_key_smem<L>(smem4, a.keyrec);
+  const uint32_t *ks = reinterpret_cast<const uint32_t *>(smem4);
+  const int nw = blockDim.x / 32, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const Group<T> g(lane);
+  uint4 *stage = smem4 + Sm::kKeyWords / 4 + (size_t)warp * kStage;
+  uint4 *table_lane = a.tables + ((size_t)blockIdx.x * nw + warp) * ((size_t)(1 << W) * (L / T / 4) * 32) + lane;
+  const uint32_t ntiles = (a.count + OPW - 1) / OPW;
+#pragma unroll 1
+  for (uint32_t tile = blockIdx.x * nw + warp; tile < ntiles; tile += gridDim.x * nw) {
+    const uint32_t base = tile * OPW;
+    const TileIO io{a.msgs, a.out, a.status, nullptr, nullptr, base, min((uint32_t)OPW, a.count - base)};
+    plain_tile_t<L, T, W, U>(ks, g, stage + g.opi, table_lane, io);
+  }
+}
+
 }  // namespace rsagpu

@@ -23,6 +23,7 @@ const void *toy_kernel_fn();
 // T lanes per operation (T = 2, 4): CRT with half size H, public exponent with L limbs
 const void *crt_kernel_t_fn(int H, int T, int W);
 const void *pub_kernel_t_fn(int L, int T);
+const void *plain_kernel_t_fn(int L, int T, int W);
 
 // windows instantiated for the private-exponent kernels
 constexpr int kMinWindow = 3;

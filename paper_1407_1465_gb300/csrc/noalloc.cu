@@ -23,6 +23,10 @@
 //   - the first call on a device looks up the array's device address
 //     (cudaGetSymbolAddress) with that device current and caches it; make that
 //     first call before any stream capture begins.
+//   - the cached address belongs to the device's primary context (the one the
+//     CUDA runtime uses); callers that run their own driver-API contexts on the
+//     same device are not supported, because the array has a separate instance
+//     in each context.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -121,7 +121,7 @@ Tune Ctx::tune_for(uint32_t nbits, int kind) const {
   // 127 K/s -> 145 K/s), and the one-lane public exponent of those sizes spills --
   // one lane otherwise (RSA-2048 CRT: 1.24 M/s on one lane, 1.10 M on two).
   if (kind == RSA_TUNE_RAGGED) return t;   // ragged batches: 0 fields stay automatic
-  if (!t.tpo) t.tpo = (L > 64 && kind != RSA_EXP_PRIVATE_PLAIN) ? 4 : 1;
+  if (!t.tpo) t.tpo = L > 64 ? 4 : 1;
   return t;
 }
 
@@ -243,6 +243,30 @@ int Ctx::run_key(const KeySlot &k, int kind, uint64_t count, const uint32_t *msg
     void *args[] = {&a};
     e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, s);
     if (e != cudaSuccess) return cuda_error(e, "launch pub_kernel_t");
+    stats.kernel_launches++;
+    last_grid = grid;
+    last_threads = threads;
+    return RSA_OK;
+  }
+  if (t.tpo > 1 && kind == RSA_EXP_PRIVATE_PLAIN) {
+    // d mod n on T lanes per operation (3072/4096-bit moduli; window 4 or 5)
+    const int T = t.tpo;
+    const void *fn = plain_kernel_t_fn((int)L, T, t.window);
+    if (!fn) return set_error(RSA_ERR_UNSUPPORTED, "no plain-exponent kernel for this size / window / lanes per operation");
+    const int warps = std::max(1, t.warps_per_cta);
+    const int threads = 32 * warps;
+    const size_t smem = (KeyLayout(L).total + 3) / 4 * 4 * 4 + (size_t)warps * (L / 4) * (32 / T) * 16;
+    const uint64_t ntiles = (count + 32 / T - 1) / (32 / T);
+    int grid = 0;
+    int rc = launch_grid(fn, threads, smem, (uint64_t)warps, ntiles, t.ctas_per_sm, &grid);
+    if (rc) return rc;
+    const size_t tbytes = (size_t)grid * warps * ((size_t)1 << t.window) * (L / T) * 128;
+    rc = ensure(w.tables, tbytes);
+    if (rc) return rc;
+    ExpArgs a{k.d_rec, msgs, out, status, (uint32_t)count, static_cast<uint4 *>(w.tables.ptr)};
+    void *args[] = {&a};
+    e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, s);
+    if (e != cudaSuccess) return cuda_error(e, "launch plain_kernel_t");
     stats.kernel_launches++;
     last_grid = grid;
     last_threads = threads;

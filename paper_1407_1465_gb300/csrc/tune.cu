@@ -102,7 +102,7 @@ extern "C" int rsa_autotune(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint6
       for (int w : windows)
         for (int wp : warps)
           for (int cps : {0, 1, 2}) {
-            if (tpo > 1 && (v == 2 || exp_sel == RSA_EXP_PRIVATE_PLAIN)) continue;  // not offered
+            if (tpo > 1 && v == 2) continue;  // not offered (shapes without a kernel fail below and are skipped)
             // the tensor-core path has its own fixed launch shape and windows 3, 4
             if (v == 3 && (tpo != 1 || wp != warps[0] || cps != 0 || (w != 3 && w != 4))) continue;
             c->tuning[{nbits, exp_sel}] = Tune{w, wp, cps, v, tpo};

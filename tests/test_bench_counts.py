@@ -89,10 +89,16 @@ def _tc_walk(bits, W):
     selected entry; the q half adds one product leaving Montgomery form; then
     Garner (two CIOS products and one H x H product)."""
     H = bits // 64
+    D = 4 * H                                                # byte digits of a prime
+    # the method's byte products per step, by enumerating digit pairs: mu's
+    # columns 0..D-1 of T_lo * m' (digit k of T_lo, digit n-k of m'), and the
+    # positions D-4 .. 2D-5 of mu * m that MMA 2 returns (digit i of mu, j-i of m)
+    pairs1 = sum(1 for n in range(D) for k in range(D) if 0 <= n - k < D)
+    pairs2 = sum(1 for j in range(D - 4, 2 * D - 4) for i in range(D) if 0 <= j - i < D)
     nwin = -(-(32 * H) // W)
     ntab = 1 << W
     nexp = (nwin - 1) * (W + 1)
-    prods = flops = 0
+    prods = flops = method = 0
     for pi in (0, 1):
         s = 0
         for st in range(ntab + nexp + (1 if pi == 0 else 0)):
@@ -106,10 +112,20 @@ def _tc_walk(bits, W):
                     s = 0
             prods += H * (H + 1) // 2 if sq else H * H
             flops += 2 * (2 * 128 * (9 * 16))                # two MMAs, N = 128, K = 144, per row
+            method += 2 * (pairs1 + pairs2)
     prods += 2 * (2 * H * H + H) + H * H
-    return prods, flops
+    return prods, flops, method
 
 
 @pytest.mark.parametrize("W", [3, 4])
 def test_tc_work_per_op_matches_the_step_loop(W):
     assert bench.tc_work_per_op(2048, W) == _tc_walk(2048, W)
+
+
+def test_measured_roofline_fraction_uses_the_probe_figure(monkeypatch):
+    """alu_roofline divides by the measured carry-chain rate, not the unit-count figure."""
+    monkeypatch.setitem(bench._PEAKS, 7, {"chain_tprod": 6.5, "imad_lane_tops": 19.5, "sm_count": 152,
+                                          "derived_tprod": bench.derived_peak_tprod(152, 2070.0)})
+    r = bench.alu_roofline(3.25, 7, "test")
+    assert r["peak"] == 6.5 and r["frac"] == 0.5 and r["peak_source"] == "measured"
+    assert abs(bench.derived_peak_tprod(152, 2070.0) - 10.06848) < 1e-9

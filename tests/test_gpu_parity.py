@@ -106,8 +106,6 @@ def test_crt_parity(torch_cuda, ctx, keys, kids, bits, count):
 @pytest.mark.parametrize("bits", [1024, 2048, 3072, 4096])
 @pytest.mark.parametrize("kind", [PUB, PLAIN])
 def test_full_modulus_parity(torch_cuda, ctx, keys, kids, bits, kind):
-    if kind == PLAIN and bits > 2048:
-        pytest.skip("plain private exponent is offered up to 2048 bits")
     key = keys[bits]
     rows = workloads.messages_below(key.n, 45, 6, ("full", bits, kind))
     got, st = run(torch_cuda, ctx, kids[bits], kind, rows)
@@ -260,8 +258,6 @@ def test_lanes_per_operation_crt(torch_cuda, ctx, keys, kids, bits, tpo):
 @pytest.mark.parametrize("tpo", [2, 4])
 @pytest.mark.parametrize("bits", [2048, 3072, 4096])
 def test_lanes_per_operation_public(torch_cuda, ctx, keys, kids, bits, tpo):
-    if bits == 2048 and tpo == 4:
-        pytest.skip("not instantiated")
     key = keys[bits]
     good, bad = _edge_rows(key)
     rows = np.concatenate([workloads.messages_below(key.n, 37, 22, ("tpo-pub", bits, tpo)), good, bad])

@@ -58,7 +58,7 @@ def build_mix(keys, kids, count, seed):
     for i in range(count):
         k = st.below(len(keys))
         key = keys[k]
-        kinds = [PUB, CRT] + ([PLAIN] if key.bits <= 2048 else [])
+        kinds = [PUB, CRT, PLAIN]
         kind = kinds[st.below(len(kinds))]
         if key.bits == 32:
             row = np.array([st.below(key.n)], dtype=np.uint32)
@@ -143,13 +143,11 @@ def test_ragged_invalid_operations(torch_cuda, ctx, mixed_keys):
     key_ids[3] = 12345                     # unknown key
     key_ids[5] = -1                        # negative id
     sels[7] = 9                            # bad kind
-    big = [i for i, (k, _, _) in enumerate(ops) if keys[k].bits == 4096]
-    sels[big[0]] = PLAIN                   # plain exponent not offered at 4096 bits
-    wide = [i for i, (k, _, _) in enumerate(ops) if keys[k].bits >= 1024 and i not in (3, 5, 7, big[0])]
+    wide = [i for i, (k, _, _) in enumerate(ops) if keys[k].bits >= 1024 and i not in (3, 5, 7)]
     offsets[wide[0]] += 1                  # misaligned row
-    bad = {3: -2, 5: -2, 7: -1, big[0]: -7, wide[0]: -1}
+    bad = {3: -2, 5: -2, 7: -1, wide[0]: -1}
     out, st, rc = run_batch(torch_cuda, ctx, key_ids, sels, offsets, packed)
-    assert rc in (-2, -1, -7)
+    assert rc in (-2, -1)
     for i, (k, kind, row) in enumerate(ops):
         if i in bad:
             assert st[i] == bad[i], (i, st[i])
