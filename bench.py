@@ -492,12 +492,15 @@ def run_bgcd(args):
     return 0
 
 
-def run_ragged(args):
-    """Ragged batch: 256 keys, 200000 operations, one rsa_modexp_batch (one graph
-    launch) per step, against a loop of one rsa_modexp_key launch per
-    (key, kind) group over the same operations."""
+def ragged_measure(steps: int, warmup: int, autotune: bool = False, loop_steps: int = 0) -> dict:
+    """The ragged workload (256 keys, 200000 operations, one rsa_modexp_batch
+    -- one graph launch -- per step) timed with CUDA events, against a loop of
+    one rsa_modexp_key launch per (key, kind) group over the same operations.
+    Sampled results are checked against the loop's and against the oracle."""
     import torch
-    from paper_1407_1465_gb300 import RsaContext, build, rsa_modexp_batch, rsa_modexp_key, rsa_products_per_op
+    import oracle
+    from paper_1407_1465_gb300 import (RSA_TUNE_RAGGED, RsaContext, build, rsa_modexp_batch, rsa_modexp_key,
+                                       rsa_products_per_op)
     build.build()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
@@ -515,72 +518,96 @@ def run_ragged(args):
     sptr = stream.cuda_stream
     # groups for the one-key-per-launch loop, gathered contiguously (untimed)
     groups = {}
-    for i, (k, s) in enumerate(zip(rb.key_ids, rb.exp_sel)):
-        groups.setdefault((int(k), int(s)), []).append(i)
+    for i, (k, sel) in enumerate(zip(rb.key_ids, rb.exp_sel)):
+        groups.setdefault((int(k), int(sel)), []).append(i)
     gbufs = []
-    for (k, s), idx in sorted(groups.items()):
+    for (k, sel), idx in sorted(groups.items()):
         rows = np.stack([rb.msgs[i] for i in idx])
         t = torch.from_numpy(rows.view(np.int32)).to(dev)
-        gbufs.append((kids[k], s, len(idx), t, torch.empty_like(t), idx))
+        gbufs.append((kids[k], sel, len(idx), t, torch.empty_like(t), idx))
     prods = 0.0
     for i in range(count):
         key = rb.keys[rb.key_ids[i]]
         prods += rsa_products_per_op(key.bits, int(rb.exp_sel[i]), key.e, 5)
 
-    tuning = None
-    if args.autotune:
-        # the ragged autotuner on this very batch (untimed): lanes per operation and CTA cap
+    tuned_ms = None
+    if autotune:
+        # the ragged autotuner on this very batch (untimed)
         from paper_1407_1465_gb300 import rsa_autotune_batch
-        tuning = rsa_autotune_batch(ctx.handle, count, key_ids, sels, offs, msgs, out)
+        tuned_ms = rsa_autotune_batch(ctx.handle, count, key_ids, sels, offs, msgs, out)["ms"]
+    tuning = ctx.get_tuning(0, RSA_TUNE_RAGGED)
 
     def step_ragged():
         rsa_modexp_batch(ctx.handle, count, key_ids, sels, offs, msgs, out, status, sptr)
 
     def step_loop():
-        for kid, s, n, t, o, _ in gbufs:
-            rsa_modexp_key(ctx.handle, kid, s, n, t, o, None, sptr)
+        for kid, sel, n, t, o, _ in gbufs:
+            rsa_modexp_key(ctx.handle, kid, sel, n, t, o, None, sptr)
 
     res = {}
-    for name, fn in (("ragged", step_ragged), ("loop", step_loop)):
-        for _ in range(args.warmup):
+    for name, fn, k_steps, k_warm in (("ragged", step_ragged, steps, warmup),
+                                      ("loop", step_loop, loop_steps or steps, min(warmup, 1 if loop_steps else warmup))):
+        for _ in range(k_warm):
             fn()
         torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k_steps)]
         for a, b in ev:
             a.record(stream)
             fn()
             b.record(stream)
         torch.cuda.synchronize()
-        ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
-        res[name] = ms
+        res[name] = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
     if ctx.sync() != 0 or not bool((status == 0).all()):
         raise RuntimeError("ragged batch reported errors")
-    # the loop's results must equal the ragged batch's
+    # the loop's results must equal the ragged batch's, and sampled ones the oracle's
     got = out.cpu().numpy().view(np.uint32)
-    for kid, s, n, t, o, idx in gbufs[:40]:
+    for kid, sel, n, t, o, idx in gbufs[:40]:
         oo = o.cpu().numpy().view(np.uint32)
         for j, i in enumerate(idx[:4]):
             off = int(rb.offsets[i])
             if not np.array_equal(got[off:off + oo.shape[1]], oo[j]):
                 raise RuntimeError("ragged and per-key results differ")
+    for i in np.random.default_rng(3).choice(count, 12, replace=False):
+        key, row, off = rb.keys[rb.key_ids[i]], rb.msgs[i], int(rb.offsets[i])
+        m = workloads.limbs_to_int(row)
+        v = oracle.crt_decrypt(m, key.d, key.p, key.q) if rb.exp_sel[i] == 1 else oracle.modexp(m, key.e, key.n)
+        if not np.array_equal(got[off:off + row.size], workloads.int_to_limbs(v, row.size)):
+            raise RuntimeError("ragged result differs from the oracle")
+    launches0 = ctx.stats()["kernel_launches"]
+    step_ragged()
+    torch.cuda.synchronize()
+    per_step = ctx.stats()["kernel_launches"] - launches0
+    ctx.close()
+    return {"value": count / (res["ragged"] / 1e3), "unit": "ops/s", "ms_per_step": res["ragged"],
+            "kernel_launches_per_step": int(per_step),
+            "one_key_per_launch": {"ms_per_step": res["loop"], "value": count / (res["loop"] / 1e3),
+                                   "launches": len(gbufs)},
+            "speedup_vs_loop": res["loop"] / res["ragged"], "tuning": tuning,
+            "autotuned_ms": tuned_ms, "products_per_step": prods, "count": count}
+
+
+def run_ragged(args):
+    """Ragged batch: 256 keys, 200000 operations, one rsa_modexp_batch (one graph
+    launch) per step, against a loop of one rsa_modexp_key launch per
+    (key, kind) group over the same operations."""
+    r = ragged_measure(args.steps, args.warmup, args.autotune)
     line = {
         "metric": "ragged-batch ops/sec (256 keys, 200000 ops, one graph launch)",
-        "value": count / (res["ragged"] / 1e3), "unit": "ops/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": res["ragged"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "value": r["value"], "unit": "ops/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic", "gpu_launches": r["kernel_launches_per_step"] * args.steps,
         "config": {"workload": "ragged: 256 seeded keys (1024/2048/3072/4096 bits at 0.1/0.5/0.2/0.2), "
                                "Zipf(1.1) counts summing to 200000, 70% CRT decrypt / 30% public",
-                   "groups": len(gbufs)},
-        "one_key_per_launch": {"ms_per_step": res["loop"], "value": count / (res["loop"] / 1e3),
-                               "launches": len(gbufs)},
-        "speedup_vs_loop": res["loop"] / res["ragged"], "tuning": tuning or "automatic",
-        "roofline": dict(alu_roofline(prods / (res["ragged"] / 1e3) / 1e12, 0,
+                   "groups": r["one_key_per_launch"]["launches"]},
+        "one_key_per_launch": r["one_key_per_launch"], "speedup_vs_loop": r["speedup_vs_loop"],
+        "tuning": r["tuning"], "autotuned": bool(args.autotune),
+        "roofline": dict(alu_roofline(r["products_per_step"] / (r["ms_per_step"] / 1e3) / 1e12, 0,
                                       "word products per second under the CIOS count 2L^2 + L per Montgomery "
-                                      "product of each operation's class (window 5 for private exponents)"),
-                         products_per_step=prods),
+                                      "product of each operation's class (window 5 for private exponents); the "
+                                      "2048-bit CRT tiles of the tensor-core group issue fewer on the CUDA cores"),
+                         products_per_step=r["products_per_step"]),
     }
     print(json.dumps(line), flush=True)
-    ctx.close()
     return 0
 
 
@@ -621,7 +648,9 @@ def serving_sweep(rates, duration, slots, window_us, key_bits=0, mix_sizes=False
         rsa_server_submit_many(ctx.handle, arr)
         rsa_server_drain(ctx.handle, 900000)
         st = rsa_server_get_stats(ctx.handle)
-        results.append({"offered_req_per_s": rate, "requests": st["completed"], "ops": st["ops_completed"],
+        offered_ops = sum(rq.count for rq in reqs) / duration
+        results.append({"offered_req_per_s": rate, "offered_ops_per_s": offered_ops,
+                        "requests": st["completed"], "ops": st["ops_completed"],
                         "sustained_ops_per_s": st["ops_completed"] / st["span_s"] if st["span_s"] else None,
                         "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3, "max_ms": st["max_us"] / 1e3,
                         "batches": st["batches"], "peak_inflight_bytes": st["peak_bytes"]})
@@ -748,6 +777,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-latency", action="store_true", help="skip the serving-latency sweep of the default run")
+    ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch measurement of the default run")
     ap.add_argument("--autotune", action="store_true", help="ragged: run the ragged autotuner on the batch first")
     args = ap.parse_args()
     if args.workload == "ragged":
@@ -935,17 +965,34 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(key, rows, public=(kind == RSA_EXP_PUBLIC), e=e_pub)
     ctx.close()
+    if rank == 0 and ws == 1 and not args.no_ragged and args.workload == "rsa2048" and args.kind == "crt":
+        # the ragged batch (256 keys, 200000 operations, one graph launch) against
+        # a loop of one launch per (key, kind) group
+        r = ragged_measure(3, 1, loop_steps=1)
+        line["ragged"] = {
+            "what": "ragged batch: 256 seeded keys (1024/2048/3072/4096 bits at 0.1/0.5/0.2/0.2), Zipf(1.1) counts "
+                    "summing to 200000 operations, 70% CRT / 30% public, one rsa_modexp_batch (one CUDA graph) per "
+                    "step; sampled results checked against the oracle",
+            "value": r["value"], "unit": "ops/s", "ms_per_step": r["ms_per_step"],
+            "one_key_per_launch": r["one_key_per_launch"], "speedup_vs_loop": r["speedup_vs_loop"],
+            "kernel_launches_per_step": r["kernel_launches_per_step"], "tuning": r["tuning"]}
     if rank == 0 and ws == 1 and not args.no_latency and args.workload == "rsa2048" and args.kind == "crt":
         # the metric's latency half: ragged-batch request latency through the
-        # serving loop (256 keys of 1024-4096 bits), a short sweep at low load
-        rates = [1000.0, 5000.0]
+        # serving loop (256 keys of 1024-4096 bits), offered load swept from
+        # 1 k to 200 k requests/s (past saturation)
+        rates = [1000.0, 2000.0, 5000.0, 10000.0, 20000.0, 50000.0, 100000.0, 200000.0]
         sweep = serving_sweep(rates, 0.5, args.slots, args.window_us)
+        rows = [{"offered_req_per_s": r["offered_req_per_s"], "offered_ops_per_s": r["offered_ops_per_s"],
+                 "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "sustained_ops_per_s": r["sustained_ops_per_s"],
+                 "peak_inflight_bytes": r["peak_inflight_bytes"]} for r in sweep]
+        kept = [x for x in rows if x["sustained_ops_per_s"] and x["sustained_ops_per_s"] >= 0.9 * x["offered_ops_per_s"]]
         line["latency"] = {
             "what": "ragged-batch request latency (arrival -> result in the host buffer) through rsa_server_*, "
                     "256 keys of 1024-4096 bits, 1-64 messages per request, 70%% CRT / 30%% public, "
-                    "0.5 s of Poisson arrivals per rate, %d slots" % args.slots,
-            "sweep": [{"offered_req_per_s": r["offered_req_per_s"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
-                       "sustained_ops_per_s": r["sustained_ops_per_s"]} for r in sweep]}
+                    "0.5 s of Poisson arrivals per rate, %d slots, 2 GiB admission budget" % args.slots,
+            "sweep": rows,
+            "knee_req_per_s": max(x["offered_req_per_s"] for x in kept) if kept else None,
+            "saturated_ops_per_s": max((x["sustained_ops_per_s"] or 0) for x in rows)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -215,19 +215,25 @@ def rsa_last_error() -> str:
 
 
 def rsa_set_tuning(ctx: int, nbits: int, exp_sel: int, window: int = 0, warps_per_cta: int = 0,
-                   ctas_per_sm: int = 0, variant: int = 0, threads_per_op: int = 0, reset: bool = False) -> None:
+                   ctas_per_sm: int = 0, variant: int = 0, threads_per_op: int = 0, window_big: int = 0,
+                   window_tc: int = 0, tc_min_ops: int = 0, reset: bool = False) -> None:
     if reset:
         check(_lib.lib().rsa_set_tuning(ctx, nbits, exp_sel, None))
         return
-    t = rsa_tuning(window, warps_per_cta, ctas_per_sm, variant, threads_per_op)
+    t = rsa_tuning(window, warps_per_cta, ctas_per_sm, variant, threads_per_op, window_big, window_tc, tc_min_ops)
     check(_lib.lib().rsa_set_tuning(ctx, nbits, exp_sel, ctypes.byref(t)))
+
+
+def _tuning_dict(t) -> dict:
+    return {"window": t.window, "warps_per_cta": t.warps_per_cta, "ctas_per_sm": t.ctas_per_sm,
+            "variant": t.variant, "threads_per_op": t.threads_per_op, "window_big": t.window_big,
+            "window_tc": t.window_tc, "tc_min_ops": t.tc_min_ops}
 
 
 def rsa_get_tuning(ctx: int, nbits: int, exp_sel: int) -> dict:
     t = rsa_tuning()
     check(_lib.lib().rsa_get_tuning(ctx, nbits, exp_sel, ctypes.byref(t)))
-    return {"window": t.window, "warps_per_cta": t.warps_per_cta, "ctas_per_sm": t.ctas_per_sm,
-            "variant": t.variant, "threads_per_op": t.threads_per_op}
+    return _tuning_dict(t)
 
 
 def rsa_autotune(ctx: int, key_id: int, exp_sel: int, count: int, cache_path: str | None = None) -> dict:
@@ -236,18 +242,18 @@ def rsa_autotune(ctx: int, key_id: int, exp_sel: int, count: int, cache_path: st
     ms = ctypes.c_double()
     check(_lib.lib().rsa_autotune(ctx, key_id, exp_sel, count, cache_path.encode() if cache_path else None,
                                   ctypes.byref(t), ctypes.byref(ms)))
-    return {"window": t.window, "warps_per_cta": t.warps_per_cta, "ctas_per_sm": t.ctas_per_sm,
-            "variant": t.variant, "threads_per_op": t.threads_per_op, "ms": ms.value}
+    return dict(_tuning_dict(t), ms=ms.value)
 
 
 def rsa_autotune_batch(ctx: int, count: int, key_ids, exp_sel, limb_offsets, msgs, out) -> dict:
-    """Time the ragged batch under each lanes-per-operation policy and resident-CTA
-    cap; installs the fastest as the RSA_TUNE_RAGGED tuning and returns it."""
+    """Tune the ragged batch (lanes per operation, the tensor-core group, CRT
+    windows, resident-CTA cap); installs the fastest as the RSA_TUNE_RAGGED
+    tuning and returns it."""
     t = rsa_tuning()
     ms = ctypes.c_double()
     check(_lib.lib().rsa_autotune_batch(ctx, count, _ptr(key_ids), _ptr(exp_sel), _ptr(limb_offsets), _ptr(msgs),
                                         _ptr(out), ctypes.byref(t), ctypes.byref(ms)))
-    return {"ctas_per_sm": t.ctas_per_sm, "threads_per_op": t.threads_per_op, "ms": ms.value}
+    return dict(_tuning_dict(t), ms=ms.value)
 
 
 def rsa_get_stats(ctx: int) -> dict:

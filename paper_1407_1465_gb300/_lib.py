@@ -41,7 +41,8 @@ class RsaError(RuntimeError):
 
 class rsa_tuning(ctypes.Structure):
     _fields_ = [("window", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("variant", ctypes.c_int32), ("threads_per_op", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("variant", ctypes.c_int32), ("threads_per_op", ctypes.c_int32),
+                ("window_big", ctypes.c_int32), ("window_tc", ctypes.c_int32), ("tc_min_ops", ctypes.c_int32)]
 
 
 class rsa_stats(ctypes.Structure):

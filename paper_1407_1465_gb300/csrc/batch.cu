@@ -31,7 +31,7 @@ __global__ void plan_reset(BatchDesc d) {
     d.bcount[i] = 0u;
     d.bfill[i] = 0u;
   }
-  if (blockIdx.x == 0 && threadIdx.x < 16 && threadIdx.x != 2) d.ctl[threadIdx.x] = 0u;  // ranges, counters
+  if (blockIdx.x == 0 && threadIdx.x < tcr::kCtlWords && threadIdx.x != 2) d.ctl[threadIdx.x] = 0u;  // ranges, counters
 }
 
 // classify each operation into a bucket (key id * 3 + kind); invalid ones get a status
@@ -109,6 +109,8 @@ __global__ void __launch_bounds__(1024) plan_tiles(BatchDesc d) {
       }
       group = g;
     }
+    // a bucket's whole tensor-core tiles (if any) take its first operations;
+    // the CUDA-core tiles cover the rest
     uint32_t my_ops = 0, my_tiles = 0;
     for (uint32_t b = b0; b < b1; ++b) {
       const uint32_t c = d.bcount[b];
@@ -116,8 +118,9 @@ __global__ void __launch_bounds__(1024) plan_tiles(BatchDesc d) {
       const int32_t cls = batch_class(d.dir[b / 3].L, (int)(b % 3), d.wide_crt32);
       if (d.class_rank[cls] != rank) continue;
       const uint32_t to = (uint32_t)batch_tile_ops(cls);
+      const uint32_t rest = c - batch_tc_tiles(d, cls, d.dir[b / 3], c) * (uint32_t)tcr::kRows;
       my_ops += c;
-      my_tiles += (c + to - 1) / to;
+      my_tiles += (rest + to - 1) / to;
     }
     uint32_t tot_ops, tot_tiles;
     uint32_t op_off = op_base + block_exclusive_scan(my_ops, &tot_ops, sh);
@@ -129,9 +132,12 @@ __global__ void __launch_bounds__(1024) plan_tiles(BatchDesc d) {
       if (d.class_rank[cls] != rank) continue;
       const uint32_t to = (uint32_t)batch_tile_ops(cls);
       d.boff[b] = op_off;
-      const uint32_t nt = (c + to - 1) / to;
+      const uint32_t skip = batch_tc_tiles(d, cls, d.dir[b / 3], c) * (uint32_t)tcr::kRows;
+      const uint32_t rest = c - skip;
+      const uint32_t nt = (rest + to - 1) / to;
       for (uint32_t j = 0; j < nt && tile_off + j < d.max_tiles; ++j)
-        d.tiles[tile_off + j] = TileDesc{(int32_t)b, (int32_t)(op_off + j * to), (int32_t)min(to, c - j * to), cls};
+        d.tiles[tile_off + j] =
+            TileDesc{(int32_t)b, (int32_t)(op_off + skip + j * to), (int32_t)min(to, rest - j * to), cls};
       op_off += c;
       tile_off += nt;
     }
@@ -142,6 +148,29 @@ __global__ void __launch_bounds__(1024) plan_tiles(BatchDesc d) {
     d.ctl[1] = min(tile_base, d.max_tiles);
     if (group >= 0) d.ctl[8 + group] = min(tile_base, d.max_tiles);
   }
+  // tensor-core chunks: up to kTiles whole tiles of one bucket each
+  if (d.tc_min_ops) {
+    uint32_t my_chunks = 0;
+    for (uint32_t b = b0; b < b1; ++b) {
+      const uint32_t c = d.bcount[b];
+      if (!c) continue;
+      const uint32_t nt = batch_tc_tiles(d, batch_class(d.dir[b / 3].L, (int)(b % 3), d.wide_crt32), d.dir[b / 3], c);
+      my_chunks += (nt + tcr::kTiles - 1) / tcr::kTiles;
+    }
+    uint32_t tot_chunks;
+    uint32_t ch = block_exclusive_scan(my_chunks, &tot_chunks, sh);
+    for (uint32_t b = b0; b < b1; ++b) {
+      const uint32_t c = d.bcount[b];
+      if (!c) continue;
+      const KeyDirEntry e = d.dir[b / 3];
+      const uint32_t nt = batch_tc_tiles(d, batch_class(e.L, (int)(b % 3), d.wide_crt32), e, c);
+      for (uint32_t t0 = 0; t0 < nt; t0 += tcr::kTiles, ++ch)
+        if (ch < d.max_tc_chunks)
+          d.tc_chunks[ch] = tcr::TcChunk{e.rec, e.tc, (int32_t)(d.boff[b] + t0 * tcr::kRows),
+                                         (int32_t)min((uint32_t)tcr::kTiles, nt - t0)};
+    }
+    if (threadIdx.x == 0) d.ctl[tcr::kCtlTcChunks] = min(tot_chunks, d.max_tc_chunks);
+  }
 }
 
 __global__ void plan_scatter(BatchDesc d) {
@@ -151,6 +180,28 @@ __global__ void plan_scatter(BatchDesc d) {
     const uint32_t pos = d.boff[b] + atomicAdd(&d.bfill[b], 1u);
     d.sorted[pos] = (int32_t)i;
   }
+}
+
+// An order-independent digest of the result rows: sum over operations of a
+// mix of (operation index, row words); rows of unknown keys count as empty.
+__device__ __forceinline__ uint64_t digest_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+__global__ void batch_digest_kernel(uint32_t count, uint32_t nkeys, const KeyDirEntry *dir, const int32_t *key_ids,
+                                    const uint64_t *offsets, const uint32_t *out, unsigned long long *acc) {
+  uint64_t local = 0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    const int32_t k = key_ids[i];
+    if (k < 0 || (uint32_t)k >= nkeys || dir[k].rec == nullptr) continue;
+    const uint32_t L = dir[k].L;
+    const uint32_t *row = out + offsets[i];
+    uint64_t h = digest_mix(0x9e3779b97f4a7c15ull + i);
+    for (uint32_t j = 0; j < L; ++j) h = digest_mix(h ^ row[j]);
+    local += h;
+  }
+  atomicAdd(acc, (unsigned long long)local);
 }
 
 // Share (percent) of one wave of the four-lane group up to which a ragged
@@ -186,12 +237,16 @@ double class_cost(int32_t cls) {
 
 }  // namespace
 
+// the tensor-core chunk list follows the tile descriptors in the same buffer
+static size_t tc_chunks_offset(uint64_t max_tiles) { return ((size_t)max_tiles * sizeof(TileDesc) + 255) / 256 * 256; }
+
 struct BatchState {
   cudaStream_t stream = nullptr;
   bool built = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaGraphNode_t nodes[4 + GRP_COUNT] = {};
+  cudaGraphNode_t nodes[6 + GRP_COUNT] = {};
+  int tc_window = 0;          // window of the tensor-core node the graph was built with
   int exec_grid = 0;
   int grids_exec[GRP_COUNT] = {};
   DevBuf keydir;
@@ -294,7 +349,7 @@ int Ctx::prepare_batch(cudaStream_t s, uint64_t max_count) {
       const KeySlot &k = keys[i];
       if (!k.used) continue;
       const KeyHeader *hd = reinterpret_cast<const KeyHeader *>(k.host_rec.data());
-      dir[i] = KeyDirEntry{k.d_rec, k.L, k.flags, k.nbits, hd->e_bits};
+      dir[i] = KeyDirEntry{k.d_rec, k.L, k.flags, k.nbits, hd->e_bits, k.d_tc};
     }
     int rc = ensure(st->keydir, dir.size() * sizeof(KeyDirEntry));
     if (rc) return rc;
@@ -307,9 +362,19 @@ int Ctx::prepare_batch(cudaStream_t s, uint64_t max_count) {
   int rc;
   if ((rc = ensure(w.aux0, (size_t)max_count * 8)) ||                  // op_bucket + sorted
       (rc = ensure(w.aux1, (size_t)nb * 12)) ||                        // bcount, bfill, boff
-      (rc = ensure(w.aux2, (size_t)max_tiles * sizeof(TileDesc))) ||
-      (rc = ensure(w.aux3, 64)))
+      (rc = ensure(w.aux2, tc_chunks_offset(max_tiles) + (max_count / tcr::kRows + 1) * sizeof(tcr::TcChunk))) ||
+      (rc = ensure(w.aux3, tcr::kCtlWords * 4)))
     return rc;
+  const Tune tr = tune_for(0, RSA_TUNE_RAGGED);
+  const bool tc_possible = tr.variant != 1;
+  if (tc_possible) {
+    // the tensor-core group: one CTA per SM, the whole shared memory of an SM
+    const void *fn = tcr::ragged_tc_half_fn(tr.window_tc);
+    if (!fn) return set_error(RSA_ERR_ARG, "no tensor-core kernel for this window");
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcr::tc_smem_bytes());
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(ragged tensor-core kernel)");
+    if ((rc = ensure(w.halves, tcr::tc_halves_bytes((uint32_t)max_count)))) return rc;
+  }
   int max_grid = 0;
   for (int g = 0; g < GRP_COUNT; ++g) {
     const void *fn = batch_exec_fn(g);
@@ -328,8 +393,34 @@ int Ctx::prepare_batch(cudaStream_t s, uint64_t max_count) {
   // window tables: one per resident warp of each group (groups run concurrently),
   // each the size its group's largest class needs
   size_t table_u4 = 0;
-  for (int gi = 0; gi < GRP_COUNT; ++gi) table_u4 += (size_t)st->grids_exec[gi] * 2 * batch_table_u4(gi);
-  return ensure(w.tables, std::max<size_t>(table_u4, 1) * 16);
+  for (int gi = 0; gi < GRP_COUNT; ++gi)
+    table_u4 += (size_t)st->grids_exec[gi] * 2 * batch_table_u4(gi, tr.window, tr.window_big);
+  // then the tensor-core group's tables (one per tile slot of its sm_count CTAs)
+  const size_t tc_bytes = tc_possible ? tcr::tc_tables_bytes(sm_count, tr.window_tc) : 0;
+  return ensure(w.tables, std::max<size_t>(table_u4 * 16 + tc_bytes, 16));
+}
+
+int Ctx::batch_digest(uint64_t count, const int32_t *key_ids, const uint64_t *offsets, const uint32_t *out,
+                      cudaStream_t s, uint64_t *digest) {
+  BatchState *st = state_for(this, s);
+  Workspace &w = ws(s);
+  if (!st->keydir.ptr || !w.aux3.ptr) return set_error(RSA_ERR_ARG, "batch_digest before a ragged batch");
+  // the digest word sits in the control block's last word pair, after the planner's words
+  unsigned long long *acc = reinterpret_cast<unsigned long long *>(static_cast<uint32_t *>(w.aux3.ptr) + 30);
+  cudaError_t e = cudaMemsetAsync(acc, 0, 8, s);
+  if (e != cudaSuccess) return cuda_error(e, "digest reset");
+  const uint32_t nkeys = std::max<uint32_t>((uint32_t)keys.size(), 1);
+  const int grid = (int)std::min<uint64_t>((count + 255) / 256, (uint64_t)sm_count * 4);
+  batch_digest_kernel<<<std::max(grid, 1), 256, 0, s>>>((uint32_t)count, nkeys,
+                                                         static_cast<const KeyDirEntry *>(st->keydir.ptr), key_ids,
+                                                         offsets, out, acc);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "digest kernel");
+  unsigned long long h = 0;
+  if ((e = cudaMemcpyAsync(&h, acc, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_error(e, "digest read");
+  *digest = h;
+  return RSA_OK;
 }
 
 uint64_t Ctx::batch_wave_ops(cudaStream_t s) {
@@ -370,6 +461,8 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
   d.ctl = static_cast<uint32_t *>(w.aux3.ptr);
   d.tables = static_cast<uint4 *>(w.tables.ptr);
   d.max_tiles = max_tiles;
+  d.tc_chunks = reinterpret_cast<tcr::TcChunk *>(static_cast<char *>(w.aux2.ptr) + tc_chunks_offset(max_tiles));
+  d.max_tc_chunks = (uint32_t)(count / tcr::kRows + 1);
   // Small batches run 2048-bit CRT with four lanes per operation and 4096-bit
   // CRT with eight: each operation finishes sooner (about 2.2x at 2048 bits),
   // and while the batch fits in one wave of the multi-lane group (8 operations
@@ -382,6 +475,15 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
     wide = tpo == 4 ? 1 : tpo == 1 ? 0 : (count <= batch_wave_ops(s) ? 1 : 0);
   }
   d.wide_crt32 = wide != 0 ? 1u : 0u;
+  // windows of the CRT classes and the tensor-core group (the ragged tuning):
+  // the group takes 2048-bit CRT buckets in the throughput shapes, unless the
+  // tuning keeps every operation on the CUDA cores (variant 1) or asks for it
+  // in every shape (variant 3)
+  const Tune tr = tune_for(0, RSA_TUNE_RAGGED);
+  d.win_small = tr.window;
+  d.win_big = tr.window_big;
+  const bool tc_on = tr.variant == 3 || (tr.variant == 0 && !d.wide_crt32);
+  d.tc_min_ops = tc_on ? (uint32_t)std::max(tr.tc_min_ops, 1) : 0u;
   {
     std::vector<int32_t> order(CLS_COUNT);
     std::iota(order.begin(), order.end(), 0);
@@ -393,20 +495,52 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
   }
   const int g_ops = (int)std::min<uint64_t>((count + 255) / 256, (uint64_t)sm_count * 8);
   const int g_nb = (int)std::min<uint32_t>((nb + 255) / 256, (uint32_t)sm_count * 8);
-  // nodes: reset -> count -> tiles -> scatter -> {one persistent kernel per group} (run concurrently)
-  constexpr int kNodes = 4 + GRP_COUNT;
+  // nodes: reset -> count -> tiles -> scatter -> tensor-core exponentiation ->
+  // {tensor-core Garner, one persistent kernel per CUDA-core group} (run concurrently).
+  // The tensor-core kernel needs whole SMs (all registers, 210 KB of shared
+  // memory), so it runs before the persistent groups fill the SMs; without
+  // tensor-core work its CTAs leave at once.
+  constexpr int kNodes = 6 + GRP_COUNT;
+  constexpr int kTcNode = 4, kGarnerNode = 5, kGroup0 = 6;
+  const void *tc_fn = tcr::ragged_tc_half_fn(tr.window_tc);
+  if (!tc_fn) return set_error(RSA_ERR_ARG, "no tensor-core kernel for this window");
   const void *fns[kNodes] = {reinterpret_cast<const void *>(&plan_reset), reinterpret_cast<const void *>(&plan_count),
                              reinterpret_cast<const void *>(&plan_tiles), reinterpret_cast<const void *>(&plan_scatter),
+                             tc_fn, tcr::ragged_tc_garner_fn(),
                              batch_exec_fn(0), batch_exec_fn(1), batch_exec_fn(2), batch_exec_fn(3)};
-  dim3 grids[kNodes] = {dim3(std::max(1, g_nb)), dim3(g_ops), dim3(1), dim3(g_ops)};
-  dim3 blocks[kNodes] = {dim3(256), dim3(256), dim3(1024), dim3(256)};
-  size_t smems[kNodes] = {0, 0, 0, 0};
+  dim3 grids[kNodes] = {dim3(std::max(1, g_nb)), dim3(g_ops), dim3(1), dim3(g_ops),
+                        dim3(sm_count), dim3(sm_count * 4)};
+  dim3 blocks[kNodes] = {dim3(256), dim3(256), dim3(1024), dim3(256), dim3(tcr::kThreads),
+                         dim3(tcr::kRaggedGarnerThreads)};
+  size_t smems[kNodes] = {0, 0, 0, 0, tcr::tc_smem_bytes(), tcr::ragged_tc_garner_smem()};
   BatchDesc dg[kNodes];
   void *args[kNodes][1];
   for (int i = 0; i < kNodes; ++i) {
     dg[i] = d;
     args[i][0] = &dg[i];
   }
+  // the tensor-core nodes take their own argument block
+  size_t group_table_u4 = 0;
+  for (int gi = 0; gi < GRP_COUNT; ++gi)
+    group_table_u4 += (size_t)grids_exec[gi] * 2 * batch_table_u4(gi, d.win_small, d.win_big);
+  tcr::RaggedTcArgs ra{};
+  ra.chunks = d.tc_chunks;
+  ra.ctl = d.ctl;
+  ra.sorted = d.sorted;
+  ra.offsets = offsets;
+  ra.msgs = msgs;
+  ra.out = out;
+  ra.status = status;
+  ra.tables = d.tables + group_table_u4;
+  ra.halves = w.halves.ptr;
+  ra.count = (uint32_t)count;
+  ra.wait_polls = tcr::kDefaultWaitPolls;
+  if (const char *ev = std::getenv("RSAGPU_TC_WAIT_POLLS")) ra.wait_polls = (uint32_t)std::strtoul(ev, nullptr, 10);
+  if (tc_on && (!w.halves.ptr || w.halves.bytes < tcr::tc_halves_bytes((uint32_t)count) ||
+                w.tables.bytes < group_table_u4 * 16 + tcr::tc_tables_bytes(sm_count, tr.window_tc)))
+    return set_error(RSA_ERR_NOMEM, "tensor-core workspace of the ragged batch is missing");
+  args[kTcNode][0] = &ra;
+  args[kGarnerNode][0] = &ra;
   // each group's warps index their own slice of the table scratch
   size_t slot_off = 0;
   // a batch with few tiles launches only the CTAs it can use (at most one
@@ -416,11 +550,12 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
   static_assert(GRP_BIG == 0 && GRP_CRT == 1 && GRP_L64 == 2 && GRP_WIDE == 3, "tile_min order");
   for (int gi = 0; gi < GRP_COUNT; ++gi) {
     const uint64_t useful = count / tile_min[gi] + std::min<uint64_t>(nb, count) + 1;
-    grids[4 + gi] = dim3((unsigned)std::min<uint64_t>((uint64_t)grids_exec[gi], useful));
-    blocks[4 + gi] = dim3(64);
-    smems[4 + gi] = batch_exec_smem_bytes(gi);
-    dg[4 + gi].tables = d.tables + slot_off;
-    slot_off += (size_t)grids_exec[gi] * 2 * batch_table_u4(gi);
+    grids[kGroup0 + gi] = dim3((unsigned)std::min<uint64_t>((uint64_t)grids_exec[gi], useful));
+    blocks[kGroup0 + gi] = dim3(64);
+    smems[kGroup0 + gi] = batch_exec_smem_bytes(gi);
+    dg[kGroup0 + gi].tables = d.tables + slot_off;
+    dg[kGroup0 + gi].table_u4 = (uint32_t)batch_table_u4(gi, d.win_small, d.win_big);
+    slot_off += (size_t)grids_exec[gi] * 2 * dg[kGroup0 + gi].table_u4;
   }
   cudaError_t e;
   auto params = [&](int i) {
@@ -432,17 +567,28 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
     p.kernelParams = args[i];
     return p;
   };
+  if (st->built && st->tc_window != tr.window_tc) {
+    // the tensor-core node's kernel changed with its window: build the graph anew
+    cudaGraphExecDestroy(st->exec);
+    cudaGraphDestroy(st->graph);
+    st->exec = nullptr;
+    st->graph = nullptr;
+    st->built = false;
+  }
   if (!st->built) {
     if ((e = cudaGraphCreate(&st->graph, 0)) != cudaSuccess) return cuda_error(e, "cudaGraphCreate");
     for (int i = 0; i < kNodes; ++i) {
       cudaKernelNodeParams p = params(i);
-      const int dep = i < 4 ? i - 1 : 3;   // the group kernels all follow the scatter
+      // planning in sequence; the tensor-core kernel after the scatter; its
+      // Garner and the CUDA-core groups after the tensor-core kernel
+      const int dep = i <= kTcNode ? i - 1 : kTcNode;
       e = cudaGraphAddKernelNode(&st->nodes[i], st->graph, dep >= 0 ? &st->nodes[dep] : nullptr, dep >= 0 ? 1 : 0, &p);
       if (e != cudaSuccess) return cuda_error(e, "cudaGraphAddKernelNode");
     }
     if ((e = cudaGraphInstantiate(&st->exec, st->graph, 0)) != cudaSuccess)
       return cuda_error(e, "cudaGraphInstantiate");
     st->built = true;
+    st->tc_window = tr.window_tc;
   } else {
     for (int i = 0; i < kNodes; ++i) {
       cudaKernelNodeParams p = params(i);
@@ -452,7 +598,7 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
   }
   if ((e = cudaGraphLaunch(st->exec, s)) != cudaSuccess) return cuda_error(e, "cudaGraphLaunch");
   stats.graph_launches++;
-  stats.kernel_launches += 4 + GRP_COUNT;
+  stats.kernel_launches += kNodes;
   return RSA_OK;
 }
 

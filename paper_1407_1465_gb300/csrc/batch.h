@@ -10,6 +10,7 @@
 #pragma once
 #include <cstdint>
 
+#include "crt_tc.h"
 #include "keyrec.h"
 
 namespace rsagpu {
@@ -17,6 +18,7 @@ namespace rsagpu {
 struct KeyDirEntry {          // one per key id; rec == null for a free slot
   const uint32_t *rec;
   uint32_t L, flags, nbits, e_bits;
+  const void *tc;             // tensor-core operands (2048-bit keys with p, q), else null
 };
 
 struct TileDesc {
@@ -41,10 +43,18 @@ enum : int32_t {
   CLS_COUNT = 15
 };
 
-// Window widths the execution kernel is compiled with, per class (3072/4096-bit
-// CRT: 5; with 4 the 256-key ragged mix ran at 717 K ops/s against 732 K).
-constexpr int kBatchWindowCrt16 = 4, kBatchWindowCrt32 = 4, kBatchWindowCrt48 = 5, kBatchWindowCrt64 = 5;
+// Window widths of the CRT classes are chosen per batch (BatchDesc::win_small
+// for 1024/2048-bit keys, win_big for 3072/4096-bit keys; 4 or 5, the ragged
+// autotuner sweeps them); these are the defaults (3072/4096-bit CRT: 5; with 4
+// the 256-key ragged mix ran at 717 K ops/s against 732 K).  Plain private
+// exponents always use kBatchWindowPlain.
+constexpr int kBatchWindowSmall = 4, kBatchWindowBig = 5, kBatchWindowMax = 5;
 constexpr int kBatchWindowPlain = 4;
+// the tensor-core group: window 3 (tables stay in L2) or 4; a 2048-bit CRT
+// bucket sends its whole 128-operation tiles there once it holds at least
+// kBatchTcMinOps operations (the rest run on the CUDA cores)
+constexpr int kBatchWindowTc = 3;
+constexpr uint32_t kBatchTcMinOps = 128;
 
 // wide: run 2048-bit CRT with four lanes per operation (CLS_CRT32W) and
 // 4096-bit CRT with eight (CLS_CRT64W)
@@ -77,15 +87,19 @@ __host__ __device__ inline int32_t batch_group(int32_t cls) {
 
 // Window-table scratch per warp (uint4) of an execution group: 2^w entries of
 // (limbs per lane)/4 uint4 for each of the 32 lanes, for the largest class the
-// group runs (each call site checks its own need against this at compile time).
+// group runs at the batch's windows (win_small: 1024/2048-bit CRT, win_big:
+// 3072/4096-bit CRT).  The kernels index tables by BatchDesc::table_u4.
 __host__ __device__ constexpr size_t batch_table_need(int w, int limbs_per_lane) {
   return ((size_t)1 << w) * (size_t)(limbs_per_lane / 4) * 32;
 }
-__host__ __device__ constexpr size_t batch_table_u4(int group) {
-  return group == GRP_BIG   ? batch_table_need(5, 16)   // CRT H=64, w=5, four lanes: 16 limbs per lane
-         : group == GRP_CRT ? batch_table_need(4, 32)   // CRT H=32, w=4; plain L=32, w=4
-         : group == GRP_L64 ? batch_table_need(4, 64)   // plain L=64, w=4
-                            : batch_table_need(kBatchWindowPlain, 32);   // plain L=128, w=4, four lanes
+__host__ __device__ constexpr size_t batch_max(size_t a, size_t b) { return a > b ? a : b; }
+__host__ __device__ constexpr size_t batch_table_u4(int group, int win_small, int win_big) {
+  return group == GRP_BIG   ? batch_max(batch_table_need(win_big, 16),     // CRT H=64, four lanes (H=48: 12)
+                                        batch_table_need(win_small, 8))    // CRT H=32 on four lanes
+         : group == GRP_CRT ? batch_max(batch_table_need(win_small, 32),   // CRT H=32 (H=16: 16 limbs)
+                                        batch_table_need(kBatchWindowPlain, 32))   // plain L=32
+         : group == GRP_L64 ? batch_table_need(kBatchWindowPlain, 64)      // plain L=64
+                            : batch_table_need(kBatchWindowPlain, 32);     // plain L=128, four lanes
 }
 
 // operations per tile of a class: CRT 32 (warp pair on the same 32), wide CRT 8
@@ -114,11 +128,24 @@ struct BatchDesc {
   TileDesc *tiles;            // [max_tiles]
   uint32_t *ctl;              // [0] unused, [1] tile count, [2] error bits,
                               // [4+g] first tile of group g, [8+g] end, [12+g] counter (g < 4)
-  uint4 *tables;              // per resident warp of the group: batch_table_u4(group)
+  uint4 *tables;              // per resident warp of the group: table_u4 uint4
+  uint32_t table_u4;          // batch_table_u4(group, win_small, win_big) of the node's group
   uint32_t max_tiles;
   int32_t class_rank[CLS_COUNT];  // position of each class in the longest-first order
   uint32_t wide_crt32;        // small batch: 2048/4096-bit CRT as CLS_CRT32W / CLS_CRT64W
+  int32_t win_small, win_big; // CRT windows of 1024/2048-bit and of 3072/4096-bit keys (4 or 5)
+  // tensor-core group: 2048-bit CRT buckets of at least tc_min_ops operations
+  // (0: none) send floor(count / 128) whole tiles there, in chunks of up to
+  // tcr::kTiles tiles of one key; max_tc_chunks bounds the chunk list
+  uint32_t tc_min_ops, max_tc_chunks;
+  tcr::TcChunk *tc_chunks;
 };
+
+// whole tensor-core tiles a bucket of c operations sends to the tensor-core group
+__host__ __device__ inline uint32_t batch_tc_tiles(const BatchDesc &d, int32_t cls, const KeyDirEntry &e, uint32_t c) {
+  if (cls != CLS_CRT32 || d.tc_min_ops == 0 || e.tc == nullptr || c < d.tc_min_ops) return 0u;
+  return c / (uint32_t)tcr::kRows;
+}
 
 const void *batch_exec_fn(int group);
 size_t batch_exec_smem_bytes(int group);

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(64, G == GRP_BIG ? 8 : 1) batch_exec_kernel(Ba
   uint32_t *ks = reinterpret_cast<uint32_t *>(smem4);
   uint4 *work = smem4 + kKeyWordsMax / 4;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint4 *table_warp = d.tables + ((size_t)blockIdx.x * 2 + warp) * batch_table_u4(G);
+  uint4 *table_warp = d.tables + ((size_t)blockIdx.x * 2 + warp) * d.table_u4;
   const uint32_t first = d.ctl[4 + G], end = d.ctl[8 + G];
 #pragma unroll 1
   for (;;) {
@@ -140,17 +140,29 @@ __global__ void __launch_bounds__(64, G == GRP_BIG ? 8 : 1) batch_exec_kernel(Ba
       static_assert(stage_u4(3, 48, 8) * 16 <= work_bytes(GRP_BIG) && stage_u4(3, 64, 8) * 16 <= work_bytes(GRP_BIG) &&
                         stage_u4(3, 32, 8) * 16 <= work_bytes(GRP_BIG) && stage_u4(3, 64, 4) * 16 <= work_bytes(GRP_BIG),
                     "work area of a four/eight-lane CRT class");
-      static_assert(batch_table_need(kBatchWindowCrt48, 48 / 4) <= batch_table_u4(GRP_BIG) &&
-                        batch_table_need(kBatchWindowCrt64, 64 / 4) <= batch_table_u4(GRP_BIG) &&
-                        batch_table_need(kBatchWindowCrt32, 32 / 4) <= batch_table_u4(GRP_BIG) &&
-                        batch_table_need(kBatchWindowCrt64, 64 / 8) <= batch_table_u4(GRP_BIG),
+      // tables: win_big entries of 16 (H=64) or 12 (H=48) limbs per lane, win_small
+      // of 8 (H=32 on four lanes), win_big of 8 (H=64 on eight lanes)
+      static_assert(batch_table_need(5, 48 / 4) <= batch_table_u4(GRP_BIG, 4, 5) &&
+                        batch_table_need(4, 64 / 4) <= batch_table_u4(GRP_BIG, 4, 4) &&
+                        batch_table_need(5, 32 / 4) <= batch_table_u4(GRP_BIG, 5, 4) &&
+                        batch_table_need(5, 64 / 8) <= batch_table_u4(GRP_BIG, 4, 5),
                     "window table of a four/eight-lane CRT class");
-      if (td.cls == CLS_CRT48) run_crt4<48, kBatchWindowCrt48>(ks, work, table_warp, warp, lane, io_pair);
-      else if (td.cls == CLS_CRT64) run_crt4<64, kBatchWindowCrt64>(ks, work, table_warp, warp, lane, io_pair);
-      else if (td.cls == CLS_CRT32W) run_crt4<32, kBatchWindowCrt32>(ks, work, table_warp, warp, lane, io_pair);
-      else if (td.cls == CLS_CRT64W) run_crt8<64, kBatchWindowCrt64>(ks, work, table_warp, warp, lane, io_pair);
+      const bool w5big = d.win_big == 5, w5small = d.win_small == 5;
+      if (td.cls == CLS_CRT48) {
+        if (w5big) run_crt4<48, 5>(ks, work, table_warp, warp, lane, io_pair);
+        else run_crt4<48, 4>(ks, work, table_warp, warp, lane, io_pair);
+      } else if (td.cls == CLS_CRT64) {
+        if (w5big) run_crt4<64, 5>(ks, work, table_warp, warp, lane, io_pair);
+        else run_crt4<64, 4>(ks, work, table_warp, warp, lane, io_pair);
+      } else if (td.cls == CLS_CRT32W) {
+        if (w5small) run_crt4<32, 5>(ks, work, table_warp, warp, lane, io_pair);
+        else run_crt4<32, 4>(ks, work, table_warp, warp, lane, io_pair);
+      } else if (td.cls == CLS_CRT64W) {
+        if (w5big) run_crt8<64, 5>(ks, work, table_warp, warp, lane, io_pair);
+        else run_crt8<64, 4>(ks, work, table_warp, warp, lane, io_pair);
+      }
     } else if constexpr (G == GRP_L64) {
-      static_assert(batch_table_need(kBatchWindowPlain, 64) <= batch_table_u4(GRP_L64), "plain L=64 table");
+      static_assert(batch_table_need(kBatchWindowPlain, 64) <= batch_table_u4(GRP_L64, 4, 4), "plain L=64 table");
       static_assert(stage_u4(4, 64, 32) * 16 <= work_bytes(GRP_L64) && stage_u4(2, 64, 32) * 16 <= work_bytes(GRP_L64),
                     "work area of the L=64 classes");
       if (wn > 0) {
@@ -163,8 +175,8 @@ __global__ void __launch_bounds__(64, G == GRP_BIG ? 8 : 1) batch_exec_kernel(Ba
       static_assert(stage_u4(4, 128, 8) * 16 <= work_bytes(GRP_WIDE) && stage_u4(4, 96, 8) * 16 <= work_bytes(GRP_WIDE) &&
                         stage_u4(2, 128, 8) * 16 <= work_bytes(GRP_WIDE),
                     "work area of the wide public and plain classes");
-      static_assert(batch_table_need(kBatchWindowPlain, 128 / 4) <= batch_table_u4(GRP_WIDE) &&
-                        batch_table_need(kBatchWindowPlain, 96 / 4) <= batch_table_u4(GRP_WIDE),
+      static_assert(batch_table_need(kBatchWindowPlain, 128 / 4) <= batch_table_u4(GRP_WIDE, 4, 4) &&
+                        batch_table_need(kBatchWindowPlain, 96 / 4) <= batch_table_u4(GRP_WIDE, 4, 4),
                     "window table of a wide plain class");
       const TileIO io8{d.msgs, d.out, d.status, d.sorted, d.offsets, (uint32_t)(td.op_start + 8 * warp),
                        (uint32_t)wn8};
@@ -176,14 +188,21 @@ __global__ void __launch_bounds__(64, G == GRP_BIG ? 8 : 1) batch_exec_kernel(Ba
       static_assert(stage_u4(3, 32, 32) * 16 <= work_bytes(GRP_CRT) && stage_u4(4, 32, 32) * 16 <= work_bytes(GRP_CRT) &&
                         stage_u4(2, 32, 32) * 16 <= work_bytes(GRP_CRT),
                     "work area of the one-lane classes");
-      static_assert(batch_table_need(kBatchWindowCrt16, 16) <= batch_table_u4(GRP_CRT) &&
-                        batch_table_need(kBatchWindowCrt32, 32) <= batch_table_u4(GRP_CRT) &&
-                        batch_table_need(kBatchWindowPlain, 32) <= batch_table_u4(GRP_CRT),
+      static_assert(batch_table_need(5, 16) <= batch_table_u4(GRP_CRT, 5, 4) &&
+                        batch_table_need(5, 32) <= batch_table_u4(GRP_CRT, 5, 4) &&
+                        batch_table_need(kBatchWindowPlain, 32) <= batch_table_u4(GRP_CRT, 4, 4),
                     "window table of a one-lane class");
       const KeyHeader &hd = *reinterpret_cast<const KeyHeader *>(ks);
+      const bool w5 = d.win_small == 5;
       switch (td.cls) {
-        case CLS_CRT16: run_crt<16, kBatchWindowCrt16>(ks, work, table_warp, warp, lane, io_pair); break;
-        case CLS_CRT32: run_crt<32, kBatchWindowCrt32>(ks, work, table_warp, warp, lane, io_pair); break;
+        case CLS_CRT16:
+          if (w5) run_crt<16, 5>(ks, work, table_warp, warp, lane, io_pair);
+          else run_crt<16, 4>(ks, work, table_warp, warp, lane, io_pair);
+          break;
+        case CLS_CRT32:
+          if (w5) run_crt<32, 5>(ks, work, table_warp, warp, lane, io_pair);
+          else run_crt<32, 4>(ks, work, table_warp, warp, lane, io_pair);
+          break;
         case CLS_PUB32: if (wn > 0) run_pub<32>(ks, work, warp, lane, io_warp); break;
         case CLS_PLAIN32: if (wn > 0) run_plain<32>(ks, work, table_warp, warp, lane, io_warp); break;
         case CLS_TOY: {

@@ -446,46 +446,134 @@ __device__ __forceinline__ void stage_get(uint32_t (&A)[kH], const uint8_t *stag
   }
 }
 
-// ---------------------------------------------------------------- exponentiation kernel (both primes)
+// ---------------------------------------------------------------- one tile's exponentiation
+// x = c * R mod m from the message row, then the constant-time fixed window
+// over the prime's exponent (T[0] = R mod m, T[1] = x, T[i] = T[i-1] x; each
+// window W squarings and one product by T[digit]); the q half (pi == 0) leaves
+// Montgomery form, the p half stays in it for the recombination.  A is the
+// thread's result.
 template <int W>
-__global__ void __launch_bounds__(kThreads, 1) crt_tc_half_kernel(HalfArgs a) {
+__device__ __forceinline__ void exp_tile(uint32_t (&A)[kH], Tile &ts, const uint32_t *msg, uint32_t pi,
+                                         const uint32_t *kc, uint8_t *stage, uint32_t stage_sa, uint4 *tbl,
+                                         int r, uint32_t polls) {
+  using Wn = Win<W>;
+  const uint32_t *Ms = kc + kKm;
+  const NSmem<kH> N{Ms};
+  const uint32_t sb = ts.sb;
+  constexpr int ntab = Wn::kEntries;                  // steps 2 .. ntab-1 build T[2 .. ntab-1]
+  constexpr int nexp = (Wn::kNwin - 1) * (W + 1);
+  const int nst = ntab + nexp + (pi == 0 ? 1 : 0);
+  int k = Wn::kNwin - 2, s = 0;
+#pragma unroll 1
+  for (int st = 0; st < nst; ++st) {
+    uint32_t bsa = stage_sa, bstr = kKb;
+    bool sq = false;
+    if (st == 0) {                      // c_lo * R mod m
+      load_row<kH>(A, msg, true);
+      bsa = sb + kOffKey + 4 * kKr2;
+      bstr = 16;
+    } else if (st == 1) {               // c_hi * R^2 mod m
+      tbl_store<W>(tbl, 1, A);
+      load_row<kH>(A, msg + kH, true);
+      bsa = sb + kOffKey + 4 * kKr3;
+      bstr = 16;
+    } else if (st < ntab) {             // table T[i] = x^i * R, i = 2 .. ntab-1
+      if (st == 2) {
+        stage_from(stage, tbl + 1 * (kH / 4) * kRows, kRows);   // c_lo * R
+        mod_add<kH>(A, SmemB{reinterpret_cast<const uint4 *>(stage), kKb / 16}, N);   // x R = c R mod m
+        tbl_store<W>(tbl, 1, A);
+        uint32_t one[kH];
+        from_uniform<kH>(one, reinterpret_cast<const uint4 *>(kc + kKone));
+        tbl_store<W>(tbl, 0, one);
+        sq = true;                        // T[2] = x^2
+      } else {
+        tbl_store<W>(tbl, st - 1, A);
+      }
+      stage_from(stage, tbl + 1 * (kH / 4) * kRows, kRows);     // B = x R
+    } else if (st < ntab + nexp) {      // windows: W squarings, then T[digit]
+      if (st == ntab) {
+        tbl_store<W>(tbl, ntab - 1, A);
+        tbl_select<W>(stage, tbl, exp_digit<W>(kc + kKexp, (uint32_t)(Wn::kNwin - 1)));
+        stage_get(A, stage);
+      }
+      if (s < W) {
+        sq = true;
+        ++s;
+        if (RSAGPU_TC_PREFETCH > 0 && s == W + 1 - RSAGPU_TC_PREFETCH && ts.leader) {
+          const uint4 *tb = tbl - r;   // the slot's table: one contiguous block
+#pragma unroll 1
+          for (int e = 0; e < Wn::kEntries; ++e)
+            tc::prefetch_l2(tb + (size_t)e * (kH / 4) * kRows, (kH / 4) * kRows * 16);
+        }
+      } else {
+        tbl_select<W>(stage, tbl, exp_digit<W>(kc + kKexp, (uint32_t)k));
+        s = 0;
+        --k;
+      }
+    } else {                            // q: leave Montgomery form
+      bsa = sb + kOffKey + 4 * kKunit;
+      bstr = 16;
+    }
+    mont_step(A, sq, bsa, bstr, ts, Ms, polls);
+    if (ts.dead) break;
+  }
+}
+
+// key constants of prime pi (0: q, 1: p) into shared memory
+__device__ __forceinline__ void load_prime_consts(uint32_t *kc, const uint32_t *keyrec, uint32_t pi, int tid) {
+  constexpr KeyLayout lay(2 * kH);
+  const uint32_t om = pi ? lay.p : lay.q, or2 = pi ? lay.r2p : lay.r2q, or3 = pi ? lay.r3p : lay.r3q;
+  const uint32_t oone = pi ? lay.onep : lay.oneq, oexp = pi ? lay.dp : lay.dq;
+  for (int i = tid; i < kKeyWords; i += kThreads) {
+    uint32_t v;
+    if (i < kKr2) v = keyrec[om + i];
+    else if (i < kKr3) v = keyrec[or2 + i - kKr2];
+    else if (i < kKone) v = keyrec[or3 + i - kKr3];
+    else if (i < kKunit) v = keyrec[oone + i - kKone];
+    else if (i < kKexp) v = (i == kKunit) ? 1u : 0u;
+    else v = keyrec[oexp + i - kKexp];
+    kc[i] = v;
+  }
+}
+
+// B images of prime pi into shared memory
+__device__ __forceinline__ void load_prime_image(uint8_t *smem, const uint4 *image, uint32_t pi, int tid) {
+  const uint4 *img = image + (size_t)pi * (kImgPrime / 16);
+  uint4 *s4 = reinterpret_cast<uint4 *>(smem + kOffBm);
+  for (int i = tid; i < (int)(kImgPrime / 16); i += kThreads) s4[i] = img[i];
+}
+
+// ---------------------------------------------------------------- exponentiation kernel (both primes)
+// Uniform batches (RAGGED = false): one key; CTA 2c + pi runs prime pi, its
+// four tile slots take tiles round-robin.  Ragged batches (RAGGED = true): the
+// CTA repeatedly takes a work item (chunk, prime) from a counter, loads that
+// key's constants and operands, and runs the chunk's tiles in its slots.
+template <int W, bool RAGGED>
+__device__ __forceinline__ void half_body(const HalfArgs &a, const RaggedTcArgs &ra) {
   using Wn = Win<W>;
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int slot = warp >> 2;                   // tile slot 0 .. kTiles-1
   const int r = ((warp & 3) << 5) | lane;       // operation within the tile = TMEM lane
-  const uint32_t pi = blockIdx.x & 1u;          // 0: q, 1: p
-  const uint32_t cta = blockIdx.x >> 1;
   const uint32_t sb = tc::smem_addr(smem);
   uint32_t *ctrl = reinterpret_cast<uint32_t *>(smem + kOffCtrl);
+  if constexpr (RAGGED) {
+    // CTAs beyond the planned work items leave before touching TMEM
+    if (blockIdx.x >= 2u * ra.ctl[kCtlTcChunks]) return;
+  }
 
   if (warp == 0) tc::tmem_alloc(sb + kOffCtrl + 48, kTmemCols);
   if (tid == 0) {
     for (int t = 0; t < kTiles; ++t) tc::mbar_init(sb + kOffCtrl + 8 * t, 1u);
     tc::mbar_init_fence();
   }
-  // key constants of this prime
-  constexpr KeyLayout lay(2 * kH);
   uint32_t *kc = reinterpret_cast<uint32_t *>(smem + kOffKey);
-  {
-    const uint32_t om = pi ? lay.p : lay.q, or2 = pi ? lay.r2p : lay.r2q, or3 = pi ? lay.r3p : lay.r3q;
-    const uint32_t oone = pi ? lay.onep : lay.oneq, oexp = pi ? lay.dp : lay.dq;
-    for (int i = tid; i < kKeyWords; i += kThreads) {
-      uint32_t v;
-      if (i < kKr2) v = a.keyrec[om + i];
-      else if (i < kKr3) v = a.keyrec[or2 + i - kKr2];
-      else if (i < kKone) v = a.keyrec[or3 + i - kKr3];
-      else if (i < kKunit) v = a.keyrec[oone + i - kKone];
-      else if (i < kKexp) v = (i == kKunit) ? 1u : 0u;
-      else v = a.keyrec[oexp + i - kKexp];
-      kc[i] = v;
-    }
+  if constexpr (!RAGGED) {
+    load_prime_consts(kc, a.keyrec, blockIdx.x & 1u, tid);
+    load_prime_image(smem, a.image, blockIdx.x & 1u, tid);
   }
-  // B images of this prime and the constant bias A block (2^-16 = fp16 0x0100)
   {
-    const uint4 *img = a.image + (size_t)pi * (kImgPrime / 16);
-    uint4 *s4 = reinterpret_cast<uint4 *>(smem + kOffBm);
-    for (int i = tid; i < (int)(kImgPrime / 16); i += kThreads) s4[i] = img[i];
+    // the constant bias A block (2^-16 = fp16 0x0100)
     uint4 *ab = reinterpret_cast<uint4 *>(smem + kOffAbias);
     for (int i = tid; i < kRows * 16 * 2 / 16; i += kThreads)
       ab[i] = make_uint4(0x01000100u, 0x01000100u, 0x01000100u, 0x01000100u);
@@ -509,83 +597,64 @@ __global__ void __launch_bounds__(kThreads, 1) crt_tc_half_kernel(HalfArgs a) {
   ts.err = false;
   ts.dead = false;
 
-  const uint32_t *Ms = kc + kKm;
-  const NSmem<kH> N{Ms};
   uint8_t *stage = smem + (ts.arow - sb) + kStageKb * kKb;   // this thread's stage (generic pointer)
   const uint32_t stage_sa = ts.arow + kStageKb * kKb;
-  uint4 *tbl = a.tables + (size_t)(blockIdx.x * kTiles + slot) * Wn::kTblU4 + r;
+  uint4 *tbl = (RAGGED ? static_cast<uint4 *>(ra.tables) : a.tables) +
+               (size_t)(blockIdx.x * kTiles + slot) * Wn::kTblU4 + r;
 
-  for (uint32_t tile = cta + a.ctas_per_prime * (uint32_t)slot; tile < a.ntiles;
-       tile += a.ctas_per_prime * kTiles) {
-    const uint32_t row = tile * kRows + (uint32_t)r;
-    const bool valid = row < a.count;
-    const uint32_t *msg = a.msgs + (size_t)(valid ? row : a.count - 1) * (2 * kH);
-    uint32_t A[kH];
-    if (!ts.dead) {
-      constexpr int ntab = Wn::kEntries;                  // steps 2 .. ntab-1 build T[2 .. ntab-1]
-      constexpr int nexp = (Wn::kNwin - 1) * (W + 1);
-      const int nst = ntab + nexp + (pi == 0 ? 1 : 0);
-      int k = Wn::kNwin - 2, s = 0;
-#pragma unroll 1
-      for (int st = 0; st < nst; ++st) {
-        uint32_t bsa = stage_sa, bstr = kKb;
-        bool sq = false;
-        if (st == 0) {                      // c_lo * R mod m
-          load_row<kH>(A, msg, true);
-          bsa = sb + kOffKey + 4 * kKr2;
-          bstr = 16;
-        } else if (st == 1) {               // c_hi * R^2 mod m
-          tbl_store<W>(tbl, 1, A);
-          load_row<kH>(A, msg + kH, true);
-          bsa = sb + kOffKey + 4 * kKr3;
-          bstr = 16;
-        } else if (st < ntab) {             // table T[i] = x^i * R, i = 2 .. ntab-1
-          if (st == 2) {
-            stage_from(stage, tbl + 1 * (kH / 4) * kRows, kRows);   // c_lo * R
-            mod_add<kH>(A, SmemB{reinterpret_cast<const uint4 *>(stage), kKb / 16}, N);   // x R = c R mod m
-            tbl_store<W>(tbl, 1, A);
-            uint32_t one[kH];
-            from_uniform<kH>(one, reinterpret_cast<const uint4 *>(kc + kKone));
-            tbl_store<W>(tbl, 0, one);
-            sq = true;                        // T[2] = x^2
-          } else {
-            tbl_store<W>(tbl, st - 1, A);
-          }
-          stage_from(stage, tbl + 1 * (kH / 4) * kRows, kRows);     // B = x R
-        } else if (st < ntab + nexp) {      // windows: W squarings, then T[digit]
-          if (st == ntab) {
-            tbl_store<W>(tbl, ntab - 1, A);
-            tbl_select<W>(stage, tbl, exp_digit<W>(kc + kKexp, (uint32_t)(Wn::kNwin - 1)));
-            stage_get(A, stage);
-          }
-          if (s < W) {
-            sq = true;
-            ++s;
-            if (RSAGPU_TC_PREFETCH > 0 && s == W + 1 - RSAGPU_TC_PREFETCH && ts.leader) {
-              const uint4 *tb = tbl - r;   // the slot's table: one contiguous block
-#pragma unroll 1
-              for (int e = 0; e < Wn::kEntries; ++e)
-                tc::prefetch_l2(tb + (size_t)e * (kH / 4) * kRows, (kH / 4) * kRows * 16);
-            }
-          } else {
-            tbl_select<W>(stage, tbl, exp_digit<W>(kc + kKexp, (uint32_t)k));
-            s = 0;
-            --k;
-          }
-        } else {                            // q: leave Montgomery form
-          bsa = sb + kOffKey + 4 * kKunit;
-          bstr = 16;
-        }
-        mont_step(A, sq, bsa, bstr, ts, Ms, a.wait_polls);
-        if (ts.dead) break;
+  if constexpr (!RAGGED) {
+    const uint32_t pi = blockIdx.x & 1u;          // 0: q, 1: p
+    const uint32_t cta = blockIdx.x >> 1;
+    for (uint32_t tile = cta + a.ctas_per_prime * (uint32_t)slot; tile < a.ntiles;
+         tile += a.ctas_per_prime * kTiles) {
+      const uint32_t row = tile * kRows + (uint32_t)r;
+      const bool valid = row < a.count;
+      const uint32_t *msg = a.msgs + (size_t)(valid ? row : a.count - 1) * (2 * kH);
+      uint32_t A[kH];
+      if (!ts.dead) exp_tile<W>(A, ts, msg, pi, kc, stage, stage_sa, tbl, r, a.wait_polls);
+      if (valid) {
+        uint4 *h = a.halves + (size_t)pi * (kH / 4) * a.count_pad + row;
+#pragma unroll
+        for (int g = 0; g < kH / 4; ++g)
+          h[(size_t)g * a.count_pad] = make_uint4(A[4 * g], A[4 * g + 1], A[4 * g + 2], A[4 * g + 3]);
+        a.herr[(size_t)pi * a.count + row] = (ts.err || ts.dead) ? 1u : 0u;
       }
     }
-    if (valid) {
-      uint4 *h = a.halves + (size_t)pi * (kH / 4) * a.count_pad + row;
+  } else {
+    const uint32_t nitems = 2u * ra.ctl[kCtlTcChunks];
+    const uint32_t cpad = (ra.count + 31u) & ~31u;
+    uint4 *halves = static_cast<uint4 *>(ra.halves);
+    uint32_t *herr = reinterpret_cast<uint32_t *>(halves + (size_t)2 * (kH / 4) * cpad);
+#pragma unroll 1
+    for (;;) {
+      // every slot is done with the previous item's constants and operands (its
+      // MMAs have completed: each slot waited for them), so they may be replaced
+      tc::fence_before_sync();
+      __syncthreads();
+      if (tid == 0) ctrl[8] = atomicAdd(&ra.ctl[kCtlTcNext], 1u);
+      __syncthreads();
+      const uint32_t item = ctrl[8];
+      if (item >= nitems) break;
+      const TcChunk ch = ra.chunks[item >> 1];
+      const uint32_t pi = item & 1u;
+      load_prime_consts(kc, ch.keyrec, pi, tid);
+      load_prime_image(smem, static_cast<const uint4 *>(ch.image), pi, tid);
+      tc::fence_proxy_async_smem();
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+      if (slot < ch.ntiles) {
+        const uint32_t pos = (uint32_t)ch.op_start + (uint32_t)slot * kRows + (uint32_t)r;
+        const uint32_t op = (uint32_t)ra.sorted[pos];
+        const uint32_t *msg = ra.msgs + ra.offsets[op];
+        uint32_t A[kH];
+        if (!ts.dead) exp_tile<W>(A, ts, msg, pi, kc, stage, stage_sa, tbl, r, ra.wait_polls);
+        uint4 *h = halves + (size_t)pi * (kH / 4) * cpad + pos;
 #pragma unroll
-      for (int g = 0; g < kH / 4; ++g)
-        h[(size_t)g * a.count_pad] = make_uint4(A[4 * g], A[4 * g + 1], A[4 * g + 2], A[4 * g + 3]);
-      a.herr[(size_t)pi * a.count + row] = (ts.err || ts.dead) ? 1u : 0u;
+        for (int g = 0; g < kH / 4; ++g)
+          h[(size_t)g * cpad] = make_uint4(A[4 * g], A[4 * g + 1], A[4 * g + 2], A[4 * g + 3]);
+        herr[(size_t)pi * ra.count + pos] = (ts.err || ts.dead) ? 1u : 0u;
+      }
     }
   }
   // a tile that gave up may still have an MMA in flight: wait for it (bounded,
@@ -599,54 +668,56 @@ __global__ void __launch_bounds__(kThreads, 1) crt_tc_half_kernel(HalfArgs a) {
   }
 }
 
+template <int W>
+__global__ void __launch_bounds__(kThreads, 1) crt_tc_half_kernel(HalfArgs a) {
+  half_body<W, false>(a, RaggedTcArgs{});
+}
+template <int W>
+__global__ void __launch_bounds__(kThreads, 1) crt_tc_ragged_half_kernel(RaggedTcArgs ra) {
+  half_body<W, true>(HalfArgs{}, ra);
+}
+
 // ---------------------------------------------------------------- Garner recombination
 // m = m_q + q * ((m_p - m_q) * qinv mod p), one thread per operation, with the
 // CIOS Montgomery product of mont.cuh (modulus p from shared memory).
 constexpr int kGThreads = 256;
 constexpr int kGKeyWords = (KeyLayout(2 * kH).total + 3) / 4 * 4;
 constexpr int kGSmem = kGKeyWords * 4 + (kGThreads / 32) * (kH / 4) * 32 * 16;
+constexpr int kRGSmem = kGKeyWords * 4 + (kRaggedGarnerThreads / 32) * (kH / 4) * 32 * 16;
 
-__global__ void __launch_bounds__(kGThreads) crt_tc_garner_kernel(GarnerArgs a) {
+// One operation: hq / hp are its m_q and m_p * R mod p (kH/4 uint4, `hstride`
+// apart); ks the key record in shared memory; stage_lane the thread's slot of
+// a [kH/4][32] uint4 stage.  Writes the L-limb row at orow (zeros unless ok)
+// and returns the status (0, RSA_ERR_RANGE -3 or RSA_ERR_TIMEOUT -6).
+__device__ __forceinline__ int32_t garner_op(const uint32_t *ks, uint4 *stage_lane, const uint4 *hq, const uint4 *hp,
+                                             size_t hstride, bool timed_out, const uint32_t *mrow, uint4 *orow,
+                                             bool valid) {
   constexpr int L = 2 * kH;
   constexpr KeyLayout lay(L);
-  extern __shared__ uint4 gsm[];
-  uint32_t *ks = reinterpret_cast<uint32_t *>(gsm);
-  for (int i = threadIdx.x; i < kGKeyWords / 4; i += kGThreads)
-    gsm[i] = (i * 4 < (int)lay.total) ? reinterpret_cast<const uint4 *>(a.keyrec)[i] : make_uint4(0u, 0u, 0u, 0u);
-  __syncthreads();
   const KeyHeader &hd = *reinterpret_cast<const KeyHeader *>(ks);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t row = blockIdx.x * kGThreads + threadIdx.x;
-  const bool valid = row < a.count;
-  const uint32_t rr = valid ? row : 0u;
-  uint4 *stage_lane = gsm + kGKeyWords / 4 + warp * (kH / 4) * 32 + lane;
   const NSmem<kH> N{ks + lay.p};
-  const uint4 *hq = a.halves + rr, *hp = a.halves + (size_t)(kH / 4) * a.count_pad + rr;
   uint32_t A[kH];
 #pragma unroll
   for (int g = 0; g < kH / 4; ++g) {
-    const uint4 v = hq[(size_t)g * a.count_pad];
+    const uint4 v = hq[(size_t)g * hstride];
     A[4 * g] = v.x; A[4 * g + 1] = v.y; A[4 * g + 2] = v.z; A[4 * g + 3] = v.w;
   }
   mont_mul<kH, 8>(A, SmemB{reinterpret_cast<const uint4 *>(ks + lay.r2p), 1}, N, hd.np_p);   // m_q * R mod p
 #pragma unroll
-  for (int g = 0; g < kH / 4; ++g) stage_lane[g * 32] = hp[(size_t)g * a.count_pad];         // m_p * R mod p
+  for (int g = 0; g < kH / 4; ++g) stage_lane[g * 32] = hp[(size_t)g * hstride];            // m_p * R mod p
   mod_rsub<kH>(A, SmemB{stage_lane, 32}, N);                                                  // (m_p - m_q) R
   mont_mul<kH, 8>(A, SmemB{reinterpret_cast<const uint4 *>(ks + lay.qinv), 1}, N, hd.np_p);  // h
   uint32_t t[kH + 2];
 #pragma unroll
   for (int g = 0; g < kH / 4; ++g) {
-    const uint4 v = hq[(size_t)g * a.count_pad];
+    const uint4 v = hq[(size_t)g * hstride];
     t[4 * g] = v.x; t[4 * g + 1] = v.y; t[4 * g + 2] = v.z; t[4 * g + 3] = v.w;
   }
   t[kH] = 0u;
   t[kH + 1] = 0u;
   const uint32_t *qs = ks + lay.q;
-  const uint32_t *mrow = a.msgs + (size_t)rr * L;
   const bool below = row_below(mrow, ks + lay.n, L);
-  const bool timed_out = a.herr[rr] != 0u || a.herr[a.count + rr] != 0u;
   const bool ok = valid && below && !timed_out;
-  uint4 *orow = reinterpret_cast<uint4 *>(a.out + (size_t)rr * L);
 #pragma unroll 1
   for (int i0 = 0; i0 < kH; i0 += 4) {
     uint32_t rv[4];
@@ -665,7 +736,59 @@ __global__ void __launch_bounds__(kGThreads) crt_tc_garner_kernel(GarnerArgs a) 
     if (valid)
       orow[kH / 4 + g] = ok ? make_uint4(t[4 * g], t[4 * g + 1], t[4 * g + 2], t[4 * g + 3])
                             : make_uint4(0u, 0u, 0u, 0u);
-  if (valid && a.status) a.status[rr] = timed_out ? -6 /* RSA_ERR_TIMEOUT */ : (below ? 0 : -3 /* RSA_ERR_RANGE */);
+  return timed_out ? -6 /* RSA_ERR_TIMEOUT */ : (below ? 0 : -3 /* RSA_ERR_RANGE */);
+}
+
+__global__ void __launch_bounds__(kGThreads) crt_tc_garner_kernel(GarnerArgs a) {
+  constexpr KeyLayout lay(2 * kH);
+  extern __shared__ uint4 gsm[];
+  uint32_t *ks = reinterpret_cast<uint32_t *>(gsm);
+  for (int i = threadIdx.x; i < kGKeyWords / 4; i += kGThreads)
+    gsm[i] = (i * 4 < (int)lay.total) ? reinterpret_cast<const uint4 *>(a.keyrec)[i] : make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t row = blockIdx.x * kGThreads + threadIdx.x;
+  const bool valid = row < a.count;
+  const uint32_t rr = valid ? row : 0u;
+  uint4 *stage_lane = gsm + kGKeyWords / 4 + warp * (kH / 4) * 32 + lane;
+  const bool timed_out = a.herr[rr] != 0u || a.herr[a.count + rr] != 0u;
+  const int32_t st = garner_op(ks, stage_lane, a.halves + rr, a.halves + (size_t)(kH / 4) * a.count_pad + rr,
+                               a.count_pad, timed_out, a.msgs + (size_t)rr * 2 * kH,
+                               reinterpret_cast<uint4 *>(a.out + (size_t)rr * 2 * kH), valid);
+  if (valid && a.status) a.status[rr] = st;
+}
+
+// Ragged batches: block b takes the (chunk, slot) tiles b, b + grid, ... of the
+// planned chunks; one thread per operation of the tile, the tile's key record
+// in shared memory.  Timeouts are also flagged in the batch's error word.
+__global__ void __launch_bounds__(kRaggedGarnerThreads) crt_tc_ragged_garner_kernel(RaggedTcArgs ra) {
+  constexpr KeyLayout lay(2 * kH);
+  extern __shared__ uint4 gsm[];
+  uint32_t *ks = reinterpret_cast<uint32_t *>(gsm);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint4 *stage_lane = gsm + kGKeyWords / 4 + warp * (kH / 4) * 32 + lane;
+  const uint32_t ntile_slots = (uint32_t)kTiles * ra.ctl[kCtlTcChunks];
+  const uint32_t cpad = (ra.count + 31u) & ~31u;
+  const uint4 *halves = static_cast<const uint4 *>(ra.halves);
+  const uint32_t *herr = reinterpret_cast<const uint32_t *>(halves + (size_t)2 * (kH / 4) * cpad);
+#pragma unroll 1
+  for (uint32_t t = blockIdx.x; t < ntile_slots; t += gridDim.x) {
+    const TcChunk ch = ra.chunks[t / kTiles];
+    const int s = (int)(t % kTiles);
+    if (s >= ch.ntiles) continue;   // uniform over the block
+    __syncthreads();                // the previous tile's key record is no longer read
+    for (int i = threadIdx.x; i < kGKeyWords / 4; i += kRaggedGarnerThreads)
+      gsm[i] = (i * 4 < (int)lay.total) ? reinterpret_cast<const uint4 *>(ch.keyrec)[i] : make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    const uint32_t pos = (uint32_t)ch.op_start + (uint32_t)s * kRows + threadIdx.x;
+    const uint32_t op = (uint32_t)ra.sorted[pos];
+    const size_t off = (size_t)ra.offsets[op];
+    const bool timed_out = herr[pos] != 0u || herr[ra.count + pos] != 0u;
+    const int32_t st = garner_op(ks, stage_lane, halves + pos, halves + (size_t)(kH / 4) * cpad + pos, cpad,
+                                 timed_out, ra.msgs + off, reinterpret_cast<uint4 *>(ra.out + off), true);
+    if (ra.status) ra.status[op] = st;
+    if (timed_out) atomicOr(&ra.ctl[2], 1u << 6);   // RSA_ERR_TIMEOUT for rsa_sync
+  }
 }
 
 // ---------------------------------------------------------------- host side
@@ -698,6 +821,14 @@ static cudaError_t launch_half(const HalfArgs &h, int grid, cudaStream_t s) {
   crt_tc_half_kernel<W><<<grid, kThreads, kSmem, s>>>(h);
   return cudaGetLastError();
 }
+
+const void *ragged_tc_half_fn(int window) {
+  if (window == 3) return reinterpret_cast<const void *>(&crt_tc_ragged_half_kernel<3>);
+  if (window == 4) return reinterpret_cast<const void *>(&crt_tc_ragged_half_kernel<4>);
+  return nullptr;
+}
+const void *ragged_tc_garner_fn() { return reinterpret_cast<const void *>(&crt_tc_ragged_garner_kernel); }
+size_t ragged_tc_garner_smem() { return (size_t)kRGSmem; }
 
 cudaError_t launch_crt_tc(const uint32_t *keyrec, const void *image, const uint32_t *msgs, uint32_t *out,
                           int32_t *status, uint32_t count, int grid, int window, void *tables, void *halves,

@@ -31,6 +31,24 @@ size_t tc_halves_bytes(uint32_t count);
 int tc_grid(uint32_t count, int sm_count);
 size_t tc_smem_bytes();
 
+// Ragged batches: the tensor-core group takes whole 128-operation tiles of
+// 2048-bit CRT buckets, grouped into chunks of up to kTiles tiles of one key
+// (one CTA runs a chunk's tiles side by side, one prime at a time).  The
+// planner writes the chunk list; the operations of a chunk are the entries
+// op_start .. op_start + 128 * ntiles - 1 of the batch's sorted operation list.
+struct TcChunk {
+  const uint32_t *keyrec;   // device key record (keyrec.h)
+  const void *image;        // the key's tensor-core operands (q image, then p image)
+  int32_t op_start;         // first position in the sorted list
+  int32_t ntiles;           // 1 .. kTiles full tiles
+};
+// control words of the ragged tensor-core group inside the batch's control
+// block (words 0-15: the planner's ranges and counters, 30-31: the ragged
+// autotuner's result digest)
+constexpr int kCtlTcChunks = 16;   // chunks planned
+constexpr int kCtlTcNext = 17;     // work-item counter of the exponentiation kernel (2 items per chunk)
+constexpr int kCtlWords = 32;      // size of the control block in words
+
 #if defined(__CUDACC__)
 // Enqueues the two-prime exponentiation kernel and the recombination kernel.
 // wait_polls bounds every wait on an MMA's completion (kDefaultWaitPolls in
@@ -40,6 +58,26 @@ constexpr uint32_t kDefaultWaitPolls = 1u << 22;
 cudaError_t launch_crt_tc(const uint32_t *keyrec, const void *image, const uint32_t *msgs, uint32_t *out,
                           int32_t *status, uint32_t count, int grid, int window, void *tables, void *halves,
                           uint32_t wait_polls, cudaStream_t s);
+
+// Arguments of the ragged tensor-core kernels (one struct for both, so the
+// batch graph passes the same parameter block to each).
+struct RaggedTcArgs {
+  const TcChunk *chunks;
+  uint32_t *ctl;                // control block (kCtlTc* words; error bits in word 2)
+  const int32_t *sorted;        // batch position -> operation index
+  const uint64_t *offsets;      // operation -> limb offset of its row
+  const uint32_t *msgs;
+  uint32_t *out;
+  int32_t *status;
+  void *tables;                 // tc_tables_bytes(grid, window)
+  void *halves;                 // tc_halves_bytes(count), indexed by sorted position
+  uint32_t count, wait_polls;
+};
+// kernel entry points for the batch graph (window 3 or 4)
+const void *ragged_tc_half_fn(int window);
+const void *ragged_tc_garner_fn();
+constexpr int kRaggedGarnerThreads = 128;
+size_t ragged_tc_garner_smem();
 #endif
 
 }  // namespace tcr

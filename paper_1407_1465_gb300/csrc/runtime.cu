@@ -104,7 +104,7 @@ static int default_window(uint32_t L, int kind) {
 }
 
 Tune Ctx::tune_for(uint32_t nbits, int kind) const {
-  Tune t{0, 0, 0, 0, 0};
+  Tune t{0, 0, 0, 0, 0, 0, 0, 0};
   auto it = tuning.find({nbits, kind});
   if (it != tuning.end()) t = it->second;
   const uint32_t L = nbits / 32;
@@ -120,7 +120,16 @@ Tune Ctx::tune_for(uint32_t nbits, int kind) const {
   // 48/64 limbs need 255 registers on one lane and 128 on four (RSA-4096 CRT:
   // 127 K/s -> 145 K/s), and the one-lane public exponent of those sizes spills --
   // one lane otherwise (RSA-2048 CRT: 1.24 M/s on one lane, 1.10 M on two).
-  if (kind == RSA_TUNE_RAGGED) return t;   // ragged batches: 0 fields stay automatic
+  if (kind == RSA_TUNE_RAGGED) {
+    // ragged batches: CRT windows 4 (1024/2048-bit) and 5 (3072/4096-bit),
+    // tensor-core group at window 3 for buckets of at least one whole tile;
+    // the lanes-per-operation policy and the variant stay automatic (0)
+    if (!t.window) t.window = 4;
+    if (!t.window_big) t.window_big = 5;
+    if (!t.window_tc) t.window_tc = 3;
+    if (!t.tc_min_ops) t.tc_min_ops = 128;
+    return t;
+  }
   if (!t.tpo) t.tpo = L > 64 ? 4 : 1;
   return t;
 }
@@ -615,11 +624,24 @@ int rsa_set_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, const rsa_tuni
   if (t->variant < 0 || t->variant > 3) return set_error(RSA_ERR_ARG, "variant must be 0 .. 3");
   if (!(t->threads_per_op == 0 || t->threads_per_op == 1 || t->threads_per_op == 2 || t->threads_per_op == 4))
     return set_error(RSA_ERR_ARG, "threads_per_op must be 0, 1, 2 or 4");
-  if (exp_sel == RSA_TUNE_RAGGED && t->threads_per_op == 2)
-    return set_error(RSA_ERR_ARG, "ragged batches: threads_per_op must be 0 (automatic), 1 or 4");
+  if (exp_sel == RSA_TUNE_RAGGED) {
+    if (t->threads_per_op == 2)
+      return set_error(RSA_ERR_ARG, "ragged batches: threads_per_op must be 0 (automatic), 1 or 4");
+    if (!(t->window == 0 || t->window == 4 || t->window == 5) || !(t->window_big == 0 || t->window_big == 4 ||
+                                                                   t->window_big == 5))
+      return set_error(RSA_ERR_ARG, "ragged batches: CRT windows must be 0 (automatic), 4 or 5");
+    if (!(t->window_tc == 0 || t->window_tc == 3 || t->window_tc == 4))
+      return set_error(RSA_ERR_ARG, "ragged batches: the tensor-core window must be 0 (automatic), 3 or 4");
+    if (!(t->variant == 0 || t->variant == 1 || t->variant == 3))
+      return set_error(RSA_ERR_ARG, "ragged batches: variant must be 0 (automatic), 1 or 3");
+    if (t->tc_min_ops < 0) return set_error(RSA_ERR_ARG, "ragged batches: tc_min_ops must be >= 0");
+  } else if (t->window_big || t->window_tc || t->tc_min_ops) {
+    return set_error(RSA_ERR_ARG, "window_big, window_tc and tc_min_ops apply to RSA_TUNE_RAGGED only");
+  }
   if (exp_sel == RSA_EXP_PRIVATE_CRT && (t->warps_per_cta & 1))
     return set_error(RSA_ERR_ARG, "CRT kernels run warp pairs: warps_per_cta must be even");
-  c->tuning[{nbits, exp_sel}] = Tune{t->window, t->warps_per_cta, t->ctas_per_sm, t->variant, t->threads_per_op};
+  c->tuning[{nbits, exp_sel}] = Tune{t->window,     t->warps_per_cta, t->ctas_per_sm, t->variant,
+                                     t->threads_per_op, t->window_big, t->window_tc,  t->tc_min_ops};
   return RSA_OK;
 }
 
@@ -633,6 +655,9 @@ int rsa_get_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, rsa_tuning *t)
   t->ctas_per_sm = x.ctas_per_sm;
   t->variant = x.variant;
   t->threads_per_op = x.tpo;
+  t->window_big = x.window_big;
+  t->window_tc = x.window_tc;
+  t->tc_min_ops = x.tc_min_ops;
   return RSA_OK;
 }
 

@@ -55,6 +55,7 @@ struct KeySlot {
 
 struct Tune {
   int window, warps_per_cta, ctas_per_sm, variant, tpo;
+  int window_big, window_tc, tc_min_ops;   // ragged batches only (rsa_tuning)
 };
 
 struct Ctx {
@@ -90,6 +91,10 @@ struct Ctx {
                 const uint32_t *msgs, uint32_t *out, int32_t *status, cudaStream_t s, int wide = -1);
   // operations one wave of the multi-lane group holds (after prepare_batch on s)
   uint64_t batch_wave_ops(cudaStream_t s);
+  // an order-independent 64-bit digest of the result rows of a ragged batch
+  // (after run_batch on s with the same arguments); synchronises s
+  int batch_digest(uint64_t count, const int32_t *key_ids, const uint64_t *offsets, const uint32_t *out,
+                   cudaStream_t s, uint64_t *digest);
   int collect_device_errors(cudaStream_t s);
   // Free everything the library keeps for stream s (its ragged-batch graph and
   // key directory, its workspace buffers) before the caller destroys s.

@@ -166,11 +166,15 @@ extern "C" int rsa_autotune(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint6
   return RSA_OK;
 }
 
-// Ragged batches: time the caller's batch under each lanes-per-operation
-// policy of the long CRT sizes (one/four lanes, four/eight lanes) and each cap
-// on resident CTAs per SM of the persistent groups (occupancy maximum, 2, 4),
-// keep the fastest as the RSA_TUNE_RAGGED tuning.  Window widths and tiles are
-// fixed per work class (batch.h).
+// Ragged batches: coordinate descent over the RSA_TUNE_RAGGED tuning on the
+// caller's own batch.  Each parameter in turn takes every value it may have
+// while the others keep their best values so far: the lanes-per-operation
+// policy of the long CRT sizes, the tensor-core group (off / on, the smallest
+// bucket it takes, its window), the CRT windows of 1024/2048-bit and of
+// 3072/4096-bit keys, and the cap on resident CTAs per SM of the persistent
+// groups.  A candidate is the median of three timed runs after a warm-up; its
+// results must equal the first candidate's (a digest of every output row), or
+// the candidate is not taken.
 extern "C" int rsa_autotune_batch(rsa_ctx *ctx, uint64_t count, const int32_t *key_ids, const uint8_t *exp_sel,
                                   const uint64_t *limb_offsets, const uint32_t *msgs, uint32_t *out,
                                   rsa_tuning *best, double *best_ms) {
@@ -184,39 +188,74 @@ extern "C" int rsa_autotune_batch(rsa_ctx *ctx, uint64_t count, const int32_t *k
   cudaSetDevice(c->device);
   const std::pair<uint32_t, int> tk{0u, RSA_TUNE_RAGGED};
   const bool had = c->tuning.count(tk) != 0;
-  const Tune saved = had ? c->tuning[tk] : Tune{0, 0, 0, 0, 0};
+  const Tune saved = had ? c->tuning[tk] : Tune{};
   cudaStream_t s = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_error(e, "autotune stream");
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  double best_t = 1e30;
-  Tune chosen{0, 0, 0, 0, 0};
   int err = RSA_OK;
-  for (int tpo : {1, 4}) {
-    for (int cps : {0, 2, 4}) {
-      c->tuning[tk] = Tune{0, 0, cps, 0, tpo};
-      if (c->run_batch(count, key_ids, exp_sel, limb_offsets, msgs, out, nullptr, s) != RSA_OK) continue;
-      float t3[3];
-      for (int r = 0; r < 3 && !err; ++r) {
-        cudaEventRecord(a, s);
-        if ((err = c->run_batch(count, key_ids, exp_sel, limb_offsets, msgs, out, nullptr, s))) break;
-        cudaEventRecord(b, s);
-        if ((e = cudaEventSynchronize(b)) != cudaSuccess) {
-          err = cuda_error(e, "autotune batch run");
-          break;
-        }
-        cudaEventElapsedTime(&t3[r], a, b);
+  bool have_ref = false;
+  uint64_t ref_digest = 0;
+  int mismatches = 0;
+  // time one candidate: the median of three runs (infinite if it does not run or disagrees)
+  auto measure = [&](const Tune &cand) -> double {
+    c->tuning[tk] = cand;
+    if (c->run_batch(count, key_ids, exp_sel, limb_offsets, msgs, out, nullptr, s) != RSA_OK) return 1e30;
+    uint64_t dg = 0;
+    if ((err = c->batch_digest(count, key_ids, limb_offsets, out, s, &dg))) return 1e30;
+    if (!have_ref) {
+      have_ref = true;
+      ref_digest = dg;
+    } else if (dg != ref_digest) {
+      ++mismatches;
+      return 1e30;
+    }
+    float t3[3];
+    for (int r = 0; r < 3; ++r) {
+      cudaEventRecord(a, s);
+      if ((err = c->run_batch(count, key_ids, exp_sel, limb_offsets, msgs, out, nullptr, s))) return 1e30;
+      cudaEventRecord(b, s);
+      if ((e = cudaEventSynchronize(b)) != cudaSuccess) {
+        err = cuda_error(e, "autotune batch run");
+        return 1e30;
       }
+      cudaEventElapsedTime(&t3[r], a, b);
+    }
+    std::sort(t3, t3 + 3);
+    return t3[1];
+  };
+  struct Dim {
+    int Tune::*field;
+    std::vector<int> values;
+  };
+  const Dim dims[] = {{&Tune::tpo, {1, 4}},          {&Tune::variant, {0, 1, 3}},    {&Tune::tc_min_ops, {128, 512}},
+                      {&Tune::window_tc, {3, 4}},     {&Tune::window, {4, 5}},        {&Tune::window_big, {5, 4}},
+                      {&Tune::ctas_per_sm, {0, 2, 4}}};
+  Tune chosen{};
+  chosen.window = 4;
+  chosen.window_big = 5;
+  chosen.window_tc = 3;
+  chosen.tc_min_ops = 128;
+  chosen.tpo = 1;
+  double best_t = measure(chosen);
+  int candidates = 1;
+  for (const Dim &d : dims) {
+    if (err) break;
+    const int incumbent = chosen.*(d.field);
+    for (int v : d.values) {
+      if (v == incumbent) continue;
+      Tune cand = chosen;
+      cand.*(d.field) = v;
+      const double t = measure(cand);
+      ++candidates;
       if (err) break;
-      std::sort(t3, t3 + 3);
-      if (t3[1] < best_t) {
-        best_t = t3[1];
-        chosen = Tune{0, 0, cps, 0, tpo};
+      if (t < best_t) {
+        best_t = t;
+        chosen = cand;
       }
     }
-    if (err) break;
   }
   // operations the batch itself rejects leave error bits on the stream: read
   // and clear them so they do not surface at the caller's next rsa_sync
@@ -230,13 +269,19 @@ extern "C" int rsa_autotune_batch(rsa_ctx *ctx, uint64_t count, const int32_t *k
     else c->tuning.erase(tk);
     return err ? err : set_error(RSA_ERR_UNSUPPORTED, "no launch shape ran for this batch");
   }
+  if (mismatches)
+    return set_error(RSA_ERR_CUDA, "ragged autotuner: " + std::to_string(mismatches) + " of " +
+                                       std::to_string(candidates) + " configurations gave different results");
   c->tuning[tk] = chosen;
   if (best) {
-    best->window = 0;
+    best->window = chosen.window;
     best->warps_per_cta = 0;
     best->ctas_per_sm = chosen.ctas_per_sm;
-    best->variant = 0;
+    best->variant = chosen.variant;
     best->threads_per_op = chosen.tpo;
+    best->window_big = chosen.window_big;
+    best->window_tc = chosen.window_tc;
+    best->tc_min_ops = chosen.tc_min_ops;
   }
   if (best_ms) *best_ms = best_t;
   return RSA_OK;

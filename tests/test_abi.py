@@ -152,9 +152,11 @@ def test_tuning_dict_has_every_field():
     from paper_1407_1465_gb300 import _lib
     import inspect
     import paper_1407_1465_gb300 as pkg
-    src = inspect.getsource(pkg.rsa_get_tuning) + inspect.getsource(pkg.rsa_autotune)
+    src = inspect.getsource(pkg._tuning_dict)
     for name, _ in _lib.rsa_tuning._fields_:
-        assert src.count('"%s"' % name) >= 2, name
+        assert ('"%s": t.%s' % (name, name)) in src, name
+    for fn in (pkg.rsa_get_tuning, pkg.rsa_autotune, pkg.rsa_autotune_batch):
+        assert "_tuning_dict(t)" in inspect.getsource(fn)
 
 
 def test_null_context_is_an_argument_error(lib):

@@ -189,8 +189,9 @@ def test_ragged_full_workload_sampled(torch_cuda, ctx):
 
 
 def test_ragged_autotune_batch(torch_cuda, ctx, mixed_keys):
-    """The ragged autotuner times the batch under each lanes-per-operation policy
-    and CTA cap, installs the fastest, and results stay exact under it."""
+    """The ragged autotuner (coordinate descent over lanes per operation, the
+    tensor-core group, the CRT windows and the CTA cap) installs the fastest
+    configuration, and results stay exact under it."""
     from paper_1407_1465_gb300 import RSA_TUNE_RAGGED, RsaError
     keys, kids = mixed_keys
     ops, key_ids, sels, offsets, packed = build_mix(keys, kids, 300, 77)
@@ -202,13 +203,20 @@ def test_ragged_autotune_batch(torch_cuda, ctx, mixed_keys):
     try:
         best = ctx.autotune_batch(k, s, o, m)
         assert best["threads_per_op"] in (1, 4) and best["ctas_per_sm"] in (0, 2, 4) and best["ms"] > 0
+        assert best["window"] in (4, 5) and best["window_big"] in (4, 5) and best["window_tc"] in (3, 4)
+        assert best["variant"] in (0, 1, 3) and best["tc_min_ops"] in (128, 512)
         t = ctx.get_tuning(0, RSA_TUNE_RAGGED)
-        assert t["threads_per_op"] == best["threads_per_op"] and t["ctas_per_sm"] == best["ctas_per_sm"]
+        for f in ("threads_per_op", "ctas_per_sm", "window", "window_big", "window_tc", "variant", "tc_min_ops"):
+            assert t[f] == best[f], f
         out, st, rc = run_batch(torch_cuda, ctx, key_ids, sels, offsets, packed)
         assert rc == 0 and (st == 0).all()
         for (kk, kind, row), off in zip(ops, offsets):
             assert np.array_equal(out[int(off):int(off) + row.size], expect_one(keys[kk], kind, row))
         with pytest.raises(RsaError):
             ctx.set_tuning(0, RSA_TUNE_RAGGED, threads_per_op=2)
+        with pytest.raises(RsaError):
+            ctx.set_tuning(0, RSA_TUNE_RAGGED, window_tc=5)
+        with pytest.raises(RsaError):
+            ctx.set_tuning(2048, CRT, window_big=4)    # ragged-only fields
     finally:
         ctx.set_tuning(0, RSA_TUNE_RAGGED, reset=True)
