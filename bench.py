@@ -492,7 +492,7 @@ def run_bgcd(args):
     return 0
 
 
-def ragged_measure(steps: int, warmup: int, autotune: bool = False, loop_steps: int = 0) -> dict:
+def ragged_measure(steps: int, warmup: int, autotune: bool = False, loop_steps: int = 0, loop: bool = True) -> dict:
     """The ragged workload (256 keys, 200000 operations, one rsa_modexp_batch
     -- one graph launch -- per step) timed with CUDA events, against a loop of
     one rsa_modexp_key launch per (key, kind) group over the same operations.
@@ -544,9 +544,11 @@ def ragged_measure(steps: int, warmup: int, autotune: bool = False, loop_steps: 
         for kid, sel, n, t, o, _ in gbufs:
             rsa_modexp_key(ctx.handle, kid, sel, n, t, o, None, sptr)
 
-    res = {}
-    for name, fn, k_steps, k_warm in (("ragged", step_ragged, steps, warmup),
-                                      ("loop", step_loop, loop_steps or steps, min(warmup, 1 if loop_steps else warmup))):
+    res = {"loop": float("nan")}
+    legs = [("ragged", step_ragged, steps, warmup)]
+    if loop:
+        legs.append(("loop", step_loop, loop_steps or steps, min(warmup, 1 if loop_steps else warmup)))
+    for name, fn, k_steps, k_warm in legs:
         for _ in range(k_warm):
             fn()
         torch.cuda.synchronize()
@@ -561,7 +563,7 @@ def ragged_measure(steps: int, warmup: int, autotune: bool = False, loop_steps: 
         raise RuntimeError("ragged batch reported errors")
     # the loop's results must equal the ragged batch's, and sampled ones the oracle's
     got = out.cpu().numpy().view(np.uint32)
-    for kid, sel, n, t, o, idx in gbufs[:40]:
+    for kid, sel, n, t, o, idx in (gbufs[:40] if loop else []):
         oo = o.cpu().numpy().view(np.uint32)
         for j, i in enumerate(idx[:4]):
             off = int(rb.offsets[i])
@@ -590,7 +592,7 @@ def run_ragged(args):
     """Ragged batch: 256 keys, 200000 operations, one rsa_modexp_batch (one graph
     launch) per step, against a loop of one rsa_modexp_key launch per
     (key, kind) group over the same operations."""
-    r = ragged_measure(args.steps, args.warmup, args.autotune)
+    r = ragged_measure(args.steps, args.warmup, args.autotune, loop=not args.no_loop)
     line = {
         "metric": "ragged-batch ops/sec (256 keys, 200000 ops, one graph launch)",
         "value": r["value"], "unit": "ops/s", "n_gpus": 1, "steps": args.steps,
@@ -778,6 +780,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-latency", action="store_true", help="skip the serving-latency sweep of the default run")
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch measurement of the default run")
+    ap.add_argument("--no-loop", action="store_true", help="ragged: skip the one-key-per-launch comparison")
     ap.add_argument("--autotune", action="store_true", help="ragged: run the ragged autotuner on the batch first")
     args = ap.parse_args()
     if args.workload == "ragged":

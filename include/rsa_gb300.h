@@ -236,22 +236,27 @@ int rsa_crt_decrypt_noalloc(const uint32_t *key_record, uint32_t nbits, uint64_t
                             const uint32_t *msgs, uint32_t *out, int32_t *op_status, void *stream);
 
 /* ---------------------------------------------------------------- serving
- * A request loop on top of rsa_modexp_batch.  A scheduler thread admits
- * requests when they have arrived and their device footprint fits the budget,
- * packs admitted requests of one modulus size (any keys and kinds of that size;
- * the oldest waiting request picks the size) into one ragged batch per free
- * slot, and runs up to max_inflight_batches batches at once on separate
+ * A request loop on top of rsa_modexp_batch.  A scheduler thread packs
+ * requests that have arrived, of one modulus size (any keys and kinds of that
+ * size; the oldest waiting request picks the size), into one ragged batch per
+ * free slot, and runs up to max_inflight_batches batches at once on separate
  * streams, so requests arriving while others are on the GPU start without
  * waiting for them (continuous batching) and a batch finishes at its own size's
- * latency.  Key state stays resident in the context.  Results are copied into
- * each request's host buffer. */
+ * latency.  Admission is by bytes in flight: every batch takes a range of one
+ * device arena of mem_budget_bytes (messages, results and per-operation
+ * metadata: 8L + 17 bytes per operation, plus alignment), and a batch that does
+ * not fit in a free range waits until batches in flight finish and give their
+ * ranges back.  Key state stays resident in the context.  Results are copied
+ * into each request's host buffer. */
 typedef struct rsa_server_cfg {
     int32_t max_inflight_batches; /* concurrent batches (streams); 0 -> 16 */
     int32_t batch_window_us;      /* wait this long after the first arrival for more; 0 -> 200 */
-    int32_t max_batch_ops;        /* operations per batch; 0 -> 65536 */
+    int32_t max_batch_ops;        /* operations per batch (and per request); 0 -> 65536 */
     int32_t flags;                /* RSA_SERVER_MIX_SIZES: a batch takes requests of every
                                      modulus size (default: one size per batch, see above) */
-    uint64_t mem_budget_bytes;    /* device bytes for in-flight requests; 0 -> 2 GiB */
+    uint64_t mem_budget_bytes;    /* device bytes for in-flight requests (one arena, counted
+                                     against the context's budget; the loop also pins the same
+                                     amount of host memory for staging); 0 -> 2 GiB */
 } rsa_server_cfg;
 #define RSA_SERVER_MIX_SIZES 1
 
@@ -268,7 +273,7 @@ typedef struct rsa_request {
 
 typedef struct rsa_server_stats {
     uint64_t submitted, completed, rejected, ops_completed, batches;
-    uint64_t peak_bytes;          /* largest device footprint of in-flight requests */
+    uint64_t peak_bytes;          /* largest arena footprint of the batches in flight */
     double p50_us, p99_us, mean_us, max_us;   /* request latency: arrival -> result in host buffer */
     double span_s;                /* first arrival -> last completion */
 } rsa_server_stats;
@@ -276,8 +281,10 @@ typedef struct rsa_server_stats {
 /* Start the request loop of `ctx` (one per context).  The buffers a request
  * points to must stay valid until it completes. */
 int rsa_server_start(rsa_ctx *ctx, const rsa_server_cfg *cfg);
-/* Queue a request; *ticket identifies it.  RSA_ERR_NOMEM when the request alone
- * exceeds the budget, RSA_ERR_KEY / RSA_ERR_ARG for a bad key or kind. */
+/* Queue a request; *ticket identifies it.  A request that fits the budget is
+ * never refused for lack of room: it waits for batches in flight.  RSA_ERR_NOMEM
+ * when the request alone exceeds the budget (or holds more than max_batch_ops
+ * messages), RSA_ERR_KEY / RSA_ERR_ARG for a bad key or kind. */
 int rsa_server_submit(rsa_ctx *ctx, const rsa_request *req, uint64_t *ticket);
 /* Queue n requests at once (in arrival order); tickets (n entries) may be NULL.
  * Stops at the first refused request and returns its error; *accepted (may be
@@ -329,6 +336,13 @@ typedef struct rsa_tuning {
                               (4 above 2048 bits, else 1).  PRIVATE_PLAIN takes 1 up to
                               2048 bits and 4 above; other combinations without a kernel
                               return RSA_ERR_UNSUPPORTED from the launching call */
+    /* The last three fields apply to RSA_TUNE_RAGGED only (0 elsewhere): */
+    int32_t window_big;    /* fixed-window width of 3072/4096-bit CRT (4 or 5; 0 = 5) */
+    int32_t window_tc;     /* window of the tensor-core group (3 or 4; 0 = 3) */
+    int32_t tc_min_ops;    /* a 2048-bit CRT bucket (one key) of at least this many
+                              operations sends its whole 128-operation tiles to the
+                              tensor-core group, up to four tiles of one key per CTA;
+                              0 = 128 */
 } rsa_tuning;
 
 /* Set (or, with NULL, reset to automatic) the launch parameters used for keys of
@@ -337,7 +351,13 @@ typedef struct rsa_tuning {
  * CTAs per SM of its persistent kernels, threads_per_op picks the lanes per
  * operation of 2048/4096-bit CRT (1: one/four lanes, the throughput shapes; 4:
  * four/eight lanes, the latency shapes; 0: automatic, the latency shapes while
- * the work fits one wave of the GPU); the other fields do not apply. */
+ * the work fits one wave of the GPU); window is the CRT window of 1024/2048-bit
+ * keys (4 or 5; 0 = 4), window_big that of 3072/4096-bit keys, window_tc and
+ * tc_min_ops shape the tensor-core group; variant 3 sends 2048-bit CRT buckets
+ * of at least tc_min_ops operations to the tensor-core group, 1 keeps every
+ * operation on the CUDA cores, 0 (automatic) uses the group except in the
+ * latency shapes; warps_per_cta does not apply.  Errors: RSA_ERR_ARG for values
+ * outside these ranges. */
 #define RSA_TUNE_RAGGED 3
 int rsa_set_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, const rsa_tuning *t);
 /* Read the parameters currently in force for (nbits, exp_sel). */

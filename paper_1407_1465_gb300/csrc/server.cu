@@ -10,7 +10,10 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <iterator>
+#include <map>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -35,26 +38,81 @@ struct Req {
   uint32_t *out = nullptr;
   int32_t *status = nullptr;
   uint64_t arrive = 0;   // steady-clock ns
-  uint64_t bytes = 0;    // device footprint
   int32_t state = 0;     // 0 queued, 1 in flight, 2 done, < 0 failed
   uint64_t done = 0;
 };
 
-// one in-flight batch: a stream, its staging buffers and the requests it carries
+// First-fit allocator over the byte range [0, size) of the in-flight arenas
+// (host-side bookkeeping only); ranges are multiples of 256 bytes and freed
+// ranges merge with their neighbours.
+class Arena {
+ public:
+  void init(size_t size) {
+    free_.clear();
+    size_ = size / 256 * 256;
+    if (size_) free_[0] = size_;
+  }
+  size_t size() const { return size_; }
+  size_t largest() const {
+    size_t m = 0;
+    for (const auto &kv : free_) m = std::max(m, kv.second);
+    return m;
+  }
+  bool alloc(size_t n, size_t *off) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < n) continue;
+      *off = it->first;
+      const size_t rest = it->second - n;
+      const size_t at = it->first + n;
+      free_.erase(it);
+      if (rest) free_[at] = rest;
+      return true;
+    }
+    return false;
+  }
+  void release(size_t off, size_t n) {
+    auto next = free_.lower_bound(off);
+    if (next != free_.end() && off + n == next->first) {
+      n += next->second;
+      next = free_.erase(next);
+    }
+    if (next != free_.begin()) {
+      auto prev = std::prev(next);
+      if (prev->first + prev->second == off) {
+        prev->second += n;
+        return;
+      }
+    }
+    free_[off] = n;
+  }
+
+ private:
+  std::map<size_t, size_t> free_;
+  size_t size_ = 0;
+};
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Bytes a batch of `ops` operations and `limbs` message limbs takes in the
+// arenas: key ids, kinds, row offsets and statuses (each 256-byte aligned),
+// then messages and results of `limbs` limbs each (rounded up to 4 limbs).
+size_t batch_bytes(uint64_t ops, uint64_t limbs) {
+  const uint64_t l4 = (limbs + 3) / 4 * 4;
+  return align256(ops * 4) + align256(ops) + align256(ops * 8) + align256(ops * 4) + align256(l4 * 4) * 2;
+}
+
+// one in-flight batch: a stream, its range of the arenas and the requests it carries
 struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
   bool busy = false;
-  size_t cap_bytes = 0;                 // device bytes for messages + results + metadata
-  uint32_t cap_ops = 0, cap_limbs = 0;
-  // pinned host staging
+  size_t off = 0, len = 0;              // the batch's range of the arenas
+  // views into the pinned host arena and the device arena at [off, off + len)
   int32_t *h_keys = nullptr;
   uint8_t *h_sel = nullptr;
   uint64_t *h_off = nullptr;
   uint32_t *h_msgs = nullptr, *h_out = nullptr;
   int32_t *h_status = nullptr;
-  // device buffers
-  void *d_buf = nullptr;
   int32_t *d_keys = nullptr;
   uint8_t *d_sel = nullptr;
   uint64_t *d_off = nullptr;
@@ -62,7 +120,6 @@ struct Slot {
   int32_t *d_status = nullptr;
   std::vector<Req *> reqs;
   std::vector<uint64_t> req_off;        // first limb of each request in the staging buffers
-  uint64_t bytes = 0;
   uint32_t ops = 0;
 };
 
@@ -80,6 +137,12 @@ struct Server {
   std::deque<Req *> queue;                      // not yet admitted, in submission order
   std::unordered_map<uint64_t, Req *> all;      // every request not yet retired
   std::vector<Slot> slots;
+  // in-flight requests live in two arenas of mem_budget_bytes at the same
+  // offsets: device memory (messages, results, metadata) and pinned host
+  // staging for the copies
+  void *d_arena = nullptr, *h_arena = nullptr;
+  size_t arena_reserved = 0;
+  Arena arena;
   uint64_t inflight_bytes = 0, peak_bytes = 0;
   uint64_t inflight_ops = 0, wave_ops = 0;       // operations on the GPU; one multi-lane wave
   uint64_t pending = 0;                         // submitted and not finished
@@ -92,60 +155,31 @@ struct Server {
   int init();
   void release();
   void loop();
-  bool launch(Slot &s, std::vector<Req *> &batch);
+  bool launch(Slot &s, std::vector<Req *> &batch, uint64_t ops, uint64_t limbs);
   void finish(Slot &s);
 };
 
-namespace {
-size_t align256(size_t x) { return (x + 255) / 256 * 256; }
-}
-
 int Server::init() {
   const int n = cfg.max_inflight_batches;
-  const size_t per_slot = cfg.mem_budget_bytes / (size_t)n;
+  const size_t budget = (size_t)cfg.mem_budget_bytes / 256 * 256;
+  if (budget < batch_bytes(1, 128)) return set_error(RSA_ERR_ARG, "memory budget too small for one request");
+  cudaError_t e;
+  int rc = ctx->reserve(budget);
+  if (rc) return rc;
+  arena_reserved = budget;
+  if ((e = cudaMalloc(&d_arena, budget)) != cudaSuccess)
+    return set_error(RSA_ERR_NOMEM, std::string("server device arena: ") + cudaGetErrorString(e));
+  if ((e = cudaMallocHost(&h_arena, budget)) != cudaSuccess) return cuda_error(e, "server pinned arena");
+  arena.init(budget);
   slots.resize(n);
   for (Slot &s : slots) {
-    s.cap_bytes = per_slot;
-    // per operation: key id 4 + kind 1 + offset 8 + status 4 (+ padding) ~ 24 bytes of metadata
-    s.cap_ops = (uint32_t)std::min<size_t>((size_t)cfg.max_batch_ops, per_slot / 64);
-    const size_t meta = align256((size_t)s.cap_ops * 4) + align256(s.cap_ops) + align256((size_t)s.cap_ops * 8) +
-                        align256((size_t)s.cap_ops * 4);
-    if (per_slot <= meta + 4096) return set_error(RSA_ERR_ARG, "memory budget too small for the slot count");
-    // messages + results; a multiple of 4 limbs keeps the result area 16-byte aligned
-    s.cap_limbs = (uint32_t)std::min<size_t>((per_slot - meta) / 8, 0xfffffff0u) & ~3u;
-    cudaError_t e;
     if ((e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming)) != cudaSuccess)
       return cuda_error(e, "server stream/event");
-    if ((e = cudaMallocHost(&s.h_keys, (size_t)s.cap_ops * 4)) != cudaSuccess ||
-        (e = cudaMallocHost(&s.h_sel, s.cap_ops)) != cudaSuccess ||
-        (e = cudaMallocHost(&s.h_off, (size_t)s.cap_ops * 8)) != cudaSuccess ||
-        (e = cudaMallocHost(&s.h_status, (size_t)s.cap_ops * 4)) != cudaSuccess ||
-        (e = cudaMallocHost(&s.h_msgs, (size_t)s.cap_limbs * 4)) != cudaSuccess ||
-        (e = cudaMallocHost(&s.h_out, (size_t)s.cap_limbs * 4)) != cudaSuccess)
-      return cuda_error(e, "server pinned staging");
-    const size_t dev = meta + (size_t)s.cap_limbs * 8;
-    int rc = ctx->reserve(dev);
-    if (rc) return rc;
-    if ((e = cudaMalloc(&s.d_buf, dev)) != cudaSuccess) {
-      ctx->release(dev);
-      return set_error(RSA_ERR_NOMEM, std::string("server device buffers: ") + cudaGetErrorString(e));
-    }
-    char *p = static_cast<char *>(s.d_buf);
-    s.d_keys = reinterpret_cast<int32_t *>(p);
-    p += align256((size_t)s.cap_ops * 4);
-    s.d_sel = reinterpret_cast<uint8_t *>(p);
-    p += align256(s.cap_ops);
-    s.d_off = reinterpret_cast<uint64_t *>(p);
-    p += align256((size_t)s.cap_ops * 8);
-    s.d_status = reinterpret_cast<int32_t *>(p);
-    p += align256((size_t)s.cap_ops * 4);
-    s.d_msgs = reinterpret_cast<uint32_t *>(p);
-    s.d_out = s.d_msgs + s.cap_limbs;
-    // the ragged path's scratch on this slot's stream, sized for the slot's
-    // largest batch now, so no buffer grows (and waits for the device) later
+    // the ragged path's scratch on this slot's stream, sized for the largest
+    // batch now, so no buffer grows (and waits for the device) later
     std::lock_guard<std::mutex> lock(ctx->mu);
-    rc = ctx->prepare_batch(s.stream, s.cap_ops);
+    rc = ctx->prepare_batch(s.stream, (uint64_t)cfg.max_batch_ops);
     if (rc) return rc;
     wave_ops = ctx->batch_wave_ops(s.stream);
   }
@@ -155,14 +189,6 @@ int Server::init() {
 void Server::release() {
   for (Slot &s : slots) {
     if (s.stream) cudaStreamSynchronize(s.stream);
-    if (s.d_buf) {
-      cudaFree(s.d_buf);
-      ctx->release(align256((size_t)s.cap_ops * 4) + align256(s.cap_ops) + align256((size_t)s.cap_ops * 8) +
-                   align256((size_t)s.cap_ops * 4) + (size_t)s.cap_limbs * 8);
-    }
-    for (void *h : {(void *)s.h_keys, (void *)s.h_sel, (void *)s.h_off, (void *)s.h_status, (void *)s.h_msgs,
-                    (void *)s.h_out})
-      if (h) cudaFreeHost(h);
     if (s.ev) cudaEventDestroy(s.ev);
     if (s.stream) {
       {
@@ -173,19 +199,40 @@ void Server::release() {
     }
   }
   slots.clear();
+  if (d_arena) cudaFree(d_arena);
+  if (h_arena) cudaFreeHost(h_arena);
+  d_arena = h_arena = nullptr;
+  if (arena_reserved) ctx->release(arena_reserved);
+  arena_reserved = 0;
   for (auto &kv : all) delete kv.second;
   all.clear();
   queue.clear();
 }
 
-// Pack `batch` into the slot's staging buffers and enqueue copies + the ragged batch.
-bool Server::launch(Slot &s, std::vector<Req *> &batch) {
+// Lay the batch out in its arena range [s.off, s.off + s.len), pack it into
+// the pinned staging and enqueue copies + the ragged batch on the slot's stream.
+bool Server::launch(Slot &s, std::vector<Req *> &batch, uint64_t nops, uint64_t nlimbs) {
   NvtxRange range("server batch");
+  {
+    char *h = static_cast<char *>(h_arena) + s.off, *d = static_cast<char *>(d_arena) + s.off;
+    size_t at = 0;
+    auto carve = [&](size_t bytes, void **hp, void **dp) {
+      *hp = h + at;
+      *dp = d + at;
+      at += align256(bytes);
+    };
+    const uint64_t l4 = (nlimbs + 3) / 4 * 4;
+    carve(nops * 4, (void **)&s.h_keys, (void **)&s.d_keys);
+    carve(nops, (void **)&s.h_sel, (void **)&s.d_sel);
+    carve(nops * 8, (void **)&s.h_off, (void **)&s.d_off);
+    carve(nops * 4, (void **)&s.h_status, (void **)&s.d_status);
+    carve(l4 * 4, (void **)&s.h_msgs, (void **)&s.d_msgs);
+    carve(l4 * 4, (void **)&s.h_out, (void **)&s.d_out);
+  }
   uint32_t op = 0;
   uint64_t limb = 0;
   s.reqs = batch;
   s.req_off.clear();
-  s.bytes = 0;
   for (Req *r : s.reqs) {
     const uint32_t step = r->L == 1 ? 1u : r->L;
     limb = r->L == 1 ? limb : (limb + 3) / 4 * 4;
@@ -198,7 +245,6 @@ bool Server::launch(Slot &s, std::vector<Req *> &batch) {
       ++op;
     }
     limb += (uint64_t)r->count * r->L;
-    s.bytes += r->bytes;
     r->state = 1;
   }
   cudaStream_t st = s.stream;
@@ -258,9 +304,11 @@ void Server::finish(Slot &s) {
     last_done = t;
     pending--;
   }
-  inflight_bytes -= s.bytes;
+  arena.release(s.off, s.len);
+  inflight_bytes -= s.len;
   inflight_ops -= s.ops;
   s.ops = 0;
+  s.len = 0;
   s.reqs.clear();
   s.busy = false;
 }
@@ -294,7 +342,9 @@ void Server::loop() {
     if (pending == 0) done_cv.notify_all();
     if (stop && queue.empty() && std::none_of(slots.begin(), slots.end(), [](const Slot &s) { return s.busy; }))
       break;
-    // 2. form a batch for a free slot from requests that have arrived and fit
+    // 2. form a batch for a free slot from requests that have arrived; it is
+    //    admitted when its bytes fit in a free range of the in-flight arena
+    //    (otherwise it waits for batches in flight to finish)
     Slot *free_slot = nullptr;
     for (Slot &s : slots)
       if (!s.busy) {
@@ -307,60 +357,81 @@ void Server::loop() {
       // A batch carries one modulus size: the oldest waiting request fixes it
       // and requests of other sizes wait for another slot, so a batch finishes
       // at its own size's latency instead of the slowest size's.  Wait
-      // (briefly) after that request's arrival for more, unless the batch is full.
+      // (briefly) after that request's arrival for more, unless the batch is
+      // full (operations or the largest free range of the arena).
       const uint64_t window = (uint64_t)cfg.batch_window_us * 1000ull;
       const uint64_t first = queue.front()->arrive;
       const uint32_t cls = queue.front()->L;
       const bool mixed = (cfg.flags & RSA_SERVER_MIX_SIZES) != 0;
-      uint32_t ops = 0;
-      uint64_t limbs = 0;
-      bool full = false;
-      for (Req *r : queue) {
-        if (r->arrive > t) break;
-        if (!mixed && r->L != cls) continue;
-        const uint64_t l = (limbs + 3) / 4 * 4 + (uint64_t)r->count * r->L;
-        if (ops + r->count > free_slot->cap_ops || l > free_slot->cap_limbs) {
-          full = true;
-          break;
-        }
-        ops += r->count;
-        limbs = l;
-      }
-      if (full || t >= first + window || stop) {
-        batch.clear();
-        ops = 0;
-        limbs = 0;
-        for (size_t qi = 0; qi < queue.size();) {
+      const size_t room = arena.largest();
+      const uint64_t max_ops = (uint64_t)cfg.max_batch_ops;
+      // requests (in queue order) that make up the batch, and whether one more would not fit
+      auto gather = [&](std::vector<size_t> *picked, uint64_t *ops_out, uint64_t *limbs_out) {
+        uint64_t ops = 0, limbs = 0;
+        bool full = false;
+        for (size_t qi = 0; qi < queue.size(); ++qi) {
           Req *r = queue[qi];
           if (r->arrive > t) break;
-          if (!mixed && r->L != cls) {
-            ++qi;
-            continue;
+          if (!mixed && r->L != cls) continue;
+          const uint64_t l = (r->L == 1 ? limbs : (limbs + 3) / 4 * 4) + (uint64_t)r->count * r->L;
+          if (ops + r->count > max_ops || batch_bytes(ops + r->count, l) > room) {
+            full = true;
+            break;
           }
-          const uint64_t l = (limbs + 3) / 4 * 4 + (uint64_t)r->count * r->L;
-          if (ops + r->count > free_slot->cap_ops || l > free_slot->cap_limbs) break;
           ops += r->count;
           limbs = l;
-          batch.push_back(r);
-          queue.erase(queue.begin() + (long)qi);
+          if (picked) picked->push_back(qi);
         }
-        if (!batch.empty()) {
-          uint64_t bytes = 0;
-          for (Req *r : batch) bytes += r->bytes;
-          inflight_bytes += bytes;
+        *ops_out = ops;
+        *limbs_out = limbs;
+        return full;
+      };
+      uint64_t ops = 0, limbs = 0;
+      const bool full = gather(nullptr, &ops, &limbs);
+      if (ops > 0 && (full || t >= first + window || stop)) {
+        std::vector<size_t> picked;
+        gather(&picked, &ops, &limbs);
+        // one pass: the picked requests leave the queue in order, the rest keep theirs
+        batch.clear();
+        std::deque<Req *> rest;
+        size_t k = 0;
+        for (size_t qi = 0; qi < queue.size(); ++qi) {
+          if (k < picked.size() && picked[k] == qi) {
+            batch.push_back(queue[qi]);
+            ++k;
+          } else {
+            rest.push_back(queue[qi]);
+          }
+        }
+        queue.swap(rest);
+        const size_t need = batch_bytes(ops, limbs);
+        size_t off = 0;
+        if (!arena.alloc(need, &off)) {
+          // cannot happen: `room` is a free range at least this large
+          for (Req *r : batch) {
+            r->state = RSA_ERR_NOMEM;
+            pending--;
+          }
+          fatal = set_error(RSA_ERR_NOMEM, "server arena allocation failed");
+        } else {
+          free_slot->off = off;
+          free_slot->len = need;
+          inflight_bytes += need;
           peak_bytes = std::max(peak_bytes, inflight_bytes);
           lock.unlock();
-          const bool ok = launch(*free_slot, batch);
+          const bool ok = launch(*free_slot, batch, ops, limbs);
           lock.lock();
           if (!ok) {
             for (Req *r : batch) {
               r->state = fatal ? fatal : RSA_ERR_CUDA;
               pending--;
             }
-            inflight_bytes -= bytes;
+            arena.release(off, need);
+            inflight_bytes -= need;
+            free_slot->len = 0;
           }
-          launched = true;
         }
+        launched = true;
       }
     }
     if (!launched) {
@@ -420,6 +491,12 @@ int rsa_server_submit(rsa_ctx *ctx, const rsa_request *req, uint64_t *ticket) {
     if (rc) return rc;
     L = k->L;
   }
+  if (req->count > (uint32_t)s->cfg.max_batch_ops ||
+      batch_bytes(req->count, (uint64_t)req->count * L) > s->arena.size()) {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->rejected++;
+    return set_error(RSA_ERR_NOMEM, "request exceeds the memory budget for requests in flight (or max_batch_ops)");
+  }
   Req *r = new Req();
   r->key_id = req->key_id;
   r->exp_sel = req->exp_sel;
@@ -428,14 +505,7 @@ int rsa_server_submit(rsa_ctx *ctx, const rsa_request *req, uint64_t *ticket) {
   r->msgs = req->msgs;
   r->out = req->out;
   r->status = req->status;
-  r->bytes = (uint64_t)req->count * (8ull * L + 24ull);
   std::lock_guard<std::mutex> lock(s->mu);
-  const Slot &s0 = s->slots[0];
-  if ((uint64_t)req->count * L + 4 > s0.cap_limbs || req->count > s0.cap_ops) {
-    delete r;
-    s->rejected++;
-    return set_error(RSA_ERR_NOMEM, "request exceeds the per-batch share of the memory budget");
-  }
   r->arrive = req->arrive_ns ? s->epoch + req->arrive_ns : now_ns();
   r->ticket = s->next_ticket++;
   if (!s->first_arrive || r->arrive < s->first_arrive) s->first_arrive = r->arrive;

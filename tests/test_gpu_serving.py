@@ -3,8 +3,10 @@
 Requests over several keys, sizes and exponent kinds arrive spread over time;
 the loop batches whatever has arrived while earlier batches are still on the
 GPU.  Every request's result must equal the oracle's and the result of the
-same messages run alone through rsa_modexp_key; a request larger than the
-memory budget allows is refused at submit.
+same messages run alone through rsa_modexp_key.  Admission is by bytes in
+flight: requests larger than a slot's share of the budget are served (waiting
+for room when the batches in flight hold it), and only a request larger than
+the whole budget is refused at submit.
 """
 import threading
 import time
@@ -71,8 +73,9 @@ def test_serving_mixed_arrivals(torch_cuda, mix_sizes):
             assert np.array_equal(out, want)
             alone = ctx.modexp_key(kids[k], kind, torch_cuda.from_numpy(msgs.view(np.int32)).cuda())
             assert np.array_equal(alone.cpu().numpy().view(np.uint32), out)
-        # a request bigger than one batch's share of the budget is refused
-        big = workloads.messages_below(keys[3].n, 60000, 4, "big")
+        # a request bigger than the whole budget (65000 x 4096-bit rows: ~68 MB
+        # of rows, results and metadata against 64 MiB) is refused
+        big = np.zeros((65000, 128), dtype=np.uint32)
         with pytest.raises(RsaError) as ei:
             rsa_server_submit(ctx.handle, kids[3], CRT, big, np.zeros_like(big))
         assert ei.value.code == -4
@@ -80,6 +83,41 @@ def test_serving_mixed_arrivals(torch_cuda, mix_sizes):
     finally:
         ctx.close()
 
+
+
+def test_serving_admission_by_bytes_in_flight(torch_cuda):
+    """Two requests that each take more than half of the budget (and far more
+    than a slot's share) are both served: the second waits until the first's
+    batch gives its bytes back; the arena never holds more than the budget."""
+    from paper_1407_1465_gb300 import (RsaContext, build, rsa_server_drain, rsa_server_get_stats, rsa_server_poll,
+                                       rsa_server_start, rsa_server_stop, rsa_server_submit)
+    build.build()
+    key = workloads.gen_keys([(2048, 0)], workloads.DEFAULT_SEED)[0]
+    budget = 40 << 20
+    ctx = RsaContext(0, mem_budget_bytes=6 << 30)
+    try:
+        kid = ctx.keyload(key.bits, key.n, key.e, key.d, key.p, key.q)
+        rsa_server_start(ctx.handle, max_inflight_batches=4, batch_window_us=100, mem_budget_bytes=budget)
+        reqs = []
+        # 40000 rows: 40000 x (8 x 64 + 17) bytes and alignment, 21 160 192 bytes of the arena
+        for r, count in enumerate([40000, 40000, 5, 17]):
+            msgs = workloads.messages_below(key.n, count, 8, ("admit", r))
+            out = np.zeros_like(msgs)
+            status = np.full(count, 99, dtype=np.int32)
+            reqs.append((rsa_server_submit(ctx.handle, kid, PUB, msgs, out, status), msgs, out, status))
+        rsa_server_drain(ctx.handle, timeout_ms=120000)
+        st = rsa_server_get_stats(ctx.handle)
+        assert st["completed"] == 4 and st["rejected"] == 0
+        assert 21_160_192 <= st["peak_bytes"] <= budget
+        for t, msgs, out, status in reqs:
+            assert rsa_server_poll(ctx.handle, t) == 1 and (status == 0).all()
+            alone = ctx.modexp_key(kid, PUB, torch_cuda.from_numpy(msgs.view(np.int32)).cuda())
+            assert np.array_equal(alone.cpu().numpy().view(np.uint32), out)
+            idx = np.arange(0, len(msgs), max(1, len(msgs) // 64))
+            assert np.array_equal(out[idx], oracle.modexp_batch(msgs[idx], key.e, key.n))
+        rsa_server_stop(ctx.handle)
+    finally:
+        ctx.close()
 
 
 def test_serving_failure_paths(torch_cuda):
