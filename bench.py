@@ -48,12 +48,12 @@ def workload_desc(bits, count, kind="crt"):
 # hash to the recorded stamp and the window matches; otherwise reported as null.
 PROFILED_TRAFFIC = {
     # (workload, variant): one ncu capture of that kernel, valid while its sources hash to the stamp
-    ("rsa2048", 3): {"window": 3, "stamp": "4ac01f94619e9b34", "dram_bytes_per_op": 1167.4,
+    ("rsa2048", 3): {"window": 3, "stamp": "4e131194285a589f", "dram_bytes_per_op": 1160.9,
                      "files": ["crt_tc.cu", "crt_tc.h", "tc.cuh", "mont.cuh", "kernels.cuh", "keyrec.h"],
                      "source": "profiles/crt_tc_half_kernel_rsa2048_w3_ncu_full.md",
                      # what binds the kernel, from the same capture (percent of peak while active)
-                     "pipes": {"issue_active_pct": 52.6, "warps_active_pct": 25.0, "alu_pipe_pct": 50.9,
-                               "fma_pipe_pct": 34.2, "tensor_pipe_pct": 19.2,
+                     "pipes": {"issue_active_pct": 52.5, "warps_active_pct": 25.0, "alu_pipe_pct": 50.9,
+                               "fma_pipe_pct": 34.1, "tensor_pipe_pct": 19.2,
                                "top_stalls": ["wait", "math_pipe_throttle", "not_selected"]}},
     ("rsa2048", 1): {"window": 4, "stamp": "2c547aada0325644", "dram_bytes_per_op": 257607.0,
                      "files": ["kernels.cuh", "mont.cuh", "inst_unit.cuh", "inst_h32.cu", "keyrec.h"],
@@ -588,6 +588,95 @@ def ragged_measure(steps: int, warmup: int, autotune: bool = False, loop_steps: 
             "autotuned_ms": tuned_ms, "products_per_step": prods, "count": count}
 
 
+def single_key_rate(bits: int, count: int, kind: str = "crt", window: int = 0, steps: int = 3, warmup: int = 2,
+                    threads_per_op: int = 0) -> dict:
+    """One uniform batch under one seeded key (inputs resident on the device,
+    L2 flushed between timed steps), timed with CUDA events; sampled results
+    are checked against the oracle.  kind: "crt" (decryption) or "public"
+    (encryption with e = 65537)."""
+    import torch
+    import oracle
+    from paper_1407_1465_gb300 import RSA_EXP_PRIVATE_CRT, RSA_EXP_PUBLIC, RsaContext, build, rsa_modexp_key
+    build.build()
+    dev = torch.device("cuda", 0)
+    key, rows = workloads.rsa_single(bits, WORKLOADS["rsa%d" % bits]["count"] if "rsa%d" % bits in WORKLOADS else count)
+    rows = rows[:count]
+    sel = RSA_EXP_PRIVATE_CRT if kind == "crt" else RSA_EXP_PUBLIC
+    ctx = RsaContext(0, mem_budget_bytes=8 << 30)
+    try:
+        kid = ctx.keyload(bits, key.n, key.e, key.d, key.p, key.q)
+        if window or threads_per_op:
+            ctx.set_tuning(bits, sel, window=window, threads_per_op=threads_per_op)
+        tune = ctx.get_tuning(bits, sel)
+        msgs = torch.from_numpy(rows.view(np.int32)).to(dev)
+        out = torch.empty_like(msgs)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        stream = torch.cuda.current_stream(dev)
+        for _ in range(warmup):
+            rsa_modexp_key(ctx.handle, kid, sel, count, msgs, out, None, stream.cuda_stream)
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rsa_modexp_key(ctx.handle, kid, sel, count, msgs, out, None, stream.cuda_stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        got = out.cpu().numpy().view(np.uint32)
+        idx = np.arange(0, count, max(1, count // 6))
+        want = (oracle.crt_batch(rows[idx], key.d, key.p, key.q) if kind == "crt"
+                else oracle.modexp_batch(rows[idx], key.e, key.n))
+        if not np.array_equal(got[idx], want):
+            raise RuntimeError("RSA-%d %s results differ from the oracle" % (bits, kind))
+        t = statistics.median(ms)
+        return {"value": count / (t / 1e3), "ms_per_batch": t, "count": count, "window": tune["window"],
+                "threads_per_op": tune["threads_per_op"], "variant": tune["variant"]}
+    finally:
+        ctx.close()
+
+
+def toy_rate(steps: int = 20, warmup: int = 3) -> dict:
+    """The paper's own example (Sec. 2): n = 17947, e = 131, d = 137 as printed;
+    4096 single-limb packets uniform in [0, 2525], encrypted then decrypted per
+    step (one launch each); checked against the oracle."""
+    import torch
+    import oracle
+    from paper_1407_1465_gb300 import RSA_EXP_PRIVATE_PLAIN, RSA_EXP_PUBLIC, RsaContext, build, rsa_modexp_key
+    build.build()
+    dev = torch.device("cuda", 0)
+    t = workloads
+    ctx = RsaContext(0)
+    try:
+        kid = ctx.keyload(32, t.TOY_N, t.TOY_E, t.TOY_D, t.TOY_P, t.TOY_Q)
+        pk = torch.from_numpy(t.toy_packets(4096).view(np.int32)).to(dev)
+        enc, dec = torch.empty_like(pk), torch.empty_like(pk)
+        sptr = torch.cuda.current_stream(dev).cuda_stream
+
+        def step():
+            rsa_modexp_key(ctx.handle, kid, RSA_EXP_PUBLIC, 4096, pk, enc, None, sptr)
+            rsa_modexp_key(ctx.handle, kid, RSA_EXP_PRIVATE_PLAIN, 4096, enc, dec, None, sptr)
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            step()
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        e_np, d_np = enc.cpu().numpy().view(np.uint32), dec.cpu().numpy().view(np.uint32)
+        p_np = t.toy_packets(4096)
+        if (list(e_np[:64]) != [oracle.modexp(int(m), t.TOY_E, t.TOY_N) for m in p_np[:64]] or
+                list(d_np[:64]) != [oracle.modexp(int(c), t.TOY_D, t.TOY_N) for c in e_np[:64]]):
+            raise RuntimeError("toy results differ from the oracle")
+        return {"value": 8192 / (ms / 1e3), "unit": "ops/s", "ms_per_step": ms, "us_per_launch": ms * 1e3 / 2}
+    finally:
+        ctx.close()
+
+
 def run_ragged(args):
     """Ragged batch: 256 keys, 200000 operations, one rsa_modexp_batch (one graph
     launch) per step, against a loop of one rsa_modexp_key launch per
@@ -781,6 +870,8 @@ def main():
     ap.add_argument("--no-latency", action="store_true", help="skip the serving-latency sweep of the default run")
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch measurement of the default run")
     ap.add_argument("--no-loop", action="store_true", help="ragged: skip the one-key-per-launch comparison")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the encryption, toy-key and RSA-4096 lines of the default run")
     ap.add_argument("--autotune", action="store_true", help="ragged: run the ragged autotuner on the batch first")
     args = ap.parse_args()
     if args.workload == "ragged":
@@ -968,6 +1059,26 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(key, rows, public=(kind == RSA_EXP_PUBLIC), e=e_pub)
     ctx.close()
+    if rank == 0 and ws == 1 and not args.no_configs and args.workload == "rsa2048" and args.kind == "crt":
+        # the other configurations of the benchmark, short and checked against the oracle:
+        # RSA-2048 encryption, the paper's toy key, RSA-4096 CRT over windows 4-6
+        enc = single_key_rate(2048, 65536, "public", steps=5, warmup=2)
+        line["encrypt"] = dict(enc, unit="encryptions/s", what="RSA-2048 encryption (e = 65537, binary method, "
+                               "Fig. 5): the benchmark key's 65536 messages, one rsa_modexp_key per step")
+        line["toy"] = dict(toy_rate(), what="the paper's toy key n = 17947, e = 131, d = 137 (Sec. 2): 4096 "
+                           "packets in [0, 2525] encrypted then decrypted per step; launch-latency bound")
+        sweep4096 = {w: single_key_rate(4096, 16384, "crt", window=w, steps=3, warmup=1) for w in (4, 5, 6)}
+        best_w = max(sweep4096, key=lambda w: sweep4096[w]["value"])
+        line["rsa4096"] = {
+            "what": "RSA-4096 CRT decryption: 1 seeded key (two 2048-bit primes), 16384 ciphertexts, window "
+                    "width swept 4-6 (four lanes per operation)",
+            "value": sweep4096[best_w]["value"], "unit": "decrypts/s", "best_window": best_w,
+            "window_sweep": {str(w): {"value": r["value"], "ms_per_batch": r["ms_per_batch"]}
+                             for w, r in sweep4096.items()},
+            "roofline": alu_roofline(rsa_products_per_op(4096, RSA_EXP_PRIVATE_CRT, e=65537, window=best_w) *
+                                     sweep4096[best_w]["value"] / 1e12, local,
+                                     "word products per second under the CIOS count 2H^2 + H per Montgomery "
+                                     "product (what the four-lane kernel issues)")}
     if rank == 0 and ws == 1 and not args.no_ragged and args.workload == "rsa2048" and args.kind == "crt":
         # the ragged batch (256 keys, 200000 operations, one graph launch) against
         # a loop of one launch per (key, kind) group

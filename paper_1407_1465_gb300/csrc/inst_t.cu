@@ -5,11 +5,12 @@
 namespace rsagpu {
 
 const void *crt_kernel_t_fn(int H, int T, int W) {
-  if (W != 4 && W != 5) return nullptr;
-#define RSAGPU_CRT_T(h, t)                                                                  \
-  if (H == h && T == t)                                                                     \
-    return W == 4 ? reinterpret_cast<const void *>(&crt_kernel_t<h, t, 4, (h / t >= 32 ? 4 : 8)>) \
-                  : reinterpret_cast<const void *>(&crt_kernel_t<h, t, 5, (h / t >= 32 ? 4 : 8)>);
+  if (W < 4 || W > 6) return nullptr;
+#define RSAGPU_CRT_T(h, t)                                                                          \
+  if (H == h && T == t)                                                                             \
+    return W == 4   ? reinterpret_cast<const void *>(&crt_kernel_t<h, t, 4, (h / t >= 32 ? 4 : 8)>) \
+           : W == 5 ? reinterpret_cast<const void *>(&crt_kernel_t<h, t, 5, (h / t >= 32 ? 4 : 8)>) \
+                    : reinterpret_cast<const void *>(&crt_kernel_t<h, t, 6, (h / t >= 32 ? 4 : 8)>);
   RSAGPU_CRT_T(32, 2)
   RSAGPU_CRT_T(32, 4)
   RSAGPU_CRT_T(48, 2)

@@ -245,7 +245,7 @@ def test_lanes_per_operation_crt(torch_cuda, ctx, keys, kids, bits, tpo):
     ng = rows.shape[0] - bad.shape[0]
     want = expect(key, CRT, rows[:ng])
     try:
-        for w in (4, 5):
+        for w in ((4, 5) if bits == 2048 else (4, 5, 6)):
             ctx.set_tuning(bits, CRT, window=w, threads_per_op=tpo)
             got, st = run(torch_cuda, ctx, kids[bits], CRT, rows)
             assert (st[:ng] == 0).all() and (st[ng:] == -3).all()
