@@ -148,6 +148,29 @@ def tc_work_per_op(bits: int, window: int):
     return issued, tensor_flops, method_flops
 
 
+def tc4_work_per_op(window: int):
+    """CUDA-core word products and tensor-core FLOPs of one RSA-4096 CRT
+    decryption on the tensor-core path (2048-bit primes, two reduction rounds
+    of r = 2^1024 per Montgomery product): per half 2 input products, 2^w - 2
+    table products, (windows - 1)(w + 1) window steps (+1 for q leaving
+    Montgomery form); every step issues a 64 x 64-limb product (squarings
+    included) and two rounds of MMA 1 (N = 128) and MMA 2 (N = 256), 9 K-steps
+    each; Garner adds two CIOS products and one 64 x 64 product.
+    Returns (issued word products, issued MMA FLOPs, method MMA FLOPs): the
+    method's share of a round is the nonzero part of its two Toeplitz products,
+    D(D+1)/2 byte products for mu = (T mod r) m' mod r and those of positions
+    D-4 .. D+251 of mu * m (m of 2D digits), D = 128."""
+    H, D = 64, 128
+    nwin = -(-32 * H // window)
+    steps = 2 * ((1 << window) + (nwin - 1) * (window + 1)) + 1
+    issued = steps * H * H + 2 * (2 * H * H + H) + H * H
+    issued_flops = steps * 2 * (9 * 2 * 128 * 16 + 9 * 2 * 256 * 16)
+    mma1 = D * (D + 1) // 2
+    mma2 = sum(min(j, D - 1) - max(0, j - (2 * D - 1)) + 1 for j in range(D - 4, D - 4 + 256))
+    method_flops = steps * 2 * 2 * (mma1 + mma2)
+    return issued, issued_flops, method_flops
+
+
 def measured_bf16_tflops():
     """Burst dense bf16 TFLOP/s from MEASURED_PEAKS.json (fp16 runs at the same
     rate), else the fallback figure for GB300."""
@@ -1009,7 +1032,8 @@ def main():
     traffic = prof["dram_bytes_per_op"] * count if prof_valid else None
     tc_path = tune["variant"] == 3 and args.kind == "crt"
     if tc_path:
-        issued, tflops_op, method_flops_op = tc_work_per_op(spec["bits"], tune["window"])
+        issued, tflops_op, method_flops_op = (tc4_work_per_op(tune["window"]) if spec["bits"] == 4096
+                                              else tc_work_per_op(spec["bits"], tune["window"]))
         roofline = alu_roofline(issued * count / (ms / 1e3) / 1e12, local,
                                 "32x32->64 word products the CUDA cores issue per second (per-message products "
                                 "A*B and squarings, the Garner step); the Montgomery reductions run on the tensor "

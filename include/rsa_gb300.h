@@ -322,11 +322,12 @@ typedef struct rsa_tuning {
     int32_t variant;       /* squarings of private exponents: 1 = through the general
                               CIOS multiply, 2 = separated square + reduction (fewer
                               word products, but a larger instruction footprint; slower
-                              on GB300); 3 = RSA-2048 CRT only: the Montgomery reduction
-                              on the tensor cores (tcgen05 MMAs of byte digits against
-                              Toeplitz matrices of p, q and -p^-1, -q^-1 mod 2^1024;
-                              the per-message product stays on the CUDA cores; windows
-                              3 and 4); 0 = automatic: 3 for RSA-2048 CRT (window 3),
+                              on GB300); 3 = RSA-2048 and RSA-4096 CRT: the Montgomery
+                              reduction on the tensor cores (tcgen05 MMAs of byte digits
+                              against Toeplitz matrices of p, q and -p^-1, -q^-1 mod
+                              2^1024; for 2048-bit primes in two rounds of 2^1024; the
+                              per-message product stays on the CUDA cores; windows 3
+                              and 4); 0 = automatic: 3 for RSA-2048 CRT (window 3),
                               1 otherwise.  For RSA_EXP_PUBLIC (moduli up to 2048
                               bits): 1 = binary method (Fig. 5), 2 = sliding windows
                               of up to `window` bits (Fig. 7; window 4..6, default 5),
@@ -399,6 +400,17 @@ int rsa_autotune_batch(rsa_ctx *ctx, uint64_t count, const int32_t *key_ids, con
  * Errors: RSA_ERR_ARG (null pointer, short buffer, even m). */
 #define RSA_TC_IMAGE_BYTES 73728
 int rsa_tc_operand_image(const uint32_t *m, void *out, size_t out_bytes);
+
+/* The same for one 2048-bit prime m of an RSA-4096 key (variant 3 at 4096 bits:
+ * the Montgomery reduction mod m, R = 2^2048, in two rounds of r = 2^1024, each
+ * a product by -m^-1 mod r and one by m), as built at key load; K = 144 as above:
+ *   bytes [0, 36864):      128 rows, row n, column k < 128: byte n-k of -m^-1 mod 2^1024
+ *   bytes [36864, 110592): 256 rows, row j, column k < 128: byte 124+j-k of m
+ * (0 where the byte index is outside 0..127, resp. 0..255).  m: 64 limbs,
+ * little-endian, odd.  out: host buffer of at least RSA_TC4_IMAGE_BYTES bytes.
+ * No GPU is used.  Errors: RSA_ERR_ARG (null pointer, short buffer, even m). */
+#define RSA_TC4_IMAGE_BYTES 110592
+int rsa_tc4_operand_image(const uint32_t *m, void *out, size_t out_bytes);
 
 /* Counters since context creation. */
 typedef struct rsa_stats {

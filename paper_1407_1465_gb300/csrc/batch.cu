@@ -212,6 +212,15 @@ uint64_t ragged_wide_fraction() {
   return p < 0 ? 0 : (uint64_t)p;
 }
 
+// Lanes per operation of 4096-bit CRT in the latency shapes: 16 (GB300,
+// serving at 1 k req/s: 4096-bit requests p50/p99 8.8/22.7 ms against
+// 12.8/27.5 ms with 8, the 256-key mix 3.5/14.9 against 4.0/17.6 ms);
+// RSAGPU_RAGGED_LANES_4096=8 selects 8.
+int lanes_4096() {
+  const char *v = std::getenv("RSAGPU_RAGGED_LANES_4096");
+  return v && std::atoi(v) == 8 ? 8 : 16;
+}
+
 // approximate word products per operation of a class, for the longest-first order
 double class_cost(int32_t cls) {
   auto mm = [](double l) { return 2.0 * l * l + l; };
@@ -223,6 +232,7 @@ double class_cost(int32_t cls) {
     case CLS_CRT64: return 2.0 * 2500 * mm(64);
     case CLS_CRT32W: return 2.0 * 1300 * mm(32) / 4;   // per lane
     case CLS_CRT64W: return 2.0 * 2500 * mm(64) / 8;
+    case CLS_CRT64X: return 2.0 * 2500 * mm(64) / 16;
     case CLS_PUB32: return 19 * mm(32);
     case CLS_PUB64: return 19 * mm(64);
     case CLS_PUB96: return 19 * mm(96);
@@ -358,7 +368,7 @@ int Ctx::prepare_batch(cudaStream_t s, uint64_t max_count) {
     st->keydir_epoch = key_epoch;
   }
   const uint32_t nb = std::max<uint32_t>(nkeys, 1) * 3;
-  const uint64_t max_tiles = max_count / 8 + nb + 1;   // smallest tile: 8 operations
+  const uint64_t max_tiles = max_count / kMinTileOps + nb + 1;   // tiles of at least kMinTileOps operations
   int rc;
   if ((rc = ensure(w.aux0, (size_t)max_count * 8)) ||                  // op_bucket + sorted
       (rc = ensure(w.aux1, (size_t)nb * 12)) ||                        // bcount, bfill, boff
@@ -438,7 +448,7 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
   Workspace &w = ws(s);
   const uint32_t nkeys = (uint32_t)keys.size();
   const uint32_t nb = std::max<uint32_t>(nkeys, 1) * 3;
-  const uint32_t max_tiles = (uint32_t)(count / 8 + nb + 1);
+  const uint32_t max_tiles = (uint32_t)(count / kMinTileOps + nb + 1);
   int grids_exec[GRP_COUNT];
   for (int g = 0; g < GRP_COUNT; ++g) grids_exec[g] = st->grids_exec[g];
 
@@ -474,7 +484,8 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
     const int tpo = tune_for(0, RSA_TUNE_RAGGED).tpo;
     wide = tpo == 4 ? 1 : tpo == 1 ? 0 : (count <= batch_wave_ops(s) ? 1 : 0);
   }
-  d.wide_crt32 = wide != 0 ? 1u : 0u;
+  // lanes per operation of 4096-bit CRT in the latency shapes (lanes_4096)
+  d.wide_crt32 = wide != 0 ? (lanes_4096() == 16 ? 2u : 1u) : 0u;
   // windows of the CRT classes and the tensor-core group (the ragged tuning):
   // the group takes 2048-bit CRT buckets in the throughput shapes, unless the
   // tuning keeps every operation on the CUDA cores (variant 1) or asks for it
@@ -546,7 +557,7 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
   // a batch with few tiles launches only the CTAs it can use (at most one
   // per tile: count / smallest tile + one partial tile per bucket), so that
   // its tiles start on separate SMs instead of wherever the first CTAs landed
-  const uint64_t tile_min[GRP_COUNT] = {d.wide_crt32 ? 4u : 8u, 32u, 32u, 16u};
+  const uint64_t tile_min[GRP_COUNT] = {d.wide_crt32 == 2 ? 2u : d.wide_crt32 ? 4u : 8u, 32u, 32u, 16u};
   static_assert(GRP_BIG == 0 && GRP_CRT == 1 && GRP_L64 == 2 && GRP_WIDE == 3, "tile_min order");
   for (int gi = 0; gi < GRP_COUNT; ++gi) {
     const uint64_t useful = count / tile_min[gi] + std::min<uint64_t>(nb, count) + 1;

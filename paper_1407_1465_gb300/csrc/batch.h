@@ -40,7 +40,9 @@ enum : int32_t {
                                                  // (the W classes: small batches, latency over throughput)
   CLS_PLAIN96 = 13, CLS_PLAIN128 = 14,           // plain private exponent of 3072/4096-bit moduli,
                                                  // four lanes per operation
-  CLS_COUNT = 15
+  CLS_CRT64X = 15,                               // CRT of 4096-bit keys, sixteen lanes per operation
+                                                 // (small batches, when asked for instead of eight)
+  CLS_COUNT = 16
 };
 
 // Window widths of the CRT classes are chosen per batch (BatchDesc::win_small
@@ -56,13 +58,13 @@ constexpr int kBatchWindowPlain = 4;
 constexpr int kBatchWindowTc = 3;
 constexpr uint32_t kBatchTcMinOps = 128;
 
-// wide: run 2048-bit CRT with four lanes per operation (CLS_CRT32W) and
-// 4096-bit CRT with eight (CLS_CRT64W)
-__host__ __device__ inline int32_t batch_class(uint32_t L, int kind, bool wide = false) {
+// wide (nonzero): run 2048-bit CRT with four lanes per operation (CLS_CRT32W)
+// and 4096-bit CRT with eight (CLS_CRT64W; wide == 2: sixteen, CLS_CRT64X)
+__host__ __device__ inline int32_t batch_class(uint32_t L, int kind, uint32_t wide = 0) {
   if (L == 1) return CLS_TOY;
   if (kind == 1)
     return L == 32 ? CLS_CRT16 : L == 64 ? (wide ? CLS_CRT32W : CLS_CRT32) : L == 96 ? CLS_CRT48
-           : L == 128 ? (wide ? CLS_CRT64W : CLS_CRT64) : -1;
+           : L == 128 ? (wide == 2 ? CLS_CRT64X : wide ? CLS_CRT64W : CLS_CRT64) : -1;
   if (kind == 0) return L == 32 ? CLS_PUB32 : L == 64 ? CLS_PUB64 : L == 96 ? CLS_PUB96 : L == 128 ? CLS_PUB128 : -1;
   if (kind == 2) return L == 32 ? CLS_PLAIN32 : L == 64 ? CLS_PLAIN64 : L == 96 ? CLS_PLAIN96 : L == 128 ? CLS_PLAIN128 : -1;
   return -1;
@@ -79,7 +81,8 @@ __host__ __device__ inline int32_t batch_class(uint32_t L, int kind, bool wide =
 //         lanes per operation
 enum : int32_t { GRP_BIG = 0, GRP_CRT = 1, GRP_L64 = 2, GRP_WIDE = 3, GRP_COUNT = 4 };
 __host__ __device__ inline int32_t batch_group(int32_t cls) {
-  if (cls == CLS_CRT48 || cls == CLS_CRT64 || cls == CLS_CRT32W || cls == CLS_CRT64W) return GRP_BIG;
+  if (cls == CLS_CRT48 || cls == CLS_CRT64 || cls == CLS_CRT32W || cls == CLS_CRT64W || cls == CLS_CRT64X)
+    return GRP_BIG;
   if (cls == CLS_PUB96 || cls == CLS_PUB128 || cls == CLS_PLAIN96 || cls == CLS_PLAIN128) return GRP_WIDE;
   if (cls == CLS_PUB64 || cls == CLS_PLAIN64) return GRP_L64;
   return GRP_CRT;
@@ -103,14 +106,25 @@ __host__ __device__ constexpr size_t batch_table_u4(int group, int win_small, in
 }
 
 // operations per tile of a class: CRT 32 (warp pair on the same 32), wide CRT 8
-// (4 lanes per operation, the pair on the same 8; 4 with 8 lanes), wide public and plain 16 (4
+// (4 lanes per operation, the pair on the same 8; 4 with 8 lanes, 2 with 16), wide public and plain 16 (4
 // lanes per operation, 8 per warp), others 64 (32 per warp)
-__host__ __device__ inline int32_t batch_tile_ops(int32_t cls) {
+__host__ __device__ constexpr int32_t batch_tile_ops(int32_t cls) {
+  if (cls == CLS_CRT64X) return 2;
   if (cls == CLS_CRT64W) return 4;
   if (cls == CLS_CRT48 || cls == CLS_CRT64 || cls == CLS_CRT32W) return 8;
   if (cls == CLS_PUB96 || cls == CLS_PUB128 || cls == CLS_PLAIN96 || cls == CLS_PLAIN128) return 16;
   return (cls == CLS_CRT16 || cls == CLS_CRT32) ? 32 : 64;
 }
+
+// the smallest tile of any class (CLS_CRT64X): the tile list holds up to
+// count / kMinTileOps + (buckets) + 1 descriptors, enough for every class
+constexpr uint32_t kMinTileOps = 2;
+__host__ __device__ constexpr bool batch_tiles_fit() {
+  for (int c = 0; c < CLS_COUNT; ++c)
+    if ((uint32_t)batch_tile_ops(c) < kMinTileOps) return false;
+  return true;
+}
+static_assert(batch_tiles_fit(), "a class has tiles smaller than kMinTileOps");
 
 struct BatchDesc {
   uint32_t count, nkeys;
@@ -132,7 +146,7 @@ struct BatchDesc {
   uint32_t table_u4;          // batch_table_u4(group, win_small, win_big) of the node's group
   uint32_t max_tiles;
   int32_t class_rank[CLS_COUNT];  // position of each class in the longest-first order
-  uint32_t wide_crt32;        // small batch: 2048/4096-bit CRT as CLS_CRT32W / CLS_CRT64W
+  uint32_t wide_crt32;        // small batch: 2048/4096-bit CRT as CLS_CRT32W / CLS_CRT64W (2: CLS_CRT64X)
   int32_t win_small, win_big; // CRT windows of 1024/2048-bit and of 3072/4096-bit keys (4 or 5)
   // tensor-core group: 2048-bit CRT buckets of at least tc_min_ops operations
   // (0: none) send floor(count / 128) whole tiles there, in chunks of up to

@@ -72,6 +72,17 @@ __device__ __forceinline__ void run_crt8(const uint32_t *ks, uint4 *work, uint4 
   crt_tile_t<H, 8, W, 8>(ks, warp == 1, g, stage_op, xb, table_warp + lane, 1, io);
 }
 
+// CRT of 4096-bit keys in small batches: sixteen lanes per operation, the pair on the same 2
+template <int H, int W>
+__device__ __forceinline__ void run_crt16(const uint32_t *ks, uint4 *work, uint4 *table_warp, int warp, int lane,
+                                          const TileIO &io) {
+  constexpr int kStage = (H / 4) * 2;
+  const Group<16> g(lane);
+  uint4 *xb = work + g.opi;
+  uint4 *stage_op = work + kStage + warp * kStage + g.opi;
+  crt_tile_t<H, 16, W, 8>(ks, warp == 1, g, stage_op, xb, table_warp + lane, 1, io);
+}
+
 template <int L>
 __device__ __forceinline__ void run_pub(const uint32_t *ks, uint4 *work, int warp, int lane, const TileIO &io) {
   constexpr int kStage = (L / 4) * 32;
@@ -138,8 +149,9 @@ __global__ void __launch_bounds__(64, G == GRP_BIG ? 8 : 1) batch_exec_kernel(Ba
                          (uint32_t)wn};
     if constexpr (G == GRP_BIG) {
       static_assert(stage_u4(3, 48, 8) * 16 <= work_bytes(GRP_BIG) && stage_u4(3, 64, 8) * 16 <= work_bytes(GRP_BIG) &&
-                        stage_u4(3, 32, 8) * 16 <= work_bytes(GRP_BIG) && stage_u4(3, 64, 4) * 16 <= work_bytes(GRP_BIG),
-                    "work area of a four/eight-lane CRT class");
+                        stage_u4(3, 32, 8) * 16 <= work_bytes(GRP_BIG) && stage_u4(3, 64, 4) * 16 <= work_bytes(GRP_BIG) &&
+                        stage_u4(3, 64, 2) * 16 <= work_bytes(GRP_BIG),
+                    "work area of a four/eight/sixteen-lane CRT class");
       // tables: win_big entries of 16 (H=64) or 12 (H=48) limbs per lane, win_small
       // of 8 (H=32 on four lanes), win_big of 8 (H=64 on eight lanes)
       static_assert(batch_table_need(5, 48 / 4) <= batch_table_u4(GRP_BIG, 4, 5) &&
@@ -160,6 +172,9 @@ __global__ void __launch_bounds__(64, G == GRP_BIG ? 8 : 1) batch_exec_kernel(Ba
       } else if (td.cls == CLS_CRT64W) {
         if (w5big) run_crt8<64, 5>(ks, work, table_warp, warp, lane, io_pair);
         else run_crt8<64, 4>(ks, work, table_warp, warp, lane, io_pair);
+      } else if (td.cls == CLS_CRT64X) {
+        if (w5big) run_crt16<64, 5>(ks, work, table_warp, warp, lane, io_pair);
+        else run_crt16<64, 4>(ks, work, table_warp, warp, lane, io_pair);
       }
     } else if constexpr (G == GRP_L64) {
       static_assert(batch_table_need(kBatchWindowPlain, 64) <= batch_table_u4(GRP_L64, 4, 4), "plain L=64 table");

@@ -110,46 +110,7 @@ struct GarnerArgs {
 };
 
 // ---------------------------------------------------------------- arithmetic pieces
-// One row of the product scan: t + a*b, the lowest limb returned and the rest
-// shifted down one limb (t[j] <- position j+1).  t < 2^(32L) on entry, so the
-// sum fits in L+1 limbs.  Even and odd limbs of a in two carry chains as in
-// mul_acc (mont.cuh).
-template <int L>
-__device__ __forceinline__ uint32_t mul_emit(uint32_t (&t)[L], const uint32_t (&a)[L], uint32_t b) {
-  const uint32_t out = mad_lo_cc(a[0], b, t[0]);
-  t[0] = madc_hi_cc(a[0], b, t[1]);
-#pragma unroll
-  for (int k = 1; k < L / 2; ++k) {
-    t[2 * k - 1] = madc_lo_cc(a[2 * k], b, t[2 * k]);
-    t[2 * k] = madc_hi_cc(a[2 * k], b, t[2 * k + 1]);
-  }
-  t[L - 1] = addc(0u, 0u);
-  t[0] = mad_lo_cc(a[1], b, t[0]);
-  t[1] = madc_hi_cc(a[1], b, t[1]);
-#pragma unroll
-  for (int k = 1; k < L / 2; ++k) {
-    t[2 * k] = madc_lo_cc(a[2 * k + 1], b, t[2 * k]);
-    t[2 * k + 1] = madc_hi_cc(a[2 * k + 1], b, t[2 * k + 1]);
-  }
-  return out;
-}
-
-__device__ __forceinline__ uint4 lds128a(uint32_t saddr) {
-  uint4 v;
-  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-               : "r"(saddr)
-               : "memory");
-  return v;
-}
-
-// Two adjacent column words (bias 0x3F000000 each, sums w < 2^23) as one
-// base-2^16 column: w_even + 256 w_odd < 2^31.01.  Shifting the odd word up a
-// byte drops its bias (0x3F000000 << 8 = 0 mod 2^32); the even word's bias is
-// its byte 3, cleared by the permute.  Neither depends on the running carry.
-__device__ __forceinline__ uint32_t pair_cols(uint32_t w_even, uint32_t w_odd) {
-  return tc::prmt(w_even, 0u, 0x4210u) + tc::prmt(w_odd, 0u, 0x2104u);
-}
+using tc::pair_cols;
 
 // t[j0 .. j0+NL) += (4*NL column words v, carry-propagated from the carry c
 // in base 2^16: two columns per step) + cin; the column carry returns in c and
@@ -237,12 +198,7 @@ __device__ __forceinline__ void sq_emit2(uint32_t c_lo, uint32_t c0, uint32_t c1
   tc_carry = addc(0u, 0u);
 }
 
-__device__ __forceinline__ void emit_digits(uint32_t arow, int p, uint32_t v) {
-  // limb p of T_lo: digits 4p..4p+3 = k-block p/2, bytes (p%2)*8 .. +7
-  asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(arow + (uint32_t)(p >> 1) * kKb + (uint32_t)(p & 1) * 8),
-               "r"(tc::prmt(v, 0u, 0x4140u)), "r"(tc::prmt(v, 0u, 0x4342u))
-               : "memory");
-}
+__device__ __forceinline__ void emit_digits(uint32_t arow, int p, uint32_t v) { tc::emit_digits(arow, p, v, kKb); }
 
 // T = A^2 for step 1 of the Montgomery product: each cross product once
 // (kH(kH-1)/2 words), doubled, plus the kH squares.  Row i adds a_i * a_j,
@@ -296,8 +252,8 @@ __device__ __forceinline__ void mont_step(uint32_t (&A)[kH], bool sq, uint32_t b
   if (sq) top = square_p(t, A, ts.arow);
 #pragma unroll 1
   for (int i0 = 0; i0 < (sq ? 0 : kH); i0 += 8) {
-    const uint4 b0 = lds128a(bsa + (uint32_t)(i0 >> 2) * bstr);
-    const uint4 b1 = lds128a(bsa + (uint32_t)((i0 >> 2) + 1) * bstr);
+    const uint4 b0 = tc::lds128(bsa + (uint32_t)(i0 >> 2) * bstr);
+    const uint4 b1 = tc::lds128(bsa + (uint32_t)((i0 >> 2) + 1) * bstr);
     uint32_t e[8];
     e[0] = mul_emit<kH>(t, A, b0.x);
     e[1] = mul_emit<kH>(t, A, b0.y);

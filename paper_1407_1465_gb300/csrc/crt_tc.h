@@ -24,6 +24,11 @@ constexpr size_t kImgKey = 2 * kImgPrime;          // q image, then p image
 // Host: the two B operands of one prime m (kH limbs, odd) in the core-matrix
 // layout the kernel copies into shared memory.  Returns false if m is even.
 bool build_tc_image(const uint32_t *m, uint8_t *out);
+// host helpers of the operand builders (tcprep.cpp)
+uint16_t f16_of_int(uint32_t x);
+size_t core_off(int row, int k, int rows);
+uint32_t byte_of(const uint32_t *w, int i);
+void neg_inverse_lo(const uint32_t *m, uint32_t *out, int n);   // -m^-1 mod 2^(32 n)
 
 // Workspace sizes for a launch of `count` operations on `grid` CTAs.
 size_t tc_tables_bytes(int grid, int window);
@@ -81,4 +86,36 @@ size_t ragged_tc_garner_smem();
 #endif
 
 }  // namespace tcr
+
+// RSA-4096 CRT with the Montgomery reduction on the tensor cores (crt_tc4.cu):
+// 2048-bit primes, two reduction rounds of r = 2^1024 per Montgomery product.
+namespace tc4 {
+constexpr int kH = 64;                   // limbs per prime (2048-bit primes)
+constexpr int kDig = 128;                // byte digits per reduction round (r = 2^1024)
+constexpr int kRows = 128;               // operations per tile (MMA M)
+constexpr int kTiles = 2;                // tiles per CTA
+constexpr int kThreads = kRows * kTiles;
+constexpr int kN1 = kDig;                // MMA 1 output columns (digits of mu)
+constexpr int kN2 = 256;                 // MMA 2 output columns (positions 124 .. 379 of mu * m)
+constexpr int kN2First = kDig - 4;
+constexpr int kKt = kDig + 16;           // K extent of the B images (digits + bias block)
+constexpr size_t kImgB1 = (size_t)kN1 * kKt * 2;   // 36864 bytes
+constexpr size_t kImgB2 = (size_t)kN2 * kKt * 2;   // 73728 bytes
+constexpr size_t kImgPrime = kImgB1 + kImgB2;      // per prime
+constexpr size_t kImgKey = 2 * kImgPrime;          // q image, then p image
+
+// Host: the two B operands of one 2048-bit prime m (kH limbs, odd): B1 = the
+// Toeplitz matrix of -m^-1 mod 2^1024 (128 x 128 + bias), B2 = that of m for
+// output positions 124 .. 379 (256 x 128 + bias).  Returns false if m is even.
+bool build_tc4_image(const uint32_t *m, uint8_t *out);
+size_t tc4_tables_bytes(int grid, int window);
+size_t tc4_halves_bytes(uint32_t count);
+int tc4_grid(uint32_t count, int sm_count);
+size_t tc4_smem_bytes();
+#if defined(__CUDACC__)
+cudaError_t launch_crt_tc4(const uint32_t *keyrec, const void *image, const uint32_t *msgs, uint32_t *out,
+                           int32_t *status, uint32_t count, int grid, int window, void *tables, void *halves,
+                           uint32_t wait_polls, cudaStream_t s);
+#endif
+}  // namespace tc4
 }  // namespace rsagpu

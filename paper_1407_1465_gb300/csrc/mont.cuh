@@ -131,6 +131,30 @@ __device__ __forceinline__ void mul_acc(uint32_t (&t)[L + 2], const uint32_t (&a
   t[L + 1] = addc(t[L + 1], 0u);
 }
 
+// One row of a product scan: t + a*b, the lowest limb returned and the rest
+// shifted down one limb (t[j] <- position j+1).  t < 2^(32L) on entry, so the
+// sum fits in L+1 limbs.  Even and odd limbs of a in two carry chains as in
+// mul_acc.
+template <int L>
+__device__ __forceinline__ uint32_t mul_emit(uint32_t (&t)[L], const uint32_t (&a)[L], uint32_t b) {
+  const uint32_t out = mad_lo_cc(a[0], b, t[0]);
+  t[0] = madc_hi_cc(a[0], b, t[1]);
+#pragma unroll
+  for (int k = 1; k < L / 2; ++k) {
+    t[2 * k - 1] = madc_lo_cc(a[2 * k], b, t[2 * k]);
+    t[2 * k] = madc_hi_cc(a[2 * k], b, t[2 * k + 1]);
+  }
+  t[L - 1] = addc(0u, 0u);
+  t[0] = mad_lo_cc(a[1], b, t[0]);
+  t[1] = madc_hi_cc(a[1], b, t[1]);
+#pragma unroll
+  for (int k = 1; k < L / 2; ++k) {
+    t[2 * k] = madc_lo_cc(a[2 * k + 1], b, t[2 * k]);
+    t[2 * k + 1] = madc_hi_cc(a[2 * k + 1], b, t[2 * k + 1]);
+  }
+  return out;
+}
+
 // q = t_0 * n'; t = (t + q*N) / 2^32.  Same even/odd chains as mul_acc; every
 // result is written one limb down (position p goes to t[p-1]), which is the
 // division by 2^32, done in place in increasing position order.

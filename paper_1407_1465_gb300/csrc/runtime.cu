@@ -189,10 +189,31 @@ int Ctx::run_key(const KeySlot &k, int kind, uint64_t count, const uint32_t *msg
     return RSA_OK;
   }
   const Tune t = tune_for(k.nbits, kind);
+  if (kind == RSA_EXP_PRIVATE_CRT && t.variant == 3 && L == 2 * (uint32_t)tc4::kH) {
+    // RSA-4096: the Montgomery reduction on the tensor cores in two rounds (crt_tc4.cu)
+    if (!k.d_tc) return set_error(RSA_ERR_UNSUPPORTED, "the tensor-core CRT path needs a key with p and q");
+    if (count > 0xFFFFFFFFull) return set_error(RSA_ERR_ARG, "count out of range");
+    if (t.window != 3 && t.window != 4)
+      return set_error(RSA_ERR_UNSUPPORTED, "the tensor-core CRT path has windows 3 and 4");
+    const int grid = tc4::tc4_grid((uint32_t)count, sm_count);
+    int rc = ensure(w.tables, tc4::tc4_tables_bytes(grid, t.window));
+    if (rc) return rc;
+    rc = ensure(w.halves, tc4::tc4_halves_bytes((uint32_t)count));
+    if (rc) return rc;
+    uint32_t polls = tcr::kDefaultWaitPolls;
+    if (const char *ev = std::getenv("RSAGPU_TC_WAIT_POLLS")) polls = (uint32_t)std::strtoul(ev, nullptr, 10);
+    e = tc4::launch_crt_tc4(k.d_rec, k.d_tc, msgs, out, status, (uint32_t)count, grid, t.window, w.tables.ptr,
+                            w.halves.ptr, polls, s);
+    if (e != cudaSuccess) return cuda_error(e, "launch crt_tc4 kernels");
+    stats.kernel_launches += 2;
+    last_grid = grid;
+    last_threads = tc4::kThreads;
+    return RSA_OK;
+  }
   if (kind == RSA_EXP_PRIVATE_CRT && t.variant == 3) {
-    // Montgomery reduction on the tensor cores (crt_tc.cu): 2048-bit keys only
+    // Montgomery reduction on the tensor cores (crt_tc.cu): 2048-bit keys
     if (L != 2 * (uint32_t)tcr::kH || !k.d_tc)
-      return set_error(RSA_ERR_UNSUPPORTED, "the tensor-core CRT path needs a 2048-bit key with p and q");
+      return set_error(RSA_ERR_UNSUPPORTED, "the tensor-core CRT path needs a 2048- or 4096-bit key with p and q");
     if (count > 0xFFFFFFFFull) return set_error(RSA_ERR_ARG, "count out of range");
     if (t.window != 3 && t.window != 4)
       return set_error(RSA_ERR_UNSUPPORTED, "the tensor-core CRT path has windows 3 and 4");
@@ -412,6 +433,13 @@ static int make_record(uint32_t nbits, const uint32_t *n, const uint32_t *e, uin
   return RSA_OK;
 }
 
+int rsa_tc4_operand_image(const uint32_t *m, void *out, size_t out_bytes) {
+  if (!m || !out) return set_error(RSA_ERR_ARG, "null pointer");
+  if (out_bytes < tc4::kImgPrime) return set_error(RSA_ERR_ARG, "output buffer too small");
+  if (!tc4::build_tc4_image(m, static_cast<uint8_t *>(out))) return set_error(RSA_ERR_ARG, "modulus must be odd");
+  return RSA_OK;
+}
+
 int rsa_tc_operand_image(const uint32_t *m, void *out, size_t out_bytes) {
   if (!m || !out) return set_error(RSA_ERR_ARG, "null argument");
   if (out_bytes < tcr::kImgPrime) return set_error(RSA_ERR_ARG, "output buffer too small");
@@ -460,14 +488,17 @@ int rsa_keyload(rsa_ctx *ctx, uint32_t nbits, const uint32_t *n, const uint32_t 
     c->release(bytes);
     return cuda_error(ce, "cudaMemcpy key record");
   }
-  // tensor-core operand images of q and p for the RSA-2048 CRT path
+  // tensor-core operand images of q and p for the RSA-2048 and RSA-4096 CRT paths
   void *dtc = nullptr;
   size_t tc_bytes = 0;
-  if (L == 2 * (uint32_t)tcr::kH && (flags & KEY_HAS_CRT)) {
-    constexpr KeyLayout lay(2 * tcr::kH);
-    std::vector<uint8_t> img(tcr::kImgKey);
-    const bool ok = tcr::build_tc_image(rec.data() + lay.q, img.data()) &&
-                    tcr::build_tc_image(rec.data() + lay.p, img.data() + tcr::kImgPrime);
+  if ((L == 2 * (uint32_t)tcr::kH || L == 2 * (uint32_t)tc4::kH) && (flags & KEY_HAS_CRT)) {
+    const bool four = L == 2 * (uint32_t)tc4::kH;
+    const KeyLayout lay(L);
+    std::vector<uint8_t> img(four ? tc4::kImgKey : tcr::kImgKey);
+    const bool ok = four ? tc4::build_tc4_image(rec.data() + lay.q, img.data()) &&
+                               tc4::build_tc4_image(rec.data() + lay.p, img.data() + tc4::kImgPrime)
+                         : tcr::build_tc_image(rec.data() + lay.q, img.data()) &&
+                               tcr::build_tc_image(rec.data() + lay.p, img.data() + tcr::kImgPrime);
     int rc2 = ok ? c->reserve(img.size()) : set_error(RSA_ERR_KEY, "p and q must be odd");
     if (rc2 == RSA_OK) {
       if (cudaMalloc(&dtc, img.size()) == cudaSuccess &&

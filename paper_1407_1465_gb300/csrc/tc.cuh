@@ -143,6 +143,31 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
 __device__ __forceinline__ void sts128(uint32_t saddr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(saddr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
+__device__ __forceinline__ uint4 lds128(uint32_t saddr) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(saddr)
+               : "memory");
+  return v;
+}
+
+// Two adjacent MMA output columns (bias 0x3F000000 each, sums w < 2^23) as one
+// base-2^16 column: w_even + 256 w_odd < 2^31.01.  Shifting the odd word up a
+// byte drops its bias (0x3F000000 << 8 = 0 mod 2^32); the even word's bias is
+// its byte 3, cleared by the permute.  Neither depends on a running carry.
+__device__ __forceinline__ uint32_t pair_cols(uint32_t w_even, uint32_t w_odd) {
+  return prmt(w_even, 0u, 0x4210u) + prmt(w_odd, 0u, 0x2104u);
+}
+
+// Limb p of a number as four fp16 byte digits into a K-major core-matrix row:
+// digits 4p .. 4p+3 are k-block p/2, bytes (p%2)*8 .. +7 of the row's slot
+// (arow: the row's address in k-block 0; kb: the k-block stride).
+__device__ __forceinline__ void emit_digits(uint32_t arow, int p, uint32_t v, uint32_t kb) {
+  asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(arow + (uint32_t)(p >> 1) * kb + (uint32_t)(p & 1) * 8),
+               "r"(prmt(v, 0u, 0x4140u)), "r"(prmt(v, 0u, 0x4342u))
+               : "memory");
+}
 
 }  // namespace tc
 }  // namespace rsagpu

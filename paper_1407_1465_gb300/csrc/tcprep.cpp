@@ -27,8 +27,6 @@
 namespace rsagpu {
 namespace tcr {
 
-namespace {
-
 // fp16 bit pattern of an integer 0 <= x < 2048 (exact).
 uint16_t f16_of_int(uint32_t x) {
   if (x == 0) return 0;
@@ -83,7 +81,7 @@ void neg_inverse(const uint32_t *m, uint32_t *out, int n) {
 
 uint32_t byte_of(const uint32_t *w, int i) { return (w[i >> 2] >> (8 * (i & 3))) & 0xFFu; }
 
-}  // namespace
+void neg_inverse_lo(const uint32_t *m, uint32_t *out, int n) { neg_inverse(m, out, n); }
 
 bool build_tc_image(const uint32_t *m, uint8_t *out) {
   if ((m[0] & 1u) == 0) return false;
@@ -118,4 +116,46 @@ bool build_tc_image(const uint32_t *m, uint8_t *out) {
 }
 
 }  // namespace tcr
+
+namespace tc4 {
+
+// The operands of one 2048-bit prime m for crt_tc4.cu, where a Montgomery
+// product reduces modulo m in two rounds of r = 2^1024:
+//   B1 (128 x 144): row n, column k < 128: byte n-k of m' = -m^-1 mod 2^1024
+//       (it depends only on m mod 2^1024); columns 128..143: 2048 (bias)
+//   B2 (256 x 144): row j = output position 124 + j of mu * m, column k < 128:
+//       byte 124+j-k of m (0 outside 0..255); columns 128..143: 2048
+bool build_tc4_image(const uint32_t *m, uint8_t *out) {
+  if ((m[0] & 1u) == 0) return false;
+  uint32_t mp[kDig / 4];
+  tcr::neg_inverse_lo(m, mp, kDig / 4);
+  std::memset(out, 0, kImgPrime);
+  uint8_t *b1 = out, *b2 = out + kImgB1;
+  const uint16_t bias = tcr::f16_of_int(2048);
+  for (int n = 0; n < kN1; ++n)
+    for (int k = 0; k < kKt; ++k) {
+      uint16_t h;
+      if (k < kDig) {
+        const int i = n - k;
+        h = (i >= 0 && i < kDig) ? tcr::f16_of_int(tcr::byte_of(mp, i)) : 0;
+      } else {
+        h = bias;
+      }
+      std::memcpy(b1 + tcr::core_off(n, k, kN1), &h, 2);
+    }
+  for (int j = 0; j < kN2; ++j)
+    for (int k = 0; k < kKt; ++k) {
+      uint16_t h;
+      if (k < kDig) {
+        const int i = kN2First + j - k;
+        h = (i >= 0 && i < 4 * kH) ? tcr::f16_of_int(tcr::byte_of(m, i)) : 0;
+      } else {
+        h = bias;
+      }
+      std::memcpy(b2 + tcr::core_off(j, k, kN2), &h, 2);
+    }
+  return true;
+}
+
+}  // namespace tc4
 }  // namespace rsagpu

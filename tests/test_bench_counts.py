@@ -129,3 +129,28 @@ def test_measured_roofline_fraction_uses_the_probe_figure(monkeypatch):
     r = bench.alu_roofline(3.25, 7, "test")
     assert r["peak"] == 6.5 and r["frac"] == 0.5 and r["peak_source"] == "measured"
     assert abs(bench.derived_peak_tprod(152, 2070.0) - 10.06848) < 1e-9
+
+
+def _tc4_walk(W):
+    """The RSA-4096 tensor-core path's work per decryption, replaying its step
+    loop (as _tc_walk) with every step a 64 x 64-limb product and two reduction
+    rounds; the method's MMA work by enumerating the digit pairs of
+    mu = (T mod 2^1024) m' and of positions 124..379 of mu * m (m: 256 digits)."""
+    H, D = 64, 128
+    pairs1 = sum(1 for n in range(D) for k in range(D) if 0 <= n - k < D)
+    pairs2 = sum(1 for j in range(D - 4, D + 252) for i in range(D) if 0 <= j - i < 2 * D)
+    nwin = -(-(32 * H) // W)
+    ntab, nexp = 1 << W, (nwin - 1) * (W + 1)
+    prods = flops = method = 0
+    for pi in (0, 1):
+        for _ in range(ntab + nexp + (1 if pi == 0 else 0)):
+            prods += H * H
+            flops += 2 * (2 * 128 * (9 * 16) + 2 * 256 * (9 * 16))
+            method += 2 * 2 * (pairs1 + pairs2)
+    prods += 2 * (2 * H * H + H) + H * H
+    return prods, flops, method
+
+
+@pytest.mark.parametrize("W", [3, 4])
+def test_tc4_work_per_op_matches_the_step_loop(W):
+    assert bench.tc4_work_per_op(W) == _tc4_walk(W)

@@ -100,12 +100,15 @@ def mixed_keys(ctx):
     return keys, kids
 
 
-@pytest.mark.parametrize("wide", ["100", "0"])
+@pytest.mark.parametrize("wide", ["100", "100/16", "0"])
 @pytest.mark.parametrize("count", [1, 63, 700])
 def test_ragged_mix_matches_oracle(torch_cuda, ctx, mixed_keys, monkeypatch, count, wide):
     """Small batches run 2048/4096-bit CRT with 4/8 lanes per operation
-    (RSAGPU_RAGGED_WIDE_PCT=100, the default); 0 forces one/four lanes."""
-    monkeypatch.setenv("RSAGPU_RAGGED_WIDE_PCT", wide)
+    (RSAGPU_RAGGED_WIDE_PCT=100, the default; "100/16": 4096-bit CRT on 16
+    lanes); 0 forces one/four lanes."""
+    pct, _, lanes = wide.partition("/")
+    monkeypatch.setenv("RSAGPU_RAGGED_WIDE_PCT", pct)
+    monkeypatch.setenv("RSAGPU_RAGGED_LANES_4096", lanes or "8")
     keys, kids = mixed_keys
     ops, key_ids, sels, offsets, packed = build_mix(keys, kids, count, 100 + count)
     out, st, rc = run_batch(torch_cuda, ctx, key_ids, sels, offsets, packed)
@@ -220,3 +223,28 @@ def test_ragged_autotune_batch(torch_cuda, ctx, mixed_keys):
             ctx.set_tuning(2048, CRT, window_big=4)    # ragged-only fields
     finally:
         ctx.set_tuning(0, RSA_TUNE_RAGGED, reset=True)
+
+
+@pytest.mark.parametrize("lanes", ["8", "16"])
+def test_ragged_small_tiles_all_run(torch_cuda, ctx, mixed_keys, monkeypatch, lanes):
+    """A batch of 4096-bit CRT operations only, small enough for the latency
+    shapes (8 or 16 lanes per operation: 4 or 2 operations per tile).  Its tiles
+    outnumber count/8 + buckets, so every tile must fit the planner's tile list
+    (a list sized for 8-operation tiles dropped the excess ones and left their
+    operations unrun).  Every result equals the same messages run through
+    rsa_modexp_key; sampled ones equal the oracle."""
+    monkeypatch.setenv("RSAGPU_RAGGED_LANES_4096", lanes)
+    keys, kids = mixed_keys
+    k = next(i for i, key in enumerate(keys) if key.bits == 4096)
+    key = keys[k]
+    count = 600
+    rows = workloads.messages_below(key.n, count, 44, ("small-tiles", lanes))
+    offsets = np.arange(count, dtype=np.uint64) * 128
+    key_ids = np.full(count, kids[k], dtype=np.int32)
+    sels = np.full(count, CRT, dtype=np.uint8)
+    out, st, rc = run_batch(torch_cuda, ctx, key_ids, sels, offsets, rows.reshape(-1).copy())
+    assert rc == 0 and (st == 0).all()
+    alone = ctx.modexp_key(kids[k], CRT, torch_cuda.from_numpy(rows.view(np.int32)).cuda())
+    assert np.array_equal(out.reshape(count, 128), alone.cpu().numpy().view(np.uint32))
+    idx = [0, 1, 299, 598, 599]
+    assert np.array_equal(out.reshape(count, 128)[idx], oracle.crt_batch(rows[idx], key.d, key.p, key.q))

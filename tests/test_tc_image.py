@@ -141,3 +141,85 @@ def test_reduction_replay_matches_integer_montgomery(lib, key):
 def test_worst_case_columns_stay_below_2_23():
     """128 products of two bytes: the largest column sum the MMAs can produce."""
     assert 128 * 255 * 255 < 2 ** 23
+
+
+# ---------------------------------------------------------------- RSA-4096: 2048-bit primes, two rounds
+R4, r4 = 1 << 2048, 1 << 1024
+
+
+def decode_k(img, off, rows):
+    return decode(img, off, rows)
+
+
+def toeplitz_m(dig, rows, first, ndig):
+    """rows x KT: row j, column k < 128: digit first + j - k of a number of ndig digits."""
+    out = np.zeros((rows, KT))
+    for j in range(rows):
+        for k in range(128):
+            i = first + j - k
+            if 0 <= i < ndig:
+                out[j, k] = dig[i]
+    out[:, 128:] = 2048.0
+    return out
+
+
+@pytest.fixture(scope="module")
+def key4096():
+    return workloads.gen_keys([(4096, 0)], workloads.DEFAULT_SEED)[0]
+
+
+def test_tc4_image_is_the_toeplitz_of_m_and_m_prime(lib, key4096):
+    from paper_1407_1465_gb300 import rsa_tc4_operand_image
+    from paper_1407_1465_gb300 import RSA_TC4_IMAGE_BYTES
+    for m in (key4096.p, key4096.q):
+        img = rsa_tc4_operand_image(m)
+        assert img.size == RSA_TC4_IMAGE_BYTES == 128 * KT * 2 + 256 * KT * 2
+        mp = (-pow(m, -1, r4)) % r4
+        b1, b2 = decode_k(img, 0, 128), decode_k(img, 128 * KT * 2, 256)
+        assert np.array_equal(b1, toeplitz_m(digits(mp), 128, 0, 128))
+        assert np.array_equal(b2, toeplitz_m(digits(m, 256), 256, 124, 256))
+
+
+def replay_round4(V, m, b1, b2):
+    """One reduction round of the RSA-4096 kernel on the decoded operands:
+    mu = (V mod r) m' mod r by MMA 1 and a carry pass, positions 124..379 of
+    mu * m by MMA 2 and 380..383 directly, the carry out of the low half from
+    four columns, then (V + mu m) / r."""
+    bias_a = np.full(16, 2.0 ** -16)
+    v_lo = digits(V % r4)
+    col1 = (np.concatenate([v_lo * 2.0 ** -24, bias_a]) @ b1.T - 0.5) * 2.0 ** 24
+    assert np.all(col1 == np.round(col1)) and col1.max() < 2 ** 23
+    mu_d, _ = carry_pass(col1.astype(np.int64))
+    w = (np.concatenate([mu_d * 2.0 ** -24, bias_a]) @ b2.T - 0.5) * 2.0 ** 24   # positions 124..379
+    assert np.all(w == np.round(w)) and w.max() < 2 ** 23
+    w = w.astype(np.int64)
+    md = digits(m, 256)
+    top = [mu_d[125] * md[255] + mu_d[126] * md[254] + mu_d[127] * md[253],
+           mu_d[126] * md[255] + mu_d[127] * md[254], mu_d[127] * md[255], 0]
+    w = np.concatenate([w, np.array(top, dtype=np.int64)])                      # positions 124..383
+    y, c = carry_pass([w[i] + v_lo[124 + i] for i in range(4)])
+    carry = c + (1 if y.any() else 0)
+    hi_d, cout = carry_pass(w[4:], carry)                                        # positions 128..383
+    mu = int.from_bytes(bytes(mu_d.astype(np.uint8)), "little")
+    return mu, (V >> 1024) + int.from_bytes(bytes(hi_d.astype(np.uint8)), "little") + (cout << 2048)
+
+
+def test_tc4_two_round_reduction_replay_matches_integer_montgomery(lib, key4096):
+    """Two rounds of r = 2^1024 give T R^-1 mod m (R = 2^2048) below 2m, over
+    random and extreme products T < m^2 (the kernel's operands are below m)."""
+    from paper_1407_1465_gb300 import rsa_tc4_operand_image
+    rng = np.random.default_rng(9)
+    for m in (key4096.p, key4096.q):
+        img = rsa_tc4_operand_image(m)
+        b1, b2 = decode_k(img, 0, 128), decode_k(img, 128 * KT * 2, 256)
+        mp1 = (-pow(m, -1, r4)) % r4
+        rinv = pow(R4, -1, m)
+        cases = [0, 1, (m - 1) ** 2, (m - 1) * (m - 2), (m - 1) * r4, r4 - 1, r4, R4 - 1, (R4 - 1) * 5 % (m * m)]
+        cases += [(int.from_bytes(rng.bytes(256), "little") % m) * (int.from_bytes(rng.bytes(256), "little") % m)
+                  for _ in range(12)]
+        for T in cases:
+            mu1, T1 = replay_round4(T, m, b1, b2)
+            assert mu1 == (T % r4) * mp1 % r4 and T1 == (T + mu1 * m) // r4 and (T + mu1 * m) % r4 == 0
+            mu2, T2 = replay_round4(T1, m, b1, b2)
+            assert T2 == (T1 + mu2 * m) // r4 and T2 < 2 * m
+            assert (T2 - m if T2 >= m else T2) == T * rinv % m
