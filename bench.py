@@ -153,9 +153,10 @@ def tc4_work_per_op(window: int):
     decryption on the tensor-core path (2048-bit primes, two reduction rounds
     of r = 2^1024 per Montgomery product): per half 2 input products, 2^w - 2
     table products, (windows - 1)(w + 1) window steps (+1 for q leaving
-    Montgomery form); every step issues a 64 x 64-limb product (squarings
-    included) and two rounds of MMA 1 (N = 128) and MMA 2 (N = 256), 9 K-steps
-    each; Garner adds two CIOS products and one 64 x 64 product.
+    Montgomery form); a squaring issues 64*65/2 word products (cross products
+    once), another step 64 x 64, and every step two rounds of MMA 1 (N = 128)
+    and MMA 2 (N = 256), 9 K-steps each; Garner adds two CIOS products and one
+    64 x 64 product.
     Returns (issued word products, issued MMA FLOPs, method MMA FLOPs): the
     method's share of a round is the nonzero part of its two Toeplitz products,
     D(D+1)/2 byte products for mu = (T mod r) m' mod r and those of positions
@@ -163,7 +164,8 @@ def tc4_work_per_op(window: int):
     H, D = 64, 128
     nwin = -(-32 * H // window)
     steps = 2 * ((1 << window) + (nwin - 1) * (window + 1)) + 1
-    issued = steps * H * H + 2 * (2 * H * H + H) + H * H
+    squares = 2 * (1 + (nwin - 1) * window)
+    issued = squares * (H * (H + 1) // 2) + (steps - squares) * H * H + 2 * (2 * H * H + H) + H * H
     issued_flops = steps * 2 * (9 * 2 * 128 * 16 + 9 * 2 * 256 * 16)
     mma1 = D * (D + 1) // 2
     mma2 = sum(min(j, D - 1) - max(0, j - (2 * D - 1)) + 1 for j in range(D - 4, D - 4 + 256))
@@ -1091,18 +1093,34 @@ def main():
                                "Fig. 5): the benchmark key's 65536 messages, one rsa_modexp_key per step")
         line["toy"] = dict(toy_rate(), what="the paper's toy key n = 17947, e = 131, d = 137 (Sec. 2): 4096 "
                            "packets in [0, 2525] encrypted then decrypted per step; launch-latency bound")
-        sweep4096 = {w: single_key_rate(4096, 16384, "crt", window=w, steps=3, warmup=1) for w in (4, 5, 6)}
+        # RSA-4096 CRT: the default path (Montgomery reductions on the tensor cores, w = 3) and the
+        # CUDA-core four-lane kernel over windows 4-6
+        tc4096 = single_key_rate(4096, 16384, "crt", steps=3, warmup=1)
+        sweep4096 = {w: single_key_rate(4096, 16384, "crt", window=w, steps=3, warmup=1, threads_per_op=4)
+                     for w in (4, 5, 6)}
         best_w = max(sweep4096, key=lambda w: sweep4096[w]["value"])
+        iss4, fl4, mfl4 = tc4_work_per_op(tc4096["window"])
+        tpk, tsrc = measured_bf16_tflops()
+        roof4 = alu_roofline(iss4 * tc4096["value"] / 1e12, local,
+                             "32x32->64 word products the CUDA cores issue per second (per-message products and "
+                             "squarings, Garner); the Montgomery reductions run on the tensor cores in two rounds")
+        roof4["tensor"] = {"achieved": mfl4 * tc4096["value"] / 1e12, "peak": tpk, "unit": "TFLOP/s",
+                           "frac": mfl4 * tc4096["value"] / 1e12 / tpk, "peak_source": tsrc,
+                           "issued_frac": fl4 * tc4096["value"] / 1e12 / tpk}
         line["rsa4096"] = {
-            "what": "RSA-4096 CRT decryption: 1 seeded key (two 2048-bit primes), 16384 ciphertexts, window "
-                    "width swept 4-6 (four lanes per operation)",
-            "value": sweep4096[best_w]["value"], "unit": "decrypts/s", "best_window": best_w,
-            "window_sweep": {str(w): {"value": r["value"], "ms_per_batch": r["ms_per_batch"]}
-                             for w, r in sweep4096.items()},
-            "roofline": alu_roofline(rsa_products_per_op(4096, RSA_EXP_PRIVATE_CRT, e=65537, window=best_w) *
-                                     sweep4096[best_w]["value"] / 1e12, local,
-                                     "word products per second under the CIOS count 2H^2 + H per Montgomery "
-                                     "product (what the four-lane kernel issues)")}
+            "what": "RSA-4096 CRT decryption: 1 seeded key (two 2048-bit primes), 16384 ciphertexts; the default "
+                    "path (tensor-core Montgomery reductions, variant 3) and the four-lane CUDA-core kernel with "
+                    "the window width swept 4-6",
+            "value": tc4096["value"], "unit": "decrypts/s", "ms_per_batch": tc4096["ms_per_batch"],
+            "window": tc4096["window"], "variant": tc4096["variant"], "roofline": roof4,
+            "cuda_core_window_sweep": {str(w): {"value": r["value"], "ms_per_batch": r["ms_per_batch"]}
+                                       for w, r in sweep4096.items()},
+            "cuda_core_best_window": best_w,
+            "cuda_core_roofline": alu_roofline(
+                rsa_products_per_op(4096, RSA_EXP_PRIVATE_CRT, e=65537, window=best_w) *
+                sweep4096[best_w]["value"] / 1e12, local,
+                "word products per second under the CIOS count 2H^2 + H per Montgomery product (what the "
+                "four-lane kernel issues)")}
     if rank == 0 and ws == 1 and not args.no_ragged and args.workload == "rsa2048" and args.kind == "crt":
         # the ragged batch (256 keys, 200000 operations, one graph launch) against
         # a loop of one launch per (key, kind) group

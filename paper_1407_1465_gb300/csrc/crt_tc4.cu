@@ -212,11 +212,77 @@ __device__ __forceinline__ uint32_t reduce_round(uint32_t (&X)[NX], uint32_t top
   return c + cin;
 }
 
+// ---------------------------------------------------------------- squaring
+// T = A^2 = 2C + D (C: the cross products a_i a_j, i < j, each once; D: the
+// squares a_k^2 at limbs 2k, 2k+1).  Row i adds a_i a_j for j > i in two carry
+// chains (odd and even j - i); after row i the limbs up to 2i+2 of C are
+// final, so T's limbs 2i+1 and 2i+2 are formed (the doubling shifts in the top
+// bit of the limb below) and leave at once, as in the product: limbs 0..31 as
+// digits, 32..63 into the high stage, 64..127 into t.
+template <int I, int J0>
+__device__ __forceinline__ void sq_chain(uint32_t (&c)[2 * kH], const uint32_t (&a)[kH]) {
+  if constexpr (J0 < kH) {
+    c[I + J0] = mad_lo_cc(a[I], a[J0], c[I + J0]);
+    c[I + J0 + 1] = madc_hi_cc(a[I], a[J0], c[I + J0 + 1]);
+#pragma unroll
+    for (int j = J0 + 2; j < kH; j += 2) {
+      c[I + j] = madc_lo_cc(a[I], a[j], c[I + j]);
+      c[I + j + 1] = madc_hi_cc(a[I], a[j], c[I + j + 1]);
+    }
+    constexpr int last = J0 + ((kH - 1 - J0) / 2) * 2;
+    c[I + last + 2] = addc(c[I + last + 2], 0u);
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void sq_out(uint32_t v, const Tile &ts, uint32_t (&t)[kH], uint32_t &top) {
+  if constexpr (P < 32) {
+    tc::emit_digits(ts.arow, P, v, kKb);
+    if constexpr (P == 31) top = v;
+  } else if constexpr (P < 64) {
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(ts.hrow + (uint32_t)((P - 32) >> 2) * (kHiBytes / 8) +
+                                                 (uint32_t)((P - 32) & 3) * 4u),
+                 "r"(v)
+                 : "memory");
+  } else {
+    t[P - 64] = v;
+  }
+}
+
+template <int I>
+__device__ __forceinline__ void sq_rows(uint32_t (&c)[2 * kH], const uint32_t (&a)[kH], uint32_t (&t)[kH],
+                                        const Tile &ts, uint32_t &tc_carry, uint32_t &top) {
+  if constexpr (I < kH - 1) {
+    sq_chain<I, I + 1>(c, a);
+    sq_chain<I, I + 2>(c, a);
+    const uint32_t x0 = __funnelshift_l(c[2 * I], c[2 * I + 1], 1), x1 = __funnelshift_l(c[2 * I + 1], c[2 * I + 2], 1);
+    (void)add_cc(tc_carry, 0xFFFFFFFFu);   // carry flag <- tc_carry
+    const uint32_t t0 = addc_cc(x0, __umulhi(a[I], a[I]));
+    const uint32_t t1 = addc_cc(x1, a[I + 1] * a[I + 1]);
+    tc_carry = addc(0u, 0u);
+    sq_out<2 * I + 1>(t0, ts, t, top);
+    sq_out<2 * I + 2>(t1, ts, t, top);
+    sq_rows<I + 1>(c, a, t, ts, tc_carry, top);
+  }
+}
+
+// T = A^2 into the A buffer (limbs 0..31), the high stage (32..63) and t (64..127); returns limb 31
+__device__ __forceinline__ uint32_t square(uint32_t (&t)[kH], const uint32_t (&a)[kH], const Tile &ts) {
+  uint32_t c[2 * kH];
+#pragma unroll
+  for (int j = 0; j < 2 * kH; ++j) c[j] = 0u;
+  uint32_t tc_carry = 0u, top = 0u;
+  sq_out<0>(a[0] * a[0], ts, t, top);
+  sq_rows<0>(c, a, t, ts, tc_carry, top);
+  t[kH - 1] = __funnelshift_l(c[2 * kH - 2], c[2 * kH - 1], 1) + __umulhi(a[kH - 1], a[kH - 1]) + tc_carry;
+  return top;
+}
+
 // ---------------------------------------------------------------- one Montgomery step
 // A = A * B * R^-1 mod m (A < m, B < m; R = 2^2048).  B: 64 limbs in shared
 // memory, groups 0..7 (limbs 0..31) at lo + g*lo_str, groups 8..15 at
 // hi + (g-8)*hi_str (the thread's stage, or a key constant).
-__device__ __forceinline__ void mont_step(uint32_t (&A)[kH], uint32_t lo, uint32_t lo_str, uint32_t hi,
+__device__ __forceinline__ void mont_step(uint32_t (&A)[kH], bool sq, uint32_t lo, uint32_t lo_str, uint32_t hi,
                                           uint32_t hi_str, Tile &ts, const uint32_t *Ms, uint32_t polls) {
   // 1. T = A * B: limbs 0..31 leave as digits (A buffer), 32..63 as words
   //    (high stage), 64..127 stay in t.  Block i0 reads B limbs i0..i0+7
@@ -227,8 +293,9 @@ __device__ __forceinline__ void mont_step(uint32_t (&A)[kH], uint32_t lo, uint32
 #pragma unroll
   for (int j = 0; j < kH; ++j) t[j] = 0u;
   uint32_t top = 0u;
+  if (sq) top = square(t, A, ts);
 #pragma unroll 1
-  for (int i0 = 0; i0 < kH; i0 += 8) {
+  for (int i0 = 0; i0 < (sq ? 0 : kH); i0 += 8) {
     const uint32_t g = (uint32_t)(i0 >> 2);
     const uint32_t a0 = g < 8 ? lo + g * lo_str : hi + (g - 8) * hi_str;
     const uint32_t a1 = g + 1 < 8 ? lo + (g + 1) * lo_str : hi + (g - 7) * hi_str;
@@ -326,11 +393,6 @@ __device__ __forceinline__ void stage_from_table(uint8_t *smem, const Tile &ts, 
 #pragma unroll
   for (int g = 0; g < kH / 4; ++g) *stage_group(smem, ts, g) = entry[g * kRows];
 }
-__device__ __forceinline__ void stage_put(uint8_t *smem, const Tile &ts, const uint32_t (&A)[kH]) {
-#pragma unroll
-  for (int g = 0; g < kH / 4; ++g)
-    *stage_group(smem, ts, g) = make_uint4(A[4 * g], A[4 * g + 1], A[4 * g + 2], A[4 * g + 3]);
-}
 __device__ __forceinline__ void stage_get(uint32_t (&A)[kH], uint8_t *smem, const Tile &ts) {
 #pragma unroll
   for (int g = 0; g < kH / 4; ++g) {
@@ -341,8 +403,8 @@ __device__ __forceinline__ void stage_get(uint32_t (&A)[kH], uint8_t *smem, cons
 
 // ---------------------------------------------------------------- one tile's exponentiation
 // x = c R mod m from the 128-limb message row (c_lo R^2 R^-1 + c_hi R^3 R^-1),
-// then the constant-time fixed window over the prime's exponent; squarings
-// stage A and run the general product.  The q half (pi == 0) leaves
+// then the constant-time fixed window over the prime's exponent (squarings by
+// `square`, products with the staged B).  The q half (pi == 0) leaves
 // Montgomery form.
 template <int W>
 __device__ __forceinline__ void exp_tile(uint32_t (&A)[kH], Tile &ts, uint8_t *smem, const uint32_t *msg, uint32_t pi,
@@ -359,6 +421,7 @@ __device__ __forceinline__ void exp_tile(uint32_t (&A)[kH], Tile &ts, uint8_t *s
 #pragma unroll 1
   for (int st = 0; st < nst; ++st) {
     uint32_t lo = slo, lo_str = kKb, hi = shi, hi_str = kHiBytes / 8;
+    bool sq = false;
     if (st == 0) {                      // c_lo * R mod m
       load_row<kH>(A, msg, true);
       lo = kca + 4 * kKr2; lo_str = 16; hi = lo + 128; hi_str = 16;
@@ -373,7 +436,7 @@ __device__ __forceinline__ void exp_tile(uint32_t (&A)[kH], Tile &ts, uint8_t *s
         uint32_t one[kH];
         from_uniform<kH>(one, reinterpret_cast<const uint4 *>(kc + kKone));
         tbl_store(tbl, 0, one);
-        stage_put(smem, ts, A);         // T[2] = x^2
+        sq = true;                      // T[2] = x^2
       } else {
         tbl_store(tbl, st - 1, A);
         stage_from_table(smem, ts, tbl + 1 * (kH / 4) * kRows);   // B = x R
@@ -385,7 +448,7 @@ __device__ __forceinline__ void exp_tile(uint32_t (&A)[kH], Tile &ts, uint8_t *s
         stage_get(A, smem, ts);
       }
       if (s < W) {
-        stage_put(smem, ts, A);
+        sq = true;
         ++s;
       } else {
         tbl_select<W>(smem, ts, tbl, exp_digit<W>(kc + kKexp, (uint32_t)k));
@@ -395,7 +458,7 @@ __device__ __forceinline__ void exp_tile(uint32_t (&A)[kH], Tile &ts, uint8_t *s
     } else {                            // q: leave Montgomery form
       lo = kca + 4 * kKunit; lo_str = 16; hi = lo + 128; hi_str = 16;
     }
-    mont_step(A, lo, lo_str, hi, hi_str, ts, Ms, polls);
+    mont_step(A, sq, lo, lo_str, hi, hi_str, ts, Ms, polls);
     if (ts.dead) break;
   }
 }

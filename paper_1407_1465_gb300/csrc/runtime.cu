@@ -108,11 +108,12 @@ Tune Ctx::tune_for(uint32_t nbits, int kind) const {
   auto it = tuning.find({nbits, kind});
   if (it != tuning.end()) t = it->second;
   const uint32_t L = nbits / 32;
-  // RSA-2048 CRT: the Montgomery reduction on the tensor cores (1.98 M/s at
-  // w = 3 against 1.25 M/s for the CUDA-core CIOS kernel on GB300)
+  // RSA-2048 and RSA-4096 CRT: the Montgomery reduction on the tensor cores
+  // (GB300, w = 3: 2.14 M/s against 1.25 M/s for the CUDA-core CIOS kernel at
+  // 2048 bits; 196 K/s against 149 K/s for the four-lane kernel at 4096 bits)
   // (only when nothing else was asked for: windows 3/4, one lane per operation)
-  if (!t.variant && kind == RSA_EXP_PRIVATE_CRT && L == 2 * (uint32_t)tcr::kH && t.tpo <= 1 &&
-      (t.window == 0 || t.window == 3 || t.window == 4))
+  if (!t.variant && kind == RSA_EXP_PRIVATE_CRT && (L == 2 * (uint32_t)tcr::kH || L == 2 * (uint32_t)tc4::kH) &&
+      t.tpo <= 1 && (t.window == 0 || t.window == 3 || t.window == 4))
     t.variant = 3;
   if (!t.window) t.window = (t.variant == 3) ? 3 : (kind == RSA_EXP_PUBLIC ? 5 : default_window(L, kind));
   if (!t.warps_per_cta) t.warps_per_cta = 4;

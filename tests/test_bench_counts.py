@@ -133,8 +133,8 @@ def test_measured_roofline_fraction_uses_the_probe_figure(monkeypatch):
 
 def _tc4_walk(W):
     """The RSA-4096 tensor-core path's work per decryption, replaying its step
-    loop (as _tc_walk) with every step a 64 x 64-limb product and two reduction
-    rounds; the method's MMA work by enumerating the digit pairs of
+    loop (as _tc_walk: squarings issue each cross product once) with two
+    reduction rounds per step; the method's MMA work by enumerating the digit pairs of
     mu = (T mod 2^1024) m' and of positions 124..379 of mu * m (m: 256 digits)."""
     H, D = 64, 128
     pairs1 = sum(1 for n in range(D) for k in range(D) if 0 <= n - k < D)
@@ -143,8 +143,17 @@ def _tc4_walk(W):
     ntab, nexp = 1 << W, (nwin - 1) * (W + 1)
     prods = flops = method = 0
     for pi in (0, 1):
-        for _ in range(ntab + nexp + (1 if pi == 0 else 0)):
-            prods += H * H
+        s = 0
+        for st in range(ntab + nexp + (1 if pi == 0 else 0)):
+            sq = False
+            if 2 <= st < ntab:
+                sq = st == 2
+            elif ntab <= st < ntab + nexp:
+                if s < W:
+                    sq, s = True, s + 1
+                else:
+                    s = 0
+            prods += H * (H + 1) // 2 if sq else H * H
             flops += 2 * (2 * 128 * (9 * 16) + 2 * 256 * (9 * 16))
             method += 2 * 2 * (pairs1 + pairs2)
     prods += 2 * (2 * H * H + H) + H * H
