@@ -327,7 +327,8 @@ typedef struct rsa_tuning {
                               against Toeplitz matrices of p, q and -p^-1, -q^-1 mod
                               2^1024; for 2048-bit primes in two rounds of 2^1024; the
                               per-message product stays on the CUDA cores; windows 3
-                              and 4); 0 = automatic: 3 for RSA-2048 and RSA-4096 CRT
+                              and 4); 0 = automatic: 3 for RSA-2048 CRT and for
+                              RSA-4096 CRT batches of at least 12288 operations
                               (window 3), 1 otherwise.  For RSA_EXP_PUBLIC (moduli up to 2048
                               bits): 1 = binary method (Fig. 5), 2 = sliding windows
                               of up to `window` bits (Fig. 7; window 4..6, default 5),

@@ -96,6 +96,8 @@ void Workspace::free_all() {
 // RSA-4096 CRT: 128 K/s, 127 K/s, 118 K/s).
 // Public exponents longer than this use sliding windows (variant 0).
 constexpr uint32_t kSlideMinBits = 64;
+// Smallest RSA-4096 CRT batch the automatic tuning sends to the tensor cores.
+constexpr uint64_t kTc4AutoMinCount = 12288;
 
 static int default_window(uint32_t L, int kind) {
   (void)L;
@@ -189,7 +191,20 @@ int Ctx::run_key(const KeySlot &k, int kind, uint64_t count, const uint32_t *msg
     stats.kernel_launches++;
     return RSA_OK;
   }
-  const Tune t = tune_for(k.nbits, kind);
+  Tune t = tune_for(k.nbits, kind);
+  // At 4096 bits a tensor-core launch costs a whole tile's exponentiation
+  // (~80 ms on GB300) however few operations it carries, while the four-lane
+  // CUDA-core kernel's time grows with the count (6.7 us per operation at full
+  // occupancy): the automatic choice takes the tensor cores from 12288
+  // operations up (an explicit variant 3 always does).
+  if (t.variant == 3 && L == 2 * (uint32_t)tc4::kH && count < kTc4AutoMinCount) {
+    auto it = tuning.find({k.nbits, kind});
+    if (it == tuning.end() || it->second.variant == 0) {
+      t.variant = 0;
+      t.tpo = 4;
+      if (it == tuning.end() || it->second.window == 0) t.window = 5;
+    }
+  }
   if (kind == RSA_EXP_PRIVATE_CRT && t.variant == 3 && L == 2 * (uint32_t)tc4::kH) {
     // RSA-4096: the Montgomery reduction on the tensor cores in two rounds (crt_tc4.cu)
     if (!k.d_tc) return set_error(RSA_ERR_UNSUPPORTED, "the tensor-core CRT path needs a key with p and q");
