@@ -31,6 +31,7 @@ import workloads  # noqa: E402
 
 WORKLOADS = {
     "rsa2048": dict(bits=2048, count=65536),
+    "rsa3072": dict(bits=3072, count=16384),
     "rsa4096": dict(bits=4096, count=16384),
 }
 
@@ -148,27 +149,29 @@ def tc_work_per_op(bits: int, window: int):
     return issued, tensor_flops, method_flops
 
 
-def tc4_work_per_op(window: int):
-    """CUDA-core word products and tensor-core FLOPs of one RSA-4096 CRT
-    decryption on the tensor-core path (2048-bit primes, two reduction rounds
-    of r = 2^1024 per Montgomery product): per half 2 input products, 2^w - 2
+def tc4_work_per_op(window: int, bits: int = 4096):
+    """CUDA-core word products and tensor-core FLOPs of one RSA-3072/4096 CRT
+    decryption on the tensor-core path (primes of H = bits/64 limbs, two
+    reduction rounds of r = 2^(16H) per Montgomery product, D = 2H digits): per half 2 input products, 2^w - 2
     table products, (windows - 1)(w + 1) window steps (+1 for q leaving
-    Montgomery form); a squaring issues 64*65/2 word products (cross products
-    once), another step 64 x 64, and every step two rounds of MMA 1 (N = 128)
-    and MMA 2 (N = 256), 9 K-steps each; Garner adds two CIOS products and one
-    64 x 64 product.
+    Montgomery form); a squaring issues H(H+1)/2 word products (cross products
+    once), another step H x H, and every step two rounds of MMA 1 (N = D) and
+    MMA 2 (N = 2D), D/16 + 1 K-steps each; Garner adds two CIOS products and
+    one H x H product.
     Returns (issued word products, issued MMA FLOPs, method MMA FLOPs): the
     method's share of a round is the nonzero part of its two Toeplitz products,
     D(D+1)/2 byte products for mu = (T mod r) m' mod r and those of positions
-    D-4 .. D+251 of mu * m (m of 2D digits), D = 128."""
-    H, D = 64, 128
+    D-4 .. 3D-5 of mu * m (m of 2D digits)."""
+    H = bits // 64
+    D = 2 * H
     nwin = -(-32 * H // window)
     steps = 2 * ((1 << window) + (nwin - 1) * (window + 1)) + 1
     squares = 2 * (1 + (nwin - 1) * window)
     issued = squares * (H * (H + 1) // 2) + (steps - squares) * H * H + 2 * (2 * H * H + H) + H * H
-    issued_flops = steps * 2 * (9 * 2 * 128 * 16 + 9 * 2 * 256 * 16)
+    ks = D // 16 + 1                     # K-steps of 16 digits, the bias block included
+    issued_flops = steps * 2 * (ks * 2 * 16 * D + ks * 2 * 16 * 2 * D)   # per round: MMA 1 (N = D), MMA 2 (N = 2D)
     mma1 = D * (D + 1) // 2
-    mma2 = sum(min(j, D - 1) - max(0, j - (2 * D - 1)) + 1 for j in range(D - 4, D - 4 + 256))
+    mma2 = sum(min(j, D - 1) - max(0, j - (2 * D - 1)) + 1 for j in range(D - 4, 3 * D - 4))
     method_flops = steps * 2 * 2 * (mma1 + mma2)
     return issued, issued_flops, method_flops
 
@@ -1034,7 +1037,8 @@ def main():
     traffic = prof["dram_bytes_per_op"] * count if prof_valid else None
     tc_path = tune["variant"] == 3 and args.kind == "crt"
     if tc_path:
-        issued, tflops_op, method_flops_op = (tc4_work_per_op(tune["window"]) if spec["bits"] == 4096
+        issued, tflops_op, method_flops_op = (tc4_work_per_op(tune["window"], spec["bits"])
+                                              if spec["bits"] in (3072, 4096)
                                               else tc_work_per_op(spec["bits"], tune["window"]))
         roofline = alu_roofline(issued * count / (ms / 1e3) / 1e12, local,
                                 "32x32->64 word products the CUDA cores issue per second (per-message products "

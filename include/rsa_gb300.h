@@ -322,14 +322,15 @@ typedef struct rsa_tuning {
     int32_t variant;       /* squarings of private exponents: 1 = through the general
                               CIOS multiply, 2 = separated square + reduction (fewer
                               word products, but a larger instruction footprint; slower
-                              on GB300); 3 = RSA-2048 and RSA-4096 CRT: the Montgomery
-                              reduction on the tensor cores (tcgen05 MMAs of byte digits
-                              against Toeplitz matrices of p, q and -p^-1, -q^-1 mod
-                              2^1024; for 2048-bit primes in two rounds of 2^1024; the
-                              per-message product stays on the CUDA cores; windows 3
-                              and 4); 0 = automatic: 3 for RSA-2048 CRT and for
-                              RSA-4096 CRT batches of at least 12288 operations
-                              (window 3), 1 otherwise.  For RSA_EXP_PUBLIC (moduli up to 2048
+                              on GB300); 3 = RSA-2048, -3072 and -4096 CRT: the
+                              Montgomery reduction on the tensor cores (tcgen05 MMAs of
+                              byte digits against Toeplitz matrices of p, q and -p^-1,
+                              -q^-1; for 1536/2048-bit primes in two rounds of half the
+                              prime size; the per-message product stays on the CUDA
+                              cores; windows 3 and 4); 0 = automatic: 3 for RSA-2048 CRT
+                              (window 3), RSA-3072 CRT batches of at least 8192
+                              operations (window 4) and RSA-4096 CRT batches of at least
+                              12288 (window 3), 1 otherwise.  For RSA_EXP_PUBLIC (moduli up to 2048
                               bits): 1 = binary method (Fig. 5), 2 = sliding windows
                               of up to `window` bits (Fig. 7; window 4..6, default 5),
                               0 = sliding for exponents longer than 64 bits */
@@ -402,16 +403,20 @@ int rsa_autotune_batch(rsa_ctx *ctx, uint64_t count, const int32_t *key_ids, con
 #define RSA_TC_IMAGE_BYTES 73728
 int rsa_tc_operand_image(const uint32_t *m, void *out, size_t out_bytes);
 
-/* The same for one 2048-bit prime m of an RSA-4096 key (variant 3 at 4096 bits:
- * the Montgomery reduction mod m, R = 2^2048, in two rounds of r = 2^1024, each
- * a product by -m^-1 mod r and one by m), as built at key load; K = 144 as above:
- *   bytes [0, 36864):      128 rows, row n, column k < 128: byte n-k of -m^-1 mod 2^1024
- *   bytes [36864, 110592): 256 rows, row j, column k < 128: byte 124+j-k of m
- * (0 where the byte index is outside 0..127, resp. 0..255).  m: 64 limbs,
- * little-endian, odd.  out: host buffer of at least RSA_TC4_IMAGE_BYTES bytes.
- * No GPU is used.  Errors: RSA_ERR_ARG (null pointer, short buffer, even m). */
-#define RSA_TC4_IMAGE_BYTES 110592
-int rsa_tc4_operand_image(const uint32_t *m, void *out, size_t out_bytes);
+/* The same for one prime m of an RSA-3072 or RSA-4096 key (prime_bits 1536 or
+ * 2048; variant 3 at those sizes): the Montgomery reduction mod m, R = 2^prime_bits,
+ * runs in two rounds of r = 2^(prime_bits/2), each a product by -m^-1 mod r and
+ * one by m.  With D = prime_bits/16 byte digits per round and K = D + 16:
+ *   bytes [0, 2 D K):       D rows, row n, column k < D: byte n-k of -m^-1 mod r
+ *   bytes [2 D K, 6 D K):   2D rows, row j, column k < D: byte D-4+j-k of m
+ *   columns D .. D+15 of both: the bias value 2048
+ * (0 where the byte index is outside 0 .. D-1, resp. 0 .. 2D-1), in the K-major
+ * core-matrix layout above.  m: prime_bits/32 limbs, little-endian, odd.  out:
+ * host buffer of at least RSA_TC_ROUND_IMAGE_BYTES(prime_bits) bytes (110592
+ * for 2048-bit primes, 64512 for 1536-bit ones).  No GPU is used.  Errors:
+ * RSA_ERR_ARG (null pointer, other sizes, short buffer, even m). */
+#define RSA_TC_ROUND_IMAGE_BYTES(prime_bits) (6u * ((prime_bits) / 16u) * ((prime_bits) / 16u + 16u))
+int rsa_tc_round_operand_image(uint32_t prime_bits, const uint32_t *m, void *out, size_t out_bytes);
 
 /* Counters since context creation. */
 typedef struct rsa_stats {

@@ -23,7 +23,7 @@ from ._lib import (RSA_ERR_ARG, RSA_ERR_CUDA, RSA_ERR_KEY, RSA_ERR_NOMEM, RSA_ER
 __all__ = [
     "RsaContext", "RsaError", "int_to_limbs", "limbs_to_int",
     "rsa_ctx_create", "rsa_ctx_destroy", "rsa_keyload", "rsa_key_record", "rsa_tc_operand_image",
-    "rsa_tc4_operand_image",
+    "rsa_tc_round_operand_image",
     "rsa_keyunload", "rsa_key_info",
     "rsa_modexp_key", "rsa_modexp_batch", "rsa_modexp_key_host", "rsa_modexp_batch_host",
     "rsa_sign_key", "rsa_verify_key", "rsa_mr_batch", "rsa_batch_gcd", "rsa_batch_gcd_host", "rsa_batch_gcd_plan",
@@ -131,15 +131,18 @@ def rsa_tc_operand_image(m: int) -> np.ndarray:
     return out
 
 
-RSA_TC4_IMAGE_BYTES = 110592
+def rsa_tc_round_image_bytes(prime_bits: int) -> int:
+    d = prime_bits // 16
+    return 6 * d * (d + 16)
 
 
-def rsa_tc4_operand_image(m: int) -> np.ndarray:
-    """Host-only: the tensor-core operand images (uint8, RSA_TC4_IMAGE_BYTES) of a
-    2048-bit odd prime m, as built at key load for the RSA-4096 variant-3 path."""
-    ma = int_to_limbs(m, 64)
-    out = np.zeros(RSA_TC4_IMAGE_BYTES, dtype=np.uint8)
-    check(_lib.lib().rsa_tc4_operand_image(_ptr(ma), _ptr(out), out.size))
+def rsa_tc_round_operand_image(prime_bits: int, m: int) -> np.ndarray:
+    """Host-only: the tensor-core operand images (uint8) of an odd prime m of
+    1536 or 2048 bits, as built at key load for the RSA-3072/4096 variant-3
+    path (two reduction rounds of half the prime size)."""
+    ma = int_to_limbs(m, prime_bits // 32)
+    out = np.zeros(rsa_tc_round_image_bytes(prime_bits), dtype=np.uint8)
+    check(_lib.lib().rsa_tc_round_operand_image(prime_bits, _ptr(ma), _ptr(out), out.size))
     return out
 
 

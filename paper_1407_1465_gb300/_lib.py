@@ -83,7 +83,7 @@ SIGNATURES = [
     ("rsa_key_record", ctypes.c_int, [ctypes.c_uint32, _P, _P, ctypes.c_uint32, _P, _P, _P, _P,
                                       ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     ("rsa_tc_operand_image", ctypes.c_int, [_P, _P, ctypes.c_size_t]),
-    ("rsa_tc4_operand_image", ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    ("rsa_tc_round_operand_image", ctypes.c_int, [ctypes.c_uint32, _P, _P, ctypes.c_size_t]),
     ("rsa_keyunload", ctypes.c_int, [_P, ctypes.c_int32]),
     ("rsa_key_info", ctypes.c_int, [_P, ctypes.c_int32, _U32P, _I32P, _I32P]),
     ("rsa_modexp_key", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P]),

@@ -87,33 +87,31 @@ size_t ragged_tc_garner_smem();
 
 }  // namespace tcr
 
-// RSA-4096 CRT with the Montgomery reduction on the tensor cores (crt_tc4.cu):
-// 2048-bit primes, two reduction rounds of r = 2^1024 per Montgomery product.
+// RSA-3072 and RSA-4096 CRT with the Montgomery reduction on the tensor cores
+// (crt_tc4.cu): primes of H = 48 or 64 limbs, two reduction rounds of
+// r = 2^(16H) per Montgomery product, D = 2H byte digits per round.
 namespace tc4 {
-constexpr int kH = 64;                   // limbs per prime (2048-bit primes)
-constexpr int kDig = 128;                // byte digits per reduction round (r = 2^1024)
 constexpr int kRows = 128;               // operations per tile (MMA M)
 constexpr int kTiles = 2;                // tiles per CTA
 constexpr int kThreads = kRows * kTiles;
-constexpr int kN1 = kDig;                // MMA 1 output columns (digits of mu)
-constexpr int kN2 = 256;                 // MMA 2 output columns (positions 124 .. 379 of mu * m)
-constexpr int kN2First = kDig - 4;
-constexpr int kKt = kDig + 16;           // K extent of the B images (digits + bias block)
-constexpr size_t kImgB1 = (size_t)kN1 * kKt * 2;   // 36864 bytes
-constexpr size_t kImgB2 = (size_t)kN2 * kKt * 2;   // 73728 bytes
-constexpr size_t kImgPrime = kImgB1 + kImgB2;      // per prime
-constexpr size_t kImgKey = 2 * kImgPrime;          // q image, then p image
+// B1: D rows (digits of mu) x (D + 16) (digits + bias block); B2: 2D rows
+// (positions D-4 .. 3D-5 of mu * m) x (D + 16); fp16
+constexpr size_t img_b1_bytes(int H) { return (size_t)(2 * H) * (2 * H + 16) * 2; }
+constexpr size_t img_b2_bytes(int H) { return (size_t)(4 * H) * (2 * H + 16) * 2; }
+constexpr size_t img_prime_bytes(int H) { return img_b1_bytes(H) + img_b2_bytes(H); }   // 110592 at H = 64
+constexpr size_t img_key_bytes(int H) { return 2 * img_prime_bytes(H); }                 // q image, then p image
+constexpr bool supported(int H) { return H == 48 || H == 64; }
 
-// Host: the two B operands of one 2048-bit prime m (kH limbs, odd): B1 = the
-// Toeplitz matrix of -m^-1 mod 2^1024 (128 x 128 + bias), B2 = that of m for
-// output positions 124 .. 379 (256 x 128 + bias).  Returns false if m is even.
-bool build_tc4_image(const uint32_t *m, uint8_t *out);
-size_t tc4_tables_bytes(int grid, int window);
-size_t tc4_halves_bytes(uint32_t count);
+// Host: the two B operands of one prime m of H limbs (odd): B1 = the Toeplitz
+// matrix of -m^-1 mod 2^(16H), B2 = that of m for output positions
+// D-4 .. 3D-5, each with the bias block.  Returns false if m is even or H is
+// not 48 or 64.
+bool build_tc4_image(const uint32_t *m, int H, uint8_t *out);
+size_t tc4_tables_bytes(int H, int grid, int window);
+size_t tc4_halves_bytes(int H, uint32_t count);
 int tc4_grid(uint32_t count, int sm_count);
-size_t tc4_smem_bytes();
 #if defined(__CUDACC__)
-cudaError_t launch_crt_tc4(const uint32_t *keyrec, const void *image, const uint32_t *msgs, uint32_t *out,
+cudaError_t launch_crt_tc4(int H, const uint32_t *keyrec, const void *image, const uint32_t *msgs, uint32_t *out,
                            int32_t *status, uint32_t count, int grid, int window, void *tables, void *halves,
                            uint32_t wait_polls, cudaStream_t s);
 #endif

@@ -96,8 +96,10 @@ void Workspace::free_all() {
 // RSA-4096 CRT: 128 K/s, 127 K/s, 118 K/s).
 // Public exponents longer than this use sliding windows (variant 0).
 constexpr uint32_t kSlideMinBits = 64;
-// Smallest RSA-4096 CRT batch the automatic tuning sends to the tensor cores.
-constexpr uint64_t kTc4AutoMinCount = 12288;
+// Smallest RSA-3072 / RSA-4096 CRT batch the automatic tuning sends to the
+// tensor cores (where the CUDA-core kernel's time reaches one tensor-core
+// launch's: GB300, 285 K/s against ~33 ms, 149 K/s against ~83 ms).
+static uint64_t tc4_auto_min_count(uint32_t L) { return L == 96 ? 8192 : 12288; }
 
 static int default_window(uint32_t L, int kind) {
   (void)L;
@@ -114,10 +116,12 @@ Tune Ctx::tune_for(uint32_t nbits, int kind) const {
   // (GB300, w = 3: 2.14 M/s against 1.25 M/s for the CUDA-core CIOS kernel at
   // 2048 bits; 196 K/s against 149 K/s for the four-lane kernel at 4096 bits)
   // (only when nothing else was asked for: windows 3/4, one lane per operation)
-  if (!t.variant && kind == RSA_EXP_PRIVATE_CRT && (L == 2 * (uint32_t)tcr::kH || L == 2 * (uint32_t)tc4::kH) &&
+  if (!t.variant && kind == RSA_EXP_PRIVATE_CRT && (L == 2 * (uint32_t)tcr::kH || tc4::supported((int)L / 2)) &&
       t.tpo <= 1 && (t.window == 0 || t.window == 3 || t.window == 4))
     t.variant = 3;
-  if (!t.window) t.window = (t.variant == 3) ? 3 : (kind == RSA_EXP_PUBLIC ? 5 : default_window(L, kind));
+  // tensor-core path: window 3 keeps the tables in L2 at 2048 and 4096 bits;
+  // at 3072 bits window 4 is faster (GB300: 502 K against 480 K decrypts/s)
+  if (!t.window) t.window = (t.variant == 3) ? (L == 96 ? 4 : 3) : (kind == RSA_EXP_PUBLIC ? 5 : default_window(L, kind));
   if (!t.warps_per_cta) t.warps_per_cta = 4;
   // lanes per operation (GB300 sweeps): four for 3072/4096-bit keys -- CRT halves of
   // 48/64 limbs need 255 registers on one lane and 128 on four (RSA-4096 CRT:
@@ -192,12 +196,13 @@ int Ctx::run_key(const KeySlot &k, int kind, uint64_t count, const uint32_t *msg
     return RSA_OK;
   }
   Tune t = tune_for(k.nbits, kind);
-  // At 4096 bits a tensor-core launch costs a whole tile's exponentiation
-  // (~80 ms on GB300) however few operations it carries, while the four-lane
-  // CUDA-core kernel's time grows with the count (6.7 us per operation at full
-  // occupancy): the automatic choice takes the tensor cores from 12288
-  // operations up (an explicit variant 3 always does).
-  if (t.variant == 3 && L == 2 * (uint32_t)tc4::kH && count < kTc4AutoMinCount) {
+  // At 3072/4096 bits a tensor-core launch costs a whole tile's exponentiation
+  // (~80 ms at 4096 bits on GB300) however few operations it carries, while
+  // the four-lane CUDA-core kernel's time grows with the count (6.7 us per
+  // 4096-bit operation at full occupancy): the automatic choice takes the
+  // tensor cores from tc4_auto_min_count operations up (an explicit variant 3
+  // always does).
+  if (t.variant == 3 && tc4::supported((int)L / 2) && count < tc4_auto_min_count(L)) {
     auto it = tuning.find({k.nbits, kind});
     if (it == tuning.end() || it->second.variant == 0) {
       t.variant = 0;
@@ -205,20 +210,21 @@ int Ctx::run_key(const KeySlot &k, int kind, uint64_t count, const uint32_t *msg
       if (it == tuning.end() || it->second.window == 0) t.window = 5;
     }
   }
-  if (kind == RSA_EXP_PRIVATE_CRT && t.variant == 3 && L == 2 * (uint32_t)tc4::kH) {
-    // RSA-4096: the Montgomery reduction on the tensor cores in two rounds (crt_tc4.cu)
+  if (kind == RSA_EXP_PRIVATE_CRT && t.variant == 3 && tc4::supported((int)L / 2)) {
+    // RSA-3072/4096: the Montgomery reduction on the tensor cores in two rounds (crt_tc4.cu)
+    const int H = (int)L / 2;
     if (!k.d_tc) return set_error(RSA_ERR_UNSUPPORTED, "the tensor-core CRT path needs a key with p and q");
     if (count > 0xFFFFFFFFull) return set_error(RSA_ERR_ARG, "count out of range");
     if (t.window != 3 && t.window != 4)
       return set_error(RSA_ERR_UNSUPPORTED, "the tensor-core CRT path has windows 3 and 4");
     const int grid = tc4::tc4_grid((uint32_t)count, sm_count);
-    int rc = ensure(w.tables, tc4::tc4_tables_bytes(grid, t.window));
+    int rc = ensure(w.tables, tc4::tc4_tables_bytes(H, grid, t.window));
     if (rc) return rc;
-    rc = ensure(w.halves, tc4::tc4_halves_bytes((uint32_t)count));
+    rc = ensure(w.halves, tc4::tc4_halves_bytes(H, (uint32_t)count));
     if (rc) return rc;
     uint32_t polls = tcr::kDefaultWaitPolls;
     if (const char *ev = std::getenv("RSAGPU_TC_WAIT_POLLS")) polls = (uint32_t)std::strtoul(ev, nullptr, 10);
-    e = tc4::launch_crt_tc4(k.d_rec, k.d_tc, msgs, out, status, (uint32_t)count, grid, t.window, w.tables.ptr,
+    e = tc4::launch_crt_tc4(H, k.d_rec, k.d_tc, msgs, out, status, (uint32_t)count, grid, t.window, w.tables.ptr,
                             w.halves.ptr, polls, s);
     if (e != cudaSuccess) return cuda_error(e, "launch crt_tc4 kernels");
     stats.kernel_launches += 2;
@@ -449,10 +455,12 @@ static int make_record(uint32_t nbits, const uint32_t *n, const uint32_t *e, uin
   return RSA_OK;
 }
 
-int rsa_tc4_operand_image(const uint32_t *m, void *out, size_t out_bytes) {
+int rsa_tc_round_operand_image(uint32_t prime_bits, const uint32_t *m, void *out, size_t out_bytes) {
   if (!m || !out) return set_error(RSA_ERR_ARG, "null pointer");
-  if (out_bytes < tc4::kImgPrime) return set_error(RSA_ERR_ARG, "output buffer too small");
-  if (!tc4::build_tc4_image(m, static_cast<uint8_t *>(out))) return set_error(RSA_ERR_ARG, "modulus must be odd");
+  if (prime_bits != 1536 && prime_bits != 2048) return set_error(RSA_ERR_ARG, "prime_bits must be 1536 or 2048");
+  const int H = (int)prime_bits / 32;
+  if (out_bytes < tc4::img_prime_bytes(H)) return set_error(RSA_ERR_ARG, "output buffer too small");
+  if (!tc4::build_tc4_image(m, H, static_cast<uint8_t *>(out))) return set_error(RSA_ERR_ARG, "modulus must be odd");
   return RSA_OK;
 }
 
@@ -507,14 +515,15 @@ int rsa_keyload(rsa_ctx *ctx, uint32_t nbits, const uint32_t *n, const uint32_t 
   // tensor-core operand images of q and p for the RSA-2048 and RSA-4096 CRT paths
   void *dtc = nullptr;
   size_t tc_bytes = 0;
-  if ((L == 2 * (uint32_t)tcr::kH || L == 2 * (uint32_t)tc4::kH) && (flags & KEY_HAS_CRT)) {
-    const bool four = L == 2 * (uint32_t)tc4::kH;
+  const int Hk = (int)L / 2;
+  if ((L == 2 * (uint32_t)tcr::kH || tc4::supported(Hk)) && (flags & KEY_HAS_CRT)) {
+    const bool rounds = tc4::supported(Hk);
     const KeyLayout lay(L);
-    std::vector<uint8_t> img(four ? tc4::kImgKey : tcr::kImgKey);
-    const bool ok = four ? tc4::build_tc4_image(rec.data() + lay.q, img.data()) &&
-                               tc4::build_tc4_image(rec.data() + lay.p, img.data() + tc4::kImgPrime)
-                         : tcr::build_tc_image(rec.data() + lay.q, img.data()) &&
-                               tcr::build_tc_image(rec.data() + lay.p, img.data() + tcr::kImgPrime);
+    std::vector<uint8_t> img(rounds ? tc4::img_key_bytes(Hk) : tcr::kImgKey);
+    const bool ok = rounds ? tc4::build_tc4_image(rec.data() + lay.q, Hk, img.data()) &&
+                                 tc4::build_tc4_image(rec.data() + lay.p, Hk, img.data() + tc4::img_prime_bytes(Hk))
+                           : tcr::build_tc_image(rec.data() + lay.q, img.data()) &&
+                                 tcr::build_tc_image(rec.data() + lay.p, img.data() + tcr::kImgPrime);
     int rc2 = ok ? c->reserve(img.size()) : set_error(RSA_ERR_KEY, "p and q must be odd");
     if (rc2 == RSA_OK) {
       if (cudaMalloc(&dtc, img.size()) == cudaSuccess &&

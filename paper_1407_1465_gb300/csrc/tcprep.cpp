@@ -119,40 +119,42 @@ bool build_tc_image(const uint32_t *m, uint8_t *out) {
 
 namespace tc4 {
 
-// The operands of one 2048-bit prime m for crt_tc4.cu, where a Montgomery
-// product reduces modulo m in two rounds of r = 2^1024:
-//   B1 (128 x 144): row n, column k < 128: byte n-k of m' = -m^-1 mod 2^1024
-//       (it depends only on m mod 2^1024); columns 128..143: 2048 (bias)
-//   B2 (256 x 144): row j = output position 124 + j of mu * m, column k < 128:
-//       byte 124+j-k of m (0 outside 0..255); columns 128..143: 2048
-bool build_tc4_image(const uint32_t *m, uint8_t *out) {
-  if ((m[0] & 1u) == 0) return false;
-  uint32_t mp[kDig / 4];
-  tcr::neg_inverse_lo(m, mp, kDig / 4);
-  std::memset(out, 0, kImgPrime);
-  uint8_t *b1 = out, *b2 = out + kImgB1;
+// The operands of one prime m of H limbs (H = 48 or 64) for crt_tc4.cu, where
+// a Montgomery product reduces modulo m in two rounds of r = 2^(16H), with
+// D = 2H byte digits per round:
+//   B1 (D x (D + 16)): row n, column k < D: byte n-k of m' = -m^-1 mod 2^(16H)
+//       (it depends only on m mod 2^(16H)); columns D .. D+15: 2048 (bias)
+//   B2 (2D x (D + 16)): row j = output position D-4+j of mu * m, column k < D:
+//       byte D-4+j-k of m (0 outside 0 .. 4H-1); columns D .. D+15: 2048
+bool build_tc4_image(const uint32_t *m, int H, uint8_t *out) {
+  if (!supported(H) || (m[0] & 1u) == 0) return false;
+  const int D = 2 * H, Kt = D + 16, N1 = D, N2 = 2 * D, first = D - 4;
+  std::vector<uint32_t> mp(H / 2);
+  tcr::neg_inverse_lo(m, mp.data(), H / 2);
+  std::memset(out, 0, img_prime_bytes(H));
+  uint8_t *b1 = out, *b2 = out + img_b1_bytes(H);
   const uint16_t bias = tcr::f16_of_int(2048);
-  for (int n = 0; n < kN1; ++n)
-    for (int k = 0; k < kKt; ++k) {
+  for (int n = 0; n < N1; ++n)
+    for (int k = 0; k < Kt; ++k) {
       uint16_t h;
-      if (k < kDig) {
+      if (k < D) {
         const int i = n - k;
-        h = (i >= 0 && i < kDig) ? tcr::f16_of_int(tcr::byte_of(mp, i)) : 0;
+        h = (i >= 0 && i < D) ? tcr::f16_of_int(tcr::byte_of(mp.data(), i)) : 0;
       } else {
         h = bias;
       }
-      std::memcpy(b1 + tcr::core_off(n, k, kN1), &h, 2);
+      std::memcpy(b1 + tcr::core_off(n, k, N1), &h, 2);
     }
-  for (int j = 0; j < kN2; ++j)
-    for (int k = 0; k < kKt; ++k) {
+  for (int j = 0; j < N2; ++j)
+    for (int k = 0; k < Kt; ++k) {
       uint16_t h;
-      if (k < kDig) {
-        const int i = kN2First + j - k;
-        h = (i >= 0 && i < 4 * kH) ? tcr::f16_of_int(tcr::byte_of(m, i)) : 0;
+      if (k < D) {
+        const int i = first + j - k;
+        h = (i >= 0 && i < 4 * H) ? tcr::f16_of_int(tcr::byte_of(m, i)) : 0;
       } else {
         h = bias;
       }
-      std::memcpy(b2 + tcr::core_off(j, k, kN2), &h, 2);
+      std::memcpy(b2 + tcr::core_off(j, k, N2), &h, 2);
     }
   return true;
 }

@@ -131,14 +131,15 @@ def test_measured_roofline_fraction_uses_the_probe_figure(monkeypatch):
     assert abs(bench.derived_peak_tprod(152, 2070.0) - 10.06848) < 1e-9
 
 
-def _tc4_walk(W):
-    """The RSA-4096 tensor-core path's work per decryption, replaying its step
-    loop (as _tc_walk: squarings issue each cross product once) with two
-    reduction rounds per step; the method's MMA work by enumerating the digit pairs of
-    mu = (T mod 2^1024) m' and of positions 124..379 of mu * m (m: 256 digits)."""
-    H, D = 64, 128
+def _tc4_walk(W, bits):
+    """The RSA-3072/4096 tensor-core path's work per decryption, replaying its
+    step loop (as _tc_walk: squarings issue each cross product once) with two
+    reduction rounds per step; the method's MMA work by enumerating the digit
+    pairs of mu = (T mod r) m' and of positions D-4 .. 3D-5 of mu * m (m: 2D digits)."""
+    H = bits // 64
+    D = 2 * H
     pairs1 = sum(1 for n in range(D) for k in range(D) if 0 <= n - k < D)
-    pairs2 = sum(1 for j in range(D - 4, D + 252) for i in range(D) if 0 <= j - i < 2 * D)
+    pairs2 = sum(1 for j in range(D - 4, 3 * D - 4) for i in range(D) if 0 <= j - i < 2 * D)
     nwin = -(-(32 * H) // W)
     ntab, nexp = 1 << W, (nwin - 1) * (W + 1)
     prods = flops = method = 0
@@ -154,12 +155,14 @@ def _tc4_walk(W):
                 else:
                     s = 0
             prods += H * (H + 1) // 2 if sq else H * H
-            flops += 2 * (2 * 128 * (9 * 16) + 2 * 256 * (9 * 16))
+            # per round: MMA 1 (N = D) and MMA 2 (N = 2D), D/16 + 1 K-steps of 16 for each of 128 rows
+            flops += 2 * (2 * D * (16 * (D // 16 + 1)) + 2 * 2 * D * (16 * (D // 16 + 1)))
             method += 2 * 2 * (pairs1 + pairs2)
     prods += 2 * (2 * H * H + H) + H * H
     return prods, flops, method
 
 
+@pytest.mark.parametrize("bits", [3072, 4096])
 @pytest.mark.parametrize("W", [3, 4])
-def test_tc4_work_per_op_matches_the_step_loop(W):
-    assert bench.tc4_work_per_op(W) == _tc4_walk(W)
+def test_tc4_work_per_op_matches_the_step_loop(W, bits):
+    assert bench.tc4_work_per_op(W, bits) == _tc4_walk(W, bits)

@@ -102,19 +102,19 @@ def test_tc_full_rsa2048_workload(torch_cuda, ctx, keys):
 
 
 def test_tc_rejects_other_sizes(torch_cuda, ctx, keys):
-    """The tensor-core path serves 2048- and 4096-bit CRT; 3072-bit keys are refused."""
+    """The tensor-core path serves 2048-, 3072- and 4096-bit CRT; 1024-bit keys are refused."""
     from paper_1407_1465_gb300 import RsaError
-    key = workloads.gen_keys([(3072, 0)], workloads.DEFAULT_SEED)[0]
-    kid = ctx.keyload(3072, key.n, key.e, key.d, key.p, key.q)
-    rows = workloads.messages_below(key.n, 4, 9, ("tc3072",))
-    ctx.set_tuning(3072, CRT, variant=TC)
+    key = workloads.gen_keys([(1024, 0)], workloads.DEFAULT_SEED)[0]
+    kid = ctx.keyload(1024, key.n, key.e, key.d, key.p, key.q)
+    rows = workloads.messages_below(key.n, 4, 9, ("tc1024",))
+    ctx.set_tuning(1024, CRT, variant=TC)
     try:
         t = torch_cuda.from_numpy(rows.view(np.int32)).cuda()
         with pytest.raises(RsaError) as ei:
             ctx.modexp_key(kid, CRT, t, torch_cuda.empty_like(t))
         assert ei.value.code == -7
     finally:
-        ctx.set_tuning(3072, CRT, reset=True)
+        ctx.set_tuning(1024, CRT, reset=True)
         ctx.keyunload(kid)
 
 

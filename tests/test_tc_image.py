@@ -143,83 +143,107 @@ def test_worst_case_columns_stay_below_2_23():
     assert 128 * 255 * 255 < 2 ** 23
 
 
-# ---------------------------------------------------------------- RSA-4096: 2048-bit primes, two rounds
-R4, r4 = 1 << 2048, 1 << 1024
+# ---------------------------------------------------------------- RSA-3072/4096: two reduction rounds
+# A prime of H limbs (1536 or 2048 bits) reduces in two rounds of r = 2^(16H)
+# with D = 2H byte digits per round: MMA 1 is D x D, MMA 2 returns positions
+# D-4 .. 3D-5 of mu * m (2D columns), positions 3D-4 .. 3D-2 come directly.
 
 
-def decode_k(img, off, rows):
-    return decode(img, off, rows)
+def decode_rows(img, off, rows, kt):
+    r = np.arange(rows)[:, None]
+    k = np.arange(kt)[None, :]
+    byte = (k // 8) * (rows // 8) * 128 + (r // 8) * 128 + (r % 8) * 16 + (k % 8) * 2
+    bits = img[off:off + rows * kt * 2].view(np.uint16)
+    return bits[byte // 2].view(np.float16).astype(np.float64)
 
 
-def toeplitz_m(dig, rows, first, ndig):
-    """rows x KT: row j, column k < 128: digit first + j - k of a number of ndig digits."""
-    out = np.zeros((rows, KT))
+def toeplitz_round(dig, rows, first, ndig, D):
+    """rows x (D + 16): row j, column k < D: digit first + j - k of a number of ndig digits; bias 2048."""
+    out = np.zeros((rows, D + 16))
     for j in range(rows):
-        for k in range(128):
+        for k in range(D):
             i = first + j - k
             if 0 <= i < ndig:
                 out[j, k] = dig[i]
-    out[:, 128:] = 2048.0
+    out[:, D:] = 2048.0
     return out
 
 
 @pytest.fixture(scope="module")
-def key4096():
-    return workloads.gen_keys([(4096, 0)], workloads.DEFAULT_SEED)[0]
+def round_keys():
+    return workloads.gen_keys([(3072, 0), (4096, 0)], workloads.DEFAULT_SEED)
 
 
-def test_tc4_image_is_the_toeplitz_of_m_and_m_prime(lib, key4096):
-    from paper_1407_1465_gb300 import rsa_tc4_operand_image
-    from paper_1407_1465_gb300 import RSA_TC4_IMAGE_BYTES
-    for m in (key4096.p, key4096.q):
-        img = rsa_tc4_operand_image(m)
-        assert img.size == RSA_TC4_IMAGE_BYTES == 128 * KT * 2 + 256 * KT * 2
-        mp = (-pow(m, -1, r4)) % r4
-        b1, b2 = decode_k(img, 0, 128), decode_k(img, 128 * KT * 2, 256)
-        assert np.array_equal(b1, toeplitz_m(digits(mp), 128, 0, 128))
-        assert np.array_equal(b2, toeplitz_m(digits(m, 256), 256, 124, 256))
+def round_operands(m, H):
+    from paper_1407_1465_gb300 import rsa_tc_round_image_bytes, rsa_tc_round_operand_image
+    D = 2 * H
+    img = rsa_tc_round_operand_image(32 * H, m)
+    assert img.size == rsa_tc_round_image_bytes(32 * H) == D * (D + 16) * 2 + 2 * D * (D + 16) * 2
+    return decode_rows(img, 0, D, D + 16), decode_rows(img, D * (D + 16) * 2, 2 * D, D + 16)
 
 
-def replay_round4(V, m, b1, b2):
-    """One reduction round of the RSA-4096 kernel on the decoded operands:
-    mu = (V mod r) m' mod r by MMA 1 and a carry pass, positions 124..379 of
-    mu * m by MMA 2 and 380..383 directly, the carry out of the low half from
-    four columns, then (V + mu m) / r."""
+def test_round_images_are_the_toeplitz_of_m_and_m_prime(lib, round_keys):
+    for key in round_keys:
+        H = key.bits // 64
+        D, r = 2 * H, 1 << (16 * H)
+        for m in (key.p, key.q):
+            b1, b2 = round_operands(m, H)
+            mp = (-pow(m, -1, r)) % r
+            assert np.array_equal(b1, toeplitz_round(digits(mp, D), D, 0, D, D))
+            assert np.array_equal(b2, toeplitz_round(digits(m, 2 * D), 2 * D, D - 4, 2 * D, D))
+
+
+def test_round_image_rejects_bad_arguments(lib, round_keys):
+    from paper_1407_1465_gb300 import RsaError, rsa_tc_round_operand_image
+    with pytest.raises(RsaError):
+        rsa_tc_round_operand_image(2048, (1 << 2047) + 2)
+    with pytest.raises(RsaError):
+        rsa_tc_round_operand_image(1024, (1 << 1023) + 1)     # only 1536- and 2048-bit primes
+
+
+def replay_round(V, m, b1, b2, H):
+    """One reduction round of crt_tc4.cu on the decoded operands: mu = (V mod r)
+    m' mod r by MMA 1 and a carry pass, positions D-4 .. 3D-5 of mu * m by MMA 2
+    and 3D-4 .. 3D-1 directly, the carry out of the low half from four columns
+    (with V's top bytes), then (V + mu m) / r."""
+    D, r = 2 * H, 1 << (16 * H)
     bias_a = np.full(16, 2.0 ** -16)
-    v_lo = digits(V % r4)
+    v_lo = digits(V % r, D)
     col1 = (np.concatenate([v_lo * 2.0 ** -24, bias_a]) @ b1.T - 0.5) * 2.0 ** 24
     assert np.all(col1 == np.round(col1)) and col1.max() < 2 ** 23
     mu_d, _ = carry_pass(col1.astype(np.int64))
-    w = (np.concatenate([mu_d * 2.0 ** -24, bias_a]) @ b2.T - 0.5) * 2.0 ** 24   # positions 124..379
+    w = (np.concatenate([mu_d * 2.0 ** -24, bias_a]) @ b2.T - 0.5) * 2.0 ** 24
     assert np.all(w == np.round(w)) and w.max() < 2 ** 23
     w = w.astype(np.int64)
-    md = digits(m, 256)
-    top = [mu_d[125] * md[255] + mu_d[126] * md[254] + mu_d[127] * md[253],
-           mu_d[126] * md[255] + mu_d[127] * md[254], mu_d[127] * md[255], 0]
-    w = np.concatenate([w, np.array(top, dtype=np.int64)])                      # positions 124..383
-    y, c = carry_pass([w[i] + v_lo[124 + i] for i in range(4)])
+    md = digits(m, 2 * D)
+    top = [mu_d[D - 3] * md[2 * D - 1] + mu_d[D - 2] * md[2 * D - 2] + mu_d[D - 1] * md[2 * D - 3],
+           mu_d[D - 2] * md[2 * D - 1] + mu_d[D - 1] * md[2 * D - 2], mu_d[D - 1] * md[2 * D - 1], 0]
+    w = np.concatenate([w, np.array(top, dtype=np.int64)])                      # positions D-4 .. 3D-1
+    y, c = carry_pass([w[i] + v_lo[D - 4 + i] for i in range(4)])
     carry = c + (1 if y.any() else 0)
-    hi_d, cout = carry_pass(w[4:], carry)                                        # positions 128..383
+    hi_d, cout = carry_pass(w[4:], carry)                                        # positions D .. 3D-1
     mu = int.from_bytes(bytes(mu_d.astype(np.uint8)), "little")
-    return mu, (V >> 1024) + int.from_bytes(bytes(hi_d.astype(np.uint8)), "little") + (cout << 2048)
+    return mu, (V >> (16 * H)) + int.from_bytes(bytes(hi_d.astype(np.uint8)), "little") + (cout << (32 * H))
 
 
-def test_tc4_two_round_reduction_replay_matches_integer_montgomery(lib, key4096):
-    """Two rounds of r = 2^1024 give T R^-1 mod m (R = 2^2048) below 2m, over
+@pytest.mark.parametrize("bits", [3072, 4096])
+def test_two_round_reduction_replay_matches_integer_montgomery(lib, round_keys, bits):
+    """Two rounds of r = 2^(16H) give T R^-1 mod m (R = 2^(32H)) below 2m, over
     random and extreme products T < m^2 (the kernel's operands are below m)."""
-    from paper_1407_1465_gb300 import rsa_tc4_operand_image
-    rng = np.random.default_rng(9)
-    for m in (key4096.p, key4096.q):
-        img = rsa_tc4_operand_image(m)
-        b1, b2 = decode_k(img, 0, 128), decode_k(img, 128 * KT * 2, 256)
-        mp1 = (-pow(m, -1, r4)) % r4
-        rinv = pow(R4, -1, m)
-        cases = [0, 1, (m - 1) ** 2, (m - 1) * (m - 2), (m - 1) * r4, r4 - 1, r4, R4 - 1, (R4 - 1) * 5 % (m * m)]
-        cases += [(int.from_bytes(rng.bytes(256), "little") % m) * (int.from_bytes(rng.bytes(256), "little") % m)
+    key = next(k for k in round_keys if k.bits == bits)
+    H = bits // 64
+    r, R = 1 << (16 * H), 1 << (32 * H)
+    rng = np.random.default_rng(9 + H)
+    for m in (key.p, key.q):
+        b1, b2 = round_operands(m, H)
+        mp1 = (-pow(m, -1, r)) % r
+        rinv = pow(R, -1, m)
+        cases = [0, 1, (m - 1) ** 2, (m - 1) * (m - 2), (m - 1) * r, r - 1, r, R - 1, (R - 1) * 5 % (m * m)]
+        cases += [(int.from_bytes(rng.bytes(4 * H), "little") % m) * (int.from_bytes(rng.bytes(4 * H), "little") % m)
                   for _ in range(12)]
         for T in cases:
-            mu1, T1 = replay_round4(T, m, b1, b2)
-            assert mu1 == (T % r4) * mp1 % r4 and T1 == (T + mu1 * m) // r4 and (T + mu1 * m) % r4 == 0
-            mu2, T2 = replay_round4(T1, m, b1, b2)
-            assert T2 == (T1 + mu2 * m) // r4 and T2 < 2 * m
+            mu1, T1 = replay_round(T, m, b1, b2, H)
+            assert mu1 == (T % r) * mp1 % r and T1 == (T + mu1 * m) // r and (T + mu1 * m) % r == 0
+            mu2, T2 = replay_round(T1, m, b1, b2, H)
+            assert T2 == (T1 + mu2 * m) // r and T2 < 2 * m
             assert (T2 - m if T2 >= m else T2) == T * rinv % m
