@@ -527,8 +527,7 @@ def ragged_measure(steps: int, warmup: int, autotune: bool = False, loop_steps: 
     Sampled results are checked against the loop's and against the oracle."""
     import torch
     import oracle
-    from paper_1407_1465_gb300 import (RSA_TUNE_RAGGED, RsaContext, build, rsa_modexp_batch, rsa_modexp_key,
-                                       rsa_products_per_op)
+    from paper_1407_1465_gb300 import (RSA_TUNE_RAGGED, RsaContext, build, rsa_modexp_batch, rsa_modexp_key)
     build.build()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
@@ -553,17 +552,13 @@ def ragged_measure(steps: int, warmup: int, autotune: bool = False, loop_steps: 
         rows = np.stack([rb.msgs[i] for i in idx])
         t = torch.from_numpy(rows.view(np.int32)).to(dev)
         gbufs.append((kids[k], sel, len(idx), t, torch.empty_like(t), idx))
-    prods = 0.0
-    for i in range(count):
-        key = rb.keys[rb.key_ids[i]]
-        prods += rsa_products_per_op(key.bits, int(rb.exp_sel[i]), key.e, 5)
-
     tuned_ms = None
     if autotune:
         # the ragged autotuner on this very batch (untimed)
         from paper_1407_1465_gb300 import rsa_autotune_batch
         tuned_ms = rsa_autotune_batch(ctx.handle, count, key_ids, sels, offs, msgs, out)["ms"]
     tuning = ctx.get_tuning(0, RSA_TUNE_RAGGED)
+    work = ragged_work(rb, tuning)
 
     def step_ragged():
         rsa_modexp_batch(ctx.handle, count, key_ids, sels, offs, msgs, out, status, sptr)
@@ -613,7 +608,41 @@ def ragged_measure(steps: int, warmup: int, autotune: bool = False, loop_steps: 
             "one_key_per_launch": {"ms_per_step": res["loop"], "value": count / (res["loop"] / 1e3),
                                    "launches": len(gbufs)},
             "speedup_vs_loop": res["loop"] / res["ragged"], "tuning": tuning,
-            "autotuned_ms": tuned_ms, "products_per_step": prods, "count": count}
+            "autotuned_ms": tuned_ms, "count": count, **work}
+
+
+def ragged_work(rb, tuning: dict) -> dict:
+    """Per-step work of the ragged batch as its kernels issue it.  A CRT bucket
+    of one 2048-, 3072- or 4096-bit key with at least tc_min_ops operations
+    sends floor(count / 128) whole tiles to its tensor-core group (2048 bits at
+    the tuned tensor-core window, 3072 at window 4, 4096 at window 3); those
+    operations issue the CUDA-core word products and MMA FLOPs of the
+    tensor-core path, every other operation the CIOS count 2L^2 + L per
+    Montgomery product (window 5 for private exponents)."""
+    from paper_1407_1465_gb300 import rsa_products_per_op
+    buckets = {}
+    for k, sel in zip(rb.key_ids, rb.exp_sel):
+        buckets[(int(k), int(sel))] = buckets.get((int(k), int(sel)), 0) + 1
+    tc_on = tuning.get("variant", 0) != 1 and tuning.get("tc_min_ops", 128) > 0
+    issued = method_flops = issued_flops = 0.0
+    tc_ops = 0
+    for (k, sel), c in buckets.items():
+        key = rb.keys[k]
+        nt = 0
+        if tc_on and sel == 1 and key.bits in (2048, 3072, 4096) and c >= tuning.get("tc_min_ops", 128):
+            nt = c // 128 * 128
+        if nt:
+            if key.bits == 2048:
+                w = tc_work_per_op(2048, tuning.get("window_tc") or 3)
+            else:
+                w = tc4_work_per_op(4 if key.bits == 3072 else 3, key.bits)
+            issued += nt * w[0]
+            issued_flops += nt * w[1]
+            method_flops += nt * w[2]
+            tc_ops += nt
+        issued += (c - nt) * rsa_products_per_op(key.bits, sel, key.e, 5)
+    return {"products_per_step": issued, "tc_ops": tc_ops, "tc_method_flops_per_step": method_flops,
+            "tc_issued_flops_per_step": issued_flops}
 
 
 def single_key_rate(bits: int, count: int, kind: str = "crt", window: int = 0, steps: int = 3, warmup: int = 2,
@@ -705,6 +734,18 @@ def toy_rate(steps: int = 20, warmup: int = 3) -> dict:
         ctx.close()
 
 
+def tensor_share(r: dict) -> dict:
+    """The tensor-core groups' MMA work of a ragged step, as a rate over the
+    whole step against the measured bf16 peak (fp16 runs at the same rate)."""
+    tpk, tsrc = measured_bf16_tflops()
+    sec = r["ms_per_step"] / 1e3
+    return {"ops_in_tiles": r["tc_ops"], "method_flops_per_step": r["tc_method_flops_per_step"],
+            "issued_flops_per_step": r["tc_issued_flops_per_step"],
+            "method_tflops_over_step": r["tc_method_flops_per_step"] / sec / 1e12,
+            "peak": tpk, "peak_source": tsrc,
+            "frac_over_step": r["tc_method_flops_per_step"] / sec / 1e12 / tpk}
+
+
 def run_ragged(args):
     """Ragged batch: 256 keys, 200000 operations, one rsa_modexp_batch (one graph
     launch) per step, against a loop of one rsa_modexp_key launch per
@@ -721,10 +762,13 @@ def run_ragged(args):
         "one_key_per_launch": r["one_key_per_launch"], "speedup_vs_loop": r["speedup_vs_loop"],
         "tuning": r["tuning"], "autotuned": bool(args.autotune),
         "roofline": dict(alu_roofline(r["products_per_step"] / (r["ms_per_step"] / 1e3) / 1e12, 0,
-                                      "word products per second under the CIOS count 2L^2 + L per Montgomery "
-                                      "product of each operation's class (window 5 for private exponents); the "
-                                      "2048-bit CRT tiles of the tensor-core group issue fewer on the CUDA cores"),
+                                      "CUDA-core word products issued per second: the CIOS count 2L^2 + L per "
+                                      "Montgomery product (window 5 for private exponents) for operations on the "
+                                      "CUDA-core groups, the tensor-core path's own count (squarings H(H+1)/2, "
+                                      "other products H^2 per half, plus Garner) for the %d operations in "
+                                      "tensor-core tiles" % r["tc_ops"]),
                          products_per_step=r["products_per_step"]),
+        "tensor_cores": tensor_share(r),
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -1135,7 +1179,9 @@ def main():
                     "step; sampled results checked against the oracle",
             "value": r["value"], "unit": "ops/s", "ms_per_step": r["ms_per_step"],
             "one_key_per_launch": r["one_key_per_launch"], "speedup_vs_loop": r["speedup_vs_loop"],
-            "kernel_launches_per_step": r["kernel_launches_per_step"], "tuning": r["tuning"]}
+            "kernel_launches_per_step": r["kernel_launches_per_step"], "tuning": r["tuning"],
+            "issued_cuda_core_tprod_per_s": r["products_per_step"] / (r["ms_per_step"] / 1e3) / 1e12,
+            "tensor_cores": tensor_share(r)}
     if rank == 0 and ws == 1 and not args.no_latency and args.workload == "rsa2048" and args.kind == "crt":
         # the metric's latency half: ragged-batch request latency through the
         # serving loop (256 keys of 1024-4096 bits), offered load swept from

@@ -148,28 +148,34 @@ __global__ void __launch_bounds__(1024) plan_tiles(BatchDesc d) {
     d.ctl[1] = min(tile_base, d.max_tiles);
     if (group >= 0) d.ctl[8 + group] = min(tile_base, d.max_tiles);
   }
-  // tensor-core chunks: up to kTiles whole tiles of one bucket each
+  // tensor-core chunks: whole tiles of one bucket, up to the group's tiles per CTA
   if (d.tc_min_ops) {
-    uint32_t my_chunks = 0;
-    for (uint32_t b = b0; b < b1; ++b) {
-      const uint32_t c = d.bcount[b];
-      if (!c) continue;
-      const uint32_t nt = batch_tc_tiles(d, batch_class(d.dir[b / 3].L, (int)(b % 3), d.wide_crt32), d.dir[b / 3], c);
-      my_chunks += (nt + tcr::kTiles - 1) / tcr::kTiles;
+    for (int32_t grp = 0; grp < TCG_COUNT; ++grp) {
+      const uint32_t per = (uint32_t)batch_tc_chunk_tiles(grp);
+      tcr::TcChunk *list = grp == TCG_2048 ? d.tc_chunks : d.tcx_chunks[grp - 1];
+      uint32_t my_chunks = 0;
+      for (uint32_t b = b0; b < b1; ++b) {
+        const uint32_t c = d.bcount[b];
+        if (!c) continue;
+        const int32_t cls = batch_class(d.dir[b / 3].L, (int)(b % 3), d.wide_crt32);
+        if (batch_tc_group(cls) != grp) continue;
+        my_chunks += (batch_tc_tiles(d, cls, d.dir[b / 3], c) + per - 1) / per;
+      }
+      uint32_t tot_chunks;
+      uint32_t ch = block_exclusive_scan(my_chunks, &tot_chunks, sh);
+      for (uint32_t b = b0; b < b1; ++b) {
+        const uint32_t c = d.bcount[b];
+        if (!c) continue;
+        const KeyDirEntry e = d.dir[b / 3];
+        const int32_t cls = batch_class(e.L, (int)(b % 3), d.wide_crt32);
+        if (batch_tc_group(cls) != grp) continue;
+        const uint32_t nt = batch_tc_tiles(d, cls, e, c);
+        for (uint32_t t0 = 0; t0 < nt; t0 += per, ++ch)
+          if (ch < d.max_tc_chunks)
+            list[ch] = tcr::TcChunk{e.rec, e.tc, (int32_t)(d.boff[b] + t0 * tcr::kRows), (int32_t)min(per, nt - t0)};
+      }
+      if (threadIdx.x == 0) d.ctl[batch_tc_ctl_word(grp)] = min(tot_chunks, d.max_tc_chunks);
     }
-    uint32_t tot_chunks;
-    uint32_t ch = block_exclusive_scan(my_chunks, &tot_chunks, sh);
-    for (uint32_t b = b0; b < b1; ++b) {
-      const uint32_t c = d.bcount[b];
-      if (!c) continue;
-      const KeyDirEntry e = d.dir[b / 3];
-      const uint32_t nt = batch_tc_tiles(d, batch_class(e.L, (int)(b % 3), d.wide_crt32), e, c);
-      for (uint32_t t0 = 0; t0 < nt; t0 += tcr::kTiles, ++ch)
-        if (ch < d.max_tc_chunks)
-          d.tc_chunks[ch] = tcr::TcChunk{e.rec, e.tc, (int32_t)(d.boff[b] + t0 * tcr::kRows),
-                                         (int32_t)min((uint32_t)tcr::kTiles, nt - t0)};
-    }
-    if (threadIdx.x == 0) d.ctl[tcr::kCtlTcChunks] = min(tot_chunks, d.max_tc_chunks);
   }
 }
 
@@ -247,15 +253,25 @@ double class_cost(int32_t cls) {
 
 }  // namespace
 
-// the tensor-core chunk list follows the tile descriptors in the same buffer
+// the tensor-core chunk lists (TCG_COUNT of them) follow the tile descriptors in the same buffer
 static size_t tc_chunks_offset(uint64_t max_tiles) { return ((size_t)max_tiles * sizeof(TileDesc) + 255) / 256 * 256; }
+// the 3072- and 4096-bit tensor-core groups: prime limbs and window (GB300:
+// window 4 at 3072 bits, 3 at 4096, as for uniform batches)
+static constexpr int kTcxH[2] = {48, 64};
+static constexpr int kTcxWindow[2] = {4, 3};
+// window tables shared by the tensor-core groups (they run one after the other)
+static size_t tc_tables_shared(int grid, int window_tc) {
+  size_t b = tcr::tc_tables_bytes(grid, window_tc);
+  for (int x = 0; x < 2; ++x) b = std::max(b, tc4::tc4_tables_bytes(kTcxH[x], grid, kTcxWindow[x]));
+  return b;
+}
 
 struct BatchState {
   cudaStream_t stream = nullptr;
   bool built = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaGraphNode_t nodes[6 + GRP_COUNT] = {};
+  cudaGraphNode_t nodes[4 + 2 * TCG_COUNT + GRP_COUNT] = {};
   int tc_window = 0;          // window of the tensor-core node the graph was built with
   int exec_grid = 0;
   int grids_exec[GRP_COUNT] = {};
@@ -324,6 +340,7 @@ void Ctx::release_stream(cudaStream_t s) {
   if (it != workspaces.end()) {
     Workspace &w = it->second;
     for (DevBuf *d : {&w.tables, &w.io_in, &w.io_out, &w.io_status, &w.aux0, &w.aux1, &w.aux2, &w.aux3, &w.halves,
+                      &w.tc_halves[0], &w.tc_halves[1],
                       &w.verify, &w.gcd0, &w.gcd1})
       if (d->ptr) {
         cudaFree(d->ptr);
@@ -372,18 +389,25 @@ int Ctx::prepare_batch(cudaStream_t s, uint64_t max_count) {
   int rc;
   if ((rc = ensure(w.aux0, (size_t)max_count * 8)) ||                  // op_bucket + sorted
       (rc = ensure(w.aux1, (size_t)nb * 12)) ||                        // bcount, bfill, boff
-      (rc = ensure(w.aux2, tc_chunks_offset(max_tiles) + (max_count / tcr::kRows + 1) * sizeof(tcr::TcChunk))) ||
+      (rc = ensure(w.aux2, tc_chunks_offset(max_tiles) + TCG_COUNT * (max_count / tcr::kRows + 1) * sizeof(tcr::TcChunk))) ||
       (rc = ensure(w.aux3, tcr::kCtlWords * 4)))
     return rc;
   const Tune tr = tune_for(0, RSA_TUNE_RAGGED);
   const bool tc_possible = tr.variant != 1;
   if (tc_possible) {
-    // the tensor-core group: one CTA per SM, the whole shared memory of an SM
+    // the tensor-core groups: one CTA per SM, the whole shared memory of an SM
     const void *fn = tcr::ragged_tc_half_fn(tr.window_tc);
     if (!fn) return set_error(RSA_ERR_ARG, "no tensor-core kernel for this window");
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcr::tc_smem_bytes());
     if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(ragged tensor-core kernel)");
     if ((rc = ensure(w.halves, tcr::tc_halves_bytes((uint32_t)max_count)))) return rc;
+    for (int x = 0; x < 2; ++x) {
+      const int H = kTcxH[x];
+      e = cudaFuncSetAttribute(tc4::ragged_tc4_half_fn(H, kTcxWindow[x]), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)tc4::tc4_smem_bytes(H));
+      if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(ragged tensor-core kernel)");
+      if ((rc = ensure(w.tc_halves[x], tc4::tc4_halves_bytes(H, (uint32_t)max_count)))) return rc;
+    }
   }
   int max_grid = 0;
   for (int g = 0; g < GRP_COUNT; ++g) {
@@ -405,8 +429,9 @@ int Ctx::prepare_batch(cudaStream_t s, uint64_t max_count) {
   size_t table_u4 = 0;
   for (int gi = 0; gi < GRP_COUNT; ++gi)
     table_u4 += (size_t)st->grids_exec[gi] * 2 * batch_table_u4(gi, tr.window, tr.window_big);
-  // then the tensor-core group's tables (one per tile slot of its sm_count CTAs)
-  const size_t tc_bytes = tc_possible ? tcr::tc_tables_bytes(sm_count, tr.window_tc) : 0;
+  // then the tensor-core groups' tables (one per tile slot of their sm_count
+  // CTAs; the groups run one after the other and share them)
+  const size_t tc_bytes = tc_possible ? tc_tables_shared(sm_count, tr.window_tc) : 0;
   return ensure(w.tables, std::max<size_t>(table_u4 * 16 + tc_bytes, 16));
 }
 
@@ -473,6 +498,8 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
   d.max_tiles = max_tiles;
   d.tc_chunks = reinterpret_cast<tcr::TcChunk *>(static_cast<char *>(w.aux2.ptr) + tc_chunks_offset(max_tiles));
   d.max_tc_chunks = (uint32_t)(count / tcr::kRows + 1);
+  d.tcx_chunks[0] = d.tc_chunks + d.max_tc_chunks;
+  d.tcx_chunks[1] = d.tc_chunks + 2 * d.max_tc_chunks;
   // Small batches run 2048-bit CRT with four lanes per operation and 4096-bit
   // CRT with eight: each operation finishes sooner (about 2.2x at 2048 bits),
   // and while the batch fits in one wave of the multi-lane group (8 operations
@@ -506,52 +533,65 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
   }
   const int g_ops = (int)std::min<uint64_t>((count + 255) / 256, (uint64_t)sm_count * 8);
   const int g_nb = (int)std::min<uint32_t>((nb + 255) / 256, (uint32_t)sm_count * 8);
-  // nodes: reset -> count -> tiles -> scatter -> {tensor-core exponentiation ->
-  // tensor-core Garner, one persistent kernel per CUDA-core group} (run
-  // concurrently).  The tensor-core kernel needs whole SMs (all registers,
-  // 210 KB of shared memory), so it is scheduled first (see the graph build);
-  // without tensor-core work its CTAs leave at once.
-  constexpr int kNodes = 6 + GRP_COUNT;
-  constexpr int kTcNode = 4, kGarnerNode = 5, kGroup0 = 6;
+  // nodes: reset -> count -> tiles -> scatter -> {the tensor-core groups
+  // (2048-, 3072-, 4096-bit CRT: exponentiation kernels in a chain, each
+  // followed by its Garner kernel), one persistent kernel per CUDA-core group}
+  // (run concurrently).  The tensor-core kernels need whole SMs (all
+  // registers, ~210 KB of shared memory), so they are scheduled first (see the
+  // graph build); without tensor-core work their CTAs leave at once.
+  constexpr int kNodes = 4 + 2 * TCG_COUNT + GRP_COUNT;
+  constexpr int kTcNode = 4, kGroup0 = 4 + 2 * TCG_COUNT;   // tensor-core group x: 4 + 2x, its Garner 5 + 2x
   const void *tc_fn = tcr::ragged_tc_half_fn(tr.window_tc);
   if (!tc_fn) return set_error(RSA_ERR_ARG, "no tensor-core kernel for this window");
   const void *fns[kNodes] = {reinterpret_cast<const void *>(&plan_reset), reinterpret_cast<const void *>(&plan_count),
                              reinterpret_cast<const void *>(&plan_tiles), reinterpret_cast<const void *>(&plan_scatter),
                              tc_fn, tcr::ragged_tc_garner_fn(),
+                             tc4::ragged_tc4_half_fn(kTcxH[0], kTcxWindow[0]), tc4::ragged_tc4_garner_fn(kTcxH[0]),
+                             tc4::ragged_tc4_half_fn(kTcxH[1], kTcxWindow[1]), tc4::ragged_tc4_garner_fn(kTcxH[1]),
                              batch_exec_fn(0), batch_exec_fn(1), batch_exec_fn(2), batch_exec_fn(3)};
   dim3 grids[kNodes] = {dim3(std::max(1, g_nb)), dim3(g_ops), dim3(1), dim3(g_ops),
+                        dim3(sm_count), dim3(sm_count * 4), dim3(sm_count), dim3(sm_count * 4),
                         dim3(sm_count), dim3(sm_count * 4)};
   dim3 blocks[kNodes] = {dim3(256), dim3(256), dim3(1024), dim3(256), dim3(tcr::kThreads),
-                         dim3(tcr::kRaggedGarnerThreads)};
-  size_t smems[kNodes] = {0, 0, 0, 0, tcr::tc_smem_bytes(), tcr::ragged_tc_garner_smem()};
+                         dim3(tcr::kRaggedGarnerThreads), dim3(tc4::kThreads), dim3(128), dim3(tc4::kThreads),
+                         dim3(128)};
+  size_t smems[kNodes] = {0, 0, 0, 0, tcr::tc_smem_bytes(), tcr::ragged_tc_garner_smem(),
+                          tc4::tc4_smem_bytes(kTcxH[0]), tc4::ragged_tc4_garner_smem(kTcxH[0]),
+                          tc4::tc4_smem_bytes(kTcxH[1]), tc4::ragged_tc4_garner_smem(kTcxH[1])};
   BatchDesc dg[kNodes];
   void *args[kNodes][1];
   for (int i = 0; i < kNodes; ++i) {
     dg[i] = d;
     args[i][0] = &dg[i];
   }
-  // the tensor-core nodes take their own argument block
+  // the tensor-core nodes take their own argument blocks
   size_t group_table_u4 = 0;
   for (int gi = 0; gi < GRP_COUNT; ++gi)
     group_table_u4 += (size_t)grids_exec[gi] * 2 * batch_table_u4(gi, d.win_small, d.win_big);
-  tcr::RaggedTcArgs ra{};
-  ra.chunks = d.tc_chunks;
-  ra.ctl = d.ctl;
-  ra.sorted = d.sorted;
-  ra.offsets = offsets;
-  ra.msgs = msgs;
-  ra.out = out;
-  ra.status = status;
-  ra.tables = d.tables + group_table_u4;
-  ra.halves = w.halves.ptr;
-  ra.count = (uint32_t)count;
-  ra.wait_polls = tcr::kDefaultWaitPolls;
-  if (const char *ev = std::getenv("RSAGPU_TC_WAIT_POLLS")) ra.wait_polls = (uint32_t)std::strtoul(ev, nullptr, 10);
+  tcr::RaggedTcArgs ra[TCG_COUNT];
+  for (int x = 0; x < TCG_COUNT; ++x) {
+    ra[x] = tcr::RaggedTcArgs{};
+    ra[x].chunks = x == TCG_2048 ? d.tc_chunks : d.tcx_chunks[x - 1];
+    ra[x].ctl = d.ctl;
+    ra[x].sorted = d.sorted;
+    ra[x].offsets = offsets;
+    ra[x].msgs = msgs;
+    ra[x].out = out;
+    ra[x].status = status;
+    ra[x].tables = d.tables + group_table_u4;
+    ra[x].halves = x == TCG_2048 ? w.halves.ptr : w.tc_halves[x - 1].ptr;
+    ra[x].count = (uint32_t)count;
+    ra[x].wait_polls = tcr::kDefaultWaitPolls;
+    if (const char *ev = std::getenv("RSAGPU_TC_WAIT_POLLS")) ra[x].wait_polls = (uint32_t)std::strtoul(ev, nullptr, 10);
+    ra[x].ctl_word = (uint32_t)batch_tc_ctl_word(x);
+    args[kTcNode + 2 * x][0] = &ra[x];
+    args[kTcNode + 2 * x + 1][0] = &ra[x];
+  }
   if (tc_on && (!w.halves.ptr || w.halves.bytes < tcr::tc_halves_bytes((uint32_t)count) ||
-                w.tables.bytes < group_table_u4 * 16 + tcr::tc_tables_bytes(sm_count, tr.window_tc)))
+                w.tc_halves[0].bytes < tc4::tc4_halves_bytes(kTcxH[0], (uint32_t)count) ||
+                w.tc_halves[1].bytes < tc4::tc4_halves_bytes(kTcxH[1], (uint32_t)count) ||
+                w.tables.bytes < group_table_u4 * 16 + tc_tables_shared(sm_count, tr.window_tc)))
     return set_error(RSA_ERR_NOMEM, "tensor-core workspace of the ragged batch is missing");
-  args[kTcNode][0] = &ra;
-  args[kGarnerNode][0] = &ra;
   // each group's warps index their own slice of the table scratch
   size_t slot_off = 0;
   // a batch with few tiles launches only the CTAs it can use (at most one
@@ -597,9 +637,14 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
     const bool overlap = !ov || std::atoi(ov) != 0;
     for (int i = 0; i < kNodes; ++i) {
       cudaKernelNodeParams p = params(i);
-      // planning in sequence; the tensor-core kernel after the scatter; its
-      // Garner after it; the CUDA-core groups after it (or after the scatter)
-      const int dep = i <= kTcNode ? i - 1 : (i == kGarnerNode || !overlap) ? kTcNode : 3;
+      // planning in sequence; the tensor-core kernels in a chain after the
+      // scatter, each Garner after its kernel; the CUDA-core groups after the
+      // scatter (or, without overlap, after the last tensor-core kernel)
+      constexpr int kLastTc = kTcNode + 2 * (TCG_COUNT - 1);
+      int dep;
+      if (i <= kTcNode) dep = i - 1;
+      else if (i < kGroup0) dep = ((i - kTcNode) & 1) ? i - 1 : i - 2;   // Garner: its kernel; kernel: the previous kernel
+      else dep = overlap ? 3 : kLastTc;
       e = cudaGraphAddKernelNode(&st->nodes[i], st->graph, dep >= 0 ? &st->nodes[dep] : nullptr, dep >= 0 ? 1 : 0, &p);
       if (e != cudaSuccess) return cuda_error(e, "cudaGraphAddKernelNode");
     }
@@ -609,8 +654,10 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
         return cuda_error(e, "cudaDeviceGetStreamPriorityRange");
       cudaLaunchAttributeValue v{};
       v.priority = greatest;
-      if ((e = cudaGraphKernelNodeSetAttribute(st->nodes[kTcNode], cudaLaunchAttributePriority, &v)) != cudaSuccess)
-        return cuda_error(e, "cudaGraphKernelNodeSetAttribute(priority)");
+      for (int x = 0; x < TCG_COUNT; ++x)
+        if ((e = cudaGraphKernelNodeSetAttribute(st->nodes[kTcNode + 2 * x], cudaLaunchAttributePriority, &v)) !=
+            cudaSuccess)
+          return cuda_error(e, "cudaGraphKernelNodeSetAttribute(priority)");
     }
     if ((e = cudaGraphInstantiate(&st->exec, st->graph, 0)) != cudaSuccess)
       return cuda_error(e, "cudaGraphInstantiate");

@@ -152,12 +152,27 @@ struct BatchDesc {
   // (0: none) send floor(count / 128) whole tiles there, in chunks of up to
   // tcr::kTiles tiles of one key; max_tc_chunks bounds the chunk list
   uint32_t tc_min_ops, max_tc_chunks;
-  tcr::TcChunk *tc_chunks;
+  tcr::TcChunk *tc_chunks;    // 2048-bit CRT chunks (up to tcr::kTiles tiles each)
+  tcr::TcChunk *tcx_chunks[2];  // 3072- and 4096-bit CRT chunks (up to tc4::kTiles tiles each)
 };
 
-// whole tensor-core tiles a bucket of c operations sends to the tensor-core group
+// Tensor-core groups of ragged batches: 2048-, 3072- and 4096-bit CRT buckets,
+// each with its chunk list and the control words chunk count / work counter.
+enum : int32_t { TCG_2048 = 0, TCG_3072 = 1, TCG_4096 = 2, TCG_COUNT = 3 };
+__host__ __device__ constexpr int32_t batch_tc_ctl_word(int32_t grp) { return tcr::kCtlTcChunks + 2 * grp; }
+__host__ __device__ constexpr int32_t batch_tc_chunk_tiles(int32_t grp) {
+  return grp == TCG_2048 ? tcr::kTiles : tc4::kTiles;
+}
+// the tensor-core group of a class (-1: none): the one-lane 2048-bit CRT class
+// and the four-lane 3072/4096-bit ones (the throughput shapes)
+__host__ __device__ inline int32_t batch_tc_group(int32_t cls) {
+  return cls == CLS_CRT32 ? TCG_2048 : cls == CLS_CRT48 ? TCG_3072 : cls == CLS_CRT64 ? TCG_4096 : -1;
+}
+static_assert(tcr::kCtlTcChunks + 2 * TCG_COUNT <= 30, "control words");
+
+// whole tensor-core tiles a bucket of c operations sends to its tensor-core group
 __host__ __device__ inline uint32_t batch_tc_tiles(const BatchDesc &d, int32_t cls, const KeyDirEntry &e, uint32_t c) {
-  if (cls != CLS_CRT32 || d.tc_min_ops == 0 || e.tc == nullptr || c < d.tc_min_ops) return 0u;
+  if (batch_tc_group(cls) < 0 || d.tc_min_ops == 0 || e.tc == nullptr || c < d.tc_min_ops) return 0u;
   return c / (uint32_t)tcr::kRows;
 }
 

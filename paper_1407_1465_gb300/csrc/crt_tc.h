@@ -77,6 +77,7 @@ struct RaggedTcArgs {
   void *tables;                 // tc_tables_bytes(grid, window)
   void *halves;                 // tc_halves_bytes(count), indexed by sorted position
   uint32_t count, wait_polls;
+  uint32_t ctl_word;            // the group's chunk count in ctl[ctl_word], its work-item counter in ctl[ctl_word + 1]
 };
 // kernel entry points for the batch graph (window 3 or 4)
 const void *ragged_tc_half_fn(int window);
@@ -114,6 +115,11 @@ int tc4_grid(uint32_t count, int sm_count);
 cudaError_t launch_crt_tc4(int H, const uint32_t *keyrec, const void *image, const uint32_t *msgs, uint32_t *out,
                            int32_t *status, uint32_t count, int grid, int window, void *tables, void *halves,
                            uint32_t wait_polls, cudaStream_t s);
+// kernel entry points for the ragged batch graph (tcr::RaggedTcArgs, chunks of up to kTiles tiles)
+const void *ragged_tc4_half_fn(int H, int window);
+const void *ragged_tc4_garner_fn(int H);
+size_t tc4_smem_bytes(int H);
+size_t ragged_tc4_garner_smem(int H);
 #endif
 }  // namespace tc4
 }  // namespace rsagpu

@@ -509,43 +509,59 @@ struct HalfArgs {
   uint32_t wait_polls;
 };
 
-template <int H, int W>
-__global__ void __launch_bounds__(kThreads, 1) crt_tc4_half_kernel(HalfArgs a) {
+// key constants of prime pi (0: q, 1: p) and its two B operands into shared memory
+template <int H>
+__device__ __forceinline__ void load_prime(uint8_t *smem, const uint32_t *keyrec, const uint4 *image, uint32_t pi,
+                                           int tid) {
+  using S = Shape<H>;
+  constexpr KeyLayout lay(2 * H);
+  uint32_t *kc = reinterpret_cast<uint32_t *>(smem + S::OffKey);
+  const uint32_t om = pi ? lay.p : lay.q, or2 = pi ? lay.r2p : lay.r2q, or3 = pi ? lay.r3p : lay.r3q;
+  const uint32_t oone = pi ? lay.onep : lay.oneq, oexp = pi ? lay.dp : lay.dq;
+  for (int i = tid; i < S::KeyWords; i += kThreads) {
+    uint32_t v;
+    if (i < S::Kr2) v = keyrec[om + i];
+    else if (i < S::Kr3) v = keyrec[or2 + i - S::Kr2];
+    else if (i < S::Kone) v = keyrec[or3 + i - S::Kr3];
+    else if (i < S::Kunit) v = keyrec[oone + i - S::Kone];
+    else if (i < S::Kexp) v = (i == S::Kunit) ? 1u : 0u;
+    else v = keyrec[oexp + i - S::Kexp];
+    kc[i] = v;
+  }
+  constexpr int img_u4 = (S::ImgB1 + S::ImgB2) / 16;
+  const uint4 *img = image + (size_t)pi * img_u4;
+  uint4 *s4 = reinterpret_cast<uint4 *>(smem + S::OffB1);
+  for (int i = tid; i < img_u4; i += kThreads) s4[i] = img[i];
+}
+
+// Uniform batches (RAGGED = false): one key; CTA 2c + pi runs prime pi, its two
+// tile slots take tiles round-robin.  Ragged batches (RAGGED = true): the CTA
+// repeatedly takes a work item (chunk, prime) from the counter
+// ctl[ra.ctl_word + 1], loads that key's constants and operands, and runs the
+// chunk's tiles (up to two) in its slots.
+template <int H, int W, bool RAGGED>
+__device__ __forceinline__ void half_body(const HalfArgs &a, const tcr::RaggedTcArgs &ra) {
   using S = Shape<H>;
   using Wn = Win<H, W>;
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int slot = warp >> 2;
   const int r = ((warp & 3) << 5) | lane;
-  const uint32_t pi = blockIdx.x & 1u;
-  const uint32_t cta = blockIdx.x >> 1;
   const uint32_t sb = tc::smem_addr(smem);
   uint32_t *ctrl = reinterpret_cast<uint32_t *>(smem + S::OffCtrl);
+  if constexpr (RAGGED) {
+    // CTAs beyond the planned work items leave before touching TMEM
+    if (blockIdx.x >= 2u * ra.ctl[ra.ctl_word]) return;
+  }
 
   if (warp == 0) tc::tmem_alloc(sb + S::OffCtrl + 48, kTmemCols);
   if (tid == 0) {
     for (int t = 0; t < kTiles; ++t) tc::mbar_init(sb + S::OffCtrl + 8 * t, 1u);
     tc::mbar_init_fence();
   }
-  constexpr KeyLayout lay(2 * H);
   uint32_t *kc = reinterpret_cast<uint32_t *>(smem + S::OffKey);
+  if constexpr (!RAGGED) load_prime<H>(smem, a.keyrec, a.image, blockIdx.x & 1u, tid);
   {
-    const uint32_t om = pi ? lay.p : lay.q, or2 = pi ? lay.r2p : lay.r2q, or3 = pi ? lay.r3p : lay.r3q;
-    const uint32_t oone = pi ? lay.onep : lay.oneq, oexp = pi ? lay.dp : lay.dq;
-    for (int i = tid; i < S::KeyWords; i += kThreads) {
-      uint32_t v;
-      if (i < S::Kr2) v = a.keyrec[om + i];
-      else if (i < S::Kr3) v = a.keyrec[or2 + i - S::Kr2];
-      else if (i < S::Kone) v = a.keyrec[or3 + i - S::Kr3];
-      else if (i < S::Kunit) v = a.keyrec[oone + i - S::Kone];
-      else if (i < S::Kexp) v = (i == S::Kunit) ? 1u : 0u;
-      else v = a.keyrec[oexp + i - S::Kexp];
-      kc[i] = v;
-    }
-    constexpr int img_u4 = (S::ImgB1 + S::ImgB2) / 16;
-    const uint4 *img = a.image + (size_t)pi * img_u4;
-    uint4 *s4 = reinterpret_cast<uint4 *>(smem + S::OffB1);
-    for (int i = tid; i < img_u4; i += kThreads) s4[i] = img[i];
     uint4 *ab = reinterpret_cast<uint4 *>(smem + S::OffAbias);
     for (int i = tid; i < kRows * 16 * 2 / 16; i += kThreads)
       ab[i] = make_uint4(0x01000100u, 0x01000100u, 0x01000100u, 0x01000100u);
@@ -569,20 +585,60 @@ __global__ void __launch_bounds__(kThreads, 1) crt_tc4_half_kernel(HalfArgs a) {
   ts.leader = (r == 0);
   ts.err = false;
   ts.dead = false;
-  uint4 *tbl = a.tables + (size_t)(blockIdx.x * kTiles + slot) * Wn::kTblU4 + r;
+  uint4 *tbl = (RAGGED ? static_cast<uint4 *>(ra.tables) : a.tables) + (size_t)(blockIdx.x * kTiles + slot) * Wn::kTblU4 + r;
 
-  for (uint32_t tile = cta + a.ctas_per_prime * (uint32_t)slot; tile < a.ntiles; tile += a.ctas_per_prime * kTiles) {
-    const uint32_t row = tile * kRows + (uint32_t)r;
-    const bool valid = row < a.count;
-    const uint32_t *msg = a.msgs + (size_t)(valid ? row : a.count - 1) * (2 * H);
-    uint32_t A[H];
-    if (!ts.dead) exp_tile<H, W>(A, ts, smem, msg, pi, kc, tbl, a.wait_polls);
-    if (valid) {
-      uint4 *h = a.halves + (size_t)pi * (H / 4) * a.count_pad + row;
+  if constexpr (!RAGGED) {
+    const uint32_t pi = blockIdx.x & 1u;
+    const uint32_t cta = blockIdx.x >> 1;
+    for (uint32_t tile = cta + a.ctas_per_prime * (uint32_t)slot; tile < a.ntiles;
+         tile += a.ctas_per_prime * kTiles) {
+      const uint32_t row = tile * kRows + (uint32_t)r;
+      const bool valid = row < a.count;
+      const uint32_t *msg = a.msgs + (size_t)(valid ? row : a.count - 1) * (2 * H);
+      uint32_t A[H];
+      if (!ts.dead) exp_tile<H, W>(A, ts, smem, msg, pi, kc, tbl, a.wait_polls);
+      if (valid) {
+        uint4 *h = a.halves + (size_t)pi * (H / 4) * a.count_pad + row;
 #pragma unroll
-      for (int g = 0; g < H / 4; ++g)
-        h[(size_t)g * a.count_pad] = make_uint4(A[4 * g], A[4 * g + 1], A[4 * g + 2], A[4 * g + 3]);
-      a.herr[(size_t)pi * a.count + row] = (ts.err || ts.dead) ? 1u : 0u;
+        for (int g = 0; g < H / 4; ++g)
+          h[(size_t)g * a.count_pad] = make_uint4(A[4 * g], A[4 * g + 1], A[4 * g + 2], A[4 * g + 3]);
+        a.herr[(size_t)pi * a.count + row] = (ts.err || ts.dead) ? 1u : 0u;
+      }
+    }
+  } else {
+    const uint32_t nitems = 2u * ra.ctl[ra.ctl_word];
+    const uint32_t cpad = (ra.count + 31u) & ~31u;
+    uint4 *halves = static_cast<uint4 *>(ra.halves);
+    uint32_t *herr = reinterpret_cast<uint32_t *>(halves + (size_t)2 * (H / 4) * cpad);
+#pragma unroll 1
+    for (;;) {
+      // every slot is done with the previous item's constants and operands
+      // (its MMAs have completed: each slot waited for them)
+      tc::fence_before_sync();
+      __syncthreads();
+      if (tid == 0) ctrl[8] = atomicAdd(&ra.ctl[ra.ctl_word + 1], 1u);
+      __syncthreads();
+      const uint32_t item = ctrl[8];
+      if (item >= nitems) break;
+      const tcr::TcChunk ch = ra.chunks[item >> 1];
+      const uint32_t pi = item & 1u;
+      load_prime<H>(smem, ch.keyrec, static_cast<const uint4 *>(ch.image), pi, tid);
+      tc::fence_proxy_async_smem();
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+      if (slot < ch.ntiles) {
+        const uint32_t pos = (uint32_t)ch.op_start + (uint32_t)slot * kRows + (uint32_t)r;
+        const uint32_t op = (uint32_t)ra.sorted[pos];
+        const uint32_t *msg = ra.msgs + ra.offsets[op];
+        uint32_t A[H];
+        if (!ts.dead) exp_tile<H, W>(A, ts, smem, msg, pi, kc, tbl, ra.wait_polls);
+        uint4 *h = halves + (size_t)pi * (H / 4) * cpad + pos;
+#pragma unroll
+        for (int g = 0; g < H / 4; ++g)
+          h[(size_t)g * cpad] = make_uint4(A[4 * g], A[4 * g + 1], A[4 * g + 2], A[4 * g + 3]);
+        herr[(size_t)pi * ra.count + pos] = (ts.err || ts.dead) ? 1u : 0u;
+      }
     }
   }
   if (ts.leader && ts.pending < 2u) (void)tc::mbar_wait(ts.mbar, ts.pending, kWaitLimit);
@@ -592,6 +648,15 @@ __global__ void __launch_bounds__(kThreads, 1) crt_tc4_half_kernel(HalfArgs a) {
     tc::fence_after_sync();
     tc::tmem_dealloc(ctrl[12], kTmemCols);
   }
+}
+
+template <int H, int W>
+__global__ void __launch_bounds__(kThreads, 1) crt_tc4_half_kernel(HalfArgs a) {
+  half_body<H, W, false>(a, tcr::RaggedTcArgs{});
+}
+template <int H, int W>
+__global__ void __launch_bounds__(kThreads, 1) crt_tc4_ragged_half_kernel(tcr::RaggedTcArgs ra) {
+  half_body<H, W, true>(HalfArgs{}, ra);
 }
 
 // ---------------------------------------------------------------- Garner recombination
@@ -614,49 +679,40 @@ struct GarnerArgs {
   uint32_t count, count_pad;
 };
 
+// One operation: hq / hp are its m_q and m_p * R mod p (H/4 uint4, `hstride`
+// apart); ks the key record in shared memory; stage_lane the thread's slot of
+// an [H/4][32] uint4 stage.  Writes the 2H-limb row at orow (zeros unless ok)
+// and returns the status (0, RSA_ERR_RANGE -3 or RSA_ERR_TIMEOUT -6).
 template <int H>
-__global__ void __launch_bounds__(kGThreads) crt_tc4_garner_kernel(GarnerArgs a) {
+__device__ __forceinline__ int32_t garner_op(const uint32_t *ks, uint4 *stage_lane, const uint4 *hq, const uint4 *hp,
+                                             size_t hstride, bool timed_out, const uint32_t *mrow, uint4 *orow,
+                                             bool valid) {
   constexpr int L = 2 * H;
   constexpr KeyLayout lay(L);
-  constexpr int KW = GarnerSmem<H>::KeyWords;
-  extern __shared__ uint4 gsm[];
-  uint32_t *ks = reinterpret_cast<uint32_t *>(gsm);
-  for (int i = threadIdx.x; i < KW / 4; i += kGThreads)
-    gsm[i] = (i * 4 < (int)lay.total) ? reinterpret_cast<const uint4 *>(a.keyrec)[i] : make_uint4(0u, 0u, 0u, 0u);
-  __syncthreads();
   const KeyHeader &hd = *reinterpret_cast<const KeyHeader *>(ks);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t row = blockIdx.x * kGThreads + threadIdx.x;
-  const bool valid = row < a.count;
-  const uint32_t rr = valid ? row : 0u;
-  uint4 *stage_lane = gsm + KW / 4 + warp * (H / 4) * 32 + lane;
   const NSmem<H> N{ks + lay.p};
-  const uint4 *hq = a.halves + rr, *hp = a.halves + (size_t)(H / 4) * a.count_pad + rr;
   uint32_t A[H];
 #pragma unroll
   for (int g = 0; g < H / 4; ++g) {
-    const uint4 v = hq[(size_t)g * a.count_pad];
+    const uint4 v = hq[(size_t)g * hstride];
     A[4 * g] = v.x; A[4 * g + 1] = v.y; A[4 * g + 2] = v.z; A[4 * g + 3] = v.w;
   }
   mont_mul<H, 4>(A, SmemB{reinterpret_cast<const uint4 *>(ks + lay.r2p), 1}, N, hd.np_p);   // m_q * R mod p
 #pragma unroll
-  for (int g = 0; g < H / 4; ++g) stage_lane[g * 32] = hp[(size_t)g * a.count_pad];         // m_p * R mod p
+  for (int g = 0; g < H / 4; ++g) stage_lane[g * 32] = hp[(size_t)g * hstride];             // m_p * R mod p
   mod_rsub<H>(A, SmemB{stage_lane, 32}, N);                                                  // (m_p - m_q) R
   mont_mul<H, 4>(A, SmemB{reinterpret_cast<const uint4 *>(ks + lay.qinv), 1}, N, hd.np_p);  // h
   uint32_t t[H + 2];
 #pragma unroll
   for (int g = 0; g < H / 4; ++g) {
-    const uint4 v = hq[(size_t)g * a.count_pad];
+    const uint4 v = hq[(size_t)g * hstride];
     t[4 * g] = v.x; t[4 * g + 1] = v.y; t[4 * g + 2] = v.z; t[4 * g + 3] = v.w;
   }
   t[H] = 0u;
   t[H + 1] = 0u;
   const uint32_t *qs = ks + lay.q;
-  const uint32_t *mrow = a.msgs + (size_t)rr * L;
   const bool below = row_below(mrow, ks + lay.n, L);
-  const bool timed_out = a.herr[rr] != 0u || a.herr[a.count + rr] != 0u;
   const bool ok = valid && below && !timed_out;
-  uint4 *orow = reinterpret_cast<uint4 *>(a.out + (size_t)rr * L);
 #pragma unroll 1
   for (int i0 = 0; i0 < H; i0 += 4) {
     uint32_t rv[4];
@@ -675,7 +731,64 @@ __global__ void __launch_bounds__(kGThreads) crt_tc4_garner_kernel(GarnerArgs a)
     if (valid)
       orow[H / 4 + g] = ok ? make_uint4(t[4 * g], t[4 * g + 1], t[4 * g + 2], t[4 * g + 3])
                            : make_uint4(0u, 0u, 0u, 0u);
-  if (valid && a.status) a.status[rr] = timed_out ? -6 /* RSA_ERR_TIMEOUT */ : (below ? 0 : -3 /* RSA_ERR_RANGE */);
+  return timed_out ? -6 /* RSA_ERR_TIMEOUT */ : (below ? 0 : -3 /* RSA_ERR_RANGE */);
+}
+
+template <int H>
+__device__ __forceinline__ void load_key_record(uint4 *gsm, const uint32_t *keyrec) {
+  constexpr KeyLayout lay(2 * H);
+  for (int i = threadIdx.x; i < GarnerSmem<H>::KeyWords / 4; i += blockDim.x)
+    gsm[i] = (i * 4 < (int)lay.total) ? reinterpret_cast<const uint4 *>(keyrec)[i] : make_uint4(0u, 0u, 0u, 0u);
+}
+
+template <int H>
+__global__ void __launch_bounds__(kGThreads) crt_tc4_garner_kernel(GarnerArgs a) {
+  extern __shared__ uint4 gsm[];
+  load_key_record<H>(gsm, a.keyrec);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t row = blockIdx.x * kGThreads + threadIdx.x;
+  const bool valid = row < a.count;
+  const uint32_t rr = valid ? row : 0u;
+  uint4 *stage_lane = gsm + GarnerSmem<H>::KeyWords / 4 + warp * (H / 4) * 32 + lane;
+  const bool timed_out = a.herr[rr] != 0u || a.herr[a.count + rr] != 0u;
+  const int32_t st = garner_op<H>(reinterpret_cast<const uint32_t *>(gsm), stage_lane, a.halves + rr,
+                                  a.halves + (size_t)(H / 4) * a.count_pad + rr, a.count_pad, timed_out,
+                                  a.msgs + (size_t)rr * 2 * H, reinterpret_cast<uint4 *>(a.out + (size_t)rr * 2 * H),
+                                  valid);
+  if (valid && a.status) a.status[rr] = st;
+}
+
+// Ragged batches: block b takes the (chunk, slot) tiles b, b + grid, ... of the
+// group's planned chunks; one thread per operation of the tile, the tile's key
+// record in shared memory.  Timeouts are also flagged in the batch's error word.
+template <int H>
+__global__ void __launch_bounds__(kGThreads) crt_tc4_ragged_garner_kernel(tcr::RaggedTcArgs ra) {
+  extern __shared__ uint4 gsm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint4 *stage_lane = gsm + GarnerSmem<H>::KeyWords / 4 + warp * (H / 4) * 32 + lane;
+  const uint32_t ntile_slots = (uint32_t)kTiles * ra.ctl[ra.ctl_word];
+  const uint32_t cpad = (ra.count + 31u) & ~31u;
+  const uint4 *halves = static_cast<const uint4 *>(ra.halves);
+  const uint32_t *herr = reinterpret_cast<const uint32_t *>(halves + (size_t)2 * (H / 4) * cpad);
+#pragma unroll 1
+  for (uint32_t t = blockIdx.x; t < ntile_slots; t += gridDim.x) {
+    const tcr::TcChunk ch = ra.chunks[t / kTiles];
+    const int s = (int)(t % kTiles);
+    if (s >= ch.ntiles) continue;   // uniform over the block
+    __syncthreads();                // the previous tile's key record is no longer read
+    load_key_record<H>(gsm, ch.keyrec);
+    __syncthreads();
+    const uint32_t pos = (uint32_t)ch.op_start + (uint32_t)s * kRows + threadIdx.x;
+    const uint32_t op = (uint32_t)ra.sorted[pos];
+    const size_t off = (size_t)ra.offsets[op];
+    const bool timed_out = herr[pos] != 0u || herr[ra.count + pos] != 0u;
+    const int32_t st = garner_op<H>(reinterpret_cast<const uint32_t *>(gsm), stage_lane, halves + pos,
+                                    halves + (size_t)(H / 4) * cpad + pos, cpad, timed_out, ra.msgs + off,
+                                    reinterpret_cast<uint4 *>(ra.out + off), true);
+    if (ra.status) ra.status[op] = st;
+    if (timed_out) atomicOr(&ra.ctl[2], 1u << 6);   // RSA_ERR_TIMEOUT for rsa_sync
+  }
 }
 
 // ---------------------------------------------------------------- host side
@@ -741,6 +854,23 @@ static cudaError_t launch_h(const uint32_t *keyrec, const void *image, const uin
   g.count_pad = cp;
   crt_tc4_garner_kernel<H><<<(count + kGThreads - 1) / kGThreads, kGThreads, GarnerSmem<H>::Bytes, s>>>(g);
   return cudaGetLastError();
+}
+
+const void *ragged_tc4_half_fn(int H, int window) {
+  if (H == 48) return window == 3 ? reinterpret_cast<const void *>(&crt_tc4_ragged_half_kernel<48, 3>)
+                                  : reinterpret_cast<const void *>(&crt_tc4_ragged_half_kernel<48, 4>);
+  if (H == 64) return window == 3 ? reinterpret_cast<const void *>(&crt_tc4_ragged_half_kernel<64, 3>)
+                                  : reinterpret_cast<const void *>(&crt_tc4_ragged_half_kernel<64, 4>);
+  return nullptr;
+}
+const void *ragged_tc4_garner_fn(int H) {
+  if (H == 48) return reinterpret_cast<const void *>(&crt_tc4_ragged_garner_kernel<48>);
+  if (H == 64) return reinterpret_cast<const void *>(&crt_tc4_ragged_garner_kernel<64>);
+  return nullptr;
+}
+size_t tc4_smem_bytes(int H) { return H == 48 ? (size_t)Shape<48>::Smem : (size_t)Shape<64>::Smem; }
+size_t ragged_tc4_garner_smem(int H) {
+  return H == 48 ? (size_t)GarnerSmem<48>::Bytes : (size_t)GarnerSmem<64>::Bytes;
 }
 
 cudaError_t launch_crt_tc4(int H, const uint32_t *keyrec, const void *image, const uint32_t *msgs, uint32_t *out,

@@ -82,7 +82,8 @@ Ctx::~Ctx() {
 }
 
 void Workspace::free_all() {
-  for (DevBuf *b : {&tables, &io_in, &io_out, &io_status, &aux0, &aux1, &aux2, &aux3, &halves, &verify, &gcd0, &gcd1}) {
+  for (DevBuf *b : {&tables, &io_in, &io_out, &io_status, &aux0, &aux1, &aux2, &aux3, &halves, &tc_halves[0],
+                    &tc_halves[1], &verify, &gcd0, &gcd1}) {
     if (b->ptr) cudaFree(b->ptr);
     b->ptr = nullptr;
     b->bytes = 0;

@@ -38,6 +38,7 @@ struct Workspace {
   DevBuf io_in, io_out, io_status;  // host-buffer entry points
   DevBuf aux0, aux1, aux2, aux3;  // ragged-batch planning buffers
   DevBuf halves;                  // tensor-core CRT path: per-prime results between its two kernels
+  DevBuf tc_halves[2];            // ragged batches: the same for the 3072- and 4096-bit tensor-core groups
   DevBuf verify;                  // rsa_verify_key: recovered representatives
   DevBuf gcd0, gcd1;              // rsa_batch_gcd: validity + block products, partial products
   void free_all();

@@ -180,7 +180,7 @@ def test_serving_restart_returns_memory(torch_cuda):
     so the loop can be started again in the same context."""
     from paper_1407_1465_gb300 import RsaContext, build, rsa_server_start, rsa_server_stop
     build.build()
-    ctx = RsaContext(0, mem_budget_bytes=3 << 30)
+    ctx = RsaContext(0, mem_budget_bytes=5 << 30)
     try:
         base = ctx.stats()["bytes_resident"]
         for _ in range(3):
