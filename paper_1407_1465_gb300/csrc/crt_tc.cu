@@ -112,24 +112,27 @@ struct GarnerArgs {
 // ---------------------------------------------------------------- arithmetic pieces
 using tc::pair_cols;
 
-// t[j0 .. j0+NL) += (4*NL column words v, carry-propagated from the carry c
-// in base 2^16: two columns per step) + cin; the column carry returns in c and
-// the limb carry in cin.  Two base-2^16 digits make one limb.
+// t[j0 .. j0+NL) += the 4*NL column words v taken as 2*NL base-2^16 columns
+// (tc::lo_halves / tc::hi_halves): s = X + Y word by word with the carry cs,
+// then t += s with the carry cin.  yb is the column below v[0]: its high half
+// (the pending carry, < 2^16) enters word j0; the last column of v returns in
+// yb.  Two carry chains of NL words, no 16-bit ripple.
 template <int NL>
-__device__ __forceinline__ void add_columns(uint32_t (&t)[kH], int j0, const uint32_t *v, uint32_t &c,
-                                            uint32_t &cin) {
-  uint32_t X[NL];
+__device__ __forceinline__ void add_columns(uint32_t (&t)[kH], int j0, const uint32_t *v, uint32_t &yb,
+                                            uint32_t &cs, uint32_t &cin) {
+  uint32_t y[2 * NL];
 #pragma unroll
-  for (int i = 0; i < NL; ++i) {
-    const uint32_t y0 = pair_cols(v[4 * i], v[4 * i + 1]) + c;
-    c = y0 >> 16;
-    const uint32_t y1 = pair_cols(v[4 * i + 2], v[4 * i + 3]) + c;
-    c = y1 >> 16;
-    X[i] = tc::prmt(y0, y1, 0x5410u);   // [y0.b0, y0.b1, y1.b0, y1.b1]
-  }
-  (void)add_cc(cin, 0xFFFFFFFFu);   // carry flag <- cin (0 or 1)
+  for (int i = 0; i < 2 * NL; ++i) y[i] = pair_cols(v[2 * i], v[2 * i + 1]);
+  uint32_t x[NL];
+  (void)add_cc(cs, 0xFFFFFFFFu);    // carry flag <- cs (0 or 1)
 #pragma unroll
-  for (int i = 0; i < NL; ++i) t[j0 + i] = addc_cc(t[j0 + i], X[i]);
+  for (int i = 0; i < NL; ++i)
+    x[i] = addc_cc(tc::lo_halves(y[2 * i], y[2 * i + 1]), tc::hi_halves(i ? y[2 * i - 1] : yb, y[2 * i]));
+  cs = addc(0u, 0u);
+  yb = y[2 * NL - 1];
+  (void)add_cc(cin, 0xFFFFFFFFu);   // carry flag <- cin
+#pragma unroll
+  for (int i = 0; i < NL; ++i) t[j0 + i] = addc_cc(t[j0 + i], x[i]);
   cin = addc(0u, 0u);
 }
 
@@ -278,11 +281,13 @@ __device__ __forceinline__ void mont_step(uint32_t (&A)[kH], bool sq, uint32_t b
   if (ts.dead) return;
   if (ts.leader) issue_mmas(ts, kOffBm);
   wait_mmas(ts, polls);
-  // 3. mu = carry-propagated columns mod R, back to shared memory as digits;
-  //    its top digits are kept for positions 252..254 of mu * m
+  // 3. mu = the column sums mod R (as 32-bit words: tc::lo_halves /
+  //    tc::hi_halves, one carry chain), back to shared memory as digits; its
+  //    top digits are kept for positions 252..254 of mu * m
   uint32_t mu_top = 0u;   // [mu_124, mu_125, mu_126, mu_127]
   {
-    uint32_t c = 0u;        // carry between base-2^16 columns
+    uint32_t yb = 0u;       // the base-2^16 column below the chunk
+    uint32_t cw = 0u;       // carry between the chunks' words
 #pragma unroll 1
     for (int c0 = 0; c0 < kDig; c0 += 16) {
       uint32_t v[16];
@@ -290,17 +295,21 @@ __device__ __forceinline__ void mont_step(uint32_t (&A)[kH], bool sq, uint32_t b
       tc::wait_ld();
       uint32_t y[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        y[j] = pair_cols(v[2 * j], v[2 * j + 1]) + c;
-        c = y[j] >> 16;
-      }
+      for (int j = 0; j < 8; ++j) y[j] = pair_cols(v[2 * j], v[2 * j + 1]);
+      uint32_t w[4];
+      (void)add_cc(cw, 0xFFFFFFFFu);   // carry flag <- cw
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        w[k] = addc_cc(tc::lo_halves(y[2 * k], y[2 * k + 1]), tc::hi_halves(k ? y[2 * k - 1] : yb, y[2 * k]));
+      cw = addc(0u, 0u);
+      yb = y[7];
       const uint32_t ad = ts.arow + (uint32_t)(c0 >> 3) * kKb;
-      // [y.b0, 0, y.b1, 0]: the two bytes of a base-2^16 digit as fp16 digits
-      tc::sts128(ad, tc::prmt(y[0], 0u, 0x4140u), tc::prmt(y[1], 0u, 0x4140u), tc::prmt(y[2], 0u, 0x4140u),
-                 tc::prmt(y[3], 0u, 0x4140u));
-      tc::sts128(ad + kKb, tc::prmt(y[4], 0u, 0x4140u), tc::prmt(y[5], 0u, 0x4140u), tc::prmt(y[6], 0u, 0x4140u),
-                 tc::prmt(y[7], 0u, 0x4140u));
-      mu_top = tc::prmt(y[6], y[7], 0x5410u);   // in the last chunk: digits 124..127
+      // [w.b0, 0, w.b1, 0], [w.b2, 0, w.b3, 0]: a word's bytes as fp16 digits
+      tc::sts128(ad, tc::prmt(w[0], 0u, 0x4140u), tc::prmt(w[0], 0u, 0x4342u), tc::prmt(w[1], 0u, 0x4140u),
+                 tc::prmt(w[1], 0u, 0x4342u));
+      tc::sts128(ad + kKb, tc::prmt(w[2], 0u, 0x4140u), tc::prmt(w[2], 0u, 0x4342u), tc::prmt(w[3], 0u, 0x4140u),
+                 tc::prmt(w[3], 0u, 0x4342u));
+      mu_top = w[3];   // in the last chunk: digits 124..127
     }
   }
   // 4. MMA 2: positions 124..251 of mu * m
@@ -324,30 +333,31 @@ __device__ __forceinline__ void mont_step(uint32_t (&A)[kH], bool sq, uint32_t b
   // 5. U = T_hi + (T_lo + mu*m) / R, then one conditional subtraction.  The
   // columns are carry-propagated 4 at a time into limbs that are added to T_hi
   // right away (the carry between chunks is kept in a register: cin).
-  uint32_t c, cin = 0u;
+  uint32_t yb, cs = 0u, cin = 0u;
   {
     uint32_t v[16];
     tc::ld16(ts.taddr + 0u, v);   // positions 124..139
     tc::wait_ld();
-    // carry out of the low half: ceil of positions 124..127 (with T's top limb) / 2^32
+    // carry out of the low half: ceil of positions 124..127 (with T's top limb)
+    // / 2^32, below 2^16; it enters limb 0 as the high half of the column below
     const uint32_t y0 = pair_cols(v[0], v[1]) + (top & 0xFFFFu);
     const uint32_t y1 = pair_cols(v[2], v[3]) + (top >> 16) + (y0 >> 16);
-    c = (y1 >> 16) + (((y0 | y1) & 0xFFFFu) != 0u ? 1u : 0u);
-    add_columns<3>(t, 0, v + 4, c, cin);              // positions 128..139: limbs 0..2
+    yb = ((y1 >> 16) + (((y0 | y1) & 0xFFFFu) != 0u ? 1u : 0u)) << 16;
+    add_columns<3>(t, 0, v + 4, yb, cs, cin);         // positions 128..139: limbs 0..2
   }
 #pragma unroll
   for (int k = 1; k < 8; ++k) {
     uint32_t v[16];
     tc::ld16(ts.taddr + (uint32_t)(16 * k), v);       // positions 124 + 16k .. +15
     tc::wait_ld();
-    add_columns<4>(t, 3 + 4 * (k - 1), v, c, cin);    // limbs 3 + 4(k-1) .. +3
+    add_columns<4>(t, 3 + 4 * (k - 1), v, yb, cs, cin);   // limbs 3 + 4(k-1) .. +3
   }
   tc::fence_before_sync();   // this tile's TMEM reads precede the next MMA (ordered by the next barrier)
-  add_columns<1>(t, kH - 1, top_cols, c, cin);        // positions 252..255: limb 31
+  add_columns<1>(t, kH - 1, top_cols, yb, cs, cin);   // positions 252..255: limb 31
   uint32_t u[kH + 2];
 #pragma unroll
   for (int j = 0; j < kH; ++j) u[j] = t[j];
-  u[kH] = c + cin;
+  u[kH] = (yb >> 16) + cs + cin;
   u[kH + 1] = 0u;
   final_sub<kH>(A, u, NSmem<kH>{Ms});
 }

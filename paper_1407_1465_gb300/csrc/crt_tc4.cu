@@ -137,30 +137,35 @@ __device__ __forceinline__ bool tile_sync(Tile &ts) {
   return ts.dead;
 }
 
-// X[j0 .. j0+NL) += (4*NL column words v, carried from c in base 2^16) + cin
+// X[j0 .. j0+NL) += the 4*NL column words v taken as 2*NL base-2^16 columns
+// (tc::lo_halves / tc::hi_halves): s = X' + Y' word by word with the carry
+// cs, then X += s with the carry cin.  yb is the column below v[0] (its high
+// half, the pending carry, enters word j0); the last column of v returns in yb.
 template <int NL, int NX>
-__device__ __forceinline__ void add_columns(uint32_t (&X)[NX], int j0, const uint32_t *v, uint32_t &c, uint32_t &cin) {
-  uint32_t Y[NL];
+__device__ __forceinline__ void add_columns(uint32_t (&X)[NX], int j0, const uint32_t *v, uint32_t &yb, uint32_t &cs,
+                                            uint32_t &cin) {
+  uint32_t s[NL];
+  (void)add_cc(cs, 0xFFFFFFFFu);    // carry flag <- cs (0 or 1)
 #pragma unroll
   for (int i = 0; i < NL; ++i) {
-    const uint32_t y0 = tc::pair_cols(v[4 * i], v[4 * i + 1]) + c;
-    c = y0 >> 16;
-    const uint32_t y1 = tc::pair_cols(v[4 * i + 2], v[4 * i + 3]) + c;
-    c = y1 >> 16;
-    Y[i] = tc::prmt(y0, y1, 0x5410u);
+    const uint32_t y0 = tc::pair_cols(v[4 * i], v[4 * i + 1]), y1 = tc::pair_cols(v[4 * i + 2], v[4 * i + 3]);
+    s[i] = addc_cc(tc::lo_halves(y0, y1), tc::hi_halves(yb, y0));
+    yb = y1;
   }
-  (void)add_cc(cin, 0xFFFFFFFFu);
+  cs = addc(0u, 0u);
+  (void)add_cc(cin, 0xFFFFFFFFu);   // carry flag <- cin
 #pragma unroll
-  for (int i = 0; i < NL; ++i) X[j0 + i] = addc_cc(X[j0 + i], Y[i]);
+  for (int i = 0; i < NL; ++i) X[j0 + i] = addc_cc(X[j0 + i], s[i]);
   cin = addc(0u, 0u);
 }
 
-// MMA 1's columns (TMEM columns 0 .. D-1) carried into mu's D digits, written
-// into the tile's A buffer; returns mu's digits D-4 .. D-1.
+// MMA 1's columns (TMEM columns 0 .. D-1) summed into mu's D digits (32-bit
+// words from tc::lo_halves / tc::hi_halves, one carry chain), written into the
+// tile's A buffer; returns mu's digits D-4 .. D-1.
 template <int H>
 __device__ __forceinline__ uint32_t mu_pass(const Tile &ts) {
   using S = Shape<H>;
-  uint32_t mu_top = 0u, c = 0u;
+  uint32_t mu_top = 0u, yb = 0u, cw = 0u;
 #pragma unroll 1
   for (int c0 = 0; c0 < S::D; c0 += 16) {
     uint32_t v[16];
@@ -168,16 +173,20 @@ __device__ __forceinline__ uint32_t mu_pass(const Tile &ts) {
     tc::wait_ld();
     uint32_t y[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      y[j] = tc::pair_cols(v[2 * j], v[2 * j + 1]) + c;
-      c = y[j] >> 16;
-    }
+    for (int j = 0; j < 8; ++j) y[j] = tc::pair_cols(v[2 * j], v[2 * j + 1]);
+    uint32_t w[4];
+    (void)add_cc(cw, 0xFFFFFFFFu);   // carry flag <- cw
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      w[k] = addc_cc(tc::lo_halves(y[2 * k], y[2 * k + 1]), tc::hi_halves(k ? y[2 * k - 1] : yb, y[2 * k]));
+    cw = addc(0u, 0u);
+    yb = y[7];
     const uint32_t ad = ts.arow + (uint32_t)(c0 >> 3) * S::Kb;
-    tc::sts128(ad, tc::prmt(y[0], 0u, 0x4140u), tc::prmt(y[1], 0u, 0x4140u), tc::prmt(y[2], 0u, 0x4140u),
-               tc::prmt(y[3], 0u, 0x4140u));
-    tc::sts128(ad + S::Kb, tc::prmt(y[4], 0u, 0x4140u), tc::prmt(y[5], 0u, 0x4140u), tc::prmt(y[6], 0u, 0x4140u),
-               tc::prmt(y[7], 0u, 0x4140u));
-    mu_top = tc::prmt(y[6], y[7], 0x5410u);   // in the last chunk: digits D-4 .. D-1
+    tc::sts128(ad, tc::prmt(w[0], 0u, 0x4140u), tc::prmt(w[0], 0u, 0x4342u), tc::prmt(w[1], 0u, 0x4140u),
+               tc::prmt(w[1], 0u, 0x4342u));
+    tc::sts128(ad + S::Kb, tc::prmt(w[2], 0u, 0x4140u), tc::prmt(w[2], 0u, 0x4342u), tc::prmt(w[3], 0u, 0x4140u),
+               tc::prmt(w[3], 0u, 0x4342u));
+    mu_top = w[3];   // in the last chunk: digits D-4 .. D-1
   }
   return mu_top;
 }
@@ -211,27 +220,28 @@ __device__ __forceinline__ uint32_t reduce_round(uint32_t (&X)[NX], uint32_t top
   uint32_t tcol[4];
   top_columns(tcol, mu_top, Ms[H - 1]);   // while the tensor core works
   wait_mma(ts, polls);
-  uint32_t c, cin = 0u;
+  uint32_t yb, cs = 0u, cin = 0u;
   {
     uint32_t v[16];
     tc::ld16(ts.taddr + 0u, v);   // positions D-4 .. D+11
     tc::wait_ld();
-    // carry out of the low half: ceil of positions D-4 .. D-1 (with V's limb HR-1) / 2^32
+    // carry out of the low half: ceil of positions D-4 .. D-1 (with V's limb
+    // HR-1) / 2^32, below 2^16; it enters as the high half of the column below
     const uint32_t y0 = tc::pair_cols(v[0], v[1]) + (top & 0xFFFFu);
     const uint32_t y1 = tc::pair_cols(v[2], v[3]) + (top >> 16) + (y0 >> 16);
-    c = (y1 >> 16) + (((y0 | y1) & 0xFFFFu) != 0u ? 1u : 0u);
-    add_columns<3>(X, B0, v + 4, c, cin);                 // positions D .. D+11
+    yb = ((y1 >> 16) + (((y0 | y1) & 0xFFFFu) != 0u ? 1u : 0u)) << 16;
+    add_columns<3>(X, B0, v + 4, yb, cs, cin);            // positions D .. D+11
   }
 #pragma unroll
   for (int k = 1; k < S::N2 / 16; ++k) {
     uint32_t v[16];
     tc::ld16(ts.taddr + (uint32_t)(16 * k), v);           // positions D-4 + 16k .. +15
     tc::wait_ld();
-    add_columns<4>(X, B0 + 3 + 4 * (k - 1), v, c, cin);
+    add_columns<4>(X, B0 + 3 + 4 * (k - 1), v, yb, cs, cin);
   }
   tc::fence_before_sync();   // this tile's TMEM reads precede its next MMA (ordered by the next barrier)
-  add_columns<1>(X, B0 + H - 1, tcol, c, cin);           // positions 3D-4 .. 3D-1
-  return c + cin;
+  add_columns<1>(X, B0 + H - 1, tcol, yb, cs, cin);      // positions 3D-4 .. 3D-1
+  return (yb >> 16) + cs + cin;
 }
 
 // ---------------------------------------------------------------- squaring

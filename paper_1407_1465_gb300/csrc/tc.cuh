@@ -155,9 +155,20 @@ __device__ __forceinline__ uint4 lds128(uint32_t saddr) {
 // Two adjacent MMA output columns (bias 0x3F000000 each, sums w < 2^23) as one
 // base-2^16 column: w_even + 256 w_odd < 2^31.01.  Shifting the odd word up a
 // byte drops its bias (0x3F000000 << 8 = 0 mod 2^32); the even word's bias is
-// its byte 3, cleared by the permute.  Neither depends on a running carry.
+// subtracted.  A shift-add and an add, neither depending on a running carry.
 __device__ __forceinline__ uint32_t pair_cols(uint32_t w_even, uint32_t w_odd) {
-  return prmt(w_even, 0u, 0x4210u) + prmt(w_odd, 0u, 0x2104u);
+  return (w_odd << 8) + (w_even - 0x3F000000u);
+}
+
+// Base-2^16 columns y_j (< 2^32) summed as sum_j y_j 2^(16j) without a
+// 16-bit ripple: with y_j = L_j + 2^16 H_j the sum is X + Y, X the string of
+// the L_j and Y that of the H_j one digit up, so two permutes per pair of
+// columns and one 32-bit add with carry per word.  The low halves of columns
+// 2k, 2k+1 (word k of X):
+__device__ __forceinline__ uint32_t lo_halves(uint32_t y_even, uint32_t y_odd) { return prmt(y_even, y_odd, 0x5410u); }
+// the high halves of columns 2k-1, 2k (word k of Y):
+__device__ __forceinline__ uint32_t hi_halves(uint32_t y_below, uint32_t y_even) {
+  return prmt(y_below, y_even, 0x7632u);
 }
 
 // Limb p of a number as four fp16 byte digits into a K-major core-matrix row:
