@@ -44,18 +44,24 @@ def workload_desc(bits, count, kind="crt"):
     return ("RSA-%d %s: 1 seeded key (two %d-bit primes, Miller-Rabin 40 rounds, e=65537), %d %s uniform "
             "in [0,n) as %d x u32 limbs" % (bits, what, bits // 2, count, items, bits // 32))
 
-# DRAM traffic of the benchmark's kernel from one ncu capture (profiles/
-# crt_kernel_rsa2048_w4_cios_ncu_full.md), valid only while the kernel sources
-# hash to the recorded stamp and the window matches; otherwise reported as null.
+# DRAM traffic of the benchmark's kernel from one ncu capture (the summaries
+# under profiles/ named in "source"), valid only while the kernel sources hash
+# to the recorded stamp and the window matches; otherwise reported as null.
 PROFILED_TRAFFIC = {
     # (workload, variant): one ncu capture of that kernel, valid while its sources hash to the stamp
-    ("rsa2048", 3): {"window": 3, "stamp": "4e131194285a589f", "dram_bytes_per_op": 1160.9,
+    ("rsa2048", 3): {"window": 3, "stamp": "f57c87bf21dadba0", "dram_bytes_per_op": 1141.2,
                      "files": ["crt_tc.cu", "crt_tc.h", "tc.cuh", "mont.cuh", "kernels.cuh", "keyrec.h"],
                      "source": "profiles/crt_tc_half_kernel_rsa2048_w3_ncu_full.md",
                      # what binds the kernel, from the same capture (percent of peak while active)
-                     "pipes": {"issue_active_pct": 52.5, "warps_active_pct": 25.0, "alu_pipe_pct": 50.9,
-                               "fma_pipe_pct": 34.1, "tensor_pipe_pct": 19.2,
-                               "top_stalls": ["wait", "math_pipe_throttle", "not_selected"]}},
+                     "pipes": {"issue_active_pct": 53.4, "warps_active_pct": 25.0, "alu_pipe_pct": 49.7,
+                               "fma_pipe_pct": 36.0, "tensor_pipe_pct": 20.0,
+                               "top_stalls": ["wait", "math_pipe_throttle", "long_scoreboard"]}},
+    ("rsa4096", 3): {"window": 3, "stamp": "3795e62e39c0ef0b", "dram_bytes_per_op": 2502.2,
+                     "files": ["crt_tc4.cu", "crt_tc.h", "tc.cuh", "mont.cuh", "kernels.cuh", "keyrec.h"],
+                     "source": "profiles/crt_tc4_half_kernel_rsa4096_w3_ncu_full.md",
+                     "pipes": {"issue_active_pct": 34.4, "warps_active_pct": 12.5, "alu_pipe_pct": 33.5,
+                               "fma_pipe_pct": 24.7, "tensor_pipe_pct": 11.6,
+                               "top_stalls": ["wait", "no_instruction", "long_scoreboard"]}},
     ("rsa2048", 1): {"window": 4, "stamp": "2c547aada0325644", "dram_bytes_per_op": 257607.0,
                      "files": ["kernels.cuh", "mont.cuh", "inst_unit.cuh", "inst_h32.cu", "keyrec.h"],
                      "source": "profiles/crt_kernel_rsa2048_w4_cios_ncu_full.md"},
@@ -1076,7 +1082,8 @@ def main():
     prods = rsa_products_per_op(spec["bits"], kind, e=e_pub, window=tune["window"])
     cios_achieved = prods * count / (ms / 1e3) / 1e12
     prof = PROFILED_TRAFFIC.get((args.workload, tune["variant"])) if args.kind == "crt" else None
-    prof_valid = bool(prof and prof["window"] == tune["window"] and tune["threads_per_op"] == 1
+    prof_valid = bool(prof and prof["window"] == tune["window"]
+                      and (tune["threads_per_op"] == 1 or tune["variant"] == 3)   # lanes: CUDA-core kernels only
                       and prof["stamp"] == kernel_stamp(prof["files"]))
     traffic = prof["dram_bytes_per_op"] * count if prof_valid else None
     tc_path = tune["variant"] == 3 and args.kind == "crt"

@@ -341,10 +341,12 @@ typedef struct rsa_tuning {
                               return RSA_ERR_UNSUPPORTED from the launching call */
     /* The last three fields apply to RSA_TUNE_RAGGED only (0 elsewhere): */
     int32_t window_big;    /* fixed-window width of 3072/4096-bit CRT (4 or 5; 0 = 5) */
-    int32_t window_tc;     /* window of the tensor-core group (3 or 4; 0 = 3) */
-    int32_t tc_min_ops;    /* a 2048-bit CRT bucket (one key) of at least this many
-                              operations sends its whole 128-operation tiles to the
-                              tensor-core group, up to four tiles of one key per CTA;
+    int32_t window_tc;     /* window of the 2048-bit tensor-core group (3 or 4; 0 = 3);
+                              the 3072- and 4096-bit groups run windows 4 and 3 */
+    int32_t tc_min_ops;    /* a 2048-, 3072- or 4096-bit CRT bucket (one key) of at
+                              least this many operations sends its whole 128-operation
+                              tiles to its size's tensor-core group, up to four tiles
+                              of one key per CTA at 2048 bits, two at 3072/4096;
                               0 = 128 */
 } rsa_tuning;
 
@@ -353,14 +355,14 @@ typedef struct rsa_tuning {
  * addresses rsa_modexp_batch and the request loop: ctas_per_sm caps the resident
  * CTAs per SM of its persistent kernels, threads_per_op picks the lanes per
  * operation of 2048/4096-bit CRT (1: one/four lanes, the throughput shapes; 4:
- * four/eight lanes, the latency shapes; 0: automatic, the latency shapes while
+ * four/sixteen lanes, the latency shapes; 0: automatic, the latency shapes while
  * the work fits one wave of the GPU); window is the CRT window of 1024/2048-bit
  * keys (4 or 5; 0 = 4), window_big that of 3072/4096-bit keys, window_tc and
- * tc_min_ops shape the tensor-core group; variant 3 sends 2048-bit CRT buckets
- * of at least tc_min_ops operations to the tensor-core group, 1 keeps every
- * operation on the CUDA cores, 0 (automatic) uses the group except in the
- * latency shapes; warps_per_cta does not apply.  Errors: RSA_ERR_ARG for values
- * outside these ranges. */
+ * tc_min_ops shape the tensor-core groups; variant 3 sends 2048/3072/4096-bit
+ * CRT buckets of at least tc_min_ops operations to their tensor-core groups, 1
+ * keeps every operation on the CUDA cores, 0 (automatic) uses the groups except
+ * in the latency shapes; warps_per_cta does not apply.  Errors: RSA_ERR_ARG for
+ * values outside these ranges. */
 #define RSA_TUNE_RAGGED 3
 int rsa_set_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, const rsa_tuning *t);
 /* Read the parameters currently in force for (nbits, exp_sel). */
@@ -368,7 +370,7 @@ int rsa_get_tuning(rsa_ctx *ctx, uint32_t nbits, int32_t exp_sel, rsa_tuning *t)
 
 /* Autotuner: time every launch shape (window 3..6 for private kinds, warps
  * per CTA 2/4/8, CTAs per SM 1/2/max, both squaring variants, lanes per operation,
- * and for RSA-2048 CRT the tensor-core path at windows 3 and 4) for key_id's
+ * and for 2048/3072/4096-bit CRT the tensor-core path at windows 3 and 4) for key_id's
  * size and kind exp_sel on a synthetic batch of `count` operations (the work
  * of these kernels does not depend on the message values), install the
  * fastest with rsa_set_tuning() and append it to the cache file `cache_path`
@@ -380,13 +382,21 @@ int rsa_autotune(rsa_ctx *ctx, int32_t key_id, int32_t exp_sel, uint64_t count, 
                  rsa_tuning *best, double *best_ms);
 
 /* Autotuner for ragged batches: times the given batch (the arguments of
- * rsa_modexp_batch, device pointers; out receives its results) under each
- * lanes-per-operation policy (threads_per_op 1 and 4) and resident-CTA cap
- * (ctas_per_sm 0 = occupancy maximum, 2, 4), installs the fastest as the
- * RSA_TUNE_RAGGED tuning and returns it in *best (*best_ms: time per batch,
- * median of three).  Window widths and tiles are fixed per work class.
- * Synchronous, on a private stream.  Errors: RSA_ERR_ARG, RSA_ERR_KEY (the
- * batch holds operations its keys cannot serve), RSA_ERR_NOMEM, RSA_ERR_CUDA. */
+ * rsa_modexp_batch, device pointers; out receives its results) by coordinate
+ * descent over the RSA_TUNE_RAGGED tuning: each field in turn takes each of its
+ * values while the others keep their best so far -- the lanes-per-operation
+ * policy (threads_per_op 1, 4), the tensor-core groups (variant 0 automatic,
+ * 1 off, 3 on), the smallest CRT bucket they take (tc_min_ops 128, 512) and the
+ * 2048-bit group's window (window_tc 3, 4), the CRT windows of 1024/2048-bit
+ * (window 4, 5) and 3072/4096-bit keys (window_big 5, 4), and the resident-CTA
+ * cap of the CUDA-core groups (ctas_per_sm 0 = occupancy maximum, 2, 4).  A
+ * candidate's time is the median of three runs after a warm-up, and its
+ * results must equal the first candidate's (a digest of every output row) or
+ * it is not taken.  Installs the fastest as the RSA_TUNE_RAGGED tuning and
+ * returns it in *best (*best_ms: time per batch).  Synchronous, on a private
+ * stream.  Errors: RSA_ERR_ARG, RSA_ERR_KEY (the batch holds operations its
+ * keys cannot serve), RSA_ERR_NOMEM, RSA_ERR_CUDA (also when candidates
+ * disagree). */
 int rsa_autotune_batch(rsa_ctx *ctx, uint64_t count, const int32_t *key_ids, const uint8_t *exp_sel,
                        const uint64_t *limb_offsets, const uint32_t *msgs, uint32_t *out, rsa_tuning *best,
                        double *best_ms);
