@@ -245,12 +245,19 @@ __device__ __forceinline__ uint32_t reduce_round(uint32_t (&X)[NX], uint32_t top
 }
 
 // ---------------------------------------------------------------- squaring
-// T = A^2 = 2C + D (C: the cross products a_i a_j, i < j, each once; D: the
-// squares a_k^2 at limbs 2k, 2k+1).  Row i adds a_i a_j for j > i in two carry
-// chains (odd and even j - i); after row i the limbs up to 2i+2 of C are
-// final, so T's limbs 2i+1 and 2i+2 are formed (the doubling shifts in the top
-// bit of the limb below) and leave at once, as in the product: limbs below
-// H/2 as digits, H/2 .. H-1 into the high stage, H .. 2H-1 into t.
+// T = A^2 with A = a_lo + a_hi r (r = 2^(32 HR), halves of HR = H/2 limbs):
+// T = a_lo^2 + 2 P r + a_hi^2 r^2, P = a_lo a_hi.  The cross product P runs
+// as a rolled loop of product rows (a_lo read back from the thread's high
+// stage, a_hi in registers); the half squares compute each of their cross
+// products once (row i adds a_i a_j for j > i in two carry chains, odd and
+// even j - i; after row i the limbs up to 2i+2 are final, so the square's
+// limbs 2i+1 and 2i+2 are formed -- the doubling shifts in the top bit of the
+// limb below -- and leave at once).  T's limbs come out in increasing order:
+// 0 .. HR-1 from a_lo^2 alone (digits into the A buffer), HR .. H-1 =
+// a_lo^2's high half + 2 P_lo (high stage), H .. 2H-1 = a_hi^2 + 2 P_hi (t).
+// Word products: HR^2 + 2 HR(HR+1)/2 = H(H+1)/2, as for a square in one
+// piece, in about half the code (the unrolled rows of two HR-limb squares
+// and one rolled row loop, instead of the rows of an H-limb square).
 template <int H, int I, int J0>
 __device__ __forceinline__ void sq_chain(uint32_t (&c)[2 * H], const uint32_t (&a)[H]) {
   if constexpr (J0 < H) {
@@ -266,50 +273,134 @@ __device__ __forceinline__ void sq_chain(uint32_t (&c)[2 * H], const uint32_t (&
   }
 }
 
-template <int H, int P>
-__device__ __forceinline__ void sq_out(uint32_t v, const Tile &ts, uint32_t (&t)[H], uint32_t &top) {
-  using S = Shape<H>;
-  if constexpr (P < S::HR) {
-    tc::emit_digits(ts.arow, P, v, S::Kb);
-    if constexpr (P == S::HR - 1) top = v;
-  } else if constexpr (P < H) {
-    asm volatile("st.shared.u32 [%0], %1;" ::"r"(ts.hrow + (uint32_t)((P - S::HR) >> 2) * kHiG +
-                                                 (uint32_t)((P - S::HR) & 3) * 4u),
-                 "r"(v)
-                 : "memory");
-  } else {
-    t[P - H] = v;
-  }
-}
-
-template <int H, int I>
-__device__ __forceinline__ void sq_rows(uint32_t (&c)[2 * H], const uint32_t (&a)[H], uint32_t (&t)[H], const Tile &ts,
-                                        uint32_t &tc_carry, uint32_t &top) {
-  if constexpr (I < H - 1) {
-    sq_chain<H, I, I + 1>(c, a);
-    sq_chain<H, I, I + 2>(c, a);
+// Rows I .. N-2 of the square of the N-limb a; limb p of the square goes to
+// emit.put<p>() (in increasing p).
+template <int N, int I, class E>
+__device__ __forceinline__ void sq_rows(uint32_t (&c)[2 * N], const uint32_t (&a)[N], uint32_t &tc_carry, E &emit) {
+  if constexpr (I < N - 1) {
+    sq_chain<N, I, I + 1>(c, a);
+    sq_chain<N, I, I + 2>(c, a);
     const uint32_t x0 = __funnelshift_l(c[2 * I], c[2 * I + 1], 1), x1 = __funnelshift_l(c[2 * I + 1], c[2 * I + 2], 1);
     (void)add_cc(tc_carry, 0xFFFFFFFFu);   // carry flag <- tc_carry
     const uint32_t t0 = addc_cc(x0, __umulhi(a[I], a[I]));
     const uint32_t t1 = addc_cc(x1, a[I + 1] * a[I + 1]);
     tc_carry = addc(0u, 0u);
-    sq_out<H, 2 * I + 1>(t0, ts, t, top);
-    sq_out<H, 2 * I + 2>(t1, ts, t, top);
-    sq_rows<H, I + 1>(c, a, t, ts, tc_carry, top);
+    emit.template put<2 * I + 1>(t0);
+    emit.template put<2 * I + 2>(t1);
+    sq_rows<N, I + 1>(c, a, tc_carry, emit);
   }
 }
 
-// T = A^2 into the A buffer, the high stage and t (see above); returns limb H/2-1
+// a^2 for an N-limb a, its 2N limbs handed to emit in increasing order
+template <int N, class E>
+__device__ __forceinline__ void half_square(const uint32_t (&a)[N], E &emit) {
+  uint32_t c[2 * N];
+#pragma unroll
+  for (int j = 0; j < 2 * N; ++j) c[j] = 0u;
+  uint32_t tc_carry = 0u;
+  emit.template put<0>(a[0] * a[0]);
+  sq_rows<N, 0>(c, a, tc_carry, emit);
+  emit.template put<2 * N - 1>(__funnelshift_l(c[2 * N - 2], c[2 * N - 1], 1) + __umulhi(a[N - 1], a[N - 1]) +
+                               tc_carry);
+}
+
+__device__ __forceinline__ uint32_t lds32(uint32_t saddr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(saddr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts32(uint32_t saddr, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;" ::"r"(saddr), "r"(v) : "memory");
+}
+
+// a_lo^2's limbs p: below HR they are T's final limbs (digits; limb HR-1 also
+// in `top`), from HR on they add 2 P_lo (P_lo in the high stage, doubled as it
+// is read: word k of 2P is P_k << 1 with P_(k-1)'s top bit) and replace it
+// there as T's limbs.  `carry` and `pprev` continue into the next emitter.
+template <int H>
+struct LowEmit {
+  const Tile &ts;
+  uint32_t top, carry, pprev;
+  template <int P>
+  __device__ __forceinline__ void put(uint32_t v) {
+    using S = Shape<H>;
+    if constexpr (P < S::HR) {
+      tc::emit_digits(ts.arow, P, v, S::Kb);
+      if constexpr (P == S::HR - 1) top = v;
+    } else {
+      constexpr int k = P - S::HR;
+      const uint32_t ad = ts.hrow + (uint32_t)(k >> 2) * kHiG + (uint32_t)(k & 3) * 4u;
+      const uint32_t pk = lds32(ad);
+      const uint32_t d = __funnelshift_l(pprev, pk, 1);
+      pprev = pk;
+      (void)add_cc(carry, 0xFFFFFFFFu);   // carry flag <- carry
+      const uint32_t w = addc_cc(v, d);
+      carry = addc(0u, 0u);
+      sts32(ad, w);
+    }
+  }
+};
+
+// a_hi^2's limbs p become T's limbs H + p in t: plus 2 P_hi (acc = P_hi; word
+// p of it takes the top bit of the word below, P_lo's last word for p = 0),
+// plus the carry out of the limbs below.
+template <int H>
+struct HighEmit {
+  uint32_t (&t)[H];
+  const uint32_t (&acc)[H / 2];
+  uint32_t carry, plast;
+  template <int P>
+  __device__ __forceinline__ void put(uint32_t v) {
+    constexpr int HR = H / 2;
+    uint32_t d = 0u;
+    if constexpr (P == 0) d = __funnelshift_l(plast, acc[0], 1);
+    else if constexpr (P < HR) d = __funnelshift_l(acc[P - 1], acc[P], 1);
+    else if constexpr (P == HR) d = acc[HR - 1] >> 31;
+    (void)add_cc(carry, 0xFFFFFFFFu);   // carry flag <- carry
+    t[P] = addc_cc(v, d);
+    carry = addc(0u, 0u);
+  }
+};
+
+// T = A^2 into the A buffer (limbs 0 .. HR-1 as digits), the high stage
+// (HR .. H-1) and t (H .. 2H-1); returns limb HR-1.  The high stage is free:
+// a squaring has no B operand.
 template <int H>
 __device__ __forceinline__ uint32_t square(uint32_t (&t)[H], const uint32_t (&a)[H], const Tile &ts) {
-  uint32_t c[2 * H];
+  constexpr int HR = H / 2;
+  static_assert(HR % 4 == 0, "halves of whole limb groups");
+  uint32_t alo[HR], ahi[HR];
 #pragma unroll
-  for (int j = 0; j < 2 * H; ++j) c[j] = 0u;
-  uint32_t tc_carry = 0u, top = 0u;
-  sq_out<H, 0>(a[0] * a[0], ts, t, top);
-  sq_rows<H, 0>(c, a, t, ts, tc_carry, top);
-  t[H - 1] = __funnelshift_l(c[2 * H - 2], c[2 * H - 1], 1) + __umulhi(a[H - 1], a[H - 1]) + tc_carry;
-  return top;
+  for (int j = 0; j < HR; ++j) {
+    alo[j] = a[j];
+    ahi[j] = a[HR + j];
+  }
+  // 1. P = a_lo a_hi: a_lo to the high stage, then rows of four limbs of
+  //    a_lo (read back) times a_hi; each row group's four emitted limbs of P
+  //    replace the four a_lo limbs it read
+#pragma unroll
+  for (int g = 0; g < HR / 4; ++g)
+    tc::sts128(ts.hrow + (uint32_t)g * kHiG, alo[4 * g], alo[4 * g + 1], alo[4 * g + 2], alo[4 * g + 3]);
+  uint32_t acc[HR];
+#pragma unroll
+  for (int j = 0; j < HR; ++j) acc[j] = 0u;
+#pragma unroll 1
+  for (int g = 0; g < HR / 4; ++g) {
+    const uint32_t ad = ts.hrow + (uint32_t)g * kHiG;
+    const uint4 b = tc::lds128(ad);
+    const uint32_t e0 = mul_emit<HR>(acc, ahi, b.x);
+    const uint32_t e1 = mul_emit<HR>(acc, ahi, b.y);
+    const uint32_t e2 = mul_emit<HR>(acc, ahi, b.z);
+    const uint32_t e3 = mul_emit<HR>(acc, ahi, b.w);
+    tc::sts128(ad, e0, e1, e2, e3);
+  }
+  // 2. a_lo^2 with 2 P_lo: T's limbs 0 .. H-1
+  LowEmit<H> lo{ts, 0u, 0u, 0u};
+  half_square<HR>(alo, lo);
+  // 3. a_hi^2 with 2 P_hi and the carry: T's limbs H .. 2H-1 (T < 2^(64H): no carry out)
+  HighEmit<H> hi{t, acc, lo.carry, lo.pprev};
+  half_square<HR>(ahi, hi);
+  return lo.top;
 }
 
 // ---------------------------------------------------------------- one Montgomery step
