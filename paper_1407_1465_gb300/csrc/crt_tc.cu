@@ -171,72 +171,98 @@ __device__ __forceinline__ void wait_mmas(Tile &ts, uint32_t polls) {
   tc::fence_after_sync();
 }
 
-// Cross products of one row of the square, a_i * a_j for j = j0, j0+2, ... < kH
-// (one parity of j), added at positions i+j (low) and i+j+1 (high) as one
-// carry chain; the chain's carry lands on the position after its last high word.
-template <int I, int J0>
-__device__ __forceinline__ void sq_chain(uint32_t (&c)[2 * kH], const uint32_t (&a)[kH]) {
-  if constexpr (J0 < kH) {
-    c[I + J0] = mad_lo_cc(a[I], a[J0], c[I + J0]);
-    c[I + J0 + 1] = madc_hi_cc(a[I], a[J0], c[I + J0 + 1]);
-#pragma unroll
-    for (int j = J0 + 2; j < kH; j += 2) {
-      c[I + j] = madc_lo_cc(a[I], a[j], c[I + j]);
-      c[I + j + 1] = madc_hi_cc(a[I], a[j], c[I + j + 1]);
-    }
-    constexpr int last = J0 + ((kH - 1 - J0) / 2) * 2;
-    c[I + last + 2] = addc(c[I + last + 2], 0u);
-  }
-}
-
-// T limbs p0, p0+1 of T = A^2 = 2C + D (C: cross products, D: the squares
-// a_k^2 at positions 2k, 2k+1); the doubling shifts in the top bit of the limb
-// below, the carry of the T chain is kept in `tc_carry` between rows.
-__device__ __forceinline__ void sq_emit2(uint32_t c_lo, uint32_t c0, uint32_t c1, uint32_t d0, uint32_t d1,
-                                         uint32_t &tc_carry, uint32_t &t0, uint32_t &t1) {
-  const uint32_t x0 = __funnelshift_l(c_lo, c0, 1), x1 = __funnelshift_l(c0, c1, 1);
-  (void)add_cc(tc_carry, 0xFFFFFFFFu);   // carry flag <- tc_carry
-  t0 = addc_cc(x0, d0);
-  t1 = addc_cc(x1, d1);
-  tc_carry = addc(0u, 0u);
-}
-
 __device__ __forceinline__ void emit_digits(uint32_t arow, int p, uint32_t v) { tc::emit_digits(arow, p, v, kKb); }
 
-// T = A^2 for step 1 of the Montgomery product: each cross product once
-// (kH(kH-1)/2 words), doubled, plus the kH squares.  Row i adds a_i * a_j,
-// j > i, in two chains (odd and even j - i); after row i the positions up to
-// 2i+2 are final, so T limbs 2i+1 and 2i+2 are formed and leave: limbs below
-// kH as digits (the thread's A row), the rest into t (= T_hi).  Returns T
-// limb kH-1.
-template <int I>
-__device__ __forceinline__ void sq_rows(uint32_t (&c)[2 * kH], const uint32_t (&a)[kH], uint32_t (&t)[kH],
-                                        uint32_t arow, uint32_t &tc_carry, uint32_t &top) {
-  if constexpr (I < kH - 1) {
-    sq_chain<I, I + 1>(c, a);
-    sq_chain<I, I + 2>(c, a);
-    uint32_t t0, t1;
-    const uint32_t dh = __umulhi(a[I], a[I]), dl = a[I + 1] * a[I + 1];
-    sq_emit2(c[2 * I], c[2 * I + 1], c[2 * I + 2], dh, dl, tc_carry, t0, t1);
-    constexpr int p0 = 2 * I + 1, p1 = 2 * I + 2;
-    if constexpr (p0 < kH) emit_digits(arow, p0, t0); else t[p0 - kH] = t0;
-    if constexpr (p1 < kH) emit_digits(arow, p1, t1); else t[p1 - kH] = t1;
-    if constexpr (p0 == kH - 1) top = t0;
-    if constexpr (p1 == kH - 1) top = t1;
-    sq_rows<I + 1>(c, a, t, arow, tc_carry, top);
-  }
-}
+// T = A^2 for step 1 of the Montgomery product, with A = a_lo + a_hi r (r =
+// 2^(32 HR), halves of HR = kH/2 limbs): T = a_lo^2 + 2 P r + a_hi^2 r^2,
+// P = a_lo a_hi.  P runs as a rolled loop of product rows (a_lo read back
+// from the thread's stage -- free in a squaring -- a_hi in registers); each
+// row group's four limbs of P replace the four limbs of a_lo it read, and P's
+// low half returns to registers before the square's digits overwrite the
+// stage.  The half squares compute each of their cross products once
+// (square_emit), and their limbs take 2P as they leave: T's limbs 0 .. HR-1
+// from a_lo^2 alone, HR .. kH-1 = a_lo^2's high half + 2 P_lo (all digits of
+// the thread's A row), kH .. 2kH-1 = a_hi^2 + 2 P_hi (t).  HR^2 + 2 HR(HR+1)/2
+// = kH(kH+1)/2 word products, in about half the code of a square in one piece.
 
+// a_lo^2's limbs p: T's limbs, plus (from p = HR on) 2 P_lo, whose word k is
+// P_k << 1 with P_(k-1)'s top bit; all leave as digits, limb kH-1 also in top
+struct LowEmit {
+  uint32_t arow;
+  const uint32_t (&plo)[kH / 2];
+  uint32_t top, carry;
+  template <int P>
+  __device__ __forceinline__ void put(uint32_t v) {
+    constexpr int HR = kH / 2;
+    if constexpr (P >= HR) {
+      constexpr int k = P - HR;
+      const uint32_t d = k ? __funnelshift_l(plo[k ? k - 1 : 0], plo[k], 1) : plo[0] << 1;
+      (void)add_cc(carry, 0xFFFFFFFFu);   // carry flag <- carry
+      v = addc_cc(v, d);
+      carry = addc(0u, 0u);
+    }
+    emit_digits(arow, P, v);
+    if constexpr (P == kH - 1) top = v;
+  }
+};
+
+// a_hi^2's limbs p become T's limbs kH + p in t: plus 2 P_hi (acc = P_hi; word
+// p takes the top bit of the word below, P_lo's last for p = 0) and the carry
+struct HighEmit {
+  uint32_t (&t)[kH];
+  const uint32_t (&acc)[kH / 2];
+  uint32_t carry, plast;
+  template <int P>
+  __device__ __forceinline__ void put(uint32_t v) {
+    constexpr int HR = kH / 2;
+    uint32_t d = 0u;
+    if constexpr (P == 0) d = __funnelshift_l(plast, acc[0], 1);
+    else if constexpr (P < HR) d = __funnelshift_l(acc[P - 1], acc[P], 1);
+    else if constexpr (P == HR) d = acc[HR - 1] >> 31;
+    (void)add_cc(carry, 0xFFFFFFFFu);   // carry flag <- carry
+    t[P] = addc_cc(v, d);
+    carry = addc(0u, 0u);
+  }
+};
+
+// Returns T limb kH-1; T_lo leaves as digits into the thread's A row, T_hi in t.
 __device__ __forceinline__ uint32_t square_p(uint32_t (&t)[kH], const uint32_t (&a)[kH], uint32_t arow) {
-  uint32_t c[2 * kH];
+  constexpr int HR = kH / 2;
+  static_assert(HR % 4 == 0, "halves of whole limb groups");
+  uint32_t alo[HR], ahi[HR];
 #pragma unroll
-  for (int j = 0; j < 2 * kH; ++j) c[j] = 0u;
-  uint32_t tc_carry = 0u, top = 0u;
-  emit_digits(arow, 0, a[0] * a[0]);                       // T_0 = lo(a_0^2)
-  sq_rows<0>(c, a, t, arow, tc_carry, top);
-  // T_63 = 2C_63 (+ the bit from C_62) + hi(a_31^2) + carry
-  t[kH - 1] = __funnelshift_l(c[2 * kH - 2], c[2 * kH - 1], 1) + __umulhi(a[kH - 1], a[kH - 1]) + tc_carry;
-  return top;
+  for (int j = 0; j < HR; ++j) {
+    alo[j] = a[j];
+    ahi[j] = a[HR + j];
+  }
+  const uint32_t st0 = arow + (uint32_t)kStageKb * kKb;   // the stage: k-blocks 8.., four raw limbs each
+#pragma unroll
+  for (int g = 0; g < HR / 4; ++g)
+    tc::sts128(st0 + (uint32_t)g * kKb, alo[4 * g], alo[4 * g + 1], alo[4 * g + 2], alo[4 * g + 3]);
+  uint32_t acc[HR];
+#pragma unroll
+  for (int j = 0; j < HR; ++j) acc[j] = 0u;
+#pragma unroll 1
+  for (int g = 0; g < HR / 4; ++g) {
+    const uint32_t ad = st0 + (uint32_t)g * kKb;
+    const uint4 b = tc::lds128(ad);
+    const uint32_t e0 = mul_emit<HR>(acc, ahi, b.x);
+    const uint32_t e1 = mul_emit<HR>(acc, ahi, b.y);
+    const uint32_t e2 = mul_emit<HR>(acc, ahi, b.z);
+    const uint32_t e3 = mul_emit<HR>(acc, ahi, b.w);
+    tc::sts128(ad, e0, e1, e2, e3);
+  }
+  uint32_t plo[HR];
+#pragma unroll
+  for (int g = 0; g < HR / 4; ++g) {
+    const uint4 v = tc::lds128(st0 + (uint32_t)g * kKb);
+    plo[4 * g] = v.x; plo[4 * g + 1] = v.y; plo[4 * g + 2] = v.z; plo[4 * g + 3] = v.w;
+  }
+  LowEmit lo{arow, plo, 0u, 0u};
+  square_emit<HR>(alo, lo);
+  HighEmit hi{t, acc, lo.carry, plo[HR - 1]};
+  square_emit<HR>(ahi, hi);
+  return lo.top;
 }
 
 // A = A * B * R^-1 mod m (A < R, B < m; result < m).  B: kH limbs in shared

@@ -249,61 +249,12 @@ __device__ __forceinline__ uint32_t reduce_round(uint32_t (&X)[NX], uint32_t top
 // T = a_lo^2 + 2 P r + a_hi^2 r^2, P = a_lo a_hi.  The cross product P runs
 // as a rolled loop of product rows (a_lo read back from the thread's high
 // stage, a_hi in registers); the half squares compute each of their cross
-// products once (row i adds a_i a_j for j > i in two carry chains, odd and
-// even j - i; after row i the limbs up to 2i+2 are final, so the square's
-// limbs 2i+1 and 2i+2 are formed -- the doubling shifts in the top bit of the
-// limb below -- and leave at once).  T's limbs come out in increasing order:
+// products once (square_emit).  T's limbs come out in increasing order:
 // 0 .. HR-1 from a_lo^2 alone (digits into the A buffer), HR .. H-1 =
 // a_lo^2's high half + 2 P_lo (high stage), H .. 2H-1 = a_hi^2 + 2 P_hi (t).
 // Word products: HR^2 + 2 HR(HR+1)/2 = H(H+1)/2, as for a square in one
 // piece, in about half the code (the unrolled rows of two HR-limb squares
 // and one rolled row loop, instead of the rows of an H-limb square).
-template <int H, int I, int J0>
-__device__ __forceinline__ void sq_chain(uint32_t (&c)[2 * H], const uint32_t (&a)[H]) {
-  if constexpr (J0 < H) {
-    c[I + J0] = mad_lo_cc(a[I], a[J0], c[I + J0]);
-    c[I + J0 + 1] = madc_hi_cc(a[I], a[J0], c[I + J0 + 1]);
-#pragma unroll
-    for (int j = J0 + 2; j < H; j += 2) {
-      c[I + j] = madc_lo_cc(a[I], a[j], c[I + j]);
-      c[I + j + 1] = madc_hi_cc(a[I], a[j], c[I + j + 1]);
-    }
-    constexpr int last = J0 + ((H - 1 - J0) / 2) * 2;
-    c[I + last + 2] = addc(c[I + last + 2], 0u);
-  }
-}
-
-// Rows I .. N-2 of the square of the N-limb a; limb p of the square goes to
-// emit.put<p>() (in increasing p).
-template <int N, int I, class E>
-__device__ __forceinline__ void sq_rows(uint32_t (&c)[2 * N], const uint32_t (&a)[N], uint32_t &tc_carry, E &emit) {
-  if constexpr (I < N - 1) {
-    sq_chain<N, I, I + 1>(c, a);
-    sq_chain<N, I, I + 2>(c, a);
-    const uint32_t x0 = __funnelshift_l(c[2 * I], c[2 * I + 1], 1), x1 = __funnelshift_l(c[2 * I + 1], c[2 * I + 2], 1);
-    (void)add_cc(tc_carry, 0xFFFFFFFFu);   // carry flag <- tc_carry
-    const uint32_t t0 = addc_cc(x0, __umulhi(a[I], a[I]));
-    const uint32_t t1 = addc_cc(x1, a[I + 1] * a[I + 1]);
-    tc_carry = addc(0u, 0u);
-    emit.template put<2 * I + 1>(t0);
-    emit.template put<2 * I + 2>(t1);
-    sq_rows<N, I + 1>(c, a, tc_carry, emit);
-  }
-}
-
-// a^2 for an N-limb a, its 2N limbs handed to emit in increasing order
-template <int N, class E>
-__device__ __forceinline__ void half_square(const uint32_t (&a)[N], E &emit) {
-  uint32_t c[2 * N];
-#pragma unroll
-  for (int j = 0; j < 2 * N; ++j) c[j] = 0u;
-  uint32_t tc_carry = 0u;
-  emit.template put<0>(a[0] * a[0]);
-  sq_rows<N, 0>(c, a, tc_carry, emit);
-  emit.template put<2 * N - 1>(__funnelshift_l(c[2 * N - 2], c[2 * N - 1], 1) + __umulhi(a[N - 1], a[N - 1]) +
-                               tc_carry);
-}
-
 __device__ __forceinline__ uint32_t lds32(uint32_t saddr) {
   uint32_t v;
   asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(saddr) : "memory");
@@ -396,10 +347,10 @@ __device__ __forceinline__ uint32_t square(uint32_t (&t)[H], const uint32_t (&a)
   }
   // 2. a_lo^2 with 2 P_lo: T's limbs 0 .. H-1
   LowEmit<H> lo{ts, 0u, 0u, 0u};
-  half_square<HR>(alo, lo);
+  square_emit<HR>(alo, lo);
   // 3. a_hi^2 with 2 P_hi and the carry: T's limbs H .. 2H-1 (T < 2^(64H): no carry out)
   HighEmit<H> hi{t, acc, lo.carry, lo.pprev};
-  half_square<HR>(ahi, hi);
+  square_emit<HR>(ahi, hi);
   return lo.top;
 }
 

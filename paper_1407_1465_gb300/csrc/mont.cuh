@@ -599,4 +599,59 @@ __device__ __forceinline__ void from_uniform(uint32_t (&A)[L], const uint4 *s) {
   }
 }
 
+// ---------------------------------------------------------------- squares, each cross product once
+// The square of an N-limb a is T = 2C + D, C the cross products a_i a_j
+// (i < j), D the squares a_k^2 at limbs 2k, 2k+1.  Row I adds a_I a_j for
+// j > I in two carry chains (odd and even j - I); after row I the limbs of C
+// up to 2I+2 are final, so T's limbs 2I+1 and 2I+2 are formed (the doubling
+// shifts in the top bit of the limb below) and handed on at once, which keeps
+// the live part of C short.  N(N+1)/2 word products.
+//
+// One chain of row I: a_I a_j for j = J0, J0+2, ... < H, added at positions
+// I+j (low) and I+j+1 (high); its carry lands after its last high word.
+template <int H, int I, int J0>
+__device__ __forceinline__ void sq_chain(uint32_t (&c)[2 * H], const uint32_t (&a)[H]) {
+  if constexpr (J0 < H) {
+    c[I + J0] = mad_lo_cc(a[I], a[J0], c[I + J0]);
+    c[I + J0 + 1] = madc_hi_cc(a[I], a[J0], c[I + J0 + 1]);
+#pragma unroll
+    for (int j = J0 + 2; j < H; j += 2) {
+      c[I + j] = madc_lo_cc(a[I], a[j], c[I + j]);
+      c[I + j + 1] = madc_hi_cc(a[I], a[j], c[I + j + 1]);
+    }
+    constexpr int last = J0 + ((H - 1 - J0) / 2) * 2;
+    c[I + last + 2] = addc(c[I + last + 2], 0u);
+  }
+}
+
+// Rows I .. N-2; limb p of T goes to emit.put<p>() (in increasing p).
+template <int N, int I, class E>
+__device__ __forceinline__ void sq_rows(uint32_t (&c)[2 * N], const uint32_t (&a)[N], uint32_t &tc_carry, E &emit) {
+  if constexpr (I < N - 1) {
+    sq_chain<N, I, I + 1>(c, a);
+    sq_chain<N, I, I + 2>(c, a);
+    const uint32_t x0 = __funnelshift_l(c[2 * I], c[2 * I + 1], 1), x1 = __funnelshift_l(c[2 * I + 1], c[2 * I + 2], 1);
+    (void)add_cc(tc_carry, 0xFFFFFFFFu);   // carry flag <- tc_carry
+    const uint32_t t0 = addc_cc(x0, __umulhi(a[I], a[I]));
+    const uint32_t t1 = addc_cc(x1, a[I + 1] * a[I + 1]);
+    tc_carry = addc(0u, 0u);
+    emit.template put<2 * I + 1>(t0);
+    emit.template put<2 * I + 2>(t1);
+    sq_rows<N, I + 1>(c, a, tc_carry, emit);
+  }
+}
+
+// T = a^2 for an N-limb a, its 2N limbs handed to emit in increasing order
+template <int N, class E>
+__device__ __forceinline__ void square_emit(const uint32_t (&a)[N], E &emit) {
+  uint32_t c[2 * N];
+#pragma unroll
+  for (int j = 0; j < 2 * N; ++j) c[j] = 0u;
+  uint32_t tc_carry = 0u;
+  emit.template put<0>(a[0] * a[0]);
+  sq_rows<N, 0>(c, a, tc_carry, emit);
+  emit.template put<2 * N - 1>(__funnelshift_l(c[2 * N - 2], c[2 * N - 1], 1) + __umulhi(a[N - 1], a[N - 1]) +
+                               tc_carry);
+}
+
 }  // namespace rsagpu
