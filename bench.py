@@ -49,19 +49,19 @@ def workload_desc(bits, count, kind="crt"):
 # to the recorded stamp and the window matches; otherwise reported as null.
 PROFILED_TRAFFIC = {
     # (workload, variant): one ncu capture of that kernel, valid while its sources hash to the stamp
-    ("rsa2048", 3): {"window": 3, "stamp": "f57c87bf21dadba0", "dram_bytes_per_op": 1141.2,
+    ("rsa2048", 3): {"window": 3, "stamp": "52c545c354cb1ae7", "dram_bytes_per_op": 1147.2,
                      "files": ["crt_tc.cu", "crt_tc.h", "tc.cuh", "mont.cuh", "kernels.cuh", "keyrec.h"],
                      "source": "profiles/crt_tc_half_kernel_rsa2048_w3_ncu_full.md",
                      # what binds the kernel, from the same capture (percent of peak while active)
-                     "pipes": {"issue_active_pct": 53.4, "warps_active_pct": 25.0, "alu_pipe_pct": 49.7,
-                               "fma_pipe_pct": 36.0, "tensor_pipe_pct": 20.0,
+                     "pipes": {"issue_active_pct": 53.8, "warps_active_pct": 25.0, "alu_pipe_pct": 44.6,
+                               "fma_pipe_pct": 38.9, "tensor_pipe_pct": 20.3,
                                "top_stalls": ["wait", "math_pipe_throttle", "long_scoreboard"]}},
-    ("rsa4096", 3): {"window": 3, "stamp": "3795e62e39c0ef0b", "dram_bytes_per_op": 2502.2,
+    ("rsa4096", 3): {"window": 3, "stamp": "4685be0fbc061b74", "dram_bytes_per_op": 2407.9,
                      "files": ["crt_tc4.cu", "crt_tc.h", "tc.cuh", "mont.cuh", "kernels.cuh", "keyrec.h"],
                      "source": "profiles/crt_tc4_half_kernel_rsa4096_w3_ncu_full.md",
-                     "pipes": {"issue_active_pct": 34.4, "warps_active_pct": 12.5, "alu_pipe_pct": 33.5,
-                               "fma_pipe_pct": 24.7, "tensor_pipe_pct": 11.6,
-                               "top_stalls": ["wait", "no_instruction", "long_scoreboard"]}},
+                     "pipes": {"issue_active_pct": 39.1, "warps_active_pct": 12.5, "alu_pipe_pct": 32.4,
+                               "fma_pipe_pct": 31.2, "tensor_pipe_pct": 14.0,
+                               "top_stalls": ["wait", "long_scoreboard", "math_pipe_throttle"]}},
     ("rsa2048", 1): {"window": 4, "stamp": "2c547aada0325644", "dram_bytes_per_op": 257607.0,
                      "files": ["kernels.cuh", "mont.cuh", "inst_unit.cuh", "inst_h32.cu", "keyrec.h"],
                      "source": "profiles/crt_kernel_rsa2048_w4_cios_ncu_full.md"},
