@@ -122,7 +122,8 @@ def alu_roofline(achieved: float, device: int, what: str) -> dict:
     return {"bound": "alu", "achieved": achieved, "peak": pk["chain_tprod"], "unit": "Tprod/s",
             "frac": achieved / pk["chain_tprod"], "peak_source": "measured",
             "peak_note": "rsa_imad_probe in this run on this GPU (%d SMs): carry-chain word products/s of the "
-                         "Montgomery-product shape (mad.lo.cc + madc.hi.cc); independent mad.lo/mad.hi lane-ops "
+                         "kernels' product-scan rows (mad.lo.cc + madc.hi.cc chains, rows overlapping as in the "
+                         "kernels), the faster of two occupancies; independent mad.lo/mad.hi lane-ops "
                          "%.2f T/s; the unit-count figure %.2f T products/s assumes a full-rate high-half multiply"
                          % (pk["sm_count"], pk["imad_lane_tops"], pk["derived_tprod"]),
             "what": what}

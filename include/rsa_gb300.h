@@ -449,7 +449,9 @@ double rsa_products_per_op(uint32_t nbits, int32_t exp_sel, uint32_t e_bits, uin
 /* Integer-multiply throughput probe on `device`: *imad_lanes_per_s receives
  * 32-bit multiply-add lane-operations per second from independent mad.lo/
  * mad.hi chains; *chain_products_per_s the 32x32->64 word products per second
- * of mad.lo.cc / madc.hi.cc carry chains shaped like the modular multiply. */
+ * of mad.lo.cc / madc.hi.cc carry chains shaped like the kernels' product scans
+ * (rows of 32 products whose multipliers do not wait for the previous row's
+ * last carry), the faster of two occupancies. */
 int rsa_imad_probe(int device, double *imad_lanes_per_s, double *chain_products_per_s);
 
 #ifdef __cplusplus

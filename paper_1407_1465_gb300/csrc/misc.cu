@@ -84,23 +84,28 @@ __global__ void imad_probe_kernel(uint32_t *sink, uint32_t iters, uint32_t seed)
   if (x == 0x9e3779b9u) sink[blockIdx.x * blockDim.x + threadIdx.x] = x;
 }
 
-// Carry chains shaped like the modular multiply: per step, t[0..33] += b * a[0..31]
-// with the even/odd mad.lo.cc / madc.hi.cc chains of mul_acc (32 word products).
+// Carry chains as the kernels' product scans run them: per step one row,
+// t[0..31] += b * a[0..31] with the even/odd mad.lo.cc / madc.hi.cc chains of
+// mul_emit (32 word products), the lowest limb leaving.  The next row's
+// multiplier is formed from that limb, the row's first result, so consecutive
+// rows overlap as they do when the multipliers come from shared memory (a
+// multiplier taken from the row's last carry would serialise the rows and
+// understate the rate the kernels can reach).
 __global__ void chain_probe_kernel(uint32_t *sink, uint32_t iters, uint32_t seed) {
-  uint32_t a[32], t[34];
+  uint32_t a[32], t[32];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) a[j] = seed * (j + 1) + threadIdx.x;
-#pragma unroll
-  for (int j = 0; j < 34; ++j) t[j] = 0u;
-  uint32_t b = seed | 1u;
-  for (uint32_t it = 0; it < iters; ++it) {
-    mul_acc<32>(t, a, b);
-    b = t[33] ^ t[0] ^ b;  // keep b data dependent so nothing is hoisted
-    t[33] = 0u;
+  for (int j = 0; j < 32; ++j) {
+    a[j] = seed * (j + 1) + threadIdx.x;
+    t[j] = 0u;
   }
-  uint32_t x = 0;
+  uint32_t b = seed | 1u, x = 0u;
+  for (uint32_t it = 0; it < iters; ++it) {
+    const uint32_t out = mul_emit<32>(t, a, b);
+    x ^= out;
+    b = out + it;   // data dependent, so nothing is hoisted
+  }
 #pragma unroll
-  for (int j = 0; j < 34; ++j) x ^= t[j];
+  for (int j = 0; j < 32; ++j) x ^= t[j];
   if (x == 0x9e3779b9u) sink[blockIdx.x * blockDim.x + threadIdx.x] = x;
 }
 

@@ -759,30 +759,39 @@ int rsa_imad_probe(int device, double *imad_lanes_per_s, double *chain_products_
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  auto run = [&](const void *fn, uint32_t iters, float *ms) -> cudaError_t {
+  auto run = [&](const void *fn, uint32_t iters, int nblocks, int nthreads, float *ms) -> cudaError_t {
     uint32_t seed = 12345u;
     void *args[] = {&sink, &iters, &seed};
-    cudaError_t r = cudaLaunchKernel(fn, dim3(blocks), dim3(threads), args, 0, nullptr);  // warm-up
+    cudaError_t r = cudaLaunchKernel(fn, dim3(nblocks), dim3(nthreads), args, 0, nullptr);  // warm-up
     if (r != cudaSuccess) return r;
     cudaEventRecord(a);
-    r = cudaLaunchKernel(fn, dim3(blocks), dim3(threads), args, 0, nullptr);
+    r = cudaLaunchKernel(fn, dim3(nblocks), dim3(nthreads), args, 0, nullptr);
     if (r != cudaSuccess) return r;
     cudaEventRecord(b);
     r = cudaEventSynchronize(b);
     cudaEventElapsedTime(ms, a, b);
     return r;
   };
-  float ms1 = 0, ms2 = 0;
+  float ms1 = 0;
   const uint32_t it1 = 20000, it2 = 4000;
-  e = run(imad_probe_fn(), it1, &ms1);
-  if (e == cudaSuccess) e = run(chain_probe_fn(), it2, &ms2);
+  e = run(imad_probe_fn(), it1, blocks, threads, &ms1);
+  // the carry-chain rows at two occupancies (as many CTAs of 256 threads as
+  // fit; 16 warps per SM), the faster counts
+  double chain = 0.0;
+  const int shapes[2][2] = {{blocks, threads}, {sms, 512}};
+  for (const auto &sh : shapes) {
+    if (e != cudaSuccess) break;
+    float ms2 = 0;
+    e = run(chain_probe_fn(), it2, sh[0], sh[1], &ms2);
+    if (e == cudaSuccess) chain = std::max(chain, (double)sh[0] * sh[1] * it2 * 32.0 / (ms2 * 1e-3));
+  }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   cudaFree(sink);
   if (e != cudaSuccess) return cuda_error(e, "probe kernel");
   const double thr = (double)threads * blocks;
   if (imad_lanes_per_s) *imad_lanes_per_s = thr * it1 * 16.0 / (ms1 * 1e-3);
-  if (chain_products_per_s) *chain_products_per_s = thr * it2 * 32.0 / (ms2 * 1e-3);
+  if (chain_products_per_s) *chain_products_per_s = chain;
   return RSA_OK;
 }
 
