@@ -621,11 +621,12 @@ def ragged_measure(steps: int, warmup: int, autotune: bool = False, loop_steps: 
 def ragged_work(rb, tuning: dict) -> dict:
     """Per-step work of the ragged batch as its kernels issue it.  A CRT bucket
     of one 2048-, 3072- or 4096-bit key with at least tc_min_ops operations
-    sends floor(count / 128) whole tiles to its tensor-core group (2048 bits at
-    the tuned tensor-core window, 3072 at window 4, 4096 at window 3); those
-    operations issue the CUDA-core word products and MMA FLOPs of the
-    tensor-core path, every other operation the CIOS count 2L^2 + L per
-    Montgomery product (window 5 for private exponents)."""
+    sends all of them to its tensor-core group (tiles of 128, the last possibly
+    partial; 2048 bits at the tuned tensor-core window, 3072 at window 4, 4096
+    at window 3); those operations issue the CUDA-core word products and MMA
+    FLOPs of the tensor-core path, every other operation the CIOS count
+    2L^2 + L per Montgomery product (window 5 for private exponents).  Rows
+    past a partial tile's operations compute too and are not counted."""
     from paper_1407_1465_gb300 import rsa_products_per_op
     buckets = {}
     for k, sel in zip(rb.key_ids, rb.exp_sel):
@@ -637,7 +638,7 @@ def ragged_work(rb, tuning: dict) -> dict:
         key = rb.keys[k]
         nt = 0
         if tc_on and sel == 1 and key.bits in (2048, 3072, 4096) and c >= tuning.get("tc_min_ops", 128):
-            nt = c // 128 * 128
+            nt = c
         if nt:
             if key.bits == 2048:
                 w = tc_work_per_op(2048, tuning.get("window_tc") or 3)

@@ -344,10 +344,10 @@ typedef struct rsa_tuning {
     int32_t window_tc;     /* window of the 2048-bit tensor-core group (3 or 4; 0 = 3);
                               the 3072- and 4096-bit groups run windows 4 and 3 */
     int32_t tc_min_ops;    /* a 2048-, 3072- or 4096-bit CRT bucket (one key) of at
-                              least this many operations sends its whole 128-operation
-                              tiles to its size's tensor-core group, up to four tiles
-                              of one key per CTA at 2048 bits, two at 3072/4096;
-                              0 = 128 */
+                              least this many operations runs on its size's tensor-core
+                              group, in tiles of 128 operations (the last one possibly
+                              partial), up to four tiles of one key per CTA at 2048
+                              bits, two at 3072/4096; 0 = 128 */
 } rsa_tuning;
 
 /* Set (or, with NULL, reset to automatic) the launch parameters used for keys of

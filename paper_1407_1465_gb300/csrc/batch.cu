@@ -109,8 +109,8 @@ __global__ void __launch_bounds__(1024) plan_tiles(BatchDesc d) {
       }
       group = g;
     }
-    // a bucket's whole tensor-core tiles (if any) take its first operations;
-    // the CUDA-core tiles cover the rest
+    // a bucket's tensor-core tiles (if any) take all its operations, else the
+    // CUDA-core tiles do
     uint32_t my_ops = 0, my_tiles = 0;
     for (uint32_t b = b0; b < b1; ++b) {
       const uint32_t c = d.bcount[b];
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(1024) plan_tiles(BatchDesc d) {
       const int32_t cls = batch_class(d.dir[b / 3].L, (int)(b % 3), d.wide_crt32);
       if (d.class_rank[cls] != rank) continue;
       const uint32_t to = (uint32_t)batch_tile_ops(cls);
-      const uint32_t rest = c - batch_tc_tiles(d, cls, d.dir[b / 3], c) * (uint32_t)tcr::kRows;
+      const uint32_t rest = c - batch_tc_ops(d, cls, d.dir[b / 3], c);
       my_ops += c;
       my_tiles += (rest + to - 1) / to;
     }
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(1024) plan_tiles(BatchDesc d) {
       if (d.class_rank[cls] != rank) continue;
       const uint32_t to = (uint32_t)batch_tile_ops(cls);
       d.boff[b] = op_off;
-      const uint32_t skip = batch_tc_tiles(d, cls, d.dir[b / 3], c) * (uint32_t)tcr::kRows;
+      const uint32_t skip = batch_tc_ops(d, cls, d.dir[b / 3], c);
       const uint32_t rest = c - skip;
       const uint32_t nt = (rest + to - 1) / to;
       for (uint32_t j = 0; j < nt && tile_off + j < d.max_tiles; ++j)
@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(1024) plan_tiles(BatchDesc d) {
         if (!c) continue;
         const int32_t cls = batch_class(d.dir[b / 3].L, (int)(b % 3), d.wide_crt32);
         if (batch_tc_group(cls) != grp) continue;
-        my_chunks += (batch_tc_tiles(d, cls, d.dir[b / 3], c) + per - 1) / per;
+        const uint32_t nt = (batch_tc_ops(d, cls, d.dir[b / 3], c) + tcr::kRows - 1) / tcr::kRows;
+        my_chunks += (nt + per - 1) / per;
       }
       uint32_t tot_chunks;
       uint32_t ch = block_exclusive_scan(my_chunks, &tot_chunks, sh);
@@ -169,10 +170,12 @@ __global__ void __launch_bounds__(1024) plan_tiles(BatchDesc d) {
         const KeyDirEntry e = d.dir[b / 3];
         const int32_t cls = batch_class(e.L, (int)(b % 3), d.wide_crt32);
         if (batch_tc_group(cls) != grp) continue;
-        const uint32_t nt = batch_tc_tiles(d, cls, e, c);
+        const uint32_t nops = batch_tc_ops(d, cls, e, c);
+        const uint32_t nt = (nops + tcr::kRows - 1) / tcr::kRows;
         for (uint32_t t0 = 0; t0 < nt; t0 += per, ++ch)
           if (ch < d.max_tc_chunks)
-            list[ch] = tcr::TcChunk{e.rec, e.tc, (int32_t)(d.boff[b] + t0 * tcr::kRows), (int32_t)min(per, nt - t0)};
+            list[ch] = tcr::TcChunk{e.rec, e.tc, (int32_t)(d.boff[b] + t0 * tcr::kRows), (int32_t)min(per, nt - t0),
+                                    (int32_t)min(per * tcr::kRows, nops - t0 * tcr::kRows), 0};
       }
       if (threadIdx.x == 0) d.ctl[batch_tc_ctl_word(grp)] = min(tot_chunks, d.max_tc_chunks);
     }
@@ -255,6 +258,12 @@ double class_cost(int32_t cls) {
 
 // the tensor-core chunk lists (TCG_COUNT of them) follow the tile descriptors in the same buffer
 static size_t tc_chunks_offset(uint64_t max_tiles) { return ((size_t)max_tiles * sizeof(TileDesc) + 255) / 256 * 256; }
+// Chunks one tensor-core group can have in a batch of `count` operations: a
+// bucket of c >= tc_min_ops operations makes at most ceil(c / 128) <= c / 128 + 1
+// chunks, and there are at most count / tc_min_ops such buckets.
+static uint64_t tc_chunk_cap(uint64_t count, int tc_min_ops) {
+  return count / tcr::kRows + count / (uint64_t)std::max(tc_min_ops, 1) + 1;
+}
 // the 3072- and 4096-bit tensor-core groups: prime limbs and window (GB300:
 // window 4 at 3072 bits, 3 at 4096, as for uniform batches)
 static constexpr int kTcxH[2] = {48, 64};
@@ -387,13 +396,14 @@ int Ctx::prepare_batch(cudaStream_t s, uint64_t max_count) {
   }
   const uint32_t nb = std::max<uint32_t>(nkeys, 1) * 3;
   const uint64_t max_tiles = max_count / kMinTileOps + nb + 1;   // tiles of at least kMinTileOps operations
+  const Tune tr = tune_for(0, RSA_TUNE_RAGGED);
+  const uint64_t chunk_cap = tc_chunk_cap(max_count, tr.tc_min_ops);
   int rc;
   if ((rc = ensure(w.aux0, (size_t)max_count * 8)) ||                  // op_bucket + sorted
       (rc = ensure(w.aux1, (size_t)nb * 12)) ||                        // bcount, bfill, boff
-      (rc = ensure(w.aux2, tc_chunks_offset(max_tiles) + TCG_COUNT * (max_count / tcr::kRows + 1) * sizeof(tcr::TcChunk))) ||
+      (rc = ensure(w.aux2, tc_chunks_offset(max_tiles) + TCG_COUNT * chunk_cap * sizeof(tcr::TcChunk))) ||
       (rc = ensure(w.aux3, tcr::kCtlWords * 4)))
     return rc;
-  const Tune tr = tune_for(0, RSA_TUNE_RAGGED);
   const bool tc_possible = tr.variant != 1;
   if (tc_possible) {
     // the tensor-core groups: one CTA per SM, the whole shared memory of an SM
@@ -498,7 +508,7 @@ int Ctx::run_batch(uint64_t count, const int32_t *key_ids, const uint8_t *exp_se
   d.tables = static_cast<uint4 *>(w.tables.ptr);
   d.max_tiles = max_tiles;
   d.tc_chunks = reinterpret_cast<tcr::TcChunk *>(static_cast<char *>(w.aux2.ptr) + tc_chunks_offset(max_tiles));
-  d.max_tc_chunks = (uint32_t)(count / tcr::kRows + 1);
+  d.max_tc_chunks = (uint32_t)tc_chunk_cap(count, tune_for(0, RSA_TUNE_RAGGED).tc_min_ops);
   d.tcx_chunks[0] = d.tc_chunks + d.max_tc_chunks;
   d.tcx_chunks[1] = d.tc_chunks + 2 * d.max_tc_chunks;
   // Small batches run 2048-bit CRT with four lanes per operation and 4096-bit

@@ -52,9 +52,9 @@ enum : int32_t {
 // exponents always use kBatchWindowPlain.
 constexpr int kBatchWindowSmall = 4, kBatchWindowBig = 5, kBatchWindowMax = 5;
 constexpr int kBatchWindowPlain = 4;
-// the tensor-core group: window 3 (tables stay in L2) or 4; a 2048-bit CRT
-// bucket sends its whole 128-operation tiles there once it holds at least
-// kBatchTcMinOps operations (the rest run on the CUDA cores)
+// the tensor-core groups: window 3 (tables stay in L2) or 4 at 2048 bits; a
+// 2048/3072/4096-bit CRT bucket runs there, in tiles of 128 operations, once
+// it holds at least kBatchTcMinOps operations (smaller ones on the CUDA cores)
 constexpr int kBatchWindowTc = 3;
 constexpr uint32_t kBatchTcMinOps = 128;
 
@@ -148,9 +148,9 @@ struct BatchDesc {
   int32_t class_rank[CLS_COUNT];  // position of each class in the longest-first order
   uint32_t wide_crt32;        // small batch: 2048/4096-bit CRT as CLS_CRT32W / CLS_CRT64W (2: CLS_CRT64X)
   int32_t win_small, win_big; // CRT windows of 1024/2048-bit and of 3072/4096-bit keys (4 or 5)
-  // tensor-core group: 2048-bit CRT buckets of at least tc_min_ops operations
-  // (0: none) send floor(count / 128) whole tiles there, in chunks of up to
-  // tcr::kTiles tiles of one key; max_tc_chunks bounds the chunk list
+  // tensor-core groups: CRT buckets of at least tc_min_ops operations (0:
+  // none) run there in ceil(count / 128) tiles, in chunks of up to
+  // batch_tc_chunk_tiles tiles of one key; max_tc_chunks bounds each chunk list
   uint32_t tc_min_ops, max_tc_chunks;
   tcr::TcChunk *tc_chunks;    // 2048-bit CRT chunks (up to tcr::kTiles tiles each)
   tcr::TcChunk *tcx_chunks[2];  // 3072- and 4096-bit CRT chunks (up to tc4::kTiles tiles each)
@@ -170,10 +170,12 @@ __host__ __device__ inline int32_t batch_tc_group(int32_t cls) {
 }
 static_assert(tcr::kCtlTcChunks + 2 * TCG_COUNT <= 30, "control words");
 
-// whole tensor-core tiles a bucket of c operations sends to its tensor-core group
-__host__ __device__ inline uint32_t batch_tc_tiles(const BatchDesc &d, int32_t cls, const KeyDirEntry &e, uint32_t c) {
+// operations a bucket of c sends to its tensor-core group: all of them (in
+// ceil(c / 128) tiles, the last one possibly partial) once c reaches
+// tc_min_ops, else none
+__host__ __device__ inline uint32_t batch_tc_ops(const BatchDesc &d, int32_t cls, const KeyDirEntry &e, uint32_t c) {
   if (batch_tc_group(cls) < 0 || d.tc_min_ops == 0 || e.tc == nullptr || c < d.tc_min_ops) return 0u;
-  return c / (uint32_t)tcr::kRows;
+  return c;
 }
 
 const void *batch_exec_fn(int group);

@@ -36,16 +36,20 @@ size_t tc_halves_bytes(uint32_t count);
 int tc_grid(uint32_t count, int sm_count);
 size_t tc_smem_bytes();
 
-// Ragged batches: the tensor-core group takes whole 128-operation tiles of
-// 2048-bit CRT buckets, grouped into chunks of up to kTiles tiles of one key
-// (one CTA runs a chunk's tiles side by side, one prime at a time).  The
-// planner writes the chunk list; the operations of a chunk are the entries
-// op_start .. op_start + 128 * ntiles - 1 of the batch's sorted operation list.
+// Ragged batches: the tensor-core group takes the 128-operation tiles of
+// CRT buckets, grouped into chunks of up to kTiles tiles of one key (one CTA
+// runs a chunk's tiles side by side, one prime at a time).  The planner writes
+// the chunk list; the operations of a chunk are the entries op_start ..
+// op_start + nops - 1 of the batch's sorted operation list, 128 per tile, the
+// last tile of a bucket possibly partial (its rows past nops compute on the
+// chunk's first operation and store nothing).
 struct TcChunk {
   const uint32_t *keyrec;   // device key record (keyrec.h)
   const void *image;        // the key's tensor-core operands (q image, then p image)
   int32_t op_start;         // first position in the sorted list
-  int32_t ntiles;           // 1 .. kTiles full tiles
+  int32_t ntiles;           // 1 .. kTiles tiles
+  int32_t nops;             // operations: 128 (ntiles - 1) < nops <= 128 ntiles
+  int32_t pad_;
 };
 // control words of the ragged tensor-core group inside the batch's control
 // block (words 0-15: the planner's ranges and counters, 30-31: the ragged

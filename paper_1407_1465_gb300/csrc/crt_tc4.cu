@@ -680,16 +680,22 @@ __device__ __forceinline__ void half_body(const HalfArgs &a, const tcr::RaggedTc
       __syncthreads();
       tc::fence_after_sync();
       if (slot < ch.ntiles) {
-        const uint32_t pos = (uint32_t)ch.op_start + (uint32_t)slot * kRows + (uint32_t)r;
+        // rows past the chunk's operations (a bucket's partial last tile)
+        // compute on its first operation and store nothing
+        const uint32_t row = (uint32_t)slot * kRows + (uint32_t)r;
+        const bool valid = row < (uint32_t)ch.nops;
+        const uint32_t pos = (uint32_t)ch.op_start + (valid ? row : 0u);
         const uint32_t op = (uint32_t)ra.sorted[pos];
         const uint32_t *msg = ra.msgs + ra.offsets[op];
         uint32_t A[H];
         if (!ts.dead) exp_tile<H, W>(A, ts, smem, msg, pi, kc, tbl, ra.wait_polls);
-        uint4 *h = halves + (size_t)pi * (H / 4) * cpad + pos;
+        if (valid) {
+          uint4 *h = halves + (size_t)pi * (H / 4) * cpad + pos;
 #pragma unroll
-        for (int g = 0; g < H / 4; ++g)
-          h[(size_t)g * cpad] = make_uint4(A[4 * g], A[4 * g + 1], A[4 * g + 2], A[4 * g + 3]);
-        herr[(size_t)pi * ra.count + pos] = (ts.err || ts.dead) ? 1u : 0u;
+          for (int g = 0; g < H / 4; ++g)
+            h[(size_t)g * cpad] = make_uint4(A[4 * g], A[4 * g + 1], A[4 * g + 2], A[4 * g + 3]);
+          herr[(size_t)pi * ra.count + pos] = (ts.err || ts.dead) ? 1u : 0u;
+        }
       }
     }
   }
@@ -831,7 +837,9 @@ __global__ void __launch_bounds__(kGThreads) crt_tc4_ragged_garner_kernel(tcr::R
     __syncthreads();                // the previous tile's key record is no longer read
     load_key_record<H>(gsm, ch.keyrec);
     __syncthreads();
-    const uint32_t pos = (uint32_t)ch.op_start + (uint32_t)s * kRows + threadIdx.x;
+    const uint32_t row = (uint32_t)s * kRows + threadIdx.x;
+    if (row >= (uint32_t)ch.nops) continue;   // past a partial last tile; rejoins at the next tile's barrier
+    const uint32_t pos = (uint32_t)ch.op_start + row;
     const uint32_t op = (uint32_t)ra.sorted[pos];
     const size_t off = (size_t)ra.offsets[op];
     const bool timed_out = herr[pos] != 0u || herr[ra.count + pos] != 0u;

@@ -130,7 +130,7 @@ Tune Ctx::tune_for(uint32_t nbits, int kind) const {
   // one lane otherwise (RSA-2048 CRT: 1.24 M/s on one lane, 1.10 M on two).
   if (kind == RSA_TUNE_RAGGED) {
     // ragged batches: CRT windows 4 (1024/2048-bit) and 5 (3072/4096-bit),
-    // tensor-core group at window 3 for buckets of at least one whole tile;
+    // tensor-core groups (2048 bits at window 3) for buckets of at least 128 operations;
     // the lanes-per-operation policy and the variant stay automatic (0)
     if (!t.window) t.window = 4;
     if (!t.window_big) t.window_big = 5;

@@ -168,11 +168,11 @@ def test_tc4_work_per_op_matches_the_step_loop(W, bits):
     assert bench.tc4_work_per_op(W, bits) == _tc4_walk(W, bits)
 
 
-def test_ragged_work_routes_whole_crt_tiles_to_the_tensor_core_count(monkeypatch):
-    """Whole 128-operation tiles of 2048/3072/4096-bit CRT buckets at or above
-    the threshold count the tensor-core path's work; the remainders, public
-    operations, 1024-bit keys, buckets below the threshold and everything with
-    the group off (variant 1) count the CIOS products."""
+def test_ragged_work_routes_crt_buckets_to_the_tensor_core_count(monkeypatch):
+    """2048/3072/4096-bit CRT buckets at or above the threshold count the
+    tensor-core path's work for all their operations; public operations,
+    1024-bit keys, buckets below the threshold and everything with the groups
+    off (variant 1) count the CIOS products."""
     import types
     import paper_1407_1465_gb300 as pkg
     monkeypatch.setattr(pkg, "rsa_products_per_op", lambda bits, sel, e=65537, window=5: 1000.0 * bits + sel)
@@ -189,10 +189,10 @@ def test_ragged_work_routes_whole_crt_tiles_to_the_tensor_core_count(monkeypatch
         assert w["tc_ops"] == 0 and w["products_per_step"] == cios and w["tc_method_flops_per_step"] == 0
     w = bench.ragged_work(rb, {"variant": 0, "tc_min_ops": 128, "window_tc": 4})
     t2, t3, t4 = bench.tc_work_per_op(2048, 4), bench.tc4_work_per_op(4, 3072), bench.tc4_work_per_op(3, 4096)
-    assert w["tc_ops"] == 256 + 128 + 256
-    want = cios - 256 * (2048e3 + 1) - 128 * (3072e3 + 1) - 256 * (4096e3 + 1) + 256 * t2[0] + 128 * t3[0] + 256 * t4[0]
+    assert w["tc_ops"] == 300 + 129 + 256
+    want = cios - 300 * (2048e3 + 1) - 129 * (3072e3 + 1) - 256 * (4096e3 + 1) + 300 * t2[0] + 129 * t3[0] + 256 * t4[0]
     assert w["products_per_step"] == want
-    assert w["tc_method_flops_per_step"] == 256 * t2[2] + 128 * t3[2] + 256 * t4[2]
-    assert w["tc_issued_flops_per_step"] == 256 * t2[1] + 128 * t3[1] + 256 * t4[1]
+    assert w["tc_method_flops_per_step"] == 300 * t2[2] + 129 * t3[2] + 256 * t4[2]
+    assert w["tc_issued_flops_per_step"] == 300 * t2[1] + 129 * t3[1] + 256 * t4[1]
     # no bucket reaches a 512-operation threshold
     assert bench.ragged_work(rb, {"variant": 0, "tc_min_ops": 512, "window_tc": 3})["tc_ops"] == 0

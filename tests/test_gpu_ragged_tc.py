@@ -1,15 +1,16 @@
 """Ragged batches with the tensor-core groups (2048-, 3072- and 4096-bit CRT on
 tcgen05 MMAs).
 
-A CRT bucket (one key) of at least tc_min_ops operations sends its whole
-128-operation tiles to its size's tensor-core group, up to four tiles of one key
-per CTA at 2048 bits and two at 3072/4096 bits; the rest of the bucket runs on
-the CUDA cores.  The mix here has a 2048-bit bucket of five tiles plus a
-remainder (two chunks: four tiles and one), one of exactly two tiles, one below
-a tile, a 3072-bit bucket of two tiles and a remainder, a 4096-bit bucket of
-three tiles and a remainder (two chunks), public operations on the same keys
-and 1024-bit CRT, shuffled; edge messages and out-of-range messages sit inside
-tensor-core tiles.  Every result is compared with the oracle, and with the same
+A CRT bucket (one key) of at least tc_min_ops operations sends all its
+operations to its size's tensor-core group, in tiles of 128 (the last one
+possibly partial), up to four tiles of one key per CTA at 2048 bits and two at
+3072/4096 bits; smaller buckets run on the CUDA cores.  The mix here has a
+2048-bit bucket of five tiles plus 37 operations (two chunks: four tiles, then
+one whole and one partial), one of exactly two tiles, one below a tile, a
+3072-bit bucket of two tiles plus 10, a 4096-bit bucket of three tiles plus 5
+(two chunks, the second ending in a partial tile), public operations on the
+same keys and 1024-bit CRT, shuffled; edge messages and out-of-range messages
+sit inside tensor-core tiles.  Every result is compared with the oracle, and with the same
 batch run with the group off and with a 512-operation threshold.  The bounded
 MMA waits of the group report RSA_ERR_TIMEOUT when their poll budget is zero.
 """
@@ -23,6 +24,10 @@ pytestmark = pytest.mark.gpu
 
 PUB, CRT = 0, 1
 RSA_ERR_RANGE, RSA_ERR_TIMEOUT = -3, -6
+# (key index, kind, count) over the keys 2048 x 3, 1024, 3072, 4096: 5 tiles + 37, exactly 2 tiles, 100
+# (below a tile); 3072: 2 tiles + 10; 4096: 3 tiles + 5
+PLAN = [(0, CRT, 5 * 128 + 37), (1, CRT, 2 * 128), (2, CRT, 100), (0, PUB, 40), (1, PUB, 25), (3, CRT, 90),
+        (4, CRT, 2 * 128 + 10), (5, CRT, 3 * 128 + 5), (5, PUB, 12)]
 
 
 @pytest.fixture(scope="module")
@@ -47,12 +52,8 @@ def mix(ctx):
     keys = workloads.gen_keys([(2048, 0), (2048, 1), (2048, 2), (1024, 0), (3072, 0), (4096, 0)],
                               workloads.DEFAULT_SEED)
     kids = [ctx.keyload(k.bits, k.n, k.e, k.d, k.p, k.q) for k in keys]
-    # (key index, kind, count): 5 tiles + 37, exactly 2 tiles, 100 (below a tile); 3072: 2 tiles + 10;
-    # 4096: 3 tiles + 5
-    plan = [(0, CRT, 5 * 128 + 37), (1, CRT, 2 * 128), (2, CRT, 100), (0, PUB, 40), (1, PUB, 25), (3, CRT, 90),
-            (4, CRT, 2 * 128 + 10), (5, CRT, 3 * 128 + 5), (5, PUB, 12)]
     ops = []
-    for k, kind, n in plan:
+    for k, kind, n in PLAN:
         key = keys[k]
         rows = workloads.messages_below(key.n, n, 3, ("tc-mix", k, kind))
         if k in (0, 4, 5) and kind == CRT:
@@ -138,8 +139,10 @@ def test_ragged_tensor_core_wait_timeout(torch_cuda, ctx, mix, monkeypatch):
         monkeypatch.delenv("RSAGPU_TC_WAIT_POLLS")
         assert rc == RSA_ERR_TIMEOUT
         timed = st == RSA_ERR_TIMEOUT
-        # the tensor-core tiles: 5 + 2 of the 2048-bit buckets, 2 of the 3072-bit one, 3 of the 4096-bit one
-        assert timed.sum() == 12 * 128
+        # every operation of the CRT buckets of at least 128 at 2048/3072/4096 bits ran on the tensor cores
+        on_tc = sum(n for k, kind, n in PLAN if kind == CRT and keys[k].bits >= 2048 and n >= 128)
+        assert on_tc == (5 * 128 + 37) + 2 * 128 + (2 * 128 + 10) + (3 * 128 + 5)
+        assert timed.sum() == on_tc
         for i, ((k, kind, row), off) in enumerate(zip(ops, offsets)):
             got = out[int(off):int(off) + row.size]
             if timed[i]:
