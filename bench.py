@@ -183,6 +183,34 @@ def tc4_work_per_op(window: int, bits: int = 4096):
     return issued, issued_flops, method_flops
 
 
+def pub_tc_work_per_op(e: int, H: int = 64):
+    """CUDA-core word products and tensor-core FLOPs of one RSA-2048 public-
+    exponent operation on the tensor-core path (n of H = 64 limbs, two
+    reduction rounds of 2^1024 per Montgomery product, as for an RSA-4096
+    prime): x R with R^2, e_bits - 1 squarings (H(H+1)/2 word products each),
+    popcount(e) - 1 multiplications by x R and the product by 1 that leaves
+    Montgomery form (H^2 each), and per Montgomery product the MMAs of
+    tc4_work_per_op.  Returns (issued word products, issued MMA FLOPs, method
+    MMA FLOPs)."""
+    D = 2 * H
+    squares = e.bit_length() - 1
+    others = 2 + bin(e).count("1") - 1
+    steps = squares + others
+    issued = squares * (H * (H + 1) // 2) + others * H * H
+    ks = D // 16 + 1
+    issued_flops = steps * 2 * (ks * 2 * 16 * D + ks * 2 * 16 * 2 * D)
+    mma1 = D * (D + 1) // 2
+    mma2 = sum(min(j, D - 1) - max(0, j - (2 * D - 1)) + 1 for j in range(D - 4, 3 * D - 4))
+    return issued, issued_flops, steps * 2 * 2 * (mma1 + mma2)
+
+
+def pub_tc_taken(bits: int, e: int, count: int, variant: int) -> bool:
+    """Whether rsa_modexp_key runs a public exponent on the tensor cores:
+    2048-bit keys, variant 3, or automatically (variant 0) for exponents up to
+    64 bits in batches of at least 4096 operations."""
+    return bits == 2048 and (variant == 3 or (variant == 0 and e.bit_length() <= 64 and count >= 4096))
+
+
 def measured_bf16_tflops():
     """Burst dense bf16 TFLOP/s from MEASURED_PEAKS.json (fp16 runs at the same
     rate), else the fallback figure for GB300."""
@@ -1088,15 +1116,19 @@ def main():
                       and (tune["threads_per_op"] == 1 or tune["variant"] == 3)   # lanes: CUDA-core kernels only
                       and prof["stamp"] == kernel_stamp(prof["files"]))
     traffic = prof["dram_bytes_per_op"] * count if prof_valid else None
-    tc_path = tune["variant"] == 3 and args.kind == "crt"
+    pub_tc = args.kind == "public" and pub_tc_taken(spec["bits"], e_pub, count, tune["variant"])
+    tc_path = (tune["variant"] == 3 and args.kind == "crt") or pub_tc
     if tc_path:
-        issued, tflops_op, method_flops_op = (tc4_work_per_op(tune["window"], spec["bits"])
-                                              if spec["bits"] in (3072, 4096)
-                                              else tc_work_per_op(spec["bits"], tune["window"]))
+        if pub_tc:
+            issued, tflops_op, method_flops_op = pub_tc_work_per_op(e_pub)
+        else:
+            issued, tflops_op, method_flops_op = (tc4_work_per_op(tune["window"], spec["bits"])
+                                                  if spec["bits"] in (3072, 4096)
+                                                  else tc_work_per_op(spec["bits"], tune["window"]))
         roofline = alu_roofline(issued * count / (ms / 1e3) / 1e12, local,
                                 "32x32->64 word products the CUDA cores issue per second (per-message products "
-                                "A*B and squarings, the Garner step); the Montgomery reductions run on the tensor "
-                                "cores and are reported under `tensor`")
+                                "A*B and squarings%s); the Montgomery reductions run on the tensor cores and are "
+                                "reported under `tensor`" % ("" if pub_tc else ", the Garner step"))
         roofline["issued_products_per_op"] = issued
         tpk, tsrc = measured_bf16_tflops()
         t_method = method_flops_op * count / (ms / 1e3) / 1e12
@@ -1147,7 +1179,8 @@ def main():
         # RSA-2048 encryption, the paper's toy key, RSA-4096 CRT over windows 4-6
         enc = single_key_rate(2048, 65536, "public", steps=5, warmup=2)
         line["encrypt"] = dict(enc, unit="encryptions/s", what="RSA-2048 encryption (e = 65537, binary method, "
-                               "Fig. 5): the benchmark key's 65536 messages, one rsa_modexp_key per step")
+                               "Fig. 5, the Montgomery reductions mod n on the tensor cores in two rounds of 2^1024): "
+                               "the benchmark key's 65536 messages, one rsa_modexp_key per step")
         line["toy"] = dict(toy_rate(), what="the paper's toy key n = 17947, e = 131, d = 137 (Sec. 2): 4096 "
                            "packets in [0, 2525] encrypted then decrypted per step; launch-latency bound")
         # RSA-4096 CRT: the default path (Montgomery reductions on the tensor cores, w = 3) and the

@@ -333,7 +333,12 @@ typedef struct rsa_tuning {
                               12288 (window 3), 1 otherwise.  For RSA_EXP_PUBLIC (moduli up to 2048
                               bits): 1 = binary method (Fig. 5), 2 = sliding windows
                               of up to `window` bits (Fig. 7; window 4..6, default 5),
-                              0 = sliding for exponents longer than 64 bits */
+                              3 = 2048-bit keys: binary method with the Montgomery
+                              reductions mod n on the tensor cores (two rounds of 2^1024,
+                              as for an RSA-4096 prime; status RSA_ERR_TIMEOUT if a
+                              bounded MMA wait gives up), 0 = automatic: 3 for 2048-bit
+                              keys, exponents up to 64 bits and at least 4096 operations,
+                              else sliding for exponents longer than 64 bits */
     int32_t threads_per_op; /* lanes cooperating on one operation: 1, 2 or 4 (numbers
                               sliced over the lanes, warp-shuffle carries); 0 = automatic
                               (4 above 2048 bits, else 1).  PRIVATE_PLAIN takes 1 up to

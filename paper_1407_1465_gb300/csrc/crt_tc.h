@@ -119,6 +119,14 @@ int tc4_grid(uint32_t count, int sm_count);
 cudaError_t launch_crt_tc4(int H, const uint32_t *keyrec, const void *image, const uint32_t *msgs, uint32_t *out,
                            int32_t *status, uint32_t count, int grid, int window, void *tables, void *halves,
                            uint32_t wait_polls, cudaStream_t s);
+// the public exponent of 2048-bit keys: x^e mod n with n's operands (build_tc4_image(n, kPubH));
+// rows of kPubH limbs; status -3 for x >= n (result zeroed), -6 when a bounded MMA wait gave up
+constexpr int kPubH = 64;
+int pub_tc4_grid(uint32_t count, int sm_count);
+size_t pub_tc4_tables_bytes(int grid);
+cudaError_t launch_pub_tc4(const uint32_t *keyrec, const void *image, const uint32_t *msgs, uint32_t *out,
+                           int32_t *status, uint32_t count, int grid, void *tables, uint32_t wait_polls,
+                           cudaStream_t s);
 // kernel entry points for the ragged batch graph (tcr::RaggedTcArgs, chunks of up to kTiles tiles)
 const void *ragged_tc4_half_fn(int H, int window);
 const void *ragged_tc4_garner_fn(int H);

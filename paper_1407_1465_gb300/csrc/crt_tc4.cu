@@ -717,6 +717,146 @@ __global__ void __launch_bounds__(kThreads, 1) crt_tc4_ragged_half_kernel(tcr::R
   half_body<H, W, true>(HalfArgs{}, ra);
 }
 
+// ---------------------------------------------------------------- public exponent of 2048-bit keys
+// C = M^e mod n for a 2048-bit n: the modulus has the shape of an RSA-4096
+// prime (H = 64 limbs), so every Montgomery product mod n (R = 2^2048) runs
+// the same two reduction rounds on the tensor cores.  e is the key's public
+// exponent, the same for every operation and not secret: left-to-right binary
+// method (Fig. 5) over its bits below the top one.  One CTA per SM, the key's
+// n operands loaded once; tiles round-robin over the CTAs' two slots.
+struct PubArgs {
+  const uint32_t *keyrec;   // the key record (an L = H-limb key)
+  const uint4 *image;       // n's two B operands (build_tc4_image)
+  const uint32_t *msgs;     // count rows of H limbs
+  uint32_t *out;            // count rows of H limbs
+  int32_t *status;          // per operation (may be null)
+  uint4 *tables;            // [grid * kTiles][H/4][kRows]: the multiplier x R per tile slot
+  uint32_t count, ntiles, wait_polls;
+};
+
+// key constants of n (Km: n, Kr2: R^2 mod n, Kone: R mod n, Kunit: 1, Kexp: e)
+// and its two B operands into shared memory
+template <int H>
+__device__ __forceinline__ void load_modulus(uint8_t *smem, const uint32_t *keyrec, const uint4 *image, int tid) {
+  using S = Shape<H>;
+  constexpr KeyLayout lay(H);
+  uint32_t *kc = reinterpret_cast<uint32_t *>(smem + S::OffKey);
+  for (int i = tid; i < S::KeyWords; i += kThreads) {
+    uint32_t v;
+    if (i < S::Kr2) v = keyrec[lay.n + i];
+    else if (i < S::Kr3) v = keyrec[lay.r2n + i - S::Kr2];
+    else if (i < S::Kone) v = 0u;
+    else if (i < S::Kunit) v = keyrec[lay.onen + i - S::Kone];
+    else if (i < S::Kexp) v = (i == S::Kunit) ? 1u : 0u;
+    else v = keyrec[lay.e + i - S::Kexp];
+    kc[i] = v;
+  }
+  constexpr int img_u4 = (S::ImgB1 + S::ImgB2) / 16;
+  uint4 *s4 = reinterpret_cast<uint4 *>(smem + S::OffB1);
+  for (int i = tid; i < img_u4; i += kThreads) s4[i] = image[i];
+}
+
+// One tile: A = x^e mod n for the thread's row x (< n checked by the caller).
+// The multiplier x R waits in the slot's table entry and is staged before each
+// multiplication (a product's digits overwrite the stage).
+template <int H>
+__device__ __forceinline__ void pub_exp_tile(uint32_t (&A)[H], Tile &ts, uint8_t *smem, const uint32_t *msg,
+                                             const uint32_t *kc, uint4 *tbl, uint32_t ebits, uint32_t polls) {
+  using S = Shape<H>;
+  const uint32_t *Ms = kc + S::Km;
+  const uint32_t *E = kc + S::Kexp;
+  const uint32_t kca = ts.sb + S::OffKey;
+  const uint32_t slo = ts.arow + S::StageKb * S::Kb, shi = ts.hrow;
+  load_row<H>(A, msg, true);
+  // x R mod n = x * R^2 * R^-1
+  mont_step<H>(A, false, kca + 4 * S::Kr2, 16, kca + 4 * S::Kr2 + 16 * (S::HR / 4), 16, ts, Ms, polls);
+  if (ts.dead) return;
+  tbl_store<H>(tbl, 0, A);
+#pragma unroll 1
+  for (int bit = (int)ebits - 2; bit >= 0; --bit) {
+    mont_step<H>(A, true, slo, S::Kb, shi, kHiG, ts, Ms, polls);
+    if (ts.dead) return;
+    if ((E[bit >> 5] >> (bit & 31)) & 1u) {   // uniform over the tile: the key's exponent
+      stage_from_table<H>(smem, ts, tbl);
+      mont_step<H>(A, false, slo, S::Kb, shi, kHiG, ts, Ms, polls);
+      if (ts.dead) return;
+    }
+  }
+  // leave Montgomery form: A * 1 * R^-1
+  mont_step<H>(A, false, kca + 4 * S::Kunit, 16, kca + 4 * S::Kunit + 16 * (S::HR / 4), 16, ts, Ms, polls);
+}
+
+template <int H>
+__global__ void __launch_bounds__(kThreads, 1) pub_tc4_kernel(PubArgs a) {
+  using S = Shape<H>;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int slot = warp >> 2;
+  const int r = ((warp & 3) << 5) | lane;
+  const uint32_t sb = tc::smem_addr(smem);
+  uint32_t *ctrl = reinterpret_cast<uint32_t *>(smem + S::OffCtrl);
+  if (warp == 0) tc::tmem_alloc(sb + S::OffCtrl + 48, kTmemCols);
+  if (tid == 0) {
+    for (int t = 0; t < kTiles; ++t) tc::mbar_init(sb + S::OffCtrl + 8 * t, 1u);
+    tc::mbar_init_fence();
+  }
+  const uint32_t *kc = reinterpret_cast<const uint32_t *>(smem + S::OffKey);
+  load_modulus<H>(smem, a.keyrec, a.image, tid);
+  {
+    uint4 *ab = reinterpret_cast<uint4 *>(smem + S::OffAbias);
+    for (int i = tid; i < kRows * 16 * 2 / 16; i += kThreads)
+      ab[i] = make_uint4(0x01000100u, 0x01000100u, 0x01000100u, 0x01000100u);
+  }
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+
+  Tile ts;
+  ts.sb = sb;
+  ts.abuf = sb + S::OffA + slot * S::ABytes;
+  ts.arow = ts.abuf + (uint32_t)(r >> 3) * 128 + (uint32_t)(r & 7) * 16;
+  ts.hrow = sb + S::OffHi + slot * S::HiBytes + (uint32_t)r * 16;
+  ts.tmem = ctrl[12] + (uint32_t)slot * S::TileCols;
+  ts.taddr = ts.tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  ts.mbar = sb + S::OffCtrl + 8 * slot;
+  ts.phase = 0u;
+  ts.pending = 2u;
+  ts.bar_id = 1 + slot;
+  ts.leader = (r == 0);
+  ts.err = false;
+  ts.dead = false;
+  uint4 *tbl = a.tables + (size_t)(blockIdx.x * kTiles + slot) * (H / 4) * kRows + r;
+  constexpr KeyLayout lay(H);
+  const uint32_t ebits = reinterpret_cast<const KeyHeader *>(a.keyrec)->e_bits;
+  for (uint32_t tile = blockIdx.x + gridDim.x * (uint32_t)slot; tile < a.ntiles; tile += gridDim.x * kTiles) {
+    const uint32_t row = tile * kRows + (uint32_t)r;
+    const bool valid = row < a.count;
+    const uint32_t *msg = a.msgs + (size_t)(valid ? row : a.count - 1) * H;
+    uint32_t A[H];
+    if (!ts.dead) pub_exp_tile<H>(A, ts, smem, msg, kc, tbl, ebits, a.wait_polls);
+    if (valid) {
+      const bool below = row_below(msg, a.keyrec + lay.n, H);
+      const bool timed_out = ts.err || ts.dead;
+      const bool ok = below && !timed_out;
+      uint4 *orow = reinterpret_cast<uint4 *>(a.out + (size_t)row * H);
+#pragma unroll
+      for (int g = 0; g < H / 4; ++g)
+        orow[g] = ok ? make_uint4(A[4 * g], A[4 * g + 1], A[4 * g + 2], A[4 * g + 3]) : make_uint4(0u, 0u, 0u, 0u);
+      if (a.status) a.status[row] = timed_out ? -6 /* RSA_ERR_TIMEOUT */ : (below ? 0 : -3 /* RSA_ERR_RANGE */);
+    }
+  }
+  // a tile that gave up may still have an MMA in flight: wait for it (bounded)
+  // before freeing TMEM
+  if (ts.leader && ts.pending < 2u) (void)tc::mbar_wait(ts.mbar, ts.pending, kWaitLimit);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(ctrl[12], kTmemCols);
+  }
+}
+
 // ---------------------------------------------------------------- Garner recombination
 // m = m_q + q * ((m_p - m_q) * qinv mod p), one thread per operation (CIOS
 // Montgomery products of mont.cuh, modulus p from shared memory).
@@ -928,6 +1068,27 @@ const void *ragged_tc4_garner_fn(int H) {
   if (H == 64) return reinterpret_cast<const void *>(&crt_tc4_ragged_garner_kernel<64>);
   return nullptr;
 }
+// ---- public exponent of 2048-bit keys
+int pub_tc4_grid(uint32_t count, int sm_count) {
+  const uint32_t ntiles = (count + kRows - 1) / kRows;
+  const uint32_t want = (ntiles + kTiles - 1) / kTiles;
+  const uint32_t cap = (uint32_t)(sm_count > 0 ? sm_count : 1);
+  return (int)(want < 1u ? 1u : (want < cap ? want : cap));
+}
+size_t pub_tc4_tables_bytes(int grid) { return (size_t)grid * kTiles * (kPubH / 4) * kRows * 16; }
+cudaError_t launch_pub_tc4(const uint32_t *keyrec, const void *image, const uint32_t *msgs, uint32_t *out,
+                           int32_t *status, uint32_t count, int grid, void *tables, uint32_t wait_polls,
+                           cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  PubArgs a{keyrec, static_cast<const uint4 *>(image), msgs, out, status, static_cast<uint4 *>(tables), count,
+            (count + kRows - 1) / kRows, wait_polls};
+  const int smem = Shape<kPubH>::Smem;
+  cudaError_t e = cudaFuncSetAttribute(pub_tc4_kernel<kPubH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  pub_tc4_kernel<kPubH><<<grid, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 size_t tc4_smem_bytes(int H) { return H == 48 ? (size_t)Shape<48>::Smem : (size_t)Shape<64>::Smem; }
 size_t ragged_tc4_garner_smem(int H) {
   return H == 48 ? (size_t)GarnerSmem<48>::Bytes : (size_t)GarnerSmem<64>::Bytes;

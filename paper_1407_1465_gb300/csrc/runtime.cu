@@ -76,6 +76,7 @@ Ctx::~Ctx() {
   for (auto &k : keys) {
     if (k.d_rec) cudaFree(k.d_rec);
     if (k.d_tc) cudaFree(k.d_tc);
+    if (k.d_tcn) cudaFree(k.d_tcn);
   }
   for (auto &kv : workspaces) kv.second.free_all();
   free_extra();
@@ -97,6 +98,8 @@ void Workspace::free_all() {
 // RSA-4096 CRT: 128 K/s, 127 K/s, 118 K/s).
 // Public exponents longer than this use sliding windows (variant 0).
 constexpr uint32_t kSlideMinBits = 64;
+// the public exponent of 2048-bit keys goes to the tensor cores from this many operations
+constexpr uint64_t kPubTcMinCount = 4096;
 // Smallest RSA-3072 / RSA-4096 CRT batch the automatic tuning sends to the
 // tensor cores (where the CUDA-core kernel's time reaches one tensor-core
 // launch's: GB300, 285 K/s against ~33 ms, 149 K/s against ~83 ms).
@@ -209,6 +212,28 @@ int Ctx::run_key(const KeySlot &k, int kind, uint64_t count, const uint32_t *msg
       t.variant = 0;
       t.tpo = 4;
       if (it == tuning.end() || it->second.window == 0) t.window = 5;
+    }
+  }
+  // The public exponent of 2048-bit keys on the tensor cores (crt_tc4.cu): n has
+  // the shape of an RSA-4096 prime, so each Montgomery product mod n runs the
+  // same two reduction rounds.  variant 3 asks for it; automatically it takes
+  // exponents up to kSlideMinBits bits (the binary method) in batches of at
+  // least kPubTcMinCount operations.
+  if (kind == RSA_EXP_PUBLIC && L == (uint32_t)tc4::kPubH && k.d_tcn) {
+    const uint32_t e_bits = k.host_rec.size() > 7 ? k.host_rec[7] : 0u;
+    if (t.variant == 3 || (t.variant == 0 && t.tpo <= 1 && e_bits <= kSlideMinBits && count >= kPubTcMinCount)) {
+      if (count > 0xFFFFFFFFull) return set_error(RSA_ERR_ARG, "count out of range");
+      const int grid = tc4::pub_tc4_grid((uint32_t)count, sm_count);
+      int rc = ensure(w.tables, tc4::pub_tc4_tables_bytes(grid));
+      if (rc) return rc;
+      uint32_t polls = tcr::kDefaultWaitPolls;
+      if (const char *ev = std::getenv("RSAGPU_TC_WAIT_POLLS")) polls = (uint32_t)std::strtoul(ev, nullptr, 10);
+      e = tc4::launch_pub_tc4(k.d_rec, k.d_tcn, msgs, out, status, (uint32_t)count, grid, w.tables.ptr, polls, s);
+      if (e != cudaSuccess) return cuda_error(e, "launch pub_tc4 kernel");
+      stats.kernel_launches += 1;
+      last_grid = grid;
+      last_threads = tc4::kThreads;
+      return RSA_OK;
     }
   }
   if (kind == RSA_EXP_PRIVATE_CRT && t.variant == 3 && tc4::supported((int)L / 2)) {
@@ -544,6 +569,36 @@ int rsa_keyload(rsa_ctx *ctx, uint32_t nbits, const uint32_t *n, const uint32_t 
       return rc2;
     }
   }
+  // n's two-round tensor-core operands: the public exponent of 2048-bit keys
+  void *dtcn = nullptr;
+  size_t tcn_bytes = 0;
+  if (L == (uint32_t)tc4::kPubH) {
+    const KeyLayout lay(L);
+    std::vector<uint8_t> img(tc4::img_prime_bytes(tc4::kPubH));
+    int rc3 = tc4::build_tc4_image(rec.data() + lay.n, tc4::kPubH, img.data()) ? c->reserve(img.size())
+                                                                              : set_error(RSA_ERR_KEY, "n must be odd");
+    if (rc3 == RSA_OK) {
+      if (cudaMalloc(&dtcn, img.size()) == cudaSuccess &&
+          cudaMemcpy(dtcn, img.data(), img.size(), cudaMemcpyHostToDevice) == cudaSuccess) {
+        tcn_bytes = img.size();
+      } else {
+        if (dtcn) cudaFree(dtcn);
+        dtcn = nullptr;
+        cudaGetLastError();
+        c->release(img.size());
+        rc3 = set_error(RSA_ERR_NOMEM, "device allocation of the tensor-core operands failed");
+      }
+    }
+    if (rc3 != RSA_OK) {
+      if (dtc) {
+        cudaFree(dtc);
+        c->release(tc_bytes);
+      }
+      cudaFree(dptr);
+      c->release(bytes);
+      return rc3;
+    }
+  }
   int32_t id = -1;
   for (size_t i = 0; i < c->keys.size(); ++i)
     if (!c->keys[i].used) {
@@ -564,6 +619,8 @@ int rsa_keyload(rsa_ctx *ctx, uint32_t nbits, const uint32_t *n, const uint32_t 
   k.host_rec = rec;
   k.d_tc = dtc;
   k.tc_bytes = tc_bytes;
+  k.d_tcn = dtcn;
+  k.tcn_bytes = tcn_bytes;
   c->key_epoch++;
   *key_id_out = id;
   return RSA_OK;
@@ -583,6 +640,10 @@ int rsa_keyunload(rsa_ctx *ctx, int32_t key_id) {
   if (k.d_tc) {
     cudaFree(k.d_tc);
     c->release(k.tc_bytes);
+  }
+  if (k.d_tcn) {
+    cudaFree(k.d_tcn);
+    c->release(k.tcn_bytes);
   }
   k = KeySlot();
   c->key_epoch++;

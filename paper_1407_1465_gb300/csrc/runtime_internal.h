@@ -52,6 +52,8 @@ struct KeySlot {
   std::vector<uint32_t> host_rec; // host copy of the record
   void *d_tc = nullptr;           // tensor-core operand images (2048-bit keys with p, q)
   size_t tc_bytes = 0;
+  void *d_tcn = nullptr;          // n's two-round tensor-core operands (2048-bit keys: public exponent)
+  size_t tcn_bytes = 0;
 };
 
 struct Tune {

@@ -196,3 +196,35 @@ def test_ragged_work_routes_crt_buckets_to_the_tensor_core_count(monkeypatch):
     assert w["tc_issued_flops_per_step"] == 300 * t2[1] + 129 * t3[1] + 256 * t4[1]
     # no bucket reaches a 512-operation threshold
     assert bench.ragged_work(rb, {"variant": 0, "tc_min_ops": 512, "window_tc": 3})["tc_ops"] == 0
+
+
+def _pub_tc_walk(e, H=64):
+    """The RSA-2048 public exponent on the tensor cores, replaying the
+    kernel's steps: x R (a general product), for each bit of e below the top
+    one a squaring and, for a 1 bit, a product by x R, then the product by 1;
+    per step two reduction rounds of MMA 1 (N = D) and MMA 2 (N = 2D) over
+    D/16 + 1 K-steps, the method's part by enumerating digit pairs."""
+    D = 2 * H
+    pairs1 = sum(1 for n in range(D) for k in range(D) if 0 <= n - k < D)
+    pairs2 = sum(1 for j in range(D - 4, 3 * D - 4) for i in range(D) if 0 <= j - i < 2 * D)
+    steps = [False]                                  # x R
+    for bit in range(e.bit_length() - 2, -1, -1):
+        steps.append(True)
+        if (e >> bit) & 1:
+            steps.append(False)
+    steps.append(False)                              # leave Montgomery form
+    prods = sum(H * (H + 1) // 2 if sq else H * H for sq in steps)
+    flops = len(steps) * 2 * (2 * D * (16 * (D // 16 + 1)) + 2 * 2 * D * (16 * (D // 16 + 1)))
+    method = len(steps) * 2 * 2 * (pairs1 + pairs2)
+    return prods, flops, method
+
+
+@pytest.mark.parametrize("e", [3, 65537, (1 << 100) + 12345, (1 << 2047) + 3])
+def test_pub_tc_work_per_op_matches_the_step_loop(e):
+    assert bench.pub_tc_work_per_op(e) == _pub_tc_walk(e)
+
+
+def test_pub_tc_taken_mirrors_the_library_rule():
+    assert bench.pub_tc_taken(2048, 65537, 4096, 0) and not bench.pub_tc_taken(2048, 65537, 4095, 0)
+    assert bench.pub_tc_taken(2048, (1 << 200) + 1, 10, 3) and not bench.pub_tc_taken(2048, (1 << 200) + 1, 65536, 0)
+    assert not bench.pub_tc_taken(4096, 65537, 65536, 0) and not bench.pub_tc_taken(2048, 65537, 65536, 1)
