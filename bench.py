@@ -49,19 +49,31 @@ def workload_desc(bits, count, kind="crt"):
 # to the recorded stamp and the window matches; otherwise reported as null.
 PROFILED_TRAFFIC = {
     # (workload, variant): one ncu capture of that kernel, valid while its sources hash to the stamp
-    ("rsa2048", 3): {"window": 3, "stamp": "52c545c354cb1ae7", "dram_bytes_per_op": 1147.2,
+    ("rsa2048", 3): {"window": 3, "stamp": "3ae443c6c031c681", "dram_bytes_per_op": 1159.3,
                      "files": ["crt_tc.cu", "crt_tc.h", "tc.cuh", "mont.cuh", "kernels.cuh", "keyrec.h"],
                      "source": "profiles/crt_tc_half_kernel_rsa2048_w3_ncu_full.md",
                      # what binds the kernel, from the same capture (percent of peak while active)
                      "pipes": {"issue_active_pct": 53.8, "warps_active_pct": 25.0, "alu_pipe_pct": 44.6,
                                "fma_pipe_pct": 38.9, "tensor_pipe_pct": 20.3,
-                               "top_stalls": ["wait", "math_pipe_throttle", "long_scoreboard"]}},
-    ("rsa4096", 3): {"window": 3, "stamp": "4685be0fbc061b74", "dram_bytes_per_op": 2407.9,
+                               "top_stalls": ["wait", "math_pipe_throttle", "long_scoreboard"],
+                               "reading": "latency and issue: no pipe saturated; 16 warps per SM (TMEM holds four "
+                                          "128-column tiles), fixed-latency carry-chain waits"}},
+    ("rsa4096", 3): {"window": 3, "stamp": "ff78cad136b25d9d", "dram_bytes_per_op": 2405.4,
                      "files": ["crt_tc4.cu", "crt_tc.h", "tc.cuh", "mont.cuh", "kernels.cuh", "keyrec.h"],
                      "source": "profiles/crt_tc4_half_kernel_rsa4096_w3_ncu_full.md",
                      "pipes": {"issue_active_pct": 39.1, "warps_active_pct": 12.5, "alu_pipe_pct": 32.4,
                                "fma_pipe_pct": 31.2, "tensor_pipe_pct": 14.0,
-                               "top_stalls": ["wait", "long_scoreboard", "math_pipe_throttle"]}},
+                               "top_stalls": ["wait", "long_scoreboard", "math_pipe_throttle"],
+                               "reading": "latency: 8 warps per SM (two tiles of 256 TMEM columns, 255 "
+                                          "registers), carry-chain waits poorly hidden"}},
+    ("rsa2048", "public-tc"): {"window": None, "stamp": "ff78cad136b25d9d", "dram_bytes_per_op": 262.0,
+                               "files": ["crt_tc4.cu", "crt_tc.h", "tc.cuh", "mont.cuh", "kernels.cuh", "keyrec.h"],
+                               "source": "profiles/pub_tc4_kernel_rsa2048_e65537_ncu_full.md",
+                               "pipes": {"issue_active_pct": 33.2, "warps_active_pct": 12.5, "alu_pipe_pct": 24.1,
+                                         "fma_pipe_pct": 28.0, "tensor_pipe_pct": 12.3,
+                                         "top_stalls": ["wait", "barrier", "long_scoreboard"],
+                                         "reading": "latency: 8 warps per SM, 19 Montgomery steps per tile, "
+                                                    "tile barriers and per-CTA operand loads weigh more"}},
     ("rsa2048", 1): {"window": 4, "stamp": "2c547aada0325644", "dram_bytes_per_op": 257607.0,
                      "files": ["kernels.cuh", "mont.cuh", "inst_unit.cuh", "inst_h32.cu", "keyrec.h"],
                      "source": "profiles/crt_kernel_rsa2048_w4_cios_ncu_full.md"},
@@ -1111,13 +1123,14 @@ def main():
     # (a slight understatement of its rate).
     prods = rsa_products_per_op(spec["bits"], kind, e=e_pub, window=tune["window"])
     cios_achieved = prods * count / (ms / 1e3) / 1e12
-    prof = PROFILED_TRAFFIC.get((args.workload, tune["variant"])) if args.kind == "crt" else None
-    prof_valid = bool(prof and prof["window"] == tune["window"]
-                      and (tune["threads_per_op"] == 1 or tune["variant"] == 3)   # lanes: CUDA-core kernels only
-                      and prof["stamp"] == kernel_stamp(prof["files"]))
-    traffic = prof["dram_bytes_per_op"] * count if prof_valid else None
     pub_tc = args.kind == "public" and pub_tc_taken(spec["bits"], e_pub, count, tune["variant"])
     tc_path = (tune["variant"] == 3 and args.kind == "crt") or pub_tc
+    prof = (PROFILED_TRAFFIC.get((args.workload, tune["variant"])) if args.kind == "crt" else
+            PROFILED_TRAFFIC.get((args.workload, "public-tc")) if pub_tc and e_pub == 65537 else None)
+    prof_valid = bool(prof and prof["window"] in (None, tune["window"])
+                      and (tune["threads_per_op"] == 1 or tc_path)   # lanes: CUDA-core kernels only
+                      and prof["stamp"] == kernel_stamp(prof["files"]))
+    traffic = prof["dram_bytes_per_op"] * count if prof_valid else None
     if tc_path:
         if pub_tc:
             issued, tflops_op, method_flops_op = pub_tc_work_per_op(e_pub)
@@ -1151,9 +1164,7 @@ def main():
                      "traffic_source": prof["source"] if traffic else None,
                      "algorithmic_io_bytes": count * L * 4 * 2})
     if prof_valid and "pipes" in prof:
-        roofline["limiter"] = dict(prof["pipes"], source=prof["source"],
-                                   reading="latency and issue: no pipe saturated; 16 warps per SM (TMEM holds "
-                                           "four 128-column tiles), fixed-latency carry-chain waits")
+        roofline["limiter"] = dict(prof["pipes"], source=prof["source"])
     if clk.get("sm_mhz"):
         roofline["sm_mhz"] = clk["sm_mhz"]
 
