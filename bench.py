@@ -49,7 +49,7 @@ def workload_desc(bits, count, kind="crt"):
 # to the recorded stamp and the window matches; otherwise reported as null.
 PROFILED_TRAFFIC = {
     # (workload, variant): one ncu capture of that kernel, valid while its sources hash to the stamp
-    ("rsa2048", 3): {"window": 3, "stamp": "3ae443c6c031c681", "dram_bytes_per_op": 1159.3,
+    ("rsa2048", 3): {"window": 3, "stamp": "364df77860a7059c", "dram_bytes_per_op": 976.6,
                      "files": ["crt_tc.cu", "crt_tc.h", "tc.cuh", "mont.cuh", "kernels.cuh", "keyrec.h"],
                      "source": "profiles/crt_tc_half_kernel_rsa2048_w3_ncu_full.md",
                      # what binds the kernel, from the same capture (percent of peak while active)
@@ -58,19 +58,19 @@ PROFILED_TRAFFIC = {
                                "top_stalls": ["wait", "math_pipe_throttle", "long_scoreboard"],
                                "reading": "latency and issue: no pipe saturated; 16 warps per SM (TMEM holds four "
                                           "128-column tiles), fixed-latency carry-chain waits"}},
-    ("rsa4096", 3): {"window": 3, "stamp": "ff78cad136b25d9d", "dram_bytes_per_op": 2405.4,
+    ("rsa4096", 3): {"window": 3, "stamp": "ace8eb20c3bbdeff", "dram_bytes_per_op": 2127.9,
                      "files": ["crt_tc4.cu", "crt_tc.h", "tc.cuh", "mont.cuh", "kernels.cuh", "keyrec.h"],
                      "source": "profiles/crt_tc4_half_kernel_rsa4096_w3_ncu_full.md",
-                     "pipes": {"issue_active_pct": 39.1, "warps_active_pct": 12.5, "alu_pipe_pct": 32.4,
+                     "pipes": {"issue_active_pct": 39.2, "warps_active_pct": 12.5, "alu_pipe_pct": 32.5,
                                "fma_pipe_pct": 31.2, "tensor_pipe_pct": 14.0,
                                "top_stalls": ["wait", "long_scoreboard", "math_pipe_throttle"],
                                "reading": "latency: 8 warps per SM (two tiles of 256 TMEM columns, 255 "
                                           "registers), carry-chain waits poorly hidden"}},
-    ("rsa2048", "public-tc"): {"window": None, "stamp": "ff78cad136b25d9d", "dram_bytes_per_op": 262.0,
+    ("rsa2048", "public-tc"): {"window": None, "stamp": "ace8eb20c3bbdeff", "dram_bytes_per_op": 263.6,
                                "files": ["crt_tc4.cu", "crt_tc.h", "tc.cuh", "mont.cuh", "kernels.cuh", "keyrec.h"],
                                "source": "profiles/pub_tc4_kernel_rsa2048_e65537_ncu_full.md",
-                               "pipes": {"issue_active_pct": 33.2, "warps_active_pct": 12.5, "alu_pipe_pct": 24.1,
-                                         "fma_pipe_pct": 28.0, "tensor_pipe_pct": 12.3,
+                               "pipes": {"issue_active_pct": 33.2, "warps_active_pct": 12.5, "alu_pipe_pct": 23.5,
+                                         "fma_pipe_pct": 28.1, "tensor_pipe_pct": 12.2,
                                          "top_stalls": ["wait", "barrier", "long_scoreboard"],
                                          "reading": "latency: 8 warps per SM, 19 Montgomery steps per tile, "
                                                     "tile barriers and per-CTA operand loads weigh more"}},

@@ -535,6 +535,16 @@ __device__ __forceinline__ void load_prime_image(uint8_t *smem, const uint4 *ima
   for (int i = tid; i < (int)(kImgPrime / 16); i += kThreads) s4[i] = img[i];
 }
 
+// A tile's window table is dead once its exponentiation returns (its last
+// read, the final multiplication's select, precedes that step's tile
+// barriers): drop its lines from L2 instead of letting them be written back
+// to DRAM; the slot's next tile writes it afresh after its own barriers.
+template <int W>
+__device__ __forceinline__ void drop_table(const uint4 *tbl, int r) {
+  const uint4 *tb = tbl - r;   // the slot's table: one contiguous block
+  if ((reinterpret_cast<uintptr_t>(tb) & 127u) == 0u) tc::discard_l2(tb, Win<W>::kTblU4 * 16u, (uint32_t)r, kRows);
+}
+
 // ---------------------------------------------------------------- exponentiation kernel (both primes)
 // Uniform batches (RAGGED = false): one key; CTA 2c + pi runs prime pi, its
 // four tile slots take tiles round-robin.  Ragged batches (RAGGED = true): the
@@ -604,6 +614,7 @@ __device__ __forceinline__ void half_body(const HalfArgs &a, const RaggedTcArgs 
       const uint32_t *msg = a.msgs + (size_t)(valid ? row : a.count - 1) * (2 * kH);
       uint32_t A[kH];
       if (!ts.dead) exp_tile<W>(A, ts, msg, pi, kc, stage, stage_sa, tbl, r, a.wait_polls);
+      drop_table<W>(tbl, r);
       if (valid) {
         uint4 *h = a.halves + (size_t)pi * (kH / 4) * a.count_pad + row;
 #pragma unroll
@@ -645,6 +656,7 @@ __device__ __forceinline__ void half_body(const HalfArgs &a, const RaggedTcArgs 
         const uint32_t *msg = ra.msgs + ra.offsets[op];
         uint32_t A[kH];
         if (!ts.dead) exp_tile<W>(A, ts, msg, pi, kc, stage, stage_sa, tbl, r, ra.wait_polls);
+        drop_table<W>(tbl, r);
         if (valid) {
           uint4 *h = halves + (size_t)pi * (kH / 4) * cpad + pos;
 #pragma unroll

@@ -549,6 +549,15 @@ __device__ __forceinline__ void exp_tile(uint32_t (&A)[H], Tile &ts, uint8_t *sm
   }
 }
 
+// A tile's window table (or the public path's multiplier slot) is dead once
+// its exponentiation returns: its last read precedes that step's tile
+// barriers.  Drop its lines from L2 instead of letting them be written back
+// to DRAM; the slot's next tile writes it afresh after its own barriers.
+__device__ __forceinline__ void drop_slot(const uint4 *tbl, int r, uint32_t u4) {
+  const uint4 *tb = tbl - r;   // the slot's block
+  if ((reinterpret_cast<uintptr_t>(tb) & 127u) == 0u) tc::discard_l2(tb, u4 * 16u, (uint32_t)r, kRows);
+}
+
 // ---------------------------------------------------------------- exponentiation kernel (both primes)
 struct HalfArgs {
   const uint32_t *keyrec;
@@ -649,6 +658,7 @@ __device__ __forceinline__ void half_body(const HalfArgs &a, const tcr::RaggedTc
       const uint32_t *msg = a.msgs + (size_t)(valid ? row : a.count - 1) * (2 * H);
       uint32_t A[H];
       if (!ts.dead) exp_tile<H, W>(A, ts, smem, msg, pi, kc, tbl, a.wait_polls);
+      drop_slot(tbl, r, Wn::kTblU4);
       if (valid) {
         uint4 *h = a.halves + (size_t)pi * (H / 4) * a.count_pad + row;
 #pragma unroll
@@ -689,6 +699,7 @@ __device__ __forceinline__ void half_body(const HalfArgs &a, const tcr::RaggedTc
         const uint32_t *msg = ra.msgs + ra.offsets[op];
         uint32_t A[H];
         if (!ts.dead) exp_tile<H, W>(A, ts, smem, msg, pi, kc, tbl, ra.wait_polls);
+        drop_slot(tbl, r, Wn::kTblU4);
         if (valid) {
           uint4 *h = halves + (size_t)pi * (H / 4) * cpad + pos;
 #pragma unroll
@@ -835,6 +846,7 @@ __global__ void __launch_bounds__(kThreads, 1) pub_tc4_kernel(PubArgs a) {
     const uint32_t *msg = a.msgs + (size_t)(valid ? row : a.count - 1) * H;
     uint32_t A[H];
     if (!ts.dead) pub_exp_tile<H>(A, ts, smem, msg, kc, tbl, ebits, a.wait_polls);
+    drop_slot(tbl, r, (H / 4) * kRows);
     if (valid) {
       const bool below = row_below(msg, a.keyrec + lay.n, H);
       const bool timed_out = ts.err || ts.dead;

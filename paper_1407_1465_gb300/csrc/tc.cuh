@@ -123,6 +123,15 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// Drops the L2 lines of [p, p + bytes) without writing them back (their data
+// is dead); p 128-byte aligned, bytes a multiple of 128.  Thread `first` of
+// `stride` threads takes every stride-th line.
+__device__ __forceinline__ void discard_l2(const void *p, uint32_t bytes, uint32_t first, uint32_t stride) {
+  const char *c = static_cast<const char *>(p);
+  for (uint32_t i = first; i < bytes / 128u; i += stride)
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(c + (size_t)i * 128u) : "memory");
+}
+
 // ---------------------------------------------------------------- misc
 // Named barrier over `nthreads` threads that also ORs a predicate across them.
 __device__ __forceinline__ bool bar_red_or(int id, int nthreads, bool pred) {
