@@ -1,8 +1,9 @@
 // mr.cu -- batch Miller-Rabin probable-prime tests (key generation, Fig. 1:
 // "choose two large primes"; the paper names no test, this is the standard one).
 //
-// One candidate per thread, 32 per warp.  Every candidate is its own modulus, so
-// its Montgomery constants are derived in the kernel:
+// One candidate per thread, 32 per warp (512/1024 bits; 2048-bit candidates
+// run on four lanes each, mr_kernel_t below).  Every candidate is its own
+// modulus, so its Montgomery constants are derived in the kernel:
 //   n' = -n^-1 mod 2^32   Newton's iteration on one word,
 //   R mod n               32L modular doublings of 1 (R = 2^(32L)),
 //   R^2 mod n             64 more doublings give 2^64 R mod n, then log2(L/2)
@@ -19,6 +20,7 @@
 #include <cstdint>
 
 #include "kernels.cuh"
+#include "kernels_t.cuh"
 #include "mont.cuh"
 #include "rsa_gb300.h"
 #include "runtime_internal.h"
@@ -221,6 +223,167 @@ __global__ void __launch_bounds__(kMrThreads) mr_kernel(MrArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- 2048-bit candidates, T lanes each
+// The same test with every number sliced over T lanes (mont_t.cuh): 64-limb
+// candidates need 255 registers on one lane (two CTAs of 128 threads per SM);
+// on four lanes a thread holds 16 limbs and more warps hide the carry chains'
+// latency.  Each candidate's own constants live contiguously in the warp's
+// global scratch (words): d = (n - 1) / 2^s zero padded to L + 4, R mod n,
+// n - R mod n and R^2 mod n, L each; the fixed-window exponentiation of
+// kernels_t.cuh reads its exponent digits and its 1 from there.
+template <int L>
+struct MrT {
+  static constexpr int kOpWords = 4 * L + 4;   // d (L + 4), one, minus one, R^2
+  static constexpr int kD = 0, kOne = L + 4, kM1 = 2 * L + 4, kR2 = 3 * L + 4;
+  template <int T, int W>
+  __host__ __device__ static constexpr size_t table_u4() { return ((size_t)1 << W) * (L / T / 4) * 32; }
+  template <int T, int W>
+  __host__ __device__ static constexpr size_t per_warp_u4() { return table_u4<T, W>() + (size_t)(32 / T) * kOpWords / 4; }
+};
+
+// every rank's slice of A equals that of the L-limb number at w (contiguous)
+template <int K, int T>
+__device__ __forceinline__ bool group_equal(const uint32_t (&A)[K], const uint32_t *w, const Group<T> &g) {
+  uint32_t diff = 0u;
+#pragma unroll
+  for (int j = 0; j < K; ++j) diff |= A[j] ^ w[g.r * K + j];
+  return g.bits(diff == 0u) == (1u << T) - 1u;
+}
+
+template <int L, int T, int W, int U>
+__device__ __forceinline__ void mr_tile_t(const MrArgs &a, uint32_t base, const Group<T> &g, uint4 *stage_op,
+                                          uint4 *table_lane, uint32_t *opw) {
+  constexpr int K = L / T, OS = 32 / T;
+  constexpr int kSqToR2 = (L == 16) ? 3 : (L == 32) ? 4 : 5;    // log2(L / 2)
+  const uint32_t idx = base + (uint32_t)g.opi;
+  const bool live = idx < a.count;
+  const uint32_t row = live ? idx : a.count - 1;
+  NRegs<K> N;
+  load_row<K>(N.n, a.cands + (size_t)row * L + g.r * K, true);
+  uint32_t above = 0u;   // any limb above limb 0 nonzero
+#pragma unroll
+  for (int j = 0; j < K; ++j) above |= (g.r == 0 && j == 0) ? 0u : N.n[j];
+  const uint32_t n0 = g.from_rank(N.n[0], 0);
+  const uint32_t above_any = g.bits(above != 0u);   // a collective: every lane, before any condition
+  const bool valid = (n0 & 1u) && (above_any != 0u || n0 >= 5u);
+  if (g.r == 0 && !valid) N.n[0] |= 1u;   // keep the arithmetic defined; the verdict is -1 anyway
+  uint32_t inv = g.from_rank(N.n[0], 0);  // n' = -n^-1 mod 2^32 (Newton, as mr_kernel)
+  const uint32_t n0f = inv;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) inv *= 2u - n0f * inv;
+  const uint32_t np = 0u - inv;
+  uint32_t *dw = opw + MrT<L>::kD, *onew = opw + MrT<L>::kOne, *m1w = opw + MrT<L>::kM1, *r2w = opw + MrT<L>::kR2;
+  // n - 1 = d 2^s: n - 1 (n odd: bit 0 cleared) into the d area, s from the
+  // lowest rank with a nonzero slice, then every rank shifts its words down
+  int s;
+  {
+    uint32_t w0 = 0u;
+    int j0 = -1;
+#pragma unroll
+    for (int j = K - 1; j >= 0; --j) {
+      const uint32_t v = (g.r == 0 && j == 0) ? (N.n[0] & ~1u) : N.n[j];
+      dw[g.r * K + j] = v;
+      if (v) { w0 = v; j0 = j; }
+    }
+    if (g.r == T - 1) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) dw[L + j] = 0u;
+    }
+    const uint32_t nz = g.bits(j0 >= 0);
+    const int r0 = nz ? __ffs(nz) - 1 : 0;
+    const int mine = j0 >= 0 ? 32 * (g.r * K + j0) + __ffs(w0) - 1 : 0;
+    s = (int)g.from_rank((uint32_t)mine, r0);
+    __syncwarp();
+    uint32_t dd[K];
+    const int q = s >> 5, sh = s & 31;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int i = g.r * K + k + q;
+      dd[k] = __funnelshift_r(i < L ? dw[i] : 0u, i + 1 < L ? dw[i + 1] : 0u, sh);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < K; ++k) dw[g.r * K + k] = dd[k];
+  }
+  // R mod n by 32L doublings of 1, n - R mod n, then R^2 mod n: 64 more
+  // doublings (2^64 R) and log2(L/2) Montgomery squarings
+  uint32_t x[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) x[j] = 0u;
+  if (g.r == 0) x[0] = 1u;
+  const SmemB st{stage_op, OS};
+#pragma unroll 1
+  for (int k = 0; k < 32 * L; ++k) {
+    to_stage_t<K, T>(stage_op, x, g);   // mod_add_t reads this rank's own slice only
+    mod_add_t<K, T>(x, st, N, g);
+  }
+#pragma unroll
+  for (int j = 0; j < K; ++j) onew[g.r * K + j] = x[j];
+  {
+    uint32_t m1[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) m1[j] = x[j];
+    to_stage_t<K, T>(stage_op, N.n, g);
+    mod_rsub_t<K, T>(m1, st, N, g);       // n - (R mod n)
+#pragma unroll
+    for (int j = 0; j < K; ++j) m1w[g.r * K + j] = m1[j];
+  }
+#pragma unroll 1
+  for (int k = 0; k < 64; ++k) {
+    to_stage_t<K, T>(stage_op, x, g);
+    mod_add_t<K, T>(x, st, N, g);
+  }
+#pragma unroll 1
+  for (int k = 0; k < kSqToR2; ++k) {
+    __syncwarp();
+    to_stage_t<K, T>(stage_op, x, g);
+    __syncwarp();
+    mont_mul_t<K, T, U>(x, st, N, np, g);
+  }
+#pragma unroll
+  for (int j = 0; j < K; ++j) r2w[g.r * K + j] = x[j];
+  __syncwarp();
+  const int s_max = __reduce_max_sync(0xffffffffu, s);
+  int verdict = 1;
+#pragma unroll 1
+  for (uint32_t rd = 0; rd < a.rounds; ++rd) {
+    uint32_t A[K];
+    load_row<K>(A, a.bases + ((size_t)row * a.rounds + rd) * L + g.r * K, true);
+    mont_mul_t<K, T, U>(A, SmemB{reinterpret_cast<const uint4 *>(r2w), 1}, N, np, g);   // a R
+    fixed_window_exp_t<K, T, W, U>(A, dw, 32 * L, onew, stage_op, table_lane, N, np, g);
+    bool pass = group_equal<K, T>(A, onew, g);
+    pass = group_equal<K, T>(A, m1w, g) || pass;
+#pragma unroll 1
+    for (int j = 1; j < s_max; ++j) {
+      __syncwarp();
+      to_stage_t<K, T>(stage_op, A, g);
+      __syncwarp();
+      mont_mul_t<K, T, U>(A, st, N, np, g);
+      const bool m1 = group_equal<K, T>(A, m1w, g);   // every lane: a collective
+      if (j < s && m1) pass = true;
+    }
+    if (!pass) verdict = 0;
+  }
+  if (live && g.r == 0) a.verdict[idx] = valid ? verdict : -1;
+}
+
+template <int L, int T, int W, int U>
+__global__ void __launch_bounds__(kMrThreads) mr_kernel_t(MrArgs a) {
+  constexpr int OPW = 32 / T;
+  extern __shared__ uint4 smem4[];
+  const int nw = blockDim.x / 32, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const Group<T> g(lane);
+  uint4 *stage = smem4 + (size_t)warp * (L / 4) * OPW;   // [L/4][32/T] uint4 per warp
+  uint4 *wbase = a.tables + (size_t)(blockIdx.x * nw + warp) * MrT<L>::template per_warp_u4<T, W>();
+  uint4 *table_lane = wbase + lane;
+  uint32_t *opw = reinterpret_cast<uint32_t *>(wbase + MrT<L>::template table_u4<T, W>()) +
+                  (size_t)g.opi * MrT<L>::kOpWords;
+  const uint32_t ntiles = (a.count + OPW - 1) / OPW;
+#pragma unroll 1
+  for (uint32_t tile = blockIdx.x * nw + warp; tile < ntiles; tile += gridDim.x * nw)
+    mr_tile_t<L, T, W, U>(a, tile * OPW, g, stage + g.opi, table_lane, opw);
+}
+
 template <int L>
 cudaError_t launch_mr(const MrArgs &h, int grid, cudaStream_t s) {
   const size_t smem = MrSmem<L>::bytes(kMrThreads / 32);
@@ -254,18 +417,39 @@ extern "C" int rsa_mr_batch(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const 
   NvtxRange range("rsa_mr_batch");
   Workspace &w = c->ws(s);
   const int L = (int)nbits / 32;
-  const uint64_t warps_needed = (count + 31) / 32;
   const int per_cta = kMrThreads / 32;
+  if (L == 64) {
+    // 2048-bit candidates: four lanes each (mr_kernel_t), as many CTAs as fit
+    constexpr int T = 4;
+    const void *fn = reinterpret_cast<const void *>(&mr_kernel_t<64, T, kMrWindow, 8>);
+    const size_t smem = (size_t)per_cta * (64 / 4) * (32 / T) * 16;
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kMrThreads, smem);
+    if (e != cudaSuccess) return cuda_error(e, "occupancy of mr_kernel_t");
+    const uint64_t warps_needed = (count + 32 / T - 1) / (32 / T);
+    const int grid = (int)std::max<uint64_t>(
+        1, std::min<uint64_t>((warps_needed + per_cta - 1) / per_cta, (uint64_t)c->sm_count * std::max(occ, 1)));
+    const size_t tbytes = (size_t)grid * per_cta * MrT<64>::per_warp_u4<T, kMrWindow>() * 16;
+    int rc = c->ensure(w.tables, tbytes);
+    if (rc) return rc;
+    MrArgs h{cands, bases, verdicts, static_cast<uint4 *>(w.tables.ptr), (uint32_t)count, rounds};
+    void *args[] = {&h};
+    e = cudaLaunchKernel(fn, dim3(grid), dim3(kMrThreads), args, smem, s);
+    if (e != cudaSuccess) return cuda_error(e, "launch mr_kernel_t");
+    c->stats.kernel_launches++;
+    c->stats.ops += count;
+    return RSA_OK;
+  }
+  const uint64_t warps_needed = (count + 31) / 32;
   const int grid = (int)std::max<uint64_t>(
-      1, std::min<uint64_t>((warps_needed + per_cta - 1) / per_cta, (uint64_t)c->sm_count * (L == 64 ? 2 : 4)));
-  const size_t per_warp_u4 = (L == 16)   ? MrSmem<16>::global_u4_per_warp<kMrWindow>()
-                             : (L == 32) ? MrSmem<32>::global_u4_per_warp<kMrWindow>()
-                                         : MrSmem<64>::global_u4_per_warp<kMrWindow>();
+      1, std::min<uint64_t>((warps_needed + per_cta - 1) / per_cta, (uint64_t)c->sm_count * 4));
+  const size_t per_warp_u4 = (L == 16) ? MrSmem<16>::global_u4_per_warp<kMrWindow>()
+                                        : MrSmem<32>::global_u4_per_warp<kMrWindow>();
   const size_t tbytes = (size_t)grid * per_cta * per_warp_u4 * 16;
   int rc = c->ensure(w.tables, tbytes);
   if (rc) return rc;
   MrArgs h{cands, bases, verdicts, static_cast<uint4 *>(w.tables.ptr), (uint32_t)count, rounds};
-  cudaError_t e = (L == 16) ? launch_mr<16>(h, grid, s) : (L == 32) ? launch_mr<32>(h, grid, s) : launch_mr<64>(h, grid, s);
+  cudaError_t e = (L == 16) ? launch_mr<16>(h, grid, s) : launch_mr<32>(h, grid, s);
   if (e != cudaSuccess) return cuda_error(e, "launch mr_kernel");
   c->stats.kernel_launches++;
   c->stats.ops += count;
