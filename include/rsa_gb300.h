@@ -167,12 +167,41 @@ int rsa_mr_batch(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *c
  * 2 when g_i = n_i (a duplicate modulus, or each prime of n_i is shared:
  * separate it with pairwise gcds), -1 for an invalid n_i.  At least one of
  * gcds and flags must be given.  All pointers are device pointers (rows
- * 16-byte aligned); the work is count^2 / 2 Montgomery-word operations of the
- * modulus size, in three kernels enqueued on `stream`.  Errors: RSA_ERR_ARG
- * (null or misaligned pointers, count above 2^26), RSA_ERR_UNSUPPORTED,
- * RSA_ERR_NOMEM, RSA_ERR_CUDA. */
+ * 16-byte aligned).  The form is chosen as rsa_batch_gcd_ex with RSA_GCD_AUTO
+ * chooses it.  Enqueued on `stream`.  Errors: RSA_ERR_ARG (null or misaligned
+ * pointers, count above 2^26), RSA_ERR_UNSUPPORTED, RSA_ERR_NOMEM,
+ * RSA_ERR_CUDA. */
 int rsa_batch_gcd(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *moduli, uint32_t *gcds,
                   int32_t *flags, void *stream);
+
+/* Forms of the batch GCD; both give the same gcds and flags.
+ * RSA_GCD_SCAN: modulus by modulus over block products of the others,
+ *   about count^2 / 2 Montgomery-word operations of the modulus size, a few
+ *   kernels, little memory.
+ * RSA_GCD_TREE: a product tree of the moduli and a remainder tree of
+ *   prod n_j modulo every n_i^2 (Montgomery remainders, no divisions), then
+ *   (prod n_j / n_i) mod n_i and a binary gcd per modulus: quasi-linear work,
+ *   products of long numbers by three-prime number-theoretic transforms.
+ *   Needs rsa_batch_gcd_tree_bytes of device memory within the context's
+ *   budget (3.8 GB for 2^17 moduli of 2048 bits, 34 GB for 2^20) and
+ *   count (rounded up to a power of two) x nbits / 32 <= 2^26.
+ * RSA_GCD_AUTO: the tree from 32768 moduli when it fits (that count and the
+ *   memory budget), else the scan. */
+#define RSA_GCD_AUTO 0
+#define RSA_GCD_SCAN 1
+#define RSA_GCD_TREE 2
+/* rsa_batch_gcd in a given form.  Errors as rsa_batch_gcd, and RSA_ERR_ARG for
+ * an unknown method or a tree beyond its size limit; RSA_ERR_NOMEM when the
+ * tree's memory exceeds the budget. */
+int rsa_batch_gcd_ex(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *moduli, uint32_t *gcds,
+                     int32_t *flags, int method, void *stream);
+/* The form RSA_GCD_AUTO takes for `count` moduli on this context now
+ * (RSA_GCD_SCAN or RSA_GCD_TREE).  No GPU work.  Errors as rsa_batch_gcd. */
+int rsa_batch_gcd_method(rsa_ctx *ctx, uint32_t nbits, uint64_t count, int *method);
+/* Device bytes the tree form takes for `count` moduli of nbits (its levels,
+ * transform scratch and twiddle tables).  Errors: RSA_ERR_UNSUPPORTED,
+ * RSA_ERR_ARG (null pointer, beyond the size limit). */
+int rsa_batch_gcd_tree_bytes(uint32_t nbits, uint64_t count, uint64_t *bytes);
 /* rsa_batch_gcd with host buffers: moduli, gcds (or NULL) and flags (or NULL)
  * are host pointers (pinned memory copies fastest); the copies in and out run
  * on `stream`, and the call returns when the results are in host memory.

@@ -18,7 +18,7 @@ import numpy as np
 from . import _lib
 from ._lib import (RSA_ERR_ARG, RSA_ERR_CUDA, RSA_ERR_KEY, RSA_ERR_NOMEM, RSA_ERR_RANGE,  # noqa: F401
                    RSA_ERR_TIMEOUT, RSA_ERR_UNSUPPORTED, RSA_ERR_VERIFY, RSA_EXP_PRIVATE_CRT, RSA_EXP_PRIVATE_PLAIN,
-                   RSA_EXP_PUBLIC, RSA_OK, RSA_TUNE_RAGGED, RsaError, check, last_error, rsa_stats, rsa_tuning)
+                   RSA_EXP_PUBLIC, RSA_GCD_AUTO, RSA_GCD_SCAN, RSA_GCD_TREE, RSA_OK, RSA_TUNE_RAGGED, RsaError, check, last_error, rsa_stats, rsa_tuning)
 
 __all__ = [
     "RsaContext", "RsaError", "int_to_limbs", "limbs_to_int",
@@ -27,6 +27,7 @@ __all__ = [
     "rsa_keyunload", "rsa_key_info",
     "rsa_modexp_key", "rsa_modexp_batch", "rsa_modexp_key_host", "rsa_modexp_batch_host",
     "rsa_sign_key", "rsa_verify_key", "rsa_mr_batch", "rsa_batch_gcd", "rsa_batch_gcd_host", "rsa_batch_gcd_plan",
+    "rsa_batch_gcd_ex", "rsa_batch_gcd_method", "rsa_batch_gcd_tree_bytes",
     "rsa_sync", "rsa_last_error", "rsa_set_tuning", "rsa_get_tuning", "rsa_get_stats",
     "rsa_products_per_op", "rsa_imad_probe", "rsa_crt_decrypt_noalloc", "rsa_autotune", "rsa_autotune_batch",
     "rsa_server_start", "rsa_server_submit", "rsa_server_submit_many", "rsa_server_clock", "rsa_server_poll", "rsa_server_drain", "rsa_server_get_stats",
@@ -184,6 +185,25 @@ def rsa_batch_gcd(ctx: int, nbits: int, count: int, moduli, gcds, flags, stream=
 def rsa_batch_gcd_host(ctx: int, nbits: int, count: int, moduli: np.ndarray, gcds, flags, stream=None) -> None:
     check(_lib.lib().rsa_batch_gcd_host(ctx, nbits, count, _ptr(moduli), _ptr(gcds), _ptr(flags),
                                         _stream_ptr(stream)))
+
+
+def rsa_batch_gcd_ex(ctx: int, nbits: int, count: int, moduli, gcds, flags, method: int, stream=None) -> None:
+    check(_lib.lib().rsa_batch_gcd_ex(ctx, nbits, count, _ptr(moduli), _ptr(gcds), _ptr(flags), method,
+                                      _stream_ptr(stream)))
+
+
+def rsa_batch_gcd_method(ctx: int, nbits: int, count: int) -> int:
+    """The form (RSA_GCD_SCAN or RSA_GCD_TREE) RSA_GCD_AUTO takes for count moduli."""
+    m = ctypes.c_int(0)
+    check(_lib.lib().rsa_batch_gcd_method(ctx, nbits, count, ctypes.byref(m)))
+    return m.value
+
+
+def rsa_batch_gcd_tree_bytes(nbits: int, count: int) -> int:
+    """Device bytes the tree form of the batch GCD needs for count moduli."""
+    b = ctypes.c_uint64(0)
+    check(_lib.lib().rsa_batch_gcd_tree_bytes(nbits, count, ctypes.byref(b)))
+    return b.value
 
 
 def rsa_batch_gcd_plan(ctx: int, nbits: int, count: int) -> tuple[int, int]:
@@ -413,17 +433,18 @@ class RsaContext:
         rsa_mr_batch(self.handle, nbits, count, cands, rounds, bases, verdicts, stream)
         return verdicts
 
-    def batch_gcd(self, nbits: int, moduli, gcds=None, flags=None, stream=None):
+    def batch_gcd(self, nbits: int, moduli, gcds=None, flags=None, stream=None, method: int = RSA_GCD_AUTO):
         """moduli: CUDA tensor [count, nbits/32] (int32 view of the limbs).
         Returns (gcds, flags): g_i = gcd(n_i, product of the other valid
-        moduli) and int32 flags 0 coprime, 1 proper factor, 2 g = n, -1 invalid."""
+        moduli) and int32 flags 0 coprime, 1 proper factor, 2 g = n, -1 invalid.
+        method: RSA_GCD_AUTO, RSA_GCD_SCAN or RSA_GCD_TREE."""
         import torch
         count = moduli.shape[0]
         if gcds is None:
             gcds = torch.empty_like(moduli)
         if flags is None:
             flags = torch.empty(count, dtype=torch.int32, device=moduli.device)
-        rsa_batch_gcd(self.handle, nbits, count, moduli, gcds, flags, stream)
+        rsa_batch_gcd_ex(self.handle, nbits, count, moduli, gcds, flags, method, stream)
         return gcds, flags
 
     def modexp_key_host(self, key_id: int, exp_sel: int, msgs: np.ndarray, out: np.ndarray | None = None,

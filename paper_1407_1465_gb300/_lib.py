@@ -26,6 +26,7 @@ RSA_EXP_PUBLIC = 0
 RSA_EXP_PRIVATE_CRT = 1
 RSA_EXP_PRIVATE_PLAIN = 2
 RSA_TUNE_RAGGED = 3          # rsa_set_tuning / rsa_get_tuning: the ragged-batch kernels
+RSA_GCD_AUTO, RSA_GCD_SCAN, RSA_GCD_TREE = 0, 1, 2   # rsa_batch_gcd_ex methods
 
 STATUS_NAMES = {
     0: "RSA_OK", -1: "RSA_ERR_ARG", -2: "RSA_ERR_KEY", -3: "RSA_ERR_RANGE", -4: "RSA_ERR_NOMEM",
@@ -93,6 +94,9 @@ SIGNATURES = [
     ("rsa_batch_gcd", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, _P, _P, _P]),
     ("rsa_batch_gcd_host", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, _P, _P, _P]),
     ("rsa_batch_gcd_plan", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, _P]),
+    ("rsa_batch_gcd_ex", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, _P, _P, ctypes.c_int, _P]),
+    ("rsa_batch_gcd_method", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P]),
+    ("rsa_batch_gcd_tree_bytes", ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64, _P]),
     ("rsa_verify_key", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P]),
     ("rsa_modexp_key_host", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P]),
     ("rsa_modexp_batch_host", ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, _P, ctypes.c_uint64, _P, _P, _P, _P]),

@@ -351,7 +351,7 @@ void Ctx::release_stream(cudaStream_t s) {
     Workspace &w = it->second;
     for (DevBuf *d : {&w.tables, &w.io_in, &w.io_out, &w.io_status, &w.aux0, &w.aux1, &w.aux2, &w.aux3, &w.halves,
                       &w.tc_halves[0], &w.tc_halves[1],
-                      &w.verify, &w.gcd0, &w.gcd1})
+                      &w.verify, &w.gcd0, &w.gcd1, &w.gcd_tree, &w.gcd_tw})
       if (d->ptr) {
         cudaFree(d->ptr);
         release(d->bytes);

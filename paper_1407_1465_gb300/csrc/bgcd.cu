@@ -34,6 +34,7 @@
 #include <cstdint>
 #include <cstdlib>
 
+#include "bgcd.cuh"
 #include "mont.cuh"
 #include "rsa_gb300.h"
 #include "runtime_internal.h"
@@ -453,55 +454,6 @@ __global__ void __launch_bounds__(kGcdThreads, MINB) bgcd_kernel(GcdArgs a) {
   }
 }
 
-// Binary gcd of u (odd) and v: strip v's factors of two, order the pair so
-// that v >= u, replace v by v - u; stops when v = 0 with the gcd in u.  Every
-// pass removes at least one bit from u + v, so at most 64L passes; the loop
-// runs until the last lane of the warp is done.
-template <int L>
-__device__ __forceinline__ void binary_gcd(uint32_t (&u)[L], uint32_t (&v)[L]) {
-#pragma unroll 1
-  for (;;) {
-    uint32_t vor = 0;
-#pragma unroll
-    for (int j = 0; j < L; ++j) vor |= v[j];
-    const bool act = vor != 0u;
-    if (!__any_sync(0xffffffffu, act)) break;
-    if (!act) continue;
-    if (v[0] == 0u) {
-#pragma unroll
-      for (int j = 0; j < L - 1; ++j) v[j] = v[j + 1];
-      v[L - 1] = 0u;
-      continue;
-    }
-    const int z = __ffs(v[0]) - 1;
-    if (z) {
-#pragma unroll
-      for (int j = 0; j < L - 1; ++j) v[j] = __funnelshift_r(v[j], v[j + 1], z);
-      v[L - 1] >>= z;
-    }
-    // borrow of v - u decides the order
-    (void)sub_cc(v[0], u[0]);
-#pragma unroll
-    for (int j = 1; j < L; ++j) (void)subc_cc(v[j], u[j]);
-    const uint32_t lt = subc(0u, 0u);                 // all ones iff v < u
-    if (lt) {                                         // (u, v) = (v, u - v)
-      uint32_t d = sub_cc(u[0], v[0]);
-      u[0] = v[0];
-      v[0] = d;
-#pragma unroll
-      for (int j = 1; j < L; ++j) {
-        d = subc_cc(u[j], v[j]);
-        u[j] = v[j];
-        v[j] = d;
-      }
-    } else {                                          // v = v - u
-      v[0] = sub_cc(v[0], u[0]);
-#pragma unroll
-      for (int j = 1; j < L; ++j) v[j] = subc_cc(v[j], u[j]);
-    }
-  }
-}
-
 // One level of the tree that multiplies the parts' partial products together:
 // part[p] = part[p] * part[p + half] for p < cur - half (Montgomery products,
 // so each level adds a power of R^-1, a unit modulo n_i).
@@ -766,17 +718,90 @@ int batch_gcd_run(Ctx *c, uint32_t nbits, uint64_t count, const uint32_t *moduli
 }  // namespace
 }  // namespace rsagpu
 
-extern "C" int rsa_batch_gcd(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *moduli, uint32_t *gcds,
-                             int32_t *flags, void *stream) {
+namespace rsagpu {
+namespace {
+
+// From this many moduli the automatic choice takes the trees (when their
+// memory fits the context's budget).
+uint64_t gcd_tree_min() {
+  const char *v = std::getenv("RSAGPU_GCD_TREE_MIN");
+  return v ? std::strtoull(v, nullptr, 10) : 32768ull;
+}
+
+bool tree_fits(uint32_t L, uint64_t count) {
+  uint64_t K = 2;
+  while (K < count) K <<= 1;
+  return K * L <= (1ull << 26);
+}
+
+int gcd_method(const Ctx *c, uint32_t nbits, uint64_t count, int method) {
+  const uint32_t L = nbits / 32;
+  if (method == RSA_GCD_AUTO) {
+    const bool tree = count >= 2 && count >= gcd_tree_min() && tree_fits(L, count) &&
+                      c->used + batch_gcd_tree_bytes(L, count) <= c->budget;
+    return tree ? RSA_GCD_TREE : RSA_GCD_SCAN;
+  }
+  return method;
+}
+
+int gcd_dispatch(Ctx *c, uint32_t nbits, uint64_t count, const uint32_t *moduli, uint32_t *gcds, int32_t *flags,
+                 int method, cudaStream_t s) {
+  method = gcd_method(c, nbits, count, method);
+  if (method == RSA_GCD_TREE) {
+    cudaSetDevice(c->device);
+    return batch_gcd_tree_run(c, nbits, count, moduli, gcds, flags, s);
+  }
+  return batch_gcd_run(c, nbits, count, moduli, gcds, flags, s);
+}
+
+int method_check(uint32_t nbits, uint64_t count, int method) {
+  if (method != RSA_GCD_AUTO && method != RSA_GCD_SCAN && method != RSA_GCD_TREE)
+    return set_error(RSA_ERR_ARG, "method must be RSA_GCD_AUTO, RSA_GCD_SCAN or RSA_GCD_TREE");
+  if (method == RSA_GCD_TREE && !tree_fits(nbits / 32, count))
+    return set_error(RSA_ERR_ARG, "tree form: count (rounded up to a power of two) times modulus words above 2^26");
+  return RSA_OK;
+}
+
+}  // namespace
+}  // namespace rsagpu
+
+extern "C" int rsa_batch_gcd_ex(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *moduli,
+                                uint32_t *gcds, int32_t *flags, int method, void *stream) {
   int rc = gcd_check(ctx, nbits, count);
   if (rc) return rc;
+  if ((rc = method_check(nbits, count, method))) return rc;
   if (count == 0) return RSA_OK;
   if (!moduli || (!gcds && !flags)) return set_error(RSA_ERR_ARG, "null pointer");
   if ((reinterpret_cast<uintptr_t>(moduli) | reinterpret_cast<uintptr_t>(gcds)) & 15u)
     return set_error(RSA_ERR_ARG, "modulus and gcd rows must be 16-byte aligned");
   Ctx *c = reinterpret_cast<Ctx *>(ctx);
   std::lock_guard<std::mutex> lock(c->mu);
-  return batch_gcd_run(c, nbits, count, moduli, gcds, flags, static_cast<cudaStream_t>(stream));
+  return gcd_dispatch(c, nbits, count, moduli, gcds, flags, method, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int rsa_batch_gcd(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *moduli, uint32_t *gcds,
+                             int32_t *flags, void *stream) {
+  return rsa_batch_gcd_ex(ctx, nbits, count, moduli, gcds, flags, RSA_GCD_AUTO, stream);
+}
+
+extern "C" int rsa_batch_gcd_method(rsa_ctx *ctx, uint32_t nbits, uint64_t count, int *method) {
+  int rc = gcd_check(ctx, nbits, count);
+  if (rc) return rc;
+  if (!method) return set_error(RSA_ERR_ARG, "null pointer");
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  std::lock_guard<std::mutex> lock(c->mu);
+  *method = gcd_method(c, nbits, count, RSA_GCD_AUTO);
+  return RSA_OK;
+}
+
+extern "C" int rsa_batch_gcd_tree_bytes(uint32_t nbits, uint64_t count, uint64_t *bytes) {
+  if (nbits != 512 && nbits != 1024 && nbits != 2048)
+    return set_error(RSA_ERR_UNSUPPORTED, "moduli of 512, 1024 or 2048 bits");
+  if (!bytes) return set_error(RSA_ERR_ARG, "null pointer");
+  if (!tree_fits(nbits / 32, count))
+    return set_error(RSA_ERR_ARG, "tree form: count (rounded up to a power of two) times modulus words above 2^26");
+  *bytes = batch_gcd_tree_bytes(nbits / 32, count);
+  return RSA_OK;
 }
 
 extern "C" int rsa_batch_gcd_host(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *moduli,
@@ -798,7 +823,8 @@ extern "C" int rsa_batch_gcd_host(rsa_ctx *ctx, uint32_t nbits, uint64_t count, 
   if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync H2D");
   uint32_t *dg = gcds ? static_cast<uint32_t *>(w.io_out.ptr) : nullptr;
   int32_t *df = flags ? static_cast<int32_t *>(w.io_status.ptr) : nullptr;
-  if ((rc = batch_gcd_run(c, nbits, count, static_cast<const uint32_t *>(w.io_in.ptr), dg, df, s))) return rc;
+  if ((rc = gcd_dispatch(c, nbits, count, static_cast<const uint32_t *>(w.io_in.ptr), dg, df, RSA_GCD_AUTO, s)))
+    return rc;
   if (gcds && (e = cudaMemcpyAsync(gcds, dg, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return cuda_error(e, "cudaMemcpyAsync D2H gcds");
   if (flags && (e = cudaMemcpyAsync(flags, df, (size_t)count * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)

@@ -1,0 +1,1033 @@
+// bgcd_tree.cu -- batch GCD by a product tree and a remainder tree, for scans
+// of many moduli (the weak-key detection the paper's introduction motivates:
+// two RSA moduli that share a prime are both factored by one gcd).
+//
+// g_i = gcd(n_i, prod_{j != i} n_j) for k moduli costs about L^2 k^2 word
+// products modulus by modulus (bgcd.cu).  With fast multiplication the trees
+// cost O(k L log^2(k L)) instead:
+//   * product tree: X_0 = the moduli (1 for invalid ones and for padding up to
+//     K = 2^T), X_{t+1}[v] = X_t[2v] X_t[2v+1]; a node of level t has
+//     s_t = L 2^t words;
+//   * remainder tree in Montgomery form, Y_t = X_t^2, mu_t = -Y_t^-1 mod
+//     2^(32 k), k = 2 s_t: Z_T = X_T, Z_t[v] = (Z_{t+1}[v/2] + q Y_t[v]) /
+//     2^(32k) with q = Z_{t+1}[v/2] mu_t[v] mod 2^(32k).  Z_t[v] is congruent
+//     to P 2^(-e) modulo Y_t[v] (P = X_T, e a multiple of 32) and stays below
+//     (T - t + 1) Y_t[v] with no subtraction, in k + 1 words;
+//   * mu at the lowest level of the remainder tree by Newton's iteration from
+//     one word (mu_hi = H mu + mu mod 2^(32w), H the words w..2w of Y mu);
+//     above it from the children (-mu_a mu_b = mu_a ~mu_b + mu_a mod 2^(32 s_t))
+//     and one Newton step;
+//   * at the leaves, per modulus: Z of its level-t0 node reduced modulo n_i^2
+//     word by word (Montgomery), so z = P 2^(-e') mod n_i^2, a multiple of n_i;
+//     u = z / n_i (exact division, word by word from the bottom) is
+//     (P / n_i) 2^(-e') mod n_i, and g_i = gcd(n_i, u) because 2 is a unit
+//     modulo the odd n_i.
+// Products of up to kSchoolMax words are formed schoolbook, one CTA per group
+// of products; longer ones by number-theoretic transforms of the 32-bit words
+// modulo three primes p = c 2^e + 1 (2013265921, 3221225473, 3489660929; every
+// column of a product of operands of up to 2^26 words is below their
+// product), recombined by Garner's method, with the carries resolved by a
+// carry-lookahead scan.  Every multiplication takes an optional addend, a
+// complemented operand and an output slice, which the Newton steps and the
+// remainder step need.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "bgcd.cuh"
+#include "mont.cuh"
+#include "rsa_gb300.h"
+#include "runtime_internal.h"
+
+namespace rsagpu {
+namespace tree {
+
+constexpr uint32_t kPrime[3] = {2013265921u, 3221225473u, 3489660929u};
+constexpr uint32_t kMaxLog = 27;            // transforms of up to 2^27 words (2-adic order of the first prime)
+constexpr uint32_t kTile = 4096;            // transform stages done in shared memory: blocks of up to 4096 words
+constexpr uint32_t kSchoolMax = 1024;       // products of at most this many words: schoolbook
+constexpr uint32_t kCarryWords = 16;        // words per thread of the carry scan
+constexpr uint32_t kCarryThreads = 256;
+constexpr uint32_t kCarryBlock = kCarryWords * kCarryThreads;
+
+// Per-prime constants of one multiplication (values in Montgomery form, R = 2^32).
+struct Primes {
+  uint32_t p[3], pinv[3];                   // p, p^-1 mod 2^32
+  uint32_t scale[3];                        // n^-1 R^2 mod p: undoes the transform's factor n and one R^-1
+  uint32_t inv12;                           // p1^-1 mod p2 (Montgomery form, modulo p2)
+  uint32_t p1m3;                            // p1 mod p3 (Montgomery form, modulo p3)
+  uint32_t inv123;                          // (p1 p2)^-1 mod p3 (Montgomery form, modulo p3)
+  const uint32_t *tw[3], *itw[3];           // nested twiddle tables: tw[len + j] = w_(2 len)^j R mod p
+};
+
+// Operand i of a batch: row (i >> shift) at p + row * stride, `words` words
+// (zero beyond), complemented bitwise when flip is set.
+struct Opnd {
+  const uint32_t *p;
+  uint64_t stride;
+  uint32_t shift, words, flip;
+};
+
+// Output of product i: words [lo, hi) of the result at p + i * stride.
+struct Out {
+  uint32_t *p;
+  uint64_t stride;
+  uint32_t lo, hi;
+};
+
+__device__ __forceinline__ uint32_t opnd_word(const Opnd &o, uint64_t i, uint32_t j) {
+  if (j >= o.words) return 0u;
+  const uint32_t w = o.p[(i >> o.shift) * o.stride + j];
+  return o.flip ? ~w : w;
+}
+
+// Montgomery product a b R^-1 mod p for a, b < p < 2^32: with m = lo(ab) p^-1,
+// ab - mp is a multiple of 2^32 and its high word hi(ab) - hi(mp) lies in (-p, p).
+__device__ __forceinline__ uint32_t mmul(uint32_t a, uint32_t b, uint32_t p, uint32_t pinv) {
+  const uint64_t t = (uint64_t)a * b;
+  const uint32_t m = (uint32_t)t * pinv;
+  const uint32_t mh = __umulhi(m, p);
+  const uint32_t th = (uint32_t)(t >> 32);
+  return th >= mh ? th - mh : th - mh + p;
+}
+
+// a + b mod p for a, b < p (the sum may wrap 2^32; then it is above p)
+__device__ __forceinline__ uint32_t madd(uint32_t a, uint32_t b, uint32_t p) {
+  const uint32_t s = a + b;
+  return (s < a || s >= p) ? s - p : s;
+}
+
+__device__ __forceinline__ uint32_t msub(uint32_t a, uint32_t b, uint32_t p) {
+  const uint32_t d = a - b;
+  return a < b ? d + p : d;
+}
+
+// ------------------------------------------------------------------ twiddles
+
+// tw[i] for 1 <= i < nmax: i = len + j (len the power of two below i) holds
+// w_(2 len)^j = root^(j nmax / (2 len)) with root of order nmax, in
+// Montgomery form; itw the same for root^-1.  One table serves every
+// transform length up to nmax.
+__global__ void twiddle_kernel(uint32_t *tw, uint32_t *itw, uint32_t nmax, uint32_t p, uint32_t pinv,
+                               uint32_t root_m, uint32_t iroot_m, uint32_t one_m) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nmax; i += gridDim.x * blockDim.x) {
+    if (i == 0) {
+      tw[0] = 0u;
+      itw[0] = 0u;
+      continue;
+    }
+    const uint32_t len = 1u << (31 - __clz(i));
+    uint32_t e = (i - len) * (nmax / (2u * len));
+    uint32_t r = one_m, ir = one_m, b = root_m, ib = iroot_m;
+    while (e) {
+      if (e & 1u) {
+        r = mmul(r, b, p, pinv);
+        ir = mmul(ir, ib, p, pinv);
+      }
+      b = mmul(b, b, p, pinv);
+      ib = mmul(ib, ib, p, pinv);
+      e >>= 1;
+    }
+    tw[i] = r;
+    itw[i] = ir;
+  }
+}
+
+// ------------------------------------------------------------------ schoolbook products
+
+// Products of nc = na + nb <= kSchoolMax words: tpp threads per product, ppb
+// products per CTA of 128 threads.  Columns c = sum_j a_j b_(c-j) as 96-bit
+// sums (round robin over the product's threads), then one thread per product
+// adds the columns' three words and the addend with a running carry and
+// stores words [lo, hi).
+__global__ void __launch_bounds__(128) school_kernel(Opnd A, Opnd B, Opnd D, Out O, uint64_t cnt, uint32_t tpp,
+                                                     uint32_t ppb) {
+  extern __shared__ uint32_t sm[];
+  const uint32_t na = A.words, nb = B.words, nc = na + nb;
+  const uint32_t slot = threadIdx.x / tpp, lt = threadIdx.x % tpp;
+  const uint64_t i = (uint64_t)blockIdx.x * ppb + slot;
+  const bool live = i < cnt;
+  uint32_t *sa = sm + (size_t)slot * (4 * nc);
+  uint32_t *sb = sa + na;
+  uint32_t *clo = sb + nb, *cmid = clo + nc, *chi = cmid + nc;
+  if (live) {
+    for (uint32_t j = lt; j < na; j += tpp) sa[j] = opnd_word(A, i, j);
+    for (uint32_t j = lt; j < nb; j += tpp) sb[j] = opnd_word(B, i, j);
+  }
+  __syncthreads();
+  if (live) {
+    for (uint32_t c = lt; c < nc; c += tpp) {
+      const uint32_t j0 = c + 1 > nb ? c + 1 - nb : 0u;
+      const uint32_t j1 = c < na ? c : na - 1;
+      uint64_t s0 = 0;
+      uint32_t s1 = 0;
+      for (uint32_t j = j0; j <= j1 && j0 <= j1; ++j) {
+        const uint64_t pr = (uint64_t)sa[j] * sb[c - j];
+        s0 += pr;
+        s1 += s0 < pr ? 1u : 0u;
+      }
+      clo[c] = (uint32_t)s0;
+      cmid[c] = (uint32_t)(s0 >> 32);
+      chi[c] = s1;
+    }
+  }
+  __syncthreads();
+  if (!live || lt != 0) return;
+  uint64_t carry = 0;
+  uint32_t *dst = O.p + i * O.stride;
+  for (uint32_t c = 0; c < O.hi; ++c) {
+    uint64_t v = carry + opnd_word(D, i, c);
+    if (c < nc) v += clo[c];
+    if (c >= 1 && c - 1 < nc) v += cmid[c - 1];
+    if (c >= 2 && c - 2 < nc) v += chi[c - 2];
+    if (c >= O.lo) dst[c - O.lo] = (uint32_t)v;
+    carry = v >> 32;
+  }
+}
+
+// ------------------------------------------------------------------ transforms
+// Buffers hold the three primes' arrays back to back (prime k at k * E), each
+// `cnt` transforms of length n, so blockIdx.y selects the prime.  Forward:
+// decimation in frequency (natural order in, bit-reversed out); inverse:
+// decimation in time (bit-reversed in, natural out) with the inverse roots,
+// so no permutation is needed between them.
+
+// F_k[i n + j] = word j of operand i mod p_k (zero for j >= words).
+__global__ void ntt_load_kernel(Opnd X, uint32_t *F, uint64_t E, uint32_t logn) {
+  const uint32_t p0 = kPrime[0], p1 = kPrime[1], p2 = kPrime[2];
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t w = opnd_word(X, e >> logn, (uint32_t)(e & ((1ull << logn) - 1)));
+    F[e] = w % p0;
+    F[E + e] = w % p1;
+    F[2 * E + e] = w % p2;
+  }
+}
+
+// Two decimation-in-frequency stages (len = 2h, then h) over quads
+// x0..x3 = F[base + j + {0, h, 2h, 3h}], base = 4h * block, j < h.
+__global__ void dif4_kernel(uint32_t *F, uint64_t E, uint32_t logh, Primes P) {
+  const uint32_t k = blockIdx.y, p = P.p[k], pinv = P.pinv[k];
+  uint32_t *f = F + k * E;
+  const uint32_t *tw = P.tw[k];
+  const uint32_t h = 1u << logh, len = 2u * h;
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E / 4; q += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t j = (uint32_t)(q & (h - 1));
+    const uint64_t b = ((q >> logh) << (logh + 2)) + j;
+    const uint32_t x0 = f[b], x1 = f[b + h], x2 = f[b + 2 * h], x3 = f[b + 3 * h];
+    const uint32_t y0 = madd(x0, x2, p), y2 = mmul(msub(x0, x2, p), tw[len + j], p, pinv);
+    const uint32_t y1 = madd(x1, x3, p), y3 = mmul(msub(x1, x3, p), tw[len + j + h], p, pinv);
+    const uint32_t wh = tw[h + j];
+    f[b] = madd(y0, y1, p);
+    f[b + h] = mmul(msub(y0, y1, p), wh, p, pinv);
+    f[b + 2 * h] = madd(y2, y3, p);
+    f[b + 3 * h] = mmul(msub(y2, y3, p), wh, p, pinv);
+  }
+}
+
+// One decimation-in-frequency stage of half-length len = 2^logl.
+__global__ void dif2_kernel(uint32_t *F, uint64_t E, uint32_t logl, Primes P) {
+  const uint32_t k = blockIdx.y, p = P.p[k], pinv = P.pinv[k];
+  uint32_t *f = F + k * E;
+  const uint32_t *tw = P.tw[k];
+  const uint32_t len = 1u << logl;
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E / 2; q += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t j = (uint32_t)(q & (len - 1));
+    const uint64_t b = ((q >> logl) << (logl + 1)) + j;
+    const uint32_t u = f[b], v = f[b + len];
+    f[b] = madd(u, v, p);
+    f[b + len] = mmul(msub(u, v, p), tw[len + j], p, pinv);
+  }
+}
+
+// Two decimation-in-time stages (h, then len = 2h) over the same quads.
+__global__ void dit4_kernel(uint32_t *F, uint64_t E, uint32_t logh, Primes P) {
+  const uint32_t k = blockIdx.y, p = P.p[k], pinv = P.pinv[k];
+  uint32_t *f = F + k * E;
+  const uint32_t *itw = P.itw[k];
+  const uint32_t h = 1u << logh, len = 2u * h;
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E / 4; q += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t j = (uint32_t)(q & (h - 1));
+    const uint64_t b = ((q >> logh) << (logh + 2)) + j;
+    const uint32_t x0 = f[b], x1 = f[b + h], x2 = f[b + 2 * h], x3 = f[b + 3 * h];
+    const uint32_t wh = itw[h + j];
+    const uint32_t v1 = mmul(x1, wh, p, pinv), v3 = mmul(x3, wh, p, pinv);
+    const uint32_t y0 = madd(x0, v1, p), y1 = msub(x0, v1, p);
+    const uint32_t y2 = madd(x2, v3, p), y3 = msub(x2, v3, p);
+    const uint32_t v2 = mmul(y2, itw[len + j], p, pinv), w3 = mmul(y3, itw[len + j + h], p, pinv);
+    f[b] = madd(y0, v2, p);
+    f[b + 2 * h] = msub(y0, v2, p);
+    f[b + h] = madd(y1, w3, p);
+    f[b + 3 * h] = msub(y1, w3, p);
+  }
+}
+
+__global__ void dit2_kernel(uint32_t *F, uint64_t E, uint32_t logl, Primes P) {
+  const uint32_t k = blockIdx.y, p = P.p[k], pinv = P.pinv[k];
+  uint32_t *f = F + k * E;
+  const uint32_t *itw = P.itw[k];
+  const uint32_t len = 1u << logl;
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E / 2; q += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t j = (uint32_t)(q & (len - 1));
+    const uint64_t b = ((q >> logl) << (logl + 1)) + j;
+    const uint32_t u = f[b], v = mmul(f[b + len], itw[len + j], p, pinv);
+    f[b] = madd(u, v, p);
+    f[b + len] = msub(u, v, p);
+  }
+}
+
+// The stages of half-length below `tile` (a power of two <= kTile dividing
+// the transform length) in shared memory, one tile per CTA of 512 threads:
+// forward (dir 0) len = tile/2 .. 1, inverse (dir 1) len = 1 .. tile/2.
+__global__ void __launch_bounds__(512) ntt_tile_kernel(uint32_t *F, uint64_t E, uint32_t tile, int dir, Primes P) {
+  __shared__ uint32_t s[kTile];
+  const uint32_t k = blockIdx.y, p = P.p[k], pinv = P.pinv[k];
+  uint32_t *f = F + k * E + (uint64_t)blockIdx.x * tile;
+  const uint32_t *tw = dir ? P.itw[k] : P.tw[k];
+  for (uint32_t x = threadIdx.x; x < tile; x += blockDim.x) s[x] = f[x];
+  const uint32_t half = tile / 2;
+  for (uint32_t st = 0; (1u << st) < tile; ++st) {
+    const uint32_t logl = dir ? st : (31 - __clz(half)) - st;
+    const uint32_t len = 1u << logl;
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < half; q += blockDim.x) {
+      const uint32_t j = q & (len - 1);
+      const uint32_t b = ((q >> logl) << (logl + 1)) + j;
+      const uint32_t w = tw[len + j];
+      const uint32_t u = s[b], v = s[b + len];
+      if (dir == 0) {
+        s[b] = madd(u, v, p);
+        s[b + len] = mmul(msub(u, v, p), w, p, pinv);
+      } else {
+        const uint32_t vw = mmul(v, w, p, pinv);
+        s[b] = madd(u, vw, p);
+        s[b + len] = msub(u, vw, p);
+      }
+    }
+  }
+  __syncthreads();
+  for (uint32_t x = threadIdx.x; x < tile; x += blockDim.x) f[x] = s[x];
+}
+
+// Pointwise products FA *= FB (or FA *= FA), each with one factor R^-1.
+__global__ void pointwise_kernel(uint32_t *FA, const uint32_t *FB, uint64_t E, Primes P) {
+  const uint32_t k = blockIdx.y, p = P.p[k], pinv = P.pinv[k];
+  uint32_t *a = FA + k * E;
+  const uint32_t *b = FB ? FB + k * E : a;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (uint64_t)gridDim.x * blockDim.x)
+    a[e] = mmul(a[e], b[e], p, pinv);
+}
+
+// ------------------------------------------------------------------ recombination and carries
+
+// Column j of product i as a 96-bit integer (three words): the residues,
+// scaled by n^-1 R^2, recombined by Garner's method
+// x = v1 + p1 v2 + p1 p2 v3 (below p1 p2 p3 < 2^95).
+__device__ __forceinline__ void column(const uint32_t *F, uint64_t E, uint64_t at, const Primes &P, uint32_t &lo,
+                                       uint32_t &mid, uint32_t &hi) {
+  const uint32_t p1 = P.p[0], p2 = P.p[1], p3 = P.p[2];
+  const uint32_t r1 = mmul(F[at], P.scale[0], p1, P.pinv[0]);
+  const uint32_t r2 = mmul(F[E + at], P.scale[1], p2, P.pinv[1]);
+  const uint32_t r3 = mmul(F[2 * E + at], P.scale[2], p3, P.pinv[2]);
+  const uint32_t v1 = r1;                                             // < p1 < p2 < p3
+  const uint32_t v2 = mmul(msub(r2, v1, p2), P.inv12, p2, P.pinv[1]);
+  const uint32_t t3 = madd(v1, mmul(v2, P.p1m3, p3, P.pinv[2]), p3);
+  const uint32_t v3 = mmul(msub(r3, t3, p3), P.inv123, p3, P.pinv[2]);
+  const uint64_t a = (uint64_t)p1 * v2 + v1;
+  const uint64_t p12 = (uint64_t)p1 * p2;
+  const uint64_t blo = p12 * v3;
+  uint32_t bhi = (uint32_t)__umul64hi(p12, v3);
+  const uint64_t s = blo + a;
+  bhi += s < a ? 1u : 0u;
+  lo = (uint32_t)s;
+  mid = (uint32_t)(s >> 32);
+  hi = bhi;
+}
+
+// Word c of product i before carries between words: lo(x_c) + mid(x_(c-1)) +
+// hi(x_(c-2)) + d_c, below 2^34.  Columns past the transform length are 0.
+struct WordSrc {
+  const uint32_t *F;
+  uint64_t E;
+  uint32_t logn;
+  Primes P;
+  Opnd D;
+};
+
+// The 16 words of one thread: base value w (low 32 bits of each word sum plus
+// the previous word's overflow) and the generate / propagate masks of the
+// carry into the next word: g bit m set when word m overflows on its own, p
+// bit m set when it is all ones (overflows only with a carry in).
+__device__ __forceinline__ void thread_words(const WordSrc &S, uint64_t i, uint32_t c0, uint32_t (&w)[kCarryWords],
+                                             uint32_t &g, uint32_t &pm) {
+  const uint32_t n = 1u << S.logn;
+  const uint64_t row = i << S.logn;
+  // columns c0-3 .. c0+15
+  uint32_t lo[kCarryWords + 3], mid[kCarryWords + 3], hi[kCarryWords + 3];
+#pragma unroll
+  for (int m = 0; m < (int)kCarryWords + 3; ++m) {
+    const int64_t c = (int64_t)c0 + m - 3;
+    if (c >= 0 && c < (int64_t)n) {
+      column(S.F, S.E, row + (uint64_t)c, S.P, lo[m], mid[m], hi[m]);
+    } else {
+      lo[m] = mid[m] = hi[m] = 0u;
+    }
+  }
+  // word sums s_c = lo_c + mid_(c-1) + hi_(c-2) + d_c for c0-1 .. c0+15
+  uint32_t prev_over = 0;
+  {
+    const int64_t c = (int64_t)c0 - 1;
+    if (c >= 0) {
+      const uint64_t s = (uint64_t)lo[2] + mid[1] + hi[0] + opnd_word(S.D, i, (uint32_t)c);
+      prev_over = (uint32_t)(s >> 32);
+    }
+  }
+  g = 0u;
+  pm = 0u;
+#pragma unroll
+  for (int m = 0; m < (int)kCarryWords; ++m) {
+    const uint64_t s = (uint64_t)lo[m + 3] + mid[m + 2] + hi[m + 1] + opnd_word(S.D, i, c0 + (uint32_t)m);
+    const uint64_t v = (uint64_t)(uint32_t)s + prev_over;
+    prev_over = (uint32_t)(s >> 32);
+    w[m] = (uint32_t)v;
+    g |= (uint32_t)(v >> 32) << m;
+    pm |= (v == 0xffffffffull ? 1u : 0u) << m;
+  }
+}
+
+// Carry into each of the 16 words given the carry into the first, and the carry out.
+__device__ __forceinline__ uint32_t apply_carries(uint32_t (&w)[kCarryWords], uint32_t g, uint32_t pm, uint32_t cin) {
+  const uint64_t a = (uint64_t)(g | pm), sum = a + g + cin;
+  const uint32_t into = (uint32_t)(sum ^ a ^ g);
+#pragma unroll
+  for (int m = 0; m < (int)kCarryWords; ++m) w[m] += (into >> m) & 1u;
+  return (uint32_t)(sum >> kCarryWords) & 1u;
+}
+
+// Block-level carry functions: each thread's run of 16 words is (G, P)
+// (carry out with no carry in; carry out only with one).  Lane runs combine
+// like the bits of a binary addition a + b + c with a = G|P, b = G: the carry
+// into bit l is bit l of (a + b + c) ^ a ^ b.
+__device__ __forceinline__ void run_gp(uint32_t g, uint32_t pm, uint32_t &G, uint32_t &Pp) {
+  const uint64_t a = (uint64_t)(g | pm);
+  const uint32_t c0 = (uint32_t)((a + g) >> kCarryWords) & 1u;
+  const uint32_t c1 = (uint32_t)((a + g + 1) >> kCarryWords) & 1u;
+  G = c0;
+  Pp = c1 & ~c0 & 1u;
+}
+
+// Carry into this thread's run, given the carry into the block; returns the
+// block's (G, P) through gb/pb when cin_block is ignored (pass 0 and 1).
+__device__ __forceinline__ uint32_t block_carry_in(uint32_t G, uint32_t Pp, uint32_t cin_block, uint32_t *gb,
+                                                   uint32_t *pb) {
+  __shared__ uint32_t wg[kCarryThreads / 32], wp[kCarryThreads / 32];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t gm = __ballot_sync(0xffffffffu, G), pmk = __ballot_sync(0xffffffffu, Pp);
+  const uint64_t a = (uint64_t)(gm | pmk);
+  const uint32_t wg0 = (uint32_t)((a + gm) >> 32), wc1 = (uint32_t)((a + gm + 1) >> 32);
+  if (lane == 0) {
+    wg[warp] = wg0;
+    wp[warp] = wc1 & ~wg0 & 1u;
+  }
+  __syncthreads();
+  uint32_t bgm = 0, bpm = 0;
+  for (uint32_t x = 0; x < kCarryThreads / 32; ++x) {
+    bgm |= wg[x] << x;
+    bpm |= wp[x] << x;
+  }
+  const uint64_t ab = (uint64_t)(bgm | bpm);
+  if (gb) {
+    const uint32_t nw = kCarryThreads / 32;
+    const uint32_t g0 = (uint32_t)((ab + bgm) >> nw) & 1u, g1 = (uint32_t)((ab + bgm + 1) >> nw) & 1u;
+    *gb = g0;
+    *pb = g1 & ~g0 & 1u;
+  }
+  const uint64_t bsum = ab + bgm + cin_block;
+  const uint32_t warp_in = (uint32_t)((bsum ^ ab ^ bgm) >> warp) & 1u;
+  const uint64_t wsum = a + gm + warp_in;
+  return (uint32_t)((wsum ^ a ^ gm) >> lane) & 1u;
+}
+
+// Pass 1: each block's carry function into flags[i * nb + b] (bit 0 generate,
+// bit 1 propagate); one CTA per (product i, block b), i = blockIdx.x / nb.
+__global__ void __launch_bounds__(kCarryThreads) carry_flags_kernel(WordSrc S, uint32_t hi_words, uint32_t nb,
+                                                                    uint8_t *flags) {
+  const uint64_t i = blockIdx.x / nb;
+  const uint32_t b = (uint32_t)(blockIdx.x % nb);
+  const uint32_t c0 = b * kCarryBlock + threadIdx.x * kCarryWords;
+  uint32_t w[kCarryWords], g = 0, pm = 0;
+  if (c0 < hi_words) thread_words(S, i, c0, w, g, pm);
+  uint32_t G, Pp, gb = 0, pb = 0;
+  run_gp(g, pm, G, Pp);
+  (void)block_carry_in(G, Pp, 0u, &gb, &pb);
+  if (threadIdx.x == 0) flags[i * nb + b] = (uint8_t)(gb | (pb << 1));
+}
+
+// Pass 2: one warp per product scans its blocks' carry functions, 32 at a
+// time, and leaves the carry into each block in flags bit 2.
+__global__ void carry_scan_kernel(uint8_t *flags, uint32_t nb, uint64_t cnt) {
+  const uint64_t i = (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (i >= cnt) return;
+  const uint32_t lane = threadIdx.x & 31;
+  uint8_t *f = flags + i * nb;
+  uint32_t cin = 0;
+  for (uint32_t base = 0; base < nb; base += 32) {
+    const uint32_t b = base + lane;
+    const uint32_t v = b < nb ? f[b] : 0u;
+    const uint32_t gm = __ballot_sync(0xffffffffu, v & 1u), pmk = __ballot_sync(0xffffffffu, (v >> 1) & 1u);
+    const uint64_t a = (uint64_t)(gm | pmk), sum = a + gm + cin;
+    const uint32_t into = (uint32_t)((sum ^ a ^ gm) >> lane) & 1u;
+    if (b < nb) f[b] = (uint8_t)(v | (into << 2));
+    cin = (uint32_t)(sum >> 32) & 1u;
+  }
+}
+
+// Pass 3: words with their carries; words [lo, hi) are stored.
+__global__ void __launch_bounds__(kCarryThreads) carry_store_kernel(WordSrc S, Out O, uint32_t nb,
+                                                                    const uint8_t *flags) {
+  const uint64_t i = blockIdx.x / nb;
+  const uint32_t b = (uint32_t)(blockIdx.x % nb);
+  const uint32_t c0 = b * kCarryBlock + threadIdx.x * kCarryWords;
+  uint32_t w[kCarryWords], g = 0, pm = 0;
+  if (c0 < O.hi) thread_words(S, i, c0, w, g, pm);
+  uint32_t G, Pp;
+  run_gp(g, pm, G, Pp);
+  const uint32_t cin_block = (flags[i * nb + b] >> 2) & 1u;
+  const uint32_t cin = block_carry_in(G, Pp, cin_block, nullptr, nullptr);
+  if (c0 >= O.hi) return;
+  (void)apply_carries(w, g, pm, cin);
+  uint32_t *dst = O.p + i * O.stride;
+#pragma unroll
+  for (int m = 0; m < (int)kCarryWords; ++m) {
+    const uint32_t c = c0 + (uint32_t)m;
+    if (c >= O.lo && c < O.hi) dst[c - O.lo] = w[m];
+  }
+}
+
+// ------------------------------------------------------------------ tree kernels
+
+__device__ __forceinline__ bool valid_row(const uint32_t *row, uint32_t L) {
+  uint32_t hi = 0;
+  for (uint32_t j = 1; j < L; ++j) hi |= row[j];
+  return (row[0] & 1u) && (hi != 0u || row[0] >= 3u);
+}
+
+// X_0: row i = n_i when valid, else 1 (also the padding rows i >= count).
+__global__ void leaves_kernel(const uint32_t *mods, uint64_t count, uint64_t K, uint32_t L, uint32_t *X0) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (uint64_t)gridDim.x * blockDim.x) {
+    const bool ok = i < count && valid_row(mods + i * L, L);
+    for (uint32_t j = 0; j < L; ++j) X0[i * L + j] = ok ? mods[i * L + j] : (j == 0 ? 1u : 0u);
+  }
+}
+
+// First word of mu: -y_0^-1 mod 2^32 (Newton's iteration on one word).
+__global__ void mu_word_kernel(const uint32_t *Y, uint64_t ys, uint32_t *mu, uint64_t ms, uint64_t cnt) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t y0 = Y[i * ys];
+    uint32_t inv = y0;
+    for (int k = 0; k < 5; ++k) inv *= 2u - y0 * inv;
+    mu[i * ms] = 0u - inv;
+  }
+}
+
+// Z_T: the root X_T in a row of zs words, zero above its s words.
+__global__ void root_kernel(const uint32_t *X, uint64_t s, uint32_t *Z, uint64_t zs) {
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < zs; j += (uint64_t)gridDim.x * blockDim.x)
+    Z[j] = j < s ? X[j] : 0u;
+}
+
+constexpr int kLeafThreads = 64;
+
+// Per-thread shared-memory words of the leaf kernel: n (L), N = n^2 (2L), the
+// reduced value r (2L + 2), the quotient u (L); column layout (word w of
+// thread x at w * blockDim + x).
+__host__ __device__ constexpr uint32_t leaf_words(uint32_t L) { return 6 * L + 2; }
+
+// One modulus per thread: z = Z(node of i at level t0) 2^(-32M) mod n_i^2 by
+// word-serial Montgomery reduction (window of 2L + 2 words in registers),
+// one conditional subtraction, u = z / n_i exactly (word by word from the
+// bottom: d = r_j n_0^-1, r -= d n_i 2^(32j)), then g_i = gcd(n_i, u).
+template <int L>
+__global__ void __launch_bounds__(kLeafThreads) tree_leaf_kernel(const uint32_t *mods, uint64_t count,
+                                                                 const uint32_t *Z, uint64_t zs, uint32_t M,
+                                                                 uint32_t t0, uint32_t *gcds, int32_t *flags) {
+  extern __shared__ uint32_t sm[];
+  const uint32_t bd = blockDim.x, x = threadIdx.x;
+  uint32_t *sn = sm + x, *sN = sm + (size_t)L * bd + x, *sr = sm + (size_t)3 * L * bd + x;
+  uint32_t *su = sm + (size_t)(5 * L + 2) * bd + x;
+  const uint64_t i = (uint64_t)blockIdx.x * bd + x;
+  const bool live = i < count;
+  const uint64_t row = live ? i : count - 1;
+  const uint32_t *nrow = mods + row * L;
+  const bool ok = live && valid_row(nrow, L);
+  for (uint32_t w = 0; w < L; ++w) sn[w * bd] = ok ? nrow[w] : (w == 0 ? 1u : 0u);
+  // N = n^2, rows of the schoolbook product with a running carry
+  for (uint32_t w = 0; w < 2 * L; ++w) sN[w * bd] = 0u;
+  for (uint32_t j = 0; j < L; ++j) {
+    const uint32_t nj = sn[j * bd];
+    uint32_t c = 0;
+    for (uint32_t m = 0; m < L; ++m) {
+      const uint64_t acc = (uint64_t)nj * sn[m * bd] + sN[(j + m) * bd] + c;
+      sN[(j + m) * bd] = (uint32_t)acc;
+      c = (uint32_t)(acc >> 32);
+    }
+    sN[(j + L) * bd] = c;
+  }
+  const uint32_t N0 = sN[0];
+  uint32_t np = N0;
+  for (int k = 0; k < 5; ++k) np *= 2u - N0 * np;
+  np = 0u - np;
+  // word-serial reduction of the node's M words
+  const uint32_t *z = Z + (row >> t0) * zs;
+  uint32_t t[2 * L + 2];
+#pragma unroll
+  for (int w = 0; w < 2 * L; ++w) t[w] = (uint32_t)w < M ? z[w] : 0u;
+  t[2 * L] = 0u;
+  t[2 * L + 1] = 0u;
+#pragma unroll 1
+  for (uint32_t s = 0; s < M; ++s) {
+    const uint32_t q = t[0] * np;
+    uint64_t acc = (uint64_t)q * sN[0] + t[0];
+    uint32_t c = (uint32_t)(acc >> 32);
+#pragma unroll
+    for (int j = 1; j < 2 * L; ++j) {
+      acc = (uint64_t)q * sN[j * bd] + t[j] + c;
+      t[j - 1] = (uint32_t)acc;
+      c = (uint32_t)(acc >> 32);
+    }
+    acc = (uint64_t)t[2 * L] + c;
+    t[2 * L - 1] = (uint32_t)acc;
+    t[2 * L] = t[2 * L + 1] + (uint32_t)(acc >> 32);
+    t[2 * L + 1] = 0u;
+    const uint32_t nx = 2 * L + s;
+    if (nx < M) {
+      acc = (uint64_t)t[2 * L - 1] + z[nx];
+      t[2 * L - 1] = (uint32_t)acc;
+      t[2 * L] += (uint32_t)(acc >> 32);
+    }
+  }
+  // t <= N: subtract N once when t >= N
+  {
+    uint32_t d[2 * L];
+    uint32_t br = 0;
+#pragma unroll
+    for (int w = 0; w < 2 * L; ++w) {
+      const uint32_t nw = sN[w * bd];
+      const uint64_t sub = (uint64_t)nw + br;
+      d[w] = t[w] - (uint32_t)sub;
+      br = ((uint64_t)t[w] < sub) ? 1u : 0u;
+    }
+    const bool ge = t[2 * L] != 0u || br == 0u;
+#pragma unroll
+    for (int w = 0; w < 2 * L; ++w) sr[w * bd] = ge ? d[w] : t[w];
+  }
+  // u = r / n exactly
+  const uint32_t n0 = sn[0];
+  uint32_t inv = n0;
+  for (int k = 0; k < 5; ++k) inv *= 2u - n0 * inv;
+  for (uint32_t j = 0; j < L; ++j) {
+    const uint32_t dj = sr[j * bd] * inv;
+    su[j * bd] = dj;
+    uint32_t br = 0;
+    for (uint32_t m = 0; m < L; ++m) {
+      const uint64_t pr = (uint64_t)dj * sn[m * bd] + br;
+      const uint32_t r = sr[(j + m) * bd], lo = (uint32_t)pr;
+      sr[(j + m) * bd] = r - lo;
+      br = (uint32_t)(pr >> 32) + (r < lo ? 1u : 0u);
+    }
+    for (uint32_t m = j + L; m < 2 * L && br; ++m) {
+      const uint32_t r = sr[m * bd];
+      sr[m * bd] = r - br;
+      br = r < br ? 1u : 0u;
+    }
+  }
+  uint32_t a[L], b[L];
+#pragma unroll
+  for (int w = 0; w < L; ++w) {
+    a[w] = sn[w * bd];
+    b[w] = ok ? su[w * bd] : 0u;
+  }
+  binary_gcd<L>(a, b);
+  if (!live) return;
+  uint32_t hi = 0, diff = 0;
+#pragma unroll
+  for (int w = 0; w < L; ++w) {
+    diff |= a[w] ^ nrow[w];
+    if (w) hi |= a[w];
+  }
+  if (gcds) {
+    uint32_t *dst = gcds + i * L;
+#pragma unroll
+    for (int w = 0; w < L; ++w) dst[w] = ok ? a[w] : 0u;
+  }
+  if (flags) flags[i] = !ok ? -1 : (hi == 0u && a[0] == 1u) ? 0 : (diff == 0u ? 2 : 1);
+}
+
+}  // namespace tree
+}  // namespace rsagpu
+
+// ------------------------------------------------------------------ host side
+
+namespace rsagpu {
+namespace tree {
+namespace {
+
+uint32_t powmod(uint64_t b, uint64_t e, uint32_t p) {
+  uint64_t r = 1;
+  b %= p;
+  while (e) {
+    if (e & 1) r = r * b % p;
+    b = b * b % p;
+    e >>= 1;
+  }
+  return (uint32_t)r;
+}
+
+uint32_t to_mont(uint32_t x, uint32_t p) { return (uint32_t)(((uint64_t)x << 32) % p); }
+
+// Smallest generator of the multiplicative group mod p: g^((p-1)/f) != 1 for
+// every prime factor f of p - 1 (found by trial division).
+uint32_t generator(uint32_t p) {
+  std::vector<uint32_t> fs;
+  uint32_t m = p - 1;
+  for (uint32_t f = 2; (uint64_t)f * f <= m; ++f) {
+    if (m % f) continue;
+    fs.push_back(f);
+    while (m % f == 0) m /= f;
+  }
+  if (m > 1) fs.push_back(m);
+  for (uint32_t g = 2;; ++g) {
+    bool ok = true;
+    for (uint32_t f : fs) ok = ok && powmod(g, (p - 1) / f, p) != 1;
+    if (ok) return g;
+  }
+}
+
+uint32_t inv32(uint32_t p) {
+  uint32_t inv = p;
+  for (int k = 0; k < 5; ++k) inv *= 2u - p * inv;
+  return inv;
+}
+
+int ilog2(uint64_t n) {
+  int l = 0;
+  while ((1ull << (l + 1)) <= n) ++l;
+  return l;
+}
+
+uint64_t pow2_at_least(uint64_t n) {
+  uint64_t v = 1;
+  while (v < n) v <<= 1;
+  return v;
+}
+
+// Device buffers of one scan, as word offsets into one arena.
+struct Plan {
+  uint32_t L = 0, T = 0, t0 = 0;
+  uint64_t K = 0, KL = 0;
+  uint64_t nmax = 0;                         // longest transform
+  std::vector<uint64_t> x_off, y_off, mu_off;  // per level
+  uint64_t z_off[2] = {0, 0}, q_off = 0, h_off = 0, fa_off = 0, fb_off = 0, flags_off = 0;
+  uint64_t words = 0;                        // arena size in words
+};
+
+Plan make_plan(uint32_t L, uint64_t count, uint32_t t0_req) {
+  Plan P;
+  P.L = L;
+  P.K = pow2_at_least(std::max<uint64_t>(count, 2));
+  P.T = (uint32_t)ilog2(P.K);
+  P.t0 = std::min(t0_req, P.T);
+  P.KL = P.K * L;
+  const uint64_t KL = P.KL;
+  uint64_t at = 0;
+  P.x_off.resize(P.T + 1);
+  for (uint32_t t = 0; t <= P.T; ++t) {
+    P.x_off[t] = at;
+    at += KL;
+  }
+  P.y_off.assign(P.T + 1, 0);
+  P.mu_off.assign(P.T + 1, 0);
+  for (uint32_t t = P.t0; t < P.T; ++t) {
+    P.y_off[t] = at;
+    at += 2 * KL;
+    P.mu_off[t] = at;
+    at += 2 * KL;
+  }
+  const uint64_t zwords = 2 * KL + 4 * (P.K >> P.t0) + 4;
+  P.z_off[0] = at;
+  at += zwords;
+  P.z_off[1] = at;
+  at += zwords;
+  P.q_off = at;
+  at += 2 * KL;
+  P.h_off = at;
+  at += KL;
+  P.fa_off = at;
+  at += 3 * 4 * KL;
+  P.fb_off = at;
+  at += 3 * 4 * KL;
+  P.flags_off = at;
+  at += (4 * KL / kCarryBlock + 2 * P.K + 64) / 4 + 1;
+  P.words = (at + 3) / 4 * 4;
+  // longest transform: the remainder step and the Newton step of level T - 1 (4 s_(T-1) words)
+  P.nmax = std::max<uint64_t>(2 * KL, kTile);
+  return P;
+}
+
+struct Runner {
+  Ctx *c;
+  cudaStream_t s;
+  uint32_t *base;
+  const Plan &P;
+  Primes pr;                                 // tables and Garner constants; scale set per product
+  uint32_t root_m[3], iroot_m[3];
+  int launches = 0;
+
+  uint32_t *at(uint64_t off) const { return base + off; }
+
+  int grid_for(uint64_t work, int threads) const {
+    const uint64_t want = (work + threads - 1) / threads;
+    const uint64_t cap = (uint64_t)c->sm_count * 8;
+    return (int)std::max<uint64_t>(1, std::min(want, cap));
+  }
+
+  // out = words [O.lo, O.hi) of A_i * B_i + D_i for i < cnt (B ignored when square)
+  int mul(const Opnd &A, const Opnd &B, const Opnd &D, const Out &O, uint64_t cnt, bool square) {
+    if (cnt == 0) return 0;
+    const uint32_t na = A.words, nb = square ? A.words : B.words, nc = na + nb;
+    if (nc <= kSchoolMax) {
+      uint32_t tpp = 1;
+      while (tpp < 128 && 2 * tpp < nc) tpp *= 2;
+      const uint32_t ppb = 128 / tpp;
+      const size_t smem = (size_t)ppb * 4 * nc * 4;
+      const uint64_t grid = (cnt + ppb - 1) / ppb;
+      school_kernel<<<(unsigned)grid, 128, smem, s>>>(A, square ? A : B, D, O, cnt, tpp, ppb);
+      ++launches;
+      return 0;
+    }
+    const uint64_t n = pow2_at_least(nc);
+    const uint32_t logn = (uint32_t)ilog2(n);
+    if (logn > kMaxLog) return set_error(RSA_ERR_ARG, "batch gcd tree: product above 2^27 words");
+    const uint64_t E = cnt * n;
+    if (E > 4 * P.KL) return set_error(RSA_ERR_ARG, "batch gcd tree: transform scratch exceeded");
+    for (int k = 0; k < 3; ++k) {
+      const uint32_t p = kPrime[k];
+      const uint32_t ninv = p - (uint32_t)((p - 1) / n);
+      const uint32_t r2 = powmod(to_mont(1, p), 2, p);
+      pr.scale[k] = (uint32_t)((uint64_t)ninv * r2 % p);
+    }
+    uint32_t *FA = at(P.fa_off), *FB = at(P.fb_off);
+    const uint32_t tile = (uint32_t)std::min<uint64_t>(n, kTile);
+    const int logt = ilog2(tile);
+    const int G = (int)logn - logt;
+    auto load = [&](const Opnd &X, uint32_t *F) {
+      ntt_load_kernel<<<grid_for(E, 256), 256, 0, s>>>(X, F, E, logn);
+      ++launches;
+    };
+    auto forward = [&](uint32_t *F) {
+      int g = G;
+      uint32_t logl = logn - 1;
+      while (g >= 2) {
+        dif4_kernel<<<dim3(grid_for(E / 4, 256), 3), 256, 0, s>>>(F, E, logl - 1, pr);
+        logl -= 2;
+        g -= 2;
+        ++launches;
+      }
+      if (g == 1) {
+        dif2_kernel<<<dim3(grid_for(E / 2, 256), 3), 256, 0, s>>>(F, E, logl, pr);
+        ++launches;
+      }
+      ntt_tile_kernel<<<dim3((unsigned)(E / tile), 3), 512, 0, s>>>(F, E, tile, 0, pr);
+      ++launches;
+    };
+    load(A, FA);
+    forward(FA);
+    if (!square) {
+      load(B, FB);
+      forward(FB);
+    }
+    pointwise_kernel<<<dim3(grid_for(E, 256), 3), 256, 0, s>>>(FA, square ? nullptr : FB, E, pr);
+    ntt_tile_kernel<<<dim3((unsigned)(E / tile), 3), 512, 0, s>>>(FA, E, tile, 1, pr);
+    launches += 2;
+    {
+      int g = G;
+      uint32_t logl = (uint32_t)logt;
+      if (g & 1) {
+        dit2_kernel<<<dim3(grid_for(E / 2, 256), 3), 256, 0, s>>>(FA, E, logl, pr);
+        ++logl;
+        --g;
+        ++launches;
+      }
+      while (g >= 2) {
+        dit4_kernel<<<dim3(grid_for(E / 4, 256), 3), 256, 0, s>>>(FA, E, logl, pr);
+        logl += 2;
+        g -= 2;
+        ++launches;
+      }
+    }
+    WordSrc S{FA, E, logn, pr, D};
+    const uint32_t nbk = (O.hi + kCarryBlock - 1) / kCarryBlock;
+    uint8_t *flags = reinterpret_cast<uint8_t *>(at(P.flags_off));
+    const uint64_t blocks = cnt * nbk;
+    carry_flags_kernel<<<(unsigned)blocks, kCarryThreads, 0, s>>>(S, O.hi, nbk, flags);
+    carry_scan_kernel<<<(unsigned)((cnt + 3) / 4), 128, 0, s>>>(flags, nbk, cnt);
+    carry_store_kernel<<<(unsigned)blocks, kCarryThreads, 0, s>>>(S, O, nbk, flags);
+    launches += 3;
+    return 0;
+  }
+};
+
+Opnd opnd(const uint32_t *p, uint64_t stride, uint32_t words, uint32_t shift = 0, uint32_t flip = 0) {
+  return Opnd{p, stride, shift, words, flip};
+}
+
+const Opnd kNone{nullptr, 0, 0, 0, 0};
+
+}  // namespace
+}  // namespace tree
+}  // namespace rsagpu
+
+namespace rsagpu {
+
+// Lowest level of the remainder tree (its nodes hold 2^t0 moduli; the leaf
+// kernel reduces a node's value modulo each n_i^2 word by word).
+static uint32_t tree_leaf_level() {
+  const char *v = std::getenv("RSAGPU_GCD_TREE_T0");
+  const int t = v ? std::atoi(v) : 2;
+  return (uint32_t)std::min(std::max(t, 0), 6);
+}
+
+uint64_t batch_gcd_tree_bytes(uint32_t L, uint64_t count) {
+  const tree::Plan P = tree::make_plan(L, count, tree_leaf_level());
+  return P.words * 4 + 6 * P.nmax * 4;
+}
+
+int batch_gcd_tree_run(Ctx *c, uint32_t nbits, uint64_t count, const uint32_t *moduli, uint32_t *gcds,
+                       int32_t *flags, cudaStream_t s) {
+  using namespace tree;
+  const uint32_t L = nbits / 32;
+  const Plan P = make_plan(L, count, tree_leaf_level());
+  if (P.nmax > (1ull << kMaxLog)) return set_error(RSA_ERR_ARG, "batch gcd tree: count * modulus words above 2^26");
+  Workspace &w = c->ws(s);
+  int rc;
+  if ((rc = c->ensure(w.gcd_tree, P.words * 4)) || (rc = c->ensure(w.gcd_tw, 6 * P.nmax * 4))) return rc;
+  NvtxRange range("rsa_batch_gcd(tree)");
+  Runner R{c, s, static_cast<uint32_t *>(w.gcd_tree.ptr), P, {}, {}, {}, 0};
+  uint32_t *tw = static_cast<uint32_t *>(w.gcd_tw.ptr);
+  const bool rebuild = w.gcd_tw_ptr != w.gcd_tw.ptr || w.gcd_tw_n < P.nmax;
+  const uint64_t tn = rebuild ? P.nmax : w.gcd_tw_n;      // table stride: the length built
+  for (int k = 0; k < 3; ++k) {
+    const uint32_t p = kPrime[k];
+    R.pr.p[k] = p;
+    R.pr.pinv[k] = inv32(p);
+    R.pr.tw[k] = tw + (2 * k) * tn;
+    R.pr.itw[k] = tw + (2 * k + 1) * tn;
+    if (rebuild) {
+      const uint32_t root = powmod(generator(p), (p - 1) / P.nmax, p);
+      const uint32_t iroot = powmod(root, p - 2, p);
+      twiddle_kernel<<<R.grid_for(P.nmax, 256), 256, 0, s>>>(tw + (2 * k) * tn, tw + (2 * k + 1) * tn,
+                                                             (uint32_t)P.nmax, p, R.pr.pinv[k], to_mont(root, p),
+                                                             to_mont(iroot, p), to_mont(1, p));
+      ++R.launches;
+    }
+  }
+  if (rebuild) {
+    w.gcd_tw_ptr = w.gcd_tw.ptr;
+    w.gcd_tw_n = P.nmax;
+  }
+  {
+    const uint32_t p1 = kPrime[0], p2 = kPrime[1], p3 = kPrime[2];
+    R.pr.inv12 = to_mont(powmod(p1, p2 - 2, p2), p2);
+    R.pr.p1m3 = to_mont(p1 % p3, p3);
+    R.pr.inv123 = to_mont(powmod((uint64_t)(p1 % p3) * (p2 % p3) % p3, p3 - 2, p3), p3);
+  }
+  const uint64_t K = P.K;
+  const uint32_t T = P.T, t0 = P.t0;
+  auto X = [&](uint32_t t) { return R.at(P.x_off[t]); };
+  auto sz = [&](uint32_t t) { return (uint64_t)L << t; };
+  leaves_kernel<<<R.grid_for(K, 256), 256, 0, s>>>(moduli, count, K, L, X(0));
+  ++R.launches;
+  // product tree
+  for (uint32_t t = 0; t < T; ++t) {
+    const uint64_t st = sz(t);
+    if ((rc = R.mul(opnd(X(t), 2 * st, (uint32_t)st), opnd(X(t) + st, 2 * st, (uint32_t)st), kNone,
+                    Out{X(t + 1), 2 * st, 0, (uint32_t)(2 * st)}, K >> (t + 1), false)))
+      return rc;
+  }
+  // squares and mu for the levels of the remainder tree
+  uint32_t *H = R.at(P.h_off);
+  for (uint32_t t = t0; t < T; ++t) {
+    const uint64_t st = sz(t), k = 2 * st, cnt = K >> t;
+    uint32_t *Y = R.at(P.y_off[t]), *mu = R.at(P.mu_off[t]);
+    if ((rc = R.mul(opnd(X(t), st, (uint32_t)st), kNone, kNone, Out{Y, k, 0, (uint32_t)k}, cnt, true))) return rc;
+    uint64_t wd;
+    if (t == t0) {
+      mu_word_kernel<<<R.grid_for(cnt, 256), 256, 0, s>>>(Y, k, mu, k, cnt);
+      ++R.launches;
+      wd = 1;
+    } else {
+      // -mu_a mu_b = mu_a ~mu_b + mu_a mod 2^(32 s_t); children's rows hold s_t words
+      uint32_t *mc = R.at(P.mu_off[t - 1]);
+      if ((rc = R.mul(opnd(mc, 2 * st, (uint32_t)st), opnd(mc + st, 2 * st, (uint32_t)st, 0, 1),
+                      opnd(mc, 2 * st, (uint32_t)st), Out{mu, k, 0, (uint32_t)st}, cnt, false)))
+        return rc;
+      wd = st;
+    }
+    for (; wd < k; wd *= 2) {
+      const uint32_t w32 = (uint32_t)wd;
+      if ((rc = R.mul(opnd(Y, k, 2 * w32), opnd(mu, k, w32), kNone, Out{H, wd, w32, 2 * w32}, cnt, false)) ||
+          (rc = R.mul(opnd(H, wd, w32), opnd(mu, k, w32), opnd(mu, k, w32), Out{mu + wd, k, 0, w32}, cnt, false)))
+        return rc;
+    }
+  }
+  // remainder tree
+  int cur = 0;
+  {
+    const uint64_t zs = 2 * sz(T) + 4;
+    root_kernel<<<R.grid_for(zs, 256), 256, 0, s>>>(X(T), sz(T), R.at(P.z_off[cur]), zs);
+    ++R.launches;
+  }
+  uint32_t *q = R.at(P.q_off);
+  for (uint32_t t = T; t-- > t0;) {
+    const uint64_t st = sz(t), k = 2 * st, cnt = K >> t, zsp = 2 * sz(t + 1) + 4, zs = 2 * st + 4;
+    const uint32_t k32 = (uint32_t)k;
+    uint32_t *Zp = R.at(P.z_off[cur]), *Zc = R.at(P.z_off[cur ^ 1]);
+    uint32_t *Y = R.at(P.y_off[t]), *mu = R.at(P.mu_off[t]);
+    if ((rc = R.mul(opnd(Zp, zsp, k32, 1), opnd(mu, k, k32), kNone, Out{q, k, 0, k32}, cnt, false)) ||
+        (rc = R.mul(opnd(q, k, k32), opnd(Y, k, k32), opnd(Zp, zsp, 2 * k32 + 1, 1), Out{Zc, zs, k32, 2 * k32 + 1},
+                    cnt, false)))
+      return rc;
+    cur ^= 1;
+  }
+  // leaves
+  {
+    const uint64_t zs = 2 * sz(t0) + 4;
+    const uint32_t M = (uint32_t)(2 * sz(t0) + 1);
+    const size_t smem = (size_t)leaf_words(L) * kLeafThreads * 4;
+    const unsigned grid = (unsigned)((count + kLeafThreads - 1) / kLeafThreads);
+    const uint32_t *Z = R.at(P.z_off[cur]);
+    cudaError_t e;
+    if (L == 16) {
+      e = cudaFuncSetAttribute(tree_leaf_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) tree_leaf_kernel<16><<<grid, kLeafThreads, smem, s>>>(moduli, count, Z, zs, M, t0, gcds, flags);
+    } else if (L == 32) {
+      e = cudaFuncSetAttribute(tree_leaf_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) tree_leaf_kernel<32><<<grid, kLeafThreads, smem, s>>>(moduli, count, Z, zs, M, t0, gcds, flags);
+    } else {
+      e = cudaFuncSetAttribute(tree_leaf_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) tree_leaf_kernel<64><<<grid, kLeafThreads, smem, s>>>(moduli, count, Z, zs, M, t0, gcds, flags);
+    }
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(tree_leaf)");
+    ++R.launches;
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "launch batch gcd tree kernels");
+  c->stats.kernel_launches += (uint64_t)R.launches;
+  c->stats.ops += count;
+  return RSA_OK;
+}
+
+}  // namespace rsagpu

@@ -84,11 +84,13 @@ Ctx::~Ctx() {
 
 void Workspace::free_all() {
   for (DevBuf *b : {&tables, &io_in, &io_out, &io_status, &aux0, &aux1, &aux2, &aux3, &halves, &tc_halves[0],
-                    &tc_halves[1], &verify, &gcd0, &gcd1}) {
+                    &tc_halves[1], &verify, &gcd0, &gcd1, &gcd_tree, &gcd_tw}) {
     if (b->ptr) cudaFree(b->ptr);
     b->ptr = nullptr;
     b->bytes = 0;
   }
+  gcd_tw_ptr = nullptr;
+  gcd_tw_n = 0;
 }
 
 // ------------------------------------------------------------------ tuning

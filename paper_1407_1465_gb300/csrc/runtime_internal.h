@@ -41,6 +41,9 @@ struct Workspace {
   DevBuf tc_halves[2];            // ragged batches: the same for the 3072- and 4096-bit tensor-core groups
   DevBuf verify;                  // rsa_verify_key: recovered representatives
   DevBuf gcd0, gcd1;              // rsa_batch_gcd: validity + block products, partial products
+  DevBuf gcd_tree, gcd_tw;        // rsa_batch_gcd, tree form: levels and transform scratch, twiddle tables
+  const void *gcd_tw_ptr = nullptr; // gcd_tw's allocation when its tables were built
+  uint64_t gcd_tw_n = 0;          // ... and the transform length they were built for
   void free_all();
 };
 

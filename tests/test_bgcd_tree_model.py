@@ -1,0 +1,338 @@
+"""CPU model of the product/remainder-tree batch GCD kernels (csrc/bgcd_tree.cu).
+
+The GPU path computes g_i = gcd(n_i, prod_{j != i} n_j) for many moduli at
+once (the weak-key scan of the paper's introduction) with a product tree and a
+remainder tree instead of a scan over all pairs.  This file restates, in
+Python integers, the exact steps and word sizes the kernels take, and checks
+them against math.gcd on small sets, so that the bounds the kernels rely on
+(no conditional subtraction in the tree, one extra word of slack, the Newton
+steps, the transform indexing) are pinned before the GPU runs them:
+
+  * product tree X_t (node of 2^t moduli, s_t = L 2^t words), padding leaves 1;
+  * Y_t = X_t^2, mu_t = -Y_t^-1 mod 2^(32*2s_t): from one word by Newton at the
+    lowest tree level, above it from the children (mu_a * ~mu_b + mu_a is
+    -mu_a mu_b) and one Newton step;
+  * Montgomery remainder tree Z_t = (Z_{t+1} + q Y_t) / 2^(32*2s_t),
+    q = Z_{t+1} mu_t mod 2^(32*2s_t), Z_T = X_T, with no subtraction
+    (Z_t < (T - t + 1) Y_t, stored in 2 s_t + 1 words);
+  * leaves: word-serial Montgomery reduction of the node's Z modulo n_i^2,
+    one conditional subtraction, exact division by n_i, gcd with n_i;
+  * products by three-prime number-theoretic transforms of 32-bit words
+    (decimation in frequency forward, in time inverse, nested twiddle table
+    tw[len + j] = w_(2len)^j), recombined by Garner's method, with an addend,
+    a complemented operand and an output slice.
+"""
+import math
+import random
+
+import pytest
+
+W = 32
+MASK = (1 << W) - 1
+PRIMES = (2013265921, 3221225473, 3489660929)   # 15*2^27+1, 3*2^30+1, 13*2^28+1
+
+
+def words(x, n):
+    return [(x >> (W * k)) & MASK for k in range(n)]
+
+
+def value(ws):
+    return sum(w << (W * k) for k, w in enumerate(ws))
+
+
+def neg_inv32(n0):
+    inv = n0
+    for _ in range(4):
+        inv = (inv * (2 - n0 * inv)) & MASK
+    return (-inv) & MASK
+
+
+def neg_inverse(y, nw, seed_mu=None, seed_w=1):
+    """mu = -y^-1 mod 2^(32 nw) by Newton doublings: with y mu = -1 + 2^(32w) (H)
+    (low w words all ones), mu_hi = H mu + mu mod 2^(32w)."""
+    if seed_mu is None:
+        mu, w = neg_inv32(y & MASK), 1
+    else:
+        mu, w = seed_mu, seed_w
+    while w < nw:
+        prod = (y % (1 << (W * 2 * w))) * mu
+        assert prod % (1 << (W * w)) == (1 << (W * w)) - 1
+        h = (prod >> (W * w)) % (1 << (W * w))
+        hi = (h * mu + mu) % (1 << (W * w))
+        mu, w = mu + (hi << (W * w)), 2 * w
+    assert (y * mu + 1) % (1 << (W * nw)) == 0
+    return mu
+
+
+def valid(n):
+    return n % 2 == 1 and n >= 3
+
+
+def tree_gcds(mods, L, t0=2):
+    count = len(mods)
+    K = 1
+    while K < max(count, 2):
+        K *= 2
+    T = K.bit_length() - 1
+    t0 = min(t0, T)
+    leaves = [m if (i < count and valid(m)) else 1 for i, m in enumerate(list(mods) + [1] * (K - count))]
+    X = [leaves]
+    for t in range(T):
+        X.append([X[t][2 * v] * X[t][2 * v + 1] for v in range(K >> (t + 1))])
+        s = L << (t + 1)
+        assert all(x < 1 << (W * s) for x in X[t + 1])
+    mu = {}
+    for t in range(t0, T):
+        s = L << t
+        Y = [x * x for x in X[t]]
+        if t == t0:
+            mu[t] = [neg_inverse(y, 2 * s) for y in Y]
+        else:
+            m = []
+            for v, y in enumerate(Y):
+                a, b = mu[t - 1][2 * v], mu[t - 1][2 * v + 1]
+                seed = (a * ((~b) % (1 << (W * s))) + a) % (1 << (W * s))    # -a b, s words
+                m.append(neg_inverse(y, 2 * s, seed, s))
+            mu[t] = m
+    Z = [X[T][0]]
+    for t in range(T - 1, t0 - 1, -1):
+        s = L << t
+        k = 2 * s
+        Zt = []
+        for v in range(K >> t):
+            zp = Z[v // 2]
+            y = X[t][v] ** 2
+            q = (zp % (1 << (W * k))) * mu[t][v] % (1 << (W * k))
+            tot = zp + q * y
+            assert tot % (1 << (W * k)) == 0
+            # the low half sums to 0 or 2^(32k): its carry is "low half of zp nonzero"
+            assert ((zp % (1 << (W * k)) + (q * y) % (1 << (W * k))) >> (W * k)) == (zp % (1 << (W * k)) != 0)
+            z = tot >> (W * k)
+            assert z < (T - t + 1) * y and z < 1 << (W * (k + 1))
+            Zt.append(z)
+        Z = Zt
+    out = []
+    s0 = L << t0
+    for i in range(count):
+        n = mods[i]
+        if not valid(n):
+            out.append((0, -1))
+            continue
+        z = Z[i >> t0]
+        M = 2 * s0 + 1
+        N = n * n
+        k = 2 * L
+        npr = neg_inv32(N & MASK)
+        t = z % (1 << (W * k))
+        for step in range(M):
+            q = (t & MASK) * npr & MASK
+            t = (t + q * N) >> W
+            nxt = k + step
+            if nxt < M:
+                t += ((z >> (W * nxt)) & MASK) << (W * (k - 1))
+        assert t <= N
+        if t >= N:
+            t -= N
+        assert t == z * pow(2, -W * M, N) % N
+        assert t % n == 0
+        # exact division, word by word from the bottom
+        inv = (-neg_inv32(n & MASK)) & MASK
+        u, r = 0, t
+        for j in range(L):
+            d = ((r >> (W * j)) & MASK) * inv & MASK
+            r -= (d * n) << (W * j)
+            u += d << (W * j)
+        assert r == 0 and u == t // n and u < n
+        g = math.gcd(n, u)
+        out.append((g, 0 if g == 1 else (2 if g == n else 1)))
+    return out
+
+
+def brute(mods):
+    res = []
+    for i, n in enumerate(mods):
+        if not valid(n):
+            res.append((0, -1))
+            continue
+        p = 1
+        for j, m in enumerate(mods):
+            if j != i and valid(m):
+                p *= m
+        g = math.gcd(n, p)
+        res.append((g, 0 if g == 1 else (2 if g == n else 1)))
+    return res
+
+
+def rand_prime(rng, bits):
+    while True:
+        c = rng.getrandbits(bits) | (1 << (bits - 1)) | 1
+        if all(pow(a, c - 1, c) == 1 for a in (2, 3, 5, 7, 11, 13)):
+            return c
+
+
+@pytest.mark.parametrize("count,t0", [(2, 2), (3, 1), (5, 2), (8, 2), (13, 3), (33, 2), (64, 0)])
+def test_tree_matches_brute_force(count, t0):
+    rng = random.Random(count * 31 + t0)
+    L = 2
+    primes = [rand_prime(rng, 32) for _ in range(2 * count)]
+    mods = [primes[2 * i] * primes[2 * i + 1] for i in range(count)]
+    if count >= 3:
+        mods[1] = primes[0] * primes[5]          # shares p0 with n0
+    if count >= 5:
+        mods[4] = mods[2]                        # duplicate
+        mods[3] = 6                              # invalid (even)
+    if count >= 8:
+        mods[7] = 1                              # invalid (< 3)
+        mods[6] = primes[1] * primes[12 % (2 * count)]
+    assert tree_gcds(mods, L, t0) == brute(mods)
+
+
+def test_tree_leading_zero_limbs_and_single_valid():
+    rng = random.Random(5)
+    small = [rand_prime(rng, 20) * rand_prime(rng, 20) for _ in range(6)]
+    small[2] = small[0]
+    assert tree_gcds(small, 4, 2) == brute(small)
+    assert tree_gcds([small[0], 4], 4, 2) == brute([small[0], 4])
+
+
+# ---------------------------------------------------------------- transform model
+
+def prime_consts(p):
+    R = 1 << W
+    e2 = 0
+    while (p - 1) % (1 << (e2 + 1)) == 0:
+        e2 += 1
+    odd = (p - 1) >> e2
+    factors = {2} | {f for f in range(3, 50, 2) if odd % f == 0 and all(f % g for g in range(3, f, 2))}
+    g = next(g for g in range(2, 100) if all(pow(g, (p - 1) // f, p) != 1 for f in factors))
+    return {"p": p, "R": R % p, "g": g, "e2": e2, "pinv": pow(p, -1, R)}
+
+
+def mmul(a, b, c):
+    p, pinv = c["p"], c["pinv"]
+    t = a * b
+    m = (t & MASK) * pinv & MASK
+    th, mh = t >> W, (m * p) >> W
+    r = th - mh
+    return r + p if r < 0 else r
+
+
+def tables(c, nmax):
+    p, R = c["p"], 1 << W
+    root = pow(c["g"], (p - 1) // nmax, p)
+    iroot = pow(root, -1, p)
+    tw, itw = [0] * nmax, [0] * nmax
+    length = 1
+    while length < nmax:
+        for j in range(length):
+            e = j * (nmax // (2 * length))
+            tw[length + j] = pow(root, e, p) * R % p
+            itw[length + j] = pow(iroot, e, p) * R % p
+        length *= 2
+    return tw, itw
+
+
+def dif(a, n, c, tw):
+    p = c["p"]
+    length = n // 2
+    while length >= 1:
+        for blk in range(0, len(a), 2 * length):
+            for j in range(length):
+                u, v = a[blk + j], a[blk + j + length]
+                a[blk + j] = (u + v) % p
+                a[blk + j + length] = mmul((u - v) % p, tw[length + j], c)
+        length //= 2
+
+
+def dit(a, n, c, itw):
+    p = c["p"]
+    length = 1
+    while length < n:
+        for blk in range(0, len(a), 2 * length):
+            for j in range(length):
+                u, v = a[blk + j], mmul(a[blk + j + length], itw[length + j], c)
+                a[blk + j] = (u + v) % p
+                a[blk + j + length] = (u - v) % p
+        length *= 2
+
+
+def garner(r):
+    p1, p2, p3 = PRIMES
+    v1 = r[0]
+    v2 = (r[1] - v1) * pow(p1, -1, p2) % p2
+    v3 = (r[2] - v1 - p1 * v2) * pow(p1 * p2, -1, p3) % p3
+    return v1 + p1 * v2 + p1 * p2 * v3
+
+
+def ntt_bmul(A, B, na, nb, D=None, flip_b=False, lo=0, hi=None, nmax=64):
+    """Batched A_i * (B_i or ~B_i) + D_i, words [lo, hi), through the transform path."""
+    cnt = len(A)
+    n = 1
+    while n < na + nb:
+        n *= 2
+    assert n <= nmax
+    cs = [prime_consts(p) for p in PRIMES]
+    res = []
+    for k, c in enumerate(cs):
+        p = c["p"]
+        tw, itw = tables(c, nmax)
+        fa = [0] * (cnt * n)
+        fb = [0] * (cnt * n)
+        for i in range(cnt):
+            aw = words(A[i], na)
+            bw = words(B[i], nb)
+            if flip_b:
+                bw = [w ^ MASK for w in bw]
+            for j in range(na):
+                fa[i * n + j] = aw[j] % p
+            for j in range(nb):
+                fb[i * n + j] = bw[j] % p
+        dif(fa, n, c, tw)
+        dif(fb, n, c, tw)
+        fa = [mmul(x, y, c) for x, y in zip(fa, fb)]
+        dit(fa, n, c, itw)
+        scale = pow(n, -1, p) * pow(1 << W, 2, p) % p
+        res.append([mmul(x, scale, c) for x in fa])
+    out = []
+    for i in range(cnt):
+        total = sum(garner([res[k][i * n + j] for k in range(3)]) << (W * j) for j in range(n))
+        if D is not None:
+            total += D[i]
+        h = hi if hi is not None else n + 2
+        out.append((total >> (W * lo)) % (1 << (W * (h - lo))))
+    return out
+
+
+@pytest.mark.parametrize("na,nb,cnt", [(3, 5, 3), (8, 8, 2), (16, 7, 2), (32, 32, 1)])
+def test_transform_product(na, nb, cnt):
+    rng = random.Random(na * 100 + nb)
+    A = [rng.getrandbits(W * na) for _ in range(cnt)]
+    B = [rng.getrandbits(W * nb) for _ in range(cnt)]
+    A[0] = (1 << (W * na)) - 1                     # all-ones words: the largest columns
+    B[0] = (1 << (W * nb)) - 1
+    got = ntt_bmul(A, B, na, nb)
+    assert got == [a * b for a, b in zip(A, B)]
+
+
+def test_transform_addend_flip_slice():
+    rng = random.Random(9)
+    na, nb = 8, 8
+    A = [rng.getrandbits(W * na) for _ in range(2)]
+    B = [rng.getrandbits(W * nb) for _ in range(2)]
+    D = [rng.getrandbits(W * (na + nb + 1)) for _ in range(2)]
+    lo, hi = 8, 17
+    got = ntt_bmul(A, B, na, nb, D=D, flip_b=True, lo=lo, hi=hi)
+    want = [((a * ((~b) % (1 << (W * nb))) + d) >> (W * lo)) % (1 << (W * (hi - lo))) for a, b, d in zip(A, B, D)]
+    assert got == want
+
+
+def test_column_bound_fits_three_primes():
+    """The largest product the tree forms has operands of 2^26 words: every
+    convolution column is below 2^26 * 2^64, under the primes' product; each
+    prime has a root of unity of order 2^27 (the longest transform)."""
+    M = PRIMES[0] * PRIMES[1] * PRIMES[2]
+    assert (1 << 26) * ((1 << 32) - 1) ** 2 < M
+    for p in PRIMES:
+        assert (p - 1) % (1 << 27) == 0
+    assert PRIMES[0] < PRIMES[1] < PRIMES[2] < 1 << 32
+    assert PRIMES[0] * PRIMES[1] < 1 << 64
