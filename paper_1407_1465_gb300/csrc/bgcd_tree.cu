@@ -49,7 +49,7 @@ namespace tree {
 constexpr uint32_t kPrime[3] = {2013265921u, 3221225473u, 3489660929u};
 constexpr uint32_t kMaxLog = 27;            // transforms of up to 2^27 words (2-adic order of the first prime)
 constexpr uint32_t kTile = 4096;            // transform stages done in shared memory: blocks of up to 4096 words
-constexpr uint32_t kSchoolMax = 1024;       // products of at most this many words: schoolbook
+constexpr uint32_t kSchoolMax = 512;        // products of at most this many words: schoolbook
 constexpr uint32_t kCarryWords = 16;        // words per thread of the carry scan
 constexpr uint32_t kCarryThreads = 256;
 constexpr uint32_t kCarryBlock = kCarryWords * kCarryThreads;
@@ -106,6 +106,15 @@ __device__ __forceinline__ uint32_t msub(uint32_t a, uint32_t b, uint32_t p) {
   return a < b ? d + p : d;
 }
 
+// prime k's entry of a per-prime parameter array (selects, no local copy)
+__device__ __forceinline__ uint32_t sel3(const uint32_t (&a)[3], uint32_t k) {
+  return k == 0 ? a[0] : k == 1 ? a[1] : a[2];
+}
+
+__device__ __forceinline__ const uint32_t *sel3p(const uint32_t *const (&a)[3], uint32_t k) {
+  return k == 0 ? a[0] : k == 1 ? a[1] : a[2];
+}
+
 // ------------------------------------------------------------------ twiddles
 
 // tw[i] for 1 <= i < nmax: i = len + j (len the power of two below i) holds
@@ -137,58 +146,6 @@ __global__ void twiddle_kernel(uint32_t *tw, uint32_t *itw, uint32_t nmax, uint3
   }
 }
 
-// ------------------------------------------------------------------ schoolbook products
-
-// Products of nc = na + nb <= kSchoolMax words: tpp threads per product, ppb
-// products per CTA of 128 threads.  Columns c = sum_j a_j b_(c-j) as 96-bit
-// sums (round robin over the product's threads), then one thread per product
-// adds the columns' three words and the addend with a running carry and
-// stores words [lo, hi).
-__global__ void __launch_bounds__(128) school_kernel(Opnd A, Opnd B, Opnd D, Out O, uint64_t cnt, uint32_t tpp,
-                                                     uint32_t ppb) {
-  extern __shared__ uint32_t sm[];
-  const uint32_t na = A.words, nb = B.words, nc = na + nb;
-  const uint32_t slot = threadIdx.x / tpp, lt = threadIdx.x % tpp;
-  const uint64_t i = (uint64_t)blockIdx.x * ppb + slot;
-  const bool live = i < cnt;
-  uint32_t *sa = sm + (size_t)slot * (4 * nc);
-  uint32_t *sb = sa + na;
-  uint32_t *clo = sb + nb, *cmid = clo + nc, *chi = cmid + nc;
-  if (live) {
-    for (uint32_t j = lt; j < na; j += tpp) sa[j] = opnd_word(A, i, j);
-    for (uint32_t j = lt; j < nb; j += tpp) sb[j] = opnd_word(B, i, j);
-  }
-  __syncthreads();
-  if (live) {
-    for (uint32_t c = lt; c < nc; c += tpp) {
-      const uint32_t j0 = c + 1 > nb ? c + 1 - nb : 0u;
-      const uint32_t j1 = c < na ? c : na - 1;
-      uint64_t s0 = 0;
-      uint32_t s1 = 0;
-      for (uint32_t j = j0; j <= j1 && j0 <= j1; ++j) {
-        const uint64_t pr = (uint64_t)sa[j] * sb[c - j];
-        s0 += pr;
-        s1 += s0 < pr ? 1u : 0u;
-      }
-      clo[c] = (uint32_t)s0;
-      cmid[c] = (uint32_t)(s0 >> 32);
-      chi[c] = s1;
-    }
-  }
-  __syncthreads();
-  if (!live || lt != 0) return;
-  uint64_t carry = 0;
-  uint32_t *dst = O.p + i * O.stride;
-  for (uint32_t c = 0; c < O.hi; ++c) {
-    uint64_t v = carry + opnd_word(D, i, c);
-    if (c < nc) v += clo[c];
-    if (c >= 1 && c - 1 < nc) v += cmid[c - 1];
-    if (c >= 2 && c - 2 < nc) v += chi[c - 2];
-    if (c >= O.lo) dst[c - O.lo] = (uint32_t)v;
-    carry = v >> 32;
-  }
-}
-
 // ------------------------------------------------------------------ transforms
 // Buffers hold the three primes' arrays back to back (prime k at k * E), each
 // `cnt` transforms of length n, so blockIdx.y selects the prime.  Forward:
@@ -196,23 +153,24 @@ __global__ void __launch_bounds__(128) school_kernel(Opnd A, Opnd B, Opnd D, Out
 // decimation in time (bit-reversed in, natural out) with the inverse roots,
 // so no permutation is needed between them.
 
-// F_k[i n + j] = word j of operand i mod p_k (zero for j >= words).
-__global__ void ntt_load_kernel(Opnd X, uint32_t *F, uint64_t E, uint32_t logn) {
+// F_k[i n + j] = word j of operand i mod p_k (zero for j >= words); prime k's
+// array at k * stride.
+__global__ void ntt_load_kernel(Opnd X, uint32_t *F, uint64_t E, uint64_t stride, uint32_t logn) {
   const uint32_t p0 = kPrime[0], p1 = kPrime[1], p2 = kPrime[2];
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t w = opnd_word(X, e >> logn, (uint32_t)(e & ((1ull << logn) - 1)));
     F[e] = w % p0;
-    F[E + e] = w % p1;
-    F[2 * E + e] = w % p2;
+    F[stride + e] = w % p1;
+    F[2 * stride + e] = w % p2;
   }
 }
 
 // Two decimation-in-frequency stages (len = 2h, then h) over quads
 // x0..x3 = F[base + j + {0, h, 2h, 3h}], base = 4h * block, j < h.
 __global__ void dif4_kernel(uint32_t *F, uint64_t E, uint32_t logh, Primes P) {
-  const uint32_t k = blockIdx.y, p = P.p[k], pinv = P.pinv[k];
+  const uint32_t k = blockIdx.y, p = sel3(P.p, k), pinv = sel3(P.pinv, k);
   uint32_t *f = F + k * E;
-  const uint32_t *tw = P.tw[k];
+  const uint32_t *tw = sel3p(P.tw, k);
   const uint32_t h = 1u << logh, len = 2u * h;
   for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E / 4; q += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t j = (uint32_t)(q & (h - 1));
@@ -228,11 +186,67 @@ __global__ void dif4_kernel(uint32_t *F, uint64_t E, uint32_t logh, Primes P) {
   }
 }
 
+// Four decimation-in-frequency stages (distances 8h, 4h, 2h, h) over the 16
+// words x_m = F[b + m h], b = 16h * block + j, j < h: at distance d h word m
+// pairs with m + d when m & d is clear, with twiddle tw[d h + j + (m mod d) h].
+__global__ void dif16_kernel(uint32_t *F, uint64_t E, uint32_t logh, Primes P) {
+  const uint32_t k = blockIdx.y, p = sel3(P.p, k), pinv = sel3(P.pinv, k);
+  uint32_t *f = F + k * E;
+  const uint32_t *tw = sel3p(P.tw, k);
+  const uint32_t h = 1u << logh;
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E / 16; q += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t j = (uint32_t)(q & (h - 1));
+    const uint64_t b = ((q >> logh) << (logh + 4)) + j;
+    uint32_t x[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) x[m] = f[b + (uint64_t)m * h];
+#pragma unroll
+    for (int d = 8; d >= 1; d /= 2) {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        if (m & d) continue;
+        const uint32_t a = x[m], c = x[m + d];
+        x[m] = madd(a, c, p);
+        x[m + d] = mmul(msub(a, c, p), tw[(uint32_t)d * h + j + (uint32_t)(m & (d - 1)) * h], p, pinv);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 16; ++m) f[b + (uint64_t)m * h] = x[m];
+  }
+}
+
+// The four decimation-in-time stages (distances h, 2h, 4h, 8h) over the same words.
+__global__ void dit16_kernel(uint32_t *F, uint64_t E, uint32_t logh, Primes P) {
+  const uint32_t k = blockIdx.y, p = sel3(P.p, k), pinv = sel3(P.pinv, k);
+  uint32_t *f = F + k * E;
+  const uint32_t *itw = sel3p(P.itw, k);
+  const uint32_t h = 1u << logh;
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E / 16; q += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t j = (uint32_t)(q & (h - 1));
+    const uint64_t b = ((q >> logh) << (logh + 4)) + j;
+    uint32_t x[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) x[m] = f[b + (uint64_t)m * h];
+#pragma unroll
+    for (int d = 1; d <= 8; d *= 2) {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        if (m & d) continue;
+        const uint32_t a = x[m], c = mmul(x[m + d], itw[(uint32_t)d * h + j + (uint32_t)(m & (d - 1)) * h], p, pinv);
+        x[m] = madd(a, c, p);
+        x[m + d] = msub(a, c, p);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 16; ++m) f[b + (uint64_t)m * h] = x[m];
+  }
+}
+
 // One decimation-in-frequency stage of half-length len = 2^logl.
 __global__ void dif2_kernel(uint32_t *F, uint64_t E, uint32_t logl, Primes P) {
-  const uint32_t k = blockIdx.y, p = P.p[k], pinv = P.pinv[k];
+  const uint32_t k = blockIdx.y, p = sel3(P.p, k), pinv = sel3(P.pinv, k);
   uint32_t *f = F + k * E;
-  const uint32_t *tw = P.tw[k];
+  const uint32_t *tw = sel3p(P.tw, k);
   const uint32_t len = 1u << logl;
   for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E / 2; q += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t j = (uint32_t)(q & (len - 1));
@@ -245,9 +259,9 @@ __global__ void dif2_kernel(uint32_t *F, uint64_t E, uint32_t logl, Primes P) {
 
 // Two decimation-in-time stages (h, then len = 2h) over the same quads.
 __global__ void dit4_kernel(uint32_t *F, uint64_t E, uint32_t logh, Primes P) {
-  const uint32_t k = blockIdx.y, p = P.p[k], pinv = P.pinv[k];
+  const uint32_t k = blockIdx.y, p = sel3(P.p, k), pinv = sel3(P.pinv, k);
   uint32_t *f = F + k * E;
-  const uint32_t *itw = P.itw[k];
+  const uint32_t *itw = sel3p(P.itw, k);
   const uint32_t h = 1u << logh, len = 2u * h;
   for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E / 4; q += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t j = (uint32_t)(q & (h - 1));
@@ -266,9 +280,9 @@ __global__ void dit4_kernel(uint32_t *F, uint64_t E, uint32_t logh, Primes P) {
 }
 
 __global__ void dit2_kernel(uint32_t *F, uint64_t E, uint32_t logl, Primes P) {
-  const uint32_t k = blockIdx.y, p = P.p[k], pinv = P.pinv[k];
+  const uint32_t k = blockIdx.y, p = sel3(P.p, k), pinv = sel3(P.pinv, k);
   uint32_t *f = F + k * E;
-  const uint32_t *itw = P.itw[k];
+  const uint32_t *itw = sel3p(P.itw, k);
   const uint32_t len = 1u << logl;
   for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E / 2; q += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t j = (uint32_t)(q & (len - 1));
@@ -279,46 +293,152 @@ __global__ void dit2_kernel(uint32_t *F, uint64_t E, uint32_t logl, Primes P) {
   }
 }
 
-// The stages of half-length below `tile` (a power of two <= kTile dividing
-// the transform length) in shared memory, one tile per CTA of 512 threads:
-// forward (dir 0) len = tile/2 .. 1, inverse (dir 1) len = 1 .. tile/2.
-__global__ void __launch_bounds__(512) ntt_tile_kernel(uint32_t *F, uint64_t E, uint32_t tile, int dir, Primes P) {
-  __shared__ uint32_t s[kTile];
-  const uint32_t k = blockIdx.y, p = P.p[k], pinv = P.pinv[k];
-  uint32_t *f = F + k * E + (uint64_t)blockIdx.x * tile;
-  const uint32_t *tw = dir ? P.itw[k] : P.tw[k];
-  for (uint32_t x = threadIdx.x; x < tile; x += blockDim.x) s[x] = f[x];
-  const uint32_t half = tile / 2;
-  for (uint32_t st = 0; (1u << st) < tile; ++st) {
-    const uint32_t logl = dir ? st : (31 - __clz(half)) - st;
-    const uint32_t len = 1u << logl;
-    __syncthreads();
-    for (uint32_t q = threadIdx.x; q < half; q += blockDim.x) {
-      const uint32_t j = q & (len - 1);
-      const uint32_t b = ((q >> logl) << (logl + 1)) + j;
-      const uint32_t w = tw[len + j];
-      const uint32_t u = s[b], v = s[b + len];
-      if (dir == 0) {
-        s[b] = madd(u, v, p);
-        s[b + len] = mmul(msub(u, v, p), w, p, pinv);
-      } else {
-        const uint32_t vw = mmul(v, w, p, pinv);
-        s[b] = madd(u, vw, p);
-        s[b + len] = msub(u, vw, p);
-      }
-    }
-  }
-  __syncthreads();
-  for (uint32_t x = threadIdx.x; x < tile; x += blockDim.x) f[x] = s[x];
+// The twelve stages of half-length below kTile run in shared memory, one tile
+// of 4096 words per CTA of 512 threads, three stages per exchange: for
+// distances 4q, 2q, q (q = 512, 64, 8, 1 forward; the reverse inverse) thread
+// t holds the eight words b + k q, b = (t / q) 8q + t mod q, whose butterflies
+// at those three distances stay among them.  Word a lives at a + a / 32
+// (padding against bank conflicts when q < 32).
+constexpr uint32_t kTileThreads = 512;
+
+__device__ __forceinline__ uint32_t pad(uint32_t a) { return a + (a >> 5); }
+
+__device__ __forceinline__ void bf_dif(uint32_t &u, uint32_t &v, uint32_t w, uint32_t p, uint32_t pinv) {
+  const uint32_t a = u, b = v;
+  u = madd(a, b, p);
+  v = mmul(msub(a, b, p), w, p, pinv);
 }
 
-// Pointwise products FA *= FB (or FA *= FA), each with one factor R^-1.
-__global__ void pointwise_kernel(uint32_t *FA, const uint32_t *FB, uint64_t E, Primes P) {
-  const uint32_t k = blockIdx.y, p = P.p[k], pinv = P.pinv[k];
-  uint32_t *a = FA + k * E;
-  const uint32_t *b = FB ? FB + k * E : a;
-  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (uint64_t)gridDim.x * blockDim.x)
-    a[e] = mmul(a[e], b[e], p, pinv);
+__device__ __forceinline__ void bf_dit(uint32_t &u, uint32_t &v, uint32_t w, uint32_t p, uint32_t pinv) {
+  const uint32_t a = u, b = mmul(v, w, p, pinv);
+  u = madd(a, b, p);
+  v = msub(a, b, p);
+}
+
+// three forward stages (distances 4q, 2q, q) on the thread's eight words;
+// the first `skip` of them are left out (tiles holding several shorter
+// transforms)
+__device__ __forceinline__ void dif8(uint32_t (&x)[8], uint32_t q, uint32_t jp, const uint32_t *tw, uint32_t p,
+                                     uint32_t pinv, uint32_t skip = 0) {
+  if (skip == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) bf_dif(x[k], x[k + 4], tw[4 * q + jp + k * q], p, pinv);
+  }
+  if (skip <= 1) {
+    const uint32_t w0 = tw[2 * q + jp], w1 = tw[2 * q + jp + q];
+    bf_dif(x[0], x[2], w0, p, pinv);
+    bf_dif(x[1], x[3], w1, p, pinv);
+    bf_dif(x[4], x[6], w0, p, pinv);
+    bf_dif(x[5], x[7], w1, p, pinv);
+  }
+  const uint32_t w = tw[q + jp];
+#pragma unroll
+  for (int k = 0; k < 8; k += 2) bf_dif(x[k], x[k + 1], w, p, pinv);
+}
+
+// three inverse stages (distances q, 2q, 4q); the last `skip` left out
+__device__ __forceinline__ void dit8(uint32_t (&x)[8], uint32_t q, uint32_t jp, const uint32_t *itw, uint32_t p,
+                                     uint32_t pinv, uint32_t skip = 0) {
+  const uint32_t w = itw[q + jp];
+#pragma unroll
+  for (int k = 0; k < 8; k += 2) bf_dit(x[k], x[k + 1], w, p, pinv);
+  if (skip <= 1) {
+    const uint32_t w0 = itw[2 * q + jp], w1 = itw[2 * q + jp + q];
+    bf_dit(x[0], x[2], w0, p, pinv);
+    bf_dit(x[1], x[3], w1, p, pinv);
+    bf_dit(x[4], x[6], w0, p, pinv);
+    bf_dit(x[5], x[7], w1, p, pinv);
+  }
+  if (skip == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) bf_dit(x[k], x[k + 4], itw[4 * q + jp + k * q], p, pinv);
+  }
+}
+
+__device__ __forceinline__ uint32_t tile_base(uint32_t q) {
+  const uint32_t t = threadIdx.x;
+  return (t / q) * 8 * q + (t & (q - 1));
+}
+
+__device__ __forceinline__ void sload8(const uint32_t *s, uint32_t b, uint32_t q, uint32_t (&x)[8]) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = s[pad(b + k * q)];
+}
+
+__device__ __forceinline__ void sstore8(uint32_t *s, uint32_t b, uint32_t q, const uint32_t (&x)[8]) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s[pad(b + k * q)] = x[k];
+}
+
+// Forward stages below kTile of every tile (the operand that is multiplied in);
+// a tile holds one 4096-word piece of a longer transform, or 2^skip
+// transforms of 4096 / 2^skip words whose first `skip` stages do not exist.
+__global__ void __launch_bounds__(kTileThreads) ntt_tile_fwd_kernel(uint32_t *F, uint64_t E, uint32_t skip,
+                                                                    Primes P) {
+  __shared__ uint32_t s[kTile + kTile / 32];
+  const uint32_t k = blockIdx.y, p = sel3(P.p, k), pinv = sel3(P.pinv, k);
+  const uint32_t *tw = sel3p(P.tw, k);
+  uint32_t *f = F + k * E + (uint64_t)blockIdx.x * kTile;
+  for (uint32_t a = threadIdx.x; a < kTile; a += kTileThreads) s[pad(a)] = f[a];
+  uint32_t x[8];
+  for (uint32_t q = kTile / 8; q >= 1; q /= 8) {
+    __syncthreads();
+    const uint32_t b = tile_base(q);
+    sload8(s, b, q, x);
+    dif8(x, q, threadIdx.x & (q - 1), tw, p, pinv, q == kTile / 8 ? skip : 0u);
+    if (q > 1) sstore8(s, b, q, x);
+  }
+  // q = 1: the thread's words are 8t .. 8t+7
+  uint4 *f4 = reinterpret_cast<uint4 *>(f + 8 * threadIdx.x);
+  f4[0] = make_uint4(x[0], x[1], x[2], x[3]);
+  f4[1] = make_uint4(x[4], x[5], x[6], x[7]);
+}
+
+// Forward stages below kTile, the pointwise product with FB (or a square;
+// each product carries one factor R^-1) and the inverse stages below kTile,
+// in one pass per tile: the last forward and the first inverse exchange (q =
+// 1) share the thread's words, so the product happens in registers.
+__global__ void __launch_bounds__(kTileThreads) ntt_tile_mul_kernel(uint32_t *FA, const uint32_t *FB, uint64_t E,
+                                                                    uint32_t skip, Primes P) {
+  __shared__ uint32_t s[kTile + kTile / 32];
+  const uint32_t k = blockIdx.y, p = sel3(P.p, k), pinv = sel3(P.pinv, k);
+  const uint32_t *tw = sel3p(P.tw, k), *itw = sel3p(P.itw, k);
+  const uint64_t off = k * E + (uint64_t)blockIdx.x * kTile;
+  uint32_t *f = FA + off;
+  for (uint32_t a = threadIdx.x; a < kTile; a += kTileThreads) s[pad(a)] = f[a];
+  uint32_t x[8];
+  for (uint32_t q = kTile / 8; q >= 1; q /= 8) {
+    __syncthreads();
+    const uint32_t b = tile_base(q);
+    sload8(s, b, q, x);
+    dif8(x, q, threadIdx.x & (q - 1), tw, p, pinv, q == kTile / 8 ? skip : 0u);
+    if (q > 1) sstore8(s, b, q, x);
+  }
+  {
+    uint32_t y[8];
+    if (FB) {
+      const uint4 *g4 = reinterpret_cast<const uint4 *>(FB + off + 8 * threadIdx.x);
+      const uint4 g0 = g4[0], g1 = g4[1];
+      y[0] = g0.x; y[1] = g0.y; y[2] = g0.z; y[3] = g0.w;
+      y[4] = g1.x; y[5] = g1.y; y[6] = g1.z; y[7] = g1.w;
+    } else {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) y[m] = x[m];
+    }
+#pragma unroll
+    for (int m = 0; m < 8; ++m) x[m] = mmul(x[m], y[m], p, pinv);
+  }
+  for (uint32_t q = 1; q <= kTile / 8; q *= 8) {
+    const uint32_t b = tile_base(q);
+    if (q > 1) {
+      __syncthreads();
+      sload8(s, b, q, x);
+    }
+    dit8(x, q, threadIdx.x & (q - 1), itw, p, pinv, q == kTile / 8 ? skip : 0u);
+    sstore8(s, b, q, x);
+  }
+  __syncthreads();
+  for (uint32_t a = threadIdx.x; a < kTile; a += kTileThreads) f[a] = s[pad(a)];
 }
 
 // ------------------------------------------------------------------ recombination and carries
@@ -421,9 +541,10 @@ __device__ __forceinline__ void run_gp(uint32_t g, uint32_t pm, uint32_t &G, uin
 
 // Carry into this thread's run, given the carry into the block; returns the
 // block's (G, P) through gb/pb when cin_block is ignored (pass 0 and 1).
+template <int NW>
 __device__ __forceinline__ uint32_t block_carry_in(uint32_t G, uint32_t Pp, uint32_t cin_block, uint32_t *gb,
                                                    uint32_t *pb) {
-  __shared__ uint32_t wg[kCarryThreads / 32], wp[kCarryThreads / 32];
+  __shared__ uint32_t wg[NW], wp[NW];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t gm = __ballot_sync(0xffffffffu, G), pmk = __ballot_sync(0xffffffffu, Pp);
   const uint64_t a = (uint64_t)(gm | pmk);
@@ -434,13 +555,13 @@ __device__ __forceinline__ uint32_t block_carry_in(uint32_t G, uint32_t Pp, uint
   }
   __syncthreads();
   uint32_t bgm = 0, bpm = 0;
-  for (uint32_t x = 0; x < kCarryThreads / 32; ++x) {
+  for (uint32_t x = 0; x < (uint32_t)NW; ++x) {
     bgm |= wg[x] << x;
     bpm |= wp[x] << x;
   }
   const uint64_t ab = (uint64_t)(bgm | bpm);
   if (gb) {
-    const uint32_t nw = kCarryThreads / 32;
+    const uint32_t nw = NW;
     const uint32_t g0 = (uint32_t)((ab + bgm) >> nw) & 1u, g1 = (uint32_t)((ab + bgm + 1) >> nw) & 1u;
     *gb = g0;
     *pb = g1 & ~g0 & 1u;
@@ -449,6 +570,92 @@ __device__ __forceinline__ uint32_t block_carry_in(uint32_t G, uint32_t Pp, uint
   const uint32_t warp_in = (uint32_t)((bsum ^ ab ^ bgm) >> warp) & 1u;
   const uint64_t wsum = a + gm + warp_in;
   return (uint32_t)((wsum ^ a ^ gm) >> lane) & 1u;
+}
+
+// ------------------------------------------------------------------ schoolbook products
+
+// Products of nc = na + nb <= kSchoolMax words: tpp threads per product, ppb
+// products per CTA of 128 threads.  Columns c = sum_j a_j b_(c-j) as 96-bit
+// sums (round robin over the product's threads), then the columns' three
+// words and the addend are added with their carries and words [lo, hi)
+// stored: by one thread per product for products of up to 128 words, else
+// by all 128 threads, each over a run of words, with carry-lookahead across
+// the runs as in the transform path.
+__global__ void __launch_bounds__(128) school_kernel(Opnd A, Opnd B, Opnd D, Out O, uint64_t cnt, uint32_t tpp,
+                                                     uint32_t ppb) {
+  extern __shared__ uint32_t sm[];
+  const uint32_t na = A.words, nb = B.words, nc = na + nb;
+  const uint32_t slot = threadIdx.x / tpp, lt = threadIdx.x % tpp;
+  const uint64_t i = (uint64_t)blockIdx.x * ppb + slot;
+  const bool live = i < cnt;
+  uint32_t *sa = sm + (size_t)slot * (4 * nc);
+  uint32_t *sb = sa + na;
+  uint32_t *clo = sb + nb, *cmid = clo + nc, *chi = cmid + nc;
+  if (live) {
+    for (uint32_t j = lt; j < na; j += tpp) sa[j] = opnd_word(A, i, j);
+    for (uint32_t j = lt; j < nb; j += tpp) sb[j] = opnd_word(B, i, j);
+  }
+  __syncthreads();
+  if (live) {
+    for (uint32_t c = lt; c < nc; c += tpp) {
+      const uint32_t j0 = c + 1 > nb ? c + 1 - nb : 0u;
+      const uint32_t j1 = c < na ? c : na - 1;
+      uint64_t s0 = 0;
+      uint32_t s1 = 0;
+      for (uint32_t j = j0; j <= j1 && j0 <= j1; ++j) {
+        const uint64_t pr = (uint64_t)sa[j] * sb[c - j];
+        s0 += pr;
+        s1 += s0 < pr ? 1u : 0u;
+      }
+      clo[c] = (uint32_t)s0;
+      cmid[c] = (uint32_t)(s0 >> 32);
+      chi[c] = s1;
+    }
+  }
+  __syncthreads();
+  // word sum s_c = lo_c + mid_(c-1) + hi_(c-2) + d_c (below 2^34)
+  auto wsum = [&](uint32_t c) -> uint64_t {
+    uint64_t v = opnd_word(D, i, c);
+    if (c < nc) v += clo[c];
+    if (c >= 1 && c - 1 < nc) v += cmid[c - 1];
+    if (c >= 2 && c - 2 < nc) v += chi[c - 2];
+    return v;
+  };
+  uint32_t *dst = O.p + i * O.stride;
+  if (ppb == 1) {
+    // one product per CTA: 128 runs of r <= 32 words, carry-lookahead across them
+    const uint32_t r = (O.hi + 127) / 128, c0 = threadIdx.x * r;
+    const uint32_t c1 = min(c0 + r, O.hi);
+    uint32_t prev = c0 >= 1 && c0 - 1 < O.hi ? (uint32_t)(wsum(c0 - 1) >> 32) : 0u;
+    uint32_t g = 0, pm = 0;
+    for (uint32_t c = c0; c < c1; ++c) {
+      const uint64_t sv = wsum(c);
+      const uint64_t v = (uint64_t)(uint32_t)sv + prev;
+      prev = (uint32_t)(sv >> 32);
+      g |= (uint32_t)(v >> 32) << (c - c0);
+      pm |= (v == 0xffffffffull ? 1u : 0u) << (c - c0);
+    }
+    const uint64_t a = (uint64_t)(g | pm);
+    const uint32_t G = (uint32_t)((a + g) >> r) & 1u;
+    const uint32_t Pp = (uint32_t)((a + g + 1) >> r) & 1u & ~G;
+    const uint32_t cin = block_carry_in<4>(G, Pp, 0u, nullptr, nullptr);
+    const uint32_t into = (uint32_t)((a + g + cin) ^ a ^ g);
+    prev = c0 >= 1 && c0 - 1 < O.hi ? (uint32_t)(wsum(c0 - 1) >> 32) : 0u;
+    for (uint32_t c = c0; c < c1; ++c) {
+      const uint64_t sv = wsum(c);
+      const uint32_t wv = (uint32_t)sv + prev + ((into >> (c - c0)) & 1u);
+      prev = (uint32_t)(sv >> 32);
+      if (c >= O.lo) dst[c - O.lo] = wv;
+    }
+    return;
+  }
+  if (!live || lt != 0) return;
+  uint64_t carry = 0;
+  for (uint32_t c = 0; c < O.hi; ++c) {
+    const uint64_t v = carry + wsum(c);
+    if (c >= O.lo) dst[c - O.lo] = (uint32_t)v;
+    carry = v >> 32;
+  }
 }
 
 // Pass 1: each block's carry function into flags[i * nb + b] (bit 0 generate,
@@ -462,7 +669,7 @@ __global__ void __launch_bounds__(kCarryThreads) carry_flags_kernel(WordSrc S, u
   if (c0 < hi_words) thread_words(S, i, c0, w, g, pm);
   uint32_t G, Pp, gb = 0, pb = 0;
   run_gp(g, pm, G, Pp);
-  (void)block_carry_in(G, Pp, 0u, &gb, &pb);
+  (void)block_carry_in<kCarryThreads / 32>(G, Pp, 0u, &gb, &pb);
   if (threadIdx.x == 0) flags[i * nb + b] = (uint8_t)(gb | (pb << 1));
 }
 
@@ -496,7 +703,7 @@ __global__ void __launch_bounds__(kCarryThreads) carry_store_kernel(WordSrc S, O
   uint32_t G, Pp;
   run_gp(g, pm, G, Pp);
   const uint32_t cin_block = (flags[i * nb + b] >> 2) & 1u;
-  const uint32_t cin = block_carry_in(G, Pp, cin_block, nullptr, nullptr);
+  const uint32_t cin = block_carry_in<kCarryThreads / 32>(G, Pp, cin_block, nullptr, nullptr);
   if (c0 >= O.hi) return;
   (void)apply_carries(w, g, pm, cin);
   uint32_t *dst = O.p + i * O.stride;
@@ -731,6 +938,7 @@ struct Plan {
   uint64_t nmax = 0;                         // longest transform
   std::vector<uint64_t> x_off, y_off, mu_off;  // per level
   uint64_t z_off[2] = {0, 0}, q_off = 0, h_off = 0, fa_off = 0, fb_off = 0, flags_off = 0;
+  uint64_t fwords = 0;                       // per-prime capacity of the transform buffers
   uint64_t words = 0;                        // arena size in words
 };
 
@@ -765,10 +973,11 @@ Plan make_plan(uint32_t L, uint64_t count, uint32_t t0_req) {
   at += 2 * KL;
   P.h_off = at;
   at += KL;
+  P.fwords = std::max<uint64_t>(4 * KL, kTile);
   P.fa_off = at;
-  at += 3 * 4 * KL;
+  at += 3 * P.fwords;
   P.fb_off = at;
-  at += 3 * 4 * KL;
+  at += 3 * P.fwords;
   P.flags_off = at;
   at += (4 * KL / kCarryBlock + 2 * P.K + 64) / 4 + 1;
   P.words = (at + 3) / 4 * 4;
@@ -811,8 +1020,9 @@ struct Runner {
     const uint64_t n = pow2_at_least(nc);
     const uint32_t logn = (uint32_t)ilog2(n);
     if (logn > kMaxLog) return set_error(RSA_ERR_ARG, "batch gcd tree: product above 2^27 words");
-    const uint64_t E = cnt * n;
-    if (E > 4 * P.KL) return set_error(RSA_ERR_ARG, "batch gcd tree: transform scratch exceeded");
+    const uint64_t E = cnt * n;                              // words per prime
+    const uint64_t Es = (E + kTile - 1) / kTile * kTile;     // per-prime stride: whole tiles
+    if (Es > P.fwords) return set_error(RSA_ERR_ARG, "batch gcd tree: transform scratch exceeded");
     for (int k = 0; k < 3; ++k) {
       const uint32_t p = kPrime[k];
       const uint32_t ninv = p - (uint32_t)((p - 1) / n);
@@ -820,55 +1030,70 @@ struct Runner {
       pr.scale[k] = (uint32_t)((uint64_t)ninv * r2 % p);
     }
     uint32_t *FA = at(P.fa_off), *FB = at(P.fb_off);
-    const uint32_t tile = (uint32_t)std::min<uint64_t>(n, kTile);
-    const int logt = ilog2(tile);
-    const int G = (int)logn - logt;
+    const int logt = ilog2(kTile);
+    const int G = std::max((int)logn - logt, 0);             // stages of half-length >= kTile: global passes
+    const uint32_t skip = (uint32_t)std::max(logt - (int)logn, 0);   // tiles of 2^skip shorter transforms
+    if (skip > 2) return set_error(RSA_ERR_ARG, "batch gcd tree: transform below 1024 words");
     auto load = [&](const Opnd &X, uint32_t *F) {
-      ntt_load_kernel<<<grid_for(E, 256), 256, 0, s>>>(X, F, E, logn);
+      ntt_load_kernel<<<grid_for(E, 256), 256, 0, s>>>(X, F, E, Es, logn);
       ++launches;
     };
-    auto forward = [&](uint32_t *F) {
+    // forward passes from the top: four stages, then two, then one
+    auto global_forward = [&](uint32_t *F) {
       int g = G;
       uint32_t logl = logn - 1;
-      while (g >= 2) {
-        dif4_kernel<<<dim3(grid_for(E / 4, 256), 3), 256, 0, s>>>(F, E, logl - 1, pr);
+      while (g >= 4) {
+        dif16_kernel<<<dim3(grid_for(Es / 16, 256), 3), 256, 0, s>>>(F, Es, logl - 3, pr);
+        logl -= 4;
+        g -= 4;
+        ++launches;
+      }
+      if (g >= 2) {
+        dif4_kernel<<<dim3(grid_for(Es / 4, 256), 3), 256, 0, s>>>(F, Es, logl - 1, pr);
         logl -= 2;
         g -= 2;
         ++launches;
       }
       if (g == 1) {
-        dif2_kernel<<<dim3(grid_for(E / 2, 256), 3), 256, 0, s>>>(F, E, logl, pr);
+        dif2_kernel<<<dim3(grid_for(Es / 2, 256), 3), 256, 0, s>>>(F, Es, logl, pr);
         ++launches;
       }
-      ntt_tile_kernel<<<dim3((unsigned)(E / tile), 3), 512, 0, s>>>(F, E, tile, 0, pr);
-      ++launches;
     };
-    load(A, FA);
-    forward(FA);
+    const dim3 tiles((unsigned)(Es / kTile), 3);
     if (!square) {
       load(B, FB);
-      forward(FB);
+      global_forward(FB);
+      ntt_tile_fwd_kernel<<<tiles, kTileThreads, 0, s>>>(FB, Es, skip, pr);
+      ++launches;
     }
-    pointwise_kernel<<<dim3(grid_for(E, 256), 3), 256, 0, s>>>(FA, square ? nullptr : FB, E, pr);
-    ntt_tile_kernel<<<dim3((unsigned)(E / tile), 3), 512, 0, s>>>(FA, E, tile, 1, pr);
-    launches += 2;
+    load(A, FA);
+    global_forward(FA);
+    ntt_tile_mul_kernel<<<tiles, kTileThreads, 0, s>>>(FA, square ? nullptr : FB, Es, skip, pr);
+    ++launches;
     {
+      // inverse passes from the bottom, the mirror of the forward order
       int g = G;
       uint32_t logl = (uint32_t)logt;
       if (g & 1) {
-        dit2_kernel<<<dim3(grid_for(E / 2, 256), 3), 256, 0, s>>>(FA, E, logl, pr);
+        dit2_kernel<<<dim3(grid_for(Es / 2, 256), 3), 256, 0, s>>>(FA, Es, logl, pr);
         ++logl;
         --g;
         ++launches;
       }
-      while (g >= 2) {
-        dit4_kernel<<<dim3(grid_for(E / 4, 256), 3), 256, 0, s>>>(FA, E, logl, pr);
+      if (g & 2) {
+        dit4_kernel<<<dim3(grid_for(Es / 4, 256), 3), 256, 0, s>>>(FA, Es, logl, pr);
         logl += 2;
         g -= 2;
         ++launches;
       }
+      while (g >= 4) {
+        dit16_kernel<<<dim3(grid_for(Es / 16, 256), 3), 256, 0, s>>>(FA, Es, logl, pr);
+        logl += 4;
+        g -= 4;
+        ++launches;
+      }
     }
-    WordSrc S{FA, E, logn, pr, D};
+    WordSrc S{FA, Es, logn, pr, D};
     const uint32_t nbk = (O.hi + kCarryBlock - 1) / kCarryBlock;
     uint8_t *flags = reinterpret_cast<uint8_t *>(at(P.flags_off));
     const uint64_t blocks = cnt * nbk;

@@ -336,3 +336,122 @@ def test_column_bound_fits_three_primes():
         assert (p - 1) % (1 << 27) == 0
     assert PRIMES[0] < PRIMES[1] < PRIMES[2] < 1 << 32
     assert PRIMES[0] * PRIMES[1] < 1 << 64
+
+
+def tile_rounds(a, c, tw, itw, other=None):
+    """The shared-memory kernels' grouping on one 4096-word tile: 512 threads,
+    thread t holds words b + k q (b = (t // q) 8q + t % q) for q = 512, 64, 8,
+    1 and runs the three stages at distances 4q, 2q, q; with ``other`` the
+    forward rounds are followed by the product and the inverse rounds."""
+    p = c["p"]
+    a = list(a)
+
+    def groups(q):
+        for t in range(512):
+            b = (t // q) * 8 * q + t % q
+            yield t % q, [b + k * q for k in range(8)]
+
+    def bf(i, j, w, inverse):
+        u, v = a[i], a[j]
+        if inverse:
+            v = mmul(v, w, c)
+            a[i], a[j] = (u + v) % p, (u - v) % p
+        else:
+            a[i], a[j] = (u + v) % p, mmul((u - v) % p, w, c)
+
+    for q in (512, 64, 8, 1):
+        for jp, ix in groups(q):
+            for k in range(4):
+                bf(ix[k], ix[k + 4], tw[4 * q + jp + k * q], False)
+            for k, w in ((0, tw[2 * q + jp]), (1, tw[2 * q + jp + q]), (4, tw[2 * q + jp]), (5, tw[2 * q + jp + q])):
+                bf(ix[k], ix[k + 2], w, False)
+            for k in range(0, 8, 2):
+                bf(ix[k], ix[k + 1], tw[q + jp], False)
+    if other is None:
+        return a
+    a = [mmul(x, y, c) for x, y in zip(a, other)]
+    for q in (1, 8, 64, 512):
+        for jp, ix in groups(q):
+            for k in range(0, 8, 2):
+                bf(ix[k], ix[k + 1], itw[q + jp], True)
+            for k, w in ((0, itw[2 * q + jp]), (1, itw[2 * q + jp + q]), (4, itw[2 * q + jp]), (5, itw[2 * q + jp + q])):
+                bf(ix[k], ix[k + 2], w, True)
+            for k in range(4):
+                bf(ix[k], ix[k + 4], itw[4 * q + jp + k * q], True)
+    return a
+
+
+def test_tile_rounds_equal_radix2_stages():
+    """Three stages per exchange on the 512-thread grouping equal the twelve
+    radix-2 stages (forward; and forward, product, inverse)."""
+    rng = random.Random(77)
+    c = prime_consts(PRIMES[1])
+    tw, itw = tables(c, 4096)
+    x = [rng.randrange(c["p"]) for _ in range(4096)]
+    y = [rng.randrange(c["p"]) for _ in range(4096)]
+    ref = list(x)
+    dif(ref, 4096, c, tw)
+    assert tile_rounds(x, c, tw, itw) == ref
+    yr = list(y)
+    dif(yr, 4096, c, tw)
+    prod = [mmul(u, v, c) for u, v in zip(ref, yr)]
+    dit(prod, 4096, c, itw)
+    assert tile_rounds(x, c, tw, itw, yr) == prod
+
+
+def pass16(a, h, c, tws, inverse):
+    """One global pass of four stages (distances 8h .. h forward, h .. 8h
+    inverse) on 16-word groups b + m h, b = 16h * block + j: at distance d h
+    word m pairs with m + d when m & d is clear, twiddle [d h + j + (m mod d) h]."""
+    p = c["p"]
+    a = list(a)
+    order = (1, 2, 4, 8) if inverse else (8, 4, 2, 1)
+    for blk in range(len(a) // (16 * h)):
+        for j in range(h):
+            b = blk * 16 * h + j
+            x = [a[b + m * h] for m in range(16)]
+            for d in order:
+                for m in range(16):
+                    if m & d:
+                        continue
+                    w = tws[d * h + j + (m & (d - 1)) * h]
+                    u, v = x[m], x[m + d]
+                    if inverse:
+                        v = mmul(v, w, c)
+                        x[m], x[m + d] = (u + v) % p, (u - v) % p
+                    else:
+                        x[m], x[m + d] = (u + v) % p, mmul((u - v) % p, w, c)
+            for m in range(16):
+                a[b + m * h] = x[m]
+    return a
+
+
+def test_radix16_pass_equals_four_stages():
+    """The four top stages of a length-2^11 transform as one pass equal the
+    radix-2 stages, forward and inverse."""
+    rng = random.Random(78)
+    c = prime_consts(PRIMES[2])
+    n = 1 << 11
+    tw, itw = tables(c, n)
+    x = [rng.randrange(c["p"]) for _ in range(2 * n)]          # two transforms back to back
+    p = c["p"]
+    ref = list(x)
+    length = n // 2
+    while length >= n // 16:                                  # stages n/2 .. n/16
+        for blk in range(0, len(ref), 2 * length):
+            for j in range(length):
+                u, v = ref[blk + j], ref[blk + j + length]
+                ref[blk + j] = (u + v) % p
+                ref[blk + j + length] = mmul((u - v) % p, tw[length + j], c)
+        length //= 2
+    assert pass16(x, n // 16, c, tw, False) == ref
+    back = list(ref)
+    length = n // 16
+    while length < n:
+        for blk in range(0, len(back), 2 * length):
+            for j in range(length):
+                u, v = back[blk + j], mmul(back[blk + j + length], itw[length + j], c)
+                back[blk + j] = (u + v) % p
+                back[blk + j + length] = (u - v) % p
+        length *= 2
+    assert pass16(ref, n // 16, c, itw, True) == back
