@@ -475,58 +475,144 @@ def bgcd_issued_products(count: int, L: int, blk: int, parts: int) -> float:
     return pre + count * per_lane
 
 
-def run_bgcd(args):
-    """Weak-key scan: g_i = gcd(n_i, product of the other moduli) over 16384
-    RSA-2048-shaped moduli (16 planted shared factors), one rsa_batch_gcd per
-    step, moduli device-resident; reported as modulus pairs/s.  e2e adds the
-    host-to-device copy of the moduli and the read-back of the flags."""
+def bgcd_tree_work(count: int, L: int, t0: int = -1, school_max: int = 512, tile: int = 4096) -> dict:
+    """Work of one tree-form batch GCD (the product sequence of
+    batch_gcd_tree_run): product tree, squares, Newton inverses (from one word
+    at the lowest remainder level t0, from the children above), the two
+    products of each remainder step, the leaves.  Products of up to
+    school_max words are schoolbook (word products); longer ones are
+    three-prime transforms (Montgomery products mod the primes: log2(n)/2 per
+    word and transform, one per word for the pointwise product, six per
+    column in each of the two recombination passes, 19 columns per 16 words)."""
+    if t0 < 0:
+        t0 = 4 if L >= 64 else 5 if L >= 32 else 6        # the library's default leaf level
+    K = 2
+    while K < count:
+        K *= 2
+    T = K.bit_length() - 1
+    t0 = min(t0, T)
+    w = {"school_products": 0, "montgomery_products": 0, "transforms": 0, "products": 0}
+
+    def mul(na, nb, cnt, hi, square=False):
+        w["products"] += cnt
+        if na + nb <= school_max:
+            w["school_products"] += cnt * na * nb
+            return
+        n = 1
+        while n < na + nb:
+            n *= 2
+        logn = n.bit_length() - 1
+        es = -(-cnt * n // tile) * tile
+        tr = 2 if square else 3
+        w["transforms"] += 3 * tr
+        w["montgomery_products"] += 3 * (tr * (es // 2) * logn + es) + 2 * 6 * cnt * (-(-hi // 16)) * 19
+
+    for t in range(T):
+        st = L << t
+        mul(st, st, K >> (t + 1), 2 * st)
+    for t in range(t0, T):
+        st, cnt = L << t, K >> t
+        k = 2 * st
+        mul(st, st, cnt, k, square=True)
+        if t == t0:
+            wd = 1
+        else:
+            mul(st, st, cnt, st)
+            wd = st
+        while wd < k:
+            mul(2 * wd, wd, cnt, 2 * wd)
+            mul(wd, wd, cnt, wd)
+            wd *= 2
+    for t in range(T - 1, t0 - 1, -1):
+        st, cnt = L << t, K >> t
+        k = 2 * st
+        mul(k, k, cnt, k)
+        mul(k, k, cnt, 2 * k + 1)
+    M = 2 * (L << t0) + 1
+    w["leaf_products"] = count * (M * 2 * L + 2 * L * L)
+    w.update(K=K, T=T, t0=t0)
+    return w
+
+
+def bgcd_measure(count: int, method: int, steps: int, warmup: int, e2e: bool = False, cpu: bool = False,
+                 check: bool = True) -> dict:
+    """One batch-GCD form timed on count RSA-2048-shaped moduli (planted shared
+    factors), moduli device-resident, CUDA events around `steps` calls; sampled
+    rows checked against the oracle.  e2e: the host-buffer entry point (moduli
+    in, flags out, copies timed).  cpu: the oracle on the host cores on a
+    bounded sample of rows."""
     import torch
     import oracle
-    from paper_1407_1465_gb300 import RsaContext, build, rsa_batch_gcd, rsa_batch_gcd_plan
+    from paper_1407_1465_gb300 import (RSA_GCD_TREE, RsaContext, build, rsa_batch_gcd_ex, rsa_batch_gcd_method,
+                                       rsa_batch_gcd_plan)
     build.build()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    count = args.count or 16384
     bits = 2048
     L = bits // 32
     rows, pairs = workloads.weak_key_moduli(count, bits)
-    ctx = RsaContext(0, mem_budget_bytes=8 << 30)
+    ctx = RsaContext(0, mem_budget_bytes=12 << 30)
     m = torch.from_numpy(rows.view(np.int32)).to(dev)
     g = torch.empty_like(m)
     fl = torch.empty(count, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
-    for _ in range(max(args.warmup, 3)):
-        rsa_batch_gcd(ctx.handle, bits, count, m, g, fl, sptr)
+    for _ in range(max(warmup, 3)):
+        rsa_batch_gcd_ex(ctx.handle, bits, count, m, g, fl, method, sptr)
     torch.cuda.synchronize()
     clk = ClockSampler(0)
     clk.start()
     launches0 = ctx.stats()["kernel_launches"]
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     ev[0].record(stream)
-    for _ in range(args.steps):
-        rsa_batch_gcd(ctx.handle, bits, count, m, g, fl, sptr)
+    for _ in range(steps):
+        rsa_batch_gcd_ex(ctx.handle, bits, count, m, g, fl, method, sptr)
     ev[1].record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
-    launches = ctx.stats()["kernel_launches"] - launches0
-    ms = ev[0].elapsed_time(ev[1]) / args.steps
-    pairs_per_s = count * (count - 1) / (ms / 1e3)
+    launches = (ctx.stats()["kernel_launches"] - launches0) // steps
+    ms = ev[0].elapsed_time(ev[1]) / steps
     flags = fl.cpu().numpy()
-    idx = sorted({0, count - 1, pairs[0][0], pairs[0][1]} | set(range(1, count, max(1, count // 6))))
-    og, of = oracle.batch_gcd(rows, rows=idx)
-    if not (np.array_equal(g.cpu().numpy().view(np.uint32)[idx], og) and np.array_equal(flags[idx], of)):
-        raise RuntimeError("batch gcd differs from the oracle")
-    blk, parts = rsa_batch_gcd_plan(ctx.handle, bits, count)
-    issued = bgcd_issued_products(count, L, blk, parts)
-    achieved = issued / (ms / 1e3) / 1e12
-    roofline = alu_roofline(achieved, 0, "issued word products of the three kernels (word reductions cost L per "
-                                         "word, half of a Montgomery multiplication)")
-    roofline.update({"traffic": None, "issued_products_per_step": issued,
-                     "definitional_products_per_step": count * (count - 1) * (2 * L * L + L)})
-    e2e = None
-    if not args.no_e2e:
-        # through rsa_batch_gcd_host: pinned host moduli in, host flags out, copies timed
+    if check:
+        idx = sorted({0, count - 1, pairs[0][0], pairs[0][1]} | set(range(1, count, max(1, count // 6))))
+        og, of = oracle.batch_gcd(rows, rows=idx)
+        if not (np.array_equal(g.cpu().numpy().view(np.uint32)[idx], og) and np.array_equal(flags[idx], of)):
+            raise RuntimeError("batch gcd differs from the oracle")
+        for i, j in pairs:
+            if flags[i] < 1 or flags[j] < 1:
+                raise RuntimeError("a planted shared factor was not found")
+    res = {"count": count, "ms_per_scan": ms, "pairs_per_s": count * (count - 1) / (ms / 1e3),
+           "moduli_per_s": count / (ms / 1e3), "gpu_launches": int(launches), "clocks": clocks,
+           "planted_pairs": len(pairs),
+           "flags": {"coprime": int((flags == 0).sum()), "factor_found": int((flags == 1).sum()),
+                     "whole_modulus": int((flags == 2).sum())}}
+    if method == RSA_GCD_TREE:
+        w = bgcd_tree_work(count, L)
+        pk = measured_imad_peak(0)
+        achieved = w["montgomery_products"] / (ms / 1e3) / 1e12
+        peak = pk["imad_lane_tops"] / 4
+        res["form"] = "tree"
+        res["roofline"] = {
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "T Montgomery products/s",
+            "frac": achieved / peak, "peak_source": "measured",
+            "peak_note": "rsa_imad_probe's independent 32-bit multiply lane rate %.2f T/s over 4 (a Montgomery "
+                         "product modulo a 32-bit prime: the 64-bit product, q = lo * p^-1, hi(q p))"
+                         % pk["imad_lane_tops"],
+            "what": "Montgomery products modulo the three transform primes per second over the whole scan "
+                    "(butterflies, pointwise products, recombination); schoolbook and leaf word products "
+                    "not counted",
+            "work": w, "traffic": None}
+    else:
+        blk, parts = rsa_batch_gcd_plan(ctx.handle, bits, count)
+        issued = bgcd_issued_products(count, L, blk, parts)
+        res["form"] = "scan"
+        res["block"], res["parts"] = blk, parts
+        res["roofline"] = alu_roofline(issued / (ms / 1e3) / 1e12, 0,
+                                       "issued word products of the three kernels (word reductions cost L per "
+                                       "word, half of a Montgomery multiplication)")
+        res["roofline"].update({"traffic": None, "issued_products_per_step": issued})
+    res["auto_form"] = "tree" if rsa_batch_gcd_method(ctx.handle, bits, count) == RSA_GCD_TREE else "scan"
+    if e2e:
         from paper_1407_1465_gb300 import rsa_batch_gcd_host
         host = torch.from_numpy(rows.view(np.int32)).pin_memory()
         fh = torch.empty(count, dtype=torch.int32).pin_memory()
@@ -534,36 +620,51 @@ def run_bgcd(args):
         torch.cuda.synchronize()
         ev2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         ev2[0].record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             rsa_batch_gcd_host(ctx.handle, bits, count, host, None, fh, sptr)
         ev2[1].record(stream)
         torch.cuda.synchronize()
-        ms2 = ev2[0].elapsed_time(ev2[1]) / args.steps
-        e2e = {"value": count * (count - 1) / (ms2 / 1e3), "unit": "pairs/s",
-               "h2d_bytes_per_step": int(rows.nbytes), "d2h_bytes_per_step": int(count * 4)}
-    cpu = None
-    if not args.no_cpu:
+        ms2 = ev2[0].elapsed_time(ev2[1]) / steps
+        res["e2e"] = {"value": count * (count - 1) / (ms2 / 1e3), "unit": "pairs/s", "form": res["auto_form"],
+                      "h2d_bytes_per_step": int(rows.nbytes), "d2h_bytes_per_step": int(count * 4)}
+    if cpu:
         threads = oracle.default_threads()
-        sample = list(range(0, count, max(1, count // (4 * threads))))[: 4 * threads]
+        sample = list(range(0, count, max(1, count // (2 * threads))))[: 2 * threads]
         t0 = time.perf_counter()
         oracle.batch_gcd(rows, rows=sample, threads=threads)
         dt = time.perf_counter() - t0
-        cpu = {"value": len(sample) * (count - 1) / dt, "unit": "pairs/s", "cores": threads,
-               "cpu_model": cpu_model(), "kind": "oracle",
-               "sample": "%d of the %d moduli (each against all %d others), oracle product mod n_i and Euclid, "
-                         "%d POSIX threads" % (len(sample), count, count - 1, threads)}
-    line = {"metric": "batch GCD modulus pairs/sec (RSA-2048 weak-key scan)", "value": pairs_per_s,
-            "unit": "pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "gpu_launches": int(launches),
-            "config": {"workload": "%d RSA-2048-shaped moduli (products of random odd 1024-bit halves), %d planted "
-                                   "shared factors, one rsa_batch_gcd per step" % (count, len(pairs)),
-                       "block": blk, "parts": parts, "l2": "moduli and block products stay L2-resident (4 MiB each)"},
-            "flags": {"coprime": int((flags == 0).sum()), "factor_found": int((flags == 1).sum()),
-                      "whole_modulus": int((flags == 2).sum())},
-            "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
-    print(json.dumps(line), flush=True)
+        res["cpu_baseline"] = {"value": len(sample) * (count - 1) / dt, "unit": "pairs/s", "cores": threads,
+                               "cpu_model": cpu_model(), "kind": "oracle",
+                               "sample": "%d of the %d moduli (each against all %d others), oracle product mod "
+                                         "n_i and Euclid, %d POSIX threads" % (len(sample), count, count - 1,
+                                                                                threads)}
     ctx.close()
+    return res
+
+
+def run_bgcd(args):
+    """Weak-key scan: g_i = gcd(n_i, product of the other moduli) over 131072
+    RSA-2048-shaped moduli (16 planted shared factors) by the product and
+    remainder trees, one rsa_batch_gcd_ex per step, moduli device-resident;
+    reported as modulus pairs/s (count (count - 1) per scan).  --count and
+    --gcd-form pick another size or the scan form."""
+    from paper_1407_1465_gb300 import RSA_GCD_SCAN, RSA_GCD_TREE
+    method = RSA_GCD_SCAN if args.gcd_form == "scan" else RSA_GCD_TREE
+    count = args.count or (16384 if method == RSA_GCD_SCAN else 131072)
+    r = bgcd_measure(count, method, args.steps, args.warmup, e2e=not args.no_e2e, cpu=not args.no_cpu)
+    line = {"metric": "batch GCD modulus pairs/sec (RSA-2048 weak-key scan)", "value": r["pairs_per_s"],
+            "unit": "pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_scan"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "gpu_launches": r["gpu_launches"], "moduli_per_s": r["moduli_per_s"],
+            "config": {"workload": "%d RSA-2048-shaped moduli (products of random odd 1024-bit halves), %d planted "
+                                   "shared factors, one rsa_batch_gcd_ex per step (%s form)"
+                                   % (count, r["planted_pairs"], r["form"]),
+                       "form": r["form"], "l2": "no flush: the scan's working set (moduli and tree levels) "
+                                                "exceeds L2 at this size" if r["form"] == "tree" else
+                                                "moduli and block products stay L2-resident (4 MiB each)"},
+            "flags": r["flags"], "roofline": r["roofline"], "clocks": r["clocks"], "e2e": r.get("e2e"),
+            "cpu_baseline": r.get("cpu_baseline")}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -974,6 +1075,7 @@ def main():
     ap.add_argument("--key-bits", type=int, default=0, help="serving: only requests under keys of this size")
     ap.add_argument("--mix-sizes", action="store_true", help="serving: batches take every modulus size")
     ap.add_argument("--mr-bits", type=int, default=1024, choices=[512, 1024, 2048], help="mr: candidate size")
+    ap.add_argument("--gcd-form", default="tree", choices=["tree", "scan"], help="bgcd: the form timed")
     ap.add_argument("--e-bits", type=int, default=0,
                     help="--kind public: a seeded random public exponent of this many bits instead of 65537")
     ap.add_argument("--kind", default="crt", choices=["crt", "public"],
@@ -1237,6 +1339,22 @@ def main():
             "kernel_launches_per_step": r["kernel_launches_per_step"], "tuning": r["tuning"],
             "issued_cuda_core_tprod_per_s": r["products_per_step"] / (r["ms_per_step"] / 1e3) / 1e12,
             "tensor_cores": tensor_share(r)}
+    if rank == 0 and ws == 1 and not args.no_configs and args.workload == "rsa2048" and args.kind == "crt":
+        # the weak-key scan (batch GCD): the tree form at 131072 moduli and, at 16384
+        # moduli, both forms (where the scan was the library's only one)
+        from paper_1407_1465_gb300 import RSA_GCD_SCAN, RSA_GCD_TREE
+        tree = bgcd_measure(131072, RSA_GCD_TREE, 3, 3)
+        small = {f: bgcd_measure(16384, m, 3, 3, check=(f == "tree")) for f, m in (("tree", RSA_GCD_TREE),
+                                                                                 ("scan", RSA_GCD_SCAN))}
+        line["bgcd"] = {
+            "what": "batch GCD weak-key scan g_i = gcd(n_i, prod_{j != i} n_j) over RSA-2048-shaped moduli with "
+                    "16 planted shared factors, one rsa_batch_gcd_ex per step; sampled rows checked against the "
+                    "oracle; the product/remainder-tree form at 131072 moduli, both forms at 16384",
+            "value": tree["pairs_per_s"], "unit": "pairs/s", "ms_per_scan": tree["ms_per_scan"],
+            "moduli": 131072, "moduli_per_s": tree["moduli_per_s"], "gpu_launches": tree["gpu_launches"],
+            "roofline": tree["roofline"],
+            "at_16384": {f: {"ms_per_scan": r["ms_per_scan"], "pairs_per_s": r["pairs_per_s"]}
+                         for f, r in small.items()}}
     if rank == 0 and ws == 1 and not args.no_latency and args.workload == "rsa2048" and args.kind == "crt":
         # the metric's latency half: ragged-batch request latency through the
         # serving loop (256 keys of 1024-4096 bits), offered load swept from

@@ -85,25 +85,42 @@ __device__ __forceinline__ uint32_t opnd_word(const Opnd &o, uint64_t i, uint32_
   return o.flip ? ~w : w;
 }
 
+// The reductions below take the borrow of a subtraction as a mask m (0 or all
+// ones) and add m * (-p) = (m ? p : 0) with one multiply-add, which keeps the
+// integer-ALU pipe (the transforms' busiest) free of compares and selects.
+__device__ __forceinline__ uint32_t add_masked_p(uint32_t x, uint32_t m, uint32_t p) { return x + m * (0u - p); }
+
 // Montgomery product a b R^-1 mod p for a, b < p < 2^32: with m = lo(ab) p^-1,
 // ab - mp is a multiple of 2^32 and its high word hi(ab) - hi(mp) lies in (-p, p).
 __device__ __forceinline__ uint32_t mmul(uint32_t a, uint32_t b, uint32_t p, uint32_t pinv) {
   const uint64_t t = (uint64_t)a * b;
   const uint32_t m = (uint32_t)t * pinv;
   const uint32_t mh = __umulhi(m, p);
-  const uint32_t th = (uint32_t)(t >> 32);
-  return th >= mh ? th - mh : th - mh + p;
+  uint32_t d, bm;
+  asm("sub.cc.u32 %0, %2, %3;\n\tsubc.u32 %1, 0, 0;" : "=r"(d), "=r"(bm) : "r"((uint32_t)(t >> 32)), "r"(mh));
+  return add_masked_p(d, bm, p);
 }
 
-// a + b mod p for a, b < p (the sum may wrap 2^32; then it is above p)
+// a + b mod p for a, b < p: s = a + b with carry c, r = s - p with borrow;
+// c - borrow is all ones exactly when a + b < p (a sum that wraps 2^32 is
+// above p and leaves s < p), and then s = r + p is the result.
 __device__ __forceinline__ uint32_t madd(uint32_t a, uint32_t b, uint32_t p) {
-  const uint32_t s = a + b;
-  return (s < a || s >= p) ? s - p : s;
+  uint32_t r, bm;
+  asm("{\n\t.reg .u32 s, c;\n\t"
+      "add.cc.u32 s, %2, %3;\n\t"
+      "addc.u32 c, 0, 0;\n\t"
+      "sub.cc.u32 %0, s, %4;\n\t"
+      "subc.u32 %1, c, 0;\n\t}"
+      : "=r"(r), "=r"(bm)
+      : "r"(a), "r"(b), "r"(p));
+  return add_masked_p(r, bm, p);
 }
 
+// a - b mod p for a, b < p
 __device__ __forceinline__ uint32_t msub(uint32_t a, uint32_t b, uint32_t p) {
-  const uint32_t d = a - b;
-  return a < b ? d + p : d;
+  uint32_t d, bm;
+  asm("sub.cc.u32 %0, %2, %3;\n\tsubc.u32 %1, 0, 0;" : "=r"(d), "=r"(bm) : "r"(a), "r"(b));
+  return add_masked_p(d, bm, p);
 }
 
 // prime k's entry of a per-prime parameter array (selects, no local copy)
@@ -165,45 +182,27 @@ __global__ void ntt_load_kernel(Opnd X, uint32_t *F, uint64_t E, uint64_t stride
   }
 }
 
-// Two decimation-in-frequency stages (len = 2h, then h) over quads
-// x0..x3 = F[base + j + {0, h, 2h, 3h}], base = 4h * block, j < h.
-__global__ void dif4_kernel(uint32_t *F, uint64_t E, uint32_t logh, Primes P) {
-  const uint32_t k = blockIdx.y, p = sel3(P.p, k), pinv = sel3(P.pinv, k);
-  uint32_t *f = F + k * E;
-  const uint32_t *tw = sel3p(P.tw, k);
-  const uint32_t h = 1u << logh, len = 2u * h;
-  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E / 4; q += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t j = (uint32_t)(q & (h - 1));
-    const uint64_t b = ((q >> logh) << (logh + 2)) + j;
-    const uint32_t x0 = f[b], x1 = f[b + h], x2 = f[b + 2 * h], x3 = f[b + 3 * h];
-    const uint32_t y0 = madd(x0, x2, p), y2 = mmul(msub(x0, x2, p), tw[len + j], p, pinv);
-    const uint32_t y1 = madd(x1, x3, p), y3 = mmul(msub(x1, x3, p), tw[len + j + h], p, pinv);
-    const uint32_t wh = tw[h + j];
-    f[b] = madd(y0, y1, p);
-    f[b + h] = mmul(msub(y0, y1, p), wh, p, pinv);
-    f[b + 2 * h] = madd(y2, y3, p);
-    f[b + 3 * h] = mmul(msub(y2, y3, p), wh, p, pinv);
-  }
-}
-
-// Four decimation-in-frequency stages (distances 8h, 4h, 2h, h) over the 16
-// words x_m = F[b + m h], b = 16h * block + j, j < h: at distance d h word m
-// pairs with m + d when m & d is clear, with twiddle tw[d h + j + (m mod d) h].
-__global__ void dif16_kernel(uint32_t *F, uint64_t E, uint32_t logh, Primes P) {
+// S decimation-in-frequency stages (distances 2^(S-1) h .. h) in one pass over
+// the 2^S words x_m = F[b + m h], b = 2^S h * block + j, j < h: at distance
+// d h word m pairs with m + d when m & d is clear, with twiddle
+// tw[d h + j + (m mod d) h].
+template <int S>
+__global__ void difr_kernel(uint32_t *F, uint64_t E, uint32_t logh, Primes P) {
+  constexpr int R = 1 << S;
   const uint32_t k = blockIdx.y, p = sel3(P.p, k), pinv = sel3(P.pinv, k);
   uint32_t *f = F + k * E;
   const uint32_t *tw = sel3p(P.tw, k);
   const uint32_t h = 1u << logh;
-  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E / 16; q += (uint64_t)gridDim.x * blockDim.x) {
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E / R; q += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t j = (uint32_t)(q & (h - 1));
-    const uint64_t b = ((q >> logh) << (logh + 4)) + j;
-    uint32_t x[16];
+    const uint64_t b = ((q >> logh) << (logh + S)) + j;
+    uint32_t x[R];
 #pragma unroll
-    for (int m = 0; m < 16; ++m) x[m] = f[b + (uint64_t)m * h];
+    for (int m = 0; m < R; ++m) x[m] = f[b + (uint64_t)m * h];
 #pragma unroll
-    for (int d = 8; d >= 1; d /= 2) {
+    for (int d = R / 2; d >= 1; d /= 2) {
 #pragma unroll
-      for (int m = 0; m < 16; ++m) {
+      for (int m = 0; m < R; ++m) {
         if (m & d) continue;
         const uint32_t a = x[m], c = x[m + d];
         x[m] = madd(a, c, p);
@@ -211,26 +210,28 @@ __global__ void dif16_kernel(uint32_t *F, uint64_t E, uint32_t logh, Primes P) {
       }
     }
 #pragma unroll
-    for (int m = 0; m < 16; ++m) f[b + (uint64_t)m * h] = x[m];
+    for (int m = 0; m < R; ++m) f[b + (uint64_t)m * h] = x[m];
   }
 }
 
-// The four decimation-in-time stages (distances h, 2h, 4h, 8h) over the same words.
-__global__ void dit16_kernel(uint32_t *F, uint64_t E, uint32_t logh, Primes P) {
+// The S decimation-in-time stages (distances h .. 2^(S-1) h) over the same words.
+template <int S>
+__global__ void ditr_kernel(uint32_t *F, uint64_t E, uint32_t logh, Primes P) {
+  constexpr int R = 1 << S;
   const uint32_t k = blockIdx.y, p = sel3(P.p, k), pinv = sel3(P.pinv, k);
   uint32_t *f = F + k * E;
   const uint32_t *itw = sel3p(P.itw, k);
   const uint32_t h = 1u << logh;
-  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E / 16; q += (uint64_t)gridDim.x * blockDim.x) {
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E / R; q += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t j = (uint32_t)(q & (h - 1));
-    const uint64_t b = ((q >> logh) << (logh + 4)) + j;
-    uint32_t x[16];
+    const uint64_t b = ((q >> logh) << (logh + S)) + j;
+    uint32_t x[R];
 #pragma unroll
-    for (int m = 0; m < 16; ++m) x[m] = f[b + (uint64_t)m * h];
+    for (int m = 0; m < R; ++m) x[m] = f[b + (uint64_t)m * h];
 #pragma unroll
-    for (int d = 1; d <= 8; d *= 2) {
+    for (int d = 1; d <= R / 2; d *= 2) {
 #pragma unroll
-      for (int m = 0; m < 16; ++m) {
+      for (int m = 0; m < R; ++m) {
         if (m & d) continue;
         const uint32_t a = x[m], c = mmul(x[m + d], itw[(uint32_t)d * h + j + (uint32_t)(m & (d - 1)) * h], p, pinv);
         x[m] = madd(a, c, p);
@@ -238,58 +239,7 @@ __global__ void dit16_kernel(uint32_t *F, uint64_t E, uint32_t logh, Primes P) {
       }
     }
 #pragma unroll
-    for (int m = 0; m < 16; ++m) f[b + (uint64_t)m * h] = x[m];
-  }
-}
-
-// One decimation-in-frequency stage of half-length len = 2^logl.
-__global__ void dif2_kernel(uint32_t *F, uint64_t E, uint32_t logl, Primes P) {
-  const uint32_t k = blockIdx.y, p = sel3(P.p, k), pinv = sel3(P.pinv, k);
-  uint32_t *f = F + k * E;
-  const uint32_t *tw = sel3p(P.tw, k);
-  const uint32_t len = 1u << logl;
-  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E / 2; q += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t j = (uint32_t)(q & (len - 1));
-    const uint64_t b = ((q >> logl) << (logl + 1)) + j;
-    const uint32_t u = f[b], v = f[b + len];
-    f[b] = madd(u, v, p);
-    f[b + len] = mmul(msub(u, v, p), tw[len + j], p, pinv);
-  }
-}
-
-// Two decimation-in-time stages (h, then len = 2h) over the same quads.
-__global__ void dit4_kernel(uint32_t *F, uint64_t E, uint32_t logh, Primes P) {
-  const uint32_t k = blockIdx.y, p = sel3(P.p, k), pinv = sel3(P.pinv, k);
-  uint32_t *f = F + k * E;
-  const uint32_t *itw = sel3p(P.itw, k);
-  const uint32_t h = 1u << logh, len = 2u * h;
-  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E / 4; q += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t j = (uint32_t)(q & (h - 1));
-    const uint64_t b = ((q >> logh) << (logh + 2)) + j;
-    const uint32_t x0 = f[b], x1 = f[b + h], x2 = f[b + 2 * h], x3 = f[b + 3 * h];
-    const uint32_t wh = itw[h + j];
-    const uint32_t v1 = mmul(x1, wh, p, pinv), v3 = mmul(x3, wh, p, pinv);
-    const uint32_t y0 = madd(x0, v1, p), y1 = msub(x0, v1, p);
-    const uint32_t y2 = madd(x2, v3, p), y3 = msub(x2, v3, p);
-    const uint32_t v2 = mmul(y2, itw[len + j], p, pinv), w3 = mmul(y3, itw[len + j + h], p, pinv);
-    f[b] = madd(y0, v2, p);
-    f[b + 2 * h] = msub(y0, v2, p);
-    f[b + h] = madd(y1, w3, p);
-    f[b + 3 * h] = msub(y1, w3, p);
-  }
-}
-
-__global__ void dit2_kernel(uint32_t *F, uint64_t E, uint32_t logl, Primes P) {
-  const uint32_t k = blockIdx.y, p = sel3(P.p, k), pinv = sel3(P.pinv, k);
-  uint32_t *f = F + k * E;
-  const uint32_t *itw = sel3p(P.itw, k);
-  const uint32_t len = 1u << logl;
-  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E / 2; q += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t j = (uint32_t)(q & (len - 1));
-    const uint64_t b = ((q >> logl) << (logl + 1)) + j;
-    const uint32_t u = f[b], v = mmul(f[b + len], itw[len + j], p, pinv);
-    f[b] = madd(u, v, p);
-    f[b + len] = msub(u, v, p);
+    for (int m = 0; m < R; ++m) f[b + (uint64_t)m * h] = x[m];
   }
 }
 
@@ -658,15 +608,27 @@ __global__ void __launch_bounds__(128) school_kernel(Opnd A, Opnd B, Opnd D, Out
   }
 }
 
-// Pass 1: each block's carry function into flags[i * nb + b] (bit 0 generate,
-// bit 1 propagate); one CTA per (product i, block b), i = blockIdx.x / nb.
-__global__ void __launch_bounds__(kCarryThreads) carry_flags_kernel(WordSrc S, uint32_t hi_words, uint32_t nb,
-                                                                    uint8_t *flags) {
+// Pass 1: each thread stores its words before the carries between words
+// (words [lo, hi) of the result) and its generate / propagate masks
+// (masks[blockIdx.x * kCarryThreads + thread], g | p << 16); each block's carry
+// function goes to flags[i * nb + b] (bit 0 generate, bit 1 propagate).  One
+// CTA per (product i, block b), i = blockIdx.x / nb.
+__global__ void __launch_bounds__(kCarryThreads) carry_words_kernel(WordSrc S, Out O, uint32_t nb, uint8_t *flags,
+                                                                    uint32_t *masks) {
   const uint64_t i = blockIdx.x / nb;
   const uint32_t b = (uint32_t)(blockIdx.x % nb);
   const uint32_t c0 = b * kCarryBlock + threadIdx.x * kCarryWords;
   uint32_t w[kCarryWords], g = 0, pm = 0;
-  if (c0 < hi_words) thread_words(S, i, c0, w, g, pm);
+  if (c0 < O.hi) {
+    thread_words(S, i, c0, w, g, pm);
+    uint32_t *dst = O.p + i * O.stride;
+#pragma unroll
+    for (int m = 0; m < (int)kCarryWords; ++m) {
+      const uint32_t c = c0 + (uint32_t)m;
+      if (c >= O.lo && c < O.hi) dst[c - O.lo] = w[m];
+    }
+  }
+  masks[(uint64_t)blockIdx.x * kCarryThreads + threadIdx.x] = g | (pm << 16);
   uint32_t G, Pp, gb = 0, pb = 0;
   run_gp(g, pm, G, Pp);
   (void)block_carry_in<kCarryThreads / 32>(G, Pp, 0u, &gb, &pb);
@@ -692,25 +654,27 @@ __global__ void carry_scan_kernel(uint8_t *flags, uint32_t nb, uint64_t cnt) {
   }
 }
 
-// Pass 3: words with their carries; words [lo, hi) are stored.
-__global__ void __launch_bounds__(kCarryThreads) carry_store_kernel(WordSrc S, Out O, uint32_t nb,
-                                                                    const uint8_t *flags) {
+// Pass 3: the carry into every word from the masks and the block's carry in;
+// the (few) stored words that receive one are incremented.
+__global__ void __launch_bounds__(kCarryThreads) carry_fix_kernel(Out O, uint32_t nb, const uint8_t *flags,
+                                                                  const uint32_t *masks) {
   const uint64_t i = blockIdx.x / nb;
   const uint32_t b = (uint32_t)(blockIdx.x % nb);
   const uint32_t c0 = b * kCarryBlock + threadIdx.x * kCarryWords;
-  uint32_t w[kCarryWords], g = 0, pm = 0;
-  if (c0 < O.hi) thread_words(S, i, c0, w, g, pm);
+  const uint32_t mk = masks[(uint64_t)blockIdx.x * kCarryThreads + threadIdx.x];
+  const uint32_t g = mk & 0xffffu, pm = mk >> 16;
   uint32_t G, Pp;
   run_gp(g, pm, G, Pp);
   const uint32_t cin_block = (flags[i * nb + b] >> 2) & 1u;
   const uint32_t cin = block_carry_in<kCarryThreads / 32>(G, Pp, cin_block, nullptr, nullptr);
-  if (c0 >= O.hi) return;
-  (void)apply_carries(w, g, pm, cin);
+  const uint64_t a = (uint64_t)(g | pm);
+  uint32_t into = (uint32_t)((a + g + cin) ^ a ^ g) & 0xffffu;
   uint32_t *dst = O.p + i * O.stride;
-#pragma unroll
-  for (int m = 0; m < (int)kCarryWords; ++m) {
-    const uint32_t c = c0 + (uint32_t)m;
-    if (c >= O.lo && c < O.hi) dst[c - O.lo] = w[m];
+  while (into) {
+    const uint32_t m = __ffs(into) - 1;
+    into &= into - 1;
+    const uint32_t c = c0 + m;
+    if (c >= O.lo && c < O.hi) dst[c - O.lo] += 1u;
   }
 }
 
@@ -748,10 +712,10 @@ __global__ void root_kernel(const uint32_t *X, uint64_t s, uint32_t *Z, uint64_t
 
 constexpr int kLeafThreads = 64;
 
-// Per-thread shared-memory words of the leaf kernel: n (L), N = n^2 (2L), the
-// reduced value r (2L + 2), the quotient u (L); column layout (word w of
-// thread x at w * blockDim + x).
-__host__ __device__ constexpr uint32_t leaf_words(uint32_t L) { return 6 * L + 2; }
+// Per-thread shared-memory words of the leaf kernel: n (L), N = n^2 (2L; the
+// reduced value r takes its place once the reduction is done), the quotient u
+// (L); column layout (word w of thread x at w * blockDim + x).
+__host__ __device__ constexpr uint32_t leaf_words(uint32_t L) { return 4 * L; }
 
 // One modulus per thread: z = Z(node of i at level t0) 2^(-32M) mod n_i^2 by
 // word-serial Montgomery reduction (window of 2L + 2 words in registers),
@@ -763,8 +727,8 @@ __global__ void __launch_bounds__(kLeafThreads) tree_leaf_kernel(const uint32_t 
                                                                  uint32_t t0, uint32_t *gcds, int32_t *flags) {
   extern __shared__ uint32_t sm[];
   const uint32_t bd = blockDim.x, x = threadIdx.x;
-  uint32_t *sn = sm + x, *sN = sm + (size_t)L * bd + x, *sr = sm + (size_t)3 * L * bd + x;
-  uint32_t *su = sm + (size_t)(5 * L + 2) * bd + x;
+  uint32_t *sn = sm + x, *sN = sm + (size_t)L * bd + x, *sr = sN;
+  uint32_t *su = sm + (size_t)(3 * L) * bd + x;
   const uint64_t i = (uint64_t)blockIdx.x * bd + x;
   const bool live = i < count;
   const uint64_t row = live ? i : count - 1;
@@ -939,6 +903,7 @@ struct Plan {
   std::vector<uint64_t> x_off, y_off, mu_off;  // per level
   uint64_t z_off[2] = {0, 0}, q_off = 0, h_off = 0, fa_off = 0, fb_off = 0, flags_off = 0;
   uint64_t fwords = 0;                       // per-prime capacity of the transform buffers
+  uint64_t carry_blocks = 0, masks_off = 0;  // carry scan: blocks of one product batch, their masks
   uint64_t words = 0;                        // arena size in words
 };
 
@@ -978,8 +943,14 @@ Plan make_plan(uint32_t L, uint64_t count, uint32_t t0_req) {
   at += 3 * P.fwords;
   P.fb_off = at;
   at += 3 * P.fwords;
+  // carry blocks of one transform product: cnt * ceil(hi / kCarryBlock) <=
+  // cnt (n + 1) / kCarryBlock + cnt with cnt n <= fwords and n >= 1024
+  P.carry_blocks = P.fwords / kCarryBlock + 2 * (P.fwords / 1024) + 2;
   P.flags_off = at;
-  at += (4 * KL / kCarryBlock + 2 * P.K + 64) / 4 + 1;
+  at += P.carry_blocks / 4 + 1;
+  at = (at + 3) / 4 * 4;
+  P.masks_off = at;
+  at += P.carry_blocks * kCarryThreads;
   P.words = (at + 3) / 4 * 4;
   // longest transform: the remainder step and the Newton step of level T - 1 (4 s_(T-1) words)
   P.nmax = std::max<uint64_t>(2 * KL, kTile);
@@ -1038,25 +1009,31 @@ struct Runner {
       ntt_load_kernel<<<grid_for(E, 256), 256, 0, s>>>(X, F, E, Es, logn);
       ++launches;
     };
-    // forward passes from the top: four stages, then two, then one
+    // global passes of up to four stages: forward from the top, the last pass
+    // taking the remainder; inverse from the bottom, the mirror order
+    auto pass = [&](bool inverse, int S, uint32_t *F, uint32_t logh) {
+      const dim3 grid(grid_for(Es >> S, 256), 3);
+      if (inverse) {
+        if (S == 1) ditr_kernel<1><<<grid, 256, 0, s>>>(F, Es, logh, pr);
+        else if (S == 2) ditr_kernel<2><<<grid, 256, 0, s>>>(F, Es, logh, pr);
+        else if (S == 3) ditr_kernel<3><<<grid, 256, 0, s>>>(F, Es, logh, pr);
+        else ditr_kernel<4><<<grid, 256, 0, s>>>(F, Es, logh, pr);
+      } else {
+        if (S == 1) difr_kernel<1><<<grid, 256, 0, s>>>(F, Es, logh, pr);
+        else if (S == 2) difr_kernel<2><<<grid, 256, 0, s>>>(F, Es, logh, pr);
+        else if (S == 3) difr_kernel<3><<<grid, 256, 0, s>>>(F, Es, logh, pr);
+        else difr_kernel<4><<<grid, 256, 0, s>>>(F, Es, logh, pr);
+      }
+      ++launches;
+    };
     auto global_forward = [&](uint32_t *F) {
       int g = G;
-      uint32_t logl = logn - 1;
-      while (g >= 4) {
-        dif16_kernel<<<dim3(grid_for(Es / 16, 256), 3), 256, 0, s>>>(F, Es, logl - 3, pr);
-        logl -= 4;
-        g -= 4;
-        ++launches;
-      }
-      if (g >= 2) {
-        dif4_kernel<<<dim3(grid_for(Es / 4, 256), 3), 256, 0, s>>>(F, Es, logl - 1, pr);
-        logl -= 2;
-        g -= 2;
-        ++launches;
-      }
-      if (g == 1) {
-        dif2_kernel<<<dim3(grid_for(Es / 2, 256), 3), 256, 0, s>>>(F, Es, logl, pr);
-        ++launches;
+      int logl = (int)logn - 1;                   // the next stage's half-length
+      while (g > 0) {
+        const int S = std::min(g, 4);
+        pass(false, S, F, (uint32_t)(logl - S + 1));
+        logl -= S;
+        g -= S;
       }
     };
     const dim3 tiles((unsigned)(Es / kTile), 3);
@@ -1071,35 +1048,29 @@ struct Runner {
     ntt_tile_mul_kernel<<<tiles, kTileThreads, 0, s>>>(FA, square ? nullptr : FB, Es, skip, pr);
     ++launches;
     {
-      // inverse passes from the bottom, the mirror of the forward order
       int g = G;
-      uint32_t logl = (uint32_t)logt;
-      if (g & 1) {
-        dit2_kernel<<<dim3(grid_for(Es / 2, 256), 3), 256, 0, s>>>(FA, Es, logl, pr);
-        ++logl;
-        --g;
-        ++launches;
+      int logl = logt;
+      const int first = g % 4;
+      if (first) {
+        pass(true, first, FA, (uint32_t)logl);
+        logl += first;
+        g -= first;
       }
-      if (g & 2) {
-        dit4_kernel<<<dim3(grid_for(Es / 4, 256), 3), 256, 0, s>>>(FA, Es, logl, pr);
-        logl += 2;
-        g -= 2;
-        ++launches;
-      }
-      while (g >= 4) {
-        dit16_kernel<<<dim3(grid_for(Es / 16, 256), 3), 256, 0, s>>>(FA, Es, logl, pr);
+      while (g > 0) {
+        pass(true, 4, FA, (uint32_t)logl);
         logl += 4;
         g -= 4;
-        ++launches;
       }
     }
     WordSrc S{FA, Es, logn, pr, D};
     const uint32_t nbk = (O.hi + kCarryBlock - 1) / kCarryBlock;
     uint8_t *flags = reinterpret_cast<uint8_t *>(at(P.flags_off));
+    uint32_t *masks = at(P.masks_off);
     const uint64_t blocks = cnt * nbk;
-    carry_flags_kernel<<<(unsigned)blocks, kCarryThreads, 0, s>>>(S, O.hi, nbk, flags);
+    if (blocks > P.carry_blocks) return set_error(RSA_ERR_ARG, "batch gcd tree: carry scratch exceeded");
+    carry_words_kernel<<<(unsigned)blocks, kCarryThreads, 0, s>>>(S, O, nbk, flags, masks);
     carry_scan_kernel<<<(unsigned)((cnt + 3) / 4), 128, 0, s>>>(flags, nbk, cnt);
-    carry_store_kernel<<<(unsigned)blocks, kCarryThreads, 0, s>>>(S, O, nbk, flags);
+    carry_fix_kernel<<<(unsigned)blocks, kCarryThreads, 0, s>>>(O, nbk, flags, masks);
     launches += 3;
     return 0;
   }
@@ -1117,16 +1088,20 @@ const Opnd kNone{nullptr, 0, 0, 0, 0};
 
 namespace rsagpu {
 
-// Lowest level of the remainder tree (its nodes hold 2^t0 moduli; the leaf
-// kernel reduces a node's value modulo each n_i^2 word by word).
-static uint32_t tree_leaf_level() {
+// Lowest level of the remainder tree: its nodes hold 2^t0 moduli and the leaf
+// kernel reduces a node's value modulo each n_i^2 word by word.  Nodes of
+// about 1024 words measured best on GB300 (131072 2048-bit moduli: t0 = 2
+// 215 ms, 3 209, 4 205, 5 207, 6 219; 1024- and 512-bit moduli: t0 = 5), so
+// t0 = log2(1024 / L).
+static uint32_t tree_leaf_level(uint32_t L) {
   const char *v = std::getenv("RSAGPU_GCD_TREE_T0");
-  const int t = v ? std::atoi(v) : 2;
+  const int def = L >= 64 ? 4 : L >= 32 ? 5 : 6;
+  const int t = v ? std::atoi(v) : def;
   return (uint32_t)std::min(std::max(t, 0), 6);
 }
 
 uint64_t batch_gcd_tree_bytes(uint32_t L, uint64_t count) {
-  const tree::Plan P = tree::make_plan(L, count, tree_leaf_level());
+  const tree::Plan P = tree::make_plan(L, count, tree_leaf_level(L));
   return P.words * 4 + 6 * P.nmax * 4;
 }
 
@@ -1134,7 +1109,7 @@ int batch_gcd_tree_run(Ctx *c, uint32_t nbits, uint64_t count, const uint32_t *m
                        int32_t *flags, cudaStream_t s) {
   using namespace tree;
   const uint32_t L = nbits / 32;
-  const Plan P = make_plan(L, count, tree_leaf_level());
+  const Plan P = make_plan(L, count, tree_leaf_level(L));
   if (P.nmax > (1ull << kMaxLog)) return set_error(RSA_ERR_ARG, "batch gcd tree: count * modulus words above 2^26");
   Workspace &w = c->ws(s);
   int rc;
