@@ -721,11 +721,14 @@ int batch_gcd_run(Ctx *c, uint32_t nbits, uint64_t count, const uint32_t *moduli
 namespace rsagpu {
 namespace {
 
-// From this many moduli the automatic choice takes the trees (when their
-// memory fits the context's budget).
-uint64_t gcd_tree_min() {
-  const char *v = std::getenv("RSAGPU_GCD_TREE_MIN");
-  return v ? std::strtoull(v, nullptr, 10) : 32768ull;
+// From this many modulus words (count x L) the automatic choice takes the
+// trees, when their memory fits the context's budget.  Measured on GB300: the
+// forms tie at 4096 2048-bit moduli (2^18 words); from 2^19 words the tree is
+// clearly ahead (8192 2048-bit moduli: scan 45 ms, tree under 24; 16384
+// 1024-bit: 43 against 12).
+uint64_t gcd_tree_min_words() {
+  const char *v = std::getenv("RSAGPU_GCD_TREE_MIN_WORDS");
+  return v ? std::strtoull(v, nullptr, 10) : (1ull << 19);
 }
 
 bool tree_fits(uint32_t L, uint64_t count) {
@@ -737,7 +740,7 @@ bool tree_fits(uint32_t L, uint64_t count) {
 int gcd_method(const Ctx *c, uint32_t nbits, uint64_t count, int method) {
   const uint32_t L = nbits / 32;
   if (method == RSA_GCD_AUTO) {
-    const bool tree = count >= 2 && count >= gcd_tree_min() && tree_fits(L, count) &&
+    const bool tree = count >= 2 && count * L >= gcd_tree_min_words() && tree_fits(L, count) &&
                       c->used + batch_gcd_tree_bytes(L, count) <= c->budget;
     return tree ? RSA_GCD_TREE : RSA_GCD_SCAN;
   }

@@ -167,6 +167,8 @@ def test_null_context_is_an_argument_error(lib):
     calls = {
         "rsa_batch_gcd": lambda: lib.rsa_batch_gcd(None, 2048, 4, None, None, None, None),
         "rsa_batch_gcd_plan": lambda: lib.rsa_batch_gcd_plan(None, 2048, 4, None, None),
+        "rsa_batch_gcd_ex": lambda: lib.rsa_batch_gcd_ex(None, 2048, 4, None, None, None, 2, None),
+        "rsa_batch_gcd_method": lambda: lib.rsa_batch_gcd_method(None, 2048, 4, None),
         "rsa_mr_batch": lambda: lib.rsa_mr_batch(None, 1024, 4, None, 1, None, None, None),
         "rsa_autotune_batch": lambda: lib.rsa_autotune_batch(None, 4, None, None, None, None, None, None, None),
         "rsa_modexp_batch": lambda: lib.rsa_modexp_batch(None, 4, None, None, None, None, None, None, None),
@@ -179,3 +181,18 @@ def test_null_context_is_an_argument_error(lib):
     for name, call in calls.items():
         assert call() == -1, name
 
+
+def test_batch_gcd_tree_bytes_host_checks(lib):
+    """rsa_batch_gcd_tree_bytes needs no device: sizes grow with the count, the
+    tree's size limit (count rounded up to a power of two times the modulus
+    words at most 2^26) and unsupported sizes are refused."""
+    import ctypes
+    b = ctypes.c_uint64(0)
+    assert lib.rsa_batch_gcd_tree_bytes(2048, 1 << 17, ctypes.byref(b)) == 0
+    small = b.value
+    assert lib.rsa_batch_gcd_tree_bytes(2048, 1 << 20, ctypes.byref(b)) == 0
+    assert b.value > 7 * small
+    assert lib.rsa_batch_gcd_tree_bytes(512, 1 << 22, ctypes.byref(b)) == 0
+    assert lib.rsa_batch_gcd_tree_bytes(2048, (1 << 20) + 1, ctypes.byref(b)) == -1
+    assert lib.rsa_batch_gcd_tree_bytes(4096, 4, ctypes.byref(b)) == -7
+    assert lib.rsa_batch_gcd_tree_bytes(2048, 4, None) == -1

@@ -228,3 +228,27 @@ def test_pub_tc_taken_mirrors_the_library_rule():
     assert bench.pub_tc_taken(2048, 65537, 4096, 0) and not bench.pub_tc_taken(2048, 65537, 4095, 0)
     assert bench.pub_tc_taken(2048, (1 << 200) + 1, 10, 3) and not bench.pub_tc_taken(2048, (1 << 200) + 1, 65536, 0)
     assert not bench.pub_tc_taken(4096, 65537, 65536, 0) and not bench.pub_tc_taken(2048, 65537, 65536, 1)
+
+
+def test_bgcd_tree_work_small_cases_by_hand():
+    """Two 2048-bit moduli: one 64 x 64-word schoolbook product (the root), the
+    leaf reduction of the root's 257 words modulo each n_i^2 (128 words), n_i^2
+    and the exact division (64^2 each).  Eight 512-bit moduli: the product tree's
+    4 + 2 + 1 schoolbook products of 16, 32, 64 words; no transform anywhere."""
+    w = bench.bgcd_tree_work(2, 64)
+    assert (w["K"], w["T"], w["t0"]) == (2, 1, 1)
+    assert w["school_products"] == 64 * 64 and w["montgomery_products"] == 0 and w["products"] == 1
+    assert w["leaf_products"] == 2 * (257 * 128 + 2 * 64 * 64)
+    w = bench.bgcd_tree_work(8, 16)
+    assert (w["T"], w["t0"]) == (3, 3)
+    assert w["school_products"] == 4 * 16 * 16 + 2 * 32 * 32 + 64 * 64 and w["montgomery_products"] == 0
+    assert w["leaf_products"] == 8 * ((2 * 128 + 1) * 32 + 2 * 16 * 16)
+
+
+def test_bgcd_tree_work_transform_count():
+    """131072 2048-bit moduli: the remainder tree's levels from t0 = 4 each run
+    two transform products (q and the quotient step) of 4 s_t words; every
+    transform product is counted once per prime and transform."""
+    w = bench.bgcd_tree_work(131072, 64)
+    assert (w["K"], w["T"], w["t0"]) == (131072, 17, 4)
+    assert w["transforms"] % 3 == 0 and w["montgomery_products"] > 1e11

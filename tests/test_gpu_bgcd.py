@@ -1,4 +1,4 @@
-"""GPU parity of the batch GCD (weak-key detection) against the oracle.
+"""GPU parity of the batch GCD (weak-key detection), scan form, against the oracle.
 
 Exact comparison of every g_i and flag: planted sharing read off known
 factorisations (small moduli in wide limb slots, leading zero limbs), real
@@ -36,9 +36,10 @@ def ctx(torch_cuda):
 
 
 def gpu_gcd(torch, ctx, nbits, rows):
+    """The scan form (RSA_GCD_SCAN); the tree form has its own tests."""
     rows = np.ascontiguousarray(rows, dtype=np.uint32)
     t = torch.from_numpy(rows.view(np.int32)).cuda()
-    g, f = ctx.batch_gcd(nbits, t)
+    g, f = ctx.batch_gcd(nbits, t, method=1)
     torch.cuda.synchronize()
     return g.cpu().numpy().view(np.uint32).reshape(rows.shape), f.cpu().numpy()
 
