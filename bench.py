@@ -477,9 +477,9 @@ def bgcd_issued_products(count: int, L: int, blk: int, parts: int) -> float:
 
 def bgcd_tree_work(count: int, L: int, t0: int = -1, school_max: int = 512, tile: int = 4096) -> dict:
     """Work of one tree-form batch GCD (the product sequence of
-    batch_gcd_tree_run): product tree, squares, Newton inverses (from one word
-    at the lowest remainder level t0, from the children above), the two
-    products of each remainder step, the leaves.  Products of up to
+    batch_gcd_tree_run): product tree; per remainder level from the top the
+    squares, the inverses (Newton from one word at the top level, one product
+    from the parent's below), the two products of the remainder step; the leaves.  Products of up to
     school_max words are schoolbook (word products); longer ones are
     three-prime transforms (Montgomery products mod the primes: log2(n)/2 per
     word and transform, one per word for the pointwise product, six per
@@ -510,22 +510,18 @@ def bgcd_tree_work(count: int, L: int, t0: int = -1, school_max: int = 512, tile
     for t in range(T):
         st = L << t
         mul(st, st, K >> (t + 1), 2 * st)
-    for t in range(t0, T):
-        st, cnt = L << t, K >> t
-        k = 2 * st
-        mul(st, st, cnt, k, square=True)
-        if t == t0:
-            wd = 1
-        else:
-            mul(st, st, cnt, st)
-            wd = st
-        while wd < k:
-            mul(2 * wd, wd, cnt, 2 * wd)
-            mul(wd, wd, cnt, wd)
-            wd *= 2
     for t in range(T - 1, t0 - 1, -1):
         st, cnt = L << t, K >> t
         k = 2 * st
+        mul(st, st, cnt, k, square=True)
+        if t == T - 1:
+            wd = 1
+            while wd < k:
+                mul(2 * wd, wd, cnt, 2 * wd)
+                mul(wd, wd, cnt, wd)
+                wd *= 2
+        else:
+            mul(k, k, cnt, k)
         mul(k, k, cnt, k)
         mul(k, k, cnt, 2 * k + 1)
     M = 2 * (L << t0) + 1

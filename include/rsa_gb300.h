@@ -185,8 +185,8 @@ int rsa_batch_gcd(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *
  *   Needs rsa_batch_gcd_tree_bytes of device memory within the context's
  *   budget (3.8 GB for 2^17 moduli of 2048 bits, 34 GB for 2^20) and
  *   count (rounded up to a power of two) x nbits / 32 <= 2^26.
- * RSA_GCD_AUTO: the tree from count x nbits / 32 >= 2^19 (8192 moduli of 2048
- *   bits, 16384 of 1024, 32768 of 512) when it fits (the size limit and the
+ * RSA_GCD_AUTO: the tree from count x nbits / 32 >= 2^18 (4096 moduli of 2048
+ *   bits, 8192 of 1024, 16384 of 512) when it fits (the size limit and the
  *   memory budget), else the scan. */
 #define RSA_GCD_AUTO 0
 #define RSA_GCD_SCAN 1

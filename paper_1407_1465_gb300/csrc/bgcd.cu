@@ -722,13 +722,12 @@ namespace rsagpu {
 namespace {
 
 // From this many modulus words (count x L) the automatic choice takes the
-// trees, when their memory fits the context's budget.  Measured on GB300: the
-// forms tie at 4096 2048-bit moduli (2^18 words); from 2^19 words the tree is
-// clearly ahead (8192 2048-bit moduli: scan 45 ms, tree under 24; 16384
-// 1024-bit: 43 against 12).
+// trees, when their memory fits the context's budget.  Measured on GB300:
+// 4096 2048-bit moduli (2^18 words) scan 15.3 ms, tree 9.3; 2048 moduli scan
+// 5.4 ms.
 uint64_t gcd_tree_min_words() {
   const char *v = std::getenv("RSAGPU_GCD_TREE_MIN_WORDS");
-  return v ? std::strtoull(v, nullptr, 10) : (1ull << 19);
+  return v ? std::strtoull(v, nullptr, 10) : (1ull << 18);
 }
 
 bool tree_fits(uint32_t L, uint64_t count) {

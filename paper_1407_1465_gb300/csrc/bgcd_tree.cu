@@ -13,10 +13,10 @@
 //     2^(32k) with q = Z_{t+1}[v/2] mu_t[v] mod 2^(32k).  Z_t[v] is congruent
 //     to P 2^(-e) modulo Y_t[v] (P = X_T, e a multiple of 32) and stays below
 //     (T - t + 1) Y_t[v] with no subtraction, in k + 1 words;
-//   * mu at the lowest level of the remainder tree by Newton's iteration from
-//     one word (mu_hi = H mu + mu mod 2^(32w), H the words w..2w of Y mu);
-//     above it from the children (-mu_a mu_b = mu_a ~mu_b + mu_a mod 2^(32 s_t))
-//     and one Newton step;
+//   * mu at the top level of the remainder tree (the root's two children) by
+//     Newton's iteration from one word (mu_hi = H mu + mu mod 2^(32w), H the
+//     words w..2w of Y mu); below it from the parent, one product per node:
+//     mu_parent = -(Y_a Y_b)^-1, so mu_a = Y_b mu_parent mod 2^(32k);
 //   * at the leaves, per modulus: Z of its level-t0 node reduced modulo n_i^2
 //     word by word (Montgomery), so z = P 2^(-e') mod n_i^2, a multiple of n_i;
 //     u = z / n_i (exact division, word by word from the bottom) is
@@ -64,12 +64,13 @@ struct Primes {
   const uint32_t *tw[3], *itw[3];           // nested twiddle tables: tw[len + j] = w_(2 len)^j R mod p
 };
 
-// Operand i of a batch: row (i >> shift) at p + row * stride, `words` words
-// (zero beyond), complemented bitwise when flip is set.
+// Operand i of a batch: row (i >> shift) ^ xr at p + row * stride (xr = 1:
+// the sibling's row), `words` words (zero beyond), complemented bitwise when
+// flip is set.
 struct Opnd {
   const uint32_t *p;
   uint64_t stride;
-  uint32_t shift, words, flip;
+  uint32_t shift, words, flip, xr;
 };
 
 // Output of product i: words [lo, hi) of the result at p + i * stride.
@@ -81,7 +82,7 @@ struct Out {
 
 __device__ __forceinline__ uint32_t opnd_word(const Opnd &o, uint64_t i, uint32_t j) {
   if (j >= o.words) return 0u;
-  const uint32_t w = o.p[(i >> o.shift) * o.stride + j];
+  const uint32_t w = o.p[((i >> o.shift) ^ o.xr) * o.stride + j];
   return o.flip ? ~w : w;
 }
 
@@ -900,7 +901,8 @@ struct Plan {
   uint32_t L = 0, T = 0, t0 = 0;
   uint64_t K = 0, KL = 0;
   uint64_t nmax = 0;                         // longest transform
-  std::vector<uint64_t> x_off, y_off, mu_off;  // per level
+  std::vector<uint64_t> x_off;               // product tree levels
+  uint64_t y_off = 0, mu_off[2] = {0, 0};    // remainder-tree level buffers
   uint64_t z_off[2] = {0, 0}, q_off = 0, h_off = 0, fa_off = 0, fb_off = 0, flags_off = 0;
   uint64_t fwords = 0;                       // per-prime capacity of the transform buffers
   uint64_t carry_blocks = 0, masks_off = 0;  // carry scan: blocks of one product batch, their masks
@@ -921,14 +923,14 @@ Plan make_plan(uint32_t L, uint64_t count, uint32_t t0_req) {
     P.x_off[t] = at;
     at += KL;
   }
-  P.y_off.assign(P.T + 1, 0);
-  P.mu_off.assign(P.T + 1, 0);
-  for (uint32_t t = P.t0; t < P.T; ++t) {
-    P.y_off[t] = at;
-    at += 2 * KL;
-    P.mu_off[t] = at;
-    at += 2 * KL;
-  }
+  // one level of the remainder tree at a time: its squares, its mu and its
+  // parent's mu (both levels hold 2 KL words)
+  P.y_off = at;
+  at += 2 * KL;
+  P.mu_off[0] = at;
+  at += 2 * KL;
+  P.mu_off[1] = at;
+  at += 2 * KL;
   const uint64_t zwords = 2 * KL + 4 * (P.K >> P.t0) + 4;
   P.z_off[0] = at;
   at += zwords;
@@ -1076,11 +1078,12 @@ struct Runner {
   }
 };
 
-Opnd opnd(const uint32_t *p, uint64_t stride, uint32_t words, uint32_t shift = 0, uint32_t flip = 0) {
-  return Opnd{p, stride, shift, words, flip};
+Opnd opnd(const uint32_t *p, uint64_t stride, uint32_t words, uint32_t shift = 0, uint32_t flip = 0,
+          uint32_t xr = 0) {
+  return Opnd{p, stride, shift, words, flip, xr};
 }
 
-const Opnd kNone{nullptr, 0, 0, 0, 0};
+const Opnd kNone{nullptr, 0, 0, 0, 0, 0};
 
 }  // namespace
 }  // namespace tree
@@ -1157,50 +1160,42 @@ int batch_gcd_tree_run(Ctx *c, uint32_t nbits, uint64_t count, const uint32_t *m
                     Out{X(t + 1), 2 * st, 0, (uint32_t)(2 * st)}, K >> (t + 1), false)))
       return rc;
   }
-  // squares and mu for the levels of the remainder tree
-  uint32_t *H = R.at(P.h_off);
-  for (uint32_t t = t0; t < T; ++t) {
-    const uint64_t st = sz(t), k = 2 * st, cnt = K >> t;
-    uint32_t *Y = R.at(P.y_off[t]), *mu = R.at(P.mu_off[t]);
-    if ((rc = R.mul(opnd(X(t), st, (uint32_t)st), kNone, kNone, Out{Y, k, 0, (uint32_t)k}, cnt, true))) return rc;
-    uint64_t wd;
-    if (t == t0) {
-      mu_word_kernel<<<R.grid_for(cnt, 256), 256, 0, s>>>(Y, k, mu, k, cnt);
-      ++R.launches;
-      wd = 1;
-    } else {
-      // -mu_a mu_b = mu_a ~mu_b + mu_a mod 2^(32 s_t); children's rows hold s_t words
-      uint32_t *mc = R.at(P.mu_off[t - 1]);
-      if ((rc = R.mul(opnd(mc, 2 * st, (uint32_t)st), opnd(mc + st, 2 * st, (uint32_t)st, 0, 1),
-                      opnd(mc, 2 * st, (uint32_t)st), Out{mu, k, 0, (uint32_t)st}, cnt, false)))
-        return rc;
-      wd = st;
-    }
-    for (; wd < k; wd *= 2) {
-      const uint32_t w32 = (uint32_t)wd;
-      if ((rc = R.mul(opnd(Y, k, 2 * w32), opnd(mu, k, w32), kNone, Out{H, wd, w32, 2 * w32}, cnt, false)) ||
-          (rc = R.mul(opnd(H, wd, w32), opnd(mu, k, w32), opnd(mu, k, w32), Out{mu + wd, k, 0, w32}, cnt, false)))
-        return rc;
-    }
-  }
-  // remainder tree
-  int cur = 0;
+  // remainder tree, one level at a time from the top: Y = X_t^2; mu = -Y^-1
+  // mod 2^(32k) by Newton from one word at the top level, below it from the
+  // parent (mu_a = Y_b mu_parent mod 2^(32k)); then q and the quotient step
+  uint32_t *H = R.at(P.h_off), *q = R.at(P.q_off), *Y = R.at(P.y_off);
+  int cur = 0, mcur = 0;
   {
     const uint64_t zs = 2 * sz(T) + 4;
     root_kernel<<<R.grid_for(zs, 256), 256, 0, s>>>(X(T), sz(T), R.at(P.z_off[cur]), zs);
     ++R.launches;
   }
-  uint32_t *q = R.at(P.q_off);
   for (uint32_t t = T; t-- > t0;) {
     const uint64_t st = sz(t), k = 2 * st, cnt = K >> t, zsp = 2 * sz(t + 1) + 4, zs = 2 * st + 4;
     const uint32_t k32 = (uint32_t)k;
     uint32_t *Zp = R.at(P.z_off[cur]), *Zc = R.at(P.z_off[cur ^ 1]);
-    uint32_t *Y = R.at(P.y_off[t]), *mu = R.at(P.mu_off[t]);
+    uint32_t *mu = R.at(P.mu_off[mcur]), *mup = R.at(P.mu_off[mcur ^ 1]);
+    if ((rc = R.mul(opnd(X(t), st, (uint32_t)st), kNone, kNone, Out{Y, k, 0, k32}, cnt, true))) return rc;
+    if (t == T - 1) {
+      mu_word_kernel<<<R.grid_for(cnt, 256), 256, 0, s>>>(Y, k, mu, k, cnt);
+      ++R.launches;
+      for (uint64_t wd = 1; wd < k; wd *= 2) {
+        const uint32_t w32 = (uint32_t)wd;
+        if ((rc = R.mul(opnd(Y, k, 2 * w32), opnd(mu, k, w32), kNone, Out{H, wd, w32, 2 * w32}, cnt, false)) ||
+            (rc = R.mul(opnd(H, wd, w32), opnd(mu, k, w32), opnd(mu, k, w32), Out{mu + wd, k, 0, w32}, cnt,
+                        false)))
+          return rc;
+      }
+    } else if ((rc = R.mul(opnd(Y, k, k32, 0, 0, 1), opnd(mup, 2 * k, k32, 1), kNone, Out{mu, k, 0, k32}, cnt,
+                           false))) {
+      return rc;
+    }
     if ((rc = R.mul(opnd(Zp, zsp, k32, 1), opnd(mu, k, k32), kNone, Out{q, k, 0, k32}, cnt, false)) ||
         (rc = R.mul(opnd(q, k, k32), opnd(Y, k, k32), opnd(Zp, zsp, 2 * k32 + 1, 1), Out{Zc, zs, k32, 2 * k32 + 1},
                     cnt, false)))
       return rc;
     cur ^= 1;
+    mcur ^= 1;
   }
   // leaves
   {

@@ -9,9 +9,9 @@ them against math.gcd on small sets, so that the bounds the kernels rely on
 steps, the transform indexing) are pinned before the GPU runs them:
 
   * product tree X_t (node of 2^t moduli, s_t = L 2^t words), padding leaves 1;
-  * Y_t = X_t^2, mu_t = -Y_t^-1 mod 2^(32*2s_t): from one word by Newton at the
-    lowest tree level, above it from the children (mu_a * ~mu_b + mu_a is
-    -mu_a mu_b) and one Newton step;
+  * Y_t = X_t^2, mu_t = -Y_t^-1 mod 2^(32*2s_t): by Newton from one word at
+    the top level of the remainder tree (the root's children), below it from
+    the parent: mu_a = Y_b mu_parent mod 2^(32*2s_t), one product;
   * Montgomery remainder tree Z_t = (Z_{t+1} + q Y_t) / 2^(32*2s_t),
     q = Z_{t+1} mu_t mod 2^(32*2s_t), Z_T = X_T, with no subtraction
     (Z_t < (T - t + 1) Y_t, stored in 2 s_t + 1 words);
@@ -81,28 +81,25 @@ def tree_gcds(mods, L, t0=2):
         X.append([X[t][2 * v] * X[t][2 * v + 1] for v in range(K >> (t + 1))])
         s = L << (t + 1)
         assert all(x < 1 << (W * s) for x in X[t + 1])
-    mu = {}
-    for t in range(t0, T):
-        s = L << t
-        Y = [x * x for x in X[t]]
-        if t == t0:
-            mu[t] = [neg_inverse(y, 2 * s) for y in Y]
-        else:
-            m = []
-            for v, y in enumerate(Y):
-                a, b = mu[t - 1][2 * v], mu[t - 1][2 * v + 1]
-                seed = (a * ((~b) % (1 << (W * s))) + a) % (1 << (W * s))    # -a b, s words
-                m.append(neg_inverse(y, 2 * s, seed, s))
-            mu[t] = m
     Z = [X[T][0]]
+    mu_parent = None
     for t in range(T - 1, t0 - 1, -1):
         s = L << t
         k = 2 * s
+        Y = [x * x for x in X[t]]
+        if t == T - 1:
+            mu_t = [neg_inverse(y, k) for y in Y]              # Newton from one word, top level only
+        else:
+            # from the parent: mu_parent = -(Y_a Y_b)^-1, so Y_b mu_parent = -Y_a^-1
+            mu_t = [Y[v ^ 1] * (mu_parent[v >> 1] % (1 << (W * k))) % (1 << (W * k)) for v in range(K >> t)]
+        for v, y in enumerate(Y):
+            assert (y * mu_t[v] + 1) % (1 << (W * k)) == 0
+        mu_parent = mu_t
         Zt = []
         for v in range(K >> t):
             zp = Z[v // 2]
-            y = X[t][v] ** 2
-            q = (zp % (1 << (W * k))) * mu[t][v] % (1 << (W * k))
+            y = Y[v]
+            q = (zp % (1 << (W * k))) * mu_t[v] % (1 << (W * k))
             tot = zp + q * y
             assert tot % (1 << (W * k)) == 0
             # the low half sums to 0 or 2^(32k): its carry is "low half of zp nonzero"

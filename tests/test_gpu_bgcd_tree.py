@@ -137,14 +137,14 @@ def test_tree_large_weak_key_scan(torch_cuda, ctx):
 
 
 def test_tree_auto_choice_and_host_form(torch_cuda, ctx):
-    """RSA_GCD_AUTO takes the tree from 2^19 modulus words (8192 2048-bit
-    moduli, 32768 512-bit) when it fits the budget; the host-buffer form
+    """RSA_GCD_AUTO takes the tree from 2^18 modulus words (4096 2048-bit
+    moduli, 16384 512-bit) when it fits the budget; the host-buffer form
     follows the same choice and equals both device forms."""
     from paper_1407_1465_gb300 import RsaContext, rsa_batch_gcd_method, rsa_batch_gcd_tree_bytes
-    assert rsa_batch_gcd_method(ctx.handle, 2048, 8192) == TREE
-    assert rsa_batch_gcd_method(ctx.handle, 2048, 8191) == SCAN
-    assert rsa_batch_gcd_method(ctx.handle, 512, 32768) == TREE
-    assert rsa_batch_gcd_method(ctx.handle, 512, 32767) == SCAN
+    assert rsa_batch_gcd_method(ctx.handle, 2048, 4096) == TREE
+    assert rsa_batch_gcd_method(ctx.handle, 2048, 4095) == SCAN
+    assert rsa_batch_gcd_method(ctx.handle, 512, 16384) == TREE
+    assert rsa_batch_gcd_method(ctx.handle, 512, 16383) == SCAN
     assert rsa_batch_gcd_method(ctx.handle, 512, 1) == SCAN
     small = RsaContext(0, mem_budget_bytes=rsa_batch_gcd_tree_bytes(2048, 32768) // 2)
     try:
