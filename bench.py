@@ -479,11 +479,14 @@ def bgcd_tree_work(count: int, L: int, t0: int = -1, school_max: int = 512, tile
     """Work of one tree-form batch GCD (the product sequence of
     batch_gcd_tree_run): product tree; per remainder level from the top the
     squares, the inverses (Newton from one word at the top level, one product
-    from the parent's below), the two products of the remainder step; the leaves.  Products of up to
-    school_max words are schoolbook (word products); longer ones are
-    three-prime transforms (Montgomery products mod the primes: log2(n)/2 per
-    word and transform, one per word for the pointwise product, six per
-    column in each of the two recombination passes, 19 columns per 16 words)."""
+    from the parent's below), the two products of the remainder step -- below
+    the top level with the level's shared transforms (each node's square
+    transformed once for two products, the parent's inverse and value once
+    for both children); the leaves.  Products of up to school_max words are schoolbook
+    (word products); longer ones are three-prime transforms, counted in
+    Montgomery products mod the primes: log2(n)/2 per word and transform, one
+    per word for a pointwise product (two for a kept square), six per column of
+    the recombination (19 columns per 16 words)."""
     if t0 < 0:
         t0 = 4 if L >= 64 else 5 if L >= 32 else 6        # the library's default leaf level
     K = 2
@@ -493,6 +496,17 @@ def bgcd_tree_work(count: int, L: int, t0: int = -1, school_max: int = 512, tile
     t0 = min(t0, T)
     w = {"school_products": 0, "montgomery_products": 0, "transforms": 0, "products": 0}
 
+    def log2(n):
+        return n.bit_length() - 1
+
+    def transform(cnt, n, pointwise=0):
+        es = -(-cnt * n // tile) * tile
+        w["transforms"] += 3
+        w["montgomery_products"] += 3 * ((es // 2) * log2(n) + pointwise * es)
+
+    def recombine(cnt, hi):
+        w["montgomery_products"] += 6 * cnt * (-(-hi // 16)) * 19
+
     def mul(na, nb, cnt, hi, square=False):
         w["products"] += cnt
         if na + nb <= school_max:
@@ -501,11 +515,11 @@ def bgcd_tree_work(count: int, L: int, t0: int = -1, school_max: int = 512, tile
         n = 1
         while n < na + nb:
             n *= 2
-        logn = n.bit_length() - 1
-        es = -(-cnt * n // tile) * tile
-        tr = 2 if square else 3
-        w["transforms"] += 3 * tr
-        w["montgomery_products"] += 3 * (tr * (es // 2) * logn + es) + 2 * 6 * cnt * (-(-hi // 16)) * 19
+        if not square:
+            transform(cnt, n)
+        transform(cnt, n, pointwise=1)
+        transform(cnt, n)
+        recombine(cnt, hi)
 
     for t in range(T):
         st = L << t
@@ -513,6 +527,22 @@ def bgcd_tree_work(count: int, L: int, t0: int = -1, school_max: int = 512, tile
     for t in range(T - 1, t0 - 1, -1):
         st, cnt = L << t, K >> t
         k = 2 * st
+        if t + 1 < T and 2 * k >= tile:
+            n = 2 * k
+            w["products"] += 3 * cnt
+            mul(st, st, cnt, k, square=True)            # Y = X^2 carried into words
+            transform(cnt, n)                           # Y^, kept for two products
+            transform(cnt // 2, n)                      # parent's mu
+            transform(cnt, n, pointwise=1)              # Y_sibling mu_parent, inverse
+            recombine(cnt, k)
+            transform(cnt, n)                           # mu
+            transform(cnt // 2, n)                      # parent's Z
+            transform(cnt, n, pointwise=1)              # mu Z_parent, inverse
+            recombine(cnt, k)
+            transform(cnt, n)                           # q
+            transform(cnt, n, pointwise=1)              # q Y, inverse
+            recombine(cnt, 2 * k + 1)
+            continue
         mul(st, st, cnt, k, square=True)
         if t == T - 1:
             wd = 1

@@ -392,6 +392,44 @@ __global__ void __launch_bounds__(kTileThreads) ntt_tile_mul_kernel(uint32_t *FA
   for (uint32_t a = threadIdx.x; a < kTile; a += kTileThreads) f[a] = s[pad(a)];
 }
 
+// Pointwise product of two forward-transformed batches and the inverse stages
+// below kTile, out of place (a cached transform stays intact): tile b of the
+// result belongs to transform i = b 4096 / n (n >= kTile) at offset o; its
+// factors are A's transform (i >> sha) ^ xra and B's transform i >> shb at
+// the same offset, each batch with its own per-prime stride.
+__global__ void __launch_bounds__(kTileThreads) ntt_tile_pinv_kernel(uint32_t *FO, uint64_t os, const uint32_t *FA,
+                                                                     uint64_t as, uint32_t sha, uint32_t xra,
+                                                                     const uint32_t *FB, uint64_t bs, uint32_t shb,
+                                                                     uint32_t logn, Primes P) {
+  __shared__ uint32_t s[kTile + kTile / 32];
+  const uint32_t k = blockIdx.y, p = sel3(P.p, k), pinv = sel3(P.pinv, k);
+  const uint32_t *itw = sel3p(P.itw, k);
+  const uint64_t first = (uint64_t)blockIdx.x * kTile;
+  const uint64_t i = first >> logn, o = first & ((1ull << logn) - 1);
+  const uint4 *a4 = reinterpret_cast<const uint4 *>(FA + k * as + ((((i >> sha) ^ xra)) << logn) + o + 8 * threadIdx.x);
+  const uint4 *b4 = reinterpret_cast<const uint4 *>(FB + k * bs + ((i >> shb) << logn) + o + 8 * threadIdx.x);
+  uint32_t x[8];
+  {
+    const uint4 a0 = a4[0], a1 = a4[1], b0 = b4[0], b1 = b4[1];
+    x[0] = mmul(a0.x, b0.x, p, pinv); x[1] = mmul(a0.y, b0.y, p, pinv);
+    x[2] = mmul(a0.z, b0.z, p, pinv); x[3] = mmul(a0.w, b0.w, p, pinv);
+    x[4] = mmul(a1.x, b1.x, p, pinv); x[5] = mmul(a1.y, b1.y, p, pinv);
+    x[6] = mmul(a1.z, b1.z, p, pinv); x[7] = mmul(a1.w, b1.w, p, pinv);
+  }
+  for (uint32_t q = 1; q <= kTile / 8; q *= 8) {
+    const uint32_t b = tile_base(q);
+    if (q > 1) {
+      __syncthreads();
+      sload8(s, b, q, x);
+    }
+    dit8(x, q, threadIdx.x & (q - 1), itw, p, pinv);
+    sstore8(s, b, q, x);
+  }
+  __syncthreads();
+  uint32_t *f = FO + k * os + first;
+  for (uint32_t a = threadIdx.x; a < kTile; a += kTileThreads) f[a] = s[pad(a)];
+}
+
 // ------------------------------------------------------------------ recombination and carries
 
 // Column j of product i as a 96-bit integer (three words): the residues,
@@ -905,6 +943,7 @@ struct Plan {
   uint64_t y_off = 0, mu_off[2] = {0, 0};    // remainder-tree level buffers
   uint64_t z_off[2] = {0, 0}, q_off = 0, h_off = 0, fa_off = 0, fb_off = 0, flags_off = 0;
   uint64_t fwords = 0;                       // per-prime capacity of the transform buffers
+  uint64_t cy_off = 0, cp_off = 0;           // cached transforms of one remainder level
   uint64_t carry_blocks = 0, masks_off = 0;  // carry scan: blocks of one product batch, their masks
   uint64_t words = 0;                        // arena size in words
 };
@@ -945,6 +984,12 @@ Plan make_plan(uint32_t L, uint64_t count, uint32_t t0_req) {
   at += 3 * P.fwords;
   P.fb_off = at;
   at += 3 * P.fwords;
+  // transforms one remainder level shares between its products: the squares
+  // (one per node) and a parent-level operand (one per two nodes)
+  P.cy_off = at;
+  at += 3 * P.fwords;
+  P.cp_off = at;
+  at += 3 * (P.fwords / 2);
   // carry blocks of one transform product: cnt * ceil(hi / kCarryBlock) <=
   // cnt (n + 1) / kCarryBlock + cnt with cnt n <= fwords and n >= 1024
   P.carry_blocks = P.fwords / kCarryBlock + 2 * (P.fwords / 1024) + 2;
@@ -976,6 +1021,102 @@ struct Runner {
     return (int)std::max<uint64_t>(1, std::min(want, cap));
   }
 
+  // scale of the recombination for transforms of length n
+  void set_scale(uint64_t n) {
+    for (int k = 0; k < 3; ++k) {
+      const uint32_t p = kPrime[k];
+      const uint32_t ninv = p - (uint32_t)((p - 1) / n);
+      const uint32_t r2 = powmod(to_mont(1, p), 2, p);
+      pr.scale[k] = (uint32_t)((uint64_t)ninv * r2 % p);
+    }
+  }
+
+  // global passes of up to four stages over Es words per prime: forward from
+  // the top (the last pass takes the remainder), inverse from the bottom
+  void pass(bool inverse, int S, uint32_t *F, uint64_t Es, uint32_t logh) {
+    const dim3 grid(grid_for(Es >> S, 256), 3);
+    if (inverse) {
+      if (S == 1) ditr_kernel<1><<<grid, 256, 0, s>>>(F, Es, logh, pr);
+      else if (S == 2) ditr_kernel<2><<<grid, 256, 0, s>>>(F, Es, logh, pr);
+      else if (S == 3) ditr_kernel<3><<<grid, 256, 0, s>>>(F, Es, logh, pr);
+      else ditr_kernel<4><<<grid, 256, 0, s>>>(F, Es, logh, pr);
+    } else {
+      if (S == 1) difr_kernel<1><<<grid, 256, 0, s>>>(F, Es, logh, pr);
+      else if (S == 2) difr_kernel<2><<<grid, 256, 0, s>>>(F, Es, logh, pr);
+      else if (S == 3) difr_kernel<3><<<grid, 256, 0, s>>>(F, Es, logh, pr);
+      else difr_kernel<4><<<grid, 256, 0, s>>>(F, Es, logh, pr);
+    }
+    ++launches;
+  }
+  void global_forward(uint32_t *F, uint64_t Es, uint32_t logn) {
+    int g = std::max((int)logn - (int)ilog2(kTile), 0);
+    int logl = (int)logn - 1;                     // the next stage's half-length
+    while (g > 0) {
+      const int S = std::min(g, 4);
+      pass(false, S, F, Es, (uint32_t)(logl - S + 1));
+      logl -= S;
+      g -= S;
+    }
+  }
+  void global_inverse(uint32_t *F, uint64_t Es, uint32_t logn) {
+    int g = std::max((int)logn - (int)ilog2(kTile), 0);
+    int logl = (int)ilog2(kTile);
+    const int first = g % 4;
+    if (first) {
+      pass(true, first, F, Es, (uint32_t)logl);
+      logl += first;
+      g -= first;
+    }
+    while (g > 0) {
+      pass(true, 4, F, Es, (uint32_t)logl);
+      logl += 4;
+      g -= 4;
+    }
+  }
+
+  // carry passes over the recombined columns of cnt products in F (per-prime
+  // stride Es, transforms of 2^logn words): words [O.lo, O.hi) of each, plus D
+  int carry(const uint32_t *F, uint64_t Es, uint32_t logn, uint64_t cnt, const Opnd &D, const Out &O) {
+    set_scale(1ull << logn);
+    WordSrc S{F, Es, logn, pr, D};
+    const uint32_t nbk = (O.hi + kCarryBlock - 1) / kCarryBlock;
+    uint8_t *flags = reinterpret_cast<uint8_t *>(at(P.flags_off));
+    uint32_t *masks = at(P.masks_off);
+    const uint64_t blocks = cnt * nbk;
+    if (blocks > P.carry_blocks) return set_error(RSA_ERR_ARG, "batch gcd tree: carry scratch exceeded");
+    carry_words_kernel<<<(unsigned)blocks, kCarryThreads, 0, s>>>(S, O, nbk, flags, masks);
+    carry_scan_kernel<<<(unsigned)((cnt + 3) / 4), 128, 0, s>>>(flags, nbk, cnt);
+    carry_fix_kernel<<<(unsigned)blocks, kCarryThreads, 0, s>>>(O, nbk, flags, masks);
+    launches += 3;
+    return 0;
+  }
+
+  // forward transforms (length 2^logn >= kTile) of cnt operands into F (per-prime
+  // stride cnt 2^logn, at most cap words)
+  int fwd(const Opnd &X, uint64_t cnt, uint32_t logn, uint32_t *F, uint64_t cap) {
+    const uint64_t E = cnt << logn;
+    if (logn < (uint32_t)ilog2(kTile) || 3 * E > cap)
+      return set_error(RSA_ERR_ARG, "batch gcd tree: cached transform out of range");
+    ntt_load_kernel<<<grid_for(E, 256), 256, 0, s>>>(X, F, E, E, logn);
+    ++launches;
+    global_forward(F, E, logn);
+    ntt_tile_fwd_kernel<<<dim3((unsigned)(E / kTile), 3), kTileThreads, 0, s>>>(F, E, 0, pr);
+    ++launches;
+    return 0;
+  }
+
+  // FO = inverse transform of the pointwise products of A's transforms
+  // (i >> sha) ^ xra (batch stride as) and B's transforms i >> shb (stride
+  // bs), i < cnt; FO's per-prime stride is cnt 2^logn
+  void mulinv(uint32_t *FO, const uint32_t *FA, uint64_t as, uint32_t sha, uint32_t xra, const uint32_t *FB,
+              uint64_t bs, uint32_t shb, uint64_t cnt, uint32_t logn) {
+    const uint64_t E = cnt << logn;
+    ntt_tile_pinv_kernel<<<dim3((unsigned)(E / kTile), 3), kTileThreads, 0, s>>>(FO, E, FA, as, sha, xra, FB, bs,
+                                                                                 shb, logn, pr);
+    ++launches;
+    global_inverse(FO, E, logn);
+  }
+
   // out = words [O.lo, O.hi) of A_i * B_i + D_i for i < cnt (B ignored when square)
   int mul(const Opnd &A, const Opnd &B, const Opnd &D, const Out &O, uint64_t cnt, bool square) {
     if (cnt == 0) return 0;
@@ -996,85 +1137,22 @@ struct Runner {
     const uint64_t E = cnt * n;                              // words per prime
     const uint64_t Es = (E + kTile - 1) / kTile * kTile;     // per-prime stride: whole tiles
     if (Es > P.fwords) return set_error(RSA_ERR_ARG, "batch gcd tree: transform scratch exceeded");
-    for (int k = 0; k < 3; ++k) {
-      const uint32_t p = kPrime[k];
-      const uint32_t ninv = p - (uint32_t)((p - 1) / n);
-      const uint32_t r2 = powmod(to_mont(1, p), 2, p);
-      pr.scale[k] = (uint32_t)((uint64_t)ninv * r2 % p);
-    }
     uint32_t *FA = at(P.fa_off), *FB = at(P.fb_off);
-    const int logt = ilog2(kTile);
-    const int G = std::max((int)logn - logt, 0);             // stages of half-length >= kTile: global passes
-    const uint32_t skip = (uint32_t)std::max(logt - (int)logn, 0);   // tiles of 2^skip shorter transforms
+    const uint32_t skip = (uint32_t)std::max((int)ilog2(kTile) - (int)logn, 0);   // tiles of 2^skip transforms
     if (skip > 2) return set_error(RSA_ERR_ARG, "batch gcd tree: transform below 1024 words");
-    auto load = [&](const Opnd &X, uint32_t *F) {
-      ntt_load_kernel<<<grid_for(E, 256), 256, 0, s>>>(X, F, E, Es, logn);
-      ++launches;
-    };
-    // global passes of up to four stages: forward from the top, the last pass
-    // taking the remainder; inverse from the bottom, the mirror order
-    auto pass = [&](bool inverse, int S, uint32_t *F, uint32_t logh) {
-      const dim3 grid(grid_for(Es >> S, 256), 3);
-      if (inverse) {
-        if (S == 1) ditr_kernel<1><<<grid, 256, 0, s>>>(F, Es, logh, pr);
-        else if (S == 2) ditr_kernel<2><<<grid, 256, 0, s>>>(F, Es, logh, pr);
-        else if (S == 3) ditr_kernel<3><<<grid, 256, 0, s>>>(F, Es, logh, pr);
-        else ditr_kernel<4><<<grid, 256, 0, s>>>(F, Es, logh, pr);
-      } else {
-        if (S == 1) difr_kernel<1><<<grid, 256, 0, s>>>(F, Es, logh, pr);
-        else if (S == 2) difr_kernel<2><<<grid, 256, 0, s>>>(F, Es, logh, pr);
-        else if (S == 3) difr_kernel<3><<<grid, 256, 0, s>>>(F, Es, logh, pr);
-        else difr_kernel<4><<<grid, 256, 0, s>>>(F, Es, logh, pr);
-      }
-      ++launches;
-    };
-    auto global_forward = [&](uint32_t *F) {
-      int g = G;
-      int logl = (int)logn - 1;                   // the next stage's half-length
-      while (g > 0) {
-        const int S = std::min(g, 4);
-        pass(false, S, F, (uint32_t)(logl - S + 1));
-        logl -= S;
-        g -= S;
-      }
-    };
     const dim3 tiles((unsigned)(Es / kTile), 3);
     if (!square) {
-      load(B, FB);
-      global_forward(FB);
+      ntt_load_kernel<<<grid_for(E, 256), 256, 0, s>>>(B, FB, E, Es, logn);
+      global_forward(FB, Es, logn);
       ntt_tile_fwd_kernel<<<tiles, kTileThreads, 0, s>>>(FB, Es, skip, pr);
-      ++launches;
+      launches += 2;
     }
-    load(A, FA);
-    global_forward(FA);
+    ntt_load_kernel<<<grid_for(E, 256), 256, 0, s>>>(A, FA, E, Es, logn);
+    global_forward(FA, Es, logn);
     ntt_tile_mul_kernel<<<tiles, kTileThreads, 0, s>>>(FA, square ? nullptr : FB, Es, skip, pr);
-    ++launches;
-    {
-      int g = G;
-      int logl = logt;
-      const int first = g % 4;
-      if (first) {
-        pass(true, first, FA, (uint32_t)logl);
-        logl += first;
-        g -= first;
-      }
-      while (g > 0) {
-        pass(true, 4, FA, (uint32_t)logl);
-        logl += 4;
-        g -= 4;
-      }
-    }
-    WordSrc S{FA, Es, logn, pr, D};
-    const uint32_t nbk = (O.hi + kCarryBlock - 1) / kCarryBlock;
-    uint8_t *flags = reinterpret_cast<uint8_t *>(at(P.flags_off));
-    uint32_t *masks = at(P.masks_off);
-    const uint64_t blocks = cnt * nbk;
-    if (blocks > P.carry_blocks) return set_error(RSA_ERR_ARG, "batch gcd tree: carry scratch exceeded");
-    carry_words_kernel<<<(unsigned)blocks, kCarryThreads, 0, s>>>(S, O, nbk, flags, masks);
-    carry_scan_kernel<<<(unsigned)((cnt + 3) / 4), 128, 0, s>>>(flags, nbk, cnt);
-    carry_fix_kernel<<<(unsigned)blocks, kCarryThreads, 0, s>>>(O, nbk, flags, masks);
-    launches += 3;
-    return 0;
+    launches += 2;
+    global_inverse(FA, Es, logn);
+    return carry(FA, Es, logn, cnt, D, O);
   }
 };
 
@@ -1175,6 +1253,36 @@ int batch_gcd_tree_run(Ctx *c, uint32_t nbits, uint64_t count, const uint32_t *m
     const uint32_t k32 = (uint32_t)k;
     uint32_t *Zp = R.at(P.z_off[cur]), *Zc = R.at(P.z_off[cur ^ 1]);
     uint32_t *mu = R.at(P.mu_off[mcur]), *mup = R.at(P.mu_off[mcur ^ 1]);
+    if (t + 1 < T && 2 * k >= kTile) {
+      // transforms shared within the level: Y^ serves the sibling's inverse and
+      // the quotient step, the parent's mu^ and Z^ serve both children.  Y is
+      // carried into words first: the pointwise square of X^ would hold the
+      // uncarried coefficients of X*X (up to s 2^64), and a product of those
+      // with k words would pass the three primes' range
+      const uint32_t logn = (uint32_t)ilog2(2 * k);
+      const uint64_t E = cnt << logn, Ep = (cnt / 2) << logn;
+      const uint64_t cap = 3 * P.fwords, capp = 3 * (P.fwords / 2);
+      uint32_t *CY = R.at(P.cy_off), *CP = R.at(P.cp_off), *FA = R.at(P.fa_off), *FO = R.at(P.fb_off);
+      if ((rc = R.mul(opnd(X(t), st, (uint32_t)st), kNone, kNone, Out{Y, k, 0, k32}, cnt, true)) ||
+          (rc = R.fwd(opnd(Y, k, k32), cnt, logn, CY, cap)) ||
+          (rc = R.fwd(opnd(mup, 2 * k, k32), cnt / 2, logn, CP, capp)))
+        return rc;
+      R.mulinv(FO, CY, E, 0, 1, CP, Ep, 1, cnt, logn);                 // Y_sibling * mu_parent
+      if ((rc = R.carry(FO, E, logn, cnt, kNone, Out{mu, k, 0, k32})) ||
+          (rc = R.fwd(opnd(mu, k, k32), cnt, logn, FA, cap)) ||
+          (rc = R.fwd(opnd(Zp, zsp, k32), cnt / 2, logn, CP, capp)))
+        return rc;
+      R.mulinv(FO, FA, E, 0, 0, CP, Ep, 1, cnt, logn);                 // mu * Z_parent
+      if ((rc = R.carry(FO, E, logn, cnt, kNone, Out{q, k, 0, k32})) ||
+          (rc = R.fwd(opnd(q, k, k32), cnt, logn, FA, cap)))
+        return rc;
+      R.mulinv(FO, FA, E, 0, 0, CY, E, 0, cnt, logn);                  // q * Y
+      if ((rc = R.carry(FO, E, logn, cnt, opnd(Zp, zsp, 2 * k32 + 1, 1), Out{Zc, zs, k32, 2 * k32 + 1})))
+        return rc;
+      cur ^= 1;
+      mcur ^= 1;
+      continue;
+    }
     if ((rc = R.mul(opnd(X(t), st, (uint32_t)st), kNone, kNone, Out{Y, k, 0, k32}, cnt, true))) return rc;
     if (t == T - 1) {
       mu_word_kernel<<<R.grid_for(cnt, 256), 256, 0, s>>>(Y, k, mu, k, cnt);

@@ -452,3 +452,16 @@ def test_radix16_pass_equals_four_stages():
                 back[blk + j + length] = (u - v) % p
         length *= 2
     assert pass16(ref, n // 16, c, itw, True) == back
+
+
+def test_uncarried_square_would_pass_the_primes_range():
+    """Why a node's square is carried into 32-bit words before its transform is
+    kept for later products: the pointwise square of X^ stands for the
+    uncarried coefficients of X*X (up to s 2^64 for s-word X), and their
+    product with a k = 2s-word operand has columns up to 2s * s 2^64 * 2^32,
+    beyond p1 p2 p3 already for s = 4 (so Garner's recombination would wrap);
+    with carried words the columns stay below 2s 2^64."""
+    M = PRIMES[0] * PRIMES[1] * PRIMES[2]
+    for s in (4, 1024, 1 << 20):
+        assert 2 * s * (s * (1 << 64)) * (1 << 32) > M
+    assert 2 * (1 << 25) * (1 << 64) < M
