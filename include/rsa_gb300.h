@@ -183,7 +183,7 @@ int rsa_batch_gcd(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *
  *   (prod n_j / n_i) mod n_i and a binary gcd per modulus: quasi-linear work,
  *   products of long numbers by three-prime number-theoretic transforms.
  *   Needs rsa_batch_gcd_tree_bytes of device memory within the context's
- *   budget (2.2 GiB for 2^17 moduli of 2048 bits, 18 GiB for 2^20) and
+ *   budget (2.7 GiB for 2^17 moduli of 2048 bits, 23 GiB for 2^20) and
  *   count (rounded up to a power of two) x nbits / 32 <= 2^26.
  * RSA_GCD_AUTO: the tree from count x nbits / 32 >= 2^18 (4096 moduli of 2048
  *   bits, 8192 of 1024, 16384 of 512) when it fits (the size limit and the
