@@ -588,6 +588,7 @@ def bgcd_measure(count: int, method: int, steps: int, warmup: int, e2e: bool = F
     torch.cuda.synchronize()
     clk = ClockSampler(0)
     clk.start()
+    time.sleep(0.3)                   # the sampler's start-up off the host thread that launches
     launches0 = ctx.stats()["kernel_launches"]
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     ev[0].record(stream)
