@@ -6,9 +6,10 @@ sharing read off known factorisations, random odd moduli (many small common
 factors) at counts that leave the trees ragged (padding leaves) and that
 reach the transform path (products above 1024 words), invalid, short and
 duplicate moduli, every leaf level of the remainder tree, the tree against
-the scan over all rows at 6000 moduli, a 2^17-modulus RSA-2048-shaped scan
-(planted pairs, divisibility of every result, sampled rows against the
-oracle), the automatic choice and the host-buffer form, and the errors.
+the scan over all rows at 6000 moduli, 2^17- and 2^20-modulus RSA-2048-shaped
+scans (planted pairs, divisibility of every result, sampled rows against the
+oracle; 2^20 is the size limit), the automatic choice and the host-buffer
+form, and the errors.
 """
 import numpy as np
 import pytest
@@ -132,6 +133,31 @@ def test_tree_large_weak_key_scan(torch_cuda, ctx):
         assert (f[k] == 0) == (gs[k] == 1) and (f[k] == 2) == (gs[k] == vals[k])
     rng = np.random.default_rng(4)
     idx = sorted(set(rng.choice(count, 6, replace=False).tolist()) | {0, count - 1, pairs[0][0], pairs[0][1]})
+    og, of = oracle.batch_gcd(rows, rows=idx)
+    assert np.array_equal(g[idx], og) and np.array_equal(f[idx], of)
+
+
+def test_tree_largest_size(torch_cuda):
+    """2^20 RSA-2048-shaped moduli, the tree's limit (2^26 modulus words:
+    transforms of 2^27 words, the first prime's 2-adic order): planted pairs
+    found, every g_i divides n_i and matches its flag, sampled rows equal the
+    oracle's."""
+    from paper_1407_1465_gb300 import RsaContext, rsa_batch_gcd_tree_bytes
+    count = 1 << 20
+    c = RsaContext(0, mem_budget_bytes=rsa_batch_gcd_tree_bytes(2048, count) + (2 << 30))
+    try:
+        rows, pairs = workloads.weak_key_moduli(count)
+        g, f = gpu_gcd(torch_cuda, c, 2048, rows)
+    finally:
+        c.close()
+    vals = workloads.rows_to_ints(rows)
+    gs = workloads.rows_to_ints(g)
+    for i, j in pairs:
+        assert f[i] >= 1 and f[j] >= 1 and gs[i] > 1
+    for k in range(count):
+        assert gs[k] >= 1 and vals[k] % gs[k] == 0
+        assert (f[k] == 0) == (gs[k] == 1) and (f[k] == 2) == (gs[k] == vals[k])
+    idx = sorted({0, 1, count // 2, count - 1, pairs[0][0], pairs[0][1], pairs[-1][0], 777777})
     og, of = oracle.batch_gcd(rows, rows=idx)
     assert np.array_equal(g[idx], og) and np.array_equal(f[idx], of)
 
