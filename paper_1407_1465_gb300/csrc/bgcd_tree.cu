@@ -751,6 +751,40 @@ __global__ void root_kernel(const uint32_t *X, uint64_t s, uint32_t *Z, uint64_t
 
 constexpr int kLeafThreads = 64;
 
+// One word of Montgomery reduction on the window t (K + 2 words) by the K-word
+// N in shared memory (word j at sN[j * bd]): t = (t + q N) / 2^32, whose low
+// word is zero by the choice of q.  Two carry chains, the even words of N and
+// then the odd ones, each a run of multiply-adds with carry.
+template <int K>
+__device__ __forceinline__ void leaf_redc_step(uint32_t (&t)[K + 2], const uint32_t *sN, uint32_t bd, uint32_t q) {
+  {
+    const uint32_t n = sN[0];
+    (void)mad_lo_cc(q, n, t[0]);
+    t[0] = madc_hi_cc(q, n, t[1]);
+  }
+#pragma unroll
+  for (int k = 1; k < K / 2; ++k) {
+    const uint32_t n = sN[(2 * k) * bd];
+    t[2 * k - 1] = madc_lo_cc(q, n, t[2 * k]);
+    t[2 * k] = madc_hi_cc(q, n, t[2 * k + 1]);
+  }
+  t[K - 1] = addc_cc(t[K], 0u);
+  t[K] = addc(t[K + 1], 0u);
+  {
+    const uint32_t n = sN[bd];
+    t[0] = mad_lo_cc(q, n, t[0]);
+    t[1] = madc_hi_cc(q, n, t[1]);
+  }
+#pragma unroll
+  for (int k = 1; k < K / 2; ++k) {
+    const uint32_t n = sN[(2 * k + 1) * bd];
+    t[2 * k] = madc_lo_cc(q, n, t[2 * k]);
+    t[2 * k + 1] = madc_hi_cc(q, n, t[2 * k + 1]);
+  }
+  t[K] = addc(t[K], 0u);
+  t[K + 1] = 0u;
+}
+
 // Per-thread shared-memory words of the leaf kernel: n (L), N = n^2 (2L; the
 // reduced value r takes its place once the reduction is done), the quotient u
 // (L); column layout (word w of thread x at w * blockDim + x).
@@ -797,26 +831,42 @@ __global__ void __launch_bounds__(kLeafThreads) tree_leaf_kernel(const uint32_t 
   for (int w = 0; w < 2 * L; ++w) t[w] = (uint32_t)w < M ? z[w] : 0u;
   t[2 * L] = 0u;
   t[2 * L + 1] = 0u;
+  if constexpr (L <= 32) {
+    // two carry chains of multiply-adds (measured faster at 512 and 1024 bits)
 #pragma unroll 1
-  for (uint32_t s = 0; s < M; ++s) {
-    const uint32_t q = t[0] * np;
-    uint64_t acc = (uint64_t)q * sN[0] + t[0];
-    uint32_t c = (uint32_t)(acc >> 32);
-#pragma unroll
-    for (int j = 1; j < 2 * L; ++j) {
-      acc = (uint64_t)q * sN[j * bd] + t[j] + c;
-      t[j - 1] = (uint32_t)acc;
-      c = (uint32_t)(acc >> 32);
+    for (uint32_t s = 0; s < M; ++s) {
+      leaf_redc_step<2 * L>(t, sN, bd, t[0] * np);
+      const uint32_t nx = 2 * L + s;
+      if (nx < M) {
+        t[2 * L - 1] = add_cc(t[2 * L - 1], z[nx]);
+        t[2 * L] = addc(t[2 * L], 0u);
+      }
     }
-    acc = (uint64_t)t[2 * L] + c;
-    t[2 * L - 1] = (uint32_t)acc;
-    t[2 * L] = t[2 * L + 1] + (uint32_t)(acc >> 32);
-    t[2 * L + 1] = 0u;
-    const uint32_t nx = 2 * L + s;
-    if (nx < M) {
-      acc = (uint64_t)t[2 * L - 1] + z[nx];
+  } else {
+    // 64-bit multiply-accumulate with a running carry: at 2048 bits the
+    // ordered carry chains need more registers than the 130-word window leaves
+    // (131072 moduli: 151 ms against 158)
+#pragma unroll 1
+    for (uint32_t s = 0; s < M; ++s) {
+      const uint32_t q = t[0] * np;
+      uint64_t acc = (uint64_t)q * sN[0] + t[0];
+      uint32_t c = (uint32_t)(acc >> 32);
+#pragma unroll
+      for (int j = 1; j < 2 * L; ++j) {
+        acc = (uint64_t)q * sN[j * bd] + t[j] + c;
+        t[j - 1] = (uint32_t)acc;
+        c = (uint32_t)(acc >> 32);
+      }
+      acc = (uint64_t)t[2 * L] + c;
       t[2 * L - 1] = (uint32_t)acc;
-      t[2 * L] += (uint32_t)(acc >> 32);
+      t[2 * L] = t[2 * L + 1] + (uint32_t)(acc >> 32);
+      t[2 * L + 1] = 0u;
+      const uint32_t nx = 2 * L + s;
+      if (nx < M) {
+        acc = (uint64_t)t[2 * L - 1] + z[nx];
+        t[2 * L - 1] = (uint32_t)acc;
+        t[2 * L] += (uint32_t)(acc >> 32);
+      }
     }
   }
   // t <= N: subtract N once when t >= N

@@ -188,6 +188,21 @@ def test_tree_auto_choice_and_host_form(torch_cuda, ctx):
     assert np.array_equal(tg[idx], og) and np.array_equal(tf[idx], of)
 
 
+def test_tree_degenerate_sets(torch_cuda, ctx):
+    """One modulus (the product of the others is empty: g = 1, flag 0), only
+    invalid moduli (every flag -1, zero rows), one valid among invalid ones."""
+    n = 1000003 * 1000033
+    for nbits in (512, 2048):
+        L = nbits // 32
+        for vals, want_g, want_f in (([n], [1], [0]), ([0, 1, 2, 4, 10], [0] * 5, [-1] * 5),
+                                     ([6, n, 1000003 * 2], [0, 1, 0], [-1, 0, -1])):
+            rows = workloads.ints_to_rows(vals, L)
+            g, f = gpu_gcd(torch_cuda, ctx, nbits, rows)
+            assert workloads.rows_to_ints(g) == want_g and f.tolist() == want_f
+            og, of = oracle.batch_gcd(rows)
+            assert np.array_equal(g, og) and np.array_equal(f, of)
+
+
 def test_tree_errors(torch_cuda, ctx):
     from paper_1407_1465_gb300 import RsaError, rsa_batch_gcd_ex, rsa_batch_gcd_tree_bytes
     t = torch_cuda.zeros((4, 64), dtype=torch_cuda.int32, device="cuda")
