@@ -1060,7 +1060,6 @@ struct Runner {
   uint32_t *base;
   const Plan &P;
   Primes pr;                                 // tables and Garner constants; scale set per product
-  uint32_t root_m[3], iroot_m[3];
   int launches = 0;
 
   uint32_t *at(uint64_t off) const { return base + off; }
@@ -1246,7 +1245,7 @@ int batch_gcd_tree_run(Ctx *c, uint32_t nbits, uint64_t count, const uint32_t *m
   int rc;
   if ((rc = c->ensure(w.gcd_tree, P.words * 4)) || (rc = c->ensure(w.gcd_tw, 6 * P.nmax * 4))) return rc;
   NvtxRange range("rsa_batch_gcd(tree)");
-  Runner R{c, s, static_cast<uint32_t *>(w.gcd_tree.ptr), P, {}, {}, {}, 0};
+  Runner R{c, s, static_cast<uint32_t *>(w.gcd_tree.ptr), P, {}, 0};
   uint32_t *tw = static_cast<uint32_t *>(w.gcd_tw.ptr);
   const bool rebuild = w.gcd_tw_ptr != w.gcd_tw.ptr || w.gcd_tw_n < P.nmax;
   const uint64_t tn = rebuild ? P.nmax : w.gcd_tw_n;      // table stride: the length built
