@@ -272,7 +272,8 @@ int rsa_crt_decrypt_noalloc(const uint32_t *key_record, uint32_t nbits, uint64_t
  * free slot, and runs up to max_inflight_batches batches at once on separate
  * streams, so requests arriving while others are on the GPU start without
  * waiting for them (continuous batching) and a batch finishes at its own size's
- * latency.  Admission is by bytes in flight: every batch takes a range of one
+ * latency.  Once the operations in flight fill a wave of the GPU, at most three
+ * batches run at once, so waiting requests gather into larger batches.  Admission is by bytes in flight: every batch takes a range of one
  * device arena of mem_budget_bytes (messages, results and per-operation
  * metadata: 8L + 17 bytes per operation, plus alignment), and a batch that does
  * not fit in a free range waits until batches in flight finish and give their
