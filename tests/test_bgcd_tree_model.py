@@ -465,3 +465,132 @@ def test_uncarried_square_would_pass_the_primes_range():
     for s in (4, 1024, 1 << 20):
         assert 2 * s * (s * (1 << 64)) * (1 << 32) > M
     assert 2 * (1 << 25) * (1 << 64) < M
+
+
+# ---------------------------------------------------------------- carry scan model
+
+CARRY_WORDS, CARRY_THREADS = 16, 256
+CARRY_BLOCK = CARRY_WORDS * CARRY_THREADS
+
+
+def lookahead_in(g, p, cin, bits):
+    """Carry into each of `bits` positions and out of the top, for generate
+    bits g and propagate bits p (disjoint): the bits of (a + g + cin) ^ a ^ g
+    with a = g | p, as the kernels compute them with one addition."""
+    a = g | p
+    s = a + g + cin
+    return (s ^ a ^ g) & ((1 << bits) - 1), (s >> bits) & 1
+
+
+def carry_kernels(cols, addend, lo, hi):
+    """The three carry kernels on one product: columns cols[j] (integers below
+    2^96 as the recombination gives them), an addend (list of words), words
+    [lo, hi) of sum_j cols[j] 2^(32 j) + addend returned."""
+    n = len(cols)
+
+    def word_sum(c):
+        v = addend[c] if c < len(addend) else 0
+        if 0 <= c < n:
+            v += cols[c] & MASK
+        if 0 <= c - 1 < n:
+            v += (cols[c - 1] >> 32) & MASK
+        if 0 <= c - 2 < n:
+            v += cols[c - 2] >> 64
+        return v
+
+    nb = -(-hi // CARRY_BLOCK)
+    # pass 1: per thread, words before inter-word carries and its masks
+    words, masks = {}, {}
+    for b in range(nb):
+        for t in range(CARRY_THREADS):
+            c0 = b * CARRY_BLOCK + t * CARRY_WORDS
+            g = p = 0
+            if c0 < hi:
+                prev = (word_sum(c0 - 1) >> 32) if c0 >= 1 else 0
+                for m in range(CARRY_WORDS):
+                    s = word_sum(c0 + m)
+                    v = (s & MASK) + prev
+                    prev = s >> 32
+                    assert prev <= 3 and v < (1 << 32) + 3
+                    words[c0 + m] = v & MASK
+                    g |= (v >> 32) << m
+                    p |= (1 if v == MASK else 0) << m
+            masks[b, t] = (g, p)
+
+    def run_gp(g, p):
+        a = g | p
+        c0 = ((a + g) >> CARRY_WORDS) & 1
+        c1 = ((a + g + 1) >> CARRY_WORDS) & 1
+        return c0, c1 & (1 - c0)
+
+    def block_carries(b, cin_block):
+        """carry into each thread's run: lanes by one addition per warp, warps by one per block"""
+        G = [run_gp(*masks[b, t])[0] for t in range(CARRY_THREADS)]
+        P = [run_gp(*masks[b, t])[1] for t in range(CARRY_THREADS)]
+        wg, wp, lane_bits = [], [], []
+        for w in range(CARRY_THREADS // 32):
+            gm = sum(G[32 * w + l] << l for l in range(32))
+            pm = sum(P[32 * w + l] << l for l in range(32))
+            a = gm | pm
+            g0 = (a + gm) >> 32
+            g1 = (a + gm + 1) >> 32
+            wg.append(g0)
+            wp.append(g1 & (1 - g0))
+            lane_bits.append((gm, pm))
+        bgm = sum(x << i for i, x in enumerate(wg))
+        bpm = sum(x << i for i, x in enumerate(wp))
+        nw = CARRY_THREADS // 32
+        blk_g = ((bgm | bpm) + bgm) >> nw & 1
+        blk_p = (((bgm | bpm) + bgm + 1) >> nw & 1) & (1 - blk_g)
+        warp_in, _ = lookahead_in(bgm, bpm, cin_block, nw)
+        into = []
+        for w in range(nw):
+            gm, pm = lane_bits[w]
+            lane_in, _ = lookahead_in(gm, pm, (warp_in >> w) & 1, 32)
+            into += [(lane_in >> l) & 1 for l in range(32)]
+        return blk_g, blk_p, into
+
+    # pass 2: the product's block carries, 32 blocks per step
+    flags = [block_carries(b, 0)[:2] for b in range(nb)]
+    cin_blocks, cin = [], 0
+    for base in range(0, nb, 32):
+        gm = sum(flags[b][0] << (b - base) for b in range(base, min(nb, base + 32)))
+        pm = sum(flags[b][1] << (b - base) for b in range(base, min(nb, base + 32)))
+        into, cin = lookahead_in(gm, pm, cin, 32)
+        cin_blocks += [(into >> (b - base)) & 1 for b in range(base, min(nb, base + 32))]
+    # pass 3: increments
+    out = dict(words)
+    for b in range(nb):
+        _, _, tin = block_carries(b, cin_blocks[b])
+        for t in range(CARRY_THREADS):
+            g, p = masks[b, t]
+            wi, _ = lookahead_in(g, p, tin[t], CARRY_WORDS)
+            for m in range(CARRY_WORDS):
+                c = b * CARRY_BLOCK + t * CARRY_WORDS + m
+                if (wi >> m) & 1 and c in out:
+                    out[c] = (out[c] + 1) & MASK
+    return [out.get(c, 0) for c in range(lo, hi)]
+
+
+@pytest.mark.parametrize("case", ["random", "ones", "ripple"])
+def test_carry_kernels_equal_integer_sums(case):
+    """The carry passes on columns below 2^96 (the recombination's range), with
+    an addend and an output slice, equal the integer sum: random columns;
+    columns that make long runs of all-ones words across thread, warp and
+    block boundaries; a single carry rippling through 2.5 blocks."""
+    rng = random.Random(hash(case) & 0xffff)
+    n = 2 * CARRY_BLOCK + 1500
+    if case == "random":
+        cols = [rng.getrandbits(90) for _ in range(n)]
+        addend = [rng.getrandbits(32) for _ in range(n + 1)]
+    elif case == "ones":
+        cols = [MASK if rng.random() < 0.97 else rng.getrandbits(33) for _ in range(n)]
+        addend = [0] * (n + 1)
+    else:
+        cols = [MASK] * n
+        cols[0] = MASK
+        addend = [1]
+    total = sum(c << (32 * j) for j, c in enumerate(cols)) + sum(a << (32 * j) for j, a in enumerate(addend))
+    lo, hi = 37, n + 2
+    got = carry_kernels(cols, addend, lo, hi)
+    assert got == words(total >> (32 * lo), hi - lo)
