@@ -594,3 +594,76 @@ def test_carry_kernels_equal_integer_sums(case):
     lo, hi = 37, n + 2
     got = carry_kernels(cols, addend, lo, hi)
     assert got == words(total >> (32 * lo), hi - lo)
+
+
+def school_carry(cols, addend, lo, hi, threads=128):
+    """The schoolbook kernel's carries for one product per CTA: thread t takes
+    the run of r = ceil(hi / threads) words from t r, its generate/propagate
+    bits combine within each warp and across the warps by one addition each."""
+    n = len(cols)
+
+    def word_sum(c):
+        v = addend[c] if c < len(addend) else 0
+        if 0 <= c < n:
+            v += cols[c] & MASK
+        if 0 <= c - 1 < n:
+            v += (cols[c - 1] >> 32) & MASK
+        if 0 <= c - 2 < n:
+            v += cols[c - 2] >> 64
+        return v
+
+    r = -(-hi // threads)
+    assert r <= 32
+    runs = []
+    for t in range(threads):
+        c0, c1 = t * r, min(t * r + r, hi)
+        prev = (word_sum(c0 - 1) >> 32) if 1 <= c0 <= hi else 0
+        g = p = 0
+        for c in range(c0, c1):
+            s = word_sum(c)
+            v = (s & MASK) + prev
+            prev = s >> 32
+            g |= (v >> 32) << (c - c0)
+            p |= (1 if v == MASK else 0) << (c - c0)
+        a = g | p
+        G = ((a + g) >> r) & 1
+        P = (((a + g + 1) >> r) & 1) & (1 - G)
+        runs.append((c0, c1, g, p, G, P))
+    nw = threads // 32
+    warp_gp = []
+    for w in range(nw):
+        gm = sum(runs[32 * w + l][4] << l for l in range(32))
+        pm = sum(runs[32 * w + l][5] << l for l in range(32))
+        a = gm | pm
+        g0 = (a + gm) >> 32
+        warp_gp.append((g0, ((a + gm + 1) >> 32) & (1 - g0), gm, pm))
+    bgm = sum(x[0] << i for i, x in enumerate(warp_gp))
+    bpm = sum(x[1] << i for i, x in enumerate(warp_gp))
+    warp_in, _ = lookahead_in(bgm, bpm, 0, nw)
+    out = {}
+    for w in range(nw):
+        _, _, gm, pm = warp_gp[w]
+        lane_in, _ = lookahead_in(gm, pm, (warp_in >> w) & 1, 32)
+        for l in range(32):
+            c0, c1, g, p, _, _ = runs[32 * w + l]
+            into, _ = lookahead_in(g, p, (lane_in >> l) & 1, r)
+            prev = (word_sum(c0 - 1) >> 32) if 1 <= c0 <= hi else 0
+            for c in range(c0, c1):
+                s = word_sum(c)
+                out[c] = ((s & MASK) + prev + ((into >> (c - c0)) & 1)) & MASK
+                prev = s >> 32
+    return [out[c] for c in range(lo, hi)]
+
+
+@pytest.mark.parametrize("nc,hi", [(130, 130), (512, 512), (1024, 1025), (2048, 2049)])
+def test_school_carry_equals_integer_sums(nc, hi):
+    """Schoolbook column sums (below 2^74 for products of up to 1024 words),
+    random and all-ones heavy, with an addend one word longer than the product
+    (the remainder step's shape), against the integer sum."""
+    rng = random.Random(nc)
+    for ones in (False, True):
+        cols = [(MASK if ones and rng.random() < 0.95 else rng.getrandbits(74)) for _ in range(nc)]
+        addend = [rng.getrandbits(32) for _ in range(hi)]
+        total = sum(c << (32 * j) for j, c in enumerate(cols)) + sum(a << (32 * j) for j, a in enumerate(addend))
+        got = school_carry(cols, addend, 3, hi)
+        assert got == words(total >> 96, hi - 3)
