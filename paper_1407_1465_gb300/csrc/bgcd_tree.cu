@@ -27,9 +27,9 @@
 // modulo three primes p = c 2^e + 1 (2013265921, 3221225473, 3489660929; every
 // column of a product of operands of up to 2^26 words is below their
 // product), recombined by Garner's method, with the carries resolved by a
-// carry-lookahead scan.  Every multiplication takes an optional addend, a
-// complemented operand and an output slice, which the Newton steps and the
-// remainder step need.
+// carry-lookahead scan.  Every multiplication takes an optional addend, an
+// output slice and operand rows chosen by the node's index (its parent's or
+// sibling's), which the Newton steps and the remainder steps need.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -64,13 +64,12 @@ struct Primes {
   const uint32_t *tw[3], *itw[3];           // nested twiddle tables: tw[len + j] = w_(2 len)^j R mod p
 };
 
-// Operand i of a batch: row (i >> shift) ^ xr at p + row * stride (xr = 1:
-// the sibling's row), `words` words (zero beyond), complemented bitwise when
-// flip is set.
+// Operand i of a batch: row (i >> shift) ^ xr at p + row * stride (shift 1:
+// the parent's row; xr = 1: the sibling's row), `words` words (zero beyond).
 struct Opnd {
   const uint32_t *p;
   uint64_t stride;
-  uint32_t shift, words, flip, xr;
+  uint32_t shift, words, xr;
 };
 
 // Output of product i: words [lo, hi) of the result at p + i * stride.
@@ -82,8 +81,7 @@ struct Out {
 
 __device__ __forceinline__ uint32_t opnd_word(const Opnd &o, uint64_t i, uint32_t j) {
   if (j >= o.words) return 0u;
-  const uint32_t w = o.p[((i >> o.shift) ^ o.xr) * o.stride + j];
-  return o.flip ? ~w : w;
+  return o.p[((i >> o.shift) ^ o.xr) * o.stride + j];
 }
 
 // The reductions below take the borrow of a subtraction as a mask m (0 or all
@@ -1205,12 +1203,11 @@ struct Runner {
   }
 };
 
-Opnd opnd(const uint32_t *p, uint64_t stride, uint32_t words, uint32_t shift = 0, uint32_t flip = 0,
-          uint32_t xr = 0) {
-  return Opnd{p, stride, shift, words, flip, xr};
+Opnd opnd(const uint32_t *p, uint64_t stride, uint32_t words, uint32_t shift = 0, uint32_t xr = 0) {
+  return Opnd{p, stride, shift, words, xr};
 }
 
-const Opnd kNone{nullptr, 0, 0, 0, 0, 0};
+const Opnd kNone{nullptr, 0, 0, 0, 0};
 
 }  // namespace
 }  // namespace tree
@@ -1343,7 +1340,7 @@ int batch_gcd_tree_run(Ctx *c, uint32_t nbits, uint64_t count, const uint32_t *m
                         false)))
           return rc;
       }
-    } else if ((rc = R.mul(opnd(Y, k, k32, 0, 0, 1), opnd(mup, 2 * k, k32, 1), kNone, Out{mu, k, 0, k32}, cnt,
+    } else if ((rc = R.mul(opnd(Y, k, k32, 0, 1), opnd(mup, 2 * k, k32, 1), kNone, Out{mu, k, 0, k32}, cnt,
                            false))) {
       return rc;
     }

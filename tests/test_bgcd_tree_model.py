@@ -19,8 +19,8 @@ steps, the transform indexing) are pinned before the GPU runs them:
     one conditional subtraction, exact division by n_i, gcd with n_i;
   * products by three-prime number-theoretic transforms of 32-bit words
     (decimation in frequency forward, in time inverse, nested twiddle table
-    tw[len + j] = w_(2len)^j), recombined by Garner's method, with an addend,
-    a complemented operand and an output slice.
+    tw[len + j] = w_(2len)^j), recombined by Garner's method, with an addend
+    and an output slice.
 """
 import math
 import random
@@ -261,8 +261,8 @@ def garner(r):
     return v1 + p1 * v2 + p1 * p2 * v3
 
 
-def ntt_bmul(A, B, na, nb, D=None, flip_b=False, lo=0, hi=None, nmax=64):
-    """Batched A_i * (B_i or ~B_i) + D_i, words [lo, hi), through the transform path."""
+def ntt_bmul(A, B, na, nb, D=None, lo=0, hi=None, nmax=64):
+    """Batched A_i * B_i + D_i, words [lo, hi), through the transform path."""
     cnt = len(A)
     n = 1
     while n < na + nb:
@@ -278,8 +278,6 @@ def ntt_bmul(A, B, na, nb, D=None, flip_b=False, lo=0, hi=None, nmax=64):
         for i in range(cnt):
             aw = words(A[i], na)
             bw = words(B[i], nb)
-            if flip_b:
-                bw = [w ^ MASK for w in bw]
             for j in range(na):
                 fa[i * n + j] = aw[j] % p
             for j in range(nb):
@@ -311,15 +309,17 @@ def test_transform_product(na, nb, cnt):
     assert got == [a * b for a, b in zip(A, B)]
 
 
-def test_transform_addend_flip_slice():
+def test_transform_addend_slice():
+    """The remainder step's shape: an addend one word longer than the product,
+    the upper half plus one word kept."""
     rng = random.Random(9)
     na, nb = 8, 8
     A = [rng.getrandbits(W * na) for _ in range(2)]
     B = [rng.getrandbits(W * nb) for _ in range(2)]
     D = [rng.getrandbits(W * (na + nb + 1)) for _ in range(2)]
     lo, hi = 8, 17
-    got = ntt_bmul(A, B, na, nb, D=D, flip_b=True, lo=lo, hi=hi)
-    want = [((a * ((~b) % (1 << (W * nb))) + d) >> (W * lo)) % (1 << (W * (hi - lo))) for a, b, d in zip(A, B, D)]
+    got = ntt_bmul(A, B, na, nb, D=D, lo=lo, hi=hi)
+    want = [((a * b + d) >> (W * lo)) % (1 << (W * (hi - lo))) for a, b, d in zip(A, B, D)]
     assert got == want
 
 
