@@ -167,8 +167,8 @@ int rsa_mr_batch(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *c
  * 2 when g_i = n_i (a duplicate modulus, or each prime of n_i is shared:
  * separate it with pairwise gcds), -1 for an invalid n_i.  At least one of
  * gcds and flags must be given.  All pointers are device pointers (rows
- * 16-byte aligned).  The form is chosen as rsa_batch_gcd_ex with RSA_GCD_AUTO
- * chooses it.  Enqueued on `stream`.  Errors: RSA_ERR_ARG (null or misaligned
+ * 16-byte aligned).  The form is the one rsa_batch_gcd_ex picks with
+ * RSA_GCD_AUTO.  Enqueued on `stream`.  Errors: RSA_ERR_ARG (null or misaligned
  * pointers, count above 2^26), RSA_ERR_UNSUPPORTED, RSA_ERR_NOMEM,
  * RSA_ERR_CUDA. */
 int rsa_batch_gcd(rsa_ctx *ctx, uint32_t nbits, uint64_t count, const uint32_t *moduli, uint32_t *gcds,
